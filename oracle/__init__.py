@@ -1,0 +1,370 @@
+"""CPU oracle for the GIRG / HRG sampler (arXiv 1905.06706).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this package.  It wraps the
+plain FP64 C restatement of the paper in ``girg_oracle.c`` (see the header of
+that file for what each function follows) with ``ctypes`` and ``numpy``; it
+shares no code with the CUDA library.
+
+The C file is compiled on first use (or by :func:`build`) with
+``-ffp-contract=off`` so that the deterministic elementary functions give the
+same bits on every IEEE machine.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "girg_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libgirg_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MAXL = 64
+
+# stats indices of the cell-pair oracle
+STAT_NAMES = (
+    "type1_pairs",
+    "type2_items",
+    "jump_draws",
+    "type2_candidates",
+    "type1_items",
+    "cell_pairs_visited",
+    "type1_edges",
+    "type2_edges",
+)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's shared library (gcc, FP contraction off)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        i64, i32, u32, u64, dbl = (ctypes.c_int64, ctypes.c_int, ctypes.c_uint32,
+                                   ctypes.c_uint64, ctypes.c_double)
+        sig = {
+            "orc_philox": (None, [P, P, P]),
+            "orc_uniform": (dbl, [u32, u32]),
+            "orc_det_log": (dbl, [dbl]),
+            "orc_det_log1p": (dbl, [dbl]),
+            "orc_det_exp": (dbl, [dbl]),
+            "orc_det_pow": (dbl, [dbl, dbl]),
+            "orc_det_sinpi": (dbl, [dbl]),
+            "orc_det_acosh": (dbl, [dbl]),
+            "orc_exact_sum": (dbl, [i64, P]),
+            "orc_girg_points": (None, [i64, i32, dbl, dbl, u64, P, P]),
+            "orc_hrg_points": (None, [i64, dbl, dbl, u64, P, P]),
+            "orc_hrg_weight": (dbl, [dbl, dbl]),
+            "orc_girg_p": (dbl, [i32, dbl, dbl, dbl, dbl, dbl, u32]),
+            "orc_girg_thresh_edge": (i32, [i32, dbl, dbl, dbl, dbl, u32]),
+            "orc_hrg_coshd": (dbl, [dbl, dbl, u32]),
+            "orc_hrg_p": (dbl, [dbl, dbl, dbl, dbl, u32]),
+            "orc_pair_coin": (dbl, [u64, u32, u32]),
+            "orc_girg_allpairs": (i64, [i64, i32, P, P, dbl, dbl, dbl, u64, P, i64]),
+            "orc_hrg_allpairs": (i64, [i64, P, P, dbl, dbl, u64, P, i64]),
+            "orc_morton": (u64, [P, i32, i32]),
+            "orc_cell_linf": (u32, [u64, u64, i32, i32]),
+            "orc_level_cap": (i32, [i64, i32]),
+            "orc_chunk_log": (i32, [dbl]),
+            "orc_girg_cellpairs": (i64, [i64, i32, P, P, dbl, dbl, dbl, dbl, u64, P, i64,
+                                         P, P, P, P, P, i64, P, i32, i32]),
+            "orc_hrg_cellpairs": (i64, [i64, P, P, dbl, dbl, u64, P, i64, P, P, P, P, P,
+                                        i64, P, i32, i32]),
+            "orc_girg_avg_degree": (dbl, [dbl, i64, i32, dbl, P, dbl]),
+            "orc_girg_solve_c": (dbl, [dbl, i64, i32, dbl, P, dbl]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+# ---------------------------------------------------------------- primitives
+
+def philox(ctr, key):
+    """Philox4x32-10 of one 128-bit counter under a 64-bit key (4 + 2 words)."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    _load().orc_philox(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def uniform(lo: int, hi: int) -> float:
+    return _load().orc_uniform(lo, hi)
+
+
+def det_log(x):
+    return _load().orc_det_log(float(x))
+
+
+def det_log1p(x):
+    return _load().orc_det_log1p(float(x))
+
+
+def det_exp(x):
+    return _load().orc_det_exp(float(x))
+
+
+def det_pow(x, y):
+    return _load().orc_det_pow(float(x), float(y))
+
+
+def det_sinpi(x):
+    return _load().orc_det_sinpi(float(x))
+
+
+def det_acosh(x):
+    return _load().orc_det_acosh(float(x))
+
+
+def exact_sum(w) -> float:
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    return _load().orc_exact_sum(len(w), _ptr(w))
+
+
+def morton(x, d: int, level: int) -> int:
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.uint32))
+    return _load().orc_morton(_ptr(x), d, level)
+
+
+def cell_linf(A: int, B: int, d: int, level: int) -> int:
+    return _load().orc_cell_linf(A, B, d, level)
+
+
+def level_cap(n: int, d: int) -> int:
+    return _load().orc_level_cap(n, d)
+
+
+def chunk_log(pbar: float) -> int:
+    return _load().orc_chunk_log(pbar)
+
+
+def pair_coin(seed: int, u: int, v: int) -> float:
+    return _load().orc_pair_coin(seed, u, v)
+
+
+def girg_p(d, T, c, W, wu, wv, D) -> float:
+    return _load().orc_girg_p(d, T, c, W, wu, wv, D)
+
+
+def girg_thresh_edge(d, c, W, wu, wv, D) -> bool:
+    return bool(_load().orc_girg_thresh_edge(d, c, W, wu, wv, D))
+
+
+def hrg_coshd(ru, rv, D) -> float:
+    return _load().orc_hrg_coshd(ru, rv, D)
+
+
+def hrg_p(T, R, ru, rv, D) -> float:
+    return _load().orc_hrg_p(T, R, ru, rv, D)
+
+
+def hrg_weight(r, R) -> float:
+    return _load().orc_hrg_weight(r, R)
+
+
+# ---------------------------------------------------------------- model inputs
+
+def girg_points(n: int, d: int, beta: float, w_min: float, seed: int):
+    """Weights (n,) float64 and positions (n, d) uint32 of the generated GIRG."""
+    w = np.zeros(n, dtype=np.float64)
+    X = np.zeros((n, d), dtype=np.uint32)
+    _load().orc_girg_points(n, d, beta, w_min, seed, _ptr(w), _ptr(X))
+    return w, X
+
+
+def hrg_points(n: int, alpha: float, R: float, seed: int):
+    """Radii (n,) float64 and angular fixed-point coordinates (n,) uint32."""
+    r = np.zeros(n, dtype=np.float64)
+    X = np.zeros(n, dtype=np.uint32)
+    _load().orc_hrg_points(n, alpha, R, seed, _ptr(r), _ptr(X))
+    return r, X
+
+
+# ---------------------------------------------------------------- samplers
+
+def _edges_array(cap):
+    return np.zeros((max(cap, 1), 2), dtype=np.uint32)
+
+
+def girg_allpairs(X, w, W, T, c, seed, cap=None):
+    """Oracle 1: (m, 2) uint32 edges (u < v) of the quadratic generator."""
+    X = np.ascontiguousarray(X, dtype=np.uint32)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    n, d = X.shape
+    if cap is None:
+        cap = 1 << 16
+    while True:
+        e = _edges_array(cap)
+        m = _load().orc_girg_allpairs(n, d, _ptr(X), _ptr(w), W, T, c, seed, _ptr(e), cap)
+        if m <= cap:
+            return e[:m].copy()
+        cap = m
+
+
+def hrg_allpairs(X, r, R, T, seed, cap=None):
+    X = np.ascontiguousarray(X, dtype=np.uint32)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    n = len(X)
+    if cap is None:
+        cap = 1 << 16
+    while True:
+        e = _edges_array(cap)
+        m = _load().orc_hrg_allpairs(n, _ptr(X), _ptr(r), R, T, seed, _ptr(e), cap)
+        if m <= cap:
+            return e[:m].copy()
+        cap = m
+
+
+class CellPairResult:
+    """Edges, statistics, sorted order, tables and (optionally) items of oracle 2."""
+
+    def __init__(self, edges, stats, order, itab, wtab, items):
+        self.edges = edges
+        self.stats = dict(zip(STAT_NAMES, (int(s) for s in stats[:8])))
+        self.visited_neighbour = stats[8:8 + 33].copy()
+        self.visited_distant = stats[8 + 33:8 + 66].copy()
+        self.visited_self = stats[8 + 66:8 + 99].copy()
+        self.order = order
+        L = int(itab[0])
+        self.L = L
+        self.level_cap = int(itab[1])
+        self.max_level = int(itab[2])
+        self.I = itab[3:3 + L].astype(np.int64)
+        self.CL = itab[3 + MAXL:3 + MAXL + MAXL * MAXL].reshape(MAXL, MAXL)[:L, :L].astype(
+            np.int64)
+        self.wmax = wtab[:L].copy()
+        self.layer_count = wtab[MAXL:MAXL + L].astype(np.int64)
+        self.items = items
+
+
+ITEM_FIELDS = ("type", "level", "A", "B", "i", "j", "a_lo", "a_hi", "b_lo", "b_hi", "tri",
+               "pbar")
+
+
+def _items_to_records(raw, k):
+    raw = raw[:k]
+    out = {}
+    for col, name in enumerate(ITEM_FIELDS):
+        if name == "pbar":
+            out[name] = raw[:, col].copy().view(np.float64)
+        else:
+            out[name] = raw[:, col].copy()
+    return out
+
+
+def girg_cellpairs(X, w, w_min, W, T, c, seed, cap=None, want_items=False, skip_sampling=False,
+                   items_cap=None, level_cap=0):
+    """Oracle 2 for GIRGs (Algorithm 1 with App. B.1)."""
+    X = np.ascontiguousarray(X, dtype=np.uint32)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    n, d = X.shape
+    if cap is None:
+        cap = 1 << 16
+    while True:
+        e = _edges_array(cap)
+        stats = np.zeros(8 + 99, dtype=np.int64)
+        order = np.zeros(max(n, 1), dtype=np.int64)
+        itab = np.zeros(3 + MAXL + MAXL * MAXL, dtype=np.int32)
+        wtab = np.zeros(2 * MAXL, dtype=np.float64)
+        nitems = np.zeros(1, dtype=np.int64)
+        icap = items_cap if items_cap is not None else (1 << 20)
+        items = np.zeros((icap if want_items else 1, 12), dtype=np.int64)
+        m = _load().orc_girg_cellpairs(
+            n, d, _ptr(X), _ptr(w), w_min, W, T, c, seed, _ptr(e), cap, _ptr(stats),
+            _ptr(order), _ptr(itab), _ptr(wtab), _ptr(items) if want_items else None,
+            icap if want_items else 0, _ptr(nitems), 1 if skip_sampling else 0, level_cap)
+        if want_items and nitems[0] > icap:
+            items_cap = int(nitems[0])
+            continue
+        if m <= cap:
+            recs = _items_to_records(items, int(nitems[0])) if want_items else None
+            return CellPairResult(e[:m].copy(), stats, order[:n], itab, wtab, recs)
+        cap = m
+
+
+def hrg_cellpairs(X, r, R, T, seed, cap=None, want_items=False, skip_sampling=False,
+                  items_cap=None, level_cap=0):
+    """Oracle 2 for HRGs through the HRG -> GIRG mapping of Sec. 2.3."""
+    X = np.ascontiguousarray(X, dtype=np.uint32)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    n = len(X)
+    if cap is None:
+        cap = 1 << 16
+    while True:
+        e = _edges_array(cap)
+        stats = np.zeros(8 + 99, dtype=np.int64)
+        order = np.zeros(max(n, 1), dtype=np.int64)
+        itab = np.zeros(3 + MAXL + MAXL * MAXL, dtype=np.int32)
+        wtab = np.zeros(2 * MAXL, dtype=np.float64)
+        nitems = np.zeros(1, dtype=np.int64)
+        icap = items_cap if items_cap is not None else (1 << 20)
+        items = np.zeros((icap if want_items else 1, 12), dtype=np.int64)
+        m = _load().orc_hrg_cellpairs(
+            n, _ptr(X), _ptr(r), R, T, seed, _ptr(e), cap, _ptr(stats), _ptr(order),
+            _ptr(itab), _ptr(wtab), _ptr(items) if want_items else None,
+            icap if want_items else 0, _ptr(nitems), 1 if skip_sampling else 0, level_cap)
+        if want_items and nitems[0] > icap:
+            items_cap = int(nitems[0])
+            continue
+        if m <= cap:
+            recs = _items_to_records(items, int(nitems[0])) if want_items else None
+            return CellPairResult(e[:m].copy(), stats, order[:n], itab, wtab, recs)
+        cap = m
+
+
+# ---------------------------------------------------------------- degree / c
+
+def girg_avg_degree(c, w, d, T, W=None):
+    """Expected average degree f(c) of App. B.2 for the given weights."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    if W is None:
+        W = exact_sum(w)
+    return _load().orc_girg_avg_degree(c, len(w), d, T, _ptr(w), W)
+
+
+def girg_solve_c(target, w, d, T, W=None):
+    """The c of Eq. 1 whose expected average degree is ``target`` (App. B.2)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    if W is None:
+        W = exact_sum(w)
+    return _load().orc_girg_solve_c(target, len(w), d, T, _ptr(w), W)
+
+
+def edge_set(edges) -> set:
+    """Set of (u, v) tuples with u < v from an (m, 2) array."""
+    e = np.asarray(edges, dtype=np.int64)
+    if len(e) == 0:
+        return set()
+    key = np.minimum(e[:, 0], e[:, 1]) * (1 << 32) + np.maximum(e[:, 0], e[:, 1])
+    return set(key.tolist())

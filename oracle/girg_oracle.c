@@ -1,0 +1,1243 @@
+/*
+ * CPU oracle for the GIRG / HRG sampler of Blaesius, Friedrich, Katzmann,
+ * Meyer, Penschuck and Weyand, "Efficiently Generating Geometric
+ * Inhomogeneous and Hyperbolic Random Graphs" (arXiv 1905.06706).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The tests, the smoke check and the CPU-baseline
+ * leg of the benchmark call this file to check the CUDA library; the
+ * library never calls it, and the two share no code, header or constant
+ * table.  Everything here is plain, sequential FP64 C, written for a reader
+ * to check against the paper by eye, not for speed.
+ *
+ * Contents
+ *   - Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), the counter-based
+ *     generator both sides implement from its published definition.
+ *   - det_log / det_log1p / det_exp / det_sinpi: elementary functions built
+ *     only from IEEE +, -, *, / and exact power-of-two scaling (argument
+ *     reduction by powers of two and ln 2, then the atanh / Taylor series).
+ *     They are evaluated in a fixed operation order so that any IEEE machine
+ *     with FMA contraction disabled reproduces them bit for bit.
+ *   - Model inputs: Pareto weights (Sec. 2.1, Sec. 5.1 step 1), uniform torus
+ *     positions in 32-bit fixed point (Sec. 2.1), HRG radii and angles
+ *     (Sec. 2.2) and the HRG->GIRG mapping (Sec. 2.3).
+ *   - Eq. 1 and its threshold variant (Sec. 2.1); the HRG connection
+ *     probability p_T(d) (Sec. 2.2) with cosh d in the cancellation-free form
+ *     cosh(r_u - r_v) + 2 sinh r_u sinh r_v sin^2(dtheta/2).
+ *   - Oracle 1: the quadratic all-pairs generator (Table 1, "Pairwise").
+ *   - Oracle 2: the cell-pair sampler, Algorithm 1 (Sec. 3.3) run
+ *     recursively from the root pair, with weight buckets and levels
+ *     (Sec. 3.1), geometric jumps (Sec. 3.2), Morton order and prefix sums
+ *     (Sec. 3.4, Lemma 1) and the double-counting rules (App. B.1).
+ *   - The expected-average-degree formula and the binary search for c
+ *     (Sec. 4.1, App. B.2).
+ *
+ * Parity unpinned: none of the functions here lacks a pin in
+ * tests/test_oracle_*.py (Philox by the Random123 known-answer vectors and an
+ * independent implementation, the elementary functions against libm and
+ * mpmath, the samplers by brute-force partition, bound and binomial tests,
+ * the degree formula by numerical integration and Monte Carlo).
+ *
+ * Conventions shared with the CUDA library (each side implements them on
+ * its own):
+ *   key of every Philox call  = (seed_lo, seed_hi) unless stated otherwise
+ *   uniform from two words    = (2*(bits64 >> 12) + 1) * 2^-53  in (0,1),
+ *                               bits64 = hi << 32 | lo
+ *   weight of vertex v        = w_min * U^(-1/(beta-1)),
+ *                               U from ctr (v_lo, v_hi, TAG_WEIGHT, 0)
+ *   coordinate k of vertex v  = word (k mod 4) of ctr (v_lo, v_hi, TAG_POS, k/4)
+ *   HRG radius of vertex v    = acosh(1 + U (cosh(alpha R) - 1)) / alpha,
+ *                               U from ctr (v_lo, v_hi, TAG_RADIUS, 0)
+ *   type-I coin of pair u<v   = U from words 0,1 of ctr (u, v, TAG_PAIR, 0)
+ *   type-II item key          = words 0,1 of ctr (A, B, l|i<<5|j<<11|TAG_ITEM<<17, 0)
+ *   type-II draw t of chunk h = Philox with the item key, ctr (h_lo, h_hi, t, TAG_DRAW);
+ *                               words 0,1 -> jump uniform, words 2,3 -> acceptance
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define TAG_WEIGHT 0x57454947u
+#define TAG_POS 0x504F5349u
+#define TAG_RADIUS 0x52414449u
+#define TAG_PAIR 0x50414952u
+#define TAG_ITEM 0x4954u
+#define TAG_DRAW 0x44524157u
+
+#define MAXL 64 /* weight layers */
+#define MAXD 8  /* dimensions */
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon et al., SC'11, Sec. 4 and the Random123 reference)  */
+/* ------------------------------------------------------------------------ */
+
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u; /* Weyl increments of the key schedule */
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t prod0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t prod1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(prod1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)prod1;
+        uint32_t n2 = (uint32_t)(prod0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)prod0;
+        c0 = n0;
+        c1 = n1;
+        c2 = n2;
+        c3 = n3;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+static void philox_seed(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                        uint32_t out[4]) {
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    orc_philox(ctr, key, out);
+}
+
+/* Uniform in (0,1) on the grid of odd multiples of 2^-53. */
+double orc_uniform(uint32_t lo, uint32_t hi) {
+    uint64_t bits = ((uint64_t)hi << 32) | lo;
+    return (double)(2 * (bits >> 12) + 1) * 0x1p-53;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Deterministic elementary functions                                         */
+/* ------------------------------------------------------------------------ */
+
+static const double LN2_HI = 0x1.62e42fee00000p-1; /* ln 2 to 32 bits */
+static const double LN2_LO = 0x1.a39ef35793c76p-33; /* ln 2 - LN2_HI */
+static const double INV_LN2 = 0x1.71547652b82fep+0;
+static const double PI_D = 0x1.921fb54442d18p+1;
+
+static double pow2i(int k) { /* exact 2^k for -1022 <= k <= 1023 */
+    uint64_t bits = (uint64_t)(k + 1023) << 52;
+    double r;
+    memcpy(&r, &bits, 8);
+    return r;
+}
+
+/* 2 atanh(s) = 2 (s + s^3/3 + s^5/5 + ...), |s| <= 0.18, 12 terms. */
+static double two_atanh_series(double s) {
+    double z = s * s;
+    double p = 1.0 / 25.0;
+    p = 1.0 / 23.0 + z * p;
+    p = 1.0 / 21.0 + z * p;
+    p = 1.0 / 19.0 + z * p;
+    p = 1.0 / 17.0 + z * p;
+    p = 1.0 / 15.0 + z * p;
+    p = 1.0 / 13.0 + z * p;
+    p = 1.0 / 11.0 + z * p;
+    p = 1.0 / 9.0 + z * p;
+    p = 1.0 / 7.0 + z * p;
+    p = 1.0 / 5.0 + z * p;
+    p = 1.0 / 3.0 + z * p;
+    double t = s * z;
+    t = t * p;
+    return 2.0 * s + 2.0 * t;
+}
+
+/* ln x = e ln 2 + ln m with x = m 2^e, m in (sqrt(1/2), sqrt(2)];
+ * ln m = 2 atanh((m-1)/(m+1)). */
+double orc_det_log(double x) {
+    if (x != x || x < 0.0) return NAN;
+    if (x == 0.0) return -INFINITY;
+    if (x == INFINITY) return INFINITY;
+    int e_adj = 0;
+    if (x < 0x1p-1022) { /* subnormal: scale into the normal range */
+        x = x * 0x1p54;
+        e_adj = -54;
+    }
+    uint64_t bits;
+    memcpy(&bits, &x, 8);
+    int e = (int)((bits >> 52) & 0x7ff) - 1023;
+    bits = (bits & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL;
+    double m;
+    memcpy(&m, &bits, 8); /* m in [1,2) */
+    if (m > 0x1.6a09e667f3bcdp+0) { /* sqrt(2) */
+        m = m * 0.5;
+        e = e + 1;
+    }
+    e = e + e_adj;
+    double s = (m - 1.0) / (m + 1.0);
+    double lm = two_atanh_series(s);
+    double ed = (double)e;
+    return ed * LN2_HI + (lm + ed * LN2_LO);
+}
+
+/* ln(1+x) for x > -1; for |x| < 1/4 via 2 atanh(x/(2+x)), else det_log(1+x). */
+double orc_det_log1p(double x) {
+    if (x != x || x < -1.0) return NAN;
+    if (x == -1.0) return -INFINITY;
+    if (x < -0.25 || x > 0.25) return orc_det_log(1.0 + x);
+    double s = x / (2.0 + x);
+    return two_atanh_series(s);
+}
+
+/* e^x = 2^k e^r, k = nearest integer to x / ln 2, r = x - k ln 2, Taylor to r^17. */
+double orc_det_exp(double x) {
+    if (x != x) return NAN;
+    if (x > 710.0) return INFINITY;
+    if (x < -746.0) return 0.0;
+    double kd = floor(x * INV_LN2 + 0.5);
+    int k = (int)kd;
+    double r = (x - kd * LN2_HI) - kd * LN2_LO;
+    double p = 1.0 / 355687428096000.0; /* 1/17! */
+    p = 1.0 / 20922789888000.0 + r * p;  /* 1/16! */
+    p = 1.0 / 1307674368000.0 + r * p;   /* 1/15! */
+    p = 1.0 / 87178291200.0 + r * p;     /* 1/14! */
+    p = 1.0 / 6227020800.0 + r * p;      /* 1/13! */
+    p = 1.0 / 479001600.0 + r * p;       /* 1/12! */
+    p = 1.0 / 39916800.0 + r * p;        /* 1/11! */
+    p = 1.0 / 3628800.0 + r * p;         /* 1/10! */
+    p = 1.0 / 362880.0 + r * p;          /* 1/9! */
+    p = 1.0 / 40320.0 + r * p;           /* 1/8! */
+    p = 1.0 / 5040.0 + r * p;            /* 1/7! */
+    p = 1.0 / 720.0 + r * p;             /* 1/6! */
+    p = 1.0 / 120.0 + r * p;             /* 1/5! */
+    p = 1.0 / 24.0 + r * p;              /* 1/4! */
+    p = 1.0 / 6.0 + r * p;               /* 1/3! */
+    p = 0.5 + r * p;                     /* 1/2! */
+    p = 1.0 + r * p;
+    p = 1.0 + r * p;
+    if (k > 1023) return (p * pow2i(1023)) * pow2i(k - 1023);
+    if (k < -1021) return (p * pow2i(k + 600)) * pow2i(-600);
+    return p * pow2i(k);
+}
+
+double orc_det_pow(double x, double y) { return orc_det_exp(y * orc_det_log(x)); }
+
+/* sin(pi x) for x in [0, 1/2]: Taylor series of sin or of cos(pi (1/2 - x)). */
+double orc_det_sinpi(double x) {
+    if (x <= 0.25) {
+        double y = x * PI_D;
+        double z = y * y;
+        double p = -1.0 / 1307674368000.0;    /* -1/15! */
+        p = 1.0 / 6227020800.0 + z * p;       /* 1/13! */
+        p = -1.0 / 39916800.0 + z * p;        /* -1/11! */
+        p = 1.0 / 362880.0 + z * p;           /* 1/9! */
+        p = -1.0 / 5040.0 + z * p;            /* -1/7! */
+        p = 1.0 / 120.0 + z * p;              /* 1/5! */
+        p = -1.0 / 6.0 + z * p;               /* -1/3! */
+        double t = y * z;
+        return y + t * p;
+    }
+    double y = (0.5 - x) * PI_D;
+    double z = y * y;
+    double p = 1.0 / 20922789888000.0;   /* 1/16! */
+    p = -1.0 / 87178291200.0 + z * p;    /* -1/14! */
+    p = 1.0 / 479001600.0 + z * p;       /* 1/12! */
+    p = -1.0 / 3628800.0 + z * p;        /* -1/10! */
+    p = 1.0 / 40320.0 + z * p;           /* 1/8! */
+    p = -1.0 / 720.0 + z * p;            /* -1/6! */
+    p = 1.0 / 24.0 + z * p;              /* 1/4! */
+    p = -0.5 + z * p;                    /* -1/2! */
+    return 1.0 + z * p;
+}
+
+/* acosh z = ln(z + sqrt(z^2 - 1)), z >= 1. */
+double orc_det_acosh(double z) { return orc_det_log(z + sqrt(z * z - 1.0)); }
+
+/* x^(1/d) for the threshold variant; x for d = 1. */
+static double root_d(double x, int d) {
+    if (d == 1) return x;
+    return orc_det_exp(orc_det_log(x) / (double)d);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact sum of positive doubles (W = sum of weights, Sec. 2.1)               */
+/* ------------------------------------------------------------------------ */
+
+/* Exact fixed-point accumulation in 128-bit integers, then one
+ * round-to-nearest-even conversion.  Returns -1 if the dynamic range does not
+ * fit 128 bits. */
+double orc_exact_sum(int64_t n, const double* w) {
+    if (n <= 0) return 0.0;
+    double wmin = w[0];
+    for (int64_t v = 1; v < n; v++)
+        if (w[v] < wmin) wmin = w[v];
+    int emin;
+    frexp(wmin, &emin);
+    int E0 = emin - 53; /* every weight is an integer multiple of 2^E0 */
+    unsigned __int128 acc = 0;
+    for (int64_t v = 0; v < n; v++) {
+        double scaled = ldexp(w[v], -E0);
+        if (scaled >= 0x1p120) return -1.0;
+        unsigned __int128 m = (unsigned __int128)scaled;
+        unsigned __int128 before = acc;
+        acc += m;
+        if (acc < before) return -1.0;
+    }
+    /* round acc to 53 significant bits, ties to even */
+    int top = 127;
+    while (top >= 0 && !((acc >> top) & 1)) top--;
+    if (top < 53) return ldexp((double)(uint64_t)acc, E0);
+    int shift = top - 52;
+    unsigned __int128 mant = acc >> shift;
+    unsigned __int128 rem = acc & ((((unsigned __int128)1) << shift) - 1);
+    unsigned __int128 half = ((unsigned __int128)1) << (shift - 1);
+    if (rem > half || (rem == half && (mant & 1))) mant += 1;
+    return ldexp((double)(uint64_t)mant, shift + E0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Model inputs (Sec. 2.1, Sec. 2.2, Sec. 5.1 steps 1-2)                      */
+/* ------------------------------------------------------------------------ */
+
+/* Pareto weights by inversion and uniform fixed-point torus positions;
+ * X is row-major [n][d]. */
+void orc_girg_points(int64_t n, int d, double beta, double w_min, uint64_t seed, double* w,
+                     uint32_t* X) {
+    double expo = -1.0 / (beta - 1.0);
+    uint32_t o[4];
+    for (int64_t v = 0; v < n; v++) {
+        uint32_t vlo = (uint32_t)v, vhi = (uint32_t)((uint64_t)v >> 32);
+        philox_seed(seed, vlo, vhi, TAG_WEIGHT, 0, o);
+        double U = orc_uniform(o[0], o[1]);
+        w[v] = w_min * orc_det_pow(U, expo);
+        for (int k = 0; k < d; k++) {
+            if ((k & 3) == 0) philox_seed(seed, vlo, vhi, TAG_POS, (uint32_t)(k >> 2), o);
+            X[v * d + k] = o[k & 3];
+        }
+    }
+}
+
+/* HRG points: radius density alpha sinh(alpha r)/(cosh(alpha R) - 1) by
+ * inversion of its CDF (cosh(alpha r) - 1)/(cosh(alpha R) - 1); the angle is
+ * theta = 2 pi X 2^-32 with X the fixed-point torus coordinate. */
+void orc_hrg_points(int64_t n, double alpha, double R, uint64_t seed, double* r, uint32_t* X) {
+    double ea = orc_det_exp(alpha * R);
+    double cosh_aR = (ea + 1.0 / ea) * 0.5;
+    uint32_t o[4];
+    for (int64_t v = 0; v < n; v++) {
+        uint32_t vlo = (uint32_t)v, vhi = (uint32_t)((uint64_t)v >> 32);
+        philox_seed(seed, vlo, vhi, TAG_RADIUS, 0, o);
+        double U = orc_uniform(o[0], o[1]);
+        r[v] = orc_det_acosh(1.0 + U * (cosh_aR - 1.0)) / alpha;
+        philox_seed(seed, vlo, vhi, TAG_POS, 0, o);
+        X[v] = o[0];
+    }
+}
+
+/* HRG -> GIRG mapping (Sec. 2.3): w = e^((R - r)/2); x = theta / 2 pi. */
+double orc_hrg_weight(double r, double R) { return orc_det_exp((R - r) * 0.5); }
+
+/* ------------------------------------------------------------------------ */
+/* Connection probabilities                                                   */
+/* ------------------------------------------------------------------------ */
+
+static uint32_t circ_diff(uint32_t a, uint32_t b) {
+    uint32_t t = a - b;
+    uint32_t u = b - a;
+    return t < u ? t : u;
+}
+
+/* L_inf torus distance in units of 2^-32 (Sec. 2.1). */
+static uint32_t torus_dist(const uint32_t* xu, const uint32_t* xv, int d) {
+    uint32_t m = 0;
+    for (int k = 0; k < d; k++) {
+        uint32_t t = circ_diff(xu[k], xv[k]);
+        if (t > m) m = t;
+    }
+    return m;
+}
+
+typedef struct {
+    int d;
+    double T, c, W;
+    int m_int;   /* 1/T when it is an integer in [1,64], else 0 */
+    double invT; /* 1/T */
+} girg_model;
+
+static void girg_model_init(girg_model* M, int d, double T, double c, double W) {
+    M->d = d;
+    M->T = T;
+    M->c = c;
+    M->W = W;
+    M->invT = T > 0.0 ? 1.0 / T : 0.0;
+    M->m_int = 0;
+    if (T > 0.0 && M->invT == floor(M->invT) && M->invT <= 64.0) M->m_int = (int)M->invT;
+}
+
+/* Eq. 1: p = min{1, c ((w_u w_v / W) / r^d)^(1/T)}; r = D 2^-32. */
+static double girg_p(const girg_model* M, double wu, double wv, uint32_t D) {
+    if (D == 0) return 1.0;
+    double q = (wu * wv) / M->W;
+    double r = (double)D * 0x1p-32;
+    double rd = r;
+    for (int k = 1; k < M->d; k++) rd = rd * r;
+    double base = q / rd;
+    double p;
+    if (M->m_int > 0) {
+        p = base;
+        for (int k = 1; k < M->m_int; k++) p = p * base;
+    } else {
+        p = orc_det_exp(M->invT * orc_det_log(base));
+    }
+    p = M->c * p;
+    return p < 1.0 ? p : 1.0;
+}
+
+/* Same formula at a real-valued distance r (used for the type-II bound). */
+static double girg_p_at(const girg_model* M, double wu, double wv, double r) {
+    double q = (wu * wv) / M->W;
+    double rd = r;
+    for (int k = 1; k < M->d; k++) rd = rd * r;
+    double base = q / rd;
+    double p;
+    if (M->m_int > 0) {
+        p = base;
+        for (int k = 1; k < M->m_int; k++) p = p * base;
+    } else {
+        p = orc_det_exp(M->invT * orc_det_log(base));
+    }
+    p = M->c * p;
+    return p < 1.0 ? p : 1.0;
+}
+
+/* Threshold variant: edge iff ||x_u - x_v|| <= c (w_u w_v / W)^(1/d). */
+static int girg_thresh_edge(const girg_model* M, double wu, double wv, uint32_t D) {
+    double q = (wu * wv) / M->W;
+    double thr = M->c * root_d(q, M->d);
+    double r = (double)D * 0x1p-32;
+    return r <= thr;
+}
+
+double orc_girg_p(int d, double T, double c, double W, double wu, double wv, uint32_t D) {
+    girg_model M;
+    girg_model_init(&M, d, T, c, W);
+    return girg_p(&M, wu, wv, D);
+}
+
+int orc_girg_thresh_edge(int d, double c, double W, double wu, double wv, uint32_t D) {
+    girg_model M;
+    girg_model_init(&M, d, 0.0, c, W);
+    return girg_thresh_edge(&M, wu, wv, D);
+}
+
+typedef struct {
+    double T, R;
+    double coshR;
+} hrg_model;
+
+static void hrg_model_init(hrg_model* H, double T, double R) {
+    H->T = T;
+    H->R = R;
+    double eR = orc_det_exp(R);
+    H->coshR = (eR + 1.0 / eR) * 0.5;
+}
+
+/* cosh of the hyperbolic distance (Sec. 2.2) in the form
+ * cosh(r_u - r_v) + 2 sinh r_u sinh r_v sin^2(dtheta / 2),
+ * with E = e^r, sh = sinh r per vertex and dtheta / 2 = pi D 2^-32. */
+static double hrg_coshd(double Eu, double shu, double Ev, double shv, uint32_t D) {
+    double s = orc_det_sinpi((double)D * 0x1p-32);
+    double ch = (Eu / Ev + Ev / Eu) * 0.5;
+    double t = shu * shv;
+    t = t * (s * s);
+    return ch + 2.0 * t;
+}
+
+/* p_T(d) = 1 / (exp((d - R) / 2T) + 1), d = acosh(cosh d). */
+static double hrg_p_from_coshd(const hrg_model* H, double coshd) {
+    double dist = orc_det_acosh(coshd);
+    return 1.0 / (orc_det_exp((dist - H->R) / (2.0 * H->T)) + 1.0);
+}
+
+double orc_hrg_coshd(double ru, double rv, uint32_t D) {
+    double Eu = orc_det_exp(ru), Ev = orc_det_exp(rv);
+    double shu = (Eu - 1.0 / Eu) * 0.5, shv = (Ev - 1.0 / Ev) * 0.5;
+    return hrg_coshd(Eu, shu, Ev, shv, D);
+}
+
+double orc_hrg_p(double T, double R, double ru, double rv, uint32_t D) {
+    hrg_model H;
+    hrg_model_init(&H, T, R);
+    double cd = orc_hrg_coshd(ru, rv, D);
+    if (T == 0.0) return cd < H.coshR ? 1.0 : 0.0;
+    return hrg_p_from_coshd(&H, cd);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Oracle 1: all pairs (Table 1 "Pairwise"), edge iff U(seed,u,v) < p_uv.     */
+/* ------------------------------------------------------------------------ */
+
+static double pair_coin(uint64_t seed, uint32_t u, uint32_t v) {
+    uint32_t o[4];
+    philox_seed(seed, u, v, TAG_PAIR, 0, o);
+    return orc_uniform(o[0], o[1]);
+}
+
+double orc_pair_coin(uint64_t seed, uint32_t u, uint32_t v) { return pair_coin(seed, u, v); }
+
+static void emit(uint32_t* edges, int64_t cap, int64_t* m, uint32_t a, uint32_t b) {
+    if (a > b) {
+        uint32_t t = a;
+        a = b;
+        b = t;
+    }
+    if (*m < cap) {
+        edges[2 * *m] = a;
+        edges[2 * *m + 1] = b;
+    }
+    (*m)++;
+}
+
+int64_t orc_girg_allpairs(int64_t n, int d, const uint32_t* X, const double* w, double W,
+                          double T, double c, uint64_t seed, uint32_t* edges, int64_t cap) {
+    girg_model M;
+    girg_model_init(&M, d, T, c, W);
+    int64_t m = 0;
+    for (int64_t u = 0; u < n; u++) {
+        for (int64_t v = u + 1; v < n; v++) {
+            uint32_t D = torus_dist(X + u * d, X + v * d, d);
+            int e;
+            if (T == 0.0)
+                e = girg_thresh_edge(&M, w[u], w[v], D);
+            else
+                e = pair_coin(seed, (uint32_t)u, (uint32_t)v) < girg_p(&M, w[u], w[v], D);
+            if (e) emit(edges, cap, &m, (uint32_t)u, (uint32_t)v);
+        }
+    }
+    return m;
+}
+
+int64_t orc_hrg_allpairs(int64_t n, const uint32_t* X, const double* r, double R, double T,
+                         uint64_t seed, uint32_t* edges, int64_t cap) {
+    hrg_model H;
+    hrg_model_init(&H, T, R);
+    double* E = malloc(sizeof(double) * (n ? n : 1));
+    double* sh = malloc(sizeof(double) * (n ? n : 1));
+    for (int64_t v = 0; v < n; v++) {
+        E[v] = orc_det_exp(r[v]);
+        sh[v] = (E[v] - 1.0 / E[v]) * 0.5;
+    }
+    int64_t m = 0;
+    for (int64_t u = 0; u < n; u++) {
+        for (int64_t v = u + 1; v < n; v++) {
+            uint32_t D = circ_diff(X[u], X[v]);
+            double cd = hrg_coshd(E[u], sh[u], E[v], sh[v], D);
+            int e;
+            if (T == 0.0)
+                e = cd < H.coshR;
+            else
+                e = pair_coin(seed, (uint32_t)u, (uint32_t)v) < hrg_p_from_coshd(&H, cd);
+            if (e) emit(edges, cap, &m, (uint32_t)u, (uint32_t)v);
+        }
+    }
+    free(E);
+    free(sh);
+    return m;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Oracle 2: the cell-pair sampler (Algorithm 1 with App. B.1)               */
+/* ------------------------------------------------------------------------ */
+
+/* Morton code of the cell containing x at level l: bit b of coordinate k
+ * lands at position b*d + (d-1-k), so coordinate 0 is the most significant
+ * bit of every d-bit group (Sec. 4.2: a3 b3 a2 b2 a1 b1 a0 b0). */
+uint64_t orc_morton(const uint32_t* x, int d, int l) {
+    uint64_t code = 0;
+    for (int b = 0; b < l; b++) {
+        for (int k = 0; k < d; k++) {
+            uint32_t coord = x[k] >> (32 - l);
+            uint64_t bit = (coord >> b) & 1u;
+            code |= bit << (b * d + (d - 1 - k));
+        }
+    }
+    return code;
+}
+
+/* Coordinates of a cell from its Morton code. */
+static void morton_decode(uint64_t code, int d, int l, uint32_t* coord) {
+    for (int k = 0; k < d; k++) coord[k] = 0;
+    for (int b = 0; b < l; b++)
+        for (int k = 0; k < d; k++) coord[k] |= (uint32_t)((code >> (b * d + (d - 1 - k))) & 1u) << b;
+}
+
+/* Largest per-dimension circular difference between the cells (their
+ * L_inf cell distance); cells are neighbours iff it is <= 1 (a cell is its
+ * own neighbour; on levels 0 and 1 all cells are neighbours). */
+static uint32_t cell_linf(uint64_t A, uint64_t B, int d, int l) {
+    uint32_t ca[MAXD], cb[MAXD];
+    morton_decode(A, d, l, ca);
+    morton_decode(B, d, l, cb);
+    uint32_t side = l >= 32 ? 0u : (1u << l);
+    uint32_t m = 0;
+    for (int k = 0; k < d; k++) {
+        uint32_t diff = ca[k] > cb[k] ? ca[k] - cb[k] : cb[k] - ca[k];
+        uint32_t wrap = side - diff;
+        if (wrap < diff) diff = wrap;
+        if (diff > m) m = diff;
+    }
+    return m;
+}
+
+uint32_t orc_cell_linf(uint64_t A, uint64_t B, int d, int l) { return cell_linf(A, B, d, l); }
+
+/* Deepest level used: levels beyond floor(32/d) have no room in a 32-bit
+ * Morton code, and levels with more than 2^(bitlen(n)+4) <= 32 n cells gain
+ * nothing (capping a comparison level only makes cells coarser; the sample
+ * stays exact because every bound is computed from the actual cells). */
+int orc_level_cap(int64_t n, int d) {
+    int bitlen = 0;
+    while (bitlen < 63 && ((int64_t)1 << bitlen) <= n) bitlen++;
+    int a = 32 / d;
+    int b = (bitlen + 4) / d;
+    if (b < 1) b = 1;
+    return a < b ? a : b;
+}
+
+/* Largest level l in [0, cap] with cell side 2^-l > kappa (1 + 2^-30),
+ * i.e. the comparison level of Sec. 3.1 for the threshold distance kappa. */
+static int level_for_kappa(double kappa, int cap) {
+    double k2 = kappa * (1.0 + 0x1p-30);
+    int l = 0;
+    while (l < cap && ldexp(1.0, -(l + 1)) > k2) l++;
+    return l;
+}
+
+/* Chunk length exponent for geometric jumps under bound pbar: 2^k pbar in
+ * [64, 128) when not clamped to [6, 62]. */
+int orc_chunk_log(double pbar) {
+    int e;
+    frexp(pbar, &e);
+    int k = 7 - e;
+    if (k < 6) k = 6;
+    if (k > 62) k = 62;
+    return k;
+}
+
+typedef struct {
+    int model; /* 0 GIRG, 1 HRG */
+    int64_t n;
+    int d;
+    uint64_t seed;
+    const uint32_t* X;
+    const double* w; /* GIRG weights, or HRG mapped weights */
+    girg_model M;
+    hrg_model H;
+    const double* r; /* HRG radii */
+    double* E;       /* HRG e^r */
+    double* sh;      /* HRG sinh r */
+    /* buckets and levels */
+    int L;
+    int64_t lcount[MAXL];
+    double wmax[MAXL];
+    double rlo[MAXL], rhi[MAXL];
+    int CL[MAXL][MAXL];
+    int I[MAXL];
+    int Dmax;
+    int lcap;
+    int64_t* order;       /* sorted position -> vertex id */
+    int64_t lstart[MAXL + 1];
+    int64_t* offs[MAXL];  /* per layer: 2^(d I(i)) + 1 prefix sums */
+    /* output */
+    uint32_t* edges;
+    int64_t cap;
+    int64_t m;
+    /* statistics: [0] type-I pairs tested, [1] type-II items, [2] jump draws,
+     * [3] type-II candidates, [4] type-I items, [5] cell pairs visited,
+     * [6] type-I edges, [7] type-II edges */
+    int64_t stats[8];
+    /* visited cell pairs per level: neighbours, distant, and (A, A) pairs */
+    int64_t lvl_nb[33], lvl_far[33], lvl_self[33];
+    /* optional item log: 12 int64 per item */
+    int64_t* items;
+    int64_t items_cap;
+    int64_t n_items;
+    int skip_sampling;
+} cp_ctx;
+
+static int layer_of(double w, double w_min) {
+    int e;
+    frexp(w / w_min, &e); /* w / w_min = m 2^e, m in [0.5, 1) */
+    int layer = e - 1;
+    if (layer < 0) layer = 0;
+    if (layer > MAXL - 1) layer = MAXL - 1;
+    return layer;
+}
+
+/* Sorting key: (bucket, Morton code of the insertion-level cell, id). */
+typedef struct {
+    int layer;
+    uint64_t cell;
+    int64_t id;
+} sort_rec;
+
+static int cmp_rec(const void* a, const void* b) {
+    const sort_rec* x = a;
+    const sort_rec* y = b;
+    if (x->layer != y->layer) return x->layer < y->layer ? -1 : 1;
+    if (x->cell != y->cell) return x->cell < y->cell ? -1 : 1;
+    if (x->id != y->id) return x->id < y->id ? -1 : 1;
+    return 0;
+}
+
+/* Comparison level of a bucket pair, Sec. 3.1 (GIRG: closed form of the
+ * threshold distance at the largest weights; HRG: level search, Sec. 4.3). */
+static int comparison_level(cp_ctx* C, int i, int j) {
+    if (C->model == 0) {
+        const girg_model* M = &C->M;
+        double qmax = (C->wmax[i] * C->wmax[j]) / M->W;
+        double kappa;
+        if (M->T > 0.0)
+            kappa = root_d(orc_det_pow(M->c, M->T) * qmax, M->d);
+        else
+            kappa = M->c * root_d(qmax, M->d);
+        return level_for_kappa(kappa, C->lcap);
+    }
+    /* HRG: deepest level whose distant cell pairs (angular gap >= one cell)
+     * cannot hold a threshold edge, by the lower bound on cosh d. */
+    double gap = 0.0;
+    if (C->rlo[j] > C->rhi[i]) gap = C->rlo[j] - C->rhi[i];
+    if (C->rlo[i] > C->rhi[j]) gap = C->rlo[i] - C->rhi[j];
+    double eg = orc_det_exp(gap);
+    double cg = (eg + 1.0 / eg) * 0.5;
+    double ei = orc_det_exp(C->rlo[i]), ej = orc_det_exp(C->rlo[j]);
+    double shi = (ei - 1.0 / ei) * 0.5, shj = (ej - 1.0 / ej) * 0.5;
+    double limit = C->H.coshR * (1.0 + 0x1p-30);
+    int l = 1;
+    while (l < C->lcap) {
+        double s = orc_det_sinpi(ldexp(1.0, -(l + 1)));
+        double t = shi * shj;
+        t = t * (s * s);
+        double lb = cg + 2.0 * t;
+        if (!(lb > limit)) break;
+        l++;
+    }
+    return l;
+}
+
+/* Upper bound on p over a distant item at level l whose cells are g cells
+ * apart (Sec. 3.2: largest weights of the buckets, smallest distance of the
+ * cells), inflated by 2^-30 and clamped to 1. */
+static double type2_bound(cp_ctx* C, int i, int j, int l, uint32_t g) {
+    double p;
+    if (C->model == 0) {
+        double rmin = (double)g * ldexp(1.0, -l);
+        p = girg_p_at(&C->M, C->wmax[i], C->wmax[j], rmin);
+    } else {
+        double gap = 0.0;
+        if (C->rlo[j] > C->rhi[i]) gap = C->rlo[j] - C->rhi[i];
+        if (C->rlo[i] > C->rhi[j]) gap = C->rlo[i] - C->rhi[j];
+        double eg = orc_det_exp(gap);
+        double cg = (eg + 1.0 / eg) * 0.5;
+        double ei = orc_det_exp(C->rlo[i]), ej = orc_det_exp(C->rlo[j]);
+        double shi = (ei - 1.0 / ei) * 0.5, shj = (ej - 1.0 / ej) * 0.5;
+        double s = orc_det_sinpi((double)g * ldexp(1.0, -l));
+        double t = shi * shj;
+        t = t * (s * s);
+        double lb = cg + 2.0 * t;
+        p = hrg_p_from_coshd(&C->H, lb);
+    }
+    p = p * (1.0 + 0x1p-30);
+    return p < 1.0 ? p : 1.0;
+}
+
+/* Does the pair of vertices (ids) form an edge under the per-pair coin? */
+static int type1_decide(cp_ctx* C, int64_t u, int64_t v) {
+    uint32_t a = (uint32_t)(u < v ? u : v), b = (uint32_t)(u < v ? v : u);
+    if (C->model == 0) {
+        uint32_t D = torus_dist(C->X + (int64_t)a * C->d, C->X + (int64_t)b * C->d, C->d);
+        if (C->M.T == 0.0) return girg_thresh_edge(&C->M, C->w[a], C->w[b], D);
+        return pair_coin(C->seed, a, b) < girg_p(&C->M, C->w[a], C->w[b], D);
+    }
+    uint32_t D = circ_diff(C->X[a], C->X[b]);
+    double cd = hrg_coshd(C->E[a], C->sh[a], C->E[b], C->sh[b], D);
+    if (C->H.T == 0.0) return cd < C->H.coshR;
+    return pair_coin(C->seed, a, b) < hrg_p_from_coshd(&C->H, cd);
+}
+
+static double pair_p(cp_ctx* C, int64_t u, int64_t v) {
+    uint32_t a = (uint32_t)(u < v ? u : v), b = (uint32_t)(u < v ? v : u);
+    if (C->model == 0) {
+        uint32_t D = torus_dist(C->X + (int64_t)a * C->d, C->X + (int64_t)b * C->d, C->d);
+        return girg_p(&C->M, C->w[a], C->w[b], D);
+    }
+    uint32_t D = circ_diff(C->X[a], C->X[b]);
+    double cd = hrg_coshd(C->E[a], C->sh[a], C->E[b], C->sh[b], D);
+    return hrg_p_from_coshd(&C->H, cd);
+}
+
+/* V_i^A as a range of sorted positions, for level(A) = l <= I(i) (Lemma 1). */
+static void vrange(cp_ctx* C, int i, uint64_t A, int l, int64_t* lo, int64_t* hi) {
+    int s = C->d * (C->I[i] - l);
+    *lo = C->lstart[i] + C->offs[i][A << s];
+    *hi = C->lstart[i] + C->offs[i][(A + 1) << s];
+}
+
+static void log_item(cp_ctx* C, int type, int l, uint64_t A, uint64_t B, int i, int j,
+                     int64_t alo, int64_t ahi, int64_t blo, int64_t bhi, int tri, double pbar) {
+    if (!C->items) return;
+    if (C->n_items < C->items_cap) {
+        int64_t* it = C->items + 12 * C->n_items;
+        it[0] = type;
+        it[1] = l;
+        it[2] = (int64_t)A;
+        it[3] = (int64_t)B;
+        it[4] = i;
+        it[5] = j;
+        it[6] = alo;
+        it[7] = ahi;
+        it[8] = blo;
+        it[9] = bhi;
+        it[10] = tri;
+        memcpy(&it[11], &pbar, 8);
+    }
+    C->n_items++;
+}
+
+/* Type I (Algorithm 1, line 3): every pair of V_i^A x V_j^B; when the item
+ * is (A, A, i, i) only pairs at sorted positions a < b (App. B.1). */
+static void type1_item(cp_ctx* C, int l, uint64_t A, uint64_t B, int i, int j) {
+    int64_t alo, ahi, blo, bhi;
+    vrange(C, i, A, l, &alo, &ahi);
+    vrange(C, j, B, l, &blo, &bhi);
+    if (alo == ahi || blo == bhi) return;
+    int tri = (A == B && i == j);
+    C->stats[4]++;
+    log_item(C, 1, l, A, B, i, j, alo, ahi, blo, bhi, tri, 1.0);
+    if (C->skip_sampling) return;
+    for (int64_t a = alo; a < ahi; a++) {
+        for (int64_t b = tri ? a + 1 : blo; b < bhi; b++) {
+            C->stats[0]++;
+            int64_t u = C->order[a], v = C->order[b];
+            if (type1_decide(C, u, v)) {
+                emit(C->edges, C->cap, &C->m, (uint32_t)u, (uint32_t)v);
+                C->stats[6]++;
+            }
+        }
+    }
+}
+
+/* Type II (Algorithm 1, lines 5-6): geometric jumps with the bound pbar over
+ * the index space idx = a |V_j^B| + b of V_i^A x V_j^B, cut into chunks of
+ * 2^k indices with their own Philox streams; a candidate is accepted with
+ * probability p_uv / pbar, as U' pbar < p_uv. */
+static void type2_item(cp_ctx* C, int l, uint64_t A, uint64_t B, int i, int j) {
+    int64_t alo, ahi, blo, bhi;
+    vrange(C, i, A, l, &alo, &ahi);
+    vrange(C, j, B, l, &blo, &bhi);
+    if (alo == ahi || blo == bhi) return;
+    uint32_t g = cell_linf(A, B, C->d, l) - 1;
+    double pbar = type2_bound(C, i, j, l, g);
+    C->stats[1]++;
+    log_item(C, 2, l, A, B, i, j, alo, ahi, blo, bhi, 0, pbar);
+    if (C->skip_sampling) return;
+    uint64_t na = (uint64_t)(ahi - alo), nb = (uint64_t)(bhi - blo);
+    uint64_t total = na * nb;
+    int k = orc_chunk_log(pbar);
+    uint64_t chunk = (uint64_t)1 << k;
+    uint64_t nchunks = (total + chunk - 1) >> k;
+    double Lb = pbar < 1.0 ? orc_det_log1p(-pbar) : 0.0;
+    uint32_t ko[4];
+    philox_seed(C->seed, (uint32_t)A, (uint32_t)B,
+                (uint32_t)l | ((uint32_t)i << 5) | ((uint32_t)j << 11) | (TAG_ITEM << 17), 0, ko);
+    uint32_t ikey[2] = {ko[0], ko[1]};
+    for (uint64_t h = 0; h < nchunks; h++) {
+        uint64_t start = h << k;
+        uint64_t len = total - start < chunk ? total - start : chunk;
+        int64_t s = -1; /* offset of the last candidate within the chunk */
+        uint32_t t = 0;
+        for (;;) {
+            uint32_t ctr[4] = {(uint32_t)h, (uint32_t)(h >> 32), t, TAG_DRAW}, o[4];
+            orc_philox(ctr, ikey, o);
+            t++;
+            C->stats[2]++;
+            double x = 0.0;
+            if (pbar < 1.0) x = floor(orc_det_log(orc_uniform(o[0], o[1])) / Lb);
+            double remaining = (double)(len - (uint64_t)(s + 1));
+            if (x >= remaining) break;
+            s = s + 1 + (int64_t)x;
+            uint64_t idx = start + (uint64_t)s;
+            int64_t u = C->order[alo + (int64_t)(idx / nb)];
+            int64_t v = C->order[blo + (int64_t)(idx % nb)];
+            C->stats[3]++;
+            if (orc_uniform(o[2], o[3]) * pbar < pair_p(C, u, v)) {
+                emit(C->edges, C->cap, &C->m, (uint32_t)u, (uint32_t)v);
+                C->stats[7]++;
+            }
+        }
+    }
+}
+
+/* Process the cell pair {A, B} (A <= B) at level l for every bucket pair,
+ * then recurse into the children while A and B are neighbours
+ * (Algorithm 1).  Bucket pairs are taken with i <= j: for A < B and i < j
+ * both orientations (A, B) and (B, A) are items, for i = j only (A, B)
+ * (App. B.1); type I uses bucket pairs with CL = l, type II those with
+ * CL >= l (Sec. 3.3). */
+static void recur(cp_ctx* C, int l, uint64_t A, uint64_t B) {
+    C->stats[5]++;
+    uint32_t linf = cell_linf(A, B, C->d, l);
+    int nb = linf <= 1;
+    if (nb)
+        C->lvl_nb[l]++;
+    else
+        C->lvl_far[l]++;
+    if (A == B) C->lvl_self[l]++;
+    for (int i = 0; i < C->L; i++) {
+        if (!C->lcount[i]) continue;
+        for (int j = i; j < C->L; j++) {
+            if (!C->lcount[j]) continue;
+            int cl = C->CL[i][j];
+            if (nb) {
+                if (cl != l) continue;
+                type1_item(C, l, A, B, i, j);
+                if (A != B && i != j) type1_item(C, l, B, A, i, j);
+            } else {
+                if (cl < l) continue;
+                int thresh = (C->model == 0) ? (C->M.T == 0.0) : (C->H.T == 0.0);
+                if (thresh) continue; /* no distant edges at T = 0 (CL margin) */
+                type2_item(C, l, A, B, i, j);
+                if (i != j) type2_item(C, l, B, A, i, j);
+            }
+        }
+    }
+    if (!nb || l >= C->Dmax) return;
+    uint64_t nc = (uint64_t)1 << C->d;
+    for (uint64_t x = 0; x < nc; x++) {
+        for (uint64_t y = (A == B ? x : 0); y < nc; y++) {
+            recur(C, l + 1, (A << C->d) | x, (B << C->d) | y);
+        }
+    }
+}
+
+/* Build buckets, levels, the sorted vertex array and the prefix sums
+ * (Sec. 3.1, Sec. 3.4, Lemma 1). w_min: the weight unit of the buckets;
+ * lcap_override > 0 replaces the default deepest level (a tuning knob that
+ * leaves the sample exact). */
+static int cp_prepare(cp_ctx* C, double w_min, int lcap_override) {
+    int64_t n = C->n;
+    int d = C->d;
+    C->lcap = orc_level_cap(n, d);
+    if (lcap_override > 0) C->lcap = lcap_override < 32 / d ? lcap_override : 32 / d;
+    memset(C->lcount, 0, sizeof(C->lcount));
+    for (int i = 0; i < MAXL; i++) {
+        C->wmax[i] = 0.0;
+        C->rlo[i] = INFINITY;
+        C->rhi[i] = -INFINITY;
+    }
+    int* lay = malloc(sizeof(int) * (n ? n : 1));
+    C->L = 0;
+    for (int64_t v = 0; v < n; v++) {
+        int li = layer_of(C->w[v], w_min);
+        lay[v] = li;
+        C->lcount[li]++;
+        if (C->w[v] > C->wmax[li]) C->wmax[li] = C->w[v];
+        if (C->model == 1) {
+            if (C->r[v] < C->rlo[li]) C->rlo[li] = C->r[v];
+            if (C->r[v] > C->rhi[li]) C->rhi[li] = C->r[v];
+        }
+        if (li + 1 > C->L) C->L = li + 1;
+    }
+    C->Dmax = 0;
+    for (int i = 0; i < C->L; i++) {
+        C->I[i] = 0;
+        for (int j = 0; j < C->L; j++) C->CL[i][j] = 0;
+    }
+    for (int i = 0; i < C->L; i++) {
+        if (!C->lcount[i]) continue;
+        for (int j = i; j < C->L; j++) {
+            if (!C->lcount[j]) continue;
+            int cl = comparison_level(C, i, j);
+            C->CL[i][j] = C->CL[j][i] = cl;
+        }
+    }
+    for (int i = 0; i < C->L; i++) {
+        if (!C->lcount[i]) continue;
+        for (int j = 0; j < C->L; j++) {
+            if (!C->lcount[j]) continue;
+            if (C->CL[i][j] > C->I[i]) C->I[i] = C->CL[i][j];
+        }
+        if (C->I[i] > C->Dmax) C->Dmax = C->I[i];
+    }
+    sort_rec* rec = malloc(sizeof(sort_rec) * (n ? n : 1));
+    for (int64_t v = 0; v < n; v++) {
+        rec[v].layer = lay[v];
+        rec[v].cell = orc_morton(C->X + v * d, d, C->I[lay[v]]);
+        rec[v].id = v;
+    }
+    qsort(rec, (size_t)n, sizeof(sort_rec), cmp_rec);
+    C->order = malloc(sizeof(int64_t) * (n ? n : 1));
+    for (int64_t p = 0; p < n; p++) C->order[p] = rec[p].id;
+    C->lstart[0] = 0;
+    for (int i = 0; i < MAXL; i++) C->lstart[i + 1] = C->lstart[i] + (i < C->L ? C->lcount[i] : 0);
+    for (int i = 0; i < MAXL; i++) C->offs[i] = NULL;
+    for (int i = 0; i < C->L; i++) {
+        uint64_t ncell = (uint64_t)1 << (d * C->I[i]);
+        int64_t* o = calloc(ncell + 1, sizeof(int64_t));
+        for (int64_t p = C->lstart[i]; p < C->lstart[i + 1]; p++) o[rec[p].cell + 1]++;
+        for (uint64_t cidx = 0; cidx < ncell; cidx++) o[cidx + 1] += o[cidx];
+        C->offs[i] = o;
+    }
+    free(rec);
+    free(lay);
+    return 0;
+}
+
+static void cp_free(cp_ctx* C) {
+    free(C->order);
+    for (int i = 0; i < MAXL; i++) free(C->offs[i]);
+    free(C->E);
+    free(C->sh);
+}
+
+/* Tables exported for tests: L, lcap, Dmax, then I[L], CL[L][L], counts[L],
+ * wmax[L] (as doubles in wtab). */
+static void export_tables(cp_ctx* C, int32_t* itab, double* wtab) {
+    if (itab) {
+        itab[0] = C->L;
+        itab[1] = C->lcap;
+        itab[2] = C->Dmax;
+        for (int i = 0; i < C->L; i++) itab[3 + i] = C->I[i];
+        for (int i = 0; i < C->L; i++)
+            for (int j = 0; j < C->L; j++) itab[3 + MAXL + i * MAXL + j] = C->CL[i][j];
+    }
+    if (wtab) {
+        for (int i = 0; i < C->L; i++) {
+            wtab[i] = C->wmax[i];
+            wtab[MAXL + i] = (double)C->lcount[i];
+        }
+    }
+}
+
+/* Oracle 2 for GIRGs.  order_out (n entries, may be NULL) receives the sorted
+ * vertex order; stats (8 + 3*33 entries) the counters and, per level, the
+ * visited neighbouring, distant and (A, A) cell pairs; items/items_cap an optional
+ * item log; skip_sampling enumerates items without drawing. */
+int64_t orc_girg_cellpairs(int64_t n, int d, const uint32_t* X, const double* w, double w_min,
+                           double W, double T, double c, uint64_t seed, uint32_t* edges,
+                           int64_t cap, int64_t* stats, int64_t* order_out, int32_t* itab,
+                           double* wtab, int64_t* items, int64_t items_cap, int64_t* n_items,
+                           int skip_sampling, int lcap_override) {
+    cp_ctx C;
+    memset(&C, 0, sizeof(C));
+    C.model = 0;
+    C.n = n;
+    C.d = d;
+    C.seed = seed;
+    C.X = X;
+    C.w = w;
+    girg_model_init(&C.M, d, T, c, W);
+    C.edges = edges;
+    C.cap = cap;
+    C.items = items;
+    C.items_cap = items_cap;
+    C.skip_sampling = skip_sampling;
+    cp_prepare(&C, w_min, lcap_override);
+    if (n > 0) recur(&C, 0, 0, 0);
+    if (stats) {
+        memcpy(stats, C.stats, sizeof(C.stats));
+        memcpy(stats + 8, C.lvl_nb, sizeof(C.lvl_nb));
+        memcpy(stats + 8 + 33, C.lvl_far, sizeof(C.lvl_far));
+        memcpy(stats + 8 + 66, C.lvl_self, sizeof(C.lvl_self));
+    }
+    if (order_out) memcpy(order_out, C.order, sizeof(int64_t) * n);
+    if (n_items) *n_items = C.n_items;
+    export_tables(&C, itab, wtab);
+    int64_t m = C.m;
+    cp_free(&C);
+    return m;
+}
+
+/* Oracle 2 for HRGs through the mapping of Sec. 2.3 (d = 1, weights
+ * e^((R-r)/2) with unit 1). */
+int64_t orc_hrg_cellpairs(int64_t n, const uint32_t* X, const double* r, double R, double T,
+                          uint64_t seed, uint32_t* edges, int64_t cap, int64_t* stats,
+                          int64_t* order_out, int32_t* itab, double* wtab, int64_t* items,
+                          int64_t items_cap, int64_t* n_items, int skip_sampling,
+                          int lcap_override) {
+    cp_ctx C;
+    memset(&C, 0, sizeof(C));
+    C.model = 1;
+    C.n = n;
+    C.d = 1;
+    C.seed = seed;
+    C.X = X;
+    C.r = r;
+    hrg_model_init(&C.H, T, R);
+    double* w = malloc(sizeof(double) * (n ? n : 1));
+    C.E = malloc(sizeof(double) * (n ? n : 1));
+    C.sh = malloc(sizeof(double) * (n ? n : 1));
+    for (int64_t v = 0; v < n; v++) {
+        w[v] = orc_hrg_weight(r[v], R);
+        C.E[v] = orc_det_exp(r[v]);
+        C.sh[v] = (C.E[v] - 1.0 / C.E[v]) * 0.5;
+    }
+    C.w = w;
+    C.edges = edges;
+    C.cap = cap;
+    C.items = items;
+    C.items_cap = items_cap;
+    C.skip_sampling = skip_sampling;
+    cp_prepare(&C, 1.0, lcap_override);
+    if (n > 0) recur(&C, 0, 0, 0);
+    if (stats) {
+        memcpy(stats, C.stats, sizeof(C.stats));
+        memcpy(stats + 8, C.lvl_nb, sizeof(C.lvl_nb));
+        memcpy(stats + 8 + 33, C.lvl_far, sizeof(C.lvl_far));
+        memcpy(stats + 8 + 66, C.lvl_self, sizeof(C.lvl_self));
+    }
+    if (order_out) memcpy(order_out, C.order, sizeof(int64_t) * n);
+    if (n_items) *n_items = C.n_items;
+    export_tables(&C, itab, wtab);
+    int64_t m = C.m;
+    cp_free(&C);
+    free(w);
+    return m;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Expected average degree and the search for c (Sec. 4.1, App. B.2)         */
+/* ------------------------------------------------------------------------ */
+
+static int cmp_desc(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return x > y ? -1 : (x < y ? 1 : 0);
+}
+
+typedef struct {
+    int64_t n;
+    int d;
+    double T, W;
+    double S1;   /* W - sum w^2 / W */
+    double S2;   /* (sum w^(1/T))^2 / W^(1/T) - sum (w^2/W)^(1/T) */
+    double* ws;  /* weights sorted descending */
+    double* pw;  /* prefix sums of ws */
+    double* pwt; /* prefix sums of ws^(1/T) */
+} deg_ctx;
+
+/* E[X_uv] of App. B.2 without the min (Eq. shortlong), as a function of
+ * q = w_u w_v / W; for T = 0 it is 2^d c^d q. */
+static double ex_uv_nomin(const deg_ctx* G, double c, double q) {
+    if (G->T == 0.0) return ldexp(pow(c, G->d), G->d) * q;
+    double T = G->T;
+    return pow(c, T) * ldexp(1.0, G->d) / (1.0 - T) * q -
+           c * pow(2.0, G->d / T) / (1.0 / T - 1.0) * pow(q, 1.0 / T);
+}
+
+/* f(c) = E[avg degree] (App. B.2): the min-free double sum minus the error
+ * over E_R, the ordered pairs u != v whose min takes effect, i.e. with
+ * k = c^(T/d) q^(1/d) > 1/2 (T > 0) or 2^d c^d q > 1 (T = 0). */
+double deg_f(const deg_ctx* G, double c) {
+    int d = G->d;
+    double T = G->T;
+    double main_term;
+    double qstar; /* pairs with q > qstar are in E_R */
+    if (T == 0.0) {
+        double cd = ldexp(pow(c, d), d);
+        main_term = cd * G->S1;
+        qstar = 1.0 / cd;
+    } else {
+        main_term = pow(c, T) * ldexp(1.0, d) / (1.0 - T) * G->S1 -
+                    c * pow(2.0, d / T) / (1.0 / T - 1.0) * G->S2;
+        qstar = ldexp(1.0, -d) / pow(c, T);
+    }
+    /* error over E_R: for each u (descending), partners v form a prefix of
+     * the descending order */
+    double err = 0.0;
+    int64_t n = G->n;
+    int64_t kpref = n; /* prefix length for the current u, shrinking */
+    for (int64_t a = 0; a < n; a++) {
+        double wu = G->ws[a];
+        double lim = qstar * G->W / wu; /* partners need w_v > lim */
+        while (kpref > 0 && !(G->ws[kpref - 1] > lim)) kpref--;
+        if (kpref == 0) break;
+        int64_t cnt = kpref;
+        double sw = G->pw[kpref];
+        double swt = T > 0.0 ? G->pwt[kpref] : 0.0;
+        if (a < kpref) { /* u itself is in the prefix: drop the self pair */
+            cnt -= 1;
+            sw -= wu;
+            if (T > 0.0) swt -= pow(wu, 1.0 / T);
+        }
+        if (cnt <= 0) continue;
+        double s;
+        if (T == 0.0) {
+            s = ldexp(pow(c, d), d) * (wu / G->W) * sw;
+        } else {
+            s = pow(c, T) * ldexp(1.0, d) / (1.0 - T) * (wu / G->W) * sw -
+                c * pow(2.0, d / T) / (1.0 / T - 1.0) * pow(wu / G->W, 1.0 / T) * swt;
+        }
+        err += s - (double)cnt;
+    }
+    return (main_term - err) / (double)n;
+}
+
+static void deg_init(deg_ctx* G, int64_t n, int d, double T, const double* w, double W) {
+    G->n = n;
+    G->d = d;
+    G->T = T;
+    G->W = W;
+    double s2 = 0.0, st = 0.0, s2t = 0.0;
+    for (int64_t v = 0; v < n; v++) {
+        s2 += w[v] * w[v];
+        if (T > 0.0) {
+            st += pow(w[v], 1.0 / T);
+            s2t += pow(w[v] * w[v] / W, 1.0 / T);
+        }
+    }
+    G->S1 = W - s2 / W;
+    G->S2 = T > 0.0 ? st * st / pow(W, 1.0 / T) - s2t : 0.0;
+    G->ws = malloc(sizeof(double) * (n ? n : 1));
+    memcpy(G->ws, w, sizeof(double) * n);
+    qsort(G->ws, (size_t)n, sizeof(double), cmp_desc);
+    G->pw = malloc(sizeof(double) * (n + 1));
+    G->pwt = malloc(sizeof(double) * (n + 1));
+    G->pw[0] = 0.0;
+    G->pwt[0] = 0.0;
+    for (int64_t a = 0; a < n; a++) {
+        G->pw[a + 1] = G->pw[a] + G->ws[a];
+        G->pwt[a + 1] = G->pwt[a] + (T > 0.0 ? pow(G->ws[a], 1.0 / T) : 0.0);
+    }
+}
+
+static void deg_free(deg_ctx* G) {
+    free(G->ws);
+    free(G->pw);
+    free(G->pwt);
+}
+
+double orc_girg_avg_degree(double c, int64_t n, int d, double T, const double* w, double W) {
+    deg_ctx G;
+    deg_init(&G, n, d, T, w, W);
+    double f = deg_f(&G, c);
+    deg_free(&G);
+    return f;
+}
+
+/* Exponential search for a bracket, then bisection on log c until the
+ * bracket is 1e-13 relative or 200 steps; f is increasing in c. */
+double orc_girg_solve_c(double target, int64_t n, int d, double T, const double* w, double W) {
+    deg_ctx G;
+    deg_init(&G, n, d, T, w, W);
+    double lo = 1.0, hi = 1.0;
+    if (deg_f(&G, 1.0) < target) {
+        while (deg_f(&G, hi) < target && hi < 1e300) hi *= 2.0;
+        lo = hi / 2.0;
+    } else {
+        while (deg_f(&G, lo) >= target && lo > 1e-300) lo /= 2.0;
+        hi = lo * 2.0;
+    }
+    for (int it = 0; it < 200 && hi - lo > 1e-13 * hi; it++) {
+        double mid = sqrt(lo * hi);
+        if (!(mid > lo && mid < hi)) mid = 0.5 * (lo + hi);
+        if (deg_f(&G, mid) < target)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    deg_free(&G);
+    return 0.5 * (lo + hi);
+}
