@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Benchmark: GIRG generation throughput (edges/s) on one GB300.
+
+Workload (the configuration the headline metric is quoted on): GIRG on the
+2-dimensional torus, n = 10^6 vertices, Pareto weights with beta = 2.5 and
+w_min = 1, temperature T = 0.5, c solved for average degree 10 (about 5e6
+edges), seed 1 + rank, int32 edge pairs.  One step = one complete
+``girg_generate`` call: weights and positions, the exact weight sum, the search
+for c, bucket/level tables, keys + prefix sums + radix sort, cell-pair
+enumeration, type-I tests, type-II geometric jumps and edge compaction.
+
+Reported:
+  value      edges/s with the output buffer resident in HBM (device-timed with CUDA
+             events around each step; L2 flushed between steps by writing 256 MB)
+  e2e        the same step through the public API with the edge list copied to
+             pinned host memory inside the timed region
+  fp64_plain the same step with every decision in FP64 (identical edge set)
+  roofline   the dominant kernel against the measured HBM bandwidth
+  cpu_baseline  the FP64 oracle (cell-pair sampler, one core) on a bounded sample
+
+--impl reference runs the FP64 CPU oracle on the host cores on the same
+configuration (a bounded sample per step) and prints the same JSON line.
+Multi-GPU: one independent graph per rank (seed 1 + rank), no collective on the
+data path; value = all ranks' edges / the slowest rank's time ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="girg_d2_n1e6_T0.5_deg10", n=1_000_000, d=2, beta=2.5, T=0.5,
+                avg_deg=10.0, w_min=1.0, seed=1, edge_bytes=4)
+METRIC = "GIRG edges/s on 1 GB300 (d=2, n=1e6, beta=2.5, T=0.5, avg deg 10)"
+CPU_SAMPLE_N = 100_000
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(cfg: dict) -> dict:
+    """The FP64 oracle (as it stands) on a bounded sample: n = 1e5, same d, beta, T,
+    average degree; points + search for c + cell-pair sampler, one host core."""
+    import oracle as O
+    n = CPU_SAMPLE_N
+    t0 = time.perf_counter()
+    w, X = O.girg_points(n, cfg["d"], cfg["beta"], cfg["w_min"], cfg["seed"])
+    W = O.exact_sum(w)
+    c = O.girg_solve_c(cfg["avg_deg"], w, cfg["d"], cfg["T"], W)
+    res = O.girg_cellpairs(X, w, cfg["w_min"], W, cfg["T"], c, cfg["seed"], cap=n * 16)
+    dt = time.perf_counter() - t0
+    m = len(res.edges)
+    return {"value": m / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"n={n} (1/10 of the workload), same d, beta, T, avg degree; "
+                      f"{m} edges in {dt:.2f} s (points + c search + cell-pair sampler)"}
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    """--impl reference: the FP64 CPU oracle on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    import oracle as O
+    cfg = WORKLOAD
+    n = CPU_SAMPLE_N
+    O.build()
+    times, edges = [], []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        w, X = O.girg_points(n, cfg["d"], cfg["beta"], cfg["w_min"], cfg["seed"] + s)
+        W = O.exact_sum(w)
+        c = O.girg_solve_c(cfg["avg_deg"], w, cfg["d"], cfg["T"], W)
+        res = O.girg_cellpairs(X, w, cfg["w_min"], W, cfg["T"], c, cfg["seed"] + s, cap=n * 16)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            edges.append(len(res.edges))
+    value = sum(edges) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg["workload"], "sample_n": n, "full_n": cfg["n"],
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                         "sample": f"n={n} per step, seeds {cfg['seed']}..; same d, beta, T, "
+                                   f"average degree"},
+        "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=None)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1905_06706_gb300 as gg
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    gg.load()
+    cfg = dict(WORKLOAD)
+    seed = cfg["seed"] + rank
+    n, d = cfg["n"], cfg["d"]
+    cap = int(n * cfg["avg_deg"] * 0.6) + 200_000
+    edges = torch.empty((cap, 2), dtype=torch.int32, device="cuda")
+    host_edges = torch.empty((cap, 2), dtype=torch.int32, pin_memory=True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(precision):
+        r = gg.girg_generate(edges, n=n, d=d, beta=cfg["beta"], T=cfg["T"],
+                             avg_deg=cfg["avg_deg"], w_min=cfg["w_min"], seed=seed,
+                             precision=precision)
+        if r.status != gg.GIRG_OK:
+            raise RuntimeError(f"girg_generate: {gg.status_string(r.status)}")
+        return r
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(precision, steps, copy_back=False):
+        ms, m_total, phases = [], 0, []
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = step(precision)
+            if copy_back:
+                host_edges[: r.num_edges].copy_(edges[: r.num_edges], non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            m_total += r.num_edges
+            phases.append(gg.last_phase_ms())
+        return ms, m_total, phases
+
+    for _ in range(args.warmup):
+        step(gg.PRECISION_FP32)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    ms, m_total, phases = timed(gg.PRECISION_FP32, args.steps)
+    barrier()
+    clock_info = clocks.stop()
+    stats = gg.last_stats()
+    t_rank = sum(ms) / 1e3
+    # e2e: public API with the edge list copied to pinned host memory
+    barrier()
+    ms_e2e, m_e2e, _ = timed(gg.PRECISION_FP32, max(3, args.steps // 2), copy_back=True)
+    # plain FP64 path (identical edge set)
+    barrier()
+    k64 = args.fp64_steps if args.fp64_steps is not None else max(3, args.steps // 4)
+    for _ in range(2):
+        step(gg.PRECISION_FP64)
+    ms64, m64, phases64 = timed(gg.PRECISION_FP64, k64)
+    barrier()
+    vals = torch.tensor([t_rank, float(m_total), sum(ms_e2e) / 1e3, float(m_e2e),
+                         sum(ms64) / 1e3, float(m64)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        gathered = [torch.zeros_like(vals) for _ in range(world)]
+        dist.all_gather(gathered, vals)
+        allv = torch.stack(gathered).cpu()
+    else:
+        allv = vals.cpu().unsqueeze(0)
+    if rank == 0:
+        t_max = float(allv[:, 0].max())
+        m_all = float(allv[:, 1].sum())
+        value = m_all / t_max
+        e2e_value = float(allv[:, 3].sum()) / float(allv[:, 2].max())
+        fp64_value = float(allv[:, 5].sum()) / float(allv[:, 4].max())
+        m_step = m_total / args.steps
+        # dominant kernel: the largest phase among the single-kernel phases
+        ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
+        hbm, peak_kind = _peaks()
+        eb = cfg["edge_bytes"] * 2
+        # type-I kernel algorithmic bytes per launch: its item list (16 B per item),
+        # the vertex records of every item side (4d + 4 + 4 B: coordinates, scale, id)
+        # and its edges; see the design doc section 5 for the per-unit figures
+        t1_items = stats["type1_items"]
+        t1_bytes = 16 * t1_items + stats.get("type1_vertex_refs", 0) * (4 * d + 8) + \
+            eb * stats.get("type1_edges", 0)
+        t1_ms = ph["type1"]
+        roof = {"kernel": "k_type1", "bound": "hbm",
+                "achieved": (t1_bytes / (t1_ms / 1e3)) / 1e9 if t1_ms > 0 else None,
+                "peak": hbm, "unit": "GB/s", "traffic": None,
+                "peak_kind": peak_kind}
+        if roof["achieved"] is not None:
+            roof["frac"] = roof["achieved"] / hbm
+        edge_roof = (m_step * eb / (statistics.mean(ms) / 1e3)) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": cfg["workload"], "n": n, "d": d, "beta": cfg["beta"],
+                       "T": cfg["T"], "avg_deg": cfg["avg_deg"], "edges_per_step": m_step,
+                       "edge_format": "int32 pairs", "parallelism": f"replicas x{world}",
+                       "l2": "flushed (256 MB write) between steps",
+                       "decisions": "FP32 with FP64 recheck in the error band"},
+            "e2e": {"value": e2e_value, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": int(m_e2e / max(1, len(ms_e2e))) * eb,
+                    "note": "inputs are the parameters; weights and positions are drawn on "
+                            "the device (Sec. 5.1 steps 1-2); the edge list is copied to "
+                            "pinned host memory each step"},
+            "fp64_plain": {"value": fp64_value, "unit": "edges/s",
+                           "ms_per_step": statistics.mean(ms64)},
+            "roofline": roof,
+            "edge_output_roofline": {"achieved": edge_roof, "peak": hbm, "unit": "GB/s",
+                                     "frac": edge_roof / hbm},
+            "phases_ms": ph,
+            "stats": stats,
+            "gpu_launches": int(stats.get("kernel_launches", 0)) * args.steps,
+            "clocks": clock_info,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(cfg)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

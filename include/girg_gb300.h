@@ -1,0 +1,172 @@
+/*
+ * C ABI of the GB300 GIRG / HRG generator (arXiv 1905.06706, Bläsius et al.).
+ *
+ * One call generates one random graph on the device: weights and positions
+ * (Sec. 2.1, Sec. 5.1 steps 1-2), the constant c for a target average degree
+ * (Sec. 4.1, App. B.2), weight buckets and the Morton-sorted vertex array with
+ * per-cell prefix sums (Sec. 3.1, Sec. 3.4, Lemma 1), the cell pairs of
+ * Algorithm 1 (Sec. 3.3, App. B.1), all-pairs tests on neighbouring cells and
+ * geometric jumps on distant cells (Sec. 3.2), and compaction of the edges
+ * into the caller's buffer.  The HRG entry point runs the same path through the
+ * mapping of Sec. 2.3 with the connection probability of Sec. 2.2.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are device pointers, others are host pointers.
+ *   - `stream` is a cudaStream_t (passed as void*); all device work is ordered
+ *     on it.  Calls return after the edge count has been copied to the host,
+ *     i.e. they synchronise the stream once at the end (and once after the
+ *     weight reductions).
+ *   - Scratch memory is allocated with cudaMallocAsync on `stream` and freed
+ *     before return; the caller owns every buffer it passes.
+ *   - Edges are unordered pairs (u, v), u < v, of original vertex ids, stored
+ *     as two uint32 (edge_bytes = 4) or two uint64 (edge_bytes = 8) per edge,
+ *     in unspecified order.  No self loops, no multi-edges.
+ *   - The edge set is a deterministic function of the parameters and seed, and
+ *     equals the FP64 oracle's edge for edge in both precision modes.
+ *   - Return value: a GIRG_* status.  On GIRG_E_CAPACITY *num_edges holds the
+ *     number of edges the graph has and the buffer holds an unspecified subset.
+ */
+#ifndef GIRG_GB300_H
+#define GIRG_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GIRG_OK 0
+#define GIRG_E_PARAM 1    /* parameter out of range (see each field) */
+#define GIRG_E_CAPACITY 2 /* edge buffer too small; *num_edges = required */
+#define GIRG_E_CUDA 3     /* a CUDA call failed */
+#define GIRG_E_RANGE 4    /* largest / smallest weight >= 2^43 (no exact 128-bit sum) */
+#define GIRG_E_INTERNAL 5 /* internal capacity or consistency check failed */
+
+#define GIRG_PRECISION_FP32 0 /* FP32 decisions, FP64 recheck inside the error band */
+#define GIRG_PRECISION_FP64 1 /* every decision in FP64 */
+
+/* GIRG parameters (Sec. 2.1).
+ *   n          number of vertices, 2 <= n < 2^31
+ *   d          dimension of the torus, 1 <= d <= 8
+ *   beta       power-law exponent of the weights, beta > 2
+ *   T          temperature, 0 <= T < 1 (0: threshold variant)
+ *   avg_deg    target expected average degree, used when c <= 0; 0 < avg_deg < n - 1
+ *   c          the constant of Eq. 1; c <= 0 means "solve from avg_deg" (App. B.2)
+ *   w_min      smallest weight, > 0
+ *   seed       64-bit seed of every Philox stream
+ *   edge_bytes 4 (uint32 endpoints) or 8 (uint64 endpoints)
+ *   precision  GIRG_PRECISION_FP32 or GIRG_PRECISION_FP64
+ *   level_cap  deepest quadtree level to use, 0 = default min(32/d, (bitlen(n)+4)/d);
+ *              a tuning knob: the sample stays exact for any value >= 1
+ */
+typedef struct {
+    int64_t n;
+    int32_t d;
+    double beta;
+    double T;
+    double avg_deg;
+    double c;
+    double w_min;
+    uint64_t seed;
+    int32_t edge_bytes;
+    int32_t precision;
+    int32_t level_cap;
+} girg_params;
+
+/* HRG parameters (Sec. 2.2).
+ *   alpha      radial dispersion, alpha > 1/2 (power-law exponent 2 alpha + 1)
+ *   T          temperature, 0 <= T < 1
+ *   R          disk radius R = 2 ln n + C (Sec. 2.2), > 0; C sets the average degree
+ *   other fields as for girg_params.
+ */
+typedef struct {
+    int64_t n;
+    double alpha;
+    double T;
+    double R;
+    uint64_t seed;
+    int32_t edge_bytes;
+    int32_t precision;
+    int32_t level_cap;
+} hrg_params;
+
+/* Generate one GIRG (Sec. 2.1) by the cell-pair sampler (Algorithm 1).
+ *   d_edges        device buffer of capacity_edges edges (layout above)
+ *   num_edges      host out: number of edges of the graph
+ *   c_used         host out (may be NULL): the c of Eq. 1 that was used
+ * Errors: GIRG_E_PARAM, GIRG_E_CAPACITY, GIRG_E_CUDA, GIRG_E_RANGE, GIRG_E_INTERNAL. */
+int girg_generate(const girg_params* params, void* d_edges, int64_t capacity_edges,
+                  int64_t* num_edges, double* c_used, void* stream);
+
+/* Generate one GIRG on caller-provided points (user-defined weights, Sec. 4.1):
+ *   d_X   device, d x n uint32, coordinate k of vertex v at d_X[k * n + v]; the
+ *         torus coordinate is d_X[k*n+v] * 2^-32
+ *   d_w   device, n doubles > 0 (the smallest one is the bucket unit w_min)
+ *   T, c  as in Eq. 1 (c > 0 required here)
+ * Other arguments as for girg_generate. */
+int girg_generate_from_points(int64_t n, int32_t d, const uint32_t* d_X, const double* d_w,
+                              double T, double c, uint64_t seed, int32_t precision,
+                              int32_t level_cap, int32_t edge_bytes, void* d_edges,
+                              int64_t capacity_edges, int64_t* num_edges, void* stream);
+
+/* Generate one HRG (Sec. 2.2) through the HRG -> GIRG mapping (Sec. 2.3). */
+int hrg_generate(const hrg_params* params, void* d_edges, int64_t capacity_edges,
+                 int64_t* num_edges, void* stream);
+
+/* The quadratic all-pairs generator (Table 1, "Pairwise") on the device: every
+ * pair u < v is tested with the same per-pair coin as the type-I tests.  Inputs as
+ * for girg_generate_from_points plus W = sum of the weights (must equal the exactly
+ * rounded sum for parity with other paths).  Quadratic work: for validation and as
+ * the plain-FP64 baseline. */
+int girg_allpairs(int64_t n, int32_t d, const uint32_t* d_X, const double* d_w, double W,
+                  double T, double c, uint64_t seed, int32_t precision, int32_t edge_bytes,
+                  void* d_edges, int64_t capacity_edges, int64_t* num_edges, void* stream);
+
+/* Weights and positions of girg_generate (Sec. 2.1, Sec. 5.1 steps 1-2) into caller
+ * buffers: d_w n doubles, d_X d x n uint32 (layout as above). */
+int girg_points(int64_t n, int32_t d, double beta, double w_min, uint64_t seed, double* d_w,
+                uint32_t* d_X, void* stream);
+
+/* Radii and angular fixed-point coordinates of hrg_generate (Sec. 2.2): d_r n doubles,
+ * d_X n uint32 (theta = 2 pi d_X[v] 2^-32). */
+int hrg_points(int64_t n, double alpha, double R, uint64_t seed, double* d_r, uint32_t* d_X,
+               void* stream);
+
+/* Expected average degree f(c) of App. B.2 for a GIRG with these parameters and
+ * weights generated from params->seed (params->c is the c evaluated). */
+int girg_expected_avg_degree(const girg_params* params, double* avg_deg, void* stream);
+
+/* Counters of the last generate call on this host thread: [0] type-I pairs tested,
+ * [1] coins drawn, [2] FP64 rechecks, [3] type-II items, [4] jump draws,
+ * [5] type-II candidates, [6] rows, [7] type-I items, [8] heavy type-II chunks,
+ * [9] edges, [10] kernel launches, [11] vertex references of the type-I items
+ * (sum of both side lengths), [12] type-I edges.  Copies min(len, 13) values; returns
+ * the number copied. */
+int girg_last_stats(int64_t* out, int32_t len);
+
+/* Milliseconds spent in each phase of the last call on this host thread
+ * (CUDA events): [0] points+reductions, [1] tables/host, [2] keys+sort+gather,
+ * [3] enumeration + type II, [4] type I, [5] heavy type II, [6] total. */
+int girg_last_phase_ms(float* out, int32_t len);
+
+/* Sorted vertex order of the bucket/Morton sort (Sec. 3.4) for the given points:
+ * d_order (device, n int64) receives the original id at each sorted position.
+ * Used to check the sort against the oracle. */
+int girg_sorted_order(int64_t n, int32_t d, const uint32_t* d_X, const double* d_w, double T,
+                      double c, int32_t level_cap, int64_t* d_order, void* stream);
+
+/* The library's deterministic FP64 elementary functions, evaluated on the host (the
+ * host builds the type-II bound tables with them; the device uses the same steps):
+ * fn 0 ln x, 1 ln(1+x), 2 e^x, 3 x^y, 4 sin(pi x) for x in [0, 1/2], 5 acosh x,
+ * 6 the GIRG probability of Eq. 1 at weights (x, y), r = 1/4, W = 1000, c = 1/2,
+ * T = 3/4, d = 2.  Returns NaN for an unknown fn.  Diagnostic; no GPU needed. */
+double girg_det_eval(int32_t fn, double x, double y);
+
+/* Human-readable name of a status code (static storage). */
+const char* girg_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GIRG_GB300_H */

@@ -48,9 +48,12 @@
  *   HRG radius of vertex v    = acosh(1 + U (cosh(alpha R) - 1)) / alpha,
  *                               U from ctr (v_lo, v_hi, TAG_RADIUS, 0)
  *   type-I coin of pair u<v   = U from words 0,1 of ctr (u, v, TAG_PAIR, 0)
+ *   type-II draw t, one chunk = ctr (A, B, l|i<<5|j<<11|TAG_LIGHT<<17, t) (items whose
+ *                               index space fits one chunk)
  *   type-II item key          = words 0,1 of ctr (A, B, l|i<<5|j<<11|TAG_ITEM<<17, 0)
- *   type-II draw t of chunk h = Philox with the item key, ctr (h_lo, h_hi, t, TAG_DRAW);
- *                               words 0,1 -> jump uniform, words 2,3 -> acceptance
+ *   type-II draw t of chunk h = Philox with the item key, ctr (h_lo, h_hi, t, TAG_DRAW)
+ *                               (items of several chunks);
+ *   in both cases words 0,1 -> jump uniform, words 2,3 -> acceptance uniform
  */
 #include <math.h>
 #include <stdint.h>
@@ -62,6 +65,7 @@
 #define TAG_RADIUS 0x52414449u
 #define TAG_PAIR 0x50414952u
 #define TAG_ITEM 0x4954u
+#define TAG_LIGHT 0x4C54u
 #define TAG_DRAW 0x44524157u
 
 #define MAXL 64 /* weight layers */
@@ -840,9 +844,9 @@ static void type2_item(cp_ctx* C, int l, uint64_t A, uint64_t B, int i, int j) {
     uint64_t chunk = (uint64_t)1 << k;
     uint64_t nchunks = (total + chunk - 1) >> k;
     double Lb = pbar < 1.0 ? orc_det_log1p(-pbar) : 0.0;
+    uint32_t pack = (uint32_t)l | ((uint32_t)i << 5) | ((uint32_t)j << 11);
     uint32_t ko[4];
-    philox_seed(C->seed, (uint32_t)A, (uint32_t)B,
-                (uint32_t)l | ((uint32_t)i << 5) | ((uint32_t)j << 11) | (TAG_ITEM << 17), 0, ko);
+    philox_seed(C->seed, (uint32_t)A, (uint32_t)B, pack | (TAG_ITEM << 17), 0, ko);
     uint32_t ikey[2] = {ko[0], ko[1]};
     for (uint64_t h = 0; h < nchunks; h++) {
         uint64_t start = h << k;
@@ -850,15 +854,25 @@ static void type2_item(cp_ctx* C, int l, uint64_t A, uint64_t B, int i, int j) {
         int64_t s = -1; /* offset of the last candidate within the chunk */
         uint32_t t = 0;
         for (;;) {
-            uint32_t ctr[4] = {(uint32_t)h, (uint32_t)(h >> 32), t, TAG_DRAW}, o[4];
-            orc_philox(ctr, ikey, o);
+            uint32_t o[4];
+            if (nchunks == 1) { /* one chunk: draw straight from the seed's streams */
+                philox_seed(C->seed, (uint32_t)A, (uint32_t)B, pack | (TAG_LIGHT << 17), t, o);
+            } else {
+                uint32_t ctr[4] = {(uint32_t)h, (uint32_t)(h >> 32), t, TAG_DRAW};
+                orc_philox(ctr, ikey, o);
+            }
             t++;
             C->stats[2]++;
-            double x = 0.0;
-            if (pbar < 1.0) x = floor(orc_det_log(orc_uniform(o[0], o[1])) / Lb);
-            double remaining = (double)(len - (uint64_t)(s + 1));
-            if (x >= remaining) break;
-            s = s + 1 + (int64_t)x;
+            /* X = floor(ln U / ln(1 - pbar)); stop when the jump leaves the chunk */
+            uint64_t remaining = len - (uint64_t)(s + 1);
+            uint64_t X = 0;
+            if (pbar < 1.0) {
+                double x = floor(orc_det_log(orc_uniform(o[0], o[1])) / Lb);
+                if (x >= 0x1p63) break;
+                X = (uint64_t)x;
+            }
+            if (X >= remaining) break;
+            s = s + 1 + (int64_t)X;
             uint64_t idx = start + (uint64_t)s;
             int64_t u = C->order[alo + (int64_t)(idx / nb)];
             int64_t v = C->order[blo + (int64_t)(idx % nb)];

@@ -1,0 +1,231 @@
+"""GB300-native GIRG / HRG generator (arXiv 1905.06706) -- Python binding.
+
+Argument marshalling only: every step of the sampler runs in the CUDA library
+``libgirg_gb300.so`` (built in-tree by :func:`build`), called through its C ABI
+(``include/girg_gb300.h``).  Tensors are PyTorch CUDA tensors; their device
+pointers and the current CUDA stream are passed to the library.  There is no
+CPU fallback: if the library or a GPU is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+from .build import LIB, build  # noqa: F401
+
+GIRG_OK = 0
+GIRG_E_PARAM = 1
+GIRG_E_CAPACITY = 2
+GIRG_E_CUDA = 3
+GIRG_E_RANGE = 4
+GIRG_E_INTERNAL = 5
+PRECISION_FP32 = 0
+PRECISION_FP64 = 1
+
+STAT_NAMES = ("type1_pairs", "coins", "rechecks", "type2_items", "jump_draws",
+              "type2_candidates", "rows", "type1_items", "heavy_chunks", "edges",
+              "kernel_launches", "type1_vertex_refs", "type1_edges")
+PHASE_NAMES = ("points_reduce", "tables", "sort", "enumerate_type2", "type1", "heavy_type2",
+               "total")
+
+
+class GirgParams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("beta", ctypes.c_double),
+                ("T", ctypes.c_double), ("avg_deg", ctypes.c_double), ("c", ctypes.c_double),
+                ("w_min", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("edge_bytes", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("level_cap", ctypes.c_int32)]
+
+
+class HrgParams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("alpha", ctypes.c_double), ("T", ctypes.c_double),
+                ("R", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("edge_bytes", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("level_cap", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes) of every entry point of include/girg_gb300.h
+P, I64, I32, U64, DBL = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                         ctypes.c_double)
+SIGNATURES = {
+    "girg_generate": (I32, [P, P, I64, P, P, P]),
+    "girg_generate_from_points": (I32, [I64, I32, P, P, DBL, DBL, U64, I32, I32, I32, P, I64, P,
+                                        P]),
+    "hrg_generate": (I32, [P, P, I64, P, P]),
+    "girg_allpairs": (I32, [I64, I32, P, P, DBL, DBL, DBL, U64, I32, I32, P, I64, P, P]),
+    "girg_points": (I32, [I64, I32, DBL, DBL, U64, P, P, P]),
+    "hrg_points": (I32, [I64, DBL, DBL, U64, P, P, P]),
+    "girg_expected_avg_degree": (I32, [P, P, P]),
+    "girg_last_stats": (I32, [P, I32]),
+    "girg_last_phase_ms": (I32, [P, I32]),
+    "girg_sorted_order": (I32, [I64, I32, P, P, DBL, DBL, I32, P, P]),
+    "girg_status_string": (ctypes.c_char_p, [I32]),
+    "girg_det_eval": (DBL, [I32, DBL, DBL]),
+}
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it first if needed); raise if impossible."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = LIB
+        if build_if_missing:
+            path = build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgirg_gb300.so not found at {path}; run build() first")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+class GirgError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: status {status} ({status_string(status)})")
+        self.status = status
+
+
+def status_string(status: int) -> str:
+    return load().girg_status_string(status).decode()
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA GPU is required (this library has no CPU path)")
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def last_stats() -> dict:
+    buf = (ctypes.c_int64 * len(STAT_NAMES))()
+    load().girg_last_stats(buf, len(STAT_NAMES))
+    return dict(zip(STAT_NAMES, list(buf)))
+
+
+def last_phase_ms() -> dict:
+    buf = (ctypes.c_float * 7)()
+    load().girg_last_phase_ms(buf, 7)
+    return dict(zip(PHASE_NAMES, list(buf)))
+
+
+@dataclass
+class Result:
+    status: int
+    num_edges: int
+    c_used: float = float("nan")
+
+
+def girg_generate(edges, *, n, d, beta, T, avg_deg=0.0, c=0.0, w_min=1.0, seed=1,
+                  precision=PRECISION_FP32, level_cap=0, stream=None) -> Result:
+    """Generate a GIRG into ``edges`` (CUDA tensor (cap, 2) of int32 or int64)."""
+    _torch()
+    lib = load()
+    eb = edges.element_size()
+    p = GirgParams(n, d, beta, T, avg_deg, c, w_min, seed, eb, precision, level_cap)
+    m = ctypes.c_int64(0)
+    cu = ctypes.c_double(0.0)
+    st = lib.girg_generate(ctypes.byref(p), _ptr(edges), edges.shape[0], ctypes.byref(m),
+                           ctypes.byref(cu), _stream(stream))
+    return Result(st, m.value, cu.value)
+
+
+def girg_generate_from_points(edges, X, w, *, T, c, seed=1, precision=PRECISION_FP32,
+                              level_cap=0, stream=None) -> Result:
+    """GIRG on caller points: X (d, n) uint32-valued int32/uint32 tensor, w (n,) float64."""
+    _torch()
+    lib = load()
+    d, n = X.shape
+    m = ctypes.c_int64(0)
+    st = lib.girg_generate_from_points(n, d, _ptr(X), _ptr(w), T, c, seed, precision, level_cap,
+                                       edges.element_size(), _ptr(edges), edges.shape[0],
+                                       ctypes.byref(m), _stream(stream))
+    return Result(st, m.value, c)
+
+
+def hrg_generate(edges, *, n, alpha, T, R, seed=1, precision=PRECISION_FP32, level_cap=0,
+                 stream=None) -> Result:
+    _torch()
+    lib = load()
+    p = HrgParams(n, alpha, T, R, seed, edges.element_size(), precision, level_cap)
+    m = ctypes.c_int64(0)
+    st = lib.hrg_generate(ctypes.byref(p), _ptr(edges), edges.shape[0], ctypes.byref(m),
+                          _stream(stream))
+    return Result(st, m.value)
+
+
+def girg_allpairs(edges, X, w, *, W, T, c, seed=1, precision=PRECISION_FP32,
+                  stream=None) -> Result:
+    _torch()
+    lib = load()
+    d, n = X.shape
+    m = ctypes.c_int64(0)
+    st = lib.girg_allpairs(n, d, _ptr(X), _ptr(w), W, T, c, seed, precision,
+                           edges.element_size(), _ptr(edges), edges.shape[0], ctypes.byref(m),
+                           _stream(stream))
+    return Result(st, m.value, c)
+
+
+def girg_points(n, d, beta, w_min=1.0, seed=1, stream=None):
+    """Weights (n,) float64 and positions (d, n) int32 (uint32 bit patterns)."""
+    torch = _torch()
+    lib = load()
+    w = torch.empty(n, dtype=torch.float64, device="cuda")
+    X = torch.empty((d, n), dtype=torch.int32, device="cuda")
+    st = lib.girg_points(n, d, beta, w_min, seed, _ptr(w), _ptr(X), _stream(stream))
+    if st != GIRG_OK:
+        raise GirgError(st, "girg_points")
+    return w, X
+
+
+def hrg_points(n, alpha, R, seed=1, stream=None):
+    torch = _torch()
+    lib = load()
+    r = torch.empty(n, dtype=torch.float64, device="cuda")
+    X = torch.empty(n, dtype=torch.int32, device="cuda")
+    st = lib.hrg_points(n, alpha, R, seed, _ptr(r), _ptr(X), _stream(stream))
+    if st != GIRG_OK:
+        raise GirgError(st, "hrg_points")
+    return r, X
+
+
+def girg_expected_avg_degree(*, n, d, beta, T, c, w_min=1.0, seed=1, stream=None) -> float:
+    _torch()
+    lib = load()
+    p = GirgParams(n, d, beta, T, 0.0, c, w_min, seed, 4, 0, 0)
+    out = ctypes.c_double(0.0)
+    st = lib.girg_expected_avg_degree(ctypes.byref(p), ctypes.byref(out), _stream(stream))
+    if st != GIRG_OK:
+        raise GirgError(st, "girg_expected_avg_degree")
+    return out.value
+
+
+def girg_sorted_order(X, w, *, T, c, level_cap=0, stream=None):
+    torch = _torch()
+    lib = load()
+    d, n = X.shape
+    order = torch.empty(n, dtype=torch.int64, device="cuda")
+    st = lib.girg_sorted_order(n, d, _ptr(X), _ptr(w), T, c, level_cap, _ptr(order),
+                               _stream(stream))
+    if st != GIRG_OK:
+        raise GirgError(st, "girg_sorted_order")
+    return order

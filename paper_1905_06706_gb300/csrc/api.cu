@@ -1,0 +1,907 @@
+// Host orchestration and the C ABI (include/girg_gb300.h).
+//
+// girg_generate: points -> exact weight sum and bucket statistics -> c (App. B.2)
+// -> bucket / level tables (Sec. 3.1) -> keys, prefix sums and radix sort
+// (Sec. 3.4, Lemma 1, Sec. 4.4) -> rows -> cell-pair enumeration with inline
+// type-II jumps (Algorithm 1, Sec. 3.2) -> type-I tiles -> multi-chunk type-II
+// items -> edge count.  The host computes the FP64 tables that every kernel
+// reads (comparison and insertion levels, type-II bounds p-bar and ln(1-p-bar)),
+// with the same deterministic arithmetic as the device.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "girg_gb300.h"
+#include "internal.cuh"
+#include "kernels.h"
+#include "solver.h"
+
+using namespace gg;
+
+thread_local unsigned long long gg::g_launches = 0;
+
+namespace {
+
+thread_local int64_t g_stats[kNumStats];
+thread_local float g_ms[7];
+
+struct CudaFail {
+    cudaError_t err;
+};
+struct Status {
+    int code;
+};
+
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) throw CudaFail{e_}; \
+    } while (0)
+
+// Scratch allocations on the stream's memory pool, freed on scope exit.
+struct Scratch {
+    cudaStream_t st;
+    std::vector<void*> ptrs;
+    explicit Scratch(cudaStream_t s) : st(s) {
+        static bool pool_set = false;
+        if (!pool_set) {
+            int dev = 0;
+            cudaMemPool_t pool;
+            if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                uint64_t thr = ~0ull;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            }
+            pool_set = true;
+        }
+    }
+    template <class T>
+    T* get(size_t count) {
+        void* p = nullptr;
+        size_t bytes = count * sizeof(T);
+        if (bytes < 256) bytes = 256;
+        CK(cudaMallocAsync(&p, bytes, st));
+        ptrs.push_back(p);
+        return static_cast<T*>(p);
+    }
+    ~Scratch() {
+        for (void* p : ptrs) cudaFreeAsync(p, st);
+    }
+};
+
+struct Timer {
+    cudaEvent_t ev[8];
+    int used = 0;
+    cudaStream_t st;
+    explicit Timer(cudaStream_t s) : st(s) {
+        for (auto& e : ev) cudaEventCreate(&e);
+    }
+    void mark() {
+        if (used < 8) cudaEventRecord(ev[used++], st);
+    }
+    ~Timer() {
+        for (auto& e : ev) cudaEventDestroy(e);
+    }
+};
+
+double round128(unsigned long long hi, unsigned long long lo, int E0) {
+    unsigned __int128 acc = ((unsigned __int128)hi << 64) | lo;
+    if (acc == 0) return 0.0;
+    int top = 127;
+    while (!((acc >> top) & 1)) --top;
+    if (top < 53) return std::ldexp((double)(uint64_t)acc, E0);
+    const int shift = top - 52;
+    unsigned __int128 mant = acc >> shift;
+    const unsigned __int128 rem = acc & ((((unsigned __int128)1) << shift) - 1);
+    const unsigned __int128 half = ((unsigned __int128)1) << (shift - 1);
+    if (rem > half || (rem == half && (mant & 1))) mant += 1;
+    return std::ldexp((double)(uint64_t)mant, shift + E0);
+}
+
+int bitlen64(uint64_t x) {
+    int b = 0;
+    while (b < 64 && (x >> b)) ++b;
+    return b;
+}
+
+int default_level_cap(int64_t n, int d) {
+    int bl = 0;
+    while (bl < 63 && ((int64_t)1 << bl) <= n) ++bl;
+    int a = 32 / d, b = (bl + 4) / d;
+    if (b < 1) b = 1;
+    return a < b ? a : b;
+}
+
+// Comparison level for the threshold distance kappa: deepest l in [0, cap] with
+// 2^-l > kappa (1 + 2^-30) (Sec. 3.1).
+int level_for_kappa(double kappa, int cap) {
+    const double k2 = kappa * (1.0 + 0x1p-30);
+    int l = 0;
+    while (l < cap && std::ldexp(1.0, -(l + 1)) > k2) ++l;
+    return l;
+}
+
+struct Problem {
+    int model = 0;  // 0 GIRG, 1 HRG
+    int64_t n = 0;
+    int d = 1;
+    double T = 0, c = 0, W = 0, w_min = 1, R = 0, alpha = 0;
+    uint64_t seed = 0;
+    int precision = 0, edge_bytes = 4, level_cap = 0;
+    const uint32_t* X = nullptr;  // d x n, original order
+    const double* w = nullptr;    // original order
+    const double* r = nullptr;    // HRG radii, original order
+    Reduce red{};
+};
+
+// Everything after the reductions: tables, sort, sampling.  If order_out is set,
+// stops after the sort and writes the sorted original ids there.
+void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edges, int64_t cap,
+                 int64_t* num_edges, int64_t* order_out) {
+    const int64_t n = P.n;
+    const int d = P.d;
+    const bool girg = P.model == 0;
+    // ---------------------------------------------------------------- tables
+    int L = 0;
+    int64_t cnt[kMaxLayers];
+    double wmax[kMaxLayers], rlo[kMaxLayers], rhi[kMaxLayers];
+    for (int i = 0; i < kMaxLayers; ++i) {
+        cnt[i] = (int64_t)P.red.cnt[i];
+        wmax[i] = bits_to_double(P.red.wmax[i]);
+        rlo[i] = bits_to_double(P.red.rmin[i]);
+        rhi[i] = bits_to_double(P.red.rmax[i]);
+        if (cnt[i]) L = i + 1;
+    }
+    int lcap = P.level_cap > 0 ? std::min(P.level_cap, 32 / d) : default_level_cap(n, d);
+    const double invT = P.T > 0.0 ? 1.0 / P.T : 0.0;
+    int m_int = 0;
+    if (P.T > 0.0 && invT == std::floor(invT) && invT <= 64.0) m_int = (int)invT;
+    double coshR = 0.0;
+    if (!girg) {
+        const double eR = det_exp(P.R);
+        coshR = (eR + 1.0 / eR) * 0.5;
+    }
+    std::vector<std::vector<int>> CL(kMaxLayers, std::vector<int>(kMaxLayers, 0));
+    int I[kMaxLayers] = {0}, CLd[kMaxLayers] = {0};
+    for (int i = 0; i < L; ++i) {
+        if (!cnt[i]) continue;
+        for (int j = i; j < L; ++j) {
+            if (!cnt[j]) continue;
+            int cl;
+            if (girg) {
+                const double qmax = (wmax[i] * wmax[j]) / P.W;
+                const double kappa = P.T > 0.0 ? root_d(det_pow(P.c, P.T) * qmax, d)
+                                               : P.c * root_d(qmax, d);
+                cl = level_for_kappa(kappa, lcap);
+            } else {
+                double gap = 0.0;
+                if (rlo[j] > rhi[i]) gap = rlo[j] - rhi[i];
+                if (rlo[i] > rhi[j]) gap = rlo[i] - rhi[j];
+                const double eg = det_exp(gap);
+                const double cg = (eg + 1.0 / eg) * 0.5;
+                const double ei = det_exp(rlo[i]), ej = det_exp(rlo[j]);
+                const double shi = (ei - 1.0 / ei) * 0.5, shj = (ej - 1.0 / ej) * 0.5;
+                const double limit = coshR * (1.0 + 0x1p-30);
+                cl = 1;
+                while (cl < lcap) {
+                    const double s = det_sinpi(std::ldexp(1.0, -(cl + 1)));
+                    double t = shi * shj;
+                    t = t * (s * s);
+                    const double lb = cg + 2.0 * t;
+                    if (!(lb > limit)) break;
+                    ++cl;
+                }
+            }
+            CL[i][j] = CL[j][i] = cl;
+        }
+    }
+    for (int i = 0; i < L; ++i) {
+        if (!cnt[i]) continue;
+        for (int j = 0; j < L; ++j) {
+            if (!cnt[j]) continue;
+            I[i] = std::max(I[i], CL[i][j]);
+            if (j >= i) CLd[i] = std::max(CLd[i], CL[i][j]);
+        }
+    }
+    uint32_t layer_base[kMaxLayers + 1], lstart[kMaxLayers + 1];
+    uint64_t total_cells = 0;
+    for (int i = 0; i <= kMaxLayers; ++i) {
+        if (total_cells >= 0xffffffffull) throw Status{GIRG_E_INTERNAL};
+        layer_base[i] = (uint32_t)total_cells;
+        if (i < L) total_cells += 1ull << (d * I[i]);
+    }
+    if (total_cells >= 0xfffffff0ull) throw Status{GIRG_E_INTERNAL};
+    {
+        uint64_t run = 0;
+        for (int i = 0; i <= kMaxLayers; ++i) {
+            lstart[i] = (uint32_t)run;
+            if (i < kMaxLayers) run += (uint64_t)cnt[i];
+        }
+    }
+    // row classes (i, l): the buckets j >= i with type I (CL = l) and type II (CL >= l >= 2)
+    int n3 = 1, n6 = 1;
+    for (int k = 0; k < d; ++k) {
+        n3 *= 3;
+        n6 *= 6;
+    }
+    const bool tzero = P.T == 0.0;
+    std::vector<uint32_t> cstart((size_t)std::max(L, 1) * (kMaxLevel + 1), 0),
+        cnent(cstart.size(), 0), ctotal(cstart.size(), 0);
+    std::vector<ClassEntry> entries;
+    for (int i = 0; i < L; ++i) {
+        if (!cnt[i]) continue;
+        for (int l = 0; l <= CLd[i]; ++l) {
+            const size_t cls = (size_t)i * (kMaxLevel + 1) + l;
+            cstart[cls] = (uint32_t)entries.size();
+            uint32_t pre = 0;
+            for (int j = i; j < L; ++j) {
+                if (!cnt[j]) continue;
+                if (!tzero && l >= 2 && CL[i][j] >= l) {
+                    entries.push_back(ClassEntry{(uint16_t)j, 2, pre});
+                    pre += (uint32_t)n6;
+                }
+                if (CL[i][j] == l) {
+                    entries.push_back(ClassEntry{(uint16_t)j, 1, pre});
+                    pre += (uint32_t)n3;
+                }
+            }
+            cnent[cls] = (uint32_t)entries.size() - cstart[cls];
+            ctotal[cls] = pre;
+        }
+    }
+    if (entries.empty()) entries.push_back(ClassEntry{0, 0, 0});
+    // type-II bounds for every (i <= j, l, g in {1, 2})
+    std::vector<TwoEntry> tii((size_t)std::max(L, 1) * std::max(L, 1) * (lcap + 1) * 2);
+    for (auto& e : tii) e = TwoEntry{0.0, 0.0, 0.0f, 0.0f, 62, 0};
+    if (!tzero) {
+        for (int i = 0; i < L; ++i) {
+            if (!cnt[i]) continue;
+            for (int j = i; j < L; ++j) {
+                if (!cnt[j]) continue;
+                for (int l = 2; l <= std::min(CL[i][j], lcap); ++l) {
+                    for (int g = 1; g <= 2; ++g) {
+                        double p;
+                        if (girg) {
+                            const double rmin = (double)g * std::ldexp(1.0, -l);
+                            p = girg_p_at(wmax[i], wmax[j], rmin, P.W, P.c, invT, m_int, d);
+                        } else {
+                            double gap = 0.0;
+                            if (rlo[j] > rhi[i]) gap = rlo[j] - rhi[i];
+                            if (rlo[i] > rhi[j]) gap = rlo[i] - rhi[j];
+                            const double eg = det_exp(gap);
+                            const double cg = (eg + 1.0 / eg) * 0.5;
+                            const double ei = det_exp(rlo[i]), ej = det_exp(rlo[j]);
+                            const double shi = (ei - 1.0 / ei) * 0.5, shj = (ej - 1.0 / ej) * 0.5;
+                            const double s = det_sinpi((double)g * std::ldexp(1.0, -l));
+                            double t = shi * shj;
+                            t = t * (s * s);
+                            const double lb = cg + 2.0 * t;
+                            p = hrg_p_from_coshd(lb, P.R, P.T);
+                        }
+                        p = p * (1.0 + 0x1p-30);
+                        const double pbar = p < 1.0 ? p : 1.0;
+                        TwoEntry e;
+                        e.pbar = pbar;
+                        e.Lb = pbar < 1.0 ? det_log1p(-pbar) : 0.0;
+                        e.log2pbar = (float)std::log2(pbar);
+                        e.invLb = pbar < 1.0 ? (float)(1.0 / e.Lb) : -INFINITY;
+                        e.k = chunk_log(pbar);
+                        e.pad = 0;
+                        tii[((((size_t)i * L + j) * (lcap + 1) + l) << 1) + (g - 1)] = e;
+                    }
+                }
+            }
+        }
+    }
+    // HRG distance filter: thresholds on cosh d for U in bins of width 1/(K-1)
+    const int K = 100;
+    std::vector<float> flo(K, 1.0f), fhi(K, INFINITY);
+    if (!girg && !tzero) {
+        for (int m = 0; m < K; ++m) {
+            const double x = (double)m / (double)(K - 1);
+            double F;
+            if (m == 0) {
+                F = INFINITY;
+            } else if (m == K - 1) {
+                F = 1.0;
+            } else {
+                double pinv = P.R + 2.0 * P.T * std::log(1.0 / x - 1.0);
+                if (pinv < 0.0) pinv = 0.0;
+                F = std::cosh(pinv);
+            }
+            float f = (float)F;
+            flo[m] = std::isinf(F) ? INFINITY : std::nextafterf(f, 0.0f) * (1.0f - 0x1p-22f);
+            fhi[m] = std::isinf(F) ? INFINITY : std::nextafterf(f, INFINITY) * (1.0f + 0x1p-22f);
+        }
+    }
+    tm.mark();  // tables done
+    // ---------------------------------------------------------------- sort
+    uint32_t* key = S.get<uint32_t>(n);
+    uint32_t* val = S.get<uint32_t>(n);
+    uint32_t* key2 = S.get<uint32_t>(n);
+    uint32_t* val2 = S.get<uint32_t>(n);
+    uint32_t* offs = S.get<uint32_t>(total_cells + 1);
+    uint32_t* stmp = S.get<uint32_t>(std::max(scan_tmp_words((int64_t)total_cells + 1), radix_tmp_words(n)));
+    CK(cudaMemsetAsync(offs, 0, (total_cells + 1) * sizeof(uint32_t), st));
+    int8_t I8[kMaxLayers];
+    for (int i = 0; i < kMaxLayers; ++i) I8[i] = (int8_t)I[i];
+    const double* wsrc = P.w;
+    launch_keys(n, d, wsrc, P.X, girg ? P.w_min : 1.0, I8, layer_base, key, val, offs, st);
+    launch_scan_u32(offs, offs, (int64_t)total_cells + 1, stmp, st);
+    uint32_t *skey, *sid;
+    radix_sort_pairs(key, val, key2, val2, n, std::max(1, bitlen64(total_cells - 1)), stmp, st, &skey, &sid);
+    if (order_out) {
+        std::vector<uint32_t> h(n);
+        CK(cudaMemcpyAsync(h.data(), sid, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::vector<int64_t> o(h.begin(), h.end());
+        CK(cudaMemcpyAsync(order_out, o.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        return;
+    }
+    uint32_t* Xs = S.get<uint32_t>((size_t)d * n);
+    double* ws = S.get<double>(n);
+    uint8_t* slayer = S.get<uint8_t>(n);
+    float *sv = nullptr, *E32 = nullptr, *einv32 = nullptr, *sh32 = nullptr;
+    float gamma = 0.0f;
+    const double log2W_half = girg ? 0.5 * std::log2(P.W) : 0.0;
+    if (girg) {
+        sv = S.get<float>(n);
+        gamma = (float)(tzero ? 0.5 * std::log2(P.c) : (P.T / (2.0 * d)) * std::log2(P.c));
+        launch_gather_girg(n, d, sid, P.X, P.w, P.w_min, log2W_half, gamma, (float)(1.0 / d), Xs,
+                           ws, sv, slayer, st);
+    } else {
+        E32 = S.get<float>(n);
+        einv32 = S.get<float>(n);
+        sh32 = S.get<float>(n);
+        launch_gather_hrg(n, sid, P.X, P.r, P.w, Xs, ws, E32, einv32, sh32, slayer, st);
+    }
+    tm.mark();  // sort done
+    // ---------------------------------------------------------------- device tables
+    TwoEntry* d_tii = S.get<TwoEntry>(tii.size());
+    uint32_t* d_cstart = S.get<uint32_t>(cstart.size());
+    uint32_t* d_cnent = S.get<uint32_t>(cnent.size());
+    uint32_t* d_ctotal = S.get<uint32_t>(ctotal.size());
+    ClassEntry* d_entries = S.get<ClassEntry>(entries.size());
+    float* d_flo = S.get<float>(K);
+    float* d_fhi = S.get<float>(K);
+    CK(cudaMemcpyAsync(d_tii, tii.data(), tii.size() * sizeof(TwoEntry), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_cstart, cstart.data(), cstart.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_cnent, cnent.data(), cnent.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_ctotal, ctotal.data(), ctotal.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_entries, entries.data(), entries.size() * sizeof(ClassEntry),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_flo, flo.data(), K * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_fhi, fhi.data(), K * 4, cudaMemcpyHostToDevice, st));
+    // rows: at most min(|V_i|, 2^(d l)) per (i, l)
+    uint64_t row_cap = 0;
+    for (int i = 0; i < L; ++i)
+        for (int l = 0; l <= CLd[i] && cnt[i]; ++l)
+            row_cap += std::min<uint64_t>((uint64_t)cnt[i], d * l >= 63 ? ~0ull : (1ull << (d * l)));
+    if (row_cap >= 0xffffffffull) throw Status{GIRG_E_INTERNAL};
+    uint64_t* rows = S.get<uint64_t>(row_cap + 1);
+    unsigned int* counters = S.get<unsigned int>(16);  // rows, t1, heavy, work[4]
+    unsigned long long* stats = S.get<unsigned long long>(kNumStats + 2);  // + edge count + chunks
+    CK(cudaMemsetAsync(counters, 0, 16 * sizeof(unsigned int), st));
+    CK(cudaMemsetAsync(stats, 0, (kNumStats + 2) * sizeof(unsigned long long), st));
+    uint64_t t1_cap = (uint64_t)n * (1 + (uint64_t)(0.75 * n3)) + 65536;
+    if (t1_cap > 0xfffffff0ull) t1_cap = 0xfffffff0ull;
+    uint64_t heavy_cap = (uint64_t)n / 16 + 4096;
+    T1Item* t1 = S.get<T1Item>(t1_cap);
+    HeavyItem* heavy = S.get<HeavyItem>(heavy_cap);
+
+    DevCfg cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.n = (int32_t)n;
+    cfg.d = d;
+    cfg.L = L;
+    cfg.model = P.model;
+    cfg.precision = P.precision;
+    cfg.tzero = tzero ? 1 : 0;
+    cfg.m_int = m_int;
+    cfg.lcap = lcap;
+    cfg.n3 = n3;
+    cfg.n6 = n6;
+    cfg.seed_lo = (uint32_t)P.seed;
+    cfg.seed_hi = (uint32_t)(P.seed >> 32);
+    cfg.mode = kModeT1 | kModeT2Light | kModeT2Heavy;
+    cfg.W = P.W;
+    cfg.c = P.c;
+    cfg.T = P.T;
+    cfg.invT = invT;
+    cfg.w_min = P.w_min;
+    cfg.R = P.R;
+    cfg.coshR = coshR;
+    cfg.dT = P.T > 0.0 ? (float)(d / P.T) : 0.0f;
+    if (girg)
+        cfg.bandG = cfg.dT * 0x1p-14f + 0x1p-15f;
+    else
+        cfg.bandG = (float)(0x1p-12 * (1.0 + (P.T > 0.0 ? 0.5 / P.T : 0.0)));
+    cfg.band_ratio = 0x1p-16f;
+    cfg.coshR32 = (float)coshR;
+    cfg.R32 = (float)P.R;
+    cfg.inv2T32 = P.T > 0.0 ? (float)(0.5 / P.T) : 0.0f;
+    cfg.filt_k = K;
+    for (int i = 0; i < kMaxLayers; ++i) {
+        cfg.I[i] = (int8_t)I[i];
+        cfg.CLd[i] = (uint8_t)CLd[i];
+    }
+    memcpy(cfg.layer_base, layer_base, sizeof(layer_base));
+    memcpy(cfg.lstart, lstart, sizeof(lstart));
+    cfg.tii = d_tii;
+    cfg.class_start = d_cstart;
+    cfg.class_nent = d_cnent;
+    cfg.class_total = d_ctotal;
+    cfg.entries = d_entries;
+    cfg.offs = offs;
+    cfg.Xs = Xs;
+    cfg.sv = sv;
+    cfg.ws = ws;
+    cfg.ids = sid;
+    cfg.skey = skey;
+    cfg.slayer = slayer;
+    cfg.E32 = E32;
+    cfg.einv32 = einv32;
+    cfg.sh32 = sh32;
+    cfg.filt_lo = d_flo;
+    cfg.filt_hi = d_fhi;
+    cfg.edges = d_edges;
+    cfg.edge_bytes = P.edge_bytes;
+    cfg.cap = cap;
+    cfg.edge_count = stats + kNumStats;
+    cfg.stats = stats;
+    cfg.rows = rows;
+    cfg.row_count = counters + 0;
+    cfg.row_cap = (uint32_t)row_cap;
+    cfg.t1 = t1;
+    cfg.t1_count = counters + 1;
+    cfg.t1_cap = (uint32_t)t1_cap;
+    cfg.heavy = heavy;
+    cfg.heavy_count = counters + 2;
+    cfg.heavy_cap = (uint32_t)heavy_cap;
+    cfg.work_counter = counters + 4;
+
+    launch_rows(cfg, rows, counters + 0, (unsigned)row_cap, st);
+    launch_enumerate(cfg, st);
+    unsigned int hc[3];
+    CK(cudaMemcpyAsync(hc, counters, 3 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hc[1] > cfg.t1_cap || hc[2] > cfg.heavy_cap) {
+        uint32_t mode = 0;
+        if (hc[1] > cfg.t1_cap) {
+            mode |= kModeT1;
+            cfg.t1 = S.get<T1Item>((size_t)hc[1] + 1024);
+            cfg.t1_cap = hc[1] + 1024;
+            CK(cudaMemsetAsync(counters + 1, 0, sizeof(unsigned int), st));
+            CK(cudaMemsetAsync(stats + kStatT1Items, 0, sizeof(unsigned long long), st));
+        }
+        if (hc[2] > cfg.heavy_cap) {
+            mode |= kModeT2Heavy;
+            cfg.heavy = S.get<HeavyItem>((size_t)hc[2] + 1024);
+            cfg.heavy_cap = hc[2] + 1024;
+            CK(cudaMemsetAsync(counters + 2, 0, sizeof(unsigned int), st));
+        }
+        CK(cudaMemsetAsync(counters + 4, 0, sizeof(unsigned int), st));
+        cfg.mode = mode;
+        launch_enumerate(cfg, st);
+        cfg.mode = kModeT1 | kModeT2Light | kModeT2Heavy;
+    }
+    tm.mark();  // enumeration + inline type II done
+    launch_type1(cfg, st);
+    tm.mark();  // type I done
+    unsigned long long* total_chunks = stats + kNumStats + 1;
+    launch_heavy_scan(cfg, total_chunks, st);
+    launch_heavy(cfg, total_chunks, st);
+    tm.mark();  // heavy type II done
+    unsigned long long hs[kNumStats + 1];
+    CK(cudaMemcpyAsync(hs, stats, (kNumStats + 1) * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, st));
+    unsigned int rc;
+    CK(cudaMemcpyAsync(&rc, counters, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    hs[kStatRows] = rc;
+    hs[kStatEdges] = hs[kNumStats];
+    for (int q = 0; q < kNumStats; ++q) g_stats[q] = (int64_t)hs[q];
+    g_stats[kStatLaunches] = (int64_t)g_launches;
+    *num_edges = (int64_t)hs[kNumStats];
+}
+
+void finish_timing(Timer& tm) {
+    for (int q = 0; q < 7; ++q) g_ms[q] = 0.0f;
+    // marks: 0 start, 1 reduce done, 2 tables, 3 sort, 4 enumerate, 5 type I, 6 heavy
+    for (int q = 1; q < tm.used && q <= 6; ++q) cudaEventElapsedTime(&g_ms[q - 1], tm.ev[q - 1], tm.ev[q]);
+    if (tm.used >= 2) cudaEventElapsedTime(&g_ms[6], tm.ev[0], tm.ev[tm.used - 1]);
+}
+
+void read_reduce(Problem& P, Reduce* d_red, cudaStream_t st) {
+    CK(cudaMemcpyAsync(&P.red, d_red, sizeof(Reduce), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+}
+
+Reduce* new_reduce(Scratch& S, cudaStream_t st) {
+    Reduce* red = S.get<Reduce>(1);
+    CK(cudaMemsetAsync(red, 0, sizeof(Reduce), st));
+    CK(cudaMemsetAsync(red->rmin, 0xff, sizeof(red->rmin), st));
+    return red;
+}
+
+int exponent_of_ulp(double w) {  // every double >= w is an integer multiple of 2^E0
+    int e;
+    std::frexp(w, &e);
+    return e - 53;
+}
+
+int check_girg(const girg_params* p) {
+    if (!p) return GIRG_E_PARAM;
+    if (p->n < 2 || p->n >= (1ll << 31)) return GIRG_E_PARAM;
+    if (p->d < 1 || p->d > kMaxDim) return GIRG_E_PARAM;
+    if (!(p->beta > 2.0) || !(p->T >= 0.0 && p->T < 1.0) || !(p->w_min > 0.0)) return GIRG_E_PARAM;
+    if (p->edge_bytes != 4 && p->edge_bytes != 8) return GIRG_E_PARAM;
+    if (p->precision != 0 && p->precision != 1) return GIRG_E_PARAM;
+    if (!(p->c > 0.0) && !(p->avg_deg > 0.0 && p->avg_deg < (double)(p->n - 1))) return GIRG_E_PARAM;
+    if (p->level_cap < 0) return GIRG_E_PARAM;
+    return GIRG_OK;
+}
+
+template <class F>
+int guarded(F&& f) {
+    try {
+        return f();
+    } catch (const CudaFail& e) {
+        fprintf(stderr, "girg_gb300: CUDA error %s\n", cudaGetErrorString(e.err));
+        return GIRG_E_CUDA;
+    } catch (const Status& s) {
+        return s.code;
+    } catch (const std::bad_alloc&) {
+        return GIRG_E_INTERNAL;
+    }
+}
+
+// Solve c for the target degree from the device sums and the heaviest weights.
+double solve_c(Problem& P, double target, Scratch& S, cudaStream_t st) {
+    DegreeModel M(P.n, P.d, P.T, P.W, P.red.s2, P.red.st, P.red.s2t);
+    double wmax = 0.0;
+    for (int i = 0; i < kMaxLayers; ++i)
+        if (P.red.cnt[i]) wmax = std::max(wmax, bits_to_double(P.red.wmax[i]));
+    M.set_wmax(wmax);
+    unsigned int* cntp = S.get<unsigned int>(1);
+    unsigned int capv = 1u << 16;
+    double* buf = S.get<double>(capv);
+    auto fetch = [&](double thr) {
+        for (;;) {
+            CK(cudaMemsetAsync(cntp, 0, sizeof(unsigned int), st));
+            launch_gather_above(P.n, P.w, thr, buf, capv, cntp, st);
+            unsigned int k = 0;
+            CK(cudaMemcpyAsync(&k, cntp, sizeof(k), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (k > capv) {
+                capv = k + 1024;
+                buf = S.get<double>(capv);
+                continue;
+            }
+            std::vector<double> h(k);
+            if (k) CK(cudaMemcpyAsync(h.data(), buf, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            M.set_top(std::move(h), thr);
+            return;
+        }
+    };
+    return M.solve(target, fetch);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* girg_status_string(int status) {
+    switch (status) {
+        case GIRG_OK: return "ok";
+        case GIRG_E_PARAM: return "parameter out of range";
+        case GIRG_E_CAPACITY: return "edge buffer too small";
+        case GIRG_E_CUDA: return "CUDA error";
+        case GIRG_E_RANGE: return "weights span too wide a range for the exact sum";
+        case GIRG_E_INTERNAL: return "internal capacity or consistency check failed";
+        default: return "unknown status";
+    }
+}
+
+double girg_det_eval(int32_t fn, double x, double y) {
+    switch (fn) {
+        case 0: return det_log(x);
+        case 1: return det_log1p(x);
+        case 2: return det_exp(x);
+        case 3: return det_pow(x, y);
+        case 4: return det_sinpi(x);
+        case 5: return det_acosh(x);
+        case 6: return girg_p_at(x, y, 0.25, 1000.0, 0.5, 1.0 / 0.75, 0, 2);
+        default: return dnan();
+    }
+}
+
+int girg_last_stats(int64_t* out, int32_t len) {
+    const int k = len < kNumStats ? len : kNumStats;
+    for (int q = 0; q < k; ++q) out[q] = g_stats[q];
+    return k;
+}
+
+int girg_last_phase_ms(float* out, int32_t len) {
+    const int k = len < 7 ? len : 7;
+    for (int q = 0; q < k; ++q) out[q] = g_ms[q];
+    return k;
+}
+
+int girg_points(int64_t n, int32_t d, double beta, double w_min, uint64_t seed, double* d_w,
+                uint32_t* d_X, void* stream) {
+    if (n < 1 || d < 1 || d > kMaxDim || !(beta > 2.0) || !(w_min > 0.0)) return GIRG_E_PARAM;
+    return guarded([&] {
+        cudaStream_t st = (cudaStream_t)stream;
+        launch_girg_points(n, d, beta, w_min, seed, d_w, d_X, st);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(st));
+        return GIRG_OK;
+    });
+}
+
+int hrg_points(int64_t n, double alpha, double R, uint64_t seed, double* d_r, uint32_t* d_X,
+               void* stream) {
+    if (n < 1 || !(alpha > 0.5) || !(R > 0.0)) return GIRG_E_PARAM;
+    return guarded([&] {
+        cudaStream_t st = (cudaStream_t)stream;
+        launch_hrg_points(n, alpha, R, seed, d_r, nullptr, d_X, st);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(st));
+        return GIRG_OK;
+    });
+}
+
+int girg_generate(const girg_params* params, void* d_edges, int64_t capacity_edges,
+                  int64_t* num_edges, double* c_used, void* stream) {
+    const int chk = check_girg(params);
+    if (chk != GIRG_OK) return chk;
+    if (!num_edges || capacity_edges < 0) return GIRG_E_PARAM;
+    return guarded([&] {
+        cudaStream_t st = (cudaStream_t)stream;
+        Scratch S(st);
+        Timer tm(st);
+        g_launches = 0;
+        tm.mark();
+        Problem P;
+        P.model = 0;
+        P.n = params->n;
+        P.d = params->d;
+        P.T = params->T;
+        P.w_min = params->w_min;
+        P.seed = params->seed;
+        P.precision = params->precision;
+        P.edge_bytes = params->edge_bytes;
+        P.level_cap = params->level_cap;
+        double* w = S.get<double>(P.n);
+        uint32_t* X = S.get<uint32_t>((size_t)P.d * P.n);
+        launch_girg_points(P.n, P.d, params->beta, P.w_min, P.seed, w, X, st);
+        P.w = w;
+        P.X = X;
+        const bool solve = !(params->c > 0.0);
+        Reduce* red = new_reduce(S, st);
+        launch_reduce(P.n, w, nullptr, P.w_min, exponent_of_ulp(P.w_min), solve ? 1 : 0,
+                      P.T > 0.0 ? 1.0 / P.T : 0.0, red, st);
+        tm.mark();
+        read_reduce(P, red, st);
+        if (P.red.range_error) return GIRG_E_RANGE;
+        P.W = round128(P.red.sum_hi, P.red.sum_lo, exponent_of_ulp(P.w_min));
+        P.c = solve ? solve_c(P, params->avg_deg, S, st) : params->c;
+        if (c_used) *c_used = P.c;
+        run_sampler(P, S, st, tm, d_edges, capacity_edges, num_edges, nullptr);
+        finish_timing(tm);
+        return *num_edges > capacity_edges ? GIRG_E_CAPACITY : GIRG_OK;
+    });
+}
+
+int girg_expected_avg_degree(const girg_params* params, double* avg_deg, void* stream) {
+    if (!params || !avg_deg || !(params->c > 0.0)) return GIRG_E_PARAM;
+    girg_params q = *params;
+    const int chk = check_girg(&q);
+    if (chk != GIRG_OK) return chk;
+    return guarded([&] {
+        cudaStream_t st = (cudaStream_t)stream;
+        Scratch S(st);
+        Problem P;
+        P.n = q.n;
+        P.d = q.d;
+        P.T = q.T;
+        P.w_min = q.w_min;
+        double* w = S.get<double>(P.n);
+        uint32_t* X = S.get<uint32_t>((size_t)P.d * P.n);
+        launch_girg_points(P.n, P.d, q.beta, P.w_min, q.seed, w, X, st);
+        P.w = w;
+        Reduce* red = new_reduce(S, st);
+        launch_reduce(P.n, w, nullptr, P.w_min, exponent_of_ulp(P.w_min), 1,
+                      P.T > 0.0 ? 1.0 / P.T : 0.0, red, st);
+        read_reduce(P, red, st);
+        if (P.red.range_error) return GIRG_E_RANGE;
+        P.W = round128(P.red.sum_hi, P.red.sum_lo, exponent_of_ulp(P.w_min));
+        DegreeModel M(P.n, P.d, P.T, P.W, P.red.s2, P.red.st, P.red.s2t);
+        double wmax = 0.0;
+        for (int i = 0; i < kMaxLayers; ++i)
+            if (P.red.cnt[i]) wmax = std::max(wmax, bits_to_double(P.red.wmax[i]));
+        M.set_wmax(wmax);
+        const double thr = 0.5 * M.needed_threshold(q.c);
+        unsigned int* cntp = S.get<unsigned int>(1);
+        unsigned int capv = (unsigned int)std::min<int64_t>(P.n, 1 << 22);
+        double* buf = S.get<double>(capv);
+        CK(cudaMemsetAsync(cntp, 0, sizeof(unsigned int), st));
+        launch_gather_above(P.n, w, thr, buf, capv, cntp, st);
+        unsigned int k = 0;
+        CK(cudaMemcpyAsync(&k, cntp, sizeof(k), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (k > capv) return GIRG_E_INTERNAL;
+        std::vector<double> h(k);
+        if (k) CK(cudaMemcpyAsync(h.data(), buf, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        M.set_top(std::move(h), thr);
+        *avg_deg = M.f(q.c);
+        return GIRG_OK;
+    });
+}
+
+static int from_points_impl(int64_t n, int32_t d, const uint32_t* d_X, const double* d_w, double T,
+                            double c, uint64_t seed, int32_t precision, int32_t level_cap,
+                            int32_t edge_bytes, void* d_edges, int64_t capacity_edges,
+                            int64_t* num_edges, int64_t* order_out, void* stream) {
+    if (n < 2 || n >= (1ll << 31) || d < 1 || d > kMaxDim || !(T >= 0.0 && T < 1.0) || !(c > 0.0))
+        return GIRG_E_PARAM;
+    if ((edge_bytes != 4 && edge_bytes != 8) || (precision != 0 && precision != 1) || level_cap < 0)
+        return GIRG_E_PARAM;
+    if (!order_out && (!num_edges || capacity_edges < 0)) return GIRG_E_PARAM;
+    return guarded([&] {
+        cudaStream_t st = (cudaStream_t)stream;
+        Scratch S(st);
+        Timer tm(st);
+        g_launches = 0;
+        tm.mark();
+        Problem P;
+        P.n = n;
+        P.d = d;
+        P.T = T;
+        P.c = c;
+        P.seed = seed;
+        P.precision = precision;
+        P.edge_bytes = edge_bytes;
+        P.level_cap = level_cap;
+        P.X = d_X;
+        P.w = d_w;
+        unsigned long long* mn = S.get<unsigned long long>(1);
+        CK(cudaMemsetAsync(mn, 0xff, sizeof(unsigned long long), st));
+        launch_min_weight(n, d_w, mn, st);
+        unsigned long long mb = 0;
+        CK(cudaMemcpyAsync(&mb, mn, sizeof(mb), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        P.w_min = bits_to_double(mb);
+        if (!(P.w_min > 0.0)) return GIRG_E_PARAM;
+        const int E0 = exponent_of_ulp(P.w_min);
+        Reduce* red = new_reduce(S, st);
+        launch_reduce(n, d_w, nullptr, P.w_min, E0, 0, 0.0, red, st);
+        tm.mark();
+        read_reduce(P, red, st);
+        if (P.red.range_error) return GIRG_E_RANGE;
+        P.W = round128(P.red.sum_hi, P.red.sum_lo, E0);
+        int64_t dummy = 0;
+        run_sampler(P, S, st, tm, d_edges, capacity_edges, num_edges ? num_edges : &dummy, order_out);
+        if (order_out) return GIRG_OK;
+        finish_timing(tm);
+        return *num_edges > capacity_edges ? GIRG_E_CAPACITY : GIRG_OK;
+    });
+}
+
+int girg_generate_from_points(int64_t n, int32_t d, const uint32_t* d_X, const double* d_w,
+                              double T, double c, uint64_t seed, int32_t precision,
+                              int32_t level_cap, int32_t edge_bytes, void* d_edges,
+                              int64_t capacity_edges, int64_t* num_edges, void* stream) {
+    return from_points_impl(n, d, d_X, d_w, T, c, seed, precision, level_cap, edge_bytes, d_edges,
+                            capacity_edges, num_edges, nullptr, stream);
+}
+
+int girg_sorted_order(int64_t n, int32_t d, const uint32_t* d_X, const double* d_w, double T,
+                      double c, int32_t level_cap, int64_t* d_order, void* stream) {
+    if (!d_order) return GIRG_E_PARAM;
+    return from_points_impl(n, d, d_X, d_w, T, c, 0, 0, level_cap, 4, nullptr, 0, nullptr,
+                            d_order, stream);
+}
+
+int hrg_generate(const hrg_params* params, void* d_edges, int64_t capacity_edges,
+                 int64_t* num_edges, void* stream) {
+    if (!params || !num_edges || capacity_edges < 0) return GIRG_E_PARAM;
+    const hrg_params& q = *params;
+    if (q.n < 2 || q.n >= (1ll << 31) || !(q.alpha > 0.5) || !(q.T >= 0.0 && q.T < 1.0) ||
+        !(q.R > 0.0))
+        return GIRG_E_PARAM;
+    if ((q.edge_bytes != 4 && q.edge_bytes != 8) || (q.precision != 0 && q.precision != 1) ||
+        q.level_cap < 0)
+        return GIRG_E_PARAM;
+    return guarded([&] {
+        cudaStream_t st = (cudaStream_t)stream;
+        Scratch S(st);
+        Timer tm(st);
+        g_launches = 0;
+        tm.mark();
+        Problem P;
+        P.model = 1;
+        P.n = q.n;
+        P.d = 1;
+        P.T = q.T;
+        P.R = q.R;
+        P.alpha = q.alpha;
+        P.w_min = 1.0;
+        P.seed = q.seed;
+        P.precision = q.precision;
+        P.edge_bytes = q.edge_bytes;
+        P.level_cap = q.level_cap;
+        double* r = S.get<double>(P.n);
+        double* w = S.get<double>(P.n);
+        uint32_t* X = S.get<uint32_t>(P.n);
+        launch_hrg_points(P.n, q.alpha, q.R, q.seed, r, w, X, st);
+        P.r = r;
+        P.w = w;
+        P.X = X;
+        Reduce* red = new_reduce(S, st);
+        launch_reduce(P.n, w, r, 1.0, exponent_of_ulp(1.0), 0, 0.0, red, st);
+        tm.mark();
+        read_reduce(P, red, st);  // the HRG needs no weight sum: a range error is harmless
+        P.W = 1.0;
+        run_sampler(P, S, st, tm, d_edges, capacity_edges, num_edges, nullptr);
+        finish_timing(tm);
+        return *num_edges > capacity_edges ? GIRG_E_CAPACITY : GIRG_OK;
+    });
+}
+
+int girg_allpairs(int64_t n, int32_t d, const uint32_t* d_X, const double* d_w, double W,
+                  double T, double c, uint64_t seed, int32_t precision, int32_t edge_bytes,
+                  void* d_edges, int64_t capacity_edges, int64_t* num_edges, void* stream) {
+    if (n < 2 || n >= (1ll << 31) || d < 1 || d > kMaxDim || !(T >= 0.0 && T < 1.0) || !(c > 0.0) ||
+        !(W > 0.0) || !num_edges || capacity_edges < 0)
+        return GIRG_E_PARAM;
+    if ((edge_bytes != 4 && edge_bytes != 8) || (precision != 0 && precision != 1)) return GIRG_E_PARAM;
+    return guarded([&] {
+        cudaStream_t st = (cudaStream_t)stream;
+        Scratch S(st);
+        float* sv = S.get<float>(n);
+        const bool tzero = T == 0.0;
+        const float gamma = (float)(tzero ? 0.5 * std::log2(c) : (T / (2.0 * d)) * std::log2(c));
+        launch_scale(n, d_w, 0.5 * std::log2(W), gamma, (float)(1.0 / d), sv, st);
+        unsigned long long* stats = S.get<unsigned long long>(kNumStats + 2);
+        CK(cudaMemsetAsync(stats, 0, (kNumStats + 2) * sizeof(unsigned long long), st));
+        DevCfg cfg;
+        memset(&cfg, 0, sizeof(cfg));
+        cfg.n = (int32_t)n;
+        cfg.d = d;
+        cfg.precision = precision;
+        cfg.tzero = tzero ? 1 : 0;
+        const double invT = T > 0.0 ? 1.0 / T : 0.0;
+        cfg.invT = invT;
+        cfg.m_int = (T > 0.0 && invT == std::floor(invT) && invT <= 64.0) ? (int)invT : 0;
+        cfg.seed_lo = (uint32_t)seed;
+        cfg.seed_hi = (uint32_t)(seed >> 32);
+        cfg.W = W;
+        cfg.c = c;
+        cfg.T = T;
+        cfg.dT = T > 0.0 ? (float)(d / T) : 0.0f;
+        cfg.bandG = cfg.dT * 0x1p-14f + 0x1p-15f;
+        cfg.band_ratio = 0x1p-16f;
+        cfg.edges = d_edges;
+        cfg.edge_bytes = edge_bytes;
+        cfg.cap = capacity_edges;
+        cfg.edge_count = stats + kNumStats;
+        cfg.stats = stats;
+        launch_allpairs(cfg, d_X, d_w, sv, st);
+        unsigned long long m = 0;
+        CK(cudaMemcpyAsync(&m, stats + kNumStats, sizeof(m), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        *num_edges = (int64_t)m;
+        return *num_edges > capacity_edges ? GIRG_E_CAPACITY : GIRG_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,265 @@
+// Device-side configuration, tables and helpers shared by the kernels.
+#pragma once
+#include <cooperative_groups.h>
+#include "common.cuh"
+
+namespace gg {
+
+// Bound p-bar of a type-II item class (bucket pair, level, gap g in {1, 2}), its
+// ln(1 - p-bar) and single-precision companions (Sec. 3.2).
+struct TwoEntry {
+    double pbar;
+    double Lb;        // ln(1 - pbar) (0 when pbar = 1)
+    float log2pbar;   // log2(pbar) rounded to float
+    float invLb;      // 1 / Lb rounded to float (-inf when pbar = 1)
+    int32_t k;        // chunk length exponent
+    int32_t pad;
+};
+
+// One entry of the bucket list of a row class (i, l): bucket j and the kind of
+// cell pairs (1: neighbours, type I; 2: distant with neighbouring parents,
+// type II), with the number of offset combinations before it.
+struct ClassEntry {
+    uint16_t j;
+    uint16_t type;
+    uint32_t prefix;
+};
+
+// A type-I item: rectangle V_i^A x V_j^B of sorted positions; bit 31 of b_len
+// marks the (A, A, i, i) items that only test pairs at positions a < b.
+struct T1Item {
+    uint32_t a_begin, a_len, b_begin, b_len;
+};
+
+// A type-II item whose index space spans several chunks.
+struct HeavyItem {
+    uint32_t a_begin, a_len, b_begin, b_len;
+    uint32_t A, B;
+    uint32_t pack;  // l | i << 5 | j << 11
+    uint32_t tii;   // index of its TwoEntry
+    uint64_t chunk_prefix;  // exclusive prefix of chunk counts (filled by a scan)
+};
+
+enum : int { kStatT1Pairs = 0, kStatCoins, kStatRecheck, kStatT2Items, kStatDraws,
+             kStatCands, kStatRows, kStatT1Items, kStatHeavyChunks, kStatEdges,
+             kStatLaunches, kStatT1VertexRefs, kStatT1Edges, kNumStats };
+
+enum : uint32_t { kModeT1 = 1u, kModeT2Light = 2u, kModeT2Heavy = 4u };
+
+struct DevCfg {
+    int32_t n, d, L, model, precision, tzero, m_int, lcap;
+    int32_t n3, n6;  // 3^d and 6^d
+    uint32_t seed_lo, seed_hi;
+    uint32_t mode;
+    double W, c, T, invT, w_min, R, coshR;
+    float dT;          // d / T (GIRG)
+    float bandG;       // band in the log2 domain of decisions
+    float band_ratio;  // relative band of kappa / r
+    float coshR32;     // cosh R rounded to float (HRG)
+    float R32, inv2T32;
+    int32_t filt_k;
+    int8_t I[kMaxLayers];
+    uint8_t CLd[kMaxLayers];
+    uint32_t layer_base[kMaxLayers + 1];
+    uint32_t lstart[kMaxLayers + 1];
+    const TwoEntry* tii;
+    const uint32_t* class_start;  // [(i * (kMaxLevel + 1) + l)] -> first entry
+    const uint32_t* class_nent;   // number of entries of the class
+    const uint32_t* class_total;  // number of offset combinations of the class
+    const ClassEntry* entries;
+    const uint32_t* offs;
+    const uint32_t* Xs;   // d x n sorted coordinates
+    const float* sv;      // sorted per-vertex scale (GIRG)
+    const double* ws;     // sorted weights (GIRG) / radii (HRG)
+    const uint32_t* ids;  // sorted original ids
+    const uint32_t* skey; // sorted keys (global cell index at the insertion level)
+    const uint8_t* slayer;
+    const float* E32;     // HRG e^r, e^-r, sinh r (sorted)
+    const float* einv32;
+    const float* sh32;
+    const float* filt_lo;  // HRG distance filter (cosh thresholds), rounded down
+    const float* filt_hi;  // rounded up
+    void* edges;
+    int32_t edge_bytes;
+    int64_t cap;
+    unsigned long long* edge_count;
+    unsigned long long* stats;
+    const uint64_t* rows;
+    const unsigned int* row_count;
+    uint32_t row_cap;
+    T1Item* t1;
+    unsigned int* t1_count;
+    uint32_t t1_cap;
+    HeavyItem* heavy;
+    unsigned int* heavy_count;
+    uint32_t heavy_cap;
+    unsigned int* work_counter;  // dynamic scheduling counters [4]
+};
+
+// --------------------------------------------------------------- bit tricks
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Put bit b of x at position b * d (x < 2^(32/d)).
+__device__ __forceinline__ uint32_t spread_bits(uint32_t x, int d) {
+    if (d == 1) return x;
+    if (d == 2) {
+        x &= 0x0000ffffu;
+        x = (x | (x << 8)) & 0x00ff00ffu;
+        x = (x | (x << 4)) & 0x0f0f0f0fu;
+        x = (x | (x << 2)) & 0x33333333u;
+        x = (x | (x << 1)) & 0x55555555u;
+        return x;
+    }
+    if (d == 4) {
+        x &= 0xffu;
+        x = (x | (x << 12)) & 0x000f000fu;
+        x = (x | (x << 6)) & 0x03030303u;
+        x = (x | (x << 3)) & 0x11111111u;
+        return x;
+    }
+    uint32_t r = 0;
+    for (int b = 0; b * d < 32 && b < 32; ++b) r |= ((x >> b) & 1u) << (b * d);
+    return r;
+}
+
+// Inverse of spread_bits.
+__device__ __forceinline__ uint32_t compact_bits(uint32_t x, int d) {
+    if (d == 1) return x;
+    if (d == 2) {
+        x &= 0x55555555u;
+        x = (x | (x >> 1)) & 0x33333333u;
+        x = (x | (x >> 2)) & 0x0f0f0f0fu;
+        x = (x | (x >> 4)) & 0x00ff00ffu;
+        x = (x | (x >> 8)) & 0x0000ffffu;
+        return x;
+    }
+    uint32_t r = 0;
+    for (int b = 0; b * d < 32 && b < 32; ++b) r |= ((x >> (b * d)) & 1u) << b;
+    return r;
+}
+
+// Morton code of cell coordinates at level l (coordinate 0 most significant
+// within every d-bit group, Sec. 4.2).
+__device__ __forceinline__ uint32_t morton_encode(const uint32_t* coord, int d) {
+    uint32_t code = 0;
+    for (int k = 0; k < d; ++k) code |= spread_bits(coord[k], d) << (d - 1 - k);
+    return code;
+}
+
+__device__ __forceinline__ void morton_decode(uint32_t code, int d, uint32_t* coord) {
+    for (int k = 0; k < d; ++k) coord[k] = compact_bits(code >> (d - 1 - k), d);
+}
+
+// --------------------------------------------------------------- edge output
+// Per-warp edge buffer in shared memory, flushed with one global atomic.
+constexpr int kEdgeBuf = 256;
+
+struct WarpEdges {
+    uint32_t* a;      // kEdgeBuf entries
+    uint32_t* b;
+    unsigned int* n;  // count (shared)
+};
+
+__device__ __forceinline__ void write_edge(const DevCfg& cfg, unsigned long long slot, uint32_t a,
+                                           uint32_t b) {
+    if ((long long)slot >= cfg.cap) return;
+    if (cfg.edge_bytes == 4) {
+        reinterpret_cast<uint2*>(cfg.edges)[slot] = make_uint2(a, b);
+    } else {
+        reinterpret_cast<ulonglong2*>(cfg.edges)[slot] = make_ulonglong2(a, b);
+    }
+}
+
+// Append one edge (u, v as original ids, any order) from any subset of lanes.
+__device__ __forceinline__ void push_edge(const DevCfg& cfg, WarpEdges& we, uint32_t u, uint32_t v) {
+    const uint32_t a = u < v ? u : v, b = u < v ? v : u;
+    const unsigned int slot = atomicAdd(we.n, 1u);
+    if (slot < (unsigned)kEdgeBuf) {
+        we.a[slot] = a;
+        we.b[slot] = b;
+    } else {
+        const unsigned long long g = atomicAdd(cfg.edge_count, 1ull);
+        write_edge(cfg, g, a, b);
+    }
+}
+
+// Whole warp: write out the buffer if it holds at least `threshold` edges.
+__device__ __forceinline__ void flush_edges(const DevCfg& cfg, WarpEdges& we, unsigned threshold) {
+    __syncwarp();
+    unsigned int cnt = *we.n;
+    if (cnt > (unsigned)kEdgeBuf) cnt = kEdgeBuf;
+    if (cnt >= threshold && cnt > 0) {
+        const int lane = threadIdx.x & 31;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(cfg.edge_count, (unsigned long long)cnt);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (unsigned int t = lane; t < cnt; t += 32) write_edge(cfg, base + t, we.a[t], we.b[t]);
+        __syncwarp();
+        if (lane == 0) *we.n = 0;
+    }
+    __syncwarp();
+}
+
+// --------------------------------------------------------------- uniforms in float
+// log2 of U = (2 (bits >> 12) + 1) 2^-53 in single precision (relative error of
+// the argument <= 2^-24).
+__device__ __forceinline__ float log2_uniform32(uint32_t lo, uint32_t hi) {
+    const unsigned long long bits = ((unsigned long long)hi << 32) | lo;
+    const float u = __ull2float_rn(2ull * (bits >> 12) + 1ull) * 0x1p-53f;
+    return log2f(u);
+}
+
+// ln U in single precision with small relative error for all U in (0,1):
+// for U >= 1/2 through 1 - U, which is exact as an integer multiple of 2^-53.
+__device__ __forceinline__ float ln_uniform32(uint32_t lo, uint32_t hi) {
+    const unsigned long long bits = ((unsigned long long)hi << 32) | lo;
+    const unsigned long long K = bits >> 12;
+    if (K >= (1ull << 51)) {
+        const unsigned long long M = (1ull << 53) - 1ull - 2ull * K;
+        return log1pf(-__ull2float_rn(M) * 0x1p-53f);
+    }
+    return logf(__ull2float_rn(2ull * K + 1ull) * 0x1p-53f);
+}
+
+// Geometric jump X = floor(ln U / ln(1 - pbar)) against the remaining length rem
+// of the chunk.  Returns 0: stop (X >= rem), 1: continue with *X, decided in
+// single precision with a 2^-19 relative error bound, or 2: undecided, the
+// caller evaluates the FP64 rule.
+__device__ __forceinline__ int jump32(uint32_t lo, uint32_t hi, float invLb, unsigned long long rem,
+                                      unsigned long long* X) {
+    const float x = ln_uniform32(lo, hi) * invLb;  // >= 0
+    const float xlo = x * (1.0f - 0x1p-19f), xhi = x * (1.0f + 0x1p-19f);
+    if (rem < (1ull << 24)) {
+        const float remf = (float)rem;
+        if (xlo >= remf) return 0;
+        if (xhi < remf && floorf(xlo) == floorf(xhi)) {
+            *X = (unsigned long long)floorf(xhi);
+            return 1;
+        }
+        return 2;
+    }
+    const float remf = (float)rem;
+    if (xlo >= remf * (1.0f + 0x1p-22f)) return 0;
+    if (xhi < 0x1p22f && floorf(xlo) == floorf(xhi)) {
+        *X = (unsigned long long)floorf(xhi);
+        return 1;
+    }
+    return 2;
+}
+
+// The exact FP64 rule: 0 stop, 1 continue with *X.
+__device__ __forceinline__ int jump64(uint32_t lo, uint32_t hi, double Lb, unsigned long long rem,
+                                      unsigned long long* X) {
+    const double x = floor(DDIV(det_log(uniform53(lo, hi)), Lb));
+    if (x >= 0x1p63) return 0;
+    const unsigned long long xi = (unsigned long long)x;
+    if (xi >= rem) return 0;
+    *X = xi;
+    return 1;
+}
+
+}  // namespace gg

@@ -1,0 +1,69 @@
+// Launchers of the device kernels (host-side declarations).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gg {
+
+struct DevCfg;
+
+// Kernel launches issued by the library on this host thread (for the benchmark's
+// launch count).
+extern thread_local unsigned long long g_launches;
+
+// Results of the weight reduction pass.
+struct Reduce {
+    unsigned long long sum_lo, sum_hi;  // exact sum of the weights in units of 2^E0
+    unsigned long long cnt[64];         // vertices per bucket
+    unsigned long long wmax[64];        // largest weight per bucket (bits)
+    unsigned long long rmin[64];        // HRG: smallest radius per bucket (bits)
+    unsigned long long rmax[64];        // HRG: largest radius per bucket (bits)
+    double s2, st, s2t;                 // sum w^2, sum w^(1/T), sum w^(2/T)
+    unsigned int range_error;
+    unsigned int pad;
+};
+
+void launch_girg_points(int64_t n, int d, double beta, double w_min, uint64_t seed, double* w,
+                        uint32_t* X, cudaStream_t st);
+void launch_hrg_points(int64_t n, double alpha, double R, uint64_t seed, double* r, double* w,
+                       uint32_t* X, cudaStream_t st);
+void launch_min_weight(int64_t n, const double* w, unsigned long long* out, cudaStream_t st);
+void launch_reduce(int64_t n, const double* w, const double* r, double w_min, int E0,
+                   int want_sums, double invT, Reduce* out, cudaStream_t st);
+void launch_gather_above(int64_t n, const double* w, double thr, double* out, unsigned int cap,
+                         unsigned int* count, cudaStream_t st);
+
+// Sorting: keys (global cell index at the insertion level) with a histogram.
+void launch_keys(int64_t n, int d, const double* w, const uint32_t* X, double w_min,
+                 const int8_t* I, const uint32_t* layer_base, uint32_t* key, uint32_t* val,
+                 uint32_t* cnt, cudaStream_t st);
+// Exclusive scan of n uint32 values in place (out may alias in); tmp >= scan_tmp_words(n).
+size_t scan_tmp_words(int64_t n);
+void launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t st);
+// Stable LSD radix sort of (key, val) on the low `bits` bits of key.
+size_t radix_tmp_words(int64_t n);
+void radix_sort_pairs(uint32_t* key, uint32_t* val, uint32_t* key_alt, uint32_t* val_alt,
+                      int64_t n, int bits, uint32_t* tmp, cudaStream_t st, uint32_t** key_out,
+                      uint32_t** val_out);
+// Sorted per-vertex arrays.
+void launch_gather_girg(int64_t n, int d, const uint32_t* perm, const uint32_t* X,
+                        const double* w, double w_min, double log2W_half, float gamma,
+                        float invd, uint32_t* Xs, double* ws, float* sv, uint8_t* slayer,
+                        cudaStream_t st);
+void launch_gather_hrg(int64_t n, const uint32_t* perm, const uint32_t* X, const double* r,
+                       const double* w, uint32_t* Xs, double* rs, float* E32, float* einv32,
+                       float* sh32, uint8_t* slayer, cudaStream_t st);
+
+// Pair sampling.
+void launch_rows(const DevCfg& cfg, uint64_t* rows, unsigned int* row_count, unsigned int cap,
+                 cudaStream_t st);
+void launch_enumerate(const DevCfg& cfg, cudaStream_t st);
+void launch_type1(const DevCfg& cfg, cudaStream_t st);
+void launch_heavy_scan(const DevCfg& cfg, unsigned long long* total_chunks, cudaStream_t st);
+void launch_heavy(const DevCfg& cfg, const unsigned long long* total_chunks, cudaStream_t st);
+void launch_allpairs(const DevCfg& cfg, const uint32_t* X, const double* w, const float* sv,
+                     cudaStream_t st);
+void launch_scale(int64_t n, const double* w, double log2W_half, float gamma, float invd,
+                  float* sv, cudaStream_t st);
+
+}  // namespace gg

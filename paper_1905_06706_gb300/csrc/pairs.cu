@@ -1,0 +1,679 @@
+// Edge sampling: the cell pairs of Algorithm 1 (Sec. 3.3) with the
+// double-counting rules of App. B.1, all-pairs tests on neighbouring cells
+// (type I), geometric jumps with rejection on distant cells (type II, Sec. 3.2),
+// and warp-aggregated compaction of the edges.
+//
+// Instead of recursing from the root pair, the device enumerates "rows"
+// (bucket i, level l, non-empty cell A of V_i at level l).  A warp takes a row
+// and its lanes take the (bucket j, cell B) combinations that Algorithm 1
+// processes with A: the neighbours B of A when CL(i,j) = l (type I) and the
+// cells B that are distant from A but have neighbouring parents when
+// CL(i,j) >= l (type II), for buckets j >= i; for j = i only B >= A (type I)
+// or B > A (type II).  This visits exactly the (cell pair, bucket pair) items
+// of the recursion, in a different order.
+//
+// Decisions are made in single precision with a rigorous error band; inside
+// the band they are recomputed with the exact FP64 rule (the same arithmetic
+// as the FP64 reference), so the edge set equals the FP64 one.
+#include "internal.cuh"
+#include "kernels.h"
+
+namespace cg = cooperative_groups;
+
+namespace gg {
+
+// ------------------------------------------------------------------ per-pair decisions
+struct Counters {
+    unsigned long long t1pairs = 0, coins = 0, recheck = 0, t2items = 0, draws = 0, cands = 0;
+};
+
+struct View {  // per-vertex arrays indexed by position
+    const uint32_t* X;
+    const float* sv;
+    const double* w;   // GIRG weights or HRG radii
+    const uint32_t* ids;  // nullptr: id = position
+    const float* E32;
+    const float* einv32;
+    const float* sh32;
+    int64_t n;
+};
+
+__device__ __forceinline__ View sorted_view(const DevCfg& cfg) {
+    return View{cfg.Xs, cfg.sv, cfg.ws, cfg.ids, cfg.E32, cfg.einv32, cfg.sh32, cfg.n};
+}
+
+__device__ __forceinline__ uint32_t vid(const View& V, uint32_t p) { return V.ids ? V.ids[p] : p; }
+
+__device__ __forceinline__ uint32_t torus_D(const DevCfg& cfg, const View& V, uint32_t pu,
+                                            uint32_t pv) {
+    uint32_t m = 0;
+    for (int k = 0; k < cfg.d; ++k) {
+        const uint32_t t = circ_diff(V.X[(int64_t)k * V.n + pu], V.X[(int64_t)k * V.n + pv]);
+        m = t > m ? t : m;
+    }
+    return m;
+}
+
+// kappa_uv / r in single precision (D > 0).
+__device__ __forceinline__ float kappa_ratio(const View& V, uint32_t pu, uint32_t pv, uint32_t D) {
+    return V.sv[pu] * V.sv[pv] * (4294967296.0f / (float)D);
+}
+
+__device__ __forceinline__ double girg_p_pair(const DevCfg& cfg, const View& V, uint32_t pu,
+                                              uint32_t pv, uint32_t D) {
+    return girg_p64(V.w[pu], V.w[pv], D, cfg.W, cfg.c, cfg.invT, cfg.m_int, cfg.d);
+}
+
+// HRG cosh d in FP64 from the radii of both vertices.
+__device__ __forceinline__ double hrg_coshd_pair(const View& V, uint32_t pu, uint32_t pv, uint32_t D) {
+    double Eu, shu, Ev, shv;
+    hrg_vertex64(V.w[pu], &Eu, &shu);
+    hrg_vertex64(V.w[pv], &Ev, &shv);
+    return hrg_coshd64(Eu, shu, Ev, shv, D);
+}
+
+__device__ __forceinline__ float hrg_coshd32(const View& V, uint32_t pu, uint32_t pv, uint32_t D) {
+    const float s = sinpif((float)D * 0x1p-32f);
+    const float ch = 0.5f * (V.E32[pu] * V.einv32[pv] + V.E32[pv] * V.einv32[pu]);
+    return ch + 2.0f * V.sh32[pu] * V.sh32[pv] * (s * s);
+}
+
+__device__ __forceinline__ float hrg_p32(const DevCfg& cfg, float cd) {
+    return 1.0f / (expf((acoshf(cd) - cfg.R32) * cfg.inv2T32) + 1.0f);
+}
+
+// Type I: edge iff U(seed, u, v) < p_uv (T > 0) or the threshold rule (T = 0).
+__device__ bool decide_t1(const DevCfg& cfg, const View& V, uint32_t pu, uint32_t pv, Counters& C) {
+    const uint32_t iu = vid(V, pu), iv = vid(V, pv);
+    const uint32_t a = iu < iv ? iu : iv, b = iu < iv ? iv : iu;
+    if (cfg.model == 0) {
+        const uint32_t D = torus_D(cfg, V, pu, pv);
+        if (D == 0) return true;
+        if (cfg.precision == 1) {
+            if (cfg.tzero) return girg_thresh64(V.w[pu], V.w[pv], D, cfg.W, cfg.c, cfg.d);
+            ++C.coins;
+            const P4 o = philox(a, b, kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
+            return uniform53(o.x, o.y) < girg_p_pair(cfg, V, pu, pv, D);
+        }
+        const float ratio = kappa_ratio(V, pu, pv, D);
+        if (cfg.tzero) {
+            if (ratio > 1.0f + cfg.band_ratio) return true;
+            if (ratio < 1.0f - cfg.band_ratio) return false;
+            ++C.recheck;
+            return girg_thresh64(V.w[pu], V.w[pv], D, cfg.W, cfg.c, cfg.d);
+        }
+        if (ratio >= 1.0f + cfg.band_ratio) return true;  // p = 1
+        const float lp = cfg.dT * log2f(ratio);          // log2 p
+        if (lp < -54.0f - cfg.bandG) return false;        // p < 2^-54 < every U
+        ++C.coins;
+        const P4 o = philox(a, b, kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
+        const float G = lp - log2_uniform32(o.x, o.y);
+        if (G > cfg.bandG) return true;
+        if (G < -cfg.bandG) return false;
+        ++C.recheck;
+        return uniform53(o.x, o.y) < girg_p_pair(cfg, V, pu, pv, D);
+    }
+    // HRG (Sec. 2.2): threshold d < R, binomial U < p_T(d)
+    const uint32_t D = circ_diff(V.X[pu], V.X[pv]);
+    if (cfg.precision == 1) {
+        const double cd = hrg_coshd_pair(V, pu, pv, D);
+        if (cfg.tzero) return cd < cfg.coshR;
+        ++C.coins;
+        const P4 o = philox(a, b, kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
+        return uniform53(o.x, o.y) < hrg_p_from_coshd(cd, cfg.R, cfg.T);
+    }
+    const float cd = hrg_coshd32(V, pu, pv, D);
+    if (cfg.tzero) {
+        if (cd < cfg.coshR32 * (1.0f - 0x1p-16f)) return true;
+        if (cd > cfg.coshR32 * (1.0f + 0x1p-16f)) return false;
+        ++C.recheck;
+        return hrg_coshd_pair(V, pu, pv, D) < cfg.coshR;
+    }
+    ++C.coins;
+    const P4 o = philox(a, b, kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
+    // distance filter (Sec. 4.3): the bin of U brackets the threshold on cosh d
+    const unsigned long long bits = ((unsigned long long)o.y << 32) | o.x;
+    const unsigned long long odd = 2ull * (bits >> 12) + 1ull;
+    const int m = (int)((odd * (unsigned long long)(cfg.filt_k - 1)) >> 53);
+    if (cd * (1.0f + 0x1p-16f) < cfg.filt_lo[m + 1]) return true;
+    if (cd * (1.0f - 0x1p-16f) >= cfg.filt_hi[m]) return false;
+    const float p32 = hrg_p32(cfg, cd);
+    const float u32 = __ull2float_rn(odd) * 0x1p-53f;
+    const float band = cfg.bandG;
+    if (u32 < p32 * (1.0f - band)) return true;
+    if (u32 > p32 * (1.0f + band)) return false;
+    ++C.recheck;
+    return uniform53(o.x, o.y) < hrg_p_from_coshd(hrg_coshd_pair(V, pu, pv, D), cfg.R, cfg.T);
+}
+
+// Type-II acceptance: accept iff U' pbar < p_uv.
+__device__ bool accept_t2(const DevCfg& cfg, const View& V, uint32_t pu, uint32_t pv, uint32_t lo,
+                          uint32_t hi, const TwoEntry& e, Counters& C) {
+    if (cfg.model == 0) {
+        const uint32_t D = torus_D(cfg, V, pu, pv);
+        if (cfg.precision == 1) {
+            const double p = D == 0 ? 1.0 : girg_p_pair(cfg, V, pu, pv, D);
+            return DMUL(uniform53(lo, hi), e.pbar) < p;
+        }
+        if (D == 0) return true;
+        const float ratio = kappa_ratio(V, pu, pv, D);
+        if (ratio >= 1.0f + cfg.band_ratio) return true;
+        const float G = cfg.dT * log2f(ratio) - log2_uniform32(lo, hi) - e.log2pbar;
+        if (G > cfg.bandG) return true;
+        if (G < -cfg.bandG) return false;
+        ++C.recheck;
+        return DMUL(uniform53(lo, hi), e.pbar) < girg_p_pair(cfg, V, pu, pv, D);
+    }
+    const uint32_t D = circ_diff(V.X[pu], V.X[pv]);
+    if (cfg.precision == 1)
+        return DMUL(uniform53(lo, hi), e.pbar) <
+               hrg_p_from_coshd(hrg_coshd_pair(V, pu, pv, D), cfg.R, cfg.T);
+    const float p32 = hrg_p32(cfg, hrg_coshd32(V, pu, pv, D));
+    const unsigned long long bits = ((unsigned long long)hi << 32) | lo;
+    const float up = __ull2float_rn(2ull * (bits >> 12) + 1ull) * 0x1p-53f * (float)e.pbar;
+    if (up < p32 * (1.0f - cfg.bandG)) return true;
+    if (up > p32 * (1.0f + cfg.bandG)) return false;
+    ++C.recheck;
+    return DMUL(uniform53(lo, hi), e.pbar) <
+           hrg_p_from_coshd(hrg_coshd_pair(V, pu, pv, D), cfg.R, cfg.T);
+}
+
+// One chunk of geometric jumps over [start, start + len) of the a x b index space
+// of a type-II item (Sec. 3.2).  Draw t of the chunk comes from `draw(t)`.
+template <class Draw>
+__device__ void jump_chunk(const DevCfg& cfg, const View& V, WarpEdges& we, const TwoEntry& e,
+                           uint32_t a_begin, uint32_t b_begin, uint32_t b_len,
+                           unsigned long long start, unsigned long long len, Draw draw,
+                           Counters& C) {
+    long long s = -1;
+    for (uint32_t t = 0;; ++t) {
+        const P4 o = draw(t);
+        ++C.draws;
+        const unsigned long long rem = len - (unsigned long long)(s + 1);
+        unsigned long long X = 0;
+        if (e.pbar < 1.0) {
+            int r = 2;
+            if (cfg.precision == 0) r = jump32(o.x, o.y, e.invLb, rem, &X);
+            if (r == 2) {
+                if (cfg.precision == 0) ++C.recheck;
+                r = jump64(o.x, o.y, e.Lb, rem, &X);
+            }
+            if (r == 0) break;
+        } else if (rem == 0) {
+            break;
+        }
+        s += 1 + (long long)X;
+        ++C.cands;
+        const unsigned long long idx = start + (unsigned long long)s;
+        uint32_t ia, ib;
+        if (idx < (1ull << 32)) {
+            ia = (uint32_t)idx / b_len;
+            ib = (uint32_t)idx - ia * b_len;
+        } else {
+            ia = (uint32_t)(idx / b_len);
+            ib = (uint32_t)(idx - (unsigned long long)ia * b_len);
+        }
+        const uint32_t pu = a_begin + ia, pv = b_begin + ib;
+        if (accept_t2(cfg, V, pu, pv, o.z, o.w, e, C)) push_edge(cfg, we, vid(V, pu), vid(V, pv));
+    }
+}
+
+__device__ __forceinline__ void flush_counters(const DevCfg& cfg, const Counters& C) {
+    unsigned long long v[6] = {C.t1pairs, C.coins, C.recheck, C.t2items, C.draws, C.cands};
+    const int idx[6] = {kStatT1Pairs, kStatCoins, kStatRecheck, kStatT2Items, kStatDraws, kStatCands};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        unsigned long long x = v[q];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(&cfg.stats[idx[q]], x);
+    }
+}
+
+// ------------------------------------------------------------------ rows
+// Row heads: the first sorted position of every non-empty (bucket i, level l, cell)
+// for l <= CL(i, i).
+__global__ void k_rows(DevCfg cfg, uint64_t* __restrict__ rows, unsigned int* __restrict__ count,
+                       unsigned int cap) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n = cfg.n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p0 = blockIdx.x * (int64_t)blockDim.x; p0 < n; p0 += stride) {
+        const int64_t p = p0 + threadIdx.x;
+        int i = 0, top = -1;
+        uint32_t cell = 0, prev = 0;
+        bool first = false;
+        if (p < n) {
+            i = cfg.slayer[p];
+            const uint32_t base = cfg.layer_base[i];
+            cell = cfg.skey[p] - base;
+            first = (uint32_t)p == cfg.lstart[i];
+            prev = first ? 0u : cfg.skey[p - 1] - base;
+            top = cfg.CLd[i];
+        }
+        unsigned int mine = 0;
+        for (int l = 0; l <= top; ++l) {
+            const int s = cfg.d * (cfg.I[i] - l);
+            if (first || ((uint64_t)cell >> s) != ((uint64_t)prev >> s)) ++mine;
+        }
+        unsigned int incl = mine;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        unsigned int base = 0;
+        if (lane == 31) base = atomicAdd(count, incl);
+        base = __shfl_sync(0xffffffffu, base, 31) + incl - mine;
+        for (int l = 0; l <= top; ++l) {
+            const int s = cfg.d * (cfg.I[i] - l);
+            if (first || ((uint64_t)cell >> s) != ((uint64_t)prev >> s)) {
+                if (base < cap)
+                    rows[base] = (uint64_t)p | ((uint64_t)l << 32) | ((uint64_t)i << 40);
+                ++base;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ enumeration
+constexpr int kEnumThreads = 256;
+constexpr int kWarps = kEnumThreads / 32;
+constexpr uint32_t kSplitB = 1024, kSplitAB = 4096;
+
+__device__ __forceinline__ uint32_t vrange_lo(const DevCfg& cfg, int j, uint32_t B, int l) {
+    const int s = cfg.d * (cfg.I[j] - l);
+    return cfg.offs[cfg.layer_base[j] + (uint32_t)((uint64_t)B << s)];
+}
+__device__ __forceinline__ uint32_t vrange_hi(const DevCfg& cfg, int j, uint32_t B, int l) {
+    const int s = cfg.d * (cfg.I[j] - l);
+    return cfg.offs[cfg.layer_base[j] + (uint32_t)(((uint64_t)B + 1) << s)];
+}
+
+// An offset digit e in {-1, 0, 1} is a distinct neighbour on a level with 2^lev cells
+// per dimension unless the grid is too small: 1 cell -> only 0; 2 cells -> not -1.
+__device__ __forceinline__ bool digit_ok(int e, int lev) {
+    if (lev == 0) return e == 0;
+    if (lev == 1) return e != -1;
+    return true;
+}
+
+__global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
+    __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
+    __shared__ unsigned int s_en[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_en[warp] = 0;
+    __syncwarp();
+    WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
+    const View V = sorted_view(cfg);
+    Counters C;
+    const int d = cfg.d;
+    const unsigned int nrows = *cfg.row_count < cfg.row_cap ? *cfg.row_count : cfg.row_cap;
+    unsigned long long t1_items_local = 0, t1_refs_local = 0;
+    for (;;) {
+        unsigned int r = 0;
+        if (lane == 0) r = atomicAdd(&cfg.work_counter[0], 1u);
+        r = __shfl_sync(0xffffffffu, r, 0);
+        if (r >= nrows) break;
+        const uint64_t row = cfg.rows[r];
+        const uint32_t p = (uint32_t)row;
+        const int l = (int)((row >> 32) & 0xff);
+        const int i = (int)(row >> 40);
+        const uint32_t base_i = cfg.layer_base[i];
+        const int sA = d * (cfg.I[i] - l);
+        const uint32_t A = (uint32_t)((uint64_t)(cfg.skey[p] - base_i) >> sA);
+        const uint32_t a_lo = vrange_lo(cfg, i, A, l), a_hi = vrange_hi(cfg, i, A, l);
+        const uint32_t a_len = a_hi - a_lo;
+        uint32_t ca[kMaxDim];
+        morton_decode(A, d, ca);
+        const uint32_t cls = (uint32_t)i * (kMaxLevel + 1) + l;
+        const uint32_t e0 = cfg.class_start[cls], ne = cfg.class_nent[cls];
+        const uint32_t total = cfg.class_total[cls];
+        const uint32_t side = (uint32_t)((1ull << l) - 1);  // coordinate mask at level l
+        for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+            const uint32_t c = c0 + lane;
+            int kind = 0;  // 1: type-I item, 2: type-II item
+            int j = 0;
+            uint32_t B = 0, b_lo = 0, b_len = 0, g = 0;
+            if (c < total) {
+                uint32_t e = e0;
+                while (e + 1 < e0 + ne && cfg.entries[e + 1].prefix <= c) ++e;
+                const ClassEntry ent = cfg.entries[e];
+                j = ent.j;
+                uint32_t off = c - ent.prefix;
+                uint32_t cb[kMaxDim];
+                bool ok = true;
+                if (ent.type == 1) {
+                    for (int k = d - 1; k >= 0; --k) {
+                        const int ek = (int)(off % 3u) - 1;
+                        off /= 3u;
+                        ok = ok && digit_ok(ek, l);
+                        cb[k] = (ca[k] + (uint32_t)ek) & side;
+                    }
+                    if (ok) {
+                        B = morton_encode(cb, d);
+                        if (j == i && B < A) ok = false;
+                    }
+                } else {
+                    const uint32_t kids = off & ((1u << d) - 1u);
+                    off >>= d;
+                    const uint32_t pside = side >> 1;
+                    uint32_t linf = 0;
+                    for (int k = d - 1; k >= 0; --k) {
+                        const int ek = (int)(off % 3u) - 1;
+                        off /= 3u;
+                        ok = ok && digit_ok(ek, l - 1);
+                        const uint32_t pk = ((ca[k] >> 1) + (uint32_t)ek) & pside;
+                        cb[k] = (pk << 1) | ((kids >> (d - 1 - k)) & 1u);
+                        const uint32_t df = (ca[k] - cb[k]) & side;
+                        const uint32_t cd = df < ((side + 1u) - df) ? df : ((side + 1u) - df);
+                        linf = cd > linf ? cd : linf;
+                    }
+                    if (ok && linf <= 1) ok = false;  // a neighbour of A, not distant
+                    if (ok) {
+                        B = morton_encode(cb, d);
+                        if (j == i && B <= A) ok = false;
+                        g = linf - 1;
+                    }
+                }
+                if (ok) {
+                    b_lo = vrange_lo(cfg, j, B, l);
+                    b_len = vrange_hi(cfg, j, B, l) - b_lo;
+                    if (b_len > 0) kind = ent.type;
+                }
+            }
+            // ---- type-I items: split, then append with one atomic per warp
+            uint32_t nsub = 0, ac = 0, bc = 0, na = 0;
+            if (kind == 1) {
+                bc = b_len < kSplitB ? b_len : kSplitB;
+                ac = kSplitAB / bc;
+                if (ac < 1) ac = 1;
+                na = (a_len + ac - 1) / ac;
+                nsub = na * ((b_len + bc - 1) / bc);
+            }
+            unsigned int incl = nsub;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            unsigned int tbase = 0;
+            if (lane == 31 && incl) tbase = atomicAdd(cfg.t1_count, incl);
+            tbase = __shfl_sync(0xffffffffu, tbase, 31) + incl - nsub;
+            if (kind == 1 && (cfg.mode & kModeT1)) {
+                const uint32_t tri = (B == A && j == i) ? 0x80000000u : 0u;
+                uint32_t q = 0;
+                for (uint32_t ya = 0; ya < a_len; ya += ac) {
+                    for (uint32_t yb = 0; yb < b_len; yb += bc, ++q) {
+                        const uint32_t slot = tbase + q;
+                        if (slot < cfg.t1_cap) {
+                            T1Item it;
+                            it.a_begin = a_lo + ya;
+                            it.a_len = (a_len - ya) < ac ? (a_len - ya) : ac;
+                            it.b_begin = b_lo + yb;
+                            it.b_len = ((b_len - yb) < bc ? (b_len - yb) : bc) | tri;
+                            cfg.t1[slot] = it;
+                        }
+                    }
+                }
+                t1_items_local += nsub;
+                // every a-chunk meets every b-chunk: sum of side lengths over sub-items
+                t1_refs_local += (unsigned long long)a_len * ((b_len + bc - 1) / bc) +
+                                 (unsigned long long)b_len * na;
+            }
+            // ---- type-II items
+            if (kind == 2) {
+                ++C.t2items;
+                const uint32_t tidx = ((((uint32_t)i * cfg.L + j) * (cfg.lcap + 1) + l) << 1) + (g - 1);
+                const TwoEntry e = cfg.tii[tidx];
+                const unsigned long long tot = (unsigned long long)a_len * b_len;
+                const uint32_t pack = (uint32_t)l | ((uint32_t)i << 5) | ((uint32_t)j << 11);
+                if (tot <= (1ull << e.k)) {
+                    if (cfg.mode & kModeT2Light) {
+                        const uint32_t s0 = cfg.seed_lo, s1 = cfg.seed_hi;
+                        const uint32_t c2 = pack | (kTagLight << 17);
+                        jump_chunk(cfg, V, we, e, a_lo, b_lo, b_len, 0ull, tot,
+                                   [&](uint32_t t) { return philox(A, B, c2, t, s0, s1); }, C);
+                    }
+                } else if (cfg.mode & kModeT2Heavy) {
+                    const unsigned int slot = atomicAdd(cfg.heavy_count, 1u);
+                    if (slot < cfg.heavy_cap) {
+                        HeavyItem h;
+                        h.a_begin = a_lo;
+                        h.a_len = a_len;
+                        h.b_begin = b_lo;
+                        h.b_len = b_len;
+                        h.A = A;
+                        h.B = B;
+                        h.pack = pack;
+                        h.tii = tidx;
+                        h.chunk_prefix = (tot + (1ull << e.k) - 1) >> e.k;  // chunk count
+                        cfg.heavy[slot] = h;
+                    }
+                }
+            }
+            flush_edges(cfg, we, kEdgeBuf / 2);
+        }
+    }
+    flush_edges(cfg, we, 1);
+    if (cfg.mode & kModeT2Light) flush_counters(cfg, C);
+    for (int o = 16; o > 0; o >>= 1) {
+        t1_items_local += __shfl_down_sync(0xffffffffu, t1_items_local, o);
+        t1_refs_local += __shfl_down_sync(0xffffffffu, t1_refs_local, o);
+    }
+    if (lane == 0 && t1_items_local) {
+        atomicAdd(&cfg.stats[kStatT1Items], t1_items_local);
+        atomicAdd(&cfg.stats[kStatT1VertexRefs], t1_refs_local);
+    }
+}
+
+// ------------------------------------------------------------------ type I
+constexpr int kT1Threads = 256;
+
+__global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
+    __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
+    __shared__ unsigned int s_en[kWarps];
+    __shared__ uint32_t s_pref[kWarps][33];
+    __shared__ T1Item s_it[kWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_en[warp] = 0;
+    __syncwarp();
+    WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
+    const View V = sorted_view(cfg);
+    Counters C;
+    const unsigned int count = *cfg.t1_count < cfg.t1_cap ? *cfg.t1_count : cfg.t1_cap;
+    unsigned long long t1_edges = 0;
+    for (;;) {
+        unsigned int bundle = 0;
+        if (lane == 0) bundle = atomicAdd(&cfg.work_counter[1], 1u);
+        bundle = __shfl_sync(0xffffffffu, bundle, 0);
+        const unsigned long long first = (unsigned long long)bundle * 32ull;
+        if (first >= count) break;
+        const unsigned long long idx = first + lane;
+        T1Item it{0u, 0u, 0u, 0u};
+        if (idx < count) it = cfg.t1[idx];
+        const uint32_t work = it.a_len * (it.b_len & 0x7fffffffu);
+        uint32_t incl = work;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        s_pref[warp][lane] = incl - work;
+        s_it[warp][lane] = it;
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+        for (uint32_t f0 = 0; f0 < tot; f0 += 32) {
+            const uint32_t f = f0 + lane;
+            bool edge = false;
+            uint32_t pu = 0, pv = 0;
+            if (f < tot) {
+                int k = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (s_pref[warp][k + step] <= f) k += step;
+                const T1Item& t = s_it[warp][k];
+                const uint32_t bl = t.b_len & 0x7fffffffu;
+                const uint32_t rr = f - s_pref[warp][k];
+                const uint32_t ia = rr / bl, ib = rr - ia * bl;
+                pu = t.a_begin + ia;
+                pv = t.b_begin + ib;
+                if (!((t.b_len & 0x80000000u) && pv <= pu)) {
+                    ++C.t1pairs;
+                    edge = decide_t1(cfg, V, pu, pv, C);
+                }
+            }
+            if (edge) {
+                push_edge(cfg, we, V.ids[pu], V.ids[pv]);
+                ++t1_edges;
+            }
+            flush_edges(cfg, we, kEdgeBuf - 32);
+        }
+    }
+    flush_edges(cfg, we, 1);
+    flush_counters(cfg, C);
+    for (int o = 16; o > 0; o >>= 1) t1_edges += __shfl_down_sync(0xffffffffu, t1_edges, o);
+    if (lane == 0 && t1_edges) atomicAdd(&cfg.stats[kStatT1Edges], t1_edges);
+}
+
+// ------------------------------------------------------------------ heavy type II
+__global__ void k_heavy_scan(DevCfg cfg, unsigned long long* total_chunks) {
+    __shared__ unsigned long long s_w[32];
+    __shared__ unsigned long long s_carry;
+    const unsigned int cnt = *cfg.heavy_count < cfg.heavy_cap ? *cfg.heavy_count : cfg.heavy_cap;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (unsigned int b0 = 0; b0 < cnt; b0 += blockDim.x) {
+        const unsigned int i = b0 + threadIdx.x;
+        const unsigned long long v = i < cnt ? cfg.heavy[i].chunk_prefix : 0ull;
+        unsigned long long incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = blockDim.x >> 5;
+            unsigned long long x = lane < nw ? s_w[lane] : 0ull, xi = x;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long t = __shfl_up_sync(0xffffffffu, xi, o);
+                if (lane >= o) xi += t;
+            }
+            if (lane < nw) s_w[lane] = xi - x;
+        }
+        __syncthreads();
+        const unsigned long long excl = s_carry + s_w[warp] + incl - v;
+        if (i < cnt) cfg.heavy[i].chunk_prefix = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total_chunks = s_carry;
+}
+
+__global__ void __launch_bounds__(kEnumThreads) k_heavy(DevCfg cfg, const unsigned long long* total_chunks) {
+    __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
+    __shared__ unsigned int s_en[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_en[warp] = 0;
+    __syncwarp();
+    WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
+    const View V = sorted_view(cfg);
+    Counters C;
+    const unsigned long long T = *total_chunks;
+    const unsigned int cnt = *cfg.heavy_count < cfg.heavy_cap ? *cfg.heavy_count : cfg.heavy_cap;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long g0 = (unsigned long long)blockIdx.x * blockDim.x; g0 < T; g0 += stride) {
+        const unsigned long long g = g0 + threadIdx.x;
+        if (g < T) {
+            unsigned int lo = 0, hi = cnt;  // last item with prefix <= g
+            while (hi - lo > 1) {
+                const unsigned int mid = (lo + hi) >> 1;
+                if (cfg.heavy[mid].chunk_prefix <= g) lo = mid; else hi = mid;
+            }
+            const HeavyItem h = cfg.heavy[lo];
+            const unsigned long long hc = g - h.chunk_prefix;
+            const TwoEntry e = cfg.tii[h.tii];
+            const P4 ko = philox(h.A, h.B, h.pack | (kTagItem << 17), 0u, cfg.seed_lo, cfg.seed_hi);
+            const unsigned long long tot = (unsigned long long)h.a_len * h.b_len;
+            const unsigned long long start = hc << e.k;
+            const unsigned long long len = (tot - start) < (1ull << e.k) ? (tot - start) : (1ull << e.k);
+            const uint32_t hlo = (uint32_t)hc, hhi = (uint32_t)(hc >> 32);
+            jump_chunk(cfg, V, we, e, h.a_begin, h.b_begin, h.b_len, start, len,
+                       [&](uint32_t t) { return philox(hlo, hhi, t, kTagDraw, ko.x, ko.y); }, C);
+        }
+        flush_edges(cfg, we, kEdgeBuf / 2);
+    }
+    flush_edges(cfg, we, 1);
+    flush_counters(cfg, C);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cfg.stats[kStatHeavyChunks], T);
+}
+
+// ------------------------------------------------------------------ all pairs
+// Every pair u < v of the original order (Table 1, "Pairwise"): tiles of
+// 64 x 64 vertices, upper triangle only.
+__global__ void __launch_bounds__(256) k_allpairs(DevCfg cfg, View V, unsigned int ntile) {
+    __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
+    __shared__ unsigned int s_en[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_en[warp] = 0;
+    __syncwarp();
+    WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
+    Counters C;
+    const unsigned long long ntri = (unsigned long long)ntile * (ntile + 1) / 2;
+    for (unsigned long long t = blockIdx.x; t < ntri; t += gridDim.x) {
+        // tile (tu, tv), tu <= tv, from the triangular index t
+        unsigned int tv = (unsigned int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while ((unsigned long long)(tv + 1) * (tv + 2) / 2 <= t) ++tv;
+        while ((unsigned long long)tv * (tv + 1) / 2 > t) --tv;
+        const unsigned int tu = (unsigned int)(t - (unsigned long long)tv * (tv + 1) / 2);
+        for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) {
+            const uint32_t u = tu * 64 + (q >> 6), v = tv * 64 + (q & 63);
+            bool edge = false;
+            if (u < v && v < (uint32_t)V.n) edge = decide_t1(cfg, V, u, v, C);
+            if (edge) push_edge(cfg, we, u, v);
+            flush_edges(cfg, we, kEdgeBuf - 32);
+        }
+    }
+    flush_edges(cfg, we, 1);
+}
+
+// ------------------------------------------------------------------ launchers
+void launch_rows(const DevCfg& cfg, uint64_t* rows, unsigned int* row_count, unsigned int cap,
+                 cudaStream_t st) {
+    int64_t b = (cfg.n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    ++g_launches;
+    k_rows<<<(unsigned)b, 256, 0, st>>>(cfg, rows, row_count, cap);
+}
+
+void launch_enumerate(const DevCfg& cfg, cudaStream_t st) {
+    ++g_launches;
+    k_enumerate<<<152 * 6, kEnumThreads, 0, st>>>(cfg);
+}
+
+void launch_type1(const DevCfg& cfg, cudaStream_t st) {
+    ++g_launches;
+    k_type1<<<152 * 6, kT1Threads, 0, st>>>(cfg);
+}
+
+void launch_heavy_scan(const DevCfg& cfg, unsigned long long* total_chunks, cudaStream_t st) {
+    ++g_launches;
+    k_heavy_scan<<<1, 1024, 0, st>>>(cfg, total_chunks);
+}
+
+void launch_heavy(const DevCfg& cfg, const unsigned long long* total_chunks, cudaStream_t st) {
+    ++g_launches;
+    k_heavy<<<152 * 4, kEnumThreads, 0, st>>>(cfg, total_chunks);
+}
+
+void launch_allpairs(const DevCfg& cfg, const uint32_t* X, const double* w, const float* sv,
+                     cudaStream_t st) {
+    View V{X, sv, w, nullptr, nullptr, nullptr, nullptr, cfg.n};
+    const unsigned int ntile = (unsigned int)((cfg.n + 63) / 64);
+    unsigned long long ntri = (unsigned long long)ntile * (ntile + 1) / 2;
+    unsigned int grid = ntri < 152ull * 8 ? (unsigned int)ntri : 152 * 8;
+    ++g_launches;
+    k_allpairs<<<grid, 256, 0, st>>>(cfg, V, ntile);
+}
+
+}  // namespace gg

@@ -1,0 +1,31 @@
+// Expected average degree f(c) and the search for c (Sec. 4.1, App. B.2).
+#pragma once
+#include <stdint.h>
+
+#include <functional>
+#include <vector>
+
+namespace gg {
+
+class DegreeModel {
+   public:
+    // s2 = sum w^2, st = sum w^(1/T), s2t = sum w^(2/T) (T > 0).
+    DegreeModel(int64_t n, int d, double T, double W, double s2, double st, double s2t);
+    // The heaviest weights: every weight strictly above `fetched_above`.
+    void set_top(std::vector<double> top, double fetched_above);
+    void set_wmax(double wmax) { wmax_ = wmax; }
+    double f(double c) const;
+    // Weight threshold below which no vertex has a partner in E_R at this c.
+    double needed_threshold(double c) const;
+    // c with f(c) = target; `fetch(t)` must call set_top with all weights above t.
+    double solve(double target, const std::function<void(double)>& fetch);
+
+   private:
+    double qstar(double c) const;
+    int64_t n_;
+    int d_;
+    double T_, W_, S1_, S2_, wmax_, have_thr_;
+    std::vector<double> top_, pre_w_, pre_wt_;
+};
+
+}  // namespace gg

@@ -1,0 +1,319 @@
+// The geometric data structure of Sec. 3.4 / Lemma 1: every vertex gets the key
+// (bucket, Morton code of its cell at the bucket's insertion level) as one dense
+// global cell index; a histogram over the cells plus an exclusive scan gives
+// the prefix sums P_C of all buckets at once, and a stable LSD radix sort of
+// (key, id) gives the vertex order (ties by original id, Sec. 4.4 sorts by
+// bucket first and Morton code second with a radix sort).  The gather kernels
+// lay out the sorted per-vertex arrays (structure of arrays, coalesced).
+#include "internal.cuh"
+#include "kernels.h"
+
+namespace gg {
+
+struct KeyTab {
+    int8_t I[kMaxLayers];
+    uint32_t base[kMaxLayers + 1];
+};
+
+__global__ void k_keys(int64_t n, int d, const double* __restrict__ w, const uint32_t* __restrict__ X,
+                       double w_min, KeyTab tab, uint32_t* __restrict__ key,
+                       uint32_t* __restrict__ val, uint32_t* __restrict__ cnt) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int layer = layer_of(w[v], w_min);
+        const int lev = tab.I[layer];
+        uint32_t coord[kMaxDim];
+        for (int k = 0; k < d; ++k) coord[k] = lev ? (X[(int64_t)k * n + v] >> (32 - lev)) : 0u;
+        const uint32_t code = lev ? morton_encode(coord, d) : 0u;
+        const uint32_t kk = tab.base[layer] + code;
+        key[v] = kk;
+        val[v] = (uint32_t)v;
+        atomicAdd(&cnt[kk], 1u);
+    }
+}
+
+// ------------------------------------------------------------------ scan
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* s_warp,
+                                                         uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        uint32_t v = lane < nw ? s_warp[lane] : 0u;
+        uint32_t vi = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, vi, o);
+            if (lane >= o) vi += t;
+        }
+        if (lane < nw) s_warp[lane] = vi - v;
+        if (lane == 31) s_warp[32] = vi;
+    }
+    __syncthreads();
+    const uint32_t r = s_warp[warp] + incl - x;
+    *total = s_warp[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_reduce(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ sums) {
+    __shared__ uint32_t s_warp[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    uint32_t acc = 0;
+    for (int it = 0; it < kScanItems; ++it) {
+        const int64_t i = base + (int64_t)it * kScanThreads + threadIdx.x;
+        if (i < n) acc += in[i];
+    }
+    uint32_t total;
+    block_exclusive_scan(acc, s_warp, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_down(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n,
+                            const uint32_t* __restrict__ prefix) {
+    __shared__ uint32_t s_warp[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t acc = 0;
+#pragma unroll
+    for (int it = 0; it < kScanItems; ++it) {
+        const int64_t i = base + it;
+        v[it] = i < n ? in[i] : 0u;
+        acc += v[it];
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(acc, s_warp, &total) + (prefix ? prefix[blockIdx.x] : 0u);
+#pragma unroll
+    for (int it = 0; it < kScanItems; ++it) {
+        const int64_t i = base + it;
+        if (i < n) out[i] = run;
+        run += v[it];
+    }
+}
+
+size_t scan_tmp_words(int64_t n) {
+    size_t words = 0;
+    int64_t m = n;
+    while (m > kScanTile) {
+        m = (m + kScanTile - 1) / kScanTile;
+        words += (size_t)m + 32;
+    }
+    return words + 64;
+}
+
+void launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t st) {
+    if (n <= 0) return;
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb == 1) {
+        ++g_launches;
+        k_scan_down<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
+        return;
+    }
+    uint32_t* sums = tmp;
+    ++g_launches;
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums);
+    launch_scan_u32(sums, sums, nb, tmp + nb + 32, st);
+    ++g_launches;
+    k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums);
+}
+
+// ------------------------------------------------------------------ radix sort
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 8;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;  // 2048 = 8 warps x 8 rounds x 32
+
+__global__ void k_radix_hist(const uint32_t* __restrict__ key, int64_t n, int shift,
+                             uint32_t* __restrict__ hist, uint32_t ntiles) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+#pragma unroll
+    for (int it = 0; it < kRadixItems; ++it) {
+        const int64_t i = base + (int64_t)it * kRadixThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(key[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRadixThreads)
+k_radix_scatter(const uint32_t* __restrict__ key, const uint32_t* __restrict__ val, int64_t n,
+                int shift, const uint32_t* __restrict__ hist, uint32_t ntiles,
+                uint32_t* __restrict__ key_out, uint32_t* __restrict__ val_out) {
+    __shared__ uint32_t wcnt[8][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < 8 * 256; t += kRadixThreads) (&wcnt[0][0])[t] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile + warp * 256;
+    uint32_t k[kRadixItems], v[kRadixItems], rank[kRadixItems];
+    int dig[kRadixItems];
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        const bool valid = i < n;
+        k[r] = valid ? key[i] : 0u;
+        v[r] = valid ? val[i] : 0u;
+        const int dg = (int)((k[r] >> shift) & 255u);
+        dig[r] = valid ? dg : -1;
+        uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const bool bit = (dg >> b) & 1;
+            const uint32_t bm = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bm : ~bm;
+        }
+        uint32_t before = 0;
+        if (valid) before = wcnt[warp][dg];
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wcnt[warp][dg] = before + __popc(peers);
+        __syncwarp();
+        rank[r] = before + __popc(peers & lanemask_lt());
+    }
+    __syncthreads();
+    {
+        uint32_t run = 0;
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t c = wcnt[w][threadIdx.x];
+            wcnt[w][threadIdx.x] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        if (dig[r] >= 0) {
+            const uint32_t pos =
+                hist[(size_t)dig[r] * ntiles + blockIdx.x] + wcnt[warp][dig[r]] + rank[r];
+            key_out[pos] = k[r];
+            val_out[pos] = v[r];
+        }
+    }
+}
+
+size_t radix_tmp_words(int64_t n) {
+    const int64_t ntiles = (n + kRadixTile - 1) / kRadixTile;
+    return (size_t)(256 * ntiles) + scan_tmp_words(256 * ntiles) + 64;
+}
+
+void radix_sort_pairs(uint32_t* key, uint32_t* val, uint32_t* key_alt, uint32_t* val_alt,
+                      int64_t n, int bits, uint32_t* tmp, cudaStream_t st, uint32_t** key_out,
+                      uint32_t** val_out) {
+    const uint32_t ntiles = (uint32_t)((n + kRadixTile - 1) / kRadixTile);
+    uint32_t* hist = tmp;
+    uint32_t* stmp = tmp + (size_t)256 * ntiles + 32;
+    uint32_t *ki = key, *vi = val, *ko = key_alt, *vo = val_alt;
+    for (int shift = 0; shift < bits; shift += 8) {
+        ++g_launches;
+        k_radix_hist<<<ntiles, kRadixThreads, 0, st>>>(ki, n, shift, hist, ntiles);
+        launch_scan_u32(hist, hist, (int64_t)256 * ntiles, stmp, st);
+        ++g_launches;
+        k_radix_scatter<<<ntiles, kRadixThreads, 0, st>>>(ki, vi, n, shift, hist, ntiles, ko, vo);
+        uint32_t* t = ki;
+        ki = ko;
+        ko = t;
+        t = vi;
+        vi = vo;
+        vo = t;
+    }
+    *key_out = ki;
+    *val_out = vi;
+}
+
+// ------------------------------------------------------------------ gathers
+// Per-vertex scale s with kappa_uv = s_u s_v (kappa: distance at which p = 1, or the
+// threshold distance at T = 0): log2 s = (log2 w - log2(W)/2) / d + gamma.  Only the
+// single-precision fast path uses it; its error is covered by the decision band.
+__global__ void k_gather_girg(int64_t n, int d, const uint32_t* __restrict__ perm,
+                              const uint32_t* __restrict__ X, const double* __restrict__ w,
+                              double w_min, double log2W_half, float gamma, float invd,
+                              uint32_t* __restrict__ Xs, double* __restrict__ ws,
+                              float* __restrict__ sv, uint8_t* __restrict__ slayer) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = perm[p];
+        for (int k = 0; k < d; ++k) Xs[(int64_t)k * n + p] = X[(int64_t)k * n + v];
+        const double wv = w[v];
+        ws[p] = wv;
+        sv[p] = exp2f((log2f((float)wv) - (float)log2W_half) * invd + gamma);
+        slayer[p] = (uint8_t)layer_of(wv, w_min);
+    }
+}
+
+__global__ void k_scale(int64_t n, const double* __restrict__ w, double log2W_half, float gamma,
+                        float invd, float* __restrict__ sv) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        sv[p] = exp2f((log2f((float)w[p]) - (float)log2W_half) * invd + gamma);
+}
+
+__global__ void k_gather_hrg(int64_t n, const uint32_t* __restrict__ perm,
+                             const uint32_t* __restrict__ X, const double* __restrict__ r,
+                             const double* __restrict__ w, uint32_t* __restrict__ Xs,
+                             double* __restrict__ rs, float* __restrict__ E32,
+                             float* __restrict__ einv32, float* __restrict__ sh32,
+                             uint8_t* __restrict__ slayer) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = perm[p];
+        Xs[p] = X[v];
+        const double rv = r[v];
+        rs[p] = rv;
+        const float rf = (float)rv;
+        E32[p] = expf(rf);
+        einv32[p] = expf(-rf);
+        sh32[p] = sinhf(rf);
+        slayer[p] = (uint8_t)layer_of(w[v], 1.0);
+    }
+}
+
+static int grid_for(int64_t n, int threads, int max_blocks) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b > max_blocks) b = max_blocks;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+void launch_keys(int64_t n, int d, const double* w, const uint32_t* X, double w_min,
+                 const int8_t* I, const uint32_t* layer_base, uint32_t* key, uint32_t* val,
+                 uint32_t* cnt, cudaStream_t st) {
+    KeyTab tab;
+    memcpy(tab.I, I, sizeof(tab.I));
+    memcpy(tab.base, layer_base, sizeof(tab.base));
+    ++g_launches;
+    k_keys<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, d, w, X, w_min, tab, key, val, cnt);
+}
+
+void launch_gather_girg(int64_t n, int d, const uint32_t* perm, const uint32_t* X,
+                        const double* w, double w_min, double log2W_half, float gamma,
+                        float invd, uint32_t* Xs, double* ws, float* sv, uint8_t* slayer,
+                        cudaStream_t st) {
+    ++g_launches;
+    k_gather_girg<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, d, perm, X, w, w_min, log2W_half,
+                                                              gamma, invd, Xs, ws, sv, slayer);
+}
+
+void launch_scale(int64_t n, const double* w, double log2W_half, float gamma, float invd,
+                  float* sv, cudaStream_t st) {
+    ++g_launches;
+    k_scale<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, w, log2W_half, gamma, invd, sv);
+}
+
+void launch_gather_hrg(int64_t n, const uint32_t* perm, const uint32_t* X, const double* r,
+                       const double* w, uint32_t* Xs, double* rs, float* E32, float* einv32,
+                       float* sh32, uint8_t* slayer, cudaStream_t st) {
+    ++g_launches;
+    k_gather_hrg<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, perm, X, r, w, Xs, rs, E32,
+                                                             einv32, sh32, slayer);
+}
+
+}  // namespace gg

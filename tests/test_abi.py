@@ -1,0 +1,119 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point that
+include/girg_gb300.h declares; parameter validation happens on the host before
+any CUDA call (so these run without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1905_06706_gb300 as gg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "girg_gb300.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b((?:girg|hrg)_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return gg.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(gg.SIGNATURES), set(names) ^ set(gg.SIGNATURES)
+
+
+def test_status_strings(lib):
+    assert gg.status_string(0) == "ok"
+    assert "too small" in gg.status_string(gg.GIRG_E_CAPACITY)
+    assert gg.status_string(99) == "unknown status"
+
+
+def _params(**kw):
+    base = dict(n=1000, d=2, beta=2.5, T=0.5, avg_deg=10.0, c=0.0, w_min=1.0, seed=1,
+                edge_bytes=4, precision=0, level_cap=0)
+    base.update(kw)
+    return gg.GirgParams(**base)
+
+
+@pytest.mark.parametrize("bad", [dict(n=1), dict(n=2 ** 31), dict(d=0), dict(d=9),
+                                 dict(beta=2.0), dict(T=1.0), dict(T=-0.1), dict(w_min=0.0),
+                                 dict(edge_bytes=2), dict(precision=2), dict(avg_deg=0.0),
+                                 dict(avg_deg=999.0), dict(level_cap=-1)])
+def test_invalid_parameters_rejected_on_host(lib, bad):
+    p = _params(**bad)
+    m = ctypes.c_int64(-1)
+    st = lib.girg_generate(ctypes.byref(p), None, 0, ctypes.byref(m), None, None)
+    assert st == gg.GIRG_E_PARAM
+    assert m.value == -1  # nothing was written
+
+
+def test_invalid_hrg_and_points_rejected(lib):
+    hp = gg.HrgParams(1000, 0.5, 0.5, 10.0, 1, 4, 0, 0)  # alpha must exceed 1/2
+    m = ctypes.c_int64(0)
+    assert lib.hrg_generate(ctypes.byref(hp), None, 0, ctypes.byref(m), None) == gg.GIRG_E_PARAM
+    hp = gg.HrgParams(1000, 0.75, 0.5, 0.0, 1, 4, 0, 0)  # R must be given
+    assert lib.hrg_generate(ctypes.byref(hp), None, 0, ctypes.byref(m), None) == gg.GIRG_E_PARAM
+    assert lib.girg_points(0, 2, 2.5, 1.0, 1, None, None, None) == gg.GIRG_E_PARAM
+    assert lib.girg_allpairs(10, 1, None, None, 0.0, 0.5, 1.0, 1, 0, 4, None, 0,
+                             ctypes.byref(m), None) == gg.GIRG_E_PARAM
+    assert lib.girg_generate_from_points(10, 1, None, None, 0.5, -1.0, 1, 0, 0, 4, None, 0,
+                                         ctypes.byref(m), None) == gg.GIRG_E_PARAM
+
+
+def test_struct_layout_matches_header(tmp_path):
+    """ctypes field offsets equal the C compiler's for both parameter structs."""
+    import subprocess
+    fields = {"girg_params": [f for f, _ in gg.GirgParams._fields_],
+              "hrg_params": [f for f, _ in gg.HrgParams._fields_]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "girg_gb300.h"',
+             "int main(void) {"]
+    for st, names in fields.items():
+        lines.append(f'printf("%zu\\n", sizeof({st}));')
+        for f in names:
+            lines.append(f'printf("%zu\\n", offsetof({st}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    expect = []
+    for cls in (gg.GirgParams, gg.HrgParams):
+        expect.append(ctypes.sizeof(cls))
+        expect.extend(getattr(cls, f).offset for f, _ in cls._fields_)
+    assert out == expect
+
+
+def test_host_deterministic_math_matches_oracle_bitwise(lib):
+    """The library's FP64 elementary functions (used for the type-II tables) and the
+    oracle's independent implementation give identical bits."""
+    import numpy as np
+
+    import oracle as O
+    rng = np.random.default_rng(21)
+    xs = np.concatenate([np.exp(rng.uniform(-700, 700, 2000)), rng.uniform(0, 3, 2000)])
+    for x in xs:
+        assert lib.girg_det_eval(0, x, 0.0) == O.det_log(x)
+        assert lib.girg_det_eval(5, 1.0 + x, 0.0) == O.det_acosh(1.0 + x)
+    for x in rng.uniform(-0.999, 3, 3000):
+        assert lib.girg_det_eval(1, x, 0.0) == O.det_log1p(x)
+    for x in rng.uniform(-745, 709, 3000):
+        assert lib.girg_det_eval(2, x, 0.0) == O.det_exp(x)
+    for x, y in zip(np.exp(rng.uniform(-50, 50, 3000)), rng.uniform(-8, 8, 3000)):
+        assert lib.girg_det_eval(3, x, y) == O.det_pow(x, y)
+    for x in rng.uniform(0, 0.5, 3000):
+        assert lib.girg_det_eval(4, x, 0.0) == O.det_sinpi(x)
+    for wu, wv in rng.uniform(1, 50, (2000, 2)):
+        assert lib.girg_det_eval(6, wu, wv) == O.girg_p(2, 0.75, 0.5, 1000.0, wu, wv, 2 ** 30)

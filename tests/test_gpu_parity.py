@@ -1,0 +1,279 @@
+"""Parity of the CUDA path with the FP64 oracle (runs on a GB300).
+
+Every comparison is exact: weights, positions and radii bit for bit, the sorted
+vertex order element for element, and edge sets edge for edge -- the library's
+FP32 decisions recheck in FP64 inside a rigorous error band with the same
+deterministic arithmetic as the oracle, so no tolerance is needed.  Inputs are
+the seeded points of the model (or synthetic points for the user-weights path),
+at sizes the oracle finishes in seconds that span many tiles, warps and a ragged
+tail, and at the benchmark's full size.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1905_06706_gb300 as gg  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    gg.load()
+
+
+def _edges(cap, eb=4):
+    return torch.empty((max(cap, 1), 2), dtype=torch.int32 if eb == 4 else torch.int64,
+                       device="cuda")
+
+
+def _set(edges, m):
+    e = edges[:m].to("cpu").numpy().astype(np.int64)
+    if e.dtype != np.int64:
+        e = e.astype(np.int64)
+    e &= 0xFFFFFFFF
+    assert np.all(e[:, 0] < e[:, 1]), "edges must be (u < v)"
+    key = e[:, 0] * (1 << 32) + e[:, 1]
+    s = set(key.tolist())
+    assert len(s) == m, "duplicate edges"
+    return s
+
+
+def _gpu_points(X_nd, w):
+    X = torch.from_numpy(np.ascontiguousarray(X_nd.T).view(np.int32)).cuda()
+    return X, torch.from_numpy(w).cuda()
+
+
+def _generate_from(X_nd, w, T, c, seed, precision, level_cap=0, cap=None):
+    X, wt = _gpu_points(X_nd, w)
+    n = len(w)
+    cap = cap or int(n * 64) + 1024
+    ed = _edges(cap)
+    r = gg.girg_generate_from_points(ed, X, wt, T=T, c=c, seed=seed, precision=precision,
+                                     level_cap=level_cap)
+    assert r.status == gg.GIRG_OK, gg.status_string(r.status)
+    return _set(ed, r.num_edges)
+
+
+# --------------------------------------------------------------------- inputs
+
+@pytest.mark.parametrize("n,d", [(100_003, 1), (65_537, 2), (40_000, 3), (30_001, 4), (1000, 8)])
+def test_points_bit_exact(n, d):
+    w_ref, X_ref = O.girg_points(n, d, 2.3, 1.5, 77)
+    w, X = gg.girg_points(n, d, 2.3, 1.5, 77)
+    assert np.array_equal(w.cpu().numpy().view(np.uint64), w_ref.view(np.uint64))
+    assert np.array_equal(X.cpu().numpy().view(np.uint32), np.ascontiguousarray(X_ref.T))
+
+
+def test_hrg_points_bit_exact():
+    n, alpha, R = 100_001, 0.75, 2 * math.log(100_001) + 1.3
+    r_ref, X_ref = O.hrg_points(n, alpha, R, 5)
+    r, X = gg.hrg_points(n, alpha, R, 5)
+    assert np.array_equal(r.cpu().numpy().view(np.uint64), r_ref.view(np.uint64))
+    assert np.array_equal(X.cpu().numpy().view(np.uint32), X_ref)
+
+
+# --------------------------------------------------------------------- all pairs
+
+@pytest.mark.parametrize("precision", [gg.PRECISION_FP32, gg.PRECISION_FP64])
+def test_allpairs_config1_edge_for_edge(precision):
+    """d = 1, n = 10^4, beta = 2.5, T = 0.5, c for average degree 10, seed 1."""
+    n, d, T = 10_000, 1, 0.5
+    w, X = O.girg_points(n, d, 2.5, 1.0, 1)
+    W = O.exact_sum(w)
+    c = O.girg_solve_c(10.0, w, d, T, W)
+    ref = O.edge_set(O.girg_allpairs(X, w, W, T, c, 1))
+    Xg, wg = _gpu_points(X, w)
+    ed = _edges(200_000)
+    r = gg.girg_allpairs(ed, Xg, wg, W=W, T=T, c=c, seed=1, precision=precision)
+    assert r.status == gg.GIRG_OK
+    assert _set(ed, r.num_edges) == ref
+
+
+@pytest.mark.parametrize("d,T", [(2, 0.0), (3, 0.7)])
+def test_allpairs_other_cases(d, T):
+    n = 3000
+    w, X = O.girg_points(n, d, 2.2, 1.0, 3)
+    W = O.exact_sum(w)
+    c = O.girg_solve_c(12.0, w, d, T, W)
+    ref = O.edge_set(O.girg_allpairs(X, w, W, T, c, 9))
+    Xg, wg = _gpu_points(X, w)
+    ed = _edges(100_000)
+    r = gg.girg_allpairs(ed, Xg, wg, W=W, T=T, c=c, seed=9)
+    assert r.status == gg.GIRG_OK and _set(ed, r.num_edges) == ref
+
+
+# --------------------------------------------------------------------- sort
+
+@pytest.mark.parametrize("n,d,T", [(50_000, 1, 0.5), (70_001, 2, 0.5), (20_000, 3, 0.0),
+                                   (10_000, 4, 0.7)])
+def test_sorted_order_matches_oracle(n, d, T):
+    w, X = O.girg_points(n, d, 2.5, 1.0, 11)
+    W = O.exact_sum(w)
+    c = O.girg_solve_c(10.0, w, d, T, W)
+    res = O.girg_cellpairs(X, w, float(w.min()), W, T, c, 1, skip_sampling=True)
+    Xg, wg = _gpu_points(X, w)
+    order = gg.girg_sorted_order(Xg, wg, T=T, c=c)
+    assert np.array_equal(order.cpu().numpy(), res.order)
+
+
+# --------------------------------------------------------------------- cell-pair sampler
+
+CASES = [(1, 0.5, 20_000), (1, 0.0, 30_000), (2, 0.5, 40_000), (2, 0.0, 40_000),
+         (2, 0.7, 25_000), (3, 0.7, 15_000), (3, 0.0, 15_000), (4, 0.5, 8_000), (1, 0.3, 50_000)]
+
+
+@pytest.mark.parametrize("d,T,n", CASES)
+@pytest.mark.parametrize("precision", [gg.PRECISION_FP32, gg.PRECISION_FP64])
+def test_cellpair_sampler_edge_for_edge(d, T, n, precision):
+    w, X = O.girg_points(n, d, 2.4, 1.0, 100 + d)
+    W = O.exact_sum(w)
+    c = O.girg_solve_c(9.0, w, d, T, W)
+    ref = O.girg_cellpairs(X, w, float(w.min()), W, T, c, 5, cap=n * 64)
+    got = _generate_from(X, w, T, c, 5, precision)
+    assert got == O.edge_set(ref.edges)
+
+
+@pytest.mark.parametrize("d,T", [(1, 0.0), (2, 0.0), (3, 0.0)])
+def test_threshold_sampler_equals_allpairs(d, T):
+    n = 8000
+    w, X = O.girg_points(n, d, 2.6, 1.0, 7)
+    W = O.exact_sum(w)
+    c = O.girg_solve_c(15.0, w, d, T, W)
+    ref = O.edge_set(O.girg_allpairs(X, w, W, T, c, 1))
+    assert _generate_from(X, w, T, c, 1, gg.PRECISION_FP32) == ref
+
+
+@pytest.mark.parametrize("lcap", [1, 2, 3, 6, 30])
+def test_level_cap_keeps_parity(lcap):
+    n, d, T = 12_000, 1, 0.6
+    w, X = O.girg_points(n, d, 2.5, 1.0, 8)
+    W = O.exact_sum(w)
+    c = O.girg_solve_c(8.0, w, d, T, W)
+    ref = O.girg_cellpairs(X, w, float(w.min()), W, T, c, 3, cap=n * 64, level_cap=lcap)
+    assert _generate_from(X, w, T, c, 3, gg.PRECISION_FP32, level_cap=lcap) == O.edge_set(ref.edges)
+
+
+def test_user_weights_synthetic_points():
+    """User-defined weights (App. B.2 / Sec. 4.1): log-normal weights, clustered positions."""
+    rng = np.random.default_rng(4)
+    n, d, T = 30_000, 2, 0.5
+    w = np.exp(rng.normal(1.0, 1.2, n))
+    X = (rng.normal(0.3, 0.1, (n, d)) % 1.0 * 2 ** 32).astype(np.uint64).astype(np.uint32)
+    W = O.exact_sum(w)
+    c = O.girg_solve_c(12.0, w, d, T, W)
+    ref = O.girg_cellpairs(X, w, float(w.min()), W, T, c, 2, cap=n * 64)
+    assert _generate_from(X, w, T, c, 2, gg.PRECISION_FP32) == O.edge_set(ref.edges)
+
+
+def test_generate_internal_points_and_c():
+    n, d, T, beta = 50_000, 2, 0.5, 2.5
+    w, X = O.girg_points(n, d, beta, 1.0, 21)
+    W = O.exact_sum(w)
+    c_ref = O.girg_solve_c(10.0, w, d, T, W)
+    ed = _edges(n * 32)
+    r = gg.girg_generate(ed, n=n, d=d, beta=beta, T=T, avg_deg=10.0, seed=21)
+    assert r.status == gg.GIRG_OK
+    assert r.c_used == pytest.approx(c_ref, rel=1e-9)
+    # the same graph with c given explicitly equals the oracle's
+    r2 = gg.girg_generate(ed, n=n, d=d, beta=beta, T=T, c=c_ref, seed=21)
+    ref = O.girg_cellpairs(X, w, 1.0, W, T, c_ref, 21, cap=n * 64)
+    assert _set(ed, r2.num_edges) == O.edge_set(ref.edges)
+    # expected degree through the C ABI
+    f = gg.girg_expected_avg_degree(n=n, d=d, beta=beta, T=T, c=c_ref, seed=21)
+    assert f == pytest.approx(10.0, rel=1e-9)
+
+
+def test_int64_edges_and_capacity():
+    n, d, T = 20_000, 2, 0.5
+    w, X = O.girg_points(n, d, 2.5, 1.0, 31)
+    W = O.exact_sum(w)
+    c = O.girg_solve_c(10.0, w, d, T, W)
+    ref = O.edge_set(O.girg_cellpairs(X, w, 1.0, W, T, c, 31, cap=n * 64).edges)
+    ed = _edges(n * 32, eb=8)
+    r = gg.girg_generate(ed, n=n, d=d, beta=2.5, T=T, c=c, seed=31)
+    assert r.status == gg.GIRG_OK and _set(ed, r.num_edges) == ref
+    small = _edges(100)
+    r = gg.girg_generate(small, n=n, d=d, beta=2.5, T=T, c=c, seed=31)
+    assert r.status == gg.GIRG_E_CAPACITY and r.num_edges == len(ref)
+
+
+def test_degenerate_inputs():
+    # two vertices, identical positions: p = 1
+    X = np.zeros((2, 1), dtype=np.uint32)
+    w = np.array([1.0, 1.0])
+    assert _generate_from(X, w, 0.5, 1e-6, 1, gg.PRECISION_FP32) == {1}
+    # all weights equal, one bucket; tiny c; large c (complete graph)
+    n = 3000
+    rng = np.random.default_rng(1)
+    X = rng.integers(0, 2 ** 32, (n, 2), dtype=np.uint64).astype(np.uint32)
+    w = np.full(n, 2.0)
+    W = O.exact_sum(w)
+    for c, T in ((1e-4, 0.5), (50.0, 0.0), (1.0, 0.9)):
+        ref = O.girg_cellpairs(X, w, 2.0, W, T, c, 4, cap=n * n)
+        assert _generate_from(X, w, T, c, 4, gg.PRECISION_FP32, cap=n * n) == O.edge_set(ref.edges)
+
+
+def test_determinism_and_precision_modes_agree():
+    n, d, T = 60_000, 2, 0.7
+    w, X = O.girg_points(n, d, 2.3, 1.0, 44)
+    W = O.exact_sum(w)
+    c = O.girg_solve_c(10.0, w, d, T, W)
+    a = _generate_from(X, w, T, c, 3, gg.PRECISION_FP32)
+    b = _generate_from(X, w, T, c, 3, gg.PRECISION_FP32)
+    e = _generate_from(X, w, T, c, 3, gg.PRECISION_FP64)
+    assert a == b == e
+
+
+# --------------------------------------------------------------------- HRG
+
+@pytest.mark.parametrize("T", [0.0, 0.5, 0.2])
+@pytest.mark.parametrize("precision", [gg.PRECISION_FP32, gg.PRECISION_FP64])
+def test_hrg_edge_for_edge(T, precision):
+    n, alpha = 40_000, 0.75
+    R = 2 * math.log(n) + 1.0
+    r, X = O.hrg_points(n, alpha, R, 13)
+    ref = O.hrg_cellpairs(X, r, R, T, 13, cap=n * 64)
+    ed = _edges(n * 64)
+    res = gg.hrg_generate(ed, n=n, alpha=alpha, T=T, R=R, seed=13, precision=precision)
+    assert res.status == gg.GIRG_OK
+    assert _set(ed, res.num_edges) == O.edge_set(ref.edges)
+
+
+def test_hrg_threshold_equals_allpairs():
+    n, alpha = 6000, 0.8
+    R = 2 * math.log(n) + 0.5
+    r, X = O.hrg_points(n, alpha, R, 2)
+    ref = O.edge_set(O.hrg_allpairs(X, r, R, 0.0, 2))
+    ed = _edges(n * 64)
+    res = gg.hrg_generate(ed, n=n, alpha=alpha, T=0.0, R=R, seed=2)
+    assert res.status == gg.GIRG_OK and _set(ed, res.num_edges) == ref
+
+
+# --------------------------------------------------------------------- full size
+
+def test_benchmark_workload_full_size_edge_for_edge():
+    """The benchmark's configuration (d = 2, n = 10^6, beta = 2.5, T = 0.5, average
+    degree 10, seed 1) in the launch configuration bench.py times, edge for edge."""
+    n, d, T, beta = 1_000_000, 2, 0.5, 2.5
+    w, X = O.girg_points(n, d, beta, 1.0, 1)
+    W = O.exact_sum(w)
+    c = O.girg_solve_c(10.0, w, d, T, W)
+    ref = O.girg_cellpairs(X, w, 1.0, W, T, c, 1, cap=n * 8)
+    ed = _edges(n * 8)
+    r = gg.girg_generate(ed, n=n, d=d, beta=beta, T=T, avg_deg=10.0, seed=1)
+    assert r.status == gg.GIRG_OK
+    assert r.c_used == pytest.approx(c, rel=1e-9)
+    r = gg.girg_generate(ed, n=n, d=d, beta=beta, T=T, c=c, seed=1)
+    assert r.status == gg.GIRG_OK
+    assert _set(ed, r.num_edges) == O.edge_set(ref.edges)
+    st = gg.last_stats()
+    assert st["type1_pairs"] == ref.stats["type1_pairs"]
+    assert st["type2_candidates"] == ref.stats["type2_candidates"]
+    assert st["jump_draws"] == ref.stats["jump_draws"]
