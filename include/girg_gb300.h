@@ -122,6 +122,28 @@ int girg_allpairs(int64_t n, int32_t d, const uint32_t* d_X, const double* d_w, 
                   double T, double c, uint64_t seed, int32_t precision, int32_t edge_bytes,
                   void* d_edges, int64_t capacity_edges, int64_t* num_edges, void* stream);
 
+/* Largest n accepted by girg_allpairs_noalloc. */
+#define GIRG_NOALLOC_MAX_N (1 << 20)
+
+/* girg_allpairs without any device allocation.  The paper has no counterpart of this
+ * entry point: it exists for callers that cannot allocate device memory, e.g. a
+ * plug-in inside a host application that owns the whole device memory pool, or a
+ * latency-critical loop where an allocation could block or fail under memory
+ * pressure.  Arguments, results and errors are those of girg_allpairs, except that
+ * n must not exceed GIRG_NOALLOC_MAX_N (larger n returns GIRG_E_PARAM before any
+ * device work).  Its scratch (a per-vertex scale and the edge counters, about 4 MiB)
+ * is a fixed device array of the library, held by every GPU that loads the library
+ * until the process exits.  The first call on a device looks up that array's device
+ * address (once per device, with the device current); make that first call before
+ * any stream capture.  All calls share the array, which keeps the last call's
+ * contents (the counters are cleared at the start of every call): calls whose device
+ * work overlaps -- on different streams or host threads -- race on it and must be
+ * serialised by the caller. */
+int girg_allpairs_noalloc(int64_t n, int32_t d, const uint32_t* d_X, const double* d_w,
+                          double W, double T, double c, uint64_t seed, int32_t precision,
+                          int32_t edge_bytes, void* d_edges, int64_t capacity_edges,
+                          int64_t* num_edges, void* stream);
+
 /* Weights and positions of girg_generate (Sec. 2.1, Sec. 5.1 steps 1-2) into caller
  * buffers: d_w n doubles, d_X d x n uint32 (layout as above). */
 int girg_points(int64_t n, int32_t d, double beta, double w_min, uint64_t seed, double* d_w,

@@ -58,6 +58,8 @@ SIGNATURES = {
                                         P]),
     "hrg_generate": (I32, [P, P, I64, P, P]),
     "girg_allpairs": (I32, [I64, I32, P, P, DBL, DBL, DBL, U64, I32, I32, P, I64, P, P]),
+    "girg_allpairs_noalloc": (I32, [I64, I32, P, P, DBL, DBL, DBL, U64, I32, I32, P, I64, P,
+                                    P]),
     "girg_points": (I32, [I64, I32, DBL, DBL, U64, P, P, P]),
     "hrg_points": (I32, [I64, DBL, DBL, U64, P, P, P]),
     "girg_expected_avg_degree": (I32, [P, P, P]),
@@ -182,6 +184,21 @@ def girg_allpairs(edges, X, w, *, W, T, c, seed=1, precision=PRECISION_FP32,
     st = lib.girg_allpairs(n, d, _ptr(X), _ptr(w), W, T, c, seed, precision,
                            edges.element_size(), _ptr(edges), edges.shape[0], ctypes.byref(m),
                            _stream(stream))
+    return Result(st, m.value, c)
+
+
+def girg_allpairs_noalloc(edges, X, w, *, W, T, c, seed=1, precision=PRECISION_FP32,
+                          stream=None) -> Result:
+    """girg_allpairs with its scratch in a fixed library-owned device array: for callers
+    that cannot allocate device memory (n <= GIRG_NOALLOC_MAX_N = 2^20).  Calls whose
+    device work overlaps share that array and must be serialised."""
+    _torch()
+    lib = load()
+    d, n = X.shape
+    m = ctypes.c_int64(0)
+    st = lib.girg_allpairs_noalloc(n, d, _ptr(X), _ptr(w), W, T, c, seed, precision,
+                                   edges.element_size(), _ptr(edges), edges.shape[0],
+                                   ctypes.byref(m), _stream(stream))
     return Result(st, m.value, c)
 
 
