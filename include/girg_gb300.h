@@ -168,7 +168,9 @@ int girg_last_stats(int64_t* out, int32_t len);
 
 /* Milliseconds spent in each phase of the last call on this host thread
  * (CUDA events): [0] points+reductions, [1] tables/host, [2] keys+sort+gather,
- * [3] enumeration + type II, [4] type I, [5] heavy type II, [6] total. */
+ * [3] enumeration + type II, [4] type I, [5] heavy type II, [6] total; host wall
+ * clock: [7] reduction readback, [8] search for c, [9] table build.  Copies
+ * min(len, 10) values; returns the number copied. */
 int girg_last_phase_ms(float* out, int32_t len);
 
 /* Sorted vertex order of the bucket/Morton sort (Sec. 3.4) for the given points:

@@ -28,7 +28,7 @@ STAT_NAMES = ("type1_pairs", "coins", "rechecks", "type2_items", "jump_draws",
               "type2_candidates", "rows", "type1_items", "heavy_chunks", "edges",
               "kernel_launches", "type1_vertex_refs", "type1_edges")
 PHASE_NAMES = ("points_reduce", "tables", "sort", "enumerate_type2", "type1", "heavy_type2",
-               "total")
+               "total", "host_reduce_readback", "host_c_search", "host_tables")
 
 
 class GirgParams(ctypes.Structure):
@@ -125,8 +125,8 @@ def last_stats() -> dict:
 
 
 def last_phase_ms() -> dict:
-    buf = (ctypes.c_float * 7)()
-    load().girg_last_phase_ms(buf, 7)
+    buf = (ctypes.c_float * len(PHASE_NAMES))()
+    load().girg_last_phase_ms(buf, len(PHASE_NAMES))
     return dict(zip(PHASE_NAMES, list(buf)))
 
 

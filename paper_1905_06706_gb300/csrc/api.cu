@@ -8,6 +8,7 @@
 // reads (comparison and insertion levels, type-II bounds p-bar and ln(1-p-bar)),
 // with the same deterministic arithmetic as the device.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -26,7 +27,7 @@ thread_local unsigned long long gg::g_launches = 0;
 namespace {
 
 thread_local int64_t g_stats[kNumStats];
-thread_local float g_ms[7];
+thread_local float g_ms[10];
 
 struct CudaFail {
     cudaError_t err;
@@ -86,6 +87,10 @@ struct Timer {
     }
 };
 
+double host_ms_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
 double round128(unsigned long long hi, unsigned long long lo, int E0) {
     unsigned __int128 acc = ((unsigned __int128)hi << 64) | lo;
     if (acc == 0) return 0.0;
@@ -143,6 +148,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     const int64_t n = P.n;
     const int d = P.d;
     const bool girg = P.model == 0;
+    const auto host_t0 = std::chrono::steady_clock::now();
     // ---------------------------------------------------------------- tables
     int L = 0;
     int64_t cnt[kMaxLayers];
@@ -220,41 +226,37 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
             if (i < kMaxLayers) run += (uint64_t)cnt[i];
         }
     }
-    // row classes (i, l): the buckets j >= i with type I (CL = l) and type II (CL >= l >= 2)
+    // row classes (i, l): the buckets j >= i with type II (CL >= l >= 2), then with
+    // type I (CL = l)
     int n3 = 1, n6 = 1;
     for (int k = 0; k < d; ++k) {
         n3 *= 3;
         n6 *= 6;
     }
     const bool tzero = P.T == 0.0;
-    std::vector<uint32_t> cstart((size_t)std::max(L, 1) * (kMaxLevel + 1), 0),
-        cnent(cstart.size(), 0), ctotal(cstart.size(), 0);
-    std::vector<ClassEntry> entries;
+    std::vector<RowClass> classes((size_t)std::max(L, 1) * (kMaxLevel + 1), RowClass{0, 0, 0});
+    std::vector<uint8_t> jlist;
     for (int i = 0; i < L; ++i) {
         if (!cnt[i]) continue;
         for (int l = 0; l <= CLd[i]; ++l) {
-            const size_t cls = (size_t)i * (kMaxLevel + 1) + l;
-            cstart[cls] = (uint32_t)entries.size();
-            uint32_t pre = 0;
-            for (int j = i; j < L; ++j) {
-                if (!cnt[j]) continue;
-                if (!tzero && l >= 2 && CL[i][j] >= l) {
-                    entries.push_back(ClassEntry{(uint16_t)j, 2, pre});
-                    pre += (uint32_t)n6;
+            RowClass rc{0, 0, (uint32_t)jlist.size()};
+            for (int j = i; j < L; ++j)
+                if (cnt[j] && !tzero && l >= 2 && CL[i][j] >= l) {
+                    jlist.push_back((uint8_t)j);
+                    ++rc.n2;
                 }
-                if (CL[i][j] == l) {
-                    entries.push_back(ClassEntry{(uint16_t)j, 1, pre});
-                    pre += (uint32_t)n3;
+            for (int j = i; j < L; ++j)
+                if (cnt[j] && CL[i][j] == l) {
+                    jlist.push_back((uint8_t)j);
+                    ++rc.n1;
                 }
-            }
-            cnent[cls] = (uint32_t)entries.size() - cstart[cls];
-            ctotal[cls] = pre;
+            classes[(size_t)i * (kMaxLevel + 1) + l] = rc;
         }
     }
-    if (entries.empty()) entries.push_back(ClassEntry{0, 0, 0});
+    if (jlist.empty()) jlist.push_back(0);
     // type-II bounds for every (i <= j, l, g in {1, 2})
     std::vector<TwoEntry> tii((size_t)std::max(L, 1) * std::max(L, 1) * (lcap + 1) * 2);
-    for (auto& e : tii) e = TwoEntry{0.0, 0.0, 0.0f, 0.0f, 62, 0};
+    for (auto& e : tii) e = TwoEntry{0.0, 0.0, 0.0f, 0.0f, 62, 0};  // never read
     if (!tzero) {
         for (int i = 0; i < L; ++i) {
             if (!cnt[i]) continue;
@@ -288,7 +290,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
                         e.log2pbar = (float)std::log2(pbar);
                         e.invLb = pbar < 1.0 ? (float)(1.0 / e.Lb) : -INFINITY;
                         e.k = chunk_log(pbar);
-                        e.pad = 0;
+                        e.one = pbar < 1.0 ? 0 : 1;
                         tii[((((size_t)i * L + j) * (lcap + 1) + l) << 1) + (g - 1)] = e;
                     }
                 }
@@ -316,6 +318,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
             fhi[m] = std::isinf(F) ? INFINITY : std::nextafterf(f, INFINITY) * (1.0f + 0x1p-22f);
         }
     }
+    g_ms[9] = (float)host_ms_since(host_t0);
     tm.mark();  // tables done
     // ---------------------------------------------------------------- sort
     uint32_t* key = S.get<uint32_t>(n);
@@ -361,18 +364,14 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     tm.mark();  // sort done
     // ---------------------------------------------------------------- device tables
     TwoEntry* d_tii = S.get<TwoEntry>(tii.size());
-    uint32_t* d_cstart = S.get<uint32_t>(cstart.size());
-    uint32_t* d_cnent = S.get<uint32_t>(cnent.size());
-    uint32_t* d_ctotal = S.get<uint32_t>(ctotal.size());
-    ClassEntry* d_entries = S.get<ClassEntry>(entries.size());
+    RowClass* d_classes = S.get<RowClass>(classes.size());
+    uint8_t* d_jlist = S.get<uint8_t>(jlist.size());
     float* d_flo = S.get<float>(K);
     float* d_fhi = S.get<float>(K);
     CK(cudaMemcpyAsync(d_tii, tii.data(), tii.size() * sizeof(TwoEntry), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_cstart, cstart.data(), cstart.size() * 4, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_cnent, cnent.data(), cnent.size() * 4, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_ctotal, ctotal.data(), ctotal.size() * 4, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_entries, entries.data(), entries.size() * sizeof(ClassEntry),
+    CK(cudaMemcpyAsync(d_classes, classes.data(), classes.size() * sizeof(RowClass),
                        cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_jlist, jlist.data(), jlist.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_flo, flo.data(), K * 4, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_fhi, fhi.data(), K * 4, cudaMemcpyHostToDevice, st));
     // rows: at most min(|V_i|, 2^(d l)) per (i, l)
@@ -431,10 +430,8 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     memcpy(cfg.layer_base, layer_base, sizeof(layer_base));
     memcpy(cfg.lstart, lstart, sizeof(lstart));
     cfg.tii = d_tii;
-    cfg.class_start = d_cstart;
-    cfg.class_nent = d_cnent;
-    cfg.class_total = d_ctotal;
-    cfg.entries = d_entries;
+    cfg.classes = d_classes;
+    cfg.jlist = d_jlist;
     cfg.offs = offs;
     cfg.Xs = Xs;
     cfg.sv = sv;
@@ -628,7 +625,7 @@ int girg_last_stats(int64_t* out, int32_t len) {
 }
 
 int girg_last_phase_ms(float* out, int32_t len) {
-    const int k = len < 7 ? len : 7;
+    const int k = len < 10 ? len : 10;
     for (int q = 0; q < k; ++q) out[q] = g_ms[q];
     return k;
 }
@@ -688,10 +685,14 @@ int girg_generate(const girg_params* params, void* d_edges, int64_t capacity_edg
         launch_reduce(P.n, w, nullptr, P.w_min, exponent_of_ulp(P.w_min), solve ? 1 : 0,
                       P.T > 0.0 ? 1.0 / P.T : 0.0, red, st);
         tm.mark();
+        auto h0 = std::chrono::steady_clock::now();
         read_reduce(P, red, st);
+        g_ms[7] = (float)host_ms_since(h0);
         if (P.red.range_error) return GIRG_E_RANGE;
         P.W = round128(P.red.sum_hi, P.red.sum_lo, exponent_of_ulp(P.w_min));
+        h0 = std::chrono::steady_clock::now();
         P.c = solve ? solve_c(P, params->avg_deg, S, st) : params->c;
+        g_ms[8] = (float)host_ms_since(h0);
         if (c_used) *c_used = P.c;
         run_sampler(P, S, st, tm, d_edges, capacity_edges, num_edges, nullptr);
         finish_timing(tm);

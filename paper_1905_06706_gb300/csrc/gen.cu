@@ -71,7 +71,7 @@ __device__ __forceinline__ void add128(unsigned long long& lo, unsigned long lon
 
 // Reductions over the weights (and radii for HRG) of all vertices.
 __global__ void k_reduce(int64_t n, const double* __restrict__ w, const double* __restrict__ r,
-                         double w_min, int E0, int want_sums, double invT, double two_invT,
+                         double w_min, int E0, int want_sums, double invT, int m_int,
                          Reduce* __restrict__ out) {
     __shared__ unsigned int s_cnt[kMaxLayers];
     __shared__ unsigned long long s_wmax[kMaxLayers];
@@ -116,8 +116,16 @@ __global__ void k_reduce(int64_t n, const double* __restrict__ w, const double* 
         if (want_sums) {
             a2 += wv * wv;
             if (invT > 0.0) {
-                at += pow(wv, invT);
-                a2t += pow(wv, two_invT);
+                // w^(1/T) by repeated products when 1/T is a small integer
+                double t;
+                if (m_int > 0) {
+                    t = wv;
+                    for (int q = 1; q < m_int; ++q) t *= wv;
+                } else {
+                    t = exp2(invT * log2(wv));
+                }
+                at += t;
+                a2t += t * t;
             }
         }
     }
@@ -225,8 +233,10 @@ void launch_min_weight(int64_t n, const double* w, unsigned long long* out, cuda
 void launch_reduce(int64_t n, const double* w, const double* r, double w_min, int E0,
                    int want_sums, double invT, Reduce* out, cudaStream_t st) {
     ++g_launches;
+    int m_int = 0;
+    if (invT > 0.0 && invT == floor(invT) && invT <= 64.0) m_int = (int)invT;
     k_reduce<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, w, r, w_min, E0, want_sums, invT,
-                                                        2.0 * invT, out);
+                                                        m_int, out);
 }
 
 void launch_gather_above(int64_t n, const double* w, double thr, double* out, unsigned int cap,

@@ -13,16 +13,16 @@ struct TwoEntry {
     float log2pbar;   // log2(pbar) rounded to float
     float invLb;      // 1 / Lb rounded to float (-inf when pbar = 1)
     int32_t k;        // chunk length exponent
-    int32_t pad;
+    int32_t one;      // pbar == 1 (no jumps: every index is a candidate)
 };
 
-// One entry of the bucket list of a row class (i, l): bucket j and the kind of
-// cell pairs (1: neighbours, type I; 2: distant with neighbouring parents,
-// type II), with the number of offset combinations before it.
-struct ClassEntry {
-    uint16_t j;
-    uint16_t type;
-    uint32_t prefix;
+// The buckets a row (bucket i, level l, cell A) pairs with: the n2 buckets j >= i
+// with CL(i,j) >= l >= 2 (distant cells, type II) at jlist[jbase .. jbase + n2),
+// then the n1 buckets with CL(i,j) = l (neighbour cells, type I).  A row has
+// n2 6^d + n1 3^d offset combinations, type II first.
+struct RowClass {
+    uint16_t n2, n1;
+    uint32_t jbase;
 };
 
 // A type-I item: rectangle V_i^A x V_j^B of sorted positions; bit 31 of b_len
@@ -63,10 +63,8 @@ struct DevCfg {
     uint32_t layer_base[kMaxLayers + 1];
     uint32_t lstart[kMaxLayers + 1];
     const TwoEntry* tii;
-    const uint32_t* class_start;  // [(i * (kMaxLevel + 1) + l)] -> first entry
-    const uint32_t* class_nent;   // number of entries of the class
-    const uint32_t* class_total;  // number of offset combinations of the class
-    const ClassEntry* entries;
+    const RowClass* classes;  // [i * (kMaxLevel + 1) + l]
+    const uint8_t* jlist;
     const uint32_t* offs;
     const uint32_t* Xs;   // d x n sorted coordinates
     const float* sv;      // sorted per-vertex scale (GIRG)
@@ -205,48 +203,60 @@ __device__ __forceinline__ void flush_edges(const DevCfg& cfg, WarpEdges& we, un
 }
 
 // --------------------------------------------------------------- uniforms in float
-// log2 of U = (2 (bits >> 12) + 1) 2^-53 in single precision (relative error of
-// the argument <= 2^-24).
-__device__ __forceinline__ float log2_uniform32(uint32_t lo, uint32_t hi) {
-    const unsigned long long bits = ((unsigned long long)hi << 32) | lo;
-    const float u = __ull2float_rn(2ull * (bits >> 12) + 1ull) * 0x1p-53f;
-    return log2f(u);
+// The uniform U = (2 (bits >> 12) + 1) 2^-53 of two Philox words (bits = hi:lo) in
+// single precision, from 32-bit conversions only: U = hi 2^-32 + (2 (lo >> 12) + 1)
+// 2^-53 with both terms exact in float and one rounding (relative error <= 2^-23).
+__device__ __forceinline__ float uniform32(uint32_t lo, uint32_t hi) {
+    return fmaf(__uint2float_rn(2u * (lo >> 12) + 1u), 0x1p-53f, __uint2float_rn(hi) * 0x1p-32f);
 }
 
-// ln U in single precision with small relative error for all U in (0,1):
-// for U >= 1/2 through 1 - U, which is exact as an integer multiple of 2^-53.
+// 1 - U in single precision: (2^32 - 1 - hi) 2^-32 + (2^21 - 1 - 2 (lo >> 12)) 2^-53.
+__device__ __forceinline__ float one_minus_uniform32(uint32_t lo, uint32_t hi) {
+    return fmaf(__uint2float_rn(0x1FFFFFu - 2u * (lo >> 12)), 0x1p-53f,
+                __uint2float_rn(~hi) * 0x1p-32f);
+}
+
+__device__ __forceinline__ float log2_uniform32(uint32_t lo, uint32_t hi) {
+    return log2f(uniform32(lo, hi));
+}
+
+// ln U in single precision with relative error ~2^-22 for all U in (0, 1): for
+// U >= 1/2 through ln(1 - (1 - U)).
 __device__ __forceinline__ float ln_uniform32(uint32_t lo, uint32_t hi) {
-    const unsigned long long bits = ((unsigned long long)hi << 32) | lo;
-    const unsigned long long K = bits >> 12;
-    if (K >= (1ull << 51)) {
-        const unsigned long long M = (1ull << 53) - 1ull - 2ull * K;
-        return log1pf(-__ull2float_rn(M) * 0x1p-53f);
-    }
-    return logf(__ull2float_rn(2ull * K + 1ull) * 0x1p-53f);
+    if (hi >= 0x80000000u) return log1pf(-one_minus_uniform32(lo, hi));
+    return logf(uniform32(lo, hi));
 }
 
 // Geometric jump X = floor(ln U / ln(1 - pbar)) against the remaining length rem
 // of the chunk.  Returns 0: stop (X >= rem), 1: continue with *X, decided in
 // single precision with a 2^-19 relative error bound, or 2: undecided, the
-// caller evaluates the FP64 rule.
+// caller evaluates the FP64 rule.  Only 32-bit conversions (the FP64 units of
+// the GPU also convert 64-bit integers).
 __device__ __forceinline__ int jump32(uint32_t lo, uint32_t hi, float invLb, unsigned long long rem,
                                       unsigned long long* X) {
     const float x = ln_uniform32(lo, hi) * invLb;  // >= 0
     const float xlo = x * (1.0f - 0x1p-19f), xhi = x * (1.0f + 0x1p-19f);
     if (rem < (1ull << 24)) {
-        const float remf = (float)rem;
+        const float remf = __uint2float_rn((uint32_t)rem);  // exact
         if (xlo >= remf) return 0;
-        if (xhi < remf && floorf(xlo) == floorf(xhi)) {
-            *X = (unsigned long long)floorf(xhi);
-            return 1;
+        if (xhi < remf) {
+            const float a = floorf(xlo), b = floorf(xhi);
+            if (a == b) {
+                *X = __float2uint_rz(b);
+                return 1;
+            }
         }
         return 2;
     }
-    const float remf = (float)rem;
-    if (xlo >= remf * (1.0f + 0x1p-22f)) return 0;
-    if (xhi < 0x1p22f && floorf(xlo) == floorf(xhi)) {
-        *X = (unsigned long long)floorf(xhi);
-        return 1;
+    const float remf = fmaf(__uint2float_rn((uint32_t)(rem >> 32)), 0x1p32f,
+                            __uint2float_rn((uint32_t)rem));
+    if (xlo >= remf * (1.0f + 0x1p-20f)) return 0;
+    if (xhi < 0x1p22f) {
+        const float a = floorf(xlo), b = floorf(xhi);
+        if (a == b) {
+            *X = __float2uint_rz(b);
+            return 1;
+        }
     }
     return 2;
 }

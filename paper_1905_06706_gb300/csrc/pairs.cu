@@ -10,15 +10,15 @@
 // cells B that are distant from A but have neighbouring parents when
 // CL(i,j) >= l (type II), for buckets j >= i; for j = i only B >= A (type I)
 // or B > A (type II).  This visits exactly the (cell pair, bucket pair) items
-// of the recursion, in a different order.
+// of the recursion, in a different order.  Neighbour and parent-neighbour cells
+// are formed by dilated (per-dimension masked) addition on Morton codes.
 //
 // Decisions are made in single precision with a rigorous error band; inside
 // the band they are recomputed with the exact FP64 rule (the same arithmetic
-// as the FP64 reference), so the edge set equals the FP64 one.
+// as the FP64 reference), so the edge set equals the FP64 one.  The kernels are
+// instantiated per dimension (d = 1..4, and a generic d <= 8).
 #include "internal.cuh"
 #include "kernels.h"
-
-namespace cg = cooperative_groups;
 
 namespace gg {
 
@@ -30,7 +30,7 @@ struct Counters {
 struct View {  // per-vertex arrays indexed by position
     const uint32_t* X;
     const float* sv;
-    const double* w;   // GIRG weights or HRG radii
+    const double* w;      // GIRG weights or HRG radii
     const uint32_t* ids;  // nullptr: id = position
     const float* E32;
     const float* einv32;
@@ -44,10 +44,12 @@ __device__ __forceinline__ View sorted_view(const DevCfg& cfg) {
 
 __device__ __forceinline__ uint32_t vid(const View& V, uint32_t p) { return V.ids ? V.ids[p] : p; }
 
-__device__ __forceinline__ uint32_t torus_D(const DevCfg& cfg, const View& V, uint32_t pu,
-                                            uint32_t pv) {
+template <int DIM>
+__device__ __forceinline__ uint32_t torus_D(int d, const View& V, uint32_t pu, uint32_t pv) {
     uint32_t m = 0;
-    for (int k = 0; k < cfg.d; ++k) {
+#pragma unroll
+    for (int k = 0; k < (DIM ? DIM : kMaxDim); ++k) {
+        if (DIM == 0 && k >= d) break;
         const uint32_t t = circ_diff(V.X[(int64_t)k * V.n + pu], V.X[(int64_t)k * V.n + pv]);
         m = t > m ? t : m;
     }
@@ -56,7 +58,7 @@ __device__ __forceinline__ uint32_t torus_D(const DevCfg& cfg, const View& V, ui
 
 // kappa_uv / r in single precision (D > 0).
 __device__ __forceinline__ float kappa_ratio(const View& V, uint32_t pu, uint32_t pv, uint32_t D) {
-    return V.sv[pu] * V.sv[pv] * (4294967296.0f / (float)D);
+    return V.sv[pu] * V.sv[pv] * __fdividef(4294967296.0f, __uint2float_rn(D));
 }
 
 __device__ __forceinline__ double girg_p_pair(const DevCfg& cfg, const View& V, uint32_t pu,
@@ -65,15 +67,38 @@ __device__ __forceinline__ double girg_p_pair(const DevCfg& cfg, const View& V, 
 }
 
 // HRG cosh d in FP64 from the radii of both vertices.
-__device__ __forceinline__ double hrg_coshd_pair(const View& V, uint32_t pu, uint32_t pv, uint32_t D) {
+__device__ __noinline__ double hrg_coshd_pair(const View& V, uint32_t pu, uint32_t pv, uint32_t D) {
     double Eu, shu, Ev, shv;
     hrg_vertex64(V.w[pu], &Eu, &shu);
     hrg_vertex64(V.w[pv], &Ev, &shv);
     return hrg_coshd64(Eu, shu, Ev, shv, D);
 }
 
+__device__ __noinline__ bool girg_t1_exact(const DevCfg& cfg, const View& V, uint32_t pu,
+                                           uint32_t pv, uint32_t D, uint32_t lo, uint32_t hi) {
+    if (cfg.tzero) return girg_thresh64(V.w[pu], V.w[pv], D, cfg.W, cfg.c, cfg.d);
+    return uniform53(lo, hi) < girg_p_pair(cfg, V, pu, pv, D);
+}
+
+__device__ __noinline__ bool hrg_t1_exact(const DevCfg& cfg, const View& V, uint32_t pu, uint32_t pv,
+                                          uint32_t D, uint32_t lo, uint32_t hi) {
+    const double cd = hrg_coshd_pair(V, pu, pv, D);
+    if (cfg.tzero) return cd < cfg.coshR;
+    return uniform53(lo, hi) < hrg_p_from_coshd(cd, cfg.R, cfg.T);
+}
+
+__device__ __noinline__ bool t2_exact(const DevCfg& cfg, const View& V, uint32_t pu, uint32_t pv,
+                                      uint32_t D, uint32_t lo, uint32_t hi, double pbar) {
+    double p;
+    if (cfg.model == 0)
+        p = D == 0 ? 1.0 : girg_p_pair(cfg, V, pu, pv, D);
+    else
+        p = hrg_p_from_coshd(hrg_coshd_pair(V, pu, pv, D), cfg.R, cfg.T);
+    return DMUL(uniform53(lo, hi), pbar) < p;
+}
+
 __device__ __forceinline__ float hrg_coshd32(const View& V, uint32_t pu, uint32_t pv, uint32_t D) {
-    const float s = sinpif((float)D * 0x1p-32f);
+    const float s = sinpif(__uint2float_rn(D) * 0x1p-32f);
     const float ch = 0.5f * (V.E32[pu] * V.einv32[pv] + V.E32[pv] * V.einv32[pu]);
     return ch + 2.0f * V.sh32[pu] * V.sh32[pv] * (s * s);
 }
@@ -83,104 +108,105 @@ __device__ __forceinline__ float hrg_p32(const DevCfg& cfg, float cd) {
 }
 
 // Type I: edge iff U(seed, u, v) < p_uv (T > 0) or the threshold rule (T = 0).
+template <int DIM>
 __device__ bool decide_t1(const DevCfg& cfg, const View& V, uint32_t pu, uint32_t pv, Counters& C) {
     const uint32_t iu = vid(V, pu), iv = vid(V, pv);
     const uint32_t a = iu < iv ? iu : iv, b = iu < iv ? iv : iu;
-    if (cfg.model == 0) {
-        const uint32_t D = torus_D(cfg, V, pu, pv);
-        if (D == 0) return true;
+    if ((DIM == 1 || DIM == 0) && cfg.model == 1) {
+        // HRG (Sec. 2.2): threshold d < R, binomial U < p_T(d)
+        const uint32_t D = circ_diff(V.X[pu], V.X[pv]);
         if (cfg.precision == 1) {
-            if (cfg.tzero) return girg_thresh64(V.w[pu], V.w[pv], D, cfg.W, cfg.c, cfg.d);
+            uint32_t lo = 0, hi = 0;
+            if (!cfg.tzero) {
+                ++C.coins;
+                const P4 o = philox(a, b, kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
+                lo = o.x;
+                hi = o.y;
+            }
+            return hrg_t1_exact(cfg, V, pu, pv, D, lo, hi);
+        }
+        const float cd = hrg_coshd32(V, pu, pv, D);
+        if (cfg.tzero) {
+            if (cd < cfg.coshR32 * (1.0f - 0x1p-16f)) return true;
+            if (cd > cfg.coshR32 * (1.0f + 0x1p-16f)) return false;
+            ++C.recheck;
+            return hrg_t1_exact(cfg, V, pu, pv, D, 0u, 0u);
+        }
+        ++C.coins;
+        const P4 o = philox(a, b, kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
+        // distance filter (Sec. 4.3): the bin of U brackets the threshold on cosh d;
+        // bin m = floor(U (K - 1)) exactly, from the 53-bit integer of U
+        const unsigned long long odd = 2ull * ((((unsigned long long)o.y << 32) | o.x) >> 12) + 1ull;
+        const int m = (int)((odd * (unsigned long long)(cfg.filt_k - 1)) >> 53);
+        if (cd * (1.0f + 0x1p-16f) < cfg.filt_lo[m + 1]) return true;
+        if (cd * (1.0f - 0x1p-16f) >= cfg.filt_hi[m]) return false;
+        const float p32 = hrg_p32(cfg, cd);
+        const float u32 = uniform32(o.x, o.y);
+        if (u32 < p32 * (1.0f - cfg.bandG)) return true;
+        if (u32 > p32 * (1.0f + cfg.bandG)) return false;
+        ++C.recheck;
+        return hrg_t1_exact(cfg, V, pu, pv, D, o.x, o.y);
+    }
+    const uint32_t D = torus_D<DIM>(cfg.d, V, pu, pv);
+    if (D == 0) return true;
+    if (cfg.precision == 1) {
+        uint32_t lo = 0, hi = 0;
+        if (!cfg.tzero) {
             ++C.coins;
             const P4 o = philox(a, b, kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
-            return uniform53(o.x, o.y) < girg_p_pair(cfg, V, pu, pv, D);
+            lo = o.x;
+            hi = o.y;
         }
-        const float ratio = kappa_ratio(V, pu, pv, D);
-        if (cfg.tzero) {
-            if (ratio > 1.0f + cfg.band_ratio) return true;
-            if (ratio < 1.0f - cfg.band_ratio) return false;
-            ++C.recheck;
-            return girg_thresh64(V.w[pu], V.w[pv], D, cfg.W, cfg.c, cfg.d);
-        }
-        if (ratio >= 1.0f + cfg.band_ratio) return true;  // p = 1
-        const float lp = cfg.dT * log2f(ratio);          // log2 p
-        if (lp < -54.0f - cfg.bandG) return false;        // p < 2^-54 < every U
-        ++C.coins;
-        const P4 o = philox(a, b, kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
-        const float G = lp - log2_uniform32(o.x, o.y);
-        if (G > cfg.bandG) return true;
-        if (G < -cfg.bandG) return false;
-        ++C.recheck;
-        return uniform53(o.x, o.y) < girg_p_pair(cfg, V, pu, pv, D);
+        return girg_t1_exact(cfg, V, pu, pv, D, lo, hi);
     }
-    // HRG (Sec. 2.2): threshold d < R, binomial U < p_T(d)
-    const uint32_t D = circ_diff(V.X[pu], V.X[pv]);
-    if (cfg.precision == 1) {
-        const double cd = hrg_coshd_pair(V, pu, pv, D);
-        if (cfg.tzero) return cd < cfg.coshR;
-        ++C.coins;
-        const P4 o = philox(a, b, kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
-        return uniform53(o.x, o.y) < hrg_p_from_coshd(cd, cfg.R, cfg.T);
-    }
-    const float cd = hrg_coshd32(V, pu, pv, D);
+    const float ratio = kappa_ratio(V, pu, pv, D);
     if (cfg.tzero) {
-        if (cd < cfg.coshR32 * (1.0f - 0x1p-16f)) return true;
-        if (cd > cfg.coshR32 * (1.0f + 0x1p-16f)) return false;
+        if (ratio > 1.0f + cfg.band_ratio) return true;
+        if (ratio < 1.0f - cfg.band_ratio) return false;
         ++C.recheck;
-        return hrg_coshd_pair(V, pu, pv, D) < cfg.coshR;
+        return girg_t1_exact(cfg, V, pu, pv, D, 0u, 0u);
     }
+    if (ratio >= 1.0f + cfg.band_ratio) return true;  // p = 1
+    const float lp = cfg.dT * log2f(ratio);          // log2 p
+    if (lp < -54.0f - cfg.bandG) return false;        // p < 2^-54 < every U
     ++C.coins;
     const P4 o = philox(a, b, kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
-    // distance filter (Sec. 4.3): the bin of U brackets the threshold on cosh d
-    const unsigned long long bits = ((unsigned long long)o.y << 32) | o.x;
-    const unsigned long long odd = 2ull * (bits >> 12) + 1ull;
-    const int m = (int)((odd * (unsigned long long)(cfg.filt_k - 1)) >> 53);
-    if (cd * (1.0f + 0x1p-16f) < cfg.filt_lo[m + 1]) return true;
-    if (cd * (1.0f - 0x1p-16f) >= cfg.filt_hi[m]) return false;
-    const float p32 = hrg_p32(cfg, cd);
-    const float u32 = __ull2float_rn(odd) * 0x1p-53f;
-    const float band = cfg.bandG;
-    if (u32 < p32 * (1.0f - band)) return true;
-    if (u32 > p32 * (1.0f + band)) return false;
+    const float G = lp - log2_uniform32(o.x, o.y);
+    if (G > cfg.bandG) return true;
+    if (G < -cfg.bandG) return false;
     ++C.recheck;
-    return uniform53(o.x, o.y) < hrg_p_from_coshd(hrg_coshd_pair(V, pu, pv, D), cfg.R, cfg.T);
+    return girg_t1_exact(cfg, V, pu, pv, D, o.x, o.y);
 }
 
 // Type-II acceptance: accept iff U' pbar < p_uv.
+template <int DIM>
 __device__ bool accept_t2(const DevCfg& cfg, const View& V, uint32_t pu, uint32_t pv, uint32_t lo,
                           uint32_t hi, const TwoEntry& e, Counters& C) {
-    if (cfg.model == 0) {
-        const uint32_t D = torus_D(cfg, V, pu, pv);
-        if (cfg.precision == 1) {
-            const double p = D == 0 ? 1.0 : girg_p_pair(cfg, V, pu, pv, D);
-            return DMUL(uniform53(lo, hi), e.pbar) < p;
-        }
-        if (D == 0) return true;
-        const float ratio = kappa_ratio(V, pu, pv, D);
-        if (ratio >= 1.0f + cfg.band_ratio) return true;
-        const float G = cfg.dT * log2f(ratio) - log2_uniform32(lo, hi) - e.log2pbar;
-        if (G > cfg.bandG) return true;
-        if (G < -cfg.bandG) return false;
+    if ((DIM == 1 || DIM == 0) && cfg.model == 1) {
+        const uint32_t D = circ_diff(V.X[pu], V.X[pv]);
+        if (cfg.precision == 1) return t2_exact(cfg, V, pu, pv, D, lo, hi, e.pbar);
+        const float p32 = hrg_p32(cfg, hrg_coshd32(V, pu, pv, D));
+        const float up = uniform32(lo, hi) * exp2f(e.log2pbar);
+        if (up < p32 * (1.0f - cfg.bandG)) return true;
+        if (up > p32 * (1.0f + cfg.bandG)) return false;
         ++C.recheck;
-        return DMUL(uniform53(lo, hi), e.pbar) < girg_p_pair(cfg, V, pu, pv, D);
+        return t2_exact(cfg, V, pu, pv, D, lo, hi, e.pbar);
     }
-    const uint32_t D = circ_diff(V.X[pu], V.X[pv]);
-    if (cfg.precision == 1)
-        return DMUL(uniform53(lo, hi), e.pbar) <
-               hrg_p_from_coshd(hrg_coshd_pair(V, pu, pv, D), cfg.R, cfg.T);
-    const float p32 = hrg_p32(cfg, hrg_coshd32(V, pu, pv, D));
-    const unsigned long long bits = ((unsigned long long)hi << 32) | lo;
-    const float up = __ull2float_rn(2ull * (bits >> 12) + 1ull) * 0x1p-53f * (float)e.pbar;
-    if (up < p32 * (1.0f - cfg.bandG)) return true;
-    if (up > p32 * (1.0f + cfg.bandG)) return false;
+    const uint32_t D = torus_D<DIM>(cfg.d, V, pu, pv);
+    if (cfg.precision == 1) return t2_exact(cfg, V, pu, pv, D, lo, hi, e.pbar);
+    if (D == 0) return true;
+    const float ratio = kappa_ratio(V, pu, pv, D);
+    if (ratio >= 1.0f + cfg.band_ratio) return true;
+    const float G = cfg.dT * log2f(ratio) - log2_uniform32(lo, hi) - e.log2pbar;
+    if (G > cfg.bandG) return true;
+    if (G < -cfg.bandG) return false;
     ++C.recheck;
-    return DMUL(uniform53(lo, hi), e.pbar) <
-           hrg_p_from_coshd(hrg_coshd_pair(V, pu, pv, D), cfg.R, cfg.T);
+    return t2_exact(cfg, V, pu, pv, D, lo, hi, e.pbar);
 }
 
 // One chunk of geometric jumps over [start, start + len) of the a x b index space
 // of a type-II item (Sec. 3.2).  Draw t of the chunk comes from `draw(t)`.
-template <class Draw>
+template <int DIM, class Draw>
 __device__ void jump_chunk(const DevCfg& cfg, const View& V, WarpEdges& we, const TwoEntry& e,
                            uint32_t a_begin, uint32_t b_begin, uint32_t b_len,
                            unsigned long long start, unsigned long long len, Draw draw,
@@ -191,7 +217,7 @@ __device__ void jump_chunk(const DevCfg& cfg, const View& V, WarpEdges& we, cons
         ++C.draws;
         const unsigned long long rem = len - (unsigned long long)(s + 1);
         unsigned long long X = 0;
-        if (e.pbar < 1.0) {
+        if (!e.one) {
             int r = 2;
             if (cfg.precision == 0) r = jump32(o.x, o.y, e.invLb, rem, &X);
             if (r == 2) {
@@ -214,7 +240,8 @@ __device__ void jump_chunk(const DevCfg& cfg, const View& V, WarpEdges& we, cons
             ib = (uint32_t)(idx - (unsigned long long)ia * b_len);
         }
         const uint32_t pu = a_begin + ia, pv = b_begin + ib;
-        if (accept_t2(cfg, V, pu, pv, o.z, o.w, e, C)) push_edge(cfg, we, vid(V, pu), vid(V, pv));
+        if (accept_t2<DIM>(cfg, V, pu, pv, o.z, o.w, e, C))
+            push_edge(cfg, we, vid(V, pu), vid(V, pv));
     }
 }
 
@@ -231,7 +258,7 @@ __device__ __forceinline__ void flush_counters(const DevCfg& cfg, const Counters
 
 // ------------------------------------------------------------------ rows
 // Row heads: the first sorted position of every non-empty (bucket i, level l, cell)
-// for l <= CL(i, i).
+// for l <= CLd(i) (the deepest comparison level of i with a bucket j >= i).
 __global__ void k_rows(DevCfg cfg, uint64_t* __restrict__ rows, unsigned int* __restrict__ count,
                        unsigned int cap) {
     const int lane = threadIdx.x & 31;
@@ -279,12 +306,12 @@ constexpr int kEnumThreads = 256;
 constexpr int kWarps = kEnumThreads / 32;
 constexpr uint32_t kSplitB = 1024, kSplitAB = 4096;
 
-__device__ __forceinline__ uint32_t vrange_lo(const DevCfg& cfg, int j, uint32_t B, int l) {
-    const int s = cfg.d * (cfg.I[j] - l);
+__device__ __forceinline__ uint32_t vrange_lo(const DevCfg& cfg, int j, uint32_t B, int l, int d) {
+    const int s = d * (cfg.I[j] - l);
     return cfg.offs[cfg.layer_base[j] + (uint32_t)((uint64_t)B << s)];
 }
-__device__ __forceinline__ uint32_t vrange_hi(const DevCfg& cfg, int j, uint32_t B, int l) {
-    const int s = cfg.d * (cfg.I[j] - l);
+__device__ __forceinline__ uint32_t vrange_hi(const DevCfg& cfg, int j, uint32_t B, int l, int d) {
+    const int s = d * (cfg.I[j] - l);
     return cfg.offs[cfg.layer_base[j] + (uint32_t)(((uint64_t)B + 1) << s)];
 }
 
@@ -296,6 +323,35 @@ __device__ __forceinline__ bool digit_ok(int e, int lev) {
     return true;
 }
 
+// Add e in {-1, 0, 1} to the coordinate held in the Morton bits `mask` of M (one
+// dimension); carries run through the other dimensions' bits, so the result wraps
+// on the torus.
+__device__ __forceinline__ uint32_t dil_add(uint32_t M, uint32_t mask, uint32_t unit, int e) {
+    const uint32_t x = M & mask;
+    if (e > 0) return ((x | ~mask) + unit) & mask;
+    if (e < 0) return (x - unit) & mask;
+    return x;
+}
+
+// Bits of dimension k (coordinate 0 most significant) of a Morton code at level l.
+__device__ __forceinline__ uint32_t dim_mask(int d, int k, int l) {
+    const int nb = d * l;  // <= 32
+    const uint32_t lowk = 1u << (d - 1 - k);
+    uint32_t pat;  // bits d-1-k, 2d-1-k, ... of a 32-bit word
+    switch (d) {
+        case 1: pat = 0xffffffffu; break;
+        case 2: pat = 0x55555555u << (1 - k); break;
+        case 3: pat = 0x49249249u << (2 - k); break;
+        case 4: pat = 0x11111111u << (3 - k); break;
+        default: {
+            pat = 0;
+            for (int b = 0; b * d < 32; ++b) pat |= lowk << (b * d);
+        }
+    }
+    return nb >= 32 ? pat : (pat & ((1u << nb) - 1u));
+}
+
+template <int DIM>
 __global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
     __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
     __shared__ unsigned int s_en[kWarps];
@@ -305,7 +361,9 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
     WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
     const View V = sorted_view(cfg);
     Counters C;
-    const int d = cfg.d;
+    const int d = DIM ? DIM : cfg.d;
+    const uint32_t n3 = DIM == 1 ? 3u : DIM == 2 ? 9u : DIM == 3 ? 27u : DIM == 4 ? 81u : (uint32_t)cfg.n3;
+    const uint32_t n6 = DIM == 1 ? 6u : DIM == 2 ? 36u : DIM == 3 ? 216u : DIM == 4 ? 1296u : (uint32_t)cfg.n6;
     const unsigned int nrows = *cfg.row_count < cfg.row_cap ? *cfg.row_count : cfg.row_cap;
     unsigned long long t1_items_local = 0, t1_refs_local = 0;
     for (;;) {
@@ -320,65 +378,71 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
         const uint32_t base_i = cfg.layer_base[i];
         const int sA = d * (cfg.I[i] - l);
         const uint32_t A = (uint32_t)((uint64_t)(cfg.skey[p] - base_i) >> sA);
-        const uint32_t a_lo = vrange_lo(cfg, i, A, l), a_hi = vrange_hi(cfg, i, A, l);
+        const uint32_t a_lo = vrange_lo(cfg, i, A, l, d), a_hi = vrange_hi(cfg, i, A, l, d);
         const uint32_t a_len = a_hi - a_lo;
-        uint32_t ca[kMaxDim];
-        morton_decode(A, d, ca);
-        const uint32_t cls = (uint32_t)i * (kMaxLevel + 1) + l;
-        const uint32_t e0 = cfg.class_start[cls], ne = cfg.class_nent[cls];
-        const uint32_t total = cfg.class_total[cls];
-        const uint32_t side = (uint32_t)((1ull << l) - 1);  // coordinate mask at level l
+        const RowClass rc = cfg.classes[(uint32_t)i * (kMaxLevel + 1) + l];
+        const uint32_t n2c = (uint32_t)rc.n2 * n6;
+        const uint32_t total = n2c + (uint32_t)rc.n1 * n3;
+        const uint32_t PA = A >> d;  // parent cell (level l - 1)
         for (uint32_t c0 = 0; c0 < total; c0 += 32) {
             const uint32_t c = c0 + lane;
             int kind = 0;  // 1: type-I item, 2: type-II item
             int j = 0;
             uint32_t B = 0, b_lo = 0, b_len = 0, g = 0;
             if (c < total) {
-                uint32_t e = e0;
-                while (e + 1 < e0 + ne && cfg.entries[e + 1].prefix <= c) ++e;
-                const ClassEntry ent = cfg.entries[e];
-                j = ent.j;
-                uint32_t off = c - ent.prefix;
-                uint32_t cb[kMaxDim];
                 bool ok = true;
-                if (ent.type == 1) {
-                    for (int k = d - 1; k >= 0; --k) {
-                        const int ek = (int)(off % 3u) - 1;
-                        off /= 3u;
-                        ok = ok && digit_ok(ek, l);
-                        cb[k] = (ca[k] + (uint32_t)ek) & side;
-                    }
-                    if (ok) {
-                        B = morton_encode(cb, d);
-                        if (j == i && B < A) ok = false;
-                    }
-                } else {
+                if (c < n2c) {  // distant cell with a neighbouring parent
+                    const uint32_t e = c / n6, off = c - e * n6;
+                    j = cfg.jlist[rc.jbase + e];
                     const uint32_t kids = off & ((1u << d) - 1u);
-                    off >>= d;
-                    const uint32_t pside = side >> 1;
-                    uint32_t linf = 0;
-                    for (int k = d - 1; k >= 0; --k) {
-                        const int ek = (int)(off % 3u) - 1;
-                        off /= 3u;
+                    uint32_t q = off >> d;
+                    uint32_t P = 0, linf = 0;
+#pragma unroll
+                    for (int k = (DIM ? DIM : kMaxDim) - 1; k >= 0; --k) {
+                        if (DIM == 0 && k >= d) continue;
+                        const int ek = (int)(q % 3u) - 1;
+                        q /= 3u;
                         ok = ok && digit_ok(ek, l - 1);
-                        const uint32_t pk = ((ca[k] >> 1) + (uint32_t)ek) & pside;
-                        cb[k] = (pk << 1) | ((kids >> (d - 1 - k)) & 1u);
-                        const uint32_t df = (ca[k] - cb[k]) & side;
-                        const uint32_t cd = df < ((side + 1u) - df) ? df : ((side + 1u) - df);
-                        linf = cd > linf ? cd : linf;
+                        P |= dil_add(PA, dim_mask(d, k, l - 1), 1u << (d - 1 - k), ek);
+                        const int alpha = (int)((A >> (d - 1 - k)) & 1u);
+                        const int kid = (int)((kids >> (d - 1 - k)) & 1u);
+                        int diff = 2 * ek + kid - alpha;
+                        diff = diff < 0 ? -diff : diff;
+                        if (l == 2 && diff > 2) diff = 4 - diff;  // 4 cells per dimension
+                        linf = (uint32_t)diff > linf ? (uint32_t)diff : linf;
                     }
                     if (ok && linf <= 1) ok = false;  // a neighbour of A, not distant
                     if (ok) {
-                        B = morton_encode(cb, d);
+                        B = (P << d) | kids;
                         if (j == i && B <= A) ok = false;
                         g = linf - 1;
                     }
+                    kind = 2;
+                } else {  // neighbour cell
+                    const uint32_t c1 = c - n2c;
+                    const uint32_t e = c1 / n3;
+                    uint32_t q = c1 - e * n3;
+                    j = cfg.jlist[rc.jbase + rc.n2 + e];
+                    uint32_t Bv = 0;
+#pragma unroll
+                    for (int k = (DIM ? DIM : kMaxDim) - 1; k >= 0; --k) {
+                        if (DIM == 0 && k >= d) continue;
+                        const int ek = (int)(q % 3u) - 1;
+                        q /= 3u;
+                        ok = ok && digit_ok(ek, l);
+                        Bv |= dil_add(A, dim_mask(d, k, l), 1u << (d - 1 - k), ek);
+                    }
+                    if (ok) {
+                        B = Bv;
+                        if (j == i && B < A) ok = false;
+                    }
+                    kind = 1;
                 }
                 if (ok) {
-                    b_lo = vrange_lo(cfg, j, B, l);
-                    b_len = vrange_hi(cfg, j, B, l) - b_lo;
-                    if (b_len > 0) kind = ent.type;
+                    b_lo = vrange_lo(cfg, j, B, l, d);
+                    b_len = vrange_hi(cfg, j, B, l, d) - b_lo;
                 }
+                if (!ok || b_len == 0) kind = 0;
             }
             // ---- type-I items: split, then append with one atomic per warp
             uint32_t nsub = 0, ac = 0, bc = 0, na = 0;
@@ -429,8 +493,8 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
                     if (cfg.mode & kModeT2Light) {
                         const uint32_t s0 = cfg.seed_lo, s1 = cfg.seed_hi;
                         const uint32_t c2 = pack | (kTagLight << 17);
-                        jump_chunk(cfg, V, we, e, a_lo, b_lo, b_len, 0ull, tot,
-                                   [&](uint32_t t) { return philox(A, B, c2, t, s0, s1); }, C);
+                        jump_chunk<DIM>(cfg, V, we, e, a_lo, b_lo, b_len, 0ull, tot,
+                                        [&](uint32_t t) { return philox(A, B, c2, t, s0, s1); }, C);
                     }
                 } else if (cfg.mode & kModeT2Heavy) {
                     const unsigned int slot = atomicAdd(cfg.heavy_count, 1u);
@@ -467,11 +531,13 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
 // ------------------------------------------------------------------ type I
 constexpr int kT1Threads = 256;
 
+template <int DIM>
 __global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
     __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
     __shared__ unsigned int s_en[kWarps];
     __shared__ uint32_t s_pref[kWarps][33];
     __shared__ T1Item s_it[kWarps][32];
+    __shared__ float s_inv[kWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) s_en[warp] = 0;
     __syncwarp();
@@ -489,7 +555,8 @@ __global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
         const unsigned long long idx = first + lane;
         T1Item it{0u, 0u, 0u, 0u};
         if (idx < count) it = cfg.t1[idx];
-        const uint32_t work = it.a_len * (it.b_len & 0x7fffffffu);
+        const uint32_t bl0 = it.b_len & 0x7fffffffu;
+        const uint32_t work = it.a_len * bl0;
         uint32_t incl = work;
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -497,6 +564,7 @@ __global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
         }
         s_pref[warp][lane] = incl - work;
         s_it[warp][lane] = it;
+        s_inv[warp][lane] = bl0 ? 1.0f / (float)bl0 : 0.0f;
         const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
         __syncwarp();
         for (uint32_t f0 = 0; f0 < tot; f0 += 32) {
@@ -508,15 +576,24 @@ __global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
 #pragma unroll
                 for (int step = 16; step > 0; step >>= 1)
                     if (s_pref[warp][k + step] <= f) k += step;
-                const T1Item& t = s_it[warp][k];
+                const T1Item t = s_it[warp][k];
                 const uint32_t bl = t.b_len & 0x7fffffffu;
                 const uint32_t rr = f - s_pref[warp][k];
-                const uint32_t ia = rr / bl, ib = rr - ia * bl;
+                // rr / bl from a float reciprocal, corrected to the exact quotient
+                uint32_t ia = __float2uint_rz(__uint2float_rn(rr) * s_inv[warp][k]);
+                int ib = (int)rr - (int)(ia * bl);
+                if (ib < 0) {
+                    --ia;
+                    ib += (int)bl;
+                } else if (ib >= (int)bl) {
+                    ++ia;
+                    ib -= (int)bl;
+                }
                 pu = t.a_begin + ia;
-                pv = t.b_begin + ib;
+                pv = t.b_begin + (uint32_t)ib;
                 if (!((t.b_len & 0x80000000u) && pv <= pu)) {
                     ++C.t1pairs;
-                    edge = decide_t1(cfg, V, pu, pv, C);
+                    edge = decide_t1<DIM>(cfg, V, pu, pv, C);
                 }
             }
             if (edge) {
@@ -569,6 +646,7 @@ __global__ void k_heavy_scan(DevCfg cfg, unsigned long long* total_chunks) {
     if (threadIdx.x == 0) *total_chunks = s_carry;
 }
 
+template <int DIM>
 __global__ void __launch_bounds__(kEnumThreads) k_heavy(DevCfg cfg, const unsigned long long* total_chunks) {
     __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
     __shared__ unsigned int s_en[kWarps];
@@ -597,8 +675,8 @@ __global__ void __launch_bounds__(kEnumThreads) k_heavy(DevCfg cfg, const unsign
             const unsigned long long start = hc << e.k;
             const unsigned long long len = (tot - start) < (1ull << e.k) ? (tot - start) : (1ull << e.k);
             const uint32_t hlo = (uint32_t)hc, hhi = (uint32_t)(hc >> 32);
-            jump_chunk(cfg, V, we, e, h.a_begin, h.b_begin, h.b_len, start, len,
-                       [&](uint32_t t) { return philox(hlo, hhi, t, kTagDraw, ko.x, ko.y); }, C);
+            jump_chunk<DIM>(cfg, V, we, e, h.a_begin, h.b_begin, h.b_len, start, len,
+                            [&](uint32_t t) { return philox(hlo, hhi, t, kTagDraw, ko.x, ko.y); }, C);
         }
         flush_edges(cfg, we, kEdgeBuf / 2);
     }
@@ -610,6 +688,7 @@ __global__ void __launch_bounds__(kEnumThreads) k_heavy(DevCfg cfg, const unsign
 // ------------------------------------------------------------------ all pairs
 // Every pair u < v of the original order (Table 1, "Pairwise"): tiles of
 // 64 x 64 vertices, upper triangle only.
+template <int DIM>
 __global__ void __launch_bounds__(256) k_allpairs(DevCfg cfg, View V, unsigned int ntile) {
     __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
     __shared__ unsigned int s_en[kWarps];
@@ -620,15 +699,18 @@ __global__ void __launch_bounds__(256) k_allpairs(DevCfg cfg, View V, unsigned i
     Counters C;
     const unsigned long long ntri = (unsigned long long)ntile * (ntile + 1) / 2;
     for (unsigned long long t = blockIdx.x; t < ntri; t += gridDim.x) {
-        // tile (tu, tv), tu <= tv, from the triangular index t
-        unsigned int tv = (unsigned int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-        while ((unsigned long long)(tv + 1) * (tv + 2) / 2 <= t) ++tv;
-        while ((unsigned long long)tv * (tv + 1) / 2 > t) --tv;
+        // tile (tu, tv), tu <= tv, from the triangular index t (integer search)
+        unsigned int lo = 0, hi = ntile;  // largest tv with tv (tv + 1) / 2 <= t
+        while (hi - lo > 1) {
+            const unsigned int mid = (lo + hi) >> 1;
+            if ((unsigned long long)mid * (mid + 1) / 2 <= t) lo = mid; else hi = mid;
+        }
+        const unsigned int tv = lo;
         const unsigned int tu = (unsigned int)(t - (unsigned long long)tv * (tv + 1) / 2);
         for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) {
             const uint32_t u = tu * 64 + (q >> 6), v = tv * 64 + (q & 63);
             bool edge = false;
-            if (u < v && v < (uint32_t)V.n) edge = decide_t1(cfg, V, u, v, C);
+            if (u < v && v < (uint32_t)V.n) edge = decide_t1<DIM>(cfg, V, u, v, C);
             if (edge) push_edge(cfg, we, u, v);
             flush_edges(cfg, we, kEdgeBuf - 32);
         }
@@ -648,12 +730,24 @@ void launch_rows(const DevCfg& cfg, uint64_t* rows, unsigned int* row_count, uns
 
 void launch_enumerate(const DevCfg& cfg, cudaStream_t st) {
     ++g_launches;
-    k_enumerate<<<152 * 6, kEnumThreads, 0, st>>>(cfg);
+    switch (cfg.d) {
+        case 1: k_enumerate<1><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
+        case 2: k_enumerate<2><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
+        case 3: k_enumerate<3><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
+        case 4: k_enumerate<4><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
+        default: k_enumerate<0><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
+    }
 }
 
 void launch_type1(const DevCfg& cfg, cudaStream_t st) {
     ++g_launches;
-    k_type1<<<152 * 6, kT1Threads, 0, st>>>(cfg);
+    switch (cfg.d) {
+        case 1: k_type1<1><<<152 * 6, kT1Threads, 0, st>>>(cfg); break;
+        case 2: k_type1<2><<<152 * 6, kT1Threads, 0, st>>>(cfg); break;
+        case 3: k_type1<3><<<152 * 6, kT1Threads, 0, st>>>(cfg); break;
+        case 4: k_type1<4><<<152 * 6, kT1Threads, 0, st>>>(cfg); break;
+        default: k_type1<0><<<152 * 6, kT1Threads, 0, st>>>(cfg); break;
+    }
 }
 
 void launch_heavy_scan(const DevCfg& cfg, unsigned long long* total_chunks, cudaStream_t st) {
@@ -663,7 +757,13 @@ void launch_heavy_scan(const DevCfg& cfg, unsigned long long* total_chunks, cuda
 
 void launch_heavy(const DevCfg& cfg, const unsigned long long* total_chunks, cudaStream_t st) {
     ++g_launches;
-    k_heavy<<<152 * 4, kEnumThreads, 0, st>>>(cfg, total_chunks);
+    switch (cfg.d) {
+        case 1: k_heavy<1><<<152 * 4, kEnumThreads, 0, st>>>(cfg, total_chunks); break;
+        case 2: k_heavy<2><<<152 * 4, kEnumThreads, 0, st>>>(cfg, total_chunks); break;
+        case 3: k_heavy<3><<<152 * 4, kEnumThreads, 0, st>>>(cfg, total_chunks); break;
+        case 4: k_heavy<4><<<152 * 4, kEnumThreads, 0, st>>>(cfg, total_chunks); break;
+        default: k_heavy<0><<<152 * 4, kEnumThreads, 0, st>>>(cfg, total_chunks); break;
+    }
 }
 
 void launch_allpairs(const DevCfg& cfg, const uint32_t* X, const double* w, const float* sv,
@@ -673,7 +773,13 @@ void launch_allpairs(const DevCfg& cfg, const uint32_t* X, const double* w, cons
     unsigned long long ntri = (unsigned long long)ntile * (ntile + 1) / 2;
     unsigned int grid = ntri < 152ull * 8 ? (unsigned int)ntri : 152 * 8;
     ++g_launches;
-    k_allpairs<<<grid, 256, 0, st>>>(cfg, V, ntile);
+    switch (cfg.d) {
+        case 1: k_allpairs<1><<<grid, 256, 0, st>>>(cfg, V, ntile); break;
+        case 2: k_allpairs<2><<<grid, 256, 0, st>>>(cfg, V, ntile); break;
+        case 3: k_allpairs<3><<<grid, 256, 0, st>>>(cfg, V, ntile); break;
+        case 4: k_allpairs<4><<<grid, 256, 0, st>>>(cfg, V, ntile); break;
+        default: k_allpairs<0><<<grid, 256, 0, st>>>(cfg, V, ntile); break;
+    }
 }
 
 }  // namespace gg

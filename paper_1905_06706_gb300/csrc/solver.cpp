@@ -31,10 +31,24 @@ void DegreeModel::set_top(std::vector<double> top, double fetched_above) {
     if (!top_.empty()) wmax_ = std::max(wmax_, top_[0]);
     pre_w_.assign(top_.size() + 1, 0.0);
     pre_wt_.assign(top_.size() + 1, 0.0);
+    wt_.assign(top_.size(), 0.0);
     for (size_t a = 0; a < top_.size(); ++a) {
+        wt_[a] = T_ > 0.0 ? power(top_[a]) : 0.0;
         pre_w_[a + 1] = pre_w_[a] + top_[a];
-        pre_wt_[a + 1] = pre_wt_[a] + (T_ > 0.0 ? std::pow(top_[a], 1.0 / T_) : 0.0);
+        pre_wt_[a + 1] = pre_wt_[a] + wt_[a];
     }
+    WT_ = T_ > 0.0 ? power(W_) : 1.0;
+}
+
+// x^(1/T): repeated products when 1/T is a small integer.
+double DegreeModel::power(double x) const {
+    const double e = 1.0 / T_;
+    if (e == std::floor(e) && e <= 16.0) {
+        double r = x;
+        for (int q = 1; q < (int)e; ++q) r *= x;
+        return r;
+    }
+    return std::pow(x, e);
 }
 
 double DegreeModel::qstar(double c) const {
@@ -62,7 +76,15 @@ double DegreeModel::f(double c) const {
     }
     const double qs = qstar(c);
     double err = 0.0;
-    size_t k = top_.size();
+    // partners of the heaviest vertex: the prefix of weights above qs W / w_max
+    // (binary search); for lighter vertices the prefix only shrinks
+    size_t k = 0;
+    if (!top_.empty()) {
+        const double lim0 = qs * W_ / top_[0];
+        k = (size_t)(std::upper_bound(top_.begin(), top_.end(), lim0,
+                                      [](double x, double y) { return x > y; }) -
+                     top_.begin());
+    }
     for (size_t a = 0; a < top_.size(); ++a) {
         const double wu = top_[a];
         const double lim = qs * W_ / wu;
@@ -72,14 +94,14 @@ double DegreeModel::f(double c) const {
         if (a < k) {
             cnt -= 1.0;
             sw -= wu;
-            if (T > 0.0) swt -= std::pow(wu, 1.0 / T);
+            if (T > 0.0) swt -= wt_[a];
         }
         if (cnt <= 0.0) continue;
         double s;
         if (T == 0.0)
             s = a1 * (wu / W_) * sw;
         else
-            s = a1 * (wu / W_) * sw - a2 * std::pow(wu / W_, 1.0 / T) * swt;
+            s = a1 * (wu / W_) * sw - a2 * (wt_[a] / WT_) * swt;
         err += s - cnt;
     }
     return (main_term - err) / (double)n_;
@@ -91,21 +113,50 @@ double DegreeModel::solve(double target, const std::function<void(double)>& fetc
         if (need < have_thr_) fetch(0.5 * need);
         return f(c);
     };
-    double lo = 1.0, hi = 1.0;
-    if (eval(1.0) < target) {
+    // start from the c at which the leading term of f alone reaches the target
+    // (c^T 2^d S1 / ((1 - T) n) = target, or 2^d c^d S1 / n = target at T = 0);
+    // the other terms only lower f, so the root lies near or above it
+    double c0;
+    if (T_ == 0.0)
+        c0 = std::pow(target * (double)n_ / (std::ldexp(1.0, d_) * S1_), 1.0 / d_);
+    else
+        c0 = std::pow(target * (double)n_ * (1.0 - T_) / (std::ldexp(1.0, d_) * S1_), 1.0 / T_);
+    if (!(c0 > 1e-300 && c0 < 1e300)) c0 = 1.0;
+    double lo = c0, hi = c0;
+    if (eval(c0) < target) {
         while (eval(hi) < target && hi < 1e300) hi *= 2.0;
         lo = hi / 2.0;
     } else {
         while (eval(lo) >= target && lo > 1e-300) lo /= 2.0;
         hi = lo * 2.0;
     }
+    // Illinois variant of regula falsi on log c: the bracket [lo, hi] with
+    // f(lo) < target <= f(hi) shrinks superlinearly; bisection steps guard it
+    double flo = eval(lo) - target, fhi = eval(hi) - target;
+    int side = 0;
     for (int it = 0; it < 200 && hi - lo > 1e-13 * hi; ++it) {
-        double mid = std::sqrt(lo * hi);
+        double mid;
+        const double a = std::log(lo), b = std::log(hi);
+        if (it % 8 == 7 || !(fhi > flo)) {
+            mid = std::sqrt(lo * hi);
+        } else {
+            mid = std::exp(b - fhi * (b - a) / (fhi - flo));
+        }
+        if (!(mid > lo && mid < hi)) mid = std::sqrt(lo * hi);
         if (!(mid > lo && mid < hi)) mid = 0.5 * (lo + hi);
-        if (eval(mid) < target)
+        const double fm = eval(mid) - target;
+        if (fm < 0.0) {
             lo = mid;
-        else
+            flo = fm;
+            if (side == -1) fhi *= 0.5;
+            side = -1;
+        } else {
             hi = mid;
+            fhi = fm;
+            if (side == 1) flo *= 0.5;
+            side = 1;
+        }
+        if (std::fabs(fm) <= 1e-14 * target) return mid;
     }
     return 0.5 * (lo + hi);
 }

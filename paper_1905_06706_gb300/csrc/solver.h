@@ -22,10 +22,11 @@ class DegreeModel {
 
    private:
     double qstar(double c) const;
+    double power(double x) const;
     int64_t n_;
     int d_;
-    double T_, W_, S1_, S2_, wmax_, have_thr_;
-    std::vector<double> top_, pre_w_, pre_wt_;
+    double T_, W_, S1_, S2_, wmax_, have_thr_, WT_ = 1.0;
+    std::vector<double> top_, pre_w_, pre_wt_, wt_;
 };
 
 }  // namespace gg
