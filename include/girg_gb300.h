@@ -159,8 +159,9 @@ int hrg_points(int64_t n, double alpha, double R, uint64_t seed, double* d_r, ui
 int girg_expected_avg_degree(const girg_params* params, double* avg_deg, void* stream);
 
 /* Counters of the last generate call on this host thread: [0] type-I pairs tested,
- * [1] coins drawn, [2] FP64 rechecks, [3] type-II items, [4] jump draws,
- * [5] type-II candidates, [6] rows, [7] type-I items, [8] heavy type-II chunks,
+ * [1] coins drawn, [2] FP64 rechecks, [3] type-II items (non-empty cell pairs),
+ * [4] jump draws, [5] type-II candidates, [6] rows, [7] type-I items, [8] chunks of
+ * multi-chunk type-II streams,
  * [9] edges, [10] kernel launches, [11] vertex references of the type-I items
  * (sum of both side lengths), [12] type-I edges.  Copies min(len, 13) values; returns
  * the number copied. */
@@ -168,7 +169,7 @@ int girg_last_stats(int64_t* out, int32_t len);
 
 /* Milliseconds spent in each phase of the last call on this host thread
  * (CUDA events): [0] points+reductions, [1] tables/host, [2] keys+sort+gather,
- * [3] enumeration + type II, [4] type I, [5] heavy type II, [6] total; host wall
+ * [3] cell-pair enumeration, [4] type I, [5] type-II streams, [6] total; host wall
  * clock: [7] reduction readback, [8] search for c, [9] table build.  Copies
  * min(len, 10) values; returns the number copied. */
 int girg_last_phase_ms(float* out, int32_t len);

@@ -304,6 +304,8 @@ def girg_cellpairs(X, w, w_min, W, T, c, seed, cap=None, want_items=False, skip_
             n, d, _ptr(X), _ptr(w), w_min, W, T, c, seed, _ptr(e), cap, _ptr(stats),
             _ptr(order), _ptr(itab), _ptr(wtab), _ptr(items) if want_items else None,
             icap if want_items else 0, _ptr(nitems), 1 if skip_sampling else 0, level_cap)
+        if m < 0:
+            raise RuntimeError("a type-II stream needs more than 2^32 chunks")
         if want_items and nitems[0] > icap:
             items_cap = int(nitems[0])
             continue
@@ -334,6 +336,8 @@ def hrg_cellpairs(X, r, R, T, seed, cap=None, want_items=False, skip_sampling=Fa
             n, _ptr(X), _ptr(r), R, T, seed, _ptr(e), cap, _ptr(stats), _ptr(order),
             _ptr(itab), _ptr(wtab), _ptr(items) if want_items else None,
             icap if want_items else 0, _ptr(nitems), 1 if skip_sampling else 0, level_cap)
+        if m < 0:
+            raise RuntimeError("a type-II stream needs more than 2^32 chunks")
         if want_items and nitems[0] > icap:
             items_cap = int(nitems[0])
             continue

@@ -48,12 +48,13 @@
  *   HRG radius of vertex v    = acosh(1 + U (cosh(alpha R) - 1)) / alpha,
  *                               U from ctr (v_lo, v_hi, TAG_RADIUS, 0)
  *   type-I coin of pair u<v   = U from words 0,1 of ctr (u, v, TAG_PAIR, 0)
- *   type-II draw t, one chunk = ctr (A, B, l|i<<5|j<<11|TAG_LIGHT<<17, t) (items whose
- *                               index space fits one chunk)
- *   type-II item key          = words 0,1 of ctr (A, B, l|i<<5|j<<11|TAG_ITEM<<17, 0)
- *   type-II draw t of chunk h = Philox with the item key, ctr (h_lo, h_hi, t, TAG_DRAW)
- *                               (items of several chunks);
- *   in both cases words 0,1 -> jump uniform, words 2,3 -> acceptance uniform
+ *   type-II streams           = for a cell A of bucket i at level l, bucket j and gap g,
+ *                               one geometric-jump stream over V_i^A x (the concatenation
+ *                               of V_j^B over its distant partner cells B with gap g, in
+ *                               increasing rank of B, see t2_rank); chunks of 2^k
+ *                               indices, 2^k pbar in [4, 8), k in [3, 31]
+ *   type-II draw t of chunk h = ctr (A, l|i<<5|j<<11|(g-1)<<17|TAG_JUMP<<18, h, t):
+ *                               words 0,1 -> jump uniform, words 2,3 -> acceptance
  */
 #include <math.h>
 #include <stdint.h>
@@ -64,9 +65,7 @@
 #define TAG_POS 0x504F5349u
 #define TAG_RADIUS 0x52414449u
 #define TAG_PAIR 0x50414952u
-#define TAG_ITEM 0x4954u
-#define TAG_LIGHT 0x4C54u
-#define TAG_DRAW 0x44524157u
+#define TAG_JUMP 0x2A4Du /* 14 bits; sets bit 31 of the second counter word */
 
 #define MAXL 64 /* weight layers */
 #define MAXD 8  /* dimensions */
@@ -611,15 +610,23 @@ static int level_for_kappa(double kappa, int cap) {
 }
 
 /* Chunk length exponent for geometric jumps under bound pbar: 2^k pbar in
- * [64, 128) when not clamped to [6, 62]. */
+ * [4, 8) when not clamped to [3, 31]. */
 int orc_chunk_log(double pbar) {
     int e;
     frexp(pbar, &e);
-    int k = 7 - e;
-    if (k < 6) k = 6;
-    if (k > 62) k = 62;
+    int k = 3 - e;
+    if (k < 3) k = 3;
+    if (k > 31) k = 31;
     return k;
 }
+
+/* A type-II item (cell pair, bucket pair) awaiting its stream: V_i^A x V_j^B at
+ * level l with gap g; rank orders B among the partners of A (t2_rank). */
+struct t2rec {
+    uint32_t A, B;
+    uint8_t l, i, j, g;
+    uint32_t rank;
+};
 
 typedef struct {
     int model; /* 0 GIRG, 1 HRG */
@@ -655,6 +662,10 @@ typedef struct {
     int64_t stats[8];
     /* visited cell pairs per level: neighbours, distant, and (A, A) pairs */
     int64_t lvl_nb[33], lvl_far[33], lvl_self[33];
+    /* type-II items collected by the recursion, sampled per stream afterwards */
+    struct t2rec* t2;
+    int64_t n_t2, cap_t2;
+    int64_t error;
     /* optional item log: 12 int64 per item */
     int64_t* items;
     int64_t items_cap;
@@ -824,10 +835,29 @@ static void type1_item(cp_ctx* C, int l, uint64_t A, uint64_t B, int i, int j) {
     }
 }
 
-/* Type II (Algorithm 1, lines 5-6): geometric jumps with the bound pbar over
- * the index space idx = a |V_j^B| + b of V_i^A x V_j^B, cut into chunks of
- * 2^k indices with their own Philox streams; a candidate is accepted with
- * probability p_uv / pbar, as U' pbar < p_uv. */
+/* Rank of a distant cell B among the partners of A at level l (>= 2): B is a
+ * child of a neighbour P of parent(A); with e_k in {-1, 0, 1} the offset of P
+ * from parent(A) in dimension k (on a level of 2 cells per dimension the other
+ * cell counts as +1) and kid_k the lowest coordinate bit of B,
+ * rank = (sum_k (e_k + 1) 3^(d-1-k)) 2^d + sum_k kid_k 2^(d-1-k). */
+static uint32_t t2_rank(uint64_t A, uint64_t B, int d, int l) {
+    uint32_t pa[MAXD], pb[MAXD], cb[MAXD];
+    morton_decode(A >> d, d, l - 1, pa);
+    morton_decode(B >> d, d, l - 1, pb);
+    morton_decode(B, d, l, cb);
+    uint32_t side = 1u << (l - 1);
+    uint32_t eidx = 0, kids = 0;
+    for (int k = 0; k < d; k++) {
+        uint32_t diff = (pb[k] - pa[k]) & (side - 1); /* 0, 1 or side - 1 */
+        int e = diff == 0 ? 0 : (diff == 1 ? 1 : -1);
+        eidx = eidx * 3 + (uint32_t)(e + 1);
+        kids = (kids << 1) | (cb[k] & 1u);
+    }
+    return (eidx << d) | kids;
+}
+
+/* Type II (Algorithm 1, lines 5-6): record the item; the candidates are chosen
+ * later by geometric jumps per stream (sample_streams). */
 static void type2_item(cp_ctx* C, int l, uint64_t A, uint64_t B, int i, int j) {
     int64_t alo, ahi, blo, bhi;
     vrange(C, i, A, l, &alo, &ahi);
@@ -838,30 +868,68 @@ static void type2_item(cp_ctx* C, int l, uint64_t A, uint64_t B, int i, int j) {
     C->stats[1]++;
     log_item(C, 2, l, A, B, i, j, alo, ahi, blo, bhi, 0, pbar);
     if (C->skip_sampling) return;
-    uint64_t na = (uint64_t)(ahi - alo), nb = (uint64_t)(bhi - blo);
-    uint64_t total = na * nb;
+    if (C->n_t2 == C->cap_t2) {
+        C->cap_t2 = C->cap_t2 ? 2 * C->cap_t2 : 1 << 16;
+        C->t2 = realloc(C->t2, sizeof(struct t2rec) * (size_t)C->cap_t2);
+    }
+    struct t2rec* r = &C->t2[C->n_t2++];
+    r->A = (uint32_t)A;
+    r->B = (uint32_t)B;
+    r->l = (uint8_t)l;
+    r->i = (uint8_t)i;
+    r->j = (uint8_t)j;
+    r->g = (uint8_t)g;
+    r->rank = t2_rank(A, B, C->d, l);
+}
+
+static int cmp_t2(const void* a, const void* b) {
+    const struct t2rec* x = a;
+    const struct t2rec* y = b;
+    if (x->l != y->l) return x->l < y->l ? -1 : 1;
+    if (x->i != y->i) return x->i < y->i ? -1 : 1;
+    if (x->j != y->j) return x->j < y->j ? -1 : 1;
+    if (x->A != y->A) return x->A < y->A ? -1 : 1;
+    if (x->g != y->g) return x->g < y->g ? -1 : 1;
+    if (x->rank != y->rank) return x->rank < y->rank ? -1 : 1;
+    return 0;
+}
+
+/* Geometric jumps (Sec. 3.2) with the bound pbar over the index space
+ * idx = a S + b of V_i^A x (V_j^B1 ++ V_j^B2 ++ ...), S the total size of the
+ * stream's partner sets, cut into chunks of 2^k indices; a candidate is
+ * accepted with probability p_uv / pbar, as U' pbar < p_uv. */
+static void sample_stream(cp_ctx* C, const struct t2rec* m, int64_t nm) {
+    int l = m[0].l, i = m[0].i, j = m[0].j;
+    uint32_t g = m[0].g;
+    uint64_t A = m[0].A;
+    int64_t alo, ahi;
+    vrange(C, i, A, l, &alo, &ahi);
+    int64_t* blo = malloc(sizeof(int64_t) * (size_t)nm);
+    uint64_t* pre = malloc(sizeof(uint64_t) * (size_t)(nm + 1));
+    pre[0] = 0;
+    for (int64_t q = 0; q < nm; q++) {
+        int64_t lo, hi;
+        vrange(C, j, m[q].B, l, &lo, &hi);
+        blo[q] = lo;
+        pre[q + 1] = pre[q] + (uint64_t)(hi - lo);
+    }
+    uint64_t na = (uint64_t)(ahi - alo), S = pre[nm];
+    uint64_t total = na * S;
+    double pbar = type2_bound(C, i, j, l, g);
     int k = orc_chunk_log(pbar);
     uint64_t chunk = (uint64_t)1 << k;
     uint64_t nchunks = (total + chunk - 1) >> k;
+    if (nchunks > 0xffffffffULL) C->error = 1;
     double Lb = pbar < 1.0 ? orc_det_log1p(-pbar) : 0.0;
-    uint32_t pack = (uint32_t)l | ((uint32_t)i << 5) | ((uint32_t)j << 11);
-    uint32_t ko[4];
-    philox_seed(C->seed, (uint32_t)A, (uint32_t)B, pack | (TAG_ITEM << 17), 0, ko);
-    uint32_t ikey[2] = {ko[0], ko[1]};
-    for (uint64_t h = 0; h < nchunks; h++) {
+    uint32_t pack = (uint32_t)l | ((uint32_t)i << 5) | ((uint32_t)j << 11) | ((g - 1) << 17) |
+                    (TAG_JUMP << 18);
+    for (uint64_t h = 0; h < nchunks && h <= 0xffffffffULL; h++) {
         uint64_t start = h << k;
         uint64_t len = total - start < chunk ? total - start : chunk;
         int64_t s = -1; /* offset of the last candidate within the chunk */
-        uint32_t t = 0;
-        for (;;) {
+        for (uint32_t t = 0;; t++) {
             uint32_t o[4];
-            if (nchunks == 1) { /* one chunk: draw straight from the seed's streams */
-                philox_seed(C->seed, (uint32_t)A, (uint32_t)B, pack | (TAG_LIGHT << 17), t, o);
-            } else {
-                uint32_t ctr[4] = {(uint32_t)h, (uint32_t)(h >> 32), t, TAG_DRAW};
-                orc_philox(ctr, ikey, o);
-            }
-            t++;
+            philox_seed(C->seed, (uint32_t)A, pack, (uint32_t)h, t, o);
             C->stats[2]++;
             /* X = floor(ln U / ln(1 - pbar)); stop when the jump leaves the chunk */
             uint64_t remaining = len - (uint64_t)(s + 1);
@@ -874,14 +942,36 @@ static void type2_item(cp_ctx* C, int l, uint64_t A, uint64_t B, int i, int j) {
             if (X >= remaining) break;
             s = s + 1 + (int64_t)X;
             uint64_t idx = start + (uint64_t)s;
-            int64_t u = C->order[alo + (int64_t)(idx / nb)];
-            int64_t v = C->order[blo + (int64_t)(idx % nb)];
+            uint64_t ib = idx % S;
+            int64_t q = 0; /* partner set holding position ib */
+            while (pre[q + 1] <= ib) q++;
+            int64_t u = C->order[alo + (int64_t)(idx / S)];
+            int64_t v = C->order[blo[q] + (int64_t)(ib - pre[q])];
             C->stats[3]++;
             if (orc_uniform(o[2], o[3]) * pbar < pair_p(C, u, v)) {
                 emit(C->edges, C->cap, &C->m, (uint32_t)u, (uint32_t)v);
                 C->stats[7]++;
             }
         }
+    }
+    free(blo);
+    free(pre);
+}
+
+/* Group the recorded type-II items into streams (same l, i, j, A and gap g),
+ * partners in increasing rank, and sample each stream. */
+static void sample_streams(cp_ctx* C) {
+    if (C->n_t2 == 0) return;
+    qsort(C->t2, (size_t)C->n_t2, sizeof(struct t2rec), cmp_t2);
+    int64_t q0 = 0;
+    while (q0 < C->n_t2) {
+        int64_t q1 = q0 + 1;
+        while (q1 < C->n_t2 && C->t2[q1].l == C->t2[q0].l && C->t2[q1].i == C->t2[q0].i &&
+               C->t2[q1].j == C->t2[q0].j && C->t2[q1].A == C->t2[q0].A &&
+               C->t2[q1].g == C->t2[q0].g)
+            q1++;
+        sample_stream(C, C->t2 + q0, q1 - q0);
+        q0 = q1;
     }
 }
 
@@ -1001,6 +1091,7 @@ static int cp_prepare(cp_ctx* C, double w_min, int lcap_override) {
 }
 
 static void cp_free(cp_ctx* C) {
+    free(C->t2);
     free(C->order);
     for (int i = 0; i < MAXL; i++) free(C->offs[i]);
     free(C->E);
@@ -1051,6 +1142,7 @@ int64_t orc_girg_cellpairs(int64_t n, int d, const uint32_t* X, const double* w,
     C.skip_sampling = skip_sampling;
     cp_prepare(&C, w_min, lcap_override);
     if (n > 0) recur(&C, 0, 0, 0);
+    sample_streams(&C);
     if (stats) {
         memcpy(stats, C.stats, sizeof(C.stats));
         memcpy(stats + 8, C.lvl_nb, sizeof(C.lvl_nb));
@@ -1060,7 +1152,7 @@ int64_t orc_girg_cellpairs(int64_t n, int d, const uint32_t* X, const double* w,
     if (order_out) memcpy(order_out, C.order, sizeof(int64_t) * n);
     if (n_items) *n_items = C.n_items;
     export_tables(&C, itab, wtab);
-    int64_t m = C.m;
+    int64_t m = C.error ? -1 : C.m;
     cp_free(&C);
     return m;
 }
@@ -1097,6 +1189,7 @@ int64_t orc_hrg_cellpairs(int64_t n, const uint32_t* X, const double* r, double 
     C.skip_sampling = skip_sampling;
     cp_prepare(&C, 1.0, lcap_override);
     if (n > 0) recur(&C, 0, 0, 0);
+    sample_streams(&C);
     if (stats) {
         memcpy(stats, C.stats, sizeof(C.stats));
         memcpy(stats + 8, C.lvl_nb, sizeof(C.lvl_nb));
@@ -1106,7 +1199,7 @@ int64_t orc_hrg_cellpairs(int64_t n, const uint32_t* X, const double* r, double 
     if (order_out) memcpy(order_out, C.order, sizeof(int64_t) * n);
     if (n_items) *n_items = C.n_items;
     export_tables(&C, itab, wtab);
-    int64_t m = C.m;
+    int64_t m = C.error ? -1 : C.m;
     cp_free(&C);
     free(w);
     return m;

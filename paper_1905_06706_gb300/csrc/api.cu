@@ -385,11 +385,16 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     unsigned long long* stats = S.get<unsigned long long>(kNumStats + 2);  // + edge count + chunks
     CK(cudaMemsetAsync(counters, 0, 16 * sizeof(unsigned int), st));
     CK(cudaMemsetAsync(stats, 0, (kNumStats + 2) * sizeof(unsigned long long), st));
-    uint64_t t1_cap = (uint64_t)n * (1 + (uint64_t)(0.75 * n3)) + 65536;
-    if (t1_cap > 0xfffffff0ull) t1_cap = 0xfffffff0ull;
-    uint64_t heavy_cap = (uint64_t)n / 16 + 4096;
+    // work lists, sized from typical counts per vertex; the enumeration only writes
+    // work (no edges), so an overflow is repaired by resizing and running it again
+    auto clamp_cap = [](uint64_t c) { return c > 0xfffffff0ull ? 0xfffffff0ull : c; };
+    uint64_t t1_cap = clamp_cap((uint64_t)n * (1 + (uint64_t)(0.75 * n3)) + 65536);
+    uint64_t stream_cap = tzero ? 1024 : clamp_cap((uint64_t)n * (2 + 2 * (uint64_t)d) + 65536);
+    uint64_t seg_cap = tzero ? 1024 : clamp_cap((uint64_t)n * (2 + (uint64_t)(1.5 * n3)) + 65536);
     T1Item* t1 = S.get<T1Item>(t1_cap);
-    HeavyItem* heavy = S.get<HeavyItem>(heavy_cap);
+    Stream* streams = S.get<Stream>(stream_cap);
+    Seg* segs = S.get<Seg>(seg_cap);
+    HeavyItem* heavy = S.get<HeavyItem>(stream_cap);
 
     DevCfg cfg;
     memset(&cfg, 0, sizeof(cfg));
@@ -405,7 +410,6 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     cfg.n6 = n6;
     cfg.seed_lo = (uint32_t)P.seed;
     cfg.seed_hi = (uint32_t)(P.seed >> 32);
-    cfg.mode = kModeT1 | kModeT2Light | kModeT2Heavy;
     cfg.W = P.W;
     cfg.c = P.c;
     cfg.T = P.T;
@@ -455,51 +459,65 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     cfg.t1 = t1;
     cfg.t1_count = counters + 1;
     cfg.t1_cap = (uint32_t)t1_cap;
+    cfg.streams = streams;
+    cfg.stream_count = counters + 2;
+    cfg.stream_cap = (uint32_t)stream_cap;
+    cfg.segs = segs;
+    cfg.seg_count = counters + 3;
+    cfg.seg_cap = (uint32_t)seg_cap;
     cfg.heavy = heavy;
-    cfg.heavy_count = counters + 2;
-    cfg.heavy_cap = (uint32_t)heavy_cap;
-    cfg.work_counter = counters + 4;
+    cfg.heavy_count = counters + 4;
+    cfg.heavy_cap = (uint32_t)stream_cap;
+    cfg.error = counters + 5;
+    cfg.work_counter = counters + 8;
 
     launch_rows(cfg, rows, counters + 0, (unsigned)row_cap, st);
     launch_enumerate(cfg, st);
-    unsigned int hc[3];
-    CK(cudaMemcpyAsync(hc, counters, 3 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (hc[1] > cfg.t1_cap || hc[2] > cfg.heavy_cap) {
-        uint32_t mode = 0;
+    for (int attempt = 0;; ++attempt) {
+        unsigned int hc[4];
+        CK(cudaMemcpyAsync(hc, counters, 4 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const bool over = hc[1] > cfg.t1_cap || hc[2] > cfg.stream_cap || hc[3] > cfg.seg_cap;
+        if (!over) break;
+        if (attempt > 0) throw Status{GIRG_E_INTERNAL};
         if (hc[1] > cfg.t1_cap) {
-            mode |= kModeT1;
-            cfg.t1 = S.get<T1Item>((size_t)hc[1] + 1024);
             cfg.t1_cap = hc[1] + 1024;
-            CK(cudaMemsetAsync(counters + 1, 0, sizeof(unsigned int), st));
-            CK(cudaMemsetAsync(stats + kStatT1Items, 0, sizeof(unsigned long long), st));
+            cfg.t1 = S.get<T1Item>(cfg.t1_cap);
         }
-        if (hc[2] > cfg.heavy_cap) {
-            mode |= kModeT2Heavy;
-            cfg.heavy = S.get<HeavyItem>((size_t)hc[2] + 1024);
-            cfg.heavy_cap = hc[2] + 1024;
-            CK(cudaMemsetAsync(counters + 2, 0, sizeof(unsigned int), st));
+        if (hc[2] > cfg.stream_cap) {
+            cfg.stream_cap = hc[2] + 1024;
+            cfg.streams = S.get<Stream>(cfg.stream_cap);
+            cfg.heavy_cap = cfg.stream_cap;
+            cfg.heavy = S.get<HeavyItem>(cfg.heavy_cap);
         }
-        CK(cudaMemsetAsync(counters + 4, 0, sizeof(unsigned int), st));
-        cfg.mode = mode;
+        if (hc[3] > cfg.seg_cap) {
+            cfg.seg_cap = hc[3] + 1024;
+            cfg.segs = S.get<Seg>(cfg.seg_cap);
+        }
+        CK(cudaMemsetAsync(counters + 1, 0, 3 * sizeof(unsigned int), st));  // t1, streams, segs
+        CK(cudaMemsetAsync(counters + 8, 0, sizeof(unsigned int), st));      // row counter
+        CK(cudaMemsetAsync(stats + kStatT1Items, 0, sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(stats + kStatT2Items, 0, sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(stats + kStatT1VertexRefs, 0, sizeof(unsigned long long), st));
         launch_enumerate(cfg, st);
-        cfg.mode = kModeT1 | kModeT2Light | kModeT2Heavy;
     }
-    tm.mark();  // enumeration + inline type II done
+    tm.mark();  // enumeration done
     launch_type1(cfg, st);
     tm.mark();  // type I done
     unsigned long long* total_chunks = stats + kNumStats + 1;
+    launch_streams(cfg, st);
     launch_heavy_scan(cfg, total_chunks, st);
     launch_heavy(cfg, total_chunks, st);
-    tm.mark();  // heavy type II done
+    tm.mark();  // type II done
     unsigned long long hs[kNumStats + 1];
     CK(cudaMemcpyAsync(hs, stats, (kNumStats + 1) * sizeof(unsigned long long),
                        cudaMemcpyDeviceToHost, st));
-    unsigned int rc;
-    CK(cudaMemcpyAsync(&rc, counters, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    unsigned int rc[6];
+    CK(cudaMemcpyAsync(rc, counters, 6 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
-    hs[kStatRows] = rc;
+    if (rc[5]) throw Status{GIRG_E_INTERNAL};
+    hs[kStatRows] = rc[0];
     hs[kStatEdges] = hs[kNumStats];
     for (int q = 0; q < kNumStats; ++q) g_stats[q] = (int64_t)hs[q];
     g_stats[kStatLaunches] = (int64_t)g_launches;

@@ -42,9 +42,7 @@ constexpr uint32_t kTagWeight = 0x57454947u;
 constexpr uint32_t kTagPos = 0x504F5349u;
 constexpr uint32_t kTagRadius = 0x52414449u;
 constexpr uint32_t kTagPair = 0x50414952u;
-constexpr uint32_t kTagItem = 0x4954u;
-constexpr uint32_t kTagLight = 0x4C54u;
-constexpr uint32_t kTagDraw = 0x44524157u;
+constexpr uint32_t kTagJump = 0x2A4Du;  // 14 bits at bit 18 of a stream's second counter word
 
 constexpr int kMaxLayers = 64;
 constexpr int kMaxDim = 8;
@@ -317,13 +315,13 @@ GG_HD int layer_of(double w, double w_min) {
 }
 
 // Chunk length exponent k of a geometric-jump stream under bound pbar:
-// 2^k pbar in [64, 128), k clamped to [6, 62].
+// 2^k pbar in [4, 8), k clamped to [3, 31].
 GG_HD int chunk_log(double pbar) {
     const int eb = (int)((double_to_bits(pbar) >> 52) & 0x7ff);
     const int e = eb - 1022;  // pbar = m 2^e, m in [0.5, 1) (pbar is normal here)
-    int k = 7 - e;
-    if (k < 6) k = 6;
-    if (k > 62) k = 62;
+    int k = 3 - e;
+    if (k < 3) k = 3;
+    if (k > 31) k = 31;
     return k;
 }
 

@@ -31,20 +31,35 @@ struct T1Item {
     uint32_t a_begin, a_len, b_begin, b_len;
 };
 
-// A type-II item whose index space spans several chunks.
-struct HeavyItem {
-    uint32_t a_begin, a_len, b_begin, b_len;
-    uint32_t A, B;
-    uint32_t pack;  // l | i << 5 | j << 11
+// A type-II stream: geometric jumps over V_i^A x (V_j^B1 ++ V_j^B2 ++ ...), the
+// distant partner cells B of A with one gap g, in increasing rank; the partner
+// sets are seg_cnt entries of the segment pool from seg_off.
+struct Stream {
+    uint32_t A;
+    uint32_t pack;  // l | i << 5 | j << 11 | (g - 1) << 17 | kTagJump << 18
+    uint32_t a_begin, a_len;
+    uint32_t seg_off, seg_cnt;
+    uint32_t S;     // total size of the partner sets
     uint32_t tii;   // index of its TwoEntry
-    uint64_t chunk_prefix;  // exclusive prefix of chunk counts (filled by a scan)
+};
+
+// One partner set of a stream: its first sorted position and the number of
+// positions of the stream's earlier partner sets.
+struct Seg {
+    uint32_t b_begin, pre;
+};
+
+// A stream of several chunks.
+struct HeavyItem {
+    uint32_t stream;
+    uint32_t pad;
+    uint64_t chunk_prefix;  // chunk count, then its exclusive prefix (filled by a scan)
 };
 
 enum : int { kStatT1Pairs = 0, kStatCoins, kStatRecheck, kStatT2Items, kStatDraws,
              kStatCands, kStatRows, kStatT1Items, kStatHeavyChunks, kStatEdges,
              kStatLaunches, kStatT1VertexRefs, kStatT1Edges, kNumStats };
 
-enum : uint32_t { kModeT1 = 1u, kModeT2Light = 2u, kModeT2Heavy = 4u };
 
 struct DevCfg {
     int32_t n, d, L, model, precision, tzero, m_int, lcap;
@@ -88,9 +103,16 @@ struct DevCfg {
     T1Item* t1;
     unsigned int* t1_count;
     uint32_t t1_cap;
+    Stream* streams;
+    unsigned int* stream_count;
+    uint32_t stream_cap;
+    Seg* segs;
+    unsigned int* seg_count;
+    uint32_t seg_cap;
     HeavyItem* heavy;
     unsigned int* heavy_count;
     uint32_t heavy_cap;
+    unsigned int* error;         // set when a stream needs 2^32 chunks or more
     unsigned int* work_counter;  // dynamic scheduling counters [4]
 };
 

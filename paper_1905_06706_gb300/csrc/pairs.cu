@@ -204,16 +204,18 @@ __device__ bool accept_t2(const DevCfg& cfg, const View& V, uint32_t pu, uint32_
     return t2_exact(cfg, V, pu, pv, D, lo, hi, e.pbar);
 }
 
-// One chunk of geometric jumps over [start, start + len) of the a x b index space
-// of a type-II item (Sec. 3.2).  Draw t of the chunk comes from `draw(t)`.
-template <int DIM, class Draw>
-__device__ void jump_chunk(const DevCfg& cfg, const View& V, WarpEdges& we, const TwoEntry& e,
-                           uint32_t a_begin, uint32_t b_begin, uint32_t b_len,
-                           unsigned long long start, unsigned long long len, Draw draw,
-                           Counters& C) {
+// One chunk of a type-II stream (Sec. 3.2): geometric jumps under the bound pbar
+// over indices [start, start + len) of the stream's index space a S, with
+// candidate idx -> (a = idx / S, b = idx mod S), b located in the partner set
+// whose positions hold it; accepted as U' pbar < p_uv.
+template <int DIM>
+__device__ void stream_chunk(const DevCfg& cfg, const View& V, WarpEdges& we, const Stream& st,
+                             const TwoEntry& e, uint32_t h, unsigned long long start,
+                             unsigned long long len, Counters& C) {
+    const unsigned long long tot = (unsigned long long)st.a_len * st.S;
     long long s = -1;
     for (uint32_t t = 0;; ++t) {
-        const P4 o = draw(t);
+        const P4 o = philox(st.A, st.pack, h, t, cfg.seed_lo, cfg.seed_hi);
         ++C.draws;
         const unsigned long long rem = len - (unsigned long long)(s + 1);
         unsigned long long X = 0;
@@ -232,14 +234,21 @@ __device__ void jump_chunk(const DevCfg& cfg, const View& V, WarpEdges& we, cons
         ++C.cands;
         const unsigned long long idx = start + (unsigned long long)s;
         uint32_t ia, ib;
-        if (idx < (1ull << 32)) {
-            ia = (uint32_t)idx / b_len;
-            ib = (uint32_t)idx - ia * b_len;
+        if (tot <= 0xffffffffull) {
+            ia = (uint32_t)idx / st.S;
+            ib = (uint32_t)idx - ia * st.S;
         } else {
-            ia = (uint32_t)(idx / b_len);
-            ib = (uint32_t)(idx - (unsigned long long)ia * b_len);
+            ia = (uint32_t)(idx / st.S);
+            ib = (uint32_t)(idx - (unsigned long long)ia * st.S);
         }
-        const uint32_t pu = a_begin + ia, pv = b_begin + ib;
+        // last partner set with pre <= ib
+        uint32_t lo = 0, hi = st.seg_cnt;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (cfg.segs[st.seg_off + mid].pre <= ib) lo = mid; else hi = mid;
+        }
+        const Seg sg = cfg.segs[st.seg_off + lo];
+        const uint32_t pu = st.a_begin + ia, pv = sg.b_begin + (ib - sg.pre);
         if (accept_t2<DIM>(cfg, V, pu, pv, o.z, o.w, e, C))
             push_edge(cfg, we, vid(V, pu), vid(V, pv));
     }
@@ -351,21 +360,81 @@ __device__ __forceinline__ uint32_t dim_mask(int d, int k, int l) {
     return nb >= 32 ? pat : (pat & ((1u << nb) - 1u));
 }
 
+// A type-II combination c (< n2 6^d) of row cell A: the distant cell B of
+// A's parent-neighbour block with offset index c mod 6^d (Morton rank order), for
+// the bucket of entry c / 6^d.  Returns whether it is a non-empty partner set,
+// with its gap g and sorted range.
+template <int DIM>
+__device__ __forceinline__ bool t2_combo(const DevCfg& cfg, const RowClass& rc, int d, uint32_t n6,
+                                         int i, int l, uint32_t A, uint32_t PA, uint32_t c,
+                                         uint32_t* e_out, int* j_out, uint32_t* g_out,
+                                         uint32_t* b_lo, uint32_t* b_len) {
+    const uint32_t e = c / n6, off = c - e * n6;
+    const int j = cfg.jlist[rc.jbase + e];
+    *e_out = e;
+    *j_out = j;
+    const uint32_t kids = off & ((1u << d) - 1u);
+    uint32_t q = off >> d;
+    uint32_t P = 0, linf = 0;
+    bool ok = true;
+#pragma unroll
+    for (int k = (DIM ? DIM : kMaxDim) - 1; k >= 0; --k) {
+        if (DIM == 0 && k >= d) continue;
+        const int ek = (int)(q % 3u) - 1;
+        q /= 3u;
+        ok = ok && digit_ok(ek, l - 1);
+        P |= dil_add(PA, dim_mask(d, k, l - 1), 1u << (d - 1 - k), ek);
+        const int alpha = (int)((A >> (d - 1 - k)) & 1u);
+        const int kid = (int)((kids >> (d - 1 - k)) & 1u);
+        int diff = 2 * ek + kid - alpha;
+        diff = diff < 0 ? -diff : diff;
+        if (l == 2 && diff > 2) diff = 4 - diff;  // 4 cells per dimension
+        linf = (uint32_t)diff > linf ? (uint32_t)diff : linf;
+    }
+    if (!ok || linf <= 1) return false;  // repeated offset, or a neighbour of A
+    const uint32_t B = (P << d) | kids;
+    if (j == i && B <= A) return false;
+    *g_out = linf - 1;
+    *b_lo = vrange_lo(cfg, j, B, l, d);
+    *b_len = vrange_hi(cfg, j, B, l, d) - *b_lo;
+    return *b_len > 0;
+}
+
+// Segmented inclusive warp scan of (count, positions) for each gap, segments =
+// runs of lanes with the same entry id.
+__device__ __forceinline__ void seg_scan(uint32_t key, uint32_t& c1, uint32_t& c2, uint32_t& s1,
+                                         uint32_t& s2) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t ku = __shfl_up_sync(0xffffffffu, key, o);
+        const uint32_t a1 = __shfl_up_sync(0xffffffffu, c1, o);
+        const uint32_t a2 = __shfl_up_sync(0xffffffffu, c2, o);
+        const uint32_t b1 = __shfl_up_sync(0xffffffffu, s1, o);
+        const uint32_t b2 = __shfl_up_sync(0xffffffffu, s2, o);
+        if (lane >= o && ku == key) {
+            c1 += a1;
+            c2 += a2;
+            s1 += b1;
+            s2 += b2;
+        }
+    }
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
-    __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
-    __shared__ unsigned int s_en[kWarps];
+    __shared__ uint32_t s_cnt[kWarps][2 * kMaxLayers];  // members per (entry, gap)
+    __shared__ uint32_t s_sum[kWarps][2 * kMaxLayers];  // positions per (entry, gap)
+    __shared__ uint32_t s_off[kWarps][2 * kMaxLayers];  // first segment per (entry, gap)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_en[warp] = 0;
-    __syncwarp();
-    WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
-    const View V = sorted_view(cfg);
-    Counters C;
     const int d = DIM ? DIM : cfg.d;
     const uint32_t n3 = DIM == 1 ? 3u : DIM == 2 ? 9u : DIM == 3 ? 27u : DIM == 4 ? 81u : (uint32_t)cfg.n3;
     const uint32_t n6 = DIM == 1 ? 6u : DIM == 2 ? 36u : DIM == 3 ? 216u : DIM == 4 ? 1296u : (uint32_t)cfg.n6;
     const unsigned int nrows = *cfg.row_count < cfg.row_cap ? *cfg.row_count : cfg.row_cap;
-    unsigned long long t1_items_local = 0, t1_refs_local = 0;
+    uint32_t* cnt_w = s_cnt[warp];
+    uint32_t* sum_w = s_sum[warp];
+    uint32_t* off_w = s_off[warp];
+    unsigned long long t1_items_local = 0, t1_refs_local = 0, t2_items_local = 0;
     for (;;) {
         unsigned int r = 0;
         if (lane == 0) r = atomicAdd(&cfg.work_counter[0], 1u);
@@ -384,67 +453,140 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
         const uint32_t n2c = (uint32_t)rc.n2 * n6;
         const uint32_t total = n2c + (uint32_t)rc.n1 * n3;
         const uint32_t PA = A >> d;  // parent cell (level l - 1)
+        const uint32_t nkeys = 2u * rc.n2;
+        // ---- type II, pass 1: members and positions of every (entry, gap)
+        if (n2c) {
+            for (uint32_t k = lane; k < nkeys; k += 32) {
+                cnt_w[k] = 0;
+                sum_w[k] = 0;
+            }
+            __syncwarp();
+            for (uint32_t c0 = 0; c0 < n2c; c0 += 32) {
+                const uint32_t c = c0 + lane;
+                uint32_t e = 0xffffffffu, g = 0, b_lo = 0, b_len = 0;
+                int j = 0;
+                bool mem = false;
+                if (c < n2c) {
+                    mem = t2_combo<DIM>(cfg, rc, d, n6, i, l, A, PA, c, &e, &j, &g, &b_lo, &b_len);
+                }
+                uint32_t c1 = mem && g == 1, c2 = mem && g == 2;
+                uint32_t s1 = c1 ? b_len : 0u, s2 = c2 ? b_len : 0u;
+                seg_scan(e, c1, c2, s1, s2);
+                const uint32_t e_next = __shfl_down_sync(0xffffffffu, e, 1);
+                if (c < n2c && (lane == 31 || e_next != e)) {
+                    cnt_w[2 * e] += c1;
+                    cnt_w[2 * e + 1] += c2;
+                    sum_w[2 * e] += s1;
+                    sum_w[2 * e + 1] += s2;
+                }
+                __syncwarp();
+            }
+            // streams: one per (entry, gap) with members; their segments reserved
+            for (uint32_t k0 = 0; k0 < nkeys; k0 += 32) {
+                const uint32_t key = k0 + lane;
+                const uint32_t m = key < nkeys ? cnt_w[key] : 0u;
+                const uint32_t has = m > 0;
+                uint32_t im = m, is = has;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t a = __shfl_up_sync(0xffffffffu, im, o);
+                    const uint32_t b = __shfl_up_sync(0xffffffffu, is, o);
+                    if (lane >= o) {
+                        im += a;
+                        is += b;
+                    }
+                }
+                uint32_t seg_base = 0, st_base = 0;
+                if (lane == 31) {
+                    if (im) seg_base = atomicAdd(cfg.seg_count, im);
+                    if (is) st_base = atomicAdd(cfg.stream_count, is);
+                }
+                seg_base = __shfl_sync(0xffffffffu, seg_base, 31) + im - m;
+                st_base = __shfl_sync(0xffffffffu, st_base, 31) + is - has;
+                if (has) {
+                    off_w[key] = seg_base;
+                    t2_items_local += m;
+                    if (st_base < cfg.stream_cap) {
+                        const uint32_t e = key >> 1, g = (key & 1u) + 1u;
+                        const uint32_t j = cfg.jlist[rc.jbase + e];
+                        Stream st;
+                        st.A = A;
+                        st.pack = (uint32_t)l | ((uint32_t)i << 5) | (j << 11) | ((g - 1) << 17) |
+                                  (kTagJump << 18);
+                        st.a_begin = a_lo;
+                        st.a_len = a_len;
+                        st.seg_off = seg_base;
+                        st.seg_cnt = m;
+                        st.S = sum_w[key];
+                        st.tii = ((((uint32_t)i * cfg.L + j) * (cfg.lcap + 1) + l) << 1) + (g - 1);
+                        cfg.streams[st_base] = st;
+                    }
+                }
+            }
+            __syncwarp();
+            for (uint32_t k = lane; k < nkeys; k += 32) {
+                cnt_w[k] = 0;
+                sum_w[k] = 0;
+            }
+            __syncwarp();
+        }
+        // ---- pass 2: segments of the streams (type II) and items (type I)
         for (uint32_t c0 = 0; c0 < total; c0 += 32) {
             const uint32_t c = c0 + lane;
-            int kind = 0;  // 1: type-I item, 2: type-II item
-            int j = 0;
-            uint32_t B = 0, b_lo = 0, b_len = 0, g = 0;
-            if (c < total) {
-                bool ok = true;
-                if (c < n2c) {  // distant cell with a neighbouring parent
-                    const uint32_t e = c / n6, off = c - e * n6;
-                    j = cfg.jlist[rc.jbase + e];
-                    const uint32_t kids = off & ((1u << d) - 1u);
-                    uint32_t q = off >> d;
-                    uint32_t P = 0, linf = 0;
-#pragma unroll
-                    for (int k = (DIM ? DIM : kMaxDim) - 1; k >= 0; --k) {
-                        if (DIM == 0 && k >= d) continue;
-                        const int ek = (int)(q % 3u) - 1;
-                        q /= 3u;
-                        ok = ok && digit_ok(ek, l - 1);
-                        P |= dil_add(PA, dim_mask(d, k, l - 1), 1u << (d - 1 - k), ek);
-                        const int alpha = (int)((A >> (d - 1 - k)) & 1u);
-                        const int kid = (int)((kids >> (d - 1 - k)) & 1u);
-                        int diff = 2 * ek + kid - alpha;
-                        diff = diff < 0 ? -diff : diff;
-                        if (l == 2 && diff > 2) diff = 4 - diff;  // 4 cells per dimension
-                        linf = (uint32_t)diff > linf ? (uint32_t)diff : linf;
-                    }
-                    if (ok && linf <= 1) ok = false;  // a neighbour of A, not distant
-                    if (ok) {
-                        B = (P << d) | kids;
-                        if (j == i && B <= A) ok = false;
-                        g = linf - 1;
-                    }
-                    kind = 2;
-                } else {  // neighbour cell
-                    const uint32_t c1 = c - n2c;
-                    const uint32_t e = c1 / n3;
-                    uint32_t q = c1 - e * n3;
-                    j = cfg.jlist[rc.jbase + rc.n2 + e];
-                    uint32_t Bv = 0;
-#pragma unroll
-                    for (int k = (DIM ? DIM : kMaxDim) - 1; k >= 0; --k) {
-                        if (DIM == 0 && k >= d) continue;
-                        const int ek = (int)(q % 3u) - 1;
-                        q /= 3u;
-                        ok = ok && digit_ok(ek, l);
-                        Bv |= dil_add(A, dim_mask(d, k, l), 1u << (d - 1 - k), ek);
-                    }
-                    if (ok) {
-                        B = Bv;
-                        if (j == i && B < A) ok = false;
-                    }
-                    kind = 1;
+            if (c0 < n2c) {
+                uint32_t e = 0xffffffffu, g = 0, b_lo = 0, b_len = 0;
+                int j = 0;
+                bool mem = false;
+                if (c < n2c) {
+                    mem = t2_combo<DIM>(cfg, rc, d, n6, i, l, A, PA, c, &e, &j, &g, &b_lo, &b_len);
+                } else {
+                    e = 0xffffffffu;
                 }
-                if (ok) {
+                uint32_t c1 = mem && g == 1, c2 = mem && g == 2;
+                uint32_t s1 = c1 ? b_len : 0u, s2 = c2 ? b_len : 0u;
+                const uint32_t own_c = c1 + c2, own_s = s1 + s2;
+                seg_scan(e, c1, c2, s1, s2);
+                if (mem) {
+                    const uint32_t key = 2 * e + (g - 1);
+                    const uint32_t pos = off_w[key] + cnt_w[key] + (g == 1 ? c1 : c2) - own_c;
+                    const uint32_t pre = sum_w[key] + (g == 1 ? s1 : s2) - own_s;
+                    if (pos < cfg.seg_cap) cfg.segs[pos] = Seg{b_lo, pre};
+                }
+                __syncwarp();
+                const uint32_t e_next = __shfl_down_sync(0xffffffffu, e, 1);
+                if (c < n2c && (lane == 31 || e_next != e)) {
+                    cnt_w[2 * e] += c1;
+                    cnt_w[2 * e + 1] += c2;
+                    sum_w[2 * e] += s1;
+                    sum_w[2 * e + 1] += s2;
+                }
+                __syncwarp();
+            }
+            // type-I items: split, then append with one atomic per warp
+            int kind = 0;
+            uint32_t B = 0, b_lo = 0, b_len = 0;
+            int j = 0;
+            if (c >= n2c && c < total) {
+                const uint32_t c1 = c - n2c;
+                const uint32_t e = c1 / n3;
+                uint32_t q = c1 - e * n3;
+                j = cfg.jlist[rc.jbase + rc.n2 + e];
+                uint32_t Bv = 0;
+                bool ok = true;
+#pragma unroll
+                for (int k = (DIM ? DIM : kMaxDim) - 1; k >= 0; --k) {
+                    if (DIM == 0 && k >= d) continue;
+                    const int ek = (int)(q % 3u) - 1;
+                    q /= 3u;
+                    ok = ok && digit_ok(ek, l);
+                    Bv |= dil_add(A, dim_mask(d, k, l), 1u << (d - 1 - k), ek);
+                }
+                if (ok && !(j == i && Bv < A)) {
+                    B = Bv;
                     b_lo = vrange_lo(cfg, j, B, l, d);
                     b_len = vrange_hi(cfg, j, B, l, d) - b_lo;
+                    if (b_len > 0) kind = 1;
                 }
-                if (!ok || b_len == 0) kind = 0;
             }
-            // ---- type-I items: split, then append with one atomic per warp
             uint32_t nsub = 0, ac = 0, bc = 0, na = 0;
             if (kind == 1) {
                 bc = b_len < kSplitB ? b_len : kSplitB;
@@ -461,7 +603,7 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
             unsigned int tbase = 0;
             if (lane == 31 && incl) tbase = atomicAdd(cfg.t1_count, incl);
             tbase = __shfl_sync(0xffffffffu, tbase, 31) + incl - nsub;
-            if (kind == 1 && (cfg.mode & kModeT1)) {
+            if (kind == 1) {
                 const uint32_t tri = (B == A && j == i) ? 0x80000000u : 0u;
                 uint32_t q = 0;
                 for (uint32_t ya = 0; ya < a_len; ya += ac) {
@@ -482,50 +624,55 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
                 t1_refs_local += (unsigned long long)a_len * ((b_len + bc - 1) / bc) +
                                  (unsigned long long)b_len * na;
             }
-            // ---- type-II items
-            if (kind == 2) {
-                ++C.t2items;
-                const uint32_t tidx = ((((uint32_t)i * cfg.L + j) * (cfg.lcap + 1) + l) << 1) + (g - 1);
-                const TwoEntry e = cfg.tii[tidx];
-                const unsigned long long tot = (unsigned long long)a_len * b_len;
-                const uint32_t pack = (uint32_t)l | ((uint32_t)i << 5) | ((uint32_t)j << 11);
-                if (tot <= (1ull << e.k)) {
-                    if (cfg.mode & kModeT2Light) {
-                        const uint32_t s0 = cfg.seed_lo, s1 = cfg.seed_hi;
-                        const uint32_t c2 = pack | (kTagLight << 17);
-                        jump_chunk<DIM>(cfg, V, we, e, a_lo, b_lo, b_len, 0ull, tot,
-                                        [&](uint32_t t) { return philox(A, B, c2, t, s0, s1); }, C);
-                    }
-                } else if (cfg.mode & kModeT2Heavy) {
-                    const unsigned int slot = atomicAdd(cfg.heavy_count, 1u);
-                    if (slot < cfg.heavy_cap) {
-                        HeavyItem h;
-                        h.a_begin = a_lo;
-                        h.a_len = a_len;
-                        h.b_begin = b_lo;
-                        h.b_len = b_len;
-                        h.A = A;
-                        h.B = B;
-                        h.pack = pack;
-                        h.tii = tidx;
-                        h.chunk_prefix = (tot + (1ull << e.k) - 1) >> e.k;  // chunk count
-                        cfg.heavy[slot] = h;
-                    }
-                }
-            }
-            flush_edges(cfg, we, kEdgeBuf / 2);
         }
     }
-    flush_edges(cfg, we, 1);
-    if (cfg.mode & kModeT2Light) flush_counters(cfg, C);
     for (int o = 16; o > 0; o >>= 1) {
         t1_items_local += __shfl_down_sync(0xffffffffu, t1_items_local, o);
         t1_refs_local += __shfl_down_sync(0xffffffffu, t1_refs_local, o);
+        t2_items_local += __shfl_down_sync(0xffffffffu, t2_items_local, o);
     }
-    if (lane == 0 && t1_items_local) {
-        atomicAdd(&cfg.stats[kStatT1Items], t1_items_local);
-        atomicAdd(&cfg.stats[kStatT1VertexRefs], t1_refs_local);
+    if (lane == 0) {
+        if (t1_items_local) atomicAdd(&cfg.stats[kStatT1Items], t1_items_local);
+        if (t1_refs_local) atomicAdd(&cfg.stats[kStatT1VertexRefs], t1_refs_local);
+        if (t2_items_local) atomicAdd(&cfg.stats[kStatT2Items], t2_items_local);
     }
+}
+
+// ------------------------------------------------------------------ type-II streams
+// Single-chunk streams are sampled here (thread per stream); streams of several
+// chunks go to the heavy list.
+template <int DIM>
+__global__ void __launch_bounds__(kEnumThreads) k_streams(DevCfg cfg) {
+    __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
+    __shared__ unsigned int s_en[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_en[warp] = 0;
+    __syncwarp();
+    WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
+    const View V = sorted_view(cfg);
+    Counters C;
+    const unsigned int count = *cfg.stream_count < cfg.stream_cap ? *cfg.stream_count : cfg.stream_cap;
+    const unsigned int stride = gridDim.x * blockDim.x;
+    for (unsigned int b0 = blockIdx.x * blockDim.x; b0 < count; b0 += stride) {
+        const unsigned int q = b0 + threadIdx.x;
+        if (q < count) {
+            const Stream st = cfg.streams[q];
+            const TwoEntry e = cfg.tii[st.tii];
+            const unsigned long long tot = (unsigned long long)st.a_len * st.S;
+            const unsigned long long nch = (tot + (1ull << e.k) - 1) >> e.k;
+            if (nch <= 1) {
+                stream_chunk<DIM>(cfg, V, we, st, e, 0u, 0ull, tot, C);
+            } else if (nch > 0xffffffffull) {
+                atomicOr(cfg.error, 1u);  // chunk indices are 32-bit counter words
+            } else {
+                const unsigned int slot = atomicAdd(cfg.heavy_count, 1u);
+                if (slot < cfg.heavy_cap) cfg.heavy[slot] = HeavyItem{q, 0u, nch};
+            }
+        }
+        flush_edges(cfg, we, kEdgeBuf / 2);
+    }
+    flush_edges(cfg, we, 1);
+    flush_counters(cfg, C);
 }
 
 // ------------------------------------------------------------------ type I
@@ -662,21 +809,19 @@ __global__ void __launch_bounds__(kEnumThreads) k_heavy(DevCfg cfg, const unsign
     for (unsigned long long g0 = (unsigned long long)blockIdx.x * blockDim.x; g0 < T; g0 += stride) {
         const unsigned long long g = g0 + threadIdx.x;
         if (g < T) {
-            unsigned int lo = 0, hi = cnt;  // last item with prefix <= g
+            unsigned int lo = 0, hi = cnt;  // last heavy stream with prefix <= g
             while (hi - lo > 1) {
                 const unsigned int mid = (lo + hi) >> 1;
                 if (cfg.heavy[mid].chunk_prefix <= g) lo = mid; else hi = mid;
             }
-            const HeavyItem h = cfg.heavy[lo];
-            const unsigned long long hc = g - h.chunk_prefix;
-            const TwoEntry e = cfg.tii[h.tii];
-            const P4 ko = philox(h.A, h.B, h.pack | (kTagItem << 17), 0u, cfg.seed_lo, cfg.seed_hi);
-            const unsigned long long tot = (unsigned long long)h.a_len * h.b_len;
-            const unsigned long long start = hc << e.k;
+            const HeavyItem hv = cfg.heavy[lo];
+            const Stream st = cfg.streams[hv.stream];
+            const TwoEntry e = cfg.tii[st.tii];
+            const unsigned long long h = g - hv.chunk_prefix;
+            const unsigned long long tot = (unsigned long long)st.a_len * st.S;
+            const unsigned long long start = h << e.k;
             const unsigned long long len = (tot - start) < (1ull << e.k) ? (tot - start) : (1ull << e.k);
-            const uint32_t hlo = (uint32_t)hc, hhi = (uint32_t)(hc >> 32);
-            jump_chunk<DIM>(cfg, V, we, e, h.a_begin, h.b_begin, h.b_len, start, len,
-                            [&](uint32_t t) { return philox(hlo, hhi, t, kTagDraw, ko.x, ko.y); }, C);
+            stream_chunk<DIM>(cfg, V, we, st, e, (uint32_t)h, start, len, C);
         }
         flush_edges(cfg, we, kEdgeBuf / 2);
     }
@@ -736,6 +881,17 @@ void launch_enumerate(const DevCfg& cfg, cudaStream_t st) {
         case 3: k_enumerate<3><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
         case 4: k_enumerate<4><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
         default: k_enumerate<0><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
+    }
+}
+
+void launch_streams(const DevCfg& cfg, cudaStream_t st) {
+    ++g_launches;
+    switch (cfg.d) {
+        case 1: k_streams<1><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
+        case 2: k_streams<2><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
+        case 3: k_streams<3><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
+        case 4: k_streams<4><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
+        default: k_streams<0><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
     }
 }
 

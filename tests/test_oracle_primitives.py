@@ -173,10 +173,11 @@ def test_level_cap_and_chunk_log():
     assert O.level_cap(10000, 1) == 18
     assert O.level_cap(1_000_000, 2) == 12
     assert O.level_cap(2 ** 24, 4) == 7
-    for p in (1.0, 0.75, 0.5, 1e-3, 1e-9):
+    for p in (0.75, 0.5, 1e-3, 3e-9):
         k = O.chunk_log(p)
-        assert 64 <= p * 2 ** k < 128
-    assert O.chunk_log(1e-30) == 62
+        assert 4 <= p * 2 ** k < 8
+    assert O.chunk_log(1.0) == 3
+    assert O.chunk_log(1e-9) == O.chunk_log(1e-30) == 31  # clamped: chunks of 2^31
 
 
 def _visit_counts(d, depth):
