@@ -390,7 +390,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     auto clamp_cap = [](uint64_t c) { return c > 0xfffffff0ull ? 0xfffffff0ull : c; };
     uint64_t t1_cap = clamp_cap((uint64_t)n * (1 + (uint64_t)(0.75 * n3)) + 65536);
     uint64_t stream_cap = tzero ? 1024 : clamp_cap((uint64_t)n * (2 + 2 * (uint64_t)d) + 65536);
-    uint64_t seg_cap = tzero ? 1024 : clamp_cap((uint64_t)n * (2 + (uint64_t)(1.5 * n3)) + 65536);
+    uint64_t seg_cap = tzero ? 1024 : clamp_cap((uint64_t)n * (4 + (uint64_t)(1.5 * n3)) + 65536);
     T1Item* t1 = S.get<T1Item>(t1_cap);
     Stream* streams = S.get<Stream>(stream_cap);
     Seg* segs = S.get<Seg>(seg_cap);
@@ -496,9 +496,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
         }
         CK(cudaMemsetAsync(counters + 1, 0, 3 * sizeof(unsigned int), st));  // t1, streams, segs
         CK(cudaMemsetAsync(counters + 8, 0, sizeof(unsigned int), st));      // row counter
-        CK(cudaMemsetAsync(stats + kStatT1Items, 0, sizeof(unsigned long long), st));
-        CK(cudaMemsetAsync(stats + kStatT2Items, 0, sizeof(unsigned long long), st));
-        CK(cudaMemsetAsync(stats + kStatT1VertexRefs, 0, sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(stats, 0, kNumStats * sizeof(unsigned long long), st));
         launch_enumerate(cfg, st);
     }
     tm.mark();  // enumeration done

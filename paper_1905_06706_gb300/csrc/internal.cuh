@@ -41,6 +41,9 @@ struct Stream {
     uint32_t seg_off, seg_cnt;
     uint32_t S;     // total size of the partner sets
     uint32_t tii;   // index of its TwoEntry
+    uint32_t s0;    // single-chunk streams: offset of the first candidate (draw 0),
+                    // already drawn by the enumeration; 0xffffffff otherwise
+    uint32_t pad;
 };
 
 // One partner set of a stream: its first sorted position and the number of

@@ -208,29 +208,39 @@ __device__ bool accept_t2(const DevCfg& cfg, const View& V, uint32_t pu, uint32_
 // over indices [start, start + len) of the stream's index space a S, with
 // candidate idx -> (a = idx / S, b = idx mod S), b located in the partner set
 // whose positions hold it; accepted as U' pbar < p_uv.
+// The geometric jump of one draw: 0 stop, 1 continue with *X.
+__device__ __forceinline__ int draw_jump(const DevCfg& cfg, const TwoEntry& e, const P4& o,
+                                         unsigned long long rem, unsigned long long* X,
+                                         Counters& C) {
+    *X = 0;
+    if (e.one) return rem == 0 ? 0 : 1;
+    int r = 2;
+    if (cfg.precision == 0) r = jump32(o.x, o.y, e.invLb, rem, X);
+    if (r == 2) {
+        if (cfg.precision == 0) ++C.recheck;
+        r = jump64(o.x, o.y, e.Lb, rem, X);
+    }
+    return r;
+}
+
+// s_first: offset of the candidate of draw 0 when the caller already took that
+// draw (-1: start from draw 0).
 template <int DIM>
 __device__ void stream_chunk(const DevCfg& cfg, const View& V, WarpEdges& we, const Stream& st,
                              const TwoEntry& e, uint32_t h, unsigned long long start,
-                             unsigned long long len, Counters& C) {
+                             unsigned long long len, long long s_first, Counters& C) {
     const unsigned long long tot = (unsigned long long)st.a_len * st.S;
     long long s = -1;
     for (uint32_t t = 0;; ++t) {
         const P4 o = philox(st.A, st.pack, h, t, cfg.seed_lo, cfg.seed_hi);
-        ++C.draws;
-        const unsigned long long rem = len - (unsigned long long)(s + 1);
-        unsigned long long X = 0;
-        if (!e.one) {
-            int r = 2;
-            if (cfg.precision == 0) r = jump32(o.x, o.y, e.invLb, rem, &X);
-            if (r == 2) {
-                if (cfg.precision == 0) ++C.recheck;
-                r = jump64(o.x, o.y, e.Lb, rem, &X);
-            }
-            if (r == 0) break;
-        } else if (rem == 0) {
-            break;
+        if (t == 0 && s_first >= 0) {
+            s = s_first;
+        } else {
+            ++C.draws;
+            unsigned long long X;
+            if (draw_jump(cfg, e, o, len - (unsigned long long)(s + 1), &X, C) == 0) break;
+            s += 1 + (long long)X;
         }
-        s += 1 + (long long)X;
         ++C.cands;
         const unsigned long long idx = start + (unsigned long long)s;
         uint32_t ia, ib;
@@ -434,6 +444,7 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
     uint32_t* cnt_w = s_cnt[warp];
     uint32_t* sum_w = s_sum[warp];
     uint32_t* off_w = s_off[warp];
+    Counters C;
     unsigned long long t1_items_local = 0, t1_refs_local = 0, t2_items_local = 0;
     for (;;) {
         unsigned int r = 0;
@@ -455,6 +466,7 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
         const uint32_t PA = A >> d;  // parent cell (level l - 1)
         const uint32_t nkeys = 2u * rc.n2;
         // ---- type II, pass 1: members and positions of every (entry, gap)
+        bool any_alive = false;
         if (n2c) {
             for (uint32_t k = lane; k < nkeys; k += 32) {
                 cnt_w[k] = 0;
@@ -463,30 +475,44 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
             __syncwarp();
             for (uint32_t c0 = 0; c0 < n2c; c0 += 32) {
                 const uint32_t c = c0 + lane;
-                uint32_t e = 0xffffffffu, g = 0, b_lo = 0, b_len = 0;
-                int j = 0;
-                bool mem = false;
                 if (c < n2c) {
-                    mem = t2_combo<DIM>(cfg, rc, d, n6, i, l, A, PA, c, &e, &j, &g, &b_lo, &b_len);
+                    uint32_t e, g = 0, b_lo, b_len;
+                    int j;
+                    if (t2_combo<DIM>(cfg, rc, d, n6, i, l, A, PA, c, &e, &j, &g, &b_lo, &b_len)) {
+                        atomicAdd(&cnt_w[2 * e + g - 1], 1u);
+                        atomicAdd(&sum_w[2 * e + g - 1], b_len);
+                    }
                 }
-                uint32_t c1 = mem && g == 1, c2 = mem && g == 2;
-                uint32_t s1 = c1 ? b_len : 0u, s2 = c2 ? b_len : 0u;
-                seg_scan(e, c1, c2, s1, s2);
-                const uint32_t e_next = __shfl_down_sync(0xffffffffu, e, 1);
-                if (c < n2c && (lane == 31 || e_next != e)) {
-                    cnt_w[2 * e] += c1;
-                    cnt_w[2 * e + 1] += c2;
-                    sum_w[2 * e] += s1;
-                    sum_w[2 * e + 1] += s2;
-                }
-                __syncwarp();
             }
-            // streams: one per (entry, gap) with members; their segments reserved
+            __syncwarp();
+            // one stream per (entry, gap) with members; draw 0 of a single-chunk
+            // stream is taken here, and a stream that stops there is finished
             for (uint32_t k0 = 0; k0 < nkeys; k0 += 32) {
                 const uint32_t key = k0 + lane;
                 const uint32_t m = key < nkeys ? cnt_w[key] : 0u;
-                const uint32_t has = m > 0;
-                uint32_t im = m, is = has;
+                uint32_t keep = 0, s0 = 0xffffffffu, tidx = 0;
+                uint32_t pack = 0;
+                if (m) {
+                    t2_items_local += m;
+                    const uint32_t e = key >> 1, g = (key & 1u) + 1u;
+                    const uint32_t j = cfg.jlist[rc.jbase + e];
+                    pack = (uint32_t)l | ((uint32_t)i << 5) | (j << 11) | ((g - 1) << 17) | (kTagJump << 18);
+                    tidx = ((((uint32_t)i * cfg.L + j) * (cfg.lcap + 1) + l) << 1) + (g - 1);
+                    const TwoEntry te = cfg.tii[tidx];
+                    const unsigned long long tot = (unsigned long long)a_len * sum_w[key];
+                    keep = 1;
+                    if (tot <= (1ull << te.k)) {
+                        const P4 o = philox(A, pack, 0u, 0u, cfg.seed_lo, cfg.seed_hi);
+                        ++C.draws;
+                        unsigned long long X;
+                        if (draw_jump(cfg, te, o, tot, &X, C) == 0)
+                            keep = 0;
+                        else
+                            s0 = (uint32_t)X;
+                    }
+                }
+                const uint32_t mk = keep ? m : 0u;
+                uint32_t im = mk, is = keep;
                 for (int o = 1; o < 32; o <<= 1) {
                     const uint32_t a = __shfl_up_sync(0xffffffffu, im, o);
                     const uint32_t b = __shfl_up_sync(0xffffffffu, is, o);
@@ -500,27 +526,24 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
                     if (im) seg_base = atomicAdd(cfg.seg_count, im);
                     if (is) st_base = atomicAdd(cfg.stream_count, is);
                 }
-                seg_base = __shfl_sync(0xffffffffu, seg_base, 31) + im - m;
-                st_base = __shfl_sync(0xffffffffu, st_base, 31) + is - has;
-                if (has) {
-                    off_w[key] = seg_base;
-                    t2_items_local += m;
-                    if (st_base < cfg.stream_cap) {
-                        const uint32_t e = key >> 1, g = (key & 1u) + 1u;
-                        const uint32_t j = cfg.jlist[rc.jbase + e];
-                        Stream st;
-                        st.A = A;
-                        st.pack = (uint32_t)l | ((uint32_t)i << 5) | (j << 11) | ((g - 1) << 17) |
-                                  (kTagJump << 18);
-                        st.a_begin = a_lo;
-                        st.a_len = a_len;
-                        st.seg_off = seg_base;
-                        st.seg_cnt = m;
-                        st.S = sum_w[key];
-                        st.tii = ((((uint32_t)i * cfg.L + j) * (cfg.lcap + 1) + l) << 1) + (g - 1);
-                        cfg.streams[st_base] = st;
-                    }
+                seg_base = __shfl_sync(0xffffffffu, seg_base, 31) + im - mk;
+                st_base = __shfl_sync(0xffffffffu, st_base, 31) + is - keep;
+                if (key < nkeys) off_w[key] = keep ? seg_base : 0xffffffffu;
+                if (keep && st_base < cfg.stream_cap) {
+                    Stream st;
+                    st.A = A;
+                    st.pack = pack;
+                    st.a_begin = a_lo;
+                    st.a_len = a_len;
+                    st.seg_off = seg_base;
+                    st.seg_cnt = m;
+                    st.S = sum_w[key];
+                    st.tii = tidx;
+                    st.s0 = s0;
+                    st.pad = 0;
+                    cfg.streams[st_base] = st;
                 }
+                any_alive = __any_sync(0xffffffffu, keep) || any_alive;
             }
             __syncwarp();
             for (uint32_t k = lane; k < nkeys; k += 32) {
@@ -529,17 +552,16 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
             }
             __syncwarp();
         }
-        // ---- pass 2: segments of the streams (type II) and items (type I)
-        for (uint32_t c0 = 0; c0 < total; c0 += 32) {
-            const uint32_t c = c0 + lane;
-            if (c0 < n2c) {
+        // ---- pass 2: partner segments of the kept streams, in rank order
+        if (any_alive) {
+            for (uint32_t c0 = 0; c0 < n2c; c0 += 32) {
+                const uint32_t c = c0 + lane;
                 uint32_t e = 0xffffffffu, g = 0, b_lo = 0, b_len = 0;
                 int j = 0;
                 bool mem = false;
                 if (c < n2c) {
                     mem = t2_combo<DIM>(cfg, rc, d, n6, i, l, A, PA, c, &e, &j, &g, &b_lo, &b_len);
-                } else {
-                    e = 0xffffffffu;
+                    if (mem && off_w[2 * e + g - 1] == 0xffffffffu) mem = false;  // finished
                 }
                 uint32_t c1 = mem && g == 1, c2 = mem && g == 2;
                 uint32_t s1 = c1 ? b_len : 0u, s2 = c2 ? b_len : 0u;
@@ -561,6 +583,10 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
                 }
                 __syncwarp();
             }
+        }
+        // ---- type I
+        for (uint32_t c0 = n2c; c0 < total; c0 += 32) {
+            const uint32_t c = c0 + lane;
             // type-I items: split, then append with one atomic per warp
             int kind = 0;
             uint32_t B = 0, b_lo = 0, b_len = 0;
@@ -636,6 +662,7 @@ __global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
         if (t1_refs_local) atomicAdd(&cfg.stats[kStatT1VertexRefs], t1_refs_local);
         if (t2_items_local) atomicAdd(&cfg.stats[kStatT2Items], t2_items_local);
     }
+    flush_counters(cfg, C);
 }
 
 // ------------------------------------------------------------------ type-II streams
@@ -661,7 +688,7 @@ __global__ void __launch_bounds__(kEnumThreads) k_streams(DevCfg cfg) {
             const unsigned long long tot = (unsigned long long)st.a_len * st.S;
             const unsigned long long nch = (tot + (1ull << e.k) - 1) >> e.k;
             if (nch <= 1) {
-                stream_chunk<DIM>(cfg, V, we, st, e, 0u, 0ull, tot, C);
+                stream_chunk<DIM>(cfg, V, we, st, e, 0u, 0ull, tot, (long long)st.s0, C);
             } else if (nch > 0xffffffffull) {
                 atomicOr(cfg.error, 1u);  // chunk indices are 32-bit counter words
             } else {
@@ -821,7 +848,7 @@ __global__ void __launch_bounds__(kEnumThreads) k_heavy(DevCfg cfg, const unsign
             const unsigned long long tot = (unsigned long long)st.a_len * st.S;
             const unsigned long long start = h << e.k;
             const unsigned long long len = (tot - start) < (1ull << e.k) ? (tot - start) : (1ull << e.k);
-            stream_chunk<DIM>(cfg, V, we, st, e, (uint32_t)h, start, len, C);
+            stream_chunk<DIM>(cfg, V, we, st, e, (uint32_t)h, start, len, -1ll, C);
         }
         flush_edges(cfg, we, kEdgeBuf / 2);
     }
