@@ -374,14 +374,20 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     CK(cudaMemcpyAsync(d_jlist, jlist.data(), jlist.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_flo, flo.data(), K * 4, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_fhi, fhi.data(), K * 4, cudaMemcpyHostToDevice, st));
-    // rows: at most min(|V_i|, 2^(d l)) per (i, l)
-    uint64_t row_cap = 0;
+    // work entries: at most min(|V_i|, 2^(d l)) rows per (i, l), one entry per bucket
+    uint64_t ent2_cap = 0, ent1_cap = 0;
     for (int i = 0; i < L; ++i)
-        for (int l = 0; l <= CLd[i] && cnt[i]; ++l)
-            row_cap += std::min<uint64_t>((uint64_t)cnt[i], d * l >= 63 ? ~0ull : (1ull << (d * l)));
-    if (row_cap >= 0xffffffffull) throw Status{GIRG_E_INTERNAL};
-    uint64_t* rows = S.get<uint64_t>(row_cap + 1);
-    unsigned int* counters = S.get<unsigned int>(16);  // rows, t1, heavy, work[4]
+        for (int l = 0; l <= CLd[i] && cnt[i]; ++l) {
+            const uint64_t rows_il =
+                std::min<uint64_t>((uint64_t)cnt[i], d * l >= 63 ? ~0ull : (1ull << (d * l)));
+            const RowClass& rc = classes[(size_t)i * (kMaxLevel + 1) + l];
+            ent2_cap += rows_il * rc.n2;
+            ent1_cap += rows_il * rc.n1;
+        }
+    if (ent2_cap >= 0xffffffffull || ent1_cap >= 0xffffffffull) throw Status{GIRG_E_INTERNAL};
+    uint64_t* ent2 = S.get<uint64_t>(ent2_cap + 1);
+    uint64_t* ent1 = S.get<uint64_t>(ent1_cap + 1);
+    unsigned int* counters = S.get<unsigned int>(16);
     unsigned long long* stats = S.get<unsigned long long>(kNumStats + 2);  // + edge count + chunks
     CK(cudaMemsetAsync(counters, 0, 16 * sizeof(unsigned int), st));
     CK(cudaMemsetAsync(stats, 0, (kNumStats + 2) * sizeof(unsigned long long), st));
@@ -453,9 +459,13 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     cfg.cap = cap;
     cfg.edge_count = stats + kNumStats;
     cfg.stats = stats;
-    cfg.rows = rows;
     cfg.row_count = counters + 0;
-    cfg.row_cap = (uint32_t)row_cap;
+    cfg.ent2 = ent2;
+    cfg.ent2_count = counters + 6;
+    cfg.ent2_cap = (uint32_t)ent2_cap;
+    cfg.ent1 = ent1;
+    cfg.ent1_count = counters + 7;
+    cfg.ent1_cap = (uint32_t)ent1_cap;
     cfg.t1 = t1;
     cfg.t1_count = counters + 1;
     cfg.t1_cap = (uint32_t)t1_cap;
@@ -471,7 +481,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     cfg.error = counters + 5;
     cfg.work_counter = counters + 8;
 
-    launch_rows(cfg, rows, counters + 0, (unsigned)row_cap, st);
+    launch_rows(cfg, st);
     launch_enumerate(cfg, st);
     for (int attempt = 0;; ++attempt) {
         unsigned int hc[4];
@@ -495,7 +505,6 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
             cfg.segs = S.get<Seg>(cfg.seg_cap);
         }
         CK(cudaMemsetAsync(counters + 1, 0, 3 * sizeof(unsigned int), st));  // t1, streams, segs
-        CK(cudaMemsetAsync(counters + 8, 0, sizeof(unsigned int), st));      // row counter
         CK(cudaMemsetAsync(stats, 0, kNumStats * sizeof(unsigned long long), st));
         launch_enumerate(cfg, st);
     }

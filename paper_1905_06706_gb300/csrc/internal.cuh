@@ -100,9 +100,13 @@ struct DevCfg {
     int64_t cap;
     unsigned long long* edge_count;
     unsigned long long* stats;
-    const uint64_t* rows;
-    const unsigned int* row_count;
-    uint32_t row_cap;
+    unsigned int* row_count;  // rows found (statistics)
+    uint64_t* ent2;           // type-II work entries (row, bucket j)
+    unsigned int* ent2_count;
+    uint32_t ent2_cap;
+    uint64_t* ent1;           // type-I work entries
+    unsigned int* ent1_count;
+    uint32_t ent1_cap;
     T1Item* t1;
     unsigned int* t1_count;
     uint32_t t1_cap;

@@ -55,8 +55,7 @@ void launch_gather_hrg(int64_t n, const uint32_t* perm, const uint32_t* X, const
                        float* sh32, uint8_t* slayer, cudaStream_t st);
 
 // Pair sampling.
-void launch_rows(const DevCfg& cfg, uint64_t* rows, unsigned int* row_count, unsigned int cap,
-                 cudaStream_t st);
+void launch_rows(const DevCfg& cfg, cudaStream_t st);
 void launch_enumerate(const DevCfg& cfg, cudaStream_t st);
 void launch_streams(const DevCfg& cfg, cudaStream_t st);
 void launch_type1(const DevCfg& cfg, cudaStream_t st);

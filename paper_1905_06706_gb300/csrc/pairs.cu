@@ -277,9 +277,15 @@ __device__ __forceinline__ void flush_counters(const DevCfg& cfg, const Counters
 
 // ------------------------------------------------------------------ rows
 // Row heads: the first sorted position of every non-empty (bucket i, level l, cell)
-// for l <= CLd(i) (the deepest comparison level of i with a bucket j >= i).
-__global__ void k_rows(DevCfg cfg, uint64_t* __restrict__ rows, unsigned int* __restrict__ count,
-                       unsigned int cap) {
+// for l <= CLd(i) (the deepest comparison level of i with a bucket j >= i).  Each
+// row becomes one work entry per bucket it pairs with: type-II entries (distant
+// cells) and type-I entries (neighbour cells) in separate lists; an entry packs
+// p | l << 32 | i << 38 | e << 44 (e: index of the bucket in the row's class).
+__device__ __forceinline__ uint64_t pack_entry(uint32_t p, int l, int i, uint32_t e) {
+    return (uint64_t)p | ((uint64_t)l << 32) | ((uint64_t)i << 38) | ((uint64_t)e << 44);
+}
+
+__global__ void k_rows(DevCfg cfg) {
     const int lane = threadIdx.x & 31;
     const int64_t n = cfg.n;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -296,25 +302,43 @@ __global__ void k_rows(DevCfg cfg, uint64_t* __restrict__ rows, unsigned int* __
             prev = first ? 0u : cfg.skey[p - 1] - base;
             top = cfg.CLd[i];
         }
-        unsigned int mine = 0;
-        for (int l = 0; l <= top; ++l) {
-            const int s = cfg.d * (cfg.I[i] - l);
-            if (first || ((uint64_t)cell >> s) != ((uint64_t)prev >> s)) ++mine;
-        }
-        unsigned int incl = mine;
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        unsigned int base = 0;
-        if (lane == 31) base = atomicAdd(count, incl);
-        base = __shfl_sync(0xffffffffu, base, 31) + incl - mine;
+        uint32_t heads = 0, m2 = 0, m1 = 0;
         for (int l = 0; l <= top; ++l) {
             const int s = cfg.d * (cfg.I[i] - l);
             if (first || ((uint64_t)cell >> s) != ((uint64_t)prev >> s)) {
-                if (base < cap)
-                    rows[base] = (uint64_t)p | ((uint64_t)l << 32) | ((uint64_t)i << 40);
-                ++base;
+                const RowClass rc = cfg.classes[(uint32_t)i * (kMaxLevel + 1) + l];
+                ++heads;
+                m2 += rc.n2;
+                m1 += rc.n1;
+            }
+        }
+        uint32_t ih = heads, i2 = m2, i1 = m1;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t a = __shfl_up_sync(0xffffffffu, ih, o);
+            const uint32_t b = __shfl_up_sync(0xffffffffu, i2, o);
+            const uint32_t c = __shfl_up_sync(0xffffffffu, i1, o);
+            if (lane >= o) {
+                ih += a;
+                i2 += b;
+                i1 += c;
+            }
+        }
+        uint32_t b2 = 0, b1 = 0;
+        if (lane == 31) {
+            if (ih) atomicAdd(cfg.row_count, ih);
+            if (i2) b2 = atomicAdd(cfg.ent2_count, i2);
+            if (i1) b1 = atomicAdd(cfg.ent1_count, i1);
+        }
+        b2 = __shfl_sync(0xffffffffu, b2, 31) + i2 - m2;
+        b1 = __shfl_sync(0xffffffffu, b1, 31) + i1 - m1;
+        for (int l = 0; l <= top; ++l) {
+            const int s = cfg.d * (cfg.I[i] - l);
+            if (first || ((uint64_t)cell >> s) != ((uint64_t)prev >> s)) {
+                const RowClass rc = cfg.classes[(uint32_t)i * (kMaxLevel + 1) + l];
+                for (uint32_t e = 0; e < rc.n2; ++e, ++b2)
+                    if (b2 < cfg.ent2_cap) cfg.ent2[b2] = pack_entry((uint32_t)p, l, i, e);
+                for (uint32_t e = 0; e < rc.n1; ++e, ++b1)
+                    if (b1 < cfg.ent1_cap) cfg.ent1[b1] = pack_entry((uint32_t)p, l, i, e);
             }
         }
     }
@@ -324,15 +348,6 @@ __global__ void k_rows(DevCfg cfg, uint64_t* __restrict__ rows, unsigned int* __
 constexpr int kEnumThreads = 256;
 constexpr int kWarps = kEnumThreads / 32;
 constexpr uint32_t kSplitB = 1024, kSplitAB = 4096;
-
-__device__ __forceinline__ uint32_t vrange_lo(const DevCfg& cfg, int j, uint32_t B, int l, int d) {
-    const int s = d * (cfg.I[j] - l);
-    return cfg.offs[cfg.layer_base[j] + (uint32_t)((uint64_t)B << s)];
-}
-__device__ __forceinline__ uint32_t vrange_hi(const DevCfg& cfg, int j, uint32_t B, int l, int d) {
-    const int s = d * (cfg.I[j] - l);
-    return cfg.offs[cfg.layer_base[j] + (uint32_t)(((uint64_t)B + 1) << s)];
-}
 
 // An offset digit e in {-1, 0, 1} is a distinct neighbour on a level with 2^lev cells
 // per dimension unless the grid is too small: 1 cell -> only 0; 2 cells -> not -1.
@@ -370,299 +385,297 @@ __device__ __forceinline__ uint32_t dim_mask(int d, int k, int l) {
     return nb >= 32 ? pat : (pat & ((1u << nb) - 1u));
 }
 
-// A type-II combination c (< n2 6^d) of row cell A: the distant cell B of
-// A's parent-neighbour block with offset index c mod 6^d (Morton rank order), for
-// the bucket of entry c / 6^d.  Returns whether it is a non-empty partner set,
-// with its gap g and sorted range.
+// The cell, range and geometry of a work entry.
+struct EntryCtx {
+    uint32_t A, a_lo, a_len;
+    int l, i, j;
+    uint32_t e;
+    RowClass rc;
+    uint32_t baseB;  // global cell index base of bucket j
+    int sB;          // shift from level l to bucket j's insertion level
+};
+
 template <int DIM>
-__device__ __forceinline__ bool t2_combo(const DevCfg& cfg, const RowClass& rc, int d, uint32_t n6,
-                                         int i, int l, uint32_t A, uint32_t PA, uint32_t c,
-                                         uint32_t* e_out, int* j_out, uint32_t* g_out,
-                                         uint32_t* b_lo, uint32_t* b_len) {
-    const uint32_t e = c / n6, off = c - e * n6;
-    const int j = cfg.jlist[rc.jbase + e];
-    *e_out = e;
-    *j_out = j;
-    const uint32_t kids = off & ((1u << d) - 1u);
-    uint32_t q = off >> d;
-    uint32_t P = 0, linf = 0;
-    bool ok = true;
-#pragma unroll
-    for (int k = (DIM ? DIM : kMaxDim) - 1; k >= 0; --k) {
-        if (DIM == 0 && k >= d) continue;
-        const int ek = (int)(q % 3u) - 1;
-        q /= 3u;
-        ok = ok && digit_ok(ek, l - 1);
-        P |= dil_add(PA, dim_mask(d, k, l - 1), 1u << (d - 1 - k), ek);
-        const int alpha = (int)((A >> (d - 1 - k)) & 1u);
-        const int kid = (int)((kids >> (d - 1 - k)) & 1u);
-        int diff = 2 * ek + kid - alpha;
-        diff = diff < 0 ? -diff : diff;
-        if (l == 2 && diff > 2) diff = 4 - diff;  // 4 cells per dimension
-        linf = (uint32_t)diff > linf ? (uint32_t)diff : linf;
-    }
-    if (!ok || linf <= 1) return false;  // repeated offset, or a neighbour of A
-    const uint32_t B = (P << d) | kids;
-    if (j == i && B <= A) return false;
-    *g_out = linf - 1;
-    *b_lo = vrange_lo(cfg, j, B, l, d);
-    *b_len = vrange_hi(cfg, j, B, l, d) - *b_lo;
-    return *b_len > 0;
+__device__ __forceinline__ EntryCtx decode_entry(const DevCfg& cfg, uint64_t ent, int d, bool type1) {
+    EntryCtx x;
+    const uint32_t p = (uint32_t)ent;
+    x.l = (int)((ent >> 32) & 0x3f);
+    x.i = (int)((ent >> 38) & 0x3f);
+    x.e = (uint32_t)(ent >> 44);
+    x.rc = cfg.classes[(uint32_t)x.i * (kMaxLevel + 1) + x.l];
+    x.j = cfg.jlist[x.rc.jbase + (type1 ? x.rc.n2 : 0u) + x.e];
+    const uint32_t base_i = cfg.layer_base[x.i];
+    const int sA = d * (cfg.I[x.i] - x.l);
+    x.A = (uint32_t)((uint64_t)(cfg.skey[p] - base_i) >> sA);
+    x.a_lo = cfg.offs[base_i + (uint32_t)((uint64_t)x.A << sA)];
+    x.a_len = cfg.offs[base_i + (uint32_t)(((uint64_t)x.A + 1) << sA)] - x.a_lo;
+    x.baseB = cfg.layer_base[x.j];
+    x.sB = d * (cfg.I[x.j] - x.l);
+    return x;
 }
 
-// Segmented inclusive warp scan of (count, positions) for each gap, segments =
-// runs of lanes with the same entry id.
-__device__ __forceinline__ void seg_scan(uint32_t key, uint32_t& c1, uint32_t& c2, uint32_t& s1,
-                                         uint32_t& s2) {
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void range_of(const DevCfg& cfg, const EntryCtx& x, uint32_t B,
+                                         uint32_t* lo, uint32_t* len) {
+    const uint32_t a = cfg.offs[x.baseB + (uint32_t)((uint64_t)B << x.sB)];
+    *lo = a;
+    *len = cfg.offs[x.baseB + (uint32_t)(((uint64_t)B + 1) << x.sB)] - a;
+}
+
+// Visit the distant partner cells B of A (children of the neighbours of A's
+// parent, not neighbours of A) in rank order, rank = (sum_k (e_k + 1) 3^(d-1-k)) 2^d
+// + sum_k kid_k 2^(d-1-k); f(B, g) for each one that counts for bucket j.
+template <int DIM, class F>
+__device__ __forceinline__ void for_partners(const EntryCtx& x, int d, F f) {
+    constexpr int DM = DIM ? DIM : kMaxDim;
+    const uint32_t n3d = DIM == 1 ? 3u : DIM == 2 ? 9u : DIM == 3 ? 27u : DIM == 4 ? 81u : 0u;
+    uint32_t n3 = n3d;
+    if (DIM == 0) {
+        n3 = 1;
+        for (int k = 0; k < d; ++k) n3 *= 3u;
+    }
+    const uint32_t PA = x.A >> d;
+    int alpha[DM];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t ku = __shfl_up_sync(0xffffffffu, key, o);
-        const uint32_t a1 = __shfl_up_sync(0xffffffffu, c1, o);
-        const uint32_t a2 = __shfl_up_sync(0xffffffffu, c2, o);
-        const uint32_t b1 = __shfl_up_sync(0xffffffffu, s1, o);
-        const uint32_t b2 = __shfl_up_sync(0xffffffffu, s2, o);
-        if (lane >= o && ku == key) {
-            c1 += a1;
-            c2 += a2;
-            s1 += b1;
-            s2 += b2;
+    for (int k = 0; k < DM; ++k) alpha[k] = (k < d) ? (int)((x.A >> (d - 1 - k)) & 1u) : 0;
+    for (uint32_t eidx = 0; eidx < n3; ++eidx) {
+        int ek[DM];
+        uint32_t q = eidx, P = 0;
+        bool ok = true;
+#pragma unroll
+        for (int k = DM - 1; k >= 0; --k) {
+            if (k >= d) {
+                ek[k] = 0;
+                continue;
+            }
+            ek[k] = (int)(q % 3u) - 1;
+            q /= 3u;
+            ok = ok && digit_ok(ek[k], x.l - 1);
+            P |= dil_add(PA, dim_mask(d, k, x.l - 1), 1u << (d - 1 - k), ek[k]);
+        }
+        if (!ok) continue;
+        const uint32_t nk = 1u << d;
+        for (uint32_t kids = 0; kids < nk; ++kids) {
+            int linf = 0;
+#pragma unroll
+            for (int k = 0; k < DM; ++k) {
+                if (k >= d) continue;
+                const int kid = (int)((kids >> (d - 1 - k)) & 1u);
+                int diff = 2 * ek[k] + kid - alpha[k];
+                diff = diff < 0 ? -diff : diff;
+                if (x.l == 2 && diff > 2) diff = 4 - diff;  // 4 cells per dimension
+                linf = diff > linf ? diff : linf;
+            }
+            if (linf <= 1) continue;  // a neighbour of A, not distant
+            const uint32_t B = (P << d) | kids;
+            if (x.j == x.i && B <= x.A) continue;
+            f(B, (uint32_t)(linf - 1));
         }
     }
 }
 
+// Type-II entries (thread per (row, bucket j)): the per-gap totals of the partner
+// sets, draw 0 of each single-chunk stream (most streams end there), and for the
+// remaining streams a descriptor plus their partner segments in rank order.
 template <int DIM>
-__global__ void __launch_bounds__(kEnumThreads) k_enumerate(DevCfg cfg) {
-    __shared__ uint32_t s_cnt[kWarps][2 * kMaxLayers];  // members per (entry, gap)
-    __shared__ uint32_t s_sum[kWarps][2 * kMaxLayers];  // positions per (entry, gap)
-    __shared__ uint32_t s_off[kWarps][2 * kMaxLayers];  // first segment per (entry, gap)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__global__ void __launch_bounds__(kEnumThreads) k_enum2(DevCfg cfg) {
+    const int lane = threadIdx.x & 31;
     const int d = DIM ? DIM : cfg.d;
-    const uint32_t n3 = DIM == 1 ? 3u : DIM == 2 ? 9u : DIM == 3 ? 27u : DIM == 4 ? 81u : (uint32_t)cfg.n3;
-    const uint32_t n6 = DIM == 1 ? 6u : DIM == 2 ? 36u : DIM == 3 ? 216u : DIM == 4 ? 1296u : (uint32_t)cfg.n6;
-    const unsigned int nrows = *cfg.row_count < cfg.row_cap ? *cfg.row_count : cfg.row_cap;
-    uint32_t* cnt_w = s_cnt[warp];
-    uint32_t* sum_w = s_sum[warp];
-    uint32_t* off_w = s_off[warp];
     Counters C;
-    unsigned long long t1_items_local = 0, t1_refs_local = 0, t2_items_local = 0;
-    for (;;) {
-        unsigned int r = 0;
-        if (lane == 0) r = atomicAdd(&cfg.work_counter[0], 1u);
-        r = __shfl_sync(0xffffffffu, r, 0);
-        if (r >= nrows) break;
-        const uint64_t row = cfg.rows[r];
-        const uint32_t p = (uint32_t)row;
-        const int l = (int)((row >> 32) & 0xff);
-        const int i = (int)(row >> 40);
-        const uint32_t base_i = cfg.layer_base[i];
-        const int sA = d * (cfg.I[i] - l);
-        const uint32_t A = (uint32_t)((uint64_t)(cfg.skey[p] - base_i) >> sA);
-        const uint32_t a_lo = vrange_lo(cfg, i, A, l, d), a_hi = vrange_hi(cfg, i, A, l, d);
-        const uint32_t a_len = a_hi - a_lo;
-        const RowClass rc = cfg.classes[(uint32_t)i * (kMaxLevel + 1) + l];
-        const uint32_t n2c = (uint32_t)rc.n2 * n6;
-        const uint32_t total = n2c + (uint32_t)rc.n1 * n3;
-        const uint32_t PA = A >> d;  // parent cell (level l - 1)
-        const uint32_t nkeys = 2u * rc.n2;
-        // ---- type II, pass 1: members and positions of every (entry, gap)
-        bool any_alive = false;
-        if (n2c) {
-            for (uint32_t k = lane; k < nkeys; k += 32) {
-                cnt_w[k] = 0;
-                sum_w[k] = 0;
-            }
-            __syncwarp();
-            for (uint32_t c0 = 0; c0 < n2c; c0 += 32) {
-                const uint32_t c = c0 + lane;
-                if (c < n2c) {
-                    uint32_t e, g = 0, b_lo, b_len;
-                    int j;
-                    if (t2_combo<DIM>(cfg, rc, d, n6, i, l, A, PA, c, &e, &j, &g, &b_lo, &b_len)) {
-                        atomicAdd(&cnt_w[2 * e + g - 1], 1u);
-                        atomicAdd(&sum_w[2 * e + g - 1], b_len);
-                    }
+    unsigned long long t2_items_local = 0;
+    const unsigned int count = *cfg.ent2_count < cfg.ent2_cap ? *cfg.ent2_count : cfg.ent2_cap;
+    const unsigned int stride = gridDim.x * blockDim.x;
+    for (unsigned int b0 = blockIdx.x * blockDim.x; b0 < count; b0 += stride) {
+        const unsigned int q = b0 + threadIdx.x;
+        const bool active = q < count;
+        EntryCtx x;
+        uint32_t cnt[2] = {0u, 0u}, sum[2] = {0u, 0u}, keep[2] = {0u, 0u}, s0[2], tidx[2];
+        uint32_t pack[2] = {0u, 0u};
+        if (active) {
+            x = decode_entry<DIM>(cfg, cfg.ent2[q], d, false);
+            for_partners<DIM>(x, d, [&](uint32_t B, uint32_t g) {
+                uint32_t lo, len;
+                range_of(cfg, x, B, &lo, &len);
+                if (len) {
+                    cnt[g - 1] += 1u;
+                    sum[g - 1] += len;
+                }
+            });
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                s0[g] = 0xffffffffu;
+                if (!cnt[g]) continue;
+                t2_items_local += cnt[g];
+                pack[g] = (uint32_t)x.l | ((uint32_t)x.i << 5) | ((uint32_t)x.j << 11) |
+                          ((uint32_t)g << 17) | (kTagJump << 18);
+                tidx[g] = ((((uint32_t)x.i * cfg.L + x.j) * (cfg.lcap + 1) + x.l) << 1) + g;
+                const TwoEntry te = cfg.tii[tidx[g]];
+                const unsigned long long tot = (unsigned long long)x.a_len * sum[g];
+                keep[g] = 1u;
+                if (tot <= (1ull << te.k)) {
+                    const P4 o = philox(x.A, pack[g], 0u, 0u, cfg.seed_lo, cfg.seed_hi);
+                    ++C.draws;
+                    unsigned long long X;
+                    if (draw_jump(cfg, te, o, tot, &X, C) == 0)
+                        keep[g] = 0u;
+                    else
+                        s0[g] = (uint32_t)X;
                 }
             }
-            __syncwarp();
-            // one stream per (entry, gap) with members; draw 0 of a single-chunk
-            // stream is taken here, and a stream that stops there is finished
-            for (uint32_t k0 = 0; k0 < nkeys; k0 += 32) {
-                const uint32_t key = k0 + lane;
-                const uint32_t m = key < nkeys ? cnt_w[key] : 0u;
-                uint32_t keep = 0, s0 = 0xffffffffu, tidx = 0;
-                uint32_t pack = 0;
-                if (m) {
-                    t2_items_local += m;
-                    const uint32_t e = key >> 1, g = (key & 1u) + 1u;
-                    const uint32_t j = cfg.jlist[rc.jbase + e];
-                    pack = (uint32_t)l | ((uint32_t)i << 5) | (j << 11) | ((g - 1) << 17) | (kTagJump << 18);
-                    tidx = ((((uint32_t)i * cfg.L + j) * (cfg.lcap + 1) + l) << 1) + (g - 1);
-                    const TwoEntry te = cfg.tii[tidx];
-                    const unsigned long long tot = (unsigned long long)a_len * sum_w[key];
-                    keep = 1;
-                    if (tot <= (1ull << te.k)) {
-                        const P4 o = philox(A, pack, 0u, 0u, cfg.seed_lo, cfg.seed_hi);
-                        ++C.draws;
-                        unsigned long long X;
-                        if (draw_jump(cfg, te, o, tot, &X, C) == 0)
-                            keep = 0;
-                        else
-                            s0 = (uint32_t)X;
-                    }
-                }
-                const uint32_t mk = keep ? m : 0u;
-                uint32_t im = mk, is = keep;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t a = __shfl_up_sync(0xffffffffu, im, o);
-                    const uint32_t b = __shfl_up_sync(0xffffffffu, is, o);
-                    if (lane >= o) {
-                        im += a;
-                        is += b;
-                    }
-                }
-                uint32_t seg_base = 0, st_base = 0;
-                if (lane == 31) {
-                    if (im) seg_base = atomicAdd(cfg.seg_count, im);
-                    if (is) st_base = atomicAdd(cfg.stream_count, is);
-                }
-                seg_base = __shfl_sync(0xffffffffu, seg_base, 31) + im - mk;
-                st_base = __shfl_sync(0xffffffffu, st_base, 31) + is - keep;
-                if (key < nkeys) off_w[key] = keep ? seg_base : 0xffffffffu;
-                if (keep && st_base < cfg.stream_cap) {
+        }
+        // one atomic per warp for the streams and one for their segments
+        const uint32_t nst = keep[0] + keep[1];
+        const uint32_t nsg = (keep[0] ? cnt[0] : 0u) + (keep[1] ? cnt[1] : 0u);
+        uint32_t ist = nst, isg = nsg;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t a = __shfl_up_sync(0xffffffffu, ist, o);
+            const uint32_t b = __shfl_up_sync(0xffffffffu, isg, o);
+            if (lane >= o) {
+                ist += a;
+                isg += b;
+            }
+        }
+        uint32_t st_base = 0, sg_base = 0;
+        if (lane == 31) {
+            if (ist) st_base = atomicAdd(cfg.stream_count, ist);
+            if (isg) sg_base = atomicAdd(cfg.seg_count, isg);
+        }
+        st_base = __shfl_sync(0xffffffffu, st_base, 31) + ist - nst;
+        sg_base = __shfl_sync(0xffffffffu, sg_base, 31) + isg - nsg;
+        if (nst) {
+            uint32_t off[2], pos[2] = {0u, 0u}, pre[2] = {0u, 0u};
+            off[0] = sg_base;
+            off[1] = sg_base + (keep[0] ? cnt[0] : 0u);
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                if (!keep[g]) continue;
+                if (st_base < cfg.stream_cap) {
                     Stream st;
-                    st.A = A;
-                    st.pack = pack;
-                    st.a_begin = a_lo;
-                    st.a_len = a_len;
-                    st.seg_off = seg_base;
-                    st.seg_cnt = m;
-                    st.S = sum_w[key];
-                    st.tii = tidx;
-                    st.s0 = s0;
+                    st.A = x.A;
+                    st.pack = pack[g];
+                    st.a_begin = x.a_lo;
+                    st.a_len = x.a_len;
+                    st.seg_off = off[g];
+                    st.seg_cnt = cnt[g];
+                    st.S = sum[g];
+                    st.tii = tidx[g];
+                    st.s0 = s0[g];
                     st.pad = 0;
                     cfg.streams[st_base] = st;
                 }
-                any_alive = __any_sync(0xffffffffu, keep) || any_alive;
+                ++st_base;
             }
-            __syncwarp();
-            for (uint32_t k = lane; k < nkeys; k += 32) {
-                cnt_w[k] = 0;
-                sum_w[k] = 0;
-            }
-            __syncwarp();
+            for_partners<DIM>(x, d, [&](uint32_t B, uint32_t g) {
+                if (!keep[g - 1]) return;
+                uint32_t lo, len;
+                range_of(cfg, x, B, &lo, &len);
+                if (!len) return;
+                const uint32_t at = off[g - 1] + pos[g - 1];
+                if (at < cfg.seg_cap) cfg.segs[at] = Seg{lo, pre[g - 1]};
+                pos[g - 1] += 1u;
+                pre[g - 1] += len;
+            });
         }
-        // ---- pass 2: partner segments of the kept streams, in rank order
-        if (any_alive) {
-            for (uint32_t c0 = 0; c0 < n2c; c0 += 32) {
-                const uint32_t c = c0 + lane;
-                uint32_t e = 0xffffffffu, g = 0, b_lo = 0, b_len = 0;
-                int j = 0;
-                bool mem = false;
-                if (c < n2c) {
-                    mem = t2_combo<DIM>(cfg, rc, d, n6, i, l, A, PA, c, &e, &j, &g, &b_lo, &b_len);
-                    if (mem && off_w[2 * e + g - 1] == 0xffffffffu) mem = false;  // finished
-                }
-                uint32_t c1 = mem && g == 1, c2 = mem && g == 2;
-                uint32_t s1 = c1 ? b_len : 0u, s2 = c2 ? b_len : 0u;
-                const uint32_t own_c = c1 + c2, own_s = s1 + s2;
-                seg_scan(e, c1, c2, s1, s2);
-                if (mem) {
-                    const uint32_t key = 2 * e + (g - 1);
-                    const uint32_t pos = off_w[key] + cnt_w[key] + (g == 1 ? c1 : c2) - own_c;
-                    const uint32_t pre = sum_w[key] + (g == 1 ? s1 : s2) - own_s;
-                    if (pos < cfg.seg_cap) cfg.segs[pos] = Seg{b_lo, pre};
-                }
-                __syncwarp();
-                const uint32_t e_next = __shfl_down_sync(0xffffffffu, e, 1);
-                if (c < n2c && (lane == 31 || e_next != e)) {
-                    cnt_w[2 * e] += c1;
-                    cnt_w[2 * e + 1] += c2;
-                    sum_w[2 * e] += s1;
-                    sum_w[2 * e + 1] += s2;
-                }
-                __syncwarp();
-            }
-        }
-        // ---- type I
-        for (uint32_t c0 = n2c; c0 < total; c0 += 32) {
-            const uint32_t c = c0 + lane;
-            // type-I items: split, then append with one atomic per warp
-            int kind = 0;
-            uint32_t B = 0, b_lo = 0, b_len = 0;
-            int j = 0;
-            if (c >= n2c && c < total) {
-                const uint32_t c1 = c - n2c;
-                const uint32_t e = c1 / n3;
-                uint32_t q = c1 - e * n3;
-                j = cfg.jlist[rc.jbase + rc.n2 + e];
-                uint32_t Bv = 0;
-                bool ok = true;
+    }
+    for (int o = 16; o > 0; o >>= 1) t2_items_local += __shfl_down_sync(0xffffffffu, t2_items_local, o);
+    if (lane == 0 && t2_items_local) atomicAdd(&cfg.stats[kStatT2Items], t2_items_local);
+    flush_counters(cfg, C);
+}
+
+// Type-I entries (thread per (row, bucket j)): every non-empty neighbour cell B
+// of A (B >= A when j = i) gives an item V_i^A x V_j^B, split into sub-items of at
+// most kSplitAB pairs.
+template <int DIM>
+__global__ void __launch_bounds__(kEnumThreads) k_enum1(DevCfg cfg) {
+    const int lane = threadIdx.x & 31;
+    const int d = DIM ? DIM : cfg.d;
+    constexpr int DM = DIM ? DIM : kMaxDim;
+    uint32_t n3 = DIM == 1 ? 3u : DIM == 2 ? 9u : DIM == 3 ? 27u : DIM == 4 ? 81u : 0u;
+    if (DIM == 0) {
+        n3 = 1;
+        for (int k = 0; k < d; ++k) n3 *= 3u;
+    }
+    unsigned long long t1_items_local = 0, t1_refs_local = 0;
+    const unsigned int count = *cfg.ent1_count < cfg.ent1_cap ? *cfg.ent1_count : cfg.ent1_cap;
+    const unsigned int stride = gridDim.x * blockDim.x;
+    for (unsigned int b0 = blockIdx.x * blockDim.x; b0 < count; b0 += stride) {
+        const unsigned int q = b0 + threadIdx.x;
+        const bool active = q < count;
+        EntryCtx x;
+        if (active) x = decode_entry<DIM>(cfg, cfg.ent1[q], d, true);
+        // neighbour cell of offset index c (digits of dimension 0 most significant)
+        auto neighbour = [&](uint32_t c, uint32_t* B) {
+            uint32_t qq = c, Bv = 0;
+            bool ok = true;
 #pragma unroll
-                for (int k = (DIM ? DIM : kMaxDim) - 1; k >= 0; --k) {
-                    if (DIM == 0 && k >= d) continue;
-                    const int ek = (int)(q % 3u) - 1;
-                    q /= 3u;
-                    ok = ok && digit_ok(ek, l);
-                    Bv |= dil_add(A, dim_mask(d, k, l), 1u << (d - 1 - k), ek);
-                }
-                if (ok && !(j == i && Bv < A)) {
-                    B = Bv;
-                    b_lo = vrange_lo(cfg, j, B, l, d);
-                    b_len = vrange_hi(cfg, j, B, l, d) - b_lo;
-                    if (b_len > 0) kind = 1;
-                }
+            for (int k = DM - 1; k >= 0; --k) {
+                if (k >= d) continue;
+                const int ek = (int)(qq % 3u) - 1;
+                qq /= 3u;
+                ok = ok && digit_ok(ek, x.l);
+                Bv |= dil_add(x.A, dim_mask(d, k, x.l), 1u << (d - 1 - k), ek);
             }
-            uint32_t nsub = 0, ac = 0, bc = 0, na = 0;
-            if (kind == 1) {
-                bc = b_len < kSplitB ? b_len : kSplitB;
-                ac = kSplitAB / bc;
-                if (ac < 1) ac = 1;
-                na = (a_len + ac - 1) / ac;
-                nsub = na * ((b_len + bc - 1) / bc);
+            *B = Bv;
+            return ok && !(x.j == x.i && Bv < x.A);
+        };
+        auto split = [&](uint32_t b_len, uint32_t* ac, uint32_t* bc, uint32_t* na) {
+            *bc = b_len < kSplitB ? b_len : kSplitB;
+            *ac = kSplitAB / *bc;
+            if (*ac < 1) *ac = 1;
+            *na = (x.a_len + *ac - 1) / *ac;
+            return *na * ((b_len + *bc - 1) / *bc);
+        };
+        uint32_t nsub = 0;
+        if (active) {
+            for (uint32_t c = 0; c < n3; ++c) {
+                uint32_t B, lo, len, ac, bc, na;
+                if (!neighbour(c, &B)) continue;
+                range_of(cfg, x, B, &lo, &len);
+                if (len) nsub += split(len, &ac, &bc, &na);
             }
-            unsigned int incl = nsub;
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
-            }
-            unsigned int tbase = 0;
-            if (lane == 31 && incl) tbase = atomicAdd(cfg.t1_count, incl);
-            tbase = __shfl_sync(0xffffffffu, tbase, 31) + incl - nsub;
-            if (kind == 1) {
-                const uint32_t tri = (B == A && j == i) ? 0x80000000u : 0u;
-                uint32_t q = 0;
-                for (uint32_t ya = 0; ya < a_len; ya += ac) {
-                    for (uint32_t yb = 0; yb < b_len; yb += bc, ++q) {
-                        const uint32_t slot = tbase + q;
-                        if (slot < cfg.t1_cap) {
+        }
+        uint32_t incl = nsub;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        uint32_t tbase = 0;
+        if (lane == 31 && incl) tbase = atomicAdd(cfg.t1_count, incl);
+        tbase = __shfl_sync(0xffffffffu, tbase, 31) + incl - nsub;
+        if (nsub) {
+            for (uint32_t c = 0; c < n3; ++c) {
+                uint32_t B, lo, len, ac, bc, na;
+                if (!neighbour(c, &B)) continue;
+                range_of(cfg, x, B, &lo, &len);
+                if (!len) continue;
+                split(len, &ac, &bc, &na);
+                const uint32_t tri = (B == x.A && x.j == x.i) ? 0x80000000u : 0u;
+                for (uint32_t ya = 0; ya < x.a_len; ya += ac) {
+                    for (uint32_t yb = 0; yb < len; yb += bc, ++tbase) {
+                        if (tbase < cfg.t1_cap) {
                             T1Item it;
-                            it.a_begin = a_lo + ya;
-                            it.a_len = (a_len - ya) < ac ? (a_len - ya) : ac;
-                            it.b_begin = b_lo + yb;
-                            it.b_len = ((b_len - yb) < bc ? (b_len - yb) : bc) | tri;
-                            cfg.t1[slot] = it;
+                            it.a_begin = x.a_lo + ya;
+                            it.a_len = (x.a_len - ya) < ac ? (x.a_len - ya) : ac;
+                            it.b_begin = lo + yb;
+                            it.b_len = ((len - yb) < bc ? (len - yb) : bc) | tri;
+                            cfg.t1[tbase] = it;
                         }
                     }
                 }
-                t1_items_local += nsub;
                 // every a-chunk meets every b-chunk: sum of side lengths over sub-items
-                t1_refs_local += (unsigned long long)a_len * ((b_len + bc - 1) / bc) +
-                                 (unsigned long long)b_len * na;
+                t1_refs_local += (unsigned long long)x.a_len * ((len + bc - 1) / bc) +
+                                 (unsigned long long)len * na;
             }
+            t1_items_local += nsub;
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
         t1_items_local += __shfl_down_sync(0xffffffffu, t1_items_local, o);
         t1_refs_local += __shfl_down_sync(0xffffffffu, t1_refs_local, o);
-        t2_items_local += __shfl_down_sync(0xffffffffu, t2_items_local, o);
     }
-    if (lane == 0) {
-        if (t1_items_local) atomicAdd(&cfg.stats[kStatT1Items], t1_items_local);
-        if (t1_refs_local) atomicAdd(&cfg.stats[kStatT1VertexRefs], t1_refs_local);
-        if (t2_items_local) atomicAdd(&cfg.stats[kStatT2Items], t2_items_local);
+    if (lane == 0 && t1_items_local) {
+        atomicAdd(&cfg.stats[kStatT1Items], t1_items_local);
+        atomicAdd(&cfg.stats[kStatT1VertexRefs], t1_refs_local);
     }
-    flush_counters(cfg, C);
 }
 
 // ------------------------------------------------------------------ type-II streams
@@ -891,23 +904,27 @@ __global__ void __launch_bounds__(256) k_allpairs(DevCfg cfg, View V, unsigned i
 }
 
 // ------------------------------------------------------------------ launchers
-void launch_rows(const DevCfg& cfg, uint64_t* rows, unsigned int* row_count, unsigned int cap,
-                 cudaStream_t st) {
+void launch_rows(const DevCfg& cfg, cudaStream_t st) {
     int64_t b = (cfg.n + 255) / 256;
     if (b > 152 * 16) b = 152 * 16;
     if (b < 1) b = 1;
     ++g_launches;
-    k_rows<<<(unsigned)b, 256, 0, st>>>(cfg, rows, row_count, cap);
+    k_rows<<<(unsigned)b, 256, 0, st>>>(cfg);
 }
 
 void launch_enumerate(const DevCfg& cfg, cudaStream_t st) {
-    ++g_launches;
+    g_launches += 2;
     switch (cfg.d) {
-        case 1: k_enumerate<1><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
-        case 2: k_enumerate<2><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
-        case 3: k_enumerate<3><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
-        case 4: k_enumerate<4><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
-        default: k_enumerate<0><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
+        case 1: k_enum2<1><<<152 * 8, kEnumThreads, 0, st>>>(cfg);
+                k_enum1<1><<<152 * 8, kEnumThreads, 0, st>>>(cfg); break;
+        case 2: k_enum2<2><<<152 * 8, kEnumThreads, 0, st>>>(cfg);
+                k_enum1<2><<<152 * 8, kEnumThreads, 0, st>>>(cfg); break;
+        case 3: k_enum2<3><<<152 * 8, kEnumThreads, 0, st>>>(cfg);
+                k_enum1<3><<<152 * 8, kEnumThreads, 0, st>>>(cfg); break;
+        case 4: k_enum2<4><<<152 * 8, kEnumThreads, 0, st>>>(cfg);
+                k_enum1<4><<<152 * 8, kEnumThreads, 0, st>>>(cfg); break;
+        default: k_enum2<0><<<152 * 8, kEnumThreads, 0, st>>>(cfg);
+                 k_enum1<0><<<152 * 8, kEnumThreads, 0, st>>>(cfg); break;
     }
 }
 
