@@ -388,9 +388,10 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     uint64_t* ent2 = S.get<uint64_t>(ent2_cap + 1);
     uint64_t* ent1 = S.get<uint64_t>(ent1_cap + 1);
     unsigned int* counters = S.get<unsigned int>(16);
-    unsigned long long* stats = S.get<unsigned long long>(kNumStats + 2);  // + edge count + chunks
+    // stats, then the edge count and the two work counters of the type-I / type-II kernels
+    unsigned long long* stats = S.get<unsigned long long>(kNumStats + 3);
     CK(cudaMemsetAsync(counters, 0, 16 * sizeof(unsigned int), st));
-    CK(cudaMemsetAsync(stats, 0, (kNumStats + 2) * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(stats, 0, (kNumStats + 3) * sizeof(unsigned long long), st));
     // work lists, sized from typical counts per vertex; the enumeration only writes
     // work (no edges), so an overflow is repaired by resizing and running it again
     auto clamp_cap = [](uint64_t c) { return c > 0xfffffff0ull ? 0xfffffff0ull : c; };
@@ -398,9 +399,10 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     uint64_t stream_cap = tzero ? 1024 : clamp_cap((uint64_t)n * (2 + 2 * (uint64_t)d) + 65536);
     uint64_t seg_cap = tzero ? 1024 : clamp_cap((uint64_t)n * (4 + (uint64_t)(1.5 * n3)) + 65536);
     T1Item* t1 = S.get<T1Item>(t1_cap);
+    uint32_t* t1_pairs = S.get<uint32_t>(t1_cap + 1);
     Stream* streams = S.get<Stream>(stream_cap);
+    uint32_t* stream_chunks = S.get<uint32_t>(stream_cap + 1);
     Seg* segs = S.get<Seg>(seg_cap);
-    HeavyItem* heavy = S.get<HeavyItem>(stream_cap);
 
     DevCfg cfg;
     memset(&cfg, 0, sizeof(cfg));
@@ -469,22 +471,21 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     cfg.t1 = t1;
     cfg.t1_count = counters + 1;
     cfg.t1_cap = (uint32_t)t1_cap;
+    cfg.t1_pairs = t1_pairs;
     cfg.streams = streams;
     cfg.stream_count = counters + 2;
     cfg.stream_cap = (uint32_t)stream_cap;
+    cfg.stream_chunks = stream_chunks;
     cfg.segs = segs;
     cfg.seg_count = counters + 3;
     cfg.seg_cap = (uint32_t)seg_cap;
-    cfg.heavy = heavy;
-    cfg.heavy_count = counters + 4;
-    cfg.heavy_cap = (uint32_t)stream_cap;
     cfg.error = counters + 5;
-    cfg.work_counter = counters + 8;
+    cfg.work64 = stats + kNumStats + 1;
 
     launch_rows(cfg, st);
     launch_enumerate(cfg, st);
+    unsigned int hc[4];  // rows, type-I items, streams, segments
     for (int attempt = 0;; ++attempt) {
-        unsigned int hc[4];
         CK(cudaMemcpyAsync(hc, counters, 4 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         const bool over = hc[1] > cfg.t1_cap || hc[2] > cfg.stream_cap || hc[3] > cfg.seg_cap;
@@ -493,12 +494,12 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
         if (hc[1] > cfg.t1_cap) {
             cfg.t1_cap = hc[1] + 1024;
             cfg.t1 = S.get<T1Item>(cfg.t1_cap);
+            cfg.t1_pairs = S.get<uint32_t>(cfg.t1_cap + 1);
         }
         if (hc[2] > cfg.stream_cap) {
             cfg.stream_cap = hc[2] + 1024;
             cfg.streams = S.get<Stream>(cfg.stream_cap);
-            cfg.heavy_cap = cfg.stream_cap;
-            cfg.heavy = S.get<HeavyItem>(cfg.heavy_cap);
+            cfg.stream_chunks = S.get<uint32_t>(cfg.stream_cap + 1);
         }
         if (hc[3] > cfg.seg_cap) {
             cfg.seg_cap = hc[3] + 1024;
@@ -509,12 +510,25 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
         launch_enumerate(cfg, st);
     }
     tm.mark();  // enumeration done
+    // exclusive prefixes of the pairs per type-I item and of the chunks per stream
+    // (one past the last entry holds the total)
+    {
+        const uint32_t n1 = std::min<uint32_t>(hc[1], cfg.t1_cap);
+        const uint32_t ns = std::min<uint32_t>(hc[2], cfg.stream_cap);
+        unsigned long long* t1_pre = S.get<unsigned long long>((size_t)n1 + 1);
+        unsigned long long* chunk_pre = S.get<unsigned long long>((size_t)ns + 1);
+        unsigned long long* tmp =
+            S.get<unsigned long long>(scan_tmp_words((int64_t)std::max(n1, ns) + 1));
+        CK(cudaMemsetAsync(cfg.t1_pairs + n1, 0, sizeof(uint32_t), st));
+        CK(cudaMemsetAsync(cfg.stream_chunks + ns, 0, sizeof(uint32_t), st));
+        launch_scan_u32_to_u64(cfg.t1_pairs, t1_pre, (int64_t)n1 + 1, tmp, st);
+        launch_scan_u32_to_u64(cfg.stream_chunks, chunk_pre, (int64_t)ns + 1, tmp, st);
+        cfg.t1_pre = t1_pre;
+        cfg.chunk_pre = chunk_pre;
+    }
     launch_type1(cfg, st);
     tm.mark();  // type I done
-    unsigned long long* total_chunks = stats + kNumStats + 1;
-    launch_streams(cfg, st);
-    launch_heavy_scan(cfg, total_chunks, st);
-    launch_heavy(cfg, total_chunks, st);
+    launch_type2(cfg, st);
     tm.mark();  // type II done
     unsigned long long hs[kNumStats + 1];
     CK(cudaMemcpyAsync(hs, stats, (kNumStats + 1) * sizeof(unsigned long long),
@@ -533,7 +547,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
 
 void finish_timing(Timer& tm) {
     for (int q = 0; q < 7; ++q) g_ms[q] = 0.0f;
-    // marks: 0 start, 1 reduce done, 2 tables, 3 sort, 4 enumerate, 5 type I, 6 heavy
+    // marks: 0 start, 1 reduce done, 2 tables, 3 sort, 4 enumerate, 5 type I, 6 type II
     for (int q = 1; q < tm.used && q <= 6; ++q) cudaEventElapsedTime(&g_ms[q - 1], tm.ev[q - 1], tm.ev[q]);
     if (tm.used >= 2) cudaEventElapsedTime(&g_ms[6], tm.ev[0], tm.ev[tm.used - 1]);
 }

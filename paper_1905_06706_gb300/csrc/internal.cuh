@@ -45,6 +45,10 @@ struct Stream {
                     // already drawn by the enumeration; 0xffffffff otherwise
     uint32_t pad;
 };
+// Work beyond the enumeration is balanced through exclusive prefixes: of the
+// pairs of the type-I items and of the chunks of the type-II streams.  A warp
+// takes the next range of pairs (chunks) from a 64-bit counter and finds the
+// item (stream) of its first pair (chunk) by a search in the prefix.
 
 // One partner set of a stream: its first sorted position and the number of
 // positions of the stream's earlier partner sets.
@@ -52,15 +56,9 @@ struct Seg {
     uint32_t b_begin, pre;
 };
 
-// A stream of several chunks.
-struct HeavyItem {
-    uint32_t stream;
-    uint32_t pad;
-    uint64_t chunk_prefix;  // chunk count, then its exclusive prefix (filled by a scan)
-};
 
 enum : int { kStatT1Pairs = 0, kStatCoins, kStatRecheck, kStatT2Items, kStatDraws,
-             kStatCands, kStatRows, kStatT1Items, kStatHeavyChunks, kStatEdges,
+             kStatCands, kStatRows, kStatT1Items, kStatT2Chunks, kStatEdges,
              kStatLaunches, kStatT1VertexRefs, kStatT1Edges, kNumStats };
 
 
@@ -110,17 +108,18 @@ struct DevCfg {
     T1Item* t1;
     unsigned int* t1_count;
     uint32_t t1_cap;
+    uint32_t* t1_pairs;                 // pairs per type-I item (a_len * b_len)
+    const unsigned long long* t1_pre;   // its exclusive prefix (t1 count + 1 entries)
     Stream* streams;
     unsigned int* stream_count;
     uint32_t stream_cap;
+    uint32_t* stream_chunks;             // chunks per stream (>= 1)
+    const unsigned long long* chunk_pre; // its exclusive prefix (stream count + 1 entries)
     Seg* segs;
     unsigned int* seg_count;
     uint32_t seg_cap;
-    HeavyItem* heavy;
-    unsigned int* heavy_count;
-    uint32_t heavy_cap;
     unsigned int* error;         // set when a stream needs 2^32 chunks or more
-    unsigned int* work_counter;  // dynamic scheduling counters [4]
+    unsigned long long* work64;  // [0] type-I pairs taken, [1] type-II chunks taken
 };
 
 // --------------------------------------------------------------- bit tricks

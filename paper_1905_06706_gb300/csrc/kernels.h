@@ -40,6 +40,9 @@ void launch_keys(int64_t n, int d, const double* w, const uint32_t* X, double w_
 // Exclusive scan of n uint32 values in place (out may alias in); tmp >= scan_tmp_words(n).
 size_t scan_tmp_words(int64_t n);
 void launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t st);
+// Exclusive scan of n uint32 counts into uint64 prefixes; tmp >= scan_tmp_words(n) uint64s.
+void launch_scan_u32_to_u64(const uint32_t* in, unsigned long long* out, int64_t n,
+                            unsigned long long* tmp, cudaStream_t st);
 // Stable LSD radix sort of (key, val) on the low `bits` bits of key.
 size_t radix_tmp_words(int64_t n);
 void radix_sort_pairs(uint32_t* key, uint32_t* val, uint32_t* key_alt, uint32_t* val_alt,
@@ -57,10 +60,9 @@ void launch_gather_hrg(int64_t n, const uint32_t* perm, const uint32_t* X, const
 // Pair sampling.
 void launch_rows(const DevCfg& cfg, cudaStream_t st);
 void launch_enumerate(const DevCfg& cfg, cudaStream_t st);
-void launch_streams(const DevCfg& cfg, cudaStream_t st);
+// Type I over the pair prefix cfg.t1_pre, type II over the chunk prefix cfg.chunk_pre.
 void launch_type1(const DevCfg& cfg, cudaStream_t st);
-void launch_heavy_scan(const DevCfg& cfg, unsigned long long* total_chunks, cudaStream_t st);
-void launch_heavy(const DevCfg& cfg, const unsigned long long* total_chunks, cudaStream_t st);
+void launch_type2(const DevCfg& cfg, cudaStream_t st);
 void launch_allpairs(const DevCfg& cfg, const uint32_t* X, const double* w, const float* sv,
                      cudaStream_t st);
 void launch_scale(int64_t n, const double* w, double log2W_half, float gamma, float invd,

@@ -23,8 +23,9 @@
 namespace gg {
 
 // ------------------------------------------------------------------ per-pair decisions
+// Per-thread event counts (statistics), summed per warp at the end of a kernel.
 struct Counters {
-    unsigned long long t1pairs = 0, coins = 0, recheck = 0, t2items = 0, draws = 0, cands = 0;
+    uint32_t t1pairs = 0, coins = 0, recheck = 0, t2items = 0, draws = 0, cands = 0;
 };
 
 struct View {  // per-vertex arrays indexed by position
@@ -204,11 +205,7 @@ __device__ bool accept_t2(const DevCfg& cfg, const View& V, uint32_t pu, uint32_
     return t2_exact(cfg, V, pu, pv, D, lo, hi, e.pbar);
 }
 
-// One chunk of a type-II stream (Sec. 3.2): geometric jumps under the bound pbar
-// over indices [start, start + len) of the stream's index space a S, with
-// candidate idx -> (a = idx / S, b = idx mod S), b located in the partner set
-// whose positions hold it; accepted as U' pbar < p_uv.
-// The geometric jump of one draw: 0 stop, 1 continue with *X.
+// The geometric jump of one draw (Sec. 3.2): 0 stop, 1 continue with *X.
 __device__ __forceinline__ int draw_jump(const DevCfg& cfg, const TwoEntry& e, const P4& o,
                                          unsigned long long rem, unsigned long long* X,
                                          Counters& C) {
@@ -221,47 +218,6 @@ __device__ __forceinline__ int draw_jump(const DevCfg& cfg, const TwoEntry& e, c
         r = jump64(o.x, o.y, e.Lb, rem, X);
     }
     return r;
-}
-
-// s_first: offset of the candidate of draw 0 when the caller already took that
-// draw (-1: start from draw 0).
-template <int DIM>
-__device__ void stream_chunk(const DevCfg& cfg, const View& V, WarpEdges& we, const Stream& st,
-                             const TwoEntry& e, uint32_t h, unsigned long long start,
-                             unsigned long long len, long long s_first, Counters& C) {
-    const unsigned long long tot = (unsigned long long)st.a_len * st.S;
-    long long s = -1;
-    for (uint32_t t = 0;; ++t) {
-        const P4 o = philox(st.A, st.pack, h, t, cfg.seed_lo, cfg.seed_hi);
-        if (t == 0 && s_first >= 0) {
-            s = s_first;
-        } else {
-            ++C.draws;
-            unsigned long long X;
-            if (draw_jump(cfg, e, o, len - (unsigned long long)(s + 1), &X, C) == 0) break;
-            s += 1 + (long long)X;
-        }
-        ++C.cands;
-        const unsigned long long idx = start + (unsigned long long)s;
-        uint32_t ia, ib;
-        if (tot <= 0xffffffffull) {
-            ia = (uint32_t)idx / st.S;
-            ib = (uint32_t)idx - ia * st.S;
-        } else {
-            ia = (uint32_t)(idx / st.S);
-            ib = (uint32_t)(idx - (unsigned long long)ia * st.S);
-        }
-        // last partner set with pre <= ib
-        uint32_t lo = 0, hi = st.seg_cnt;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (cfg.segs[st.seg_off + mid].pre <= ib) lo = mid; else hi = mid;
-        }
-        const Seg sg = cfg.segs[st.seg_off + lo];
-        const uint32_t pu = st.a_begin + ia, pv = sg.b_begin + (ib - sg.pre);
-        if (accept_t2<DIM>(cfg, V, pu, pv, o.z, o.w, e, C))
-            push_edge(cfg, we, vid(V, pu), vid(V, pv));
-    }
 }
 
 __device__ __forceinline__ void flush_counters(const DevCfg& cfg, const Counters& C) {
@@ -549,6 +505,15 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum2(DevCfg cfg) {
             for (int g = 0; g < 2; ++g) {
                 if (!keep[g]) continue;
                 if (st_base < cfg.stream_cap) {
+                    // chunks of 2^k indices; a stream needing 2^32 or more is an error
+                    const int k = cfg.tii[tidx[g]].k;
+                    const unsigned long long tot = (unsigned long long)x.a_len * sum[g];
+                    unsigned long long nch = (tot + (1ull << k) - 1) >> k;
+                    if (nch > 0xffffffffull) {
+                        atomicOr(cfg.error, 1u);
+                        nch = 1;
+                    }
+                    cfg.stream_chunks[st_base] = (uint32_t)nch;
                     Stream st;
                     st.A = x.A;
                     st.pack = pack[g];
@@ -656,8 +621,10 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum1(DevCfg cfg) {
                             it.a_begin = x.a_lo + ya;
                             it.a_len = (x.a_len - ya) < ac ? (x.a_len - ya) : ac;
                             it.b_begin = lo + yb;
-                            it.b_len = ((len - yb) < bc ? (len - yb) : bc) | tri;
+                            const uint32_t blen = (len - yb) < bc ? (len - yb) : bc;
+                            it.b_len = blen | tri;
                             cfg.t1[tbase] = it;
+                            cfg.t1_pairs[tbase] = it.a_len * blen;
                         }
                     }
                 }
@@ -678,96 +645,99 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum1(DevCfg cfg) {
     }
 }
 
-// ------------------------------------------------------------------ type-II streams
-// Single-chunk streams are sampled here (thread per stream); streams of several
-// chunks go to the heavy list.
-template <int DIM>
-__global__ void __launch_bounds__(kEnumThreads) k_streams(DevCfg cfg) {
-    __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
-    __shared__ unsigned int s_en[kWarps];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_en[warp] = 0;
-    __syncwarp();
-    WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
-    const View V = sorted_view(cfg);
-    Counters C;
-    const unsigned int count = *cfg.stream_count < cfg.stream_cap ? *cfg.stream_count : cfg.stream_cap;
-    const unsigned int stride = gridDim.x * blockDim.x;
-    for (unsigned int b0 = blockIdx.x * blockDim.x; b0 < count; b0 += stride) {
-        const unsigned int q = b0 + threadIdx.x;
-        if (q < count) {
-            const Stream st = cfg.streams[q];
-            const TwoEntry e = cfg.tii[st.tii];
-            const unsigned long long tot = (unsigned long long)st.a_len * st.S;
-            const unsigned long long nch = (tot + (1ull << e.k) - 1) >> e.k;
-            if (nch <= 1) {
-                stream_chunk<DIM>(cfg, V, we, st, e, 0u, 0ull, tot, (long long)st.s0, C);
-            } else if (nch > 0xffffffffull) {
-                atomicOr(cfg.error, 1u);  // chunk indices are 32-bit counter words
-            } else {
-                const unsigned int slot = atomicAdd(cfg.heavy_count, 1u);
-                if (slot < cfg.heavy_cap) cfg.heavy[slot] = HeavyItem{q, 0u, nch};
-            }
-        }
-        flush_edges(cfg, we, kEdgeBuf / 2);
+// ------------------------------------------------------------------ balanced work
+// Largest q in [0, nq) with pre[q] <= f, for a nondecreasing prefix with
+// pre[0] <= f < pre[nq]: a 32-way search in which the lanes test 32 pivots at
+// once, so about log_32(nq) dependent loads.  All lanes return the same q.
+__device__ __forceinline__ uint32_t warp_search(const unsigned long long* pre, uint32_t nq,
+                                                unsigned long long f) {
+    const int lane = threadIdx.x & 31;
+    uint32_t lo = 0, hi = nq;  // pre[lo] <= f < pre[hi]
+    while (hi - lo > 1) {
+        const uint32_t span = hi - lo;
+        const uint32_t piv = lo + (uint32_t)(((unsigned long long)span * (uint32_t)(lane + 1)) >> 5);
+        const bool ok = piv < hi && pre[piv] <= f;
+        const int k = __popc(__ballot_sync(0xffffffffu, ok));  // pivots 0 .. k-1 are <= f
+        const uint32_t nlo = __shfl_sync(0xffffffffu, piv, k > 0 ? k - 1 : 0);
+        const uint32_t nhi = __shfl_sync(0xffffffffu, piv, k < 31 ? k : 31);
+        if (k > 0) lo = nlo;
+        hi = nhi;
     }
-    flush_edges(cfg, we, 1);
-    flush_counters(cfg, C);
+    return lo;
+}
+
+// For each lane: the largest j in [0, 31] with v_j <= f, where v_j is lane j's
+// value, v is nondecreasing in the lane index and v_0 <= f.
+__device__ __forceinline__ int warp_last_le(unsigned long long v, unsigned long long f) {
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const unsigned long long x = __shfl_sync(0xffffffffu, v, j + step);
+        if (x <= f) j += step;
+    }
+    return j;
 }
 
 // ------------------------------------------------------------------ type I
+// Every pair of every type-I item (Algorithm 1: "emit each edge with p_uv").  The
+// pairs of all items form one index space through the exclusive prefix t1_pre;
+// a warp takes kT1Grab consecutive pairs at a time, so all warps end together
+// whatever the item sizes.  A round tests up to 32 consecutive pairs, lane f the
+// pair f0 + f, whose item it finds in a window of 32 consecutive items held one
+// per lane; the window starts at the item of f0 and the round stops at the end
+// of the window's last item.
 constexpr int kT1Threads = 256;
+constexpr unsigned kT1Grab = 1024;
 
 template <int DIM>
 __global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
     __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
     __shared__ unsigned int s_en[kWarps];
-    __shared__ uint32_t s_pref[kWarps][33];
-    __shared__ T1Item s_it[kWarps][32];
-    __shared__ float s_inv[kWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) s_en[warp] = 0;
     __syncwarp();
     WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
     const View V = sorted_view(cfg);
     Counters C;
-    const unsigned int count = *cfg.t1_count < cfg.t1_cap ? *cfg.t1_count : cfg.t1_cap;
-    unsigned long long t1_edges = 0;
+    const uint32_t nit = *cfg.t1_count < cfg.t1_cap ? *cfg.t1_count : cfg.t1_cap;
+    const unsigned long long* pre = cfg.t1_pre;
+    const unsigned long long total = pre[nit];
+    uint32_t t1_edges = 0;
     for (;;) {
-        unsigned int bundle = 0;
-        if (lane == 0) bundle = atomicAdd(&cfg.work_counter[1], 1u);
-        bundle = __shfl_sync(0xffffffffu, bundle, 0);
-        const unsigned long long first = (unsigned long long)bundle * 32ull;
-        if (first >= count) break;
-        const unsigned long long idx = first + lane;
-        T1Item it{0u, 0u, 0u, 0u};
-        if (idx < count) it = cfg.t1[idx];
-        const uint32_t bl0 = it.b_len & 0x7fffffffu;
-        const uint32_t work = it.a_len * bl0;
-        uint32_t incl = work;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        s_pref[warp][lane] = incl - work;
-        s_it[warp][lane] = it;
-        s_inv[warp][lane] = bl0 ? 1.0f / (float)bl0 : 0.0f;
-        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-        __syncwarp();
-        for (uint32_t f0 = 0; f0 < tot; f0 += 32) {
-            const uint32_t f = f0 + lane;
+        unsigned long long F0 = 0;
+        if (lane == 0) F0 = atomicAdd(&cfg.work64[0], (unsigned long long)kT1Grab);
+        F0 = __shfl_sync(0xffffffffu, F0, 0);
+        if (F0 >= total) break;
+        const unsigned long long F1 = F0 + kT1Grab < total ? F0 + kT1Grab : total;
+        uint32_t k = warp_search(pre, nit, F0), wk = 0xffffffffu;
+        unsigned long long wpre = 0, wend = 0;
+        T1Item wit{0u, 0u, 0u, 0u};
+        for (unsigned long long f0 = F0; f0 < F1;) {
+            if (k != wk) {  // window: items k .. k + 31 with their first and end pairs
+                const uint32_t q = k + (uint32_t)lane;
+                wpre = q <= nit ? pre[q] : ~0ull;
+                wend = q < nit ? pre[q + 1] : ~0ull;
+                if (q < nit) wit = cfg.t1[q];
+                wk = k;
+            }
+            // the round: pairs [f0, fe), at most 32 and inside the window
+            const unsigned long long wlast = __shfl_sync(0xffffffffu, wend, 31);
+            unsigned long long fe = f0 + 32;
+            if (fe > wlast) fe = wlast;
+            if (fe > F1) fe = F1;
+            const unsigned long long f = f0 + (unsigned long long)lane;
+            const int j = warp_last_le(wpre, f);
+            const uint32_t a_begin = __shfl_sync(0xffffffffu, wit.a_begin, j);
+            const uint32_t b_begin = __shfl_sync(0xffffffffu, wit.b_begin, j);
+            const uint32_t b_len = __shfl_sync(0xffffffffu, wit.b_len, j);
+            const unsigned long long pj = __shfl_sync(0xffffffffu, wpre, j);
             bool edge = false;
             uint32_t pu = 0, pv = 0;
-            if (f < tot) {
-                int k = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
-                    if (s_pref[warp][k + step] <= f) k += step;
-                const T1Item t = s_it[warp][k];
-                const uint32_t bl = t.b_len & 0x7fffffffu;
-                const uint32_t rr = f - s_pref[warp][k];
-                // rr / bl from a float reciprocal, corrected to the exact quotient
-                uint32_t ia = __float2uint_rz(__uint2float_rn(rr) * s_inv[warp][k]);
+            if (f < fe) {
+                const uint32_t bl = b_len & 0x7fffffffu;
+                const uint32_t rr = (uint32_t)(f - pj);
+                // rr / bl from a float reciprocal (rr < 2^24), corrected to the exact quotient
+                uint32_t ia = __float2uint_rz(__uint2float_rn(rr) * __frcp_rn((float)bl));
                 int ib = (int)rr - (int)(ia * bl);
                 if (ib < 0) {
                     --ia;
@@ -776,9 +746,9 @@ __global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
                     ++ia;
                     ib -= (int)bl;
                 }
-                pu = t.a_begin + ia;
-                pv = t.b_begin + (uint32_t)ib;
-                if (!((t.b_len & 0x80000000u) && pv <= pu)) {
+                pu = a_begin + ia;
+                pv = b_begin + (uint32_t)ib;
+                if (!((b_len & 0x80000000u) && pv <= pu)) {
                     ++C.t1pairs;
                     edge = decide_t1<DIM>(cfg, V, pu, pv, C);
                 }
@@ -788,53 +758,35 @@ __global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
                 ++t1_edges;
             }
             flush_edges(cfg, we, kEdgeBuf - 32);
+            // the next round starts in the first item that ends after fe
+            f0 = fe;
+            k += (uint32_t)__popc(__ballot_sync(0xffffffffu, wend <= fe));
         }
     }
     flush_edges(cfg, we, 1);
     flush_counters(cfg, C);
-    for (int o = 16; o > 0; o >>= 1) t1_edges += __shfl_down_sync(0xffffffffu, t1_edges, o);
-    if (lane == 0 && t1_edges) atomicAdd(&cfg.stats[kStatT1Edges], t1_edges);
+    unsigned long long te = t1_edges;
+    for (int o = 16; o > 0; o >>= 1) te += __shfl_down_sync(0xffffffffu, te, o);
+    if (lane == 0 && te) atomicAdd(&cfg.stats[kStatT1Edges], te);
 }
 
-// ------------------------------------------------------------------ heavy type II
-__global__ void k_heavy_scan(DevCfg cfg, unsigned long long* total_chunks) {
-    __shared__ unsigned long long s_w[32];
-    __shared__ unsigned long long s_carry;
-    const unsigned int cnt = *cfg.heavy_count < cfg.heavy_cap ? *cfg.heavy_count : cfg.heavy_cap;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (unsigned int b0 = 0; b0 < cnt; b0 += blockDim.x) {
-        const unsigned int i = b0 + threadIdx.x;
-        const unsigned long long v = i < cnt ? cfg.heavy[i].chunk_prefix : 0ull;
-        unsigned long long incl = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) s_w[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            const int nw = blockDim.x >> 5;
-            unsigned long long x = lane < nw ? s_w[lane] : 0ull, xi = x;
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long t = __shfl_up_sync(0xffffffffu, xi, o);
-                if (lane >= o) xi += t;
-            }
-            if (lane < nw) s_w[lane] = xi - x;
-        }
-        __syncthreads();
-        const unsigned long long excl = s_carry + s_w[warp] + incl - v;
-        if (i < cnt) cfg.heavy[i].chunk_prefix = excl;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) s_carry = excl + v;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *total_chunks = s_carry;
-}
+// ------------------------------------------------------------------ type II
+// Geometric jumps (Sec. 3.2) over every chunk of every type-II stream: chunk h of
+// a stream covers indices [h 2^k, min((h + 1) 2^k, a S)) of its index space
+// idx = a S + b (a in V_i^A, b in the concatenated partner sets), and draw t of
+// the chunk is Philox of (A, pack, h, t): words 0, 1 give the jump, words 2, 3
+// the acceptance U' pbar < p_uv.  Single-chunk streams whose draw 0 the
+// enumeration already took resume at draw 1 with its candidate s0.
+//
+// A lane works one chunk at a time and draws once per round; a lane whose chunk
+// ended takes the next chunk of the warp's bundle (32 consecutive chunks of the
+// global chunk space, fetched with one atomic and mapped to streams with one
+// warp search), so the lanes stay busy however unequal the chunks are.
+constexpr int kT2Threads = 256;
+constexpr int kT2RefillMin = 4;  // refill idle lanes once this many are idle
 
 template <int DIM>
-__global__ void __launch_bounds__(kEnumThreads) k_heavy(DevCfg cfg, const unsigned long long* total_chunks) {
+__global__ void __launch_bounds__(kT2Threads) k_type2(DevCfg cfg) {
     __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
     __shared__ unsigned int s_en[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -843,31 +795,120 @@ __global__ void __launch_bounds__(kEnumThreads) k_heavy(DevCfg cfg, const unsign
     WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
     const View V = sorted_view(cfg);
     Counters C;
-    const unsigned long long T = *total_chunks;
-    const unsigned int cnt = *cfg.heavy_count < cfg.heavy_cap ? *cfg.heavy_count : cfg.heavy_cap;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long g0 = (unsigned long long)blockIdx.x * blockDim.x; g0 < T; g0 += stride) {
-        const unsigned long long g = g0 + threadIdx.x;
-        if (g < T) {
-            unsigned int lo = 0, hi = cnt;  // last heavy stream with prefix <= g
-            while (hi - lo > 1) {
-                const unsigned int mid = (lo + hi) >> 1;
-                if (cfg.heavy[mid].chunk_prefix <= g) lo = mid; else hi = mid;
+    const uint32_t nst = *cfg.stream_count < cfg.stream_cap ? *cfg.stream_count : cfg.stream_cap;
+    const unsigned long long* pre = cfg.chunk_pre;
+    const unsigned long long total = pre[nst];
+    // the warp's bundle: lane j holds stream and chunk index of bundle chunk j
+    uint32_t bq = 0, bh = 0;
+    int bn = 0, bcur = 0;
+    bool drained = false;
+    // the lane's chunk
+    bool live = false, resumed = false;
+    Stream st{};
+    TwoEntry e{};
+    uint32_t h = 0, t = 0;
+    long long s = -1;
+    unsigned long long start = 0, len = 0;
+    bool small = true;  // index space below 2^32
+    for (;;) {
+        uint32_t idle = __ballot_sync(0xffffffffu, !live);
+        if (__popc(idle) >= kT2RefillMin || idle == 0xffffffffu) {
+            while (idle) {
+                if (bcur == bn) {
+                    if (drained) break;
+                    unsigned long long g0 = 0;
+                    if (lane == 0) g0 = atomicAdd(&cfg.work64[1], 32ull);
+                    g0 = __shfl_sync(0xffffffffu, g0, 0);
+                    if (g0 >= total) {
+                        drained = true;
+                        break;
+                    }
+                    if (g0 + 32 >= total) drained = true;
+                    // streams q0 .. q0 + 31 hold the bundle (every stream has a chunk)
+                    const uint32_t q0 = warp_search(pre, nst, g0);
+                    const uint32_t qw = q0 + (uint32_t)lane;
+                    const unsigned long long v = qw <= nst ? pre[qw] : ~0ull;
+                    const unsigned long long g = g0 + (unsigned long long)lane;
+                    const int j = warp_last_le(v, g);
+                    const unsigned long long base = __shfl_sync(0xffffffffu, v, j);
+                    bq = q0 + (uint32_t)j;
+                    bh = (uint32_t)(g - base);
+                    bn = (int)(total - g0 < 32ull ? total - g0 : 32ull);
+                    bcur = 0;
+                }
+                const int nidle = __popc(idle);
+                const int take = nidle < bn - bcur ? nidle : bn - bcur;
+                const int r = __popc(idle & lanemask_lt());
+                const int src = (bcur + r) & 31;
+                const uint32_t q = __shfl_sync(0xffffffffu, bq, src);
+                const uint32_t hh = __shfl_sync(0xffffffffu, bh, src);
+                if (((idle >> lane) & 1u) && r < take) {
+                    st = cfg.streams[q];
+                    e = cfg.tii[st.tii];
+                    const unsigned long long tot = (unsigned long long)st.a_len * st.S;
+                    small = tot <= 0xffffffffull;
+                    h = hh;
+                    start = (unsigned long long)h << e.k;
+                    len = tot - start < (1ull << e.k) ? tot - start : (1ull << e.k);
+                    t = 0;
+                    s = -1;
+                    resumed = st.s0 != 0xffffffffu;
+                    live = true;
+                }
+                bcur += take;
+                idle = __ballot_sync(0xffffffffu, !live);
             }
-            const HeavyItem hv = cfg.heavy[lo];
-            const Stream st = cfg.streams[hv.stream];
-            const TwoEntry e = cfg.tii[st.tii];
-            const unsigned long long h = g - hv.chunk_prefix;
-            const unsigned long long tot = (unsigned long long)st.a_len * st.S;
-            const unsigned long long start = h << e.k;
-            const unsigned long long len = (tot - start) < (1ull << e.k) ? (tot - start) : (1ull << e.k);
-            stream_chunk<DIM>(cfg, V, we, st, e, (uint32_t)h, start, len, -1ll, C);
         }
-        flush_edges(cfg, we, kEdgeBuf / 2);
+        if (!__any_sync(0xffffffffu, live)) {
+            if (drained && bcur == bn) break;
+            continue;
+        }
+        bool edge = false;
+        uint32_t pu = 0, pv = 0;
+        if (live) {
+            const P4 o = philox(st.A, st.pack, h, t, cfg.seed_lo, cfg.seed_hi);
+            bool cand = true;
+            if (t == 0 && resumed) {
+                s = (long long)st.s0;
+            } else {
+                ++C.draws;
+                unsigned long long X;
+                if (draw_jump(cfg, e, o, len - (unsigned long long)(s + 1), &X, C) == 0) {
+                    live = false;
+                    cand = false;
+                } else {
+                    s += 1 + (long long)X;
+                }
+            }
+            ++t;
+            if (cand) {
+                ++C.cands;
+                const unsigned long long idx = start + (unsigned long long)s;
+                uint32_t ia, ib;
+                if (small) {
+                    ia = (uint32_t)idx / st.S;
+                    ib = (uint32_t)idx - ia * st.S;
+                } else {
+                    ia = (uint32_t)(idx / st.S);
+                    ib = (uint32_t)(idx - (unsigned long long)ia * st.S);
+                }
+                uint32_t lo = 0, hi = st.seg_cnt;  // last partner set with pre <= ib
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (cfg.segs[st.seg_off + mid].pre <= ib) lo = mid; else hi = mid;
+                }
+                const Seg sg = cfg.segs[st.seg_off + lo];
+                pu = st.a_begin + ia;
+                pv = sg.b_begin + (ib - sg.pre);
+                edge = accept_t2<DIM>(cfg, V, pu, pv, o.z, o.w, e, C);
+            }
+        }
+        if (edge) push_edge(cfg, we, vid(V, pu), vid(V, pv));
+        flush_edges(cfg, we, kEdgeBuf - 32);
     }
     flush_edges(cfg, we, 1);
     flush_counters(cfg, C);
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cfg.stats[kStatHeavyChunks], T);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cfg.stats[kStatT2Chunks], total);
 }
 
 // ------------------------------------------------------------------ all pairs
@@ -928,41 +969,51 @@ void launch_enumerate(const DevCfg& cfg, cudaStream_t st) {
     }
 }
 
-void launch_streams(const DevCfg& cfg, cudaStream_t st) {
-    ++g_launches;
-    switch (cfg.d) {
-        case 1: k_streams<1><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
-        case 2: k_streams<2><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
-        case 3: k_streams<3><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
-        case 4: k_streams<4><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
-        default: k_streams<0><<<152 * 6, kEnumThreads, 0, st>>>(cfg); break;
-    }
+// Blocks of a persistent launch: the resident blocks per SM times the SMs.
+template <class K>
+static unsigned persistent_grid(K kernel, int threads) {
+    int dev = 0, sms = 152, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0) != cudaSuccess ||
+        per < 1)
+        per = 1;
+    return (unsigned)(sms * per);
 }
 
 void launch_type1(const DevCfg& cfg, cudaStream_t st) {
     ++g_launches;
     switch (cfg.d) {
-        case 1: k_type1<1><<<152 * 6, kT1Threads, 0, st>>>(cfg); break;
-        case 2: k_type1<2><<<152 * 6, kT1Threads, 0, st>>>(cfg); break;
-        case 3: k_type1<3><<<152 * 6, kT1Threads, 0, st>>>(cfg); break;
-        case 4: k_type1<4><<<152 * 6, kT1Threads, 0, st>>>(cfg); break;
-        default: k_type1<0><<<152 * 6, kT1Threads, 0, st>>>(cfg); break;
+#define GG_T1(D)                                                                     \
+    {                                                                                \
+        static const unsigned grid = persistent_grid(k_type1<D>, kT1Threads);        \
+        k_type1<D><<<grid, kT1Threads, 0, st>>>(cfg);                                \
+        break;                                                                       \
+    }
+        case 1: GG_T1(1)
+        case 2: GG_T1(2)
+        case 3: GG_T1(3)
+        case 4: GG_T1(4)
+        default: GG_T1(0)
+#undef GG_T1
     }
 }
 
-void launch_heavy_scan(const DevCfg& cfg, unsigned long long* total_chunks, cudaStream_t st) {
-    ++g_launches;
-    k_heavy_scan<<<1, 1024, 0, st>>>(cfg, total_chunks);
-}
-
-void launch_heavy(const DevCfg& cfg, const unsigned long long* total_chunks, cudaStream_t st) {
+void launch_type2(const DevCfg& cfg, cudaStream_t st) {
     ++g_launches;
     switch (cfg.d) {
-        case 1: k_heavy<1><<<152 * 4, kEnumThreads, 0, st>>>(cfg, total_chunks); break;
-        case 2: k_heavy<2><<<152 * 4, kEnumThreads, 0, st>>>(cfg, total_chunks); break;
-        case 3: k_heavy<3><<<152 * 4, kEnumThreads, 0, st>>>(cfg, total_chunks); break;
-        case 4: k_heavy<4><<<152 * 4, kEnumThreads, 0, st>>>(cfg, total_chunks); break;
-        default: k_heavy<0><<<152 * 4, kEnumThreads, 0, st>>>(cfg, total_chunks); break;
+#define GG_T2(D)                                                                     \
+    {                                                                                \
+        static const unsigned grid = persistent_grid(k_type2<D>, kT2Threads);        \
+        k_type2<D><<<grid, kT2Threads, 0, st>>>(cfg);                                \
+        break;                                                                       \
+    }
+        case 1: GG_T2(1)
+        case 2: GG_T2(2)
+        case 3: GG_T2(3)
+        case 4: GG_T2(4)
+        default: GG_T2(0)
+#undef GG_T2
     }
 }
 

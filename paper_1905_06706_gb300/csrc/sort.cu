@@ -33,65 +33,69 @@ __global__ void k_keys(int64_t n, int d, const double* __restrict__ w, const uin
 }
 
 // ------------------------------------------------------------------ scan
+// Exclusive scans: 32-bit counts into 32- or 64-bit prefixes (reduce per tile,
+// scan of the tile sums, down-sweep).
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* s_warp,
-                                                         uint32_t* total) {
+template <class T>
+__device__ __forceinline__ T block_exclusive_scan(T x, T* s_warp, T* total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t incl = x;
+    T incl = x;
     for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        const T t = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += t;
     }
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
     if (warp == 0) {
         const int nw = blockDim.x >> 5;
-        uint32_t v = lane < nw ? s_warp[lane] : 0u;
-        uint32_t vi = v;
+        T v = lane < nw ? s_warp[lane] : T(0);
+        T vi = v;
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, vi, o);
+            const T t = __shfl_up_sync(0xffffffffu, vi, o);
             if (lane >= o) vi += t;
         }
         if (lane < nw) s_warp[lane] = vi - v;
         if (lane == 31) s_warp[32] = vi;
     }
     __syncthreads();
-    const uint32_t r = s_warp[warp] + incl - x;
+    const T r = s_warp[warp] + incl - x;
     *total = s_warp[32];
     __syncthreads();
     return r;
 }
 
-__global__ void k_scan_reduce(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ sums) {
-    __shared__ uint32_t s_warp[33];
+template <class Tin, class T>
+__global__ void k_scan_reduce(const Tin* __restrict__ in, int64_t n, T* __restrict__ sums) {
+    __shared__ T s_warp[33];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    uint32_t acc = 0;
+    T acc = 0;
     for (int it = 0; it < kScanItems; ++it) {
         const int64_t i = base + (int64_t)it * kScanThreads + threadIdx.x;
-        if (i < n) acc += in[i];
+        if (i < n) acc += (T)in[i];
     }
-    uint32_t total;
-    block_exclusive_scan(acc, s_warp, &total);
+    T total;
+    block_exclusive_scan<T>(acc, s_warp, &total);
     if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
-__global__ void k_scan_down(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n,
-                            const uint32_t* __restrict__ prefix) {
-    __shared__ uint32_t s_warp[33];
+template <class Tin, class T>
+__global__ void k_scan_down(const Tin* __restrict__ in, T* __restrict__ out, int64_t n,
+                            const T* __restrict__ prefix) {
+    __shared__ T s_warp[33];
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    uint32_t v[kScanItems];
-    uint32_t acc = 0;
+    T v[kScanItems];
+    T acc = 0;
 #pragma unroll
     for (int it = 0; it < kScanItems; ++it) {
         const int64_t i = base + it;
-        v[it] = i < n ? in[i] : 0u;
+        v[it] = i < n ? (T)in[i] : T(0);
         acc += v[it];
     }
-    uint32_t total;
-    uint32_t run = block_exclusive_scan(acc, s_warp, &total) + (prefix ? prefix[blockIdx.x] : 0u);
+    T total;
+    T run = block_exclusive_scan<T>(acc, s_warp, &total) + (prefix ? prefix[blockIdx.x] : T(0));
 #pragma unroll
     for (int it = 0; it < kScanItems; ++it) {
         const int64_t i = base + it;
@@ -110,20 +114,30 @@ size_t scan_tmp_words(int64_t n) {
     return words + 64;
 }
 
-void launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t st) {
+template <class Tin, class T>
+static void scan_impl(const Tin* in, T* out, int64_t n, T* tmp, cudaStream_t st) {
     if (n <= 0) return;
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
     if (nb == 1) {
         ++g_launches;
-        k_scan_down<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
+        k_scan_down<Tin, T><<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
         return;
     }
-    uint32_t* sums = tmp;
+    T* sums = tmp;
     ++g_launches;
-    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums);
-    launch_scan_u32(sums, sums, nb, tmp + nb + 32, st);
+    k_scan_reduce<Tin, T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums);
+    scan_impl<T, T>(sums, sums, nb, tmp + nb + 32, st);
     ++g_launches;
-    k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums);
+    k_scan_down<Tin, T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums);
+}
+
+void launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t st) {
+    scan_impl<uint32_t, uint32_t>(in, out, n, tmp, st);
+}
+
+void launch_scan_u32_to_u64(const uint32_t* in, unsigned long long* out, int64_t n,
+                            unsigned long long* tmp, cudaStream_t st) {
+    scan_impl<uint32_t, unsigned long long>(in, out, n, tmp, st);
 }
 
 // ------------------------------------------------------------------ radix sort
