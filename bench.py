@@ -53,6 +53,33 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def kernel_source_digest() -> str:
+    """SHA-256 (16 hex digits) of the sources the sampling kernels are built from."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("pairs.cu", "internal.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1905_06706_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, when the
+    summary was taken from the current source of the sampling kernels (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_girg_d2_n1e6.md")
+    try:
+        digest = kernel_source_digest()
+        with open(path) as f:
+            for ln in f:
+                if ln.startswith("traffic_bytes_per_launch:"):
+                    parts = ln.split()
+                    if len(parts) >= 4 and parts[2] == "kernel-source-sha256" and parts[3] == digest:
+                        return int(parts[1])
+    except (OSError, ValueError):
+        pass
+    return None
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -269,21 +296,27 @@ def main():
         e2e_value = (float(allv[:, 3].sum()) / float(allv[:, 2].max())) if ms_e2e else None
         fp64_value = (float(allv[:, 5].sum()) / float(allv[:, 4].max())) if ms64 else None
         m_step = m_total / args.steps
-        # dominant kernel: the largest phase among the single-kernel phases
+        # dominant kernel: the longer of the two single-kernel sampling phases
         ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
         hbm, peak_kind = _peaks()
         eb = cfg["edge_bytes"] * 2
-        # type-I kernel algorithmic bytes per launch: its item list (16 B per item),
-        # the vertex records of every item side (4d + 4 + 4 B: coordinates, scale, id)
-        # and its edges; see the design doc section 5 for the per-unit figures
-        t1_items = stats["type1_items"]
-        t1_bytes = 16 * t1_items + stats.get("type1_vertex_refs", 0) * (4 * d + 8) + \
-            eb * stats.get("type1_edges", 0)
-        t1_ms = ph["type1"]
-        roof = {"kernel": "k_type1", "bound": "hbm",
-                "achieved": (t1_bytes / (t1_ms / 1e3)) / 1e9 if t1_ms > 0 else None,
-                "peak": hbm, "unit": "GB/s", "traffic": None,
-                "peak_kind": peak_kind}
+        vrec = 4 * d + 8  # coordinates, scale, id of one vertex
+        t2_edges = stats["edges"] - stats["type1_edges"]
+        # algorithmic bytes per launch (per-unit figures in the design doc section 6)
+        algo = {
+            "k_type1": (24 * stats["type1_items"] + vrec * stats["type1_vertex_refs"] +
+                        eb * stats["type1_edges"], ph["type1"]),
+            "k_type2": (48 * stats["type2_streams"] +
+                        (8 + 2 * vrec) * stats["type2_candidates"] + eb * t2_edges,
+                        ph["type2"]),
+        }
+        kname = max(algo, key=lambda k: algo[k][1])
+        kbytes, kms = algo[kname]
+        traffic = _ncu_traffic(kname)
+        roof = {"kernel": kname, "bound": "hbm",
+                "achieved": (kbytes / (kms / 1e3)) / 1e9 if kms > 0 else None,
+                "peak": hbm, "unit": "GB/s", "traffic": traffic,
+                "peak_kind": peak_kind, "algorithmic_bytes": kbytes, "launch_ms": kms}
         if roof["achieved"] is not None:
             roof["frac"] = roof["achieved"] / hbm
         edge_roof = (m_step * eb / (statistics.mean(ms) / 1e3)) / 1e9

@@ -162,8 +162,8 @@ int girg_expected_avg_degree(const girg_params* params, double* avg_deg, void* s
  * [1] coins drawn, [2] FP64 rechecks, [3] type-II items (non-empty cell pairs),
  * [4] jump draws, [5] type-II candidates, [6] rows, [7] type-I items, [8] chunks of
  * all type-II streams, [9] edges, [10] kernel launches, [11] vertex references of the type-I items
- * (sum of both side lengths), [12] type-I edges.  Copies min(len, 13) values; returns
- * the number copied. */
+ * (sum of both side lengths), [12] type-I edges, [13] type-II streams.  Copies
+ * min(len, 14) values; returns the number copied. */
 int girg_last_stats(int64_t* out, int32_t len);
 
 /* Milliseconds spent in each phase of the last call on this host thread

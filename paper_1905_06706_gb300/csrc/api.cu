@@ -512,9 +512,9 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     tm.mark();  // enumeration done
     // exclusive prefixes of the pairs per type-I item and of the chunks per stream
     // (one past the last entry holds the total)
+    const uint32_t ns = std::min<uint32_t>(hc[2], cfg.stream_cap);
     {
         const uint32_t n1 = std::min<uint32_t>(hc[1], cfg.t1_cap);
-        const uint32_t ns = std::min<uint32_t>(hc[2], cfg.stream_cap);
         unsigned long long* t1_pre = S.get<unsigned long long>((size_t)n1 + 1);
         unsigned long long* chunk_pre = S.get<unsigned long long>((size_t)ns + 1);
         unsigned long long* tmp =
@@ -540,6 +540,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     if (rc[5]) throw Status{GIRG_E_INTERNAL};
     hs[kStatRows] = rc[0];
     hs[kStatEdges] = hs[kNumStats];
+    hs[kStatStreams] = ns;
     for (int q = 0; q < kNumStats; ++q) g_stats[q] = (int64_t)hs[q];
     g_stats[kStatLaunches] = (int64_t)g_launches;
     *num_edges = (int64_t)hs[kNumStats];
