@@ -95,6 +95,8 @@ def _load():
                                         i64, P, i32, i32]),
             "orc_girg_avg_degree": (dbl, [dbl, i64, i32, dbl, P, dbl]),
             "orc_girg_solve_c": (dbl, [dbl, i64, i32, dbl, P, dbl]),
+            "orc_hrg_avg_degree": (dbl, [i64, dbl, dbl, dbl]),
+            "orc_hrg_solve_R": (dbl, [i64, dbl, dbl, dbl]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -363,6 +365,16 @@ def girg_solve_c(target, w, d, T, W=None):
     if W is None:
         W = exact_sum(w)
     return _load().orc_girg_solve_c(target, len(w), d, T, _ptr(w), W)
+
+
+def hrg_avg_degree(n, alpha, T, R):
+    """Expected average degree of an HRG (radius R), by quadrature of its definition."""
+    return _load().orc_hrg_avg_degree(n, alpha, T, R)
+
+
+def hrg_solve_R(n, alpha, T, target):
+    """The disk radius R with expected average degree ``target`` (bisection)."""
+    return _load().orc_hrg_solve_R(n, alpha, T, target)
 
 
 def edge_set(edges) -> set:

@@ -61,6 +61,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
 #define TAG_WEIGHT 0x57454947u
 #define TAG_POS 0x504F5349u
 #define TAG_RADIUS 0x52414449u
@@ -1346,5 +1350,231 @@ double orc_girg_solve_c(double target, int64_t n, int d, double T, const double*
             hi = mid;
     }
     deg_free(&G);
+    return 0.5 * (lo + hi);
+}
+
+/* ------------------------------------------------------------------ HRG degree
+ * The paper states only that R = 2 ln n + C with C setting the average degree
+ * (Sec. 2.2); the oracle computes the expected average degree from the model's
+ * definition.  Two vertices are independent with radius density
+ * alpha sinh(alpha r) / (cosh(alpha R) - 1) on [0, R] and uniform angles, so
+ * E[deg] = (n - 1) P(edge).  With G(t) = P(dist < t) for two random vertices:
+ *   T = 0:  P(edge) = G(R)  (edge iff dist < R);
+ *   T > 0:  P(edge) = E[p_T(dist)] = E[G(t)] for t logistic with location R and
+ *           scale 2T, since p_T(x) = 1/(exp((x - R)/2T) + 1) is the probability
+ *           that such a t exceeds x.
+ * G(t) = int int f(r1) f(r2) Phi(r1, r2, t) dr1 dr2, where Phi is the fraction of
+ * angle differences in [0, pi] with dist < t: 1 if t >= r1 + r2, 0 if
+ * t <= |r1 - r2|, else (2/pi) asin(sqrt((cosh t - cosh(r1 - r2)) /
+ * (2 sinh r1 sinh r2))) by the law of cosines of Sec. 2.2.
+ *
+ * Quadrature: in y = R - r; every interval between the points where Phi stops
+ * being smooth is mapped by y = a + (b - a)(1 - cos s)/2, s in [0, pi] (which
+ * absorbs the square-root behaviour of Phi at those points) and integrated by
+ * composite Gauss-Legendre rules; the region where Phi = 1 uses the radial CDF
+ * in closed form.  The t integral uses the same rule on panels growing
+ * geometrically away from R, truncated where the logistic weight is below
+ * e^-40. */
+
+#define HRG_GL_M 8     /* Gauss-Legendre points per panel */
+#define HRG_Y_PANELS 4 /* panels per smooth interval in y */
+#define HRG_T_PANELS 2 /* panels per t interval */
+
+static double hrg_glx[HRG_GL_M], hrg_glw[HRG_GL_M];
+static int hrg_gl_ready = 0;
+
+/* Nodes and weights of the m-point Gauss-Legendre rule on [-1, 1], by Newton's
+ * method on the Legendre polynomial P_m (three-term recurrence). */
+static void gauss_legendre(int m, double* x, double* w) {
+    for (int i = 0; i < m; i++) {
+        double z = cos(M_PI * (i + 0.75) / (m + 0.5)), pm = 0.0, dp = 0.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= m; k++) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            pm = p1;
+            dp = m * (z * p1 - p0) / (z * z - 1.0);
+            double dz = pm / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= m; k++) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = m * (z * p1 - p0) / (z * z - 1.0);
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+typedef struct {
+    double alpha, R, chR; /* chR = cosh(alpha R) - 1 */
+} hrg_radial;
+
+/* density and CDF of y = R - r */
+static double hrg_fy(const hrg_radial* H, double y) {
+    return H->alpha * sinh(H->alpha * (H->R - y)) / H->chR;
+}
+static double hrg_Fy(const hrg_radial* H, double y) {
+    return (H->chR - (cosh(H->alpha * (H->R - y)) - 1.0)) / H->chR;
+}
+
+static double hrg_phi(double r1, double r2, double t, double cht) {
+    if (t >= r1 + r2) return 1.0;
+    if (t <= fabs(r1 - r2)) return 0.0;
+    double s = (cht - cosh(r1 - r2)) / (2.0 * sinh(r1) * sinh(r2));
+    if (s <= 0.0) return 0.0;
+    if (s >= 1.0) return 1.0;
+    return (2.0 / M_PI) * asin(sqrt(s));
+}
+
+/* int_a^b g(y) dy with y = a + (b - a)(1 - cos s)/2 and `panels` Gauss-Legendre
+ * panels on s in [0, pi]: fills nodes and weights, returns their number. */
+static int cos_rule(double a, double b, int panels, double* y, double* wt) {
+    int k = 0;
+    for (int p = 0; p < panels; p++) {
+        double s0 = M_PI * p / panels, s1 = M_PI * (p + 1) / panels;
+        for (int i = 0; i < HRG_GL_M; i++) {
+            double s = 0.5 * (s0 + s1) + 0.5 * (s1 - s0) * hrg_glx[i];
+            y[k] = a + (b - a) * (1.0 - cos(s)) * 0.5;
+            wt[k] = 0.5 * (s1 - s0) * hrg_glw[i] * (b - a) * 0.5 * sin(s);
+            k++;
+        }
+    }
+    return k;
+}
+
+/* G(t) = P(dist < t) for two independent random vertices. */
+static double hrg_dist_cdf(const hrg_radial* H, double t) {
+    const double R = H->R;
+    if (t <= 0.0) return 0.0;
+    if (t >= 2.0 * R) return 1.0;
+    const double cht = cosh(t);
+    double bp[5];
+    int nb = 0;
+    bp[nb++] = 0.0;
+    double cand[3] = {R - t, 2.0 * R - t, t};
+    for (int q = 0; q < 3; q++)
+        if (cand[q] > 0.0 && cand[q] < R) bp[nb++] = cand[q];
+    bp[nb++] = R;
+    for (int a = 1; a < nb; a++) /* sort the few breakpoints */
+        for (int b = a; b > 0 && bp[b] < bp[b - 1]; b--) {
+            double tmp = bp[b];
+            bp[b] = bp[b - 1];
+            bp[b - 1] = tmp;
+        }
+    double y1s[HRG_Y_PANELS * HRG_GL_M], w1s[HRG_Y_PANELS * HRG_GL_M];
+    double y2s[HRG_Y_PANELS * HRG_GL_M], w2s[HRG_Y_PANELS * HRG_GL_M];
+    double total = 0.0;
+    for (int iv = 0; iv + 1 < nb; iv++) {
+        if (!(bp[iv + 1] > bp[iv])) continue;
+        int k1 = cos_rule(bp[iv], bp[iv + 1], HRG_Y_PANELS, y1s, w1s);
+        for (int a = 0; a < k1; a++) {
+            double y1 = y1s[a], r1 = R - y1;
+            double c1 = y1 - t > 0.0 ? y1 - t : 0.0; /* Phi > 0 only for y2 in (c1, c2) */
+            double c2 = y1 + t < R ? y1 + t : R;
+            double b1 = 2.0 * R - t - y1; /* Phi = 1 for y2 >= b1 */
+            if (!(c2 > c1)) continue;
+            double inner = 0.0;
+            if (b1 <= c1) {
+                inner = hrg_Fy(H, c2) - hrg_Fy(H, c1);
+            } else {
+                double hi = c2 < b1 ? c2 : b1;
+                int k2 = cos_rule(c1, hi, HRG_Y_PANELS, y2s, w2s);
+                for (int b = 0; b < k2; b++)
+                    inner += w2s[b] * hrg_fy(H, y2s[b]) * hrg_phi(r1, R - y2s[b], t, cht);
+                if (b1 < c2) inner += hrg_Fy(H, c2) - hrg_Fy(H, b1);
+            }
+            total += w1s[a] * hrg_fy(H, y1) * inner;
+        }
+    }
+    return total;
+}
+
+/* Probability of an edge between two random vertices. */
+static double hrg_edge_prob(double alpha, double T, double R) {
+    if (!hrg_gl_ready) {
+        gauss_legendre(HRG_GL_M, hrg_glx, hrg_glw);
+        hrg_gl_ready = 1;
+    }
+    hrg_radial H = {alpha, R, cosh(alpha * R) - 1.0};
+    if (T == 0.0) return hrg_dist_cdf(&H, R);
+    /* logistic density of t: e / (2T (1 + e)^2), e = exp(-|t - R| / 2T) */
+    const double s = 2.0 * T, lo = R - 40.0 * s > 0.0 ? R - 40.0 * s : 0.0;
+    const double hi = R + 40.0 * s < 2.0 * R ? R + 40.0 * s : 2.0 * R;
+    double edges_t[2 * 64 + 2];
+    int ne = 0;
+    double ws = s;
+    double x = R;
+    double left[64];
+    int nl = 0;
+    while (x > lo && nl < 64) {
+        x = x - ws > lo ? x - ws : lo;
+        left[nl++] = x;
+        ws *= 2.0;
+    }
+    for (int q = nl - 1; q >= 0; q--) edges_t[ne++] = left[q];
+    edges_t[ne++] = R;
+    x = R;
+    ws = s;
+    while (x < hi && ne < 2 * 64 + 1) {
+        x = x + ws < hi ? x + ws : hi;
+        edges_t[ne++] = x;
+        ws *= 2.0;
+    }
+    double ts[HRG_T_PANELS * HRG_GL_M], wts[HRG_T_PANELS * HRG_GL_M];
+    double total = 0.0;
+    for (int q = 0; q + 1 < ne; q++) {
+        if (!(edges_t[q + 1] > edges_t[q])) continue;
+        int k = cos_rule(edges_t[q], edges_t[q + 1], HRG_T_PANELS, ts, wts);
+        for (int a = 0; a < k; a++) {
+            double e = exp(-fabs(ts[a] - R) / s);
+            double dens = e / (s * (1.0 + e) * (1.0 + e));
+            total += wts[a] * dens * hrg_dist_cdf(&H, ts[a]);
+        }
+    }
+    /* t above the truncation: G = 1 there when hi = 2R, and the logistic mass
+     * beyond R + 40 s is below e^-40 otherwise */
+    double eh = exp(-(hi - R) / s);
+    total += eh / (1.0 + eh);
+    return total;
+}
+
+double orc_hrg_avg_degree(int64_t n, double alpha, double T, double R) {
+    return (double)(n - 1) * hrg_edge_prob(alpha, T, R);
+}
+
+/* The R with expected average degree `target`: E[deg] decreases in R; bracket by
+ * unit steps from 2 ln n, then bisect to a relative width of 1e-12. */
+double orc_hrg_solve_R(int64_t n, double alpha, double T, double target) {
+    double lo = 2.0 * log((double)n), hi = lo;
+    if (orc_hrg_avg_degree(n, alpha, T, lo) >= target) {
+        hi = lo + 1.0;
+        while (orc_hrg_avg_degree(n, alpha, T, hi) >= target && hi < 600.0) {
+            lo = hi;
+            hi += 1.0;
+        }
+    } else {
+        lo = hi - 1.0;
+        while (lo > 1e-3 && orc_hrg_avg_degree(n, alpha, T, lo) < target) {
+            hi = lo;
+            lo = lo - 1.0 > 1e-3 ? lo - 1.0 : 1e-3;
+        }
+    }
+    for (int it = 0; it < 200 && hi - lo > 1e-12 * hi; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (orc_hrg_avg_degree(n, alpha, T, mid) >= target)
+            lo = mid;
+        else
+            hi = mid;
+    }
     return 0.5 * (lo + hi);
 }
