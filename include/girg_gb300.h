@@ -76,13 +76,16 @@ typedef struct {
 /* HRG parameters (Sec. 2.2).
  *   alpha      radial dispersion, alpha > 1/2 (power-law exponent 2 alpha + 1)
  *   T          temperature, 0 <= T < 1
- *   R          disk radius R = 2 ln n + C (Sec. 2.2), > 0; C sets the average degree
+ *   avg_deg    target expected average degree, used when R <= 0 (0 < avg_deg < n - 1)
+ *   R          disk radius R = 2 ln n + C (Sec. 2.2); R <= 0: solved from avg_deg
+ *              (hrg_solve_radius)
  *   other fields as for girg_params.
  */
 typedef struct {
     int64_t n;
     double alpha;
     double T;
+    double avg_deg;
     double R;
     uint64_t seed;
     int32_t edge_bytes;
@@ -109,9 +112,24 @@ int girg_generate_from_points(int64_t n, int32_t d, const uint32_t* d_X, const d
                               int32_t level_cap, int32_t edge_bytes, void* d_edges,
                               int64_t capacity_edges, int64_t* num_edges, void* stream);
 
-/* Generate one HRG (Sec. 2.2) through the HRG -> GIRG mapping (Sec. 2.3). */
+/* Generate one HRG (Sec. 2.2) through the HRG -> GIRG mapping (Sec. 2.3).
+ *   R_used   host out (may be NULL): the disk radius used (params->R, or the solved one)
+ * Other arguments and errors as for girg_generate. */
 int hrg_generate(const hrg_params* params, void* d_edges, int64_t capacity_edges,
-                 int64_t* num_edges, void* stream);
+                 int64_t* num_edges, double* R_used, void* stream);
+
+/* Expected average degree of an HRG with n vertices, dispersion alpha, temperature T
+ * and disk radius R (host computation, no GPU).  The paper gives no formula (Sec. 2.2:
+ * R = 2 ln n + C, C sets the degree); this is (n - 1) P(edge) for two random vertices,
+ * P(edge) = P(dist < R) at T = 0 and E[P(dist < t)] for t logistic with location R
+ * and scale 2T at T > 0, by numerical quadrature (relative error about 1e-11).
+ * Errors: GIRG_E_PARAM (n < 2, alpha <= 1/2, T outside [0, 1), R outside (0, 350]). */
+int hrg_expected_avg_degree(int64_t n, double alpha, double T, double R, double* avg_deg);
+
+/* The disk radius R whose expected average degree (hrg_expected_avg_degree) equals
+ * avg_deg, to 1e-13 relative (host computation, no GPU).
+ * Errors: GIRG_E_PARAM (as above, or avg_deg outside (0, n - 1) or unreachable). */
+int hrg_solve_radius(int64_t n, double alpha, double T, double avg_deg, double* R);
 
 /* The quadratic all-pairs generator (Table 1, "Pairwise") on the device: every
  * pair u < v is tested with the same per-pair coin as the type-I tests.  Inputs as

@@ -41,7 +41,7 @@ class GirgParams(ctypes.Structure):
 
 class HrgParams(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("alpha", ctypes.c_double), ("T", ctypes.c_double),
-                ("R", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("avg_deg", ctypes.c_double), ("R", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("edge_bytes", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("level_cap", ctypes.c_int32)]
 
@@ -56,7 +56,9 @@ SIGNATURES = {
     "girg_generate": (I32, [P, P, I64, P, P, P]),
     "girg_generate_from_points": (I32, [I64, I32, P, P, DBL, DBL, U64, I32, I32, I32, P, I64, P,
                                         P]),
-    "hrg_generate": (I32, [P, P, I64, P, P]),
+    "hrg_generate": (I32, [P, P, I64, P, P, P]),
+    "hrg_expected_avg_degree": (I32, [I64, DBL, DBL, DBL, P]),
+    "hrg_solve_radius": (I32, [I64, DBL, DBL, DBL, P]),
     "girg_allpairs": (I32, [I64, I32, P, P, DBL, DBL, DBL, U64, I32, I32, P, I64, P, P]),
     "girg_allpairs_noalloc": (I32, [I64, I32, P, P, DBL, DBL, DBL, U64, I32, I32, P, I64, P,
                                     P]),
@@ -135,6 +137,7 @@ class Result:
     status: int
     num_edges: int
     c_used: float = float("nan")
+    R_used: float = float("nan")
 
 
 def girg_generate(edges, *, n, d, beta, T, avg_deg=0.0, c=0.0, w_min=1.0, seed=1,
@@ -164,15 +167,36 @@ def girg_generate_from_points(edges, X, w, *, T, c, seed=1, precision=PRECISION_
     return Result(st, m.value, c)
 
 
-def hrg_generate(edges, *, n, alpha, T, R, seed=1, precision=PRECISION_FP32, level_cap=0,
-                 stream=None) -> Result:
+def hrg_generate(edges, *, n, alpha, T, R=0.0, avg_deg=0.0, seed=1, precision=PRECISION_FP32,
+                 level_cap=0, stream=None) -> Result:
+    """Generate an HRG into ``edges``; R <= 0 solves the radius from ``avg_deg``.
+    The radius used is returned in ``R_used``."""
     _torch()
     lib = load()
-    p = HrgParams(n, alpha, T, R, seed, edges.element_size(), precision, level_cap)
+    p = HrgParams(n, alpha, T, avg_deg, R, seed, edges.element_size(), precision, level_cap)
     m = ctypes.c_int64(0)
+    r_used = ctypes.c_double(float("nan"))
     st = lib.hrg_generate(ctypes.byref(p), _ptr(edges), edges.shape[0], ctypes.byref(m),
-                          _stream(stream))
-    return Result(st, m.value)
+                          ctypes.byref(r_used), _stream(stream))
+    return Result(st, m.value, R_used=r_used.value)
+
+
+def hrg_expected_avg_degree(n, alpha, T, R) -> float:
+    """Expected average degree of an HRG (host computation, no GPU needed)."""
+    out = ctypes.c_double(0.0)
+    st = load().hrg_expected_avg_degree(n, alpha, T, R, ctypes.byref(out))
+    if st != GIRG_OK:
+        raise GirgError(st, "hrg_expected_avg_degree")
+    return out.value
+
+
+def hrg_solve_radius(n, alpha, T, avg_deg) -> float:
+    """Disk radius R with the given expected average degree (host computation)."""
+    out = ctypes.c_double(0.0)
+    st = load().hrg_solve_radius(n, alpha, T, avg_deg, ctypes.byref(out))
+    if st != GIRG_OK:
+        raise GirgError(st, "hrg_solve_radius")
+    return out.value
 
 
 def girg_allpairs(edges, X, w, *, W, T, c, seed=1, precision=PRECISION_FP32,

@@ -851,16 +851,38 @@ int girg_sorted_order(int64_t n, int32_t d, const uint32_t* d_X, const double* d
                             d_order, stream);
 }
 
-int hrg_generate(const hrg_params* params, void* d_edges, int64_t capacity_edges,
-                 int64_t* num_edges, void* stream) {
-    if (!params || !num_edges || capacity_edges < 0) return GIRG_E_PARAM;
-    const hrg_params& q = *params;
-    if (q.n < 2 || q.n >= (1ll << 31) || !(q.alpha > 0.5) || !(q.T >= 0.0 && q.T < 1.0) ||
-        !(q.R > 0.0))
+static bool hrg_shape_ok(int64_t n, double alpha, double T) {
+    return n >= 2 && n < (1ll << 31) && alpha > 0.5 && alpha < 1e6 && T >= 0.0 && T < 1.0;
+}
+
+int hrg_expected_avg_degree(int64_t n, double alpha, double T, double R, double* avg_deg) {
+    if (!avg_deg || !hrg_shape_ok(n, alpha, T) || !(R > 0.0 && R <= 350.0)) return GIRG_E_PARAM;
+    *avg_deg = hrg_expected_degree(n, alpha, T, R);
+    return GIRG_OK;
+}
+
+int hrg_solve_radius(int64_t n, double alpha, double T, double avg_deg, double* R) {
+    if (!R || !hrg_shape_ok(n, alpha, T) || !(avg_deg > 0.0 && avg_deg < (double)(n - 1)))
         return GIRG_E_PARAM;
+    const double r = hrg_radius_for_degree(n, alpha, T, avg_deg);
+    if (!(r > 0.0 && r <= 350.0)) return GIRG_E_PARAM;
+    *R = r;
+    return GIRG_OK;
+}
+
+int hrg_generate(const hrg_params* params, void* d_edges, int64_t capacity_edges,
+                 int64_t* num_edges, double* R_used, void* stream) {
+    if (!params || !num_edges || capacity_edges < 0) return GIRG_E_PARAM;
+    hrg_params q = *params;
+    if (!hrg_shape_ok(q.n, q.alpha, q.T) || !(q.R <= 350.0)) return GIRG_E_PARAM;
     if ((q.edge_bytes != 4 && q.edge_bytes != 8) || (q.precision != 0 && q.precision != 1) ||
         q.level_cap < 0)
         return GIRG_E_PARAM;
+    if (!(q.R > 0.0)) {
+        const int s = hrg_solve_radius(q.n, q.alpha, q.T, q.avg_deg, &q.R);
+        if (s != GIRG_OK) return s;
+    }
+    if (R_used) *R_used = q.R;
     return guarded([&] {
         cudaStream_t st = (cudaStream_t)stream;
         Scratch S(st);

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <thread>
 
 namespace gg {
 
@@ -157,6 +158,218 @@ double DegreeModel::solve(double target, const std::function<void(double)>& fetc
             side = 1;
         }
         if (std::fabs(fm) <= 1e-14 * target) return mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+}  // namespace gg
+
+// ---------------------------------------------------------------- HRG degree
+// P(dist < t) for two independent vertices of the hyperbolic disk: radii r with
+// density alpha sinh(alpha r) / (cosh(alpha R) - 1), angle difference uniform on
+// [0, pi].  For radii r1, r2 the share of angle differences with dist < t is 1 when
+// t >= r1 + r2, 0 when t <= |r1 - r2| and otherwise (2/pi) asin(sqrt(s)) with
+// s = (cosh t - cosh(r1 - r2)) / (2 sinh r1 sinh r2) (hyperbolic law of cosines).
+// The double integral runs in y = R - r over the intervals on which that share is
+// smooth; each interval is mapped by y = a + (b - a)(1 - cos u)/2 (which removes
+// the square-root behaviour at its ends) and integrated with Gauss-Legendre panels;
+// where the share is 1 the radial CDF is used in closed form.
+namespace gg {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+constexpr int kGL = 10;      // Gauss-Legendre points per panel
+constexpr int kYPanels = 3;  // panels per smooth y interval
+constexpr int kTPanels = 2;  // panels per t interval
+
+struct GaussLegendre {
+    double x[kGL], w[kGL];
+    GaussLegendre() {
+        // roots of P_kGL by Newton's method from Tricomi's initial guesses
+        for (int i = 0; i < kGL; ++i) {
+            const double th = kPi * (4.0 * (i + 1) - 1.0) / (4.0 * kGL + 2.0);
+            double z = std::cos(th), dp = 1.0;
+            for (int it = 0; it < 60; ++it) {
+                double pk = z, pkm1 = 1.0;  // P_1, P_0
+                for (int k = 2; k <= kGL; ++k) {
+                    const double pn = ((2 * k - 1) * z * pk - (k - 1) * pkm1) / k;
+                    pkm1 = pk;
+                    pk = pn;
+                }
+                dp = kGL * (pkm1 - z * pk) / (1.0 - z * z);
+                const double step = pk / dp;
+                z -= step;
+                if (std::fabs(step) <= 1e-17) break;
+            }
+            double pk = z, pkm1 = 1.0;
+            for (int k = 2; k <= kGL; ++k) {
+                const double pn = ((2 * k - 1) * z * pk - (k - 1) * pkm1) / k;
+                pkm1 = pk;
+                pk = pn;
+            }
+            dp = kGL * (pkm1 - z * pk) / (1.0 - z * z);
+            x[i] = z;
+            w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        }
+    }
+};
+
+const GaussLegendre& gl() {
+    static const GaussLegendre g;
+    return g;
+}
+
+// Nodes and weights of int_a^b under y = a + (b - a)(1 - cos u)/2, u in [0, pi].
+int cos_mapped_rule(double a, double b, int panels, double* y, double* wt) {
+    const GaussLegendre& g = gl();
+    int k = 0;
+    for (int p = 0; p < panels; ++p) {
+        const double u0 = kPi * p / panels, u1 = kPi * (p + 1) / panels;
+        const double h = 0.5 * (u1 - u0), m = 0.5 * (u0 + u1);
+        for (int i = 0; i < kGL; ++i) {
+            const double u = m + h * g.x[i];
+            y[k] = a + 0.5 * (b - a) * (1.0 - std::cos(u));
+            wt[k] = h * g.w[i] * 0.5 * (b - a) * std::sin(u);
+            ++k;
+        }
+    }
+    return k;
+}
+
+struct Disk {
+    double alpha, R, cm1;  // cm1 = cosh(alpha R) - 1
+    double dens(double y) const { return alpha * std::sinh(alpha * (R - y)) / cm1; }
+    double cdf(double y) const { return 1.0 - (std::cosh(alpha * (R - y)) - 1.0) / cm1; }
+};
+
+double share_below(double r1, double r2, double t, double cosh_t) {
+    if (t >= r1 + r2) return 1.0;
+    if (t <= std::fabs(r1 - r2)) return 0.0;
+    const double s = (cosh_t - std::cosh(r1 - r2)) / (2.0 * std::sinh(r1) * std::sinh(r2));
+    if (!(s > 0.0)) return 0.0;
+    if (s >= 1.0) return 1.0;
+    return (2.0 / kPi) * std::asin(std::sqrt(s));
+}
+
+double dist_cdf(const Disk& D, double t) {
+    const double R = D.R;
+    if (t <= 0.0) return 0.0;
+    if (t >= 2.0 * R) return 1.0;
+    const double ct = std::cosh(t);
+    std::vector<double> cuts = {0.0, R};
+    for (double c : {R - t, 2.0 * R - t, t})
+        if (c > 0.0 && c < R) cuts.push_back(c);
+    std::sort(cuts.begin(), cuts.end());
+    double ya[kYPanels * kGL], wa[kYPanels * kGL], yb[kYPanels * kGL], wb[kYPanels * kGL];
+    double sum = 0.0;
+    for (size_t q = 0; q + 1 < cuts.size(); ++q) {
+        if (!(cuts[q + 1] > cuts[q])) continue;
+        const int na = cos_mapped_rule(cuts[q], cuts[q + 1], kYPanels, ya, wa);
+        for (int a = 0; a < na; ++a) {
+            const double y1 = ya[a];
+            const double lo = std::max(0.0, y1 - t), hi = std::min(R, y1 + t);
+            const double full = 2.0 * R - t - y1;  // share = 1 for y2 >= full
+            if (!(hi > lo)) continue;
+            double in = 0.0;
+            if (full <= lo) {
+                in = D.cdf(hi) - D.cdf(lo);
+            } else {
+                const double top = std::min(hi, full);
+                const int nb = cos_mapped_rule(lo, top, kYPanels, yb, wb);
+                for (int b = 0; b < nb; ++b)
+                    in += wb[b] * D.dens(yb[b]) * share_below(R - y1, R - yb[b], t, ct);
+                if (full < hi) in += D.cdf(hi) - D.cdf(full);
+            }
+            sum += wa[a] * D.dens(y1) * in;
+        }
+    }
+    return sum;
+}
+
+}  // namespace
+
+double hrg_expected_degree(int64_t n, double alpha, double T, double R) {
+    const Disk D{alpha, R, std::cosh(alpha * R) - 1.0};
+    if (T == 0.0) return (double)(n - 1) * dist_cdf(D, R);
+    // t panels growing geometrically away from R; the logistic weight outside
+    // R +- 80 T is below e^-40
+    const double s = 2.0 * T, tlo = std::max(0.0, R - 40.0 * s), thi = std::min(2.0 * R, R + 40.0 * s);
+    std::vector<double> cuts = {R};
+    for (double x = R, w = s; x > tlo; w *= 2.0) cuts.push_back(x = std::max(tlo, x - w));
+    for (double x = R, w = s; x < thi; w *= 2.0) cuts.push_back(x = std::min(thi, x + w));
+    std::sort(cuts.begin(), cuts.end());
+    std::vector<double> ts, ws;
+    double tb[kTPanels * kGL], wtb[kTPanels * kGL];
+    for (size_t q = 0; q + 1 < cuts.size(); ++q) {
+        if (!(cuts[q + 1] > cuts[q])) continue;
+        const int k = cos_mapped_rule(cuts[q], cuts[q + 1], kTPanels, tb, wtb);
+        for (int a = 0; a < k; ++a) {
+            const double e = std::exp(-std::fabs(tb[a] - R) / s);
+            ts.push_back(tb[a]);
+            ws.push_back(wtb[a] * e / (s * (1.0 + e) * (1.0 + e)));
+        }
+    }
+    // the distance CDF at every node, spread over host threads; summed in node order
+    std::vector<double> g(ts.size(), 0.0);
+    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const size_t nthreads = std::min<size_t>(hw, ts.size());
+    std::vector<std::thread> pool;
+    for (size_t th = 0; th < nthreads; ++th)
+        pool.emplace_back([&, th] {
+            for (size_t i = th; i < ts.size(); i += nthreads) g[i] = dist_cdf(D, ts[i]);
+        });
+    for (auto& t : pool) t.join();
+    double p = 0.0;
+    for (size_t i = 0; i < ts.size(); ++i) p += ws[i] * g[i];
+    const double eh = std::exp(-(thi - R) / s);
+    p += eh / (1.0 + eh);  // t beyond thi: the distance CDF is 1 (or the weight negligible)
+    return (double)(n - 1) * p;
+}
+
+double hrg_radius_for_degree(int64_t n, double alpha, double T, double target) {
+    // start from the large-R limit E ~ K n e^(-R/2), K = 8 alpha^2 / (pi (2 alpha - 1)^2)
+    // times pi T / sin(pi T); ln E is nearly linear in R, so regula falsi (Illinois)
+    // on ln E(R) - ln target converges in a few steps
+    double K = 8.0 * alpha * alpha / (kPi * (2.0 * alpha - 1.0) * (2.0 * alpha - 1.0));
+    if (T > 0.0) K *= kPi * T / std::sin(kPi * T);
+    double r0 = 2.0 * std::log(K * (double)n / target);
+    if (!(r0 > 1e-3 && r0 < 700.0)) r0 = std::min(700.0, std::max(1.0, 2.0 * std::log((double)n)));
+    auto F = [&](double R) { return std::log(hrg_expected_degree(n, alpha, T, R)) - std::log(target); };
+    double lo = r0, hi = r0, flo = F(r0), fhi = flo;
+    if (flo == 0.0) return r0;
+    // F decreases in R: find lo with F >= 0 and hi with F < 0
+    for (double step = 0.5; flo < 0.0; step *= 2.0) {
+        hi = lo;
+        fhi = flo;
+        lo = std::max(1e-3, lo - step);
+        flo = F(lo);
+        if (lo <= 1e-3 && flo < 0.0) return std::nan("");
+    }
+    for (double step = 0.5; fhi >= 0.0; step *= 2.0) {
+        lo = hi;
+        flo = fhi;
+        hi = std::min(700.0, hi + step);
+        fhi = F(hi);
+        if (hi >= 700.0 && fhi >= 0.0) return std::nan("");
+    }
+    int side = 0;
+    for (int it = 0; it < 200 && hi - lo > 1e-13 * hi; ++it) {
+        double mid = (it % 6 == 5) ? 0.5 * (lo + hi) : hi - fhi * (hi - lo) / (fhi - flo);
+        if (!(mid > lo && mid < hi)) mid = 0.5 * (lo + hi);
+        const double fm = F(mid);
+        if (std::fabs(fm) <= 1e-14) return mid;
+        if (fm >= 0.0) {
+            lo = mid;
+            flo = fm;
+            if (side == 1) fhi *= 0.5;
+            side = 1;
+        } else {
+            hi = mid;
+            fhi = fm;
+            if (side == -1) flo *= 0.5;
+            side = -1;
+        }
     }
     return 0.5 * (lo + hi);
 }

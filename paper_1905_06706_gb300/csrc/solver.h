@@ -30,3 +30,16 @@ class DegreeModel {
 };
 
 }  // namespace gg
+
+namespace gg {
+
+// Expected average degree of an HRG with n vertices, dispersion alpha, temperature T
+// and disk radius R (Sec. 2.2), and the R that gives a target degree.  The paper
+// gives no formula; this integrates the model's definition: (n - 1) times the
+// probability that two random vertices are adjacent, which is P(dist < R) at T = 0
+// and E[P(dist < t)] over t ~ logistic(R, 2T) at T > 0.
+double hrg_expected_degree(int64_t n, double alpha, double T, double R);
+// R with hrg_expected_degree(n, alpha, T, R) = target (NaN if none in (0, 700)).
+double hrg_radius_for_degree(int64_t n, double alpha, double T, double target);
+
+}  // namespace gg

@@ -58,11 +58,14 @@ def test_invalid_parameters_rejected_on_host(lib, bad):
 
 
 def test_invalid_hrg_and_points_rejected(lib):
-    hp = gg.HrgParams(1000, 0.5, 0.5, 10.0, 1, 4, 0, 0)  # alpha must exceed 1/2
     m = ctypes.c_int64(0)
-    assert lib.hrg_generate(ctypes.byref(hp), None, 0, ctypes.byref(m), None) == gg.GIRG_E_PARAM
-    hp = gg.HrgParams(1000, 0.75, 0.5, 0.0, 1, 4, 0, 0)  # R must be given
-    assert lib.hrg_generate(ctypes.byref(hp), None, 0, ctypes.byref(m), None) == gg.GIRG_E_PARAM
+    for hp in (gg.HrgParams(1000, 0.5, 0.5, 0.0, 10.0, 1, 4, 0, 0),    # alpha must exceed 1/2
+               gg.HrgParams(1000, 0.75, 0.5, 0.0, 0.0, 1, 4, 0, 0),    # R or avg_deg needed
+               gg.HrgParams(1000, 0.75, 0.5, 999.0, 0.0, 1, 4, 0, 0),  # avg_deg < n - 1
+               gg.HrgParams(1000, 0.75, 1.0, 0.0, 10.0, 1, 4, 0, 0),   # T < 1
+               gg.HrgParams(1000, 0.75, 0.5, 0.0, 10.0, 1, 2, 0, 0)):  # edge_bytes 4 or 8
+        assert lib.hrg_generate(ctypes.byref(hp), None, 0, ctypes.byref(m), None,
+                                None) == gg.GIRG_E_PARAM
     assert lib.girg_points(0, 2, 2.5, 1.0, 1, None, None, None) == gg.GIRG_E_PARAM
     assert lib.girg_allpairs(10, 1, None, None, 0.0, 0.5, 1.0, 1, 0, 4, None, 0,
                              ctypes.byref(m), None) == gg.GIRG_E_PARAM
@@ -117,3 +120,31 @@ def test_host_deterministic_math_matches_oracle_bitwise(lib):
         assert lib.girg_det_eval(4, x, 0.0) == O.det_sinpi(x)
     for wu, wv in rng.uniform(1, 50, (2000, 2)):
         assert lib.girg_det_eval(6, wu, wv) == O.girg_p(2, 0.75, 0.5, 1000.0, wu, wv, 2 ** 30)
+
+
+# ------------------------------------------------------------------ HRG radius (host code)
+
+@pytest.mark.parametrize("alpha,T,R", [(0.75, 0.0, 12.0), (0.75, 0.5, 20.0), (0.9, 0.3, 31.0),
+                                       (0.6, 0.8, 25.0)])
+def test_hrg_expected_degree_matches_oracle(lib, alpha, T, R):
+    import oracle as O
+    n = 10 ** 6
+    got = gg.hrg_expected_avg_degree(n, alpha, T, R)
+    ref = O.hrg_avg_degree(n, alpha, T, R)
+    assert abs(got - ref) <= 1e-9 * ref
+
+
+@pytest.mark.parametrize("n,alpha,T,deg", [(10 ** 7, 0.75, 0.5, 10.0), (10 ** 4, 0.75, 0.0, 8.0),
+                                           (10 ** 5, 1.1, 0.7, 20.0)])
+def test_hrg_radius_matches_oracle(lib, n, alpha, T, deg):
+    import oracle as O
+    R = gg.hrg_solve_radius(n, alpha, T, deg)
+    assert abs(R - O.hrg_solve_R(n, alpha, T, deg)) <= 1e-9 * R
+    assert abs(gg.hrg_expected_avg_degree(n, alpha, T, R) - deg) <= 1e-11 * deg
+
+
+def test_hrg_radius_rejects_bad_targets(lib):
+    out = ctypes.c_double(0.0)
+    assert lib.hrg_solve_radius(1000, 0.75, 0.5, 0.0, ctypes.byref(out)) == gg.GIRG_E_PARAM
+    assert lib.hrg_solve_radius(1000, 0.75, 0.5, 999.0, ctypes.byref(out)) == gg.GIRG_E_PARAM
+    assert lib.hrg_expected_avg_degree(1000, 0.75, 0.5, -1.0, ctypes.byref(out)) == gg.GIRG_E_PARAM

@@ -256,6 +256,23 @@ def test_hrg_threshold_equals_allpairs():
     assert res.status == gg.GIRG_OK and _set(ed, res.num_edges) == ref
 
 
+@pytest.mark.parametrize("T,deg", [(0.5, 10.0), (0.0, 6.0)])
+def test_hrg_solved_radius_edge_for_edge(T, deg):
+    """R <= 0: the radius is solved from the target degree (host quadrature); the graph
+    equals the oracle's at that radius and its average degree is near the target."""
+    n, alpha = 60_000, 0.75
+    R = O.hrg_solve_R(n, alpha, T, deg)
+    ed = _edges(n * 64)
+    res = gg.hrg_generate(ed, n=n, alpha=alpha, T=T, avg_deg=deg, seed=21)
+    assert res.status == gg.GIRG_OK
+    assert abs(res.R_used - R) <= 1e-9 * R
+    r, X = O.hrg_points(n, alpha, res.R_used, 21)
+    ref = O.hrg_cellpairs(X, r, res.R_used, T, 21, cap=n * 64)
+    assert _set(ed, res.num_edges) == O.edge_set(ref.edges)
+    # one sample: the average degree lies within a few standard deviations of deg
+    assert abs(2.0 * res.num_edges / n - deg) < 0.15 * deg
+
+
 # --------------------------------------------------------------------- full size
 
 def test_benchmark_workload_full_size_edge_for_edge():
