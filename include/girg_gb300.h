@@ -54,7 +54,10 @@ extern "C" {
  *   c          the constant of Eq. 1; c <= 0 means "solve from avg_deg" (App. B.2)
  *   w_min      smallest weight, > 0
  *   seed       64-bit seed of every Philox stream
- *   edge_bytes 4 (uint32 endpoints) or 8 (uint64 endpoints)
+ *   edge_bytes 4 (uint32 endpoints), 8 (uint64 endpoints) or 0 (count-only: no edge
+ *              is stored, d_edges may be NULL and capacity_edges is ignored; the
+ *              edge count and the checksum of girg_last_stats are still produced, as
+ *              the paper's benchmarks replace storage by a checksum, Sec. 5)
  *   precision  GIRG_PRECISION_FP32 or GIRG_PRECISION_FP64
  *   level_cap  deepest quadtree level to use, 0 = default min(32/d, (bitlen(n)+4)/d);
  *              a tuning knob: the sample stays exact for any value >= 1
@@ -180,8 +183,10 @@ int girg_expected_avg_degree(const girg_params* params, double* avg_deg, void* s
  * [1] coins drawn, [2] FP64 rechecks, [3] type-II items (non-empty cell pairs),
  * [4] jump draws, [5] type-II candidates, [6] rows, [7] type-I items, [8] chunks of
  * all type-II streams, [9] edges, [10] kernel launches, [11] vertex references of the type-I items
- * (sum of both side lengths), [12] type-I edges, [13] type-II streams.  Copies
- * min(len, 14) values; returns the number copied. */
+ * (sum of both side lengths), [12] type-I edges, [13] type-II streams, [14] edge
+ * checksum: the sum mod 2^64 over the edges (u < v) of the splitmix64 finalizer of
+ * u 2^32 + v (as an int64 bit pattern; independent of the edge order).  Copies
+ * min(len, 15) values; returns the number copied. */
 int girg_last_stats(int64_t* out, int32_t len);
 
 /* Milliseconds spent in each phase of the last call on this host thread

@@ -377,6 +377,26 @@ def hrg_solve_R(n, alpha, T, target):
     return _load().orc_hrg_solve_R(n, alpha, T, target)
 
 
+def splitmix64_finalize(z):
+    """The output function of splitmix64 (Steele, Lea, Flood, OOPSLA 2014) on uint64."""
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def edge_checksum(edges) -> int:
+    """Order-independent checksum of an edge list: the sum mod 2^64 of
+    splitmix64_finalize(u 2^32 + v) over the edges, u < v."""
+    e = np.asarray(edges, dtype=np.uint64).reshape(-1, 2)
+    if len(e) == 0:
+        return 0
+    key = (np.minimum(e[:, 0], e[:, 1]) << np.uint64(32)) | np.maximum(e[:, 0], e[:, 1])
+    with np.errstate(over="ignore"):
+        return int(np.sum(splitmix64_finalize(key), dtype=np.uint64))
+
+
 def edge_set(edges) -> set:
     """Set of (u, v) tuples with u < v from an (m, 2) array."""
     e = np.asarray(edges, dtype=np.int64)

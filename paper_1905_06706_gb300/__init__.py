@@ -26,7 +26,8 @@ PRECISION_FP64 = 1
 
 STAT_NAMES = ("type1_pairs", "coins", "rechecks", "type2_items", "jump_draws",
               "type2_candidates", "rows", "type1_items", "type2_chunks", "edges",
-              "kernel_launches", "type1_vertex_refs", "type1_edges", "type2_streams")
+              "kernel_launches", "type1_vertex_refs", "type1_edges", "type2_streams",
+              "edge_checksum")
 PHASE_NAMES = ("points_reduce", "tables", "sort", "enumerate", "type1", "type2",
                "total", "host_reduce_readback", "host_c_search", "host_tables")
 
@@ -123,7 +124,9 @@ def _ptr(t):
 def last_stats() -> dict:
     buf = (ctypes.c_int64 * len(STAT_NAMES))()
     load().girg_last_stats(buf, len(STAT_NAMES))
-    return dict(zip(STAT_NAMES, list(buf)))
+    out = dict(zip(STAT_NAMES, list(buf)))
+    out["edge_checksum"] &= (1 << 64) - 1  # unsigned
+    return out
 
 
 def last_phase_ms() -> dict:
@@ -140,17 +143,25 @@ class Result:
     R_used: float = float("nan")
 
 
+def _edge_args(edges):
+    """(edge_bytes, pointer, capacity) of an edge buffer; None means count-only."""
+    if edges is None:
+        return 0, None, 0
+    return edges.element_size(), _ptr(edges), edges.shape[0]
+
+
 def girg_generate(edges, *, n, d, beta, T, avg_deg=0.0, c=0.0, w_min=1.0, seed=1,
                   precision=PRECISION_FP32, level_cap=0, stream=None) -> Result:
-    """Generate a GIRG into ``edges`` (CUDA tensor (cap, 2) of int32 or int64)."""
+    """Generate a GIRG into ``edges`` (CUDA tensor (cap, 2) of int32 or int64; None:
+    count-only, see ``last_stats()['edge_checksum']``)."""
     _torch()
     lib = load()
-    eb = edges.element_size()
+    eb, ep, cap = _edge_args(edges)
     p = GirgParams(n, d, beta, T, avg_deg, c, w_min, seed, eb, precision, level_cap)
     m = ctypes.c_int64(0)
     cu = ctypes.c_double(0.0)
-    st = lib.girg_generate(ctypes.byref(p), _ptr(edges), edges.shape[0], ctypes.byref(m),
-                           ctypes.byref(cu), _stream(stream))
+    st = lib.girg_generate(ctypes.byref(p), ep, cap, ctypes.byref(m), ctypes.byref(cu),
+                           _stream(stream))
     return Result(st, m.value, cu.value)
 
 
@@ -161,9 +172,9 @@ def girg_generate_from_points(edges, X, w, *, T, c, seed=1, precision=PRECISION_
     lib = load()
     d, n = X.shape
     m = ctypes.c_int64(0)
+    eb, ep, cap = _edge_args(edges)
     st = lib.girg_generate_from_points(n, d, _ptr(X), _ptr(w), T, c, seed, precision, level_cap,
-                                       edges.element_size(), _ptr(edges), edges.shape[0],
-                                       ctypes.byref(m), _stream(stream))
+                                       eb, ep, cap, ctypes.byref(m), _stream(stream))
     return Result(st, m.value, c)
 
 
@@ -173,10 +184,11 @@ def hrg_generate(edges, *, n, alpha, T, R=0.0, avg_deg=0.0, seed=1, precision=PR
     The radius used is returned in ``R_used``."""
     _torch()
     lib = load()
-    p = HrgParams(n, alpha, T, avg_deg, R, seed, edges.element_size(), precision, level_cap)
+    eb, ep, cap = _edge_args(edges)
+    p = HrgParams(n, alpha, T, avg_deg, R, seed, eb, precision, level_cap)
     m = ctypes.c_int64(0)
     r_used = ctypes.c_double(float("nan"))
-    st = lib.hrg_generate(ctypes.byref(p), _ptr(edges), edges.shape[0], ctypes.byref(m),
+    st = lib.hrg_generate(ctypes.byref(p), ep, cap, ctypes.byref(m),
                           ctypes.byref(r_used), _stream(stream))
     return Result(st, m.value, R_used=r_used.value)
 

@@ -458,7 +458,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     cfg.filt_hi = d_fhi;
     cfg.edges = d_edges;
     cfg.edge_bytes = P.edge_bytes;
-    cfg.cap = cap;
+    cfg.cap = P.edge_bytes == 0 ? INT64_MAX : cap;  // count-only: nothing is stored
     cfg.edge_count = stats + kNumStats;
     cfg.stats = stats;
     cfg.row_count = counters + 0;
@@ -576,7 +576,7 @@ int check_girg(const girg_params* p) {
     if (p->n < 2 || p->n >= (1ll << 31)) return GIRG_E_PARAM;
     if (p->d < 1 || p->d > kMaxDim) return GIRG_E_PARAM;
     if (!(p->beta > 2.0) || !(p->T >= 0.0 && p->T < 1.0) || !(p->w_min > 0.0)) return GIRG_E_PARAM;
-    if (p->edge_bytes != 4 && p->edge_bytes != 8) return GIRG_E_PARAM;
+    if (p->edge_bytes != 0 && p->edge_bytes != 4 && p->edge_bytes != 8) return GIRG_E_PARAM;
     if (p->precision != 0 && p->precision != 1) return GIRG_E_PARAM;
     if (!(p->c > 0.0) && !(p->avg_deg > 0.0 && p->avg_deg < (double)(p->n - 1))) return GIRG_E_PARAM;
     if (p->level_cap < 0) return GIRG_E_PARAM;
@@ -597,13 +597,51 @@ int guarded(F&& f) {
     }
 }
 
-// Solve c for the target degree from the device sums and the heaviest weights.
-double solve_c(Problem& P, double target, Scratch& S, cudaStream_t st) {
+// Host copy of the heaviest weights gathered and sorted on the device together with
+// the reduction (pinned, one per host thread, kept for the life of the process).
+struct TopWeights {
+    unsigned int count[2];  // gathered, sorted flag
+    double thr;             // every weight above thr was gathered
+    double w[kTopSortMax];
+};
+
+TopWeights* pinned_top() {
+    thread_local TopWeights* p = nullptr;
+    if (!p) {
+        void* q = nullptr;
+        CK(cudaMallocHost(&q, sizeof(TopWeights)));
+        p = static_cast<TopWeights*>(q);
+    }
+    return p;
+}
+
+// Launch the device-side gather of the heaviest weights and queue their copy into
+// the pinned host buffer (read after the next synchronisation).
+TopWeights* queue_top_weights(Problem& P, const Reduce* red, double target, Scratch& S,
+                              cudaStream_t st) {
+    unsigned int* cnt = S.get<unsigned int>(2);
+    double* thr = S.get<double>(1);
+    double* buf = S.get<double>(kTopSortMax);
+    CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned int), st));
+    launch_top_weights(P.n, P.w, red, P.d, P.T, target, exponent_of_ulp(P.w_min), thr, buf,
+                       kTopSortMax, cnt, st);
+    TopWeights* h = pinned_top();
+    CK(cudaMemcpyAsync(h->count, cnt, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&h->thr, thr, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h->w, buf, sizeof(h->w), cudaMemcpyDeviceToHost, st));
+    return h;
+}
+
+// Solve c for the target degree from the device sums and the heaviest weights
+// (`pre`: weights gathered with the reduction, if any).
+double solve_c(Problem& P, double target, Scratch& S, cudaStream_t st, const TopWeights* pre) {
     DegreeModel M(P.n, P.d, P.T, P.W, P.red.s2, P.red.st, P.red.s2t);
     double wmax = 0.0;
     for (int i = 0; i < kMaxLayers; ++i)
         if (P.red.cnt[i]) wmax = std::max(wmax, bits_to_double(P.red.wmax[i]));
     M.set_wmax(wmax);
+    if (pre && pre->count[1] == 1u && pre->count[0] <= kTopSortMax && pre->thr > 0.0)
+        M.set_top(std::vector<double>(pre->w, pre->w + pre->count[0]), pre->thr, true);
     unsigned int* cntp = S.get<unsigned int>(1);
     unsigned int capv = 1u << 16;
     double* buf = S.get<double>(capv);
@@ -724,6 +762,7 @@ int girg_generate(const girg_params* params, void* d_edges, int64_t capacity_edg
         Reduce* red = new_reduce(S, st);
         launch_reduce(P.n, w, nullptr, P.w_min, exponent_of_ulp(P.w_min), solve ? 1 : 0,
                       P.T > 0.0 ? 1.0 / P.T : 0.0, red, st);
+        const TopWeights* top = solve ? queue_top_weights(P, red, params->avg_deg, S, st) : nullptr;
         tm.mark();
         auto h0 = std::chrono::steady_clock::now();
         read_reduce(P, red, st);
@@ -731,12 +770,12 @@ int girg_generate(const girg_params* params, void* d_edges, int64_t capacity_edg
         if (P.red.range_error) return GIRG_E_RANGE;
         P.W = round128(P.red.sum_hi, P.red.sum_lo, exponent_of_ulp(P.w_min));
         h0 = std::chrono::steady_clock::now();
-        P.c = solve ? solve_c(P, params->avg_deg, S, st) : params->c;
+        P.c = solve ? solve_c(P, params->avg_deg, S, st, top) : params->c;
         g_ms[8] = (float)host_ms_since(h0);
         if (c_used) *c_used = P.c;
         run_sampler(P, S, st, tm, d_edges, capacity_edges, num_edges, nullptr);
         finish_timing(tm);
-        return *num_edges > capacity_edges ? GIRG_E_CAPACITY : GIRG_OK;
+        return P.edge_bytes != 0 && *num_edges > capacity_edges ? GIRG_E_CAPACITY : GIRG_OK;
     });
 }
 
@@ -793,7 +832,8 @@ static int from_points_impl(int64_t n, int32_t d, const uint32_t* d_X, const dou
                             int64_t* num_edges, int64_t* order_out, void* stream) {
     if (n < 2 || n >= (1ll << 31) || d < 1 || d > kMaxDim || !(T >= 0.0 && T < 1.0) || !(c > 0.0))
         return GIRG_E_PARAM;
-    if ((edge_bytes != 4 && edge_bytes != 8) || (precision != 0 && precision != 1) || level_cap < 0)
+    if ((edge_bytes != 0 && edge_bytes != 4 && edge_bytes != 8) || (precision != 0 && precision != 1) ||
+        level_cap < 0)
         return GIRG_E_PARAM;
     if (!order_out && (!num_edges || capacity_edges < 0)) return GIRG_E_PARAM;
     return guarded([&] {
@@ -832,7 +872,7 @@ static int from_points_impl(int64_t n, int32_t d, const uint32_t* d_X, const dou
         run_sampler(P, S, st, tm, d_edges, capacity_edges, num_edges ? num_edges : &dummy, order_out);
         if (order_out) return GIRG_OK;
         finish_timing(tm);
-        return *num_edges > capacity_edges ? GIRG_E_CAPACITY : GIRG_OK;
+        return edge_bytes != 0 && *num_edges > capacity_edges ? GIRG_E_CAPACITY : GIRG_OK;
     });
 }
 
@@ -875,7 +915,8 @@ int hrg_generate(const hrg_params* params, void* d_edges, int64_t capacity_edges
     if (!params || !num_edges || capacity_edges < 0) return GIRG_E_PARAM;
     hrg_params q = *params;
     if (!hrg_shape_ok(q.n, q.alpha, q.T) || !(q.R <= 350.0)) return GIRG_E_PARAM;
-    if ((q.edge_bytes != 4 && q.edge_bytes != 8) || (q.precision != 0 && q.precision != 1) ||
+    if ((q.edge_bytes != 0 && q.edge_bytes != 4 && q.edge_bytes != 8) ||
+        (q.precision != 0 && q.precision != 1) ||
         q.level_cap < 0)
         return GIRG_E_PARAM;
     if (!(q.R > 0.0)) {
@@ -915,7 +956,7 @@ int hrg_generate(const hrg_params* params, void* d_edges, int64_t capacity_edges
         P.W = 1.0;
         run_sampler(P, S, st, tm, d_edges, capacity_edges, num_edges, nullptr);
         finish_timing(tm);
-        return *num_edges > capacity_edges ? GIRG_E_CAPACITY : GIRG_OK;
+        return P.edge_bytes != 0 && *num_edges > capacity_edges ? GIRG_E_CAPACITY : GIRG_OK;
     });
 }
 

@@ -199,6 +199,82 @@ __global__ void k_gather_above(int64_t n, const double* __restrict__ w, double t
     }
 }
 
+// Weight threshold for the heaviest weights the search for c will need (App. B.2):
+// 0.9 times the weight below which no vertex has a partner in E_R at the c0 where
+// the leading term of f(c) reaches the target.  The root lies at or a little above
+// c0, where that weight is smaller; the search starts at c0 and fetches more weights
+// only if it moves further.  One thread; an estimate, so CUDA's pow is good enough.
+__global__ void k_top_threshold(const Reduce* __restrict__ red, int64_t n, int d, double T,
+                                double target, int E0, double* __restrict__ thr) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double W = ldexp((double)red->sum_hi * 0x1p64 + (double)red->sum_lo, E0);
+    double wmax = 0.0;
+    for (int i = 0; i < 64; ++i)
+        if (red->cnt[i]) wmax = fmax(wmax, __longlong_as_double((long long)red->wmax[i]));
+    const double S1 = W - red->s2 / W, two_d = ldexp(1.0, d);
+    double qs;
+    if (T > 0.0) {
+        const double c0 = pow(target * (double)n * (1.0 - T) / (two_d * S1), 1.0 / T);
+        qs = 1.0 / (two_d * pow(c0, T));
+    } else {
+        const double c0 = pow(target * (double)n / (two_d * S1), 1.0 / d);
+        qs = 1.0 / (two_d * pow(c0, (double)d));
+    }
+    const double t = 0.9 * qs * W / wmax;
+    *thr = (t > 0.0 && t < 1e300) ? t : 0.0;
+}
+
+__global__ void k_gather_above_dev(int64_t n, const double* __restrict__ w,
+                                   const double* __restrict__ thr, double* __restrict__ out,
+                                   unsigned int cap, unsigned int* __restrict__ count) {
+    const double t = *thr;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const double wv = w[v];
+        if (wv > t) {
+            const unsigned int s = atomicAdd(count, 1u);
+            if (s < cap) out[s] = wv;
+        }
+    }
+}
+
+// Sort the gathered weights in decreasing order (one block, bitonic network in
+// shared memory on the bit patterns, which order positive doubles); count[1] = 1
+// when sorted, 0 when there were more than kTopSortMax.
+__global__ void __launch_bounds__(1024) k_sort_top(double* __restrict__ buf,
+                                                   unsigned int* __restrict__ count) {
+    extern __shared__ unsigned long long s_key[];
+    const unsigned int k = count[0];
+    if (k > kTopSortMax) {
+        if (threadIdx.x == 0) count[1] = 0u;
+        return;
+    }
+    unsigned int m = 1;
+    while (m < k) m <<= 1;
+    for (unsigned int i = threadIdx.x; i < m; i += blockDim.x)
+        s_key[i] = i < k ? (unsigned long long)__double_as_longlong(buf[i]) : 0ull;
+    __syncthreads();
+    for (unsigned int size = 2; size <= m; size <<= 1) {
+        for (unsigned int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (unsigned int i = threadIdx.x; i < m; i += blockDim.x) {
+                const unsigned int j = i ^ stride;
+                if (j > i) {
+                    const bool desc = (i & size) == 0;  // final order: decreasing
+                    const unsigned long long a = s_key[i], b = s_key[j];
+                    if (desc ? (a < b) : (a > b)) {
+                        s_key[i] = b;
+                        s_key[j] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (unsigned int i = threadIdx.x; i < k; i += blockDim.x)
+        buf[i] = __longlong_as_double((long long)s_key[i]);
+    if (threadIdx.x == 0) count[1] = 1u;
+}
+
 // ------------------------------------------------------------------ launchers
 static int grid_for(int64_t n, int threads, int max_blocks) {
     int64_t b = (n + threads - 1) / threads;
@@ -243,6 +319,21 @@ void launch_gather_above(int64_t n, const double* w, double thr, double* out, un
                          unsigned int* count, cudaStream_t st) {
     ++g_launches;
     k_gather_above<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, w, thr, out, cap, count);
+}
+
+void launch_top_weights(int64_t n, const double* w, const Reduce* red, int d, double T,
+                        double target, int E0, double* thr, double* out, unsigned int cap,
+                        unsigned int* count, cudaStream_t st) {
+    static const bool attr = [] {
+        return cudaFuncSetAttribute(k_sort_top, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(kTopSortMax * sizeof(unsigned long long))) ==
+               cudaSuccess;
+    }();
+    (void)attr;
+    g_launches += 3;
+    k_top_threshold<<<1, 32, 0, st>>>(red, n, d, T, target, E0, thr);
+    k_gather_above_dev<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, w, thr, out, cap, count);
+    k_sort_top<<<1, 1024, kTopSortMax * sizeof(unsigned long long), st>>>(out, count);
 }
 
 }  // namespace gg

@@ -59,7 +59,8 @@ struct Seg {
 
 enum : int { kStatT1Pairs = 0, kStatCoins, kStatRecheck, kStatT2Items, kStatDraws,
              kStatCands, kStatRows, kStatT1Items, kStatT2Chunks, kStatEdges,
-             kStatLaunches, kStatT1VertexRefs, kStatT1Edges, kStatStreams, kNumStats };
+             kStatLaunches, kStatT1VertexRefs, kStatT1Edges, kStatStreams, kStatChecksum,
+             kNumStats };
 
 
 struct DevCfg {
@@ -190,9 +191,18 @@ struct WarpEdges {
     unsigned int* n;  // count (shared)
 };
 
+// Order-independent checksum of an edge set: the sum mod 2^64 of the splitmix64
+// finalizer (Steele, Lea, Flood, OOPSLA 2014) of u 2^32 + v over the edges (u < v).
+__device__ __forceinline__ unsigned long long edge_mix(uint32_t a, uint32_t b) {
+    unsigned long long z = ((unsigned long long)a << 32) | b;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
 __device__ __forceinline__ void write_edge(const DevCfg& cfg, unsigned long long slot, uint32_t a,
                                            uint32_t b) {
-    if ((long long)slot >= cfg.cap) return;
+    if (cfg.edge_bytes == 0 || (long long)slot >= cfg.cap) return;  // count-only / overflow
     if (cfg.edge_bytes == 4) {
         reinterpret_cast<uint2*>(cfg.edges)[slot] = make_uint2(a, b);
     } else {
@@ -210,6 +220,7 @@ __device__ __forceinline__ void push_edge(const DevCfg& cfg, WarpEdges& we, uint
     } else {
         const unsigned long long g = atomicAdd(cfg.edge_count, 1ull);
         write_edge(cfg, g, a, b);
+        atomicAdd(&cfg.stats[kStatChecksum], edge_mix(a, b));
     }
 }
 
@@ -223,7 +234,13 @@ __device__ __forceinline__ void flush_edges(const DevCfg& cfg, WarpEdges& we, un
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(cfg.edge_count, (unsigned long long)cnt);
         base = __shfl_sync(0xffffffffu, base, 0);
-        for (unsigned int t = lane; t < cnt; t += 32) write_edge(cfg, base + t, we.a[t], we.b[t]);
+        unsigned long long mix = 0;
+        for (unsigned int t = lane; t < cnt; t += 32) {
+            write_edge(cfg, base + t, we.a[t], we.b[t]);
+            mix += edge_mix(we.a[t], we.b[t]);
+        }
+        for (int o = 16; o > 0; o >>= 1) mix += __shfl_down_sync(0xffffffffu, mix, o);
+        if (lane == 0) atomicAdd(&cfg.stats[kStatChecksum], mix);
         __syncwarp();
         if (lane == 0) *we.n = 0;
     }

@@ -32,6 +32,13 @@ void launch_reduce(int64_t n, const double* w, const double* r, double w_min, in
                    int want_sums, double invT, Reduce* out, cudaStream_t st);
 void launch_gather_above(int64_t n, const double* w, double thr, double* out, unsigned int cap,
                          unsigned int* count, cudaStream_t st);
+// The heaviest weights for the search for c, without a host round trip: a threshold
+// estimated on the device from the reduction, the weights above it (count[0]) and,
+// when count[0] <= kTopSortMax, sorted in decreasing order (count[1] = 1).
+constexpr unsigned int kTopSortMax = 16384;
+void launch_top_weights(int64_t n, const double* w, const Reduce* red, int d, double T,
+                        double target, int E0, double* thr, double* out, unsigned int cap,
+                        unsigned int* count, cudaStream_t st);
 
 // Sorting: keys (global cell index at the insertion level) with a histogram.
 void launch_keys(int64_t n, int d, const double* w, const uint32_t* X, double w_min,

@@ -783,10 +783,10 @@ __global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
 // global chunk space, fetched with one atomic and mapped to streams with one
 // warp search), so the lanes stay busy however unequal the chunks are.
 constexpr int kT2Threads = 256;
-constexpr int kT2RefillMin = 4;  // refill idle lanes once this many are idle
+constexpr int kT2RefillMin = 8;  // refill idle lanes once this many are idle
 
 template <int DIM>
-__global__ void __launch_bounds__(kT2Threads) k_type2(DevCfg cfg) {
+__global__ void __launch_bounds__(kT2Threads, 4) k_type2(DevCfg cfg) {
     __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
     __shared__ unsigned int s_en[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

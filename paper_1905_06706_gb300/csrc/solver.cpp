@@ -25,8 +25,8 @@ DegreeModel::DegreeModel(int64_t n, int d, double T, double W, double s2, double
     have_thr_ = INFINITY;
 }
 
-void DegreeModel::set_top(std::vector<double> top, double fetched_above) {
-    std::sort(top.begin(), top.end(), [](double a, double b) { return a > b; });
+void DegreeModel::set_top(std::vector<double> top, double fetched_above, bool descending) {
+    if (!descending) std::sort(top.begin(), top.end(), [](double a, double b) { return a > b; });
     top_ = std::move(top);
     have_thr_ = fetched_above;
     if (!top_.empty()) wmax_ = std::max(wmax_, top_[0]);
@@ -123,13 +123,19 @@ double DegreeModel::solve(double target, const std::function<void(double)>& fetc
     else
         c0 = std::pow(target * (double)n_ * (1.0 - T_) / (std::ldexp(1.0, d_) * S1_), 1.0 / T_);
     if (!(c0 > 1e-300 && c0 < 1e300)) c0 = 1.0;
+    // bracket with steps growing from 5% (the root is usually within a few percent
+    // of c0, and small steps keep the needed weights within those already fetched)
     double lo = c0, hi = c0;
     if (eval(c0) < target) {
-        while (eval(hi) < target && hi < 1e300) hi *= 2.0;
-        lo = hi / 2.0;
+        for (double f = 1.05; eval(hi) < target && hi < 1e300; f = f * f) {
+            lo = hi;
+            hi *= f;
+        }
     } else {
-        while (eval(lo) >= target && lo > 1e-300) lo /= 2.0;
-        hi = lo * 2.0;
+        for (double f = 1.05; eval(lo) >= target && lo > 1e-300; f = f * f) {
+            hi = lo;
+            lo /= f;
+        }
     }
     // Illinois variant of regula falsi on log c: the bracket [lo, hi] with
     // f(lo) < target <= f(hi) shrinks superlinearly; bisection steps guard it

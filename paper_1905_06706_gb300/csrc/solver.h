@@ -11,8 +11,9 @@ class DegreeModel {
    public:
     // s2 = sum w^2, st = sum w^(1/T), s2t = sum w^(2/T) (T > 0).
     DegreeModel(int64_t n, int d, double T, double W, double s2, double st, double s2t);
-    // The heaviest weights: every weight strictly above `fetched_above`.
-    void set_top(std::vector<double> top, double fetched_above);
+    // The heaviest weights: every weight strictly above `fetched_above` (`descending`:
+    // already in decreasing order).
+    void set_top(std::vector<double> top, double fetched_above, bool descending = false);
     void set_wmax(double wmax) { wmax_ = wmax; }
     double f(double c) const;
     // Weight threshold below which no vertex has a partner in E_R at this c.

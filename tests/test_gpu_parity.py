@@ -273,6 +273,44 @@ def test_hrg_solved_radius_edge_for_edge(T, deg):
     assert abs(2.0 * res.num_edges / n - deg) < 0.15 * deg
 
 
+# --------------------------------------------------------------------- count-only mode
+
+@pytest.mark.parametrize("d,T", [(2, 0.5), (1, 0.0), (3, 0.7)])
+def test_checksum_and_count_only_mode(d, T):
+    """The edge checksum equals the oracle's; count-only (no edge buffer) gives the same
+    count and checksum as a run that stores the edges."""
+    n = 30_000
+    w, X = O.girg_points(n, d, 2.4, 1.0, 7 + d)
+    W = O.exact_sum(w)
+    c = O.girg_solve_c(9.0, w, d, T, W)
+    ref = O.girg_cellpairs(X, w, float(w.min()), W, T, c, 5, cap=n * 64)
+    Xg, wg = _gpu_points(X, w)
+    ed = _edges(n * 64)
+    r = gg.girg_generate_from_points(ed, Xg, wg, T=T, c=c, seed=5)
+    st = gg.last_stats()
+    assert r.status == gg.GIRG_OK and r.num_edges == len(ref.edges)
+    assert st["edge_checksum"] == O.edge_checksum(ref.edges)
+    r0 = gg.girg_generate_from_points(None, Xg, wg, T=T, c=c, seed=5)
+    st0 = gg.last_stats()
+    assert r0.status == gg.GIRG_OK and r0.num_edges == r.num_edges
+    assert st0["edge_checksum"] == st["edge_checksum"]
+
+
+def test_count_only_generate_and_hrg():
+    n = 200_000
+    ed = _edges(n * 8)
+    r = gg.girg_generate(ed, n=n, d=2, beta=2.5, T=0.5, avg_deg=10.0, seed=4)
+    cs = gg.last_stats()["edge_checksum"]
+    r0 = gg.girg_generate(None, n=n, d=2, beta=2.5, T=0.5, avg_deg=10.0, seed=4)
+    assert r.status == r0.status == gg.GIRG_OK and r0.num_edges == r.num_edges
+    assert gg.last_stats()["edge_checksum"] == cs
+    assert cs == O.edge_checksum(ed[: r.num_edges].cpu().numpy())
+    h = gg.hrg_generate(ed, n=n, alpha=0.75, T=0.5, avg_deg=10.0, seed=4)
+    hc = gg.last_stats()["edge_checksum"]
+    h0 = gg.hrg_generate(None, n=n, alpha=0.75, T=0.5, avg_deg=10.0, seed=4)
+    assert h0.num_edges == h.num_edges and gg.last_stats()["edge_checksum"] == hc
+
+
 # --------------------------------------------------------------------- full size
 
 def test_benchmark_workload_full_size_edge_for_edge():

@@ -217,3 +217,19 @@ def test_visited_cell_pairs_heavy_tasks_d2():
     assert res.visited_distant[0] == 0 and res.visited_distant[1] == 0
     # level 1: 4 cells -> 4 * 5 / 2 unordered pairs incl. self
     assert res.visited_neighbour[1] == 10
+
+
+def test_splitmix64_finalizer_known_outputs():
+    """The edge checksum's mixing function against the first outputs of splitmix64."""
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "splitmix64_seed0.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    for k, state, out in rows:
+        assert int(state, 16) == (int(k) * 0x9E3779B97F4A7C15) % (1 << 64)
+        assert int(O.splitmix64_finalize(np.uint64(int(state, 16)))) == int(out, 16)
+
+
+def test_edge_checksum_is_order_independent():
+    rng = np.random.default_rng(3)
+    e = rng.integers(0, 1 << 31, size=(1000, 2))
+    assert O.edge_checksum(e) == O.edge_checksum(e[::-1]) == O.edge_checksum(e[:, ::-1])
+    assert O.edge_checksum(e[:999]) != O.edge_checksum(e)
