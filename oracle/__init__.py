@@ -13,6 +13,7 @@ same bits on every IEEE machine.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -94,7 +95,8 @@ def _load():
             "orc_hrg_cellpairs": (i64, [i64, P, P, dbl, dbl, u64, P, i64, P, P, P, P, P,
                                         i64, P, i32, i32]),
             "orc_girg_avg_degree": (dbl, [dbl, i64, i32, dbl, P, dbl]),
-            "orc_girg_solve_c": (dbl, [dbl, i64, i32, dbl, P, dbl]),
+            "orc_girg_solve_K": (dbl, [dbl, i64, i32, dbl, P, dbl]),
+            "orc_girg_K_of_c": (dbl, [dbl, i32, dbl]),
             "orc_hrg_avg_degree": (dbl, [i64, dbl, dbl, dbl]),
             "orc_hrg_solve_R": (dbl, [i64, dbl, dbl, dbl]),
         }
@@ -175,12 +177,29 @@ def pair_coin(seed: int, u: int, v: int) -> float:
     return _load().orc_pair_coin(seed, u, v)
 
 
-def girg_p(d, T, c, W, wu, wv, D) -> float:
-    return _load().orc_girg_p(d, T, c, W, wu, wv, D)
+def K_of_c(c, d, T) -> float:
+    """The scale K of the model for the c of Eq. 1: c^T (T > 0) or c^d (T = 0)."""
+    return _load().orc_girg_K_of_c(c, d, T)
 
 
-def girg_thresh_edge(d, c, W, wu, wv, D) -> bool:
-    return bool(_load().orc_girg_thresh_edge(d, c, W, wu, wv, D))
+def c_of_K(K, d, T) -> float:
+    """The c of Eq. 1 for a scale K (0 or inf where it leaves the range of doubles)."""
+    e = math.log(K) / (T if T > 0.0 else d)
+    return 0.0 if e < -745.0 else (math.inf if e > 709.0 else math.exp(e))
+
+
+def _scale(c, d, T, K):
+    return K if K is not None else K_of_c(c, d, T)
+
+
+def girg_p(d, T, c, W, wu, wv, D, K=None) -> float:
+    """Eq. 1, p = min{1, (K q / r^d)^(1/T)} with K = c^T (c ignored if K is given)."""
+    return _load().orc_girg_p(d, T, _scale(c, d, T, K), W, wu, wv, D)
+
+
+def girg_thresh_edge(d, c, W, wu, wv, D, K=None) -> bool:
+    """Threshold variant: r^d <= K w_u w_v / W with K = c^d."""
+    return bool(_load().orc_girg_thresh_edge(d, _scale(c, d, 0.0, K), W, wu, wv, D))
 
 
 def hrg_coshd(ru, rv, D) -> float:
@@ -219,16 +238,17 @@ def _edges_array(cap):
     return np.zeros((max(cap, 1), 2), dtype=np.uint32)
 
 
-def girg_allpairs(X, w, W, T, c, seed, cap=None):
+def girg_allpairs(X, w, W, T, c, seed, cap=None, K=None):
     """Oracle 1: (m, 2) uint32 edges (u < v) of the quadratic generator."""
     X = np.ascontiguousarray(X, dtype=np.uint32)
     w = np.ascontiguousarray(w, dtype=np.float64)
     n, d = X.shape
+    K = _scale(c, d, T, K)
     if cap is None:
         cap = 1 << 16
     while True:
         e = _edges_array(cap)
-        m = _load().orc_girg_allpairs(n, d, _ptr(X), _ptr(w), W, T, c, seed, _ptr(e), cap)
+        m = _load().orc_girg_allpairs(n, d, _ptr(X), _ptr(w), W, T, K, seed, _ptr(e), cap)
         if m <= cap:
             return e[:m].copy()
         cap = m
@@ -286,11 +306,12 @@ def _items_to_records(raw, k):
 
 
 def girg_cellpairs(X, w, w_min, W, T, c, seed, cap=None, want_items=False, skip_sampling=False,
-                   items_cap=None, level_cap=0):
+                   items_cap=None, level_cap=0, K=None):
     """Oracle 2 for GIRGs (Algorithm 1 with App. B.1)."""
     X = np.ascontiguousarray(X, dtype=np.uint32)
     w = np.ascontiguousarray(w, dtype=np.float64)
     n, d = X.shape
+    K = _scale(c, d, T, K)
     if cap is None:
         cap = 1 << 16
     while True:
@@ -303,7 +324,7 @@ def girg_cellpairs(X, w, w_min, W, T, c, seed, cap=None, want_items=False, skip_
         icap = items_cap if items_cap is not None else (1 << 20)
         items = np.zeros((icap if want_items else 1, 12), dtype=np.int64)
         m = _load().orc_girg_cellpairs(
-            n, d, _ptr(X), _ptr(w), w_min, W, T, c, seed, _ptr(e), cap, _ptr(stats),
+            n, d, _ptr(X), _ptr(w), w_min, W, T, K, seed, _ptr(e), cap, _ptr(stats),
             _ptr(order), _ptr(itab), _ptr(wtab), _ptr(items) if want_items else None,
             icap if want_items else 0, _ptr(nitems), 1 if skip_sampling else 0, level_cap)
         if m < 0:
@@ -351,20 +372,25 @@ def hrg_cellpairs(X, r, R, T, seed, cap=None, want_items=False, skip_sampling=Fa
 
 # ---------------------------------------------------------------- degree / c
 
-def girg_avg_degree(c, w, d, T, W=None):
-    """Expected average degree f(c) of App. B.2 for the given weights."""
+def girg_avg_degree(c, w, d, T, W=None, K=None):
+    """Expected average degree f of App. B.2 for the given weights at c (or scale K)."""
     w = np.ascontiguousarray(w, dtype=np.float64)
     if W is None:
         W = exact_sum(w)
-    return _load().orc_girg_avg_degree(c, len(w), d, T, _ptr(w), W)
+    return _load().orc_girg_avg_degree(_scale(c, d, T, K), len(w), d, T, _ptr(w), W)
+
+
+def girg_solve_K(target, w, d, T, W=None):
+    """The scale K (c^T, or c^d at T = 0) whose expected average degree is ``target``."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    if W is None:
+        W = exact_sum(w)
+    return _load().orc_girg_solve_K(target, len(w), d, T, _ptr(w), W)
 
 
 def girg_solve_c(target, w, d, T, W=None):
     """The c of Eq. 1 whose expected average degree is ``target`` (App. B.2)."""
-    w = np.ascontiguousarray(w, dtype=np.float64)
-    if W is None:
-        W = exact_sum(w)
-    return _load().orc_girg_solve_c(target, len(w), d, T, _ptr(w), W)
+    return c_of_K(girg_solve_K(target, w, d, T, W), d, T)
 
 
 def hrg_avg_degree(n, alpha, T, R):

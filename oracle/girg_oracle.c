@@ -357,76 +357,78 @@ static uint32_t torus_dist(const uint32_t* xu, const uint32_t* xv, int d) {
     return m;
 }
 
+/* The GIRG model with its scale K: K = c^T for T > 0 and K = c^d for T = 0,
+ * c the constant of Eq. 1.  Eq. 1 reads p = min{1, (K q / r^d)^(1/T)} with
+ * q = w_u w_v / W, and the threshold variant connects iff r^d <= K q.  K stays
+ * a moderate number for every T, where c = K^(1/T) leaves the range of doubles
+ * as T -> 0. */
 typedef struct {
     int d;
-    double T, c, W;
+    double T, K, W;
     int m_int;   /* 1/T when it is an integer in [1,64], else 0 */
     double invT; /* 1/T */
 } girg_model;
 
-static void girg_model_init(girg_model* M, int d, double T, double c, double W) {
+static void girg_model_init(girg_model* M, int d, double T, double K, double W) {
     M->d = d;
     M->T = T;
-    M->c = c;
+    M->K = K;
     M->W = W;
     M->invT = T > 0.0 ? 1.0 / T : 0.0;
     M->m_int = 0;
     if (T > 0.0 && M->invT == floor(M->invT) && M->invT <= 64.0) M->m_int = (int)M->invT;
 }
 
-/* Eq. 1: p = min{1, c ((w_u w_v / W) / r^d)^(1/T)}; r = D 2^-32. */
-static double girg_p(const girg_model* M, double wu, double wv, uint32_t D) {
-    if (D == 0) return 1.0;
-    double q = (wu * wv) / M->W;
-    double r = (double)D * 0x1p-32;
-    double rd = r;
-    for (int k = 1; k < M->d; k++) rd = rd * r;
-    double base = q / rd;
-    double p;
-    if (M->m_int > 0) {
-        p = base;
-        for (int k = 1; k < M->m_int; k++) p = p * base;
-    } else {
-        p = orc_det_exp(M->invT * orc_det_log(base));
-    }
-    p = M->c * p;
-    return p < 1.0 ? p : 1.0;
-}
-
-/* Same formula at a real-valued distance r (used for the type-II bound). */
+/* Eq. 1 at distance r: x = K q / r^d, p = 1 if x >= 1 else x^(1/T) (repeated
+ * products when 1/T is an integer). */
 static double girg_p_at(const girg_model* M, double wu, double wv, double r) {
     double q = (wu * wv) / M->W;
     double rd = r;
     for (int k = 1; k < M->d; k++) rd = rd * r;
-    double base = q / rd;
+    double x = (M->K * q) / rd;
+    if (x >= 1.0) return 1.0;
     double p;
     if (M->m_int > 0) {
-        p = base;
-        for (int k = 1; k < M->m_int; k++) p = p * base;
+        p = x;
+        for (int k = 1; k < M->m_int; k++) p = p * x;
     } else {
-        p = orc_det_exp(M->invT * orc_det_log(base));
+        p = orc_det_exp(M->invT * orc_det_log(x));
     }
-    p = M->c * p;
-    return p < 1.0 ? p : 1.0;
+    return p;
 }
 
-/* Threshold variant: edge iff ||x_u - x_v|| <= c (w_u w_v / W)^(1/d). */
+/* Eq. 1 at the fixed-point distance D (r = D 2^-32; r = 0 gives p = 1). */
+static double girg_p(const girg_model* M, double wu, double wv, uint32_t D) {
+    if (D == 0) return 1.0;
+    return girg_p_at(M, wu, wv, (double)D * 0x1p-32);
+}
+
+/* Threshold variant: edge iff ||x_u - x_v||^d <= K w_u w_v / W (r <= c q^(1/d)). */
 static int girg_thresh_edge(const girg_model* M, double wu, double wv, uint32_t D) {
     double q = (wu * wv) / M->W;
-    double thr = M->c * root_d(q, M->d);
     double r = (double)D * 0x1p-32;
-    return r <= thr;
+    double rd = r;
+    for (int k = 1; k < M->d; k++) rd = rd * r;
+    return rd <= M->K * q;
 }
 
-double orc_girg_p(int d, double T, double c, double W, double wu, double wv, uint32_t D) {
+/* K from the c of Eq. 1: c^T (T > 0) or c^d (T = 0). */
+double orc_girg_K_of_c(double c, int d, double T) {
+    if (T > 0.0) return orc_det_pow(c, T);
+    double k = c;
+    for (int i = 1; i < d; i++) k = k * c;
+    return k;
+}
+
+double orc_girg_p(int d, double T, double K, double W, double wu, double wv, uint32_t D) {
     girg_model M;
-    girg_model_init(&M, d, T, c, W);
+    girg_model_init(&M, d, T, K, W);
     return girg_p(&M, wu, wv, D);
 }
 
-int orc_girg_thresh_edge(int d, double c, double W, double wu, double wv, uint32_t D) {
+int orc_girg_thresh_edge(int d, double K, double W, double wu, double wv, uint32_t D) {
     girg_model M;
-    girg_model_init(&M, d, 0.0, c, W);
+    girg_model_init(&M, d, 0.0, K, W);
     return girg_thresh_edge(&M, wu, wv, D);
 }
 
@@ -499,9 +501,9 @@ static void emit(uint32_t* edges, int64_t cap, int64_t* m, uint32_t a, uint32_t 
 }
 
 int64_t orc_girg_allpairs(int64_t n, int d, const uint32_t* X, const double* w, double W,
-                          double T, double c, uint64_t seed, uint32_t* edges, int64_t cap) {
+                          double T, double K, uint64_t seed, uint32_t* edges, int64_t cap) {
     girg_model M;
-    girg_model_init(&M, d, T, c, W);
+    girg_model_init(&M, d, T, K, W);
     int64_t m = 0;
     for (int64_t u = 0; u < n; u++) {
         for (int64_t v = u + 1; v < n; v++) {
@@ -708,11 +710,8 @@ static int comparison_level(cp_ctx* C, int i, int j) {
     if (C->model == 0) {
         const girg_model* M = &C->M;
         double qmax = (C->wmax[i] * C->wmax[j]) / M->W;
-        double kappa;
-        if (M->T > 0.0)
-            kappa = root_d(orc_det_pow(M->c, M->T) * qmax, M->d);
-        else
-            kappa = M->c * root_d(qmax, M->d);
+        /* the distance at which p reaches 1 (T > 0) or the threshold (T = 0) */
+        double kappa = root_d(M->K * qmax, M->d);
         return level_for_kappa(kappa, C->lcap);
     }
     /* HRG: deepest level whose distant cell pairs (angular gap >= one cell)
@@ -1126,7 +1125,7 @@ static void export_tables(cp_ctx* C, int32_t* itab, double* wtab) {
  * visited neighbouring, distant and (A, A) cell pairs; items/items_cap an optional
  * item log; skip_sampling enumerates items without drawing. */
 int64_t orc_girg_cellpairs(int64_t n, int d, const uint32_t* X, const double* w, double w_min,
-                           double W, double T, double c, uint64_t seed, uint32_t* edges,
+                           double W, double T, double K, uint64_t seed, uint32_t* edges,
                            int64_t cap, int64_t* stats, int64_t* order_out, int32_t* itab,
                            double* wtab, int64_t* items, int64_t items_cap, int64_t* n_items,
                            int skip_sampling, int lcap_override) {
@@ -1138,7 +1137,7 @@ int64_t orc_girg_cellpairs(int64_t n, int d, const uint32_t* X, const double* w,
     C.seed = seed;
     C.X = X;
     C.w = w;
-    girg_model_init(&C.M, d, T, c, W);
+    girg_model_init(&C.M, d, T, K, W);
     C.edges = edges;
     C.cap = cap;
     C.items = items;
@@ -1210,7 +1209,7 @@ int64_t orc_hrg_cellpairs(int64_t n, const uint32_t* X, const double* r, double 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Expected average degree and the search for c (Sec. 4.1, App. B.2)         */
+/* Expected average degree and the search for the scale (Sec. 4.1, App. B.2) */
 /* ------------------------------------------------------------------------ */
 
 static int cmp_desc(const void* a, const void* b) {
@@ -1218,123 +1217,109 @@ static int cmp_desc(const void* a, const void* b) {
     return x > y ? -1 : (x < y ? 1 : 0);
 }
 
+/* For a pair u != v let z = 2^d K w_u w_v / W.  Integrating Eq. 1 over the
+ * uniform position of v on the torus (an L-infinity ball of volume (2r)^d):
+ * p = 1 for r^d <= K q, so if z >= 1 the whole torus (r <= 1/2) gives p = 1 and
+ * E[X_uv] = 1 (the pairs E_R of App. B.2); otherwise
+ *   E[X_uv] = z / (1 - T) - T z^(1/T) / (1 - T)   (T > 0),   z   (T = 0).
+ * f(K) = (1/n) sum over ordered pairs u != v.  With the weights sorted in
+ * decreasing order, the E_R partners of u are a prefix (w_v >= 1 / (A w_u),
+ * A = 2^d K / W) and the other partners the suffix; their sums of w_v and of
+ * w_v^(1/T) come from suffix sums accumulated from the light end, the latter as
+ * a log-sum-exp so that no power of a weight is ever formed (z^(1/T) < 1 on the
+ * suffix, while w^(1/T) alone leaves the range of doubles for small T). */
 typedef struct {
     int64_t n;
     int d;
     double T, W;
-    double S1;   /* W - sum w^2 / W */
-    double S2;   /* (sum w^(1/T))^2 / W^(1/T) - sum (w^2/W)^(1/T) */
-    double* ws;  /* weights sorted descending */
-    double* pw;  /* prefix sums of ws */
-    double* pwt; /* prefix sums of ws^(1/T) */
+    double* ws;  /* weights, decreasing */
+    double* lw;  /* their logarithms */
+    double* suf; /* suf[i] = sum_{j >= i} ws[j] */
+    double* lse; /* lse[i] = log sum_{j >= i} exp(lw[j] / T) (T > 0) */
 } deg_ctx;
-
-/* E[X_uv] of App. B.2 without the min (Eq. shortlong), as a function of
- * q = w_u w_v / W; for T = 0 it is 2^d c^d q. */
-static double ex_uv_nomin(const deg_ctx* G, double c, double q) {
-    if (G->T == 0.0) return ldexp(pow(c, G->d), G->d) * q;
-    double T = G->T;
-    return pow(c, T) * ldexp(1.0, G->d) / (1.0 - T) * q -
-           c * pow(2.0, G->d / T) / (1.0 / T - 1.0) * pow(q, 1.0 / T);
-}
-
-/* f(c) = E[avg degree] (App. B.2): the min-free double sum minus the error
- * over E_R, the ordered pairs u != v whose min takes effect, i.e. with
- * k = c^(T/d) q^(1/d) > 1/2 (T > 0) or 2^d c^d q > 1 (T = 0). */
-double deg_f(const deg_ctx* G, double c) {
-    int d = G->d;
-    double T = G->T;
-    double main_term;
-    double qstar; /* pairs with q > qstar are in E_R */
-    if (T == 0.0) {
-        double cd = ldexp(pow(c, d), d);
-        main_term = cd * G->S1;
-        qstar = 1.0 / cd;
-    } else {
-        main_term = pow(c, T) * ldexp(1.0, d) / (1.0 - T) * G->S1 -
-                    c * pow(2.0, d / T) / (1.0 / T - 1.0) * G->S2;
-        qstar = ldexp(1.0, -d) / pow(c, T);
-    }
-    /* error over E_R: for each u (descending), partners v form a prefix of
-     * the descending order */
-    double err = 0.0;
-    int64_t n = G->n;
-    int64_t kpref = n; /* prefix length for the current u, shrinking */
-    for (int64_t a = 0; a < n; a++) {
-        double wu = G->ws[a];
-        double lim = qstar * G->W / wu; /* partners need w_v > lim */
-        while (kpref > 0 && !(G->ws[kpref - 1] > lim)) kpref--;
-        if (kpref == 0) break;
-        int64_t cnt = kpref;
-        double sw = G->pw[kpref];
-        double swt = T > 0.0 ? G->pwt[kpref] : 0.0;
-        if (a < kpref) { /* u itself is in the prefix: drop the self pair */
-            cnt -= 1;
-            sw -= wu;
-            if (T > 0.0) swt -= pow(wu, 1.0 / T);
-        }
-        if (cnt <= 0) continue;
-        double s;
-        if (T == 0.0) {
-            s = ldexp(pow(c, d), d) * (wu / G->W) * sw;
-        } else {
-            s = pow(c, T) * ldexp(1.0, d) / (1.0 - T) * (wu / G->W) * sw -
-                c * pow(2.0, d / T) / (1.0 / T - 1.0) * pow(wu / G->W, 1.0 / T) * swt;
-        }
-        err += s - (double)cnt;
-    }
-    return (main_term - err) / (double)n;
-}
 
 static void deg_init(deg_ctx* G, int64_t n, int d, double T, const double* w, double W) {
     G->n = n;
     G->d = d;
     G->T = T;
     G->W = W;
-    double s2 = 0.0, st = 0.0, s2t = 0.0;
-    for (int64_t v = 0; v < n; v++) {
-        s2 += w[v] * w[v];
-        if (T > 0.0) {
-            st += pow(w[v], 1.0 / T);
-            s2t += pow(w[v] * w[v] / W, 1.0 / T);
-        }
-    }
-    G->S1 = W - s2 / W;
-    G->S2 = T > 0.0 ? st * st / pow(W, 1.0 / T) - s2t : 0.0;
-    G->ws = malloc(sizeof(double) * (n ? n : 1));
-    memcpy(G->ws, w, sizeof(double) * n);
+    size_t sz = sizeof(double) * (size_t)(n + 1);
+    G->ws = malloc(sz);
+    G->lw = malloc(sz);
+    G->suf = malloc(sz);
+    G->lse = malloc(sz);
+    memcpy(G->ws, w, sizeof(double) * (size_t)n);
     qsort(G->ws, (size_t)n, sizeof(double), cmp_desc);
-    G->pw = malloc(sizeof(double) * (n + 1));
-    G->pwt = malloc(sizeof(double) * (n + 1));
-    G->pw[0] = 0.0;
-    G->pwt[0] = 0.0;
-    for (int64_t a = 0; a < n; a++) {
-        G->pw[a + 1] = G->pw[a] + G->ws[a];
-        G->pwt[a + 1] = G->pwt[a] + (T > 0.0 ? pow(G->ws[a], 1.0 / T) : 0.0);
+    G->suf[n] = 0.0;
+    G->lse[n] = -INFINITY;
+    for (int64_t i = n - 1; i >= 0; i--) {
+        G->lw[i] = log(G->ws[i]);
+        G->suf[i] = G->suf[i + 1] + G->ws[i];
+        if (T > 0.0) {
+            double b = G->lw[i] / T; /* the largest term of the suffix from i */
+            G->lse[i] = b + log1p(exp(G->lse[i + 1] - b));
+        }
     }
 }
 
 static void deg_free(deg_ctx* G) {
     free(G->ws);
-    free(G->pw);
-    free(G->pwt);
+    free(G->lw);
+    free(G->suf);
+    free(G->lse);
 }
 
-double orc_girg_avg_degree(double c, int64_t n, int d, double T, const double* w, double W) {
+static double deg_f(const deg_ctx* G, double K) {
+    const int64_t n = G->n;
+    const double T = G->T, A = ldexp(K, G->d) / G->W, lA = log(A);
+    double total = 0.0;
+    int64_t k = n; /* E_R partners of u: indices < k (shrinks as w_u decreases) */
+    for (int64_t u = 0; u < n; u++) {
+        while (k > 0 && A * G->ws[u] * G->ws[k - 1] < 1.0) k--;
+        double cnt = (double)k - (u < k ? 1.0 : 0.0);
+        /* suffix [k, n) without u */
+        double sw, ls;
+        if (u < k) {
+            sw = G->suf[k];
+            ls = G->lse[k];
+        } else if (u == k) {
+            sw = G->suf[k + 1];
+            ls = G->lse[k + 1];
+        } else {
+            sw = G->suf[k] - G->ws[u];
+            ls = T > 0.0 ? G->lse[k] + log1p(-exp(G->lw[u] / T - G->lse[k])) : 0.0;
+        }
+        double z_sum = A * G->ws[u] * sw;
+        double e = z_sum;
+        if (T > 0.0) {
+            double zt_sum = exp((lA + G->lw[u]) / T + ls); /* sum of z^(1/T) */
+            e = (z_sum - T * zt_sum) / (1.0 - T);
+        }
+        total += cnt + e;
+    }
+    return total / (double)n;
+}
+
+double orc_girg_avg_degree(double K, int64_t n, int d, double T, const double* w, double W) {
     deg_ctx G;
     deg_init(&G, n, d, T, w, W);
-    double f = deg_f(&G, c);
+    double f = deg_f(&G, K);
     deg_free(&G);
     return f;
 }
 
-/* Exponential search for a bracket, then bisection on log c until the
- * bracket is 1e-13 relative or 200 steps; f is increasing in c. */
-double orc_girg_solve_c(double target, int64_t n, int d, double T, const double* w, double W) {
+/* The scale K with f(K) = target: f increases with K.  Start from the K at
+ * which the E_R-free sum alone reaches the target, bracket by doubling or
+ * halving, then bisect on log K until the bracket is 1e-13 relative. */
+double orc_girg_solve_K(double target, int64_t n, int d, double T, const double* w, double W) {
     deg_ctx G;
     deg_init(&G, n, d, T, w, W);
-    double lo = 1.0, hi = 1.0;
-    if (deg_f(&G, 1.0) < target) {
+    double s2 = 0.0;
+    for (int64_t i = n - 1; i >= 0; i--) s2 += G.ws[i] * G.ws[i];
+    double K0 = target * (double)n * W * (T > 0.0 ? 1.0 - T : 1.0) / (ldexp(1.0, d) * (W * W - s2));
+    if (!(K0 > 1e-300 && K0 < 1e300)) K0 = 1.0;
+    double lo = K0, hi = K0;
+    if (deg_f(&G, K0) < target) {
         while (deg_f(&G, hi) < target && hi < 1e300) hi *= 2.0;
         lo = hi / 2.0;
     } else {
