@@ -136,6 +136,117 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+BATCH = dict(workload="girg_batch_mixed", n_lo=1e3, n_hi=1e6, dims=(1, 2, 3), beta=(2.1, 3.0),
+             T=(0.0, 0.9), deg=(4.0, 32.0), base_seed=1, offered_load=1.5)
+
+
+def _splitmix64(x: int) -> int:
+    x = (x + 0x9E3779B97F4A7C15) % (1 << 64)
+    z = ((x ^ (x >> 30)) * 0xBF58476D1CE4E5B9) % (1 << 64)
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) % (1 << 64)
+    return z ^ (z >> 31)
+
+
+def batch_requests(k: int) -> list:
+    """The mixed request set: n log-uniform in [1e3, 1e6], d in {1, 2, 3}, beta uniform in
+    [2.1, 3.0], T uniform in [0, 0.9], average degree log-uniform in [4, 32], seed of
+    request r = splitmix64(base_seed 2^32 + r)."""
+    import numpy as np
+    rng = np.random.default_rng(BATCH["base_seed"])
+    out = []
+    for r in range(k):
+        out.append(dict(n=int(math.exp(rng.uniform(math.log(BATCH["n_lo"]), math.log(BATCH["n_hi"])))),
+                        d=int(rng.choice(BATCH["dims"])), beta=float(rng.uniform(*BATCH["beta"])),
+                        T=float(rng.uniform(*BATCH["T"])),
+                        avg_deg=float(math.exp(rng.uniform(math.log(BATCH["deg"][0]),
+                                                           math.log(BATCH["deg"][1])))),
+                        seed=_splitmix64((BATCH["base_seed"] << 32) + r)))
+    return out
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(q * (len(xs) - 1) + 0.5))] if xs else None
+
+
+def run_batched(gg, torch, k: int, workers_grid=(4, 8, 16)) -> dict:
+    """Batched/served generation of k mixed requests: one-at-a-time plain calls versus the
+    continuous-batching server (closed-loop capacity, and Poisson arrivals at 1.5x the
+    plain capacity with p50 / p99 latency from arrival to completion)."""
+    import numpy as np
+    reqs = batch_requests(k)
+    caps = [int(q["n"] * q["avg_deg"]) + 4096 for q in reqs]  # twice the expected edges
+    offs = [0]
+    for c in caps:
+        offs.append(offs[-1] + c)
+    arena = torch.empty((offs[-1], 2), dtype=torch.int32, device="cuda")
+    views = [arena[offs[i]:offs[i + 1]] for i in range(k)]
+    # plain: one request at a time on one stream
+    for q, v in zip(reqs[:8], views[:8]):
+        gg.girg_generate(v, **q)
+    torch.cuda.synchronize()
+    service, edges, bad = [], 0, 0
+    t_all = time.perf_counter()
+    for q, v in zip(reqs, views):
+        t0 = time.perf_counter()
+        r = gg.girg_generate(v, **q)
+        service.append(time.perf_counter() - t0)
+        edges += r.num_edges
+        bad += r.status != gg.GIRG_OK
+    plain_s = time.perf_counter() - t_all
+    rate = BATCH["offered_load"] * k / plain_s  # requests per second offered
+    rng = np.random.default_rng(BATCH["base_seed"] + 1)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=k))
+    # a single FIFO server with the measured service times sees these latencies
+    done, plain_lat = 0.0, []
+    for a, sv in zip(arrivals, service):
+        done = max(done, a) + sv
+        plain_lat.append(done - a)
+
+    def serve(workers, idx, arrive):
+        with gg.Server(workers=workers, memory_budget_bytes=96 << 30) as srv:
+            t0 = srv.clock_us()
+            for j, i in enumerate(idx):
+                if arrive is not None:
+                    wait = t0 + arrive[j] * 1e6 - srv.clock_us()
+                    if wait > 0:
+                        time.sleep(wait / 1e6)
+                srv.submit(i, views[i], **reqs[i])
+            res = []
+            while len(res) < len(idx):
+                res += srv.poll(4096, wait_for=1)
+        return t0, res
+
+    # autotune the number of workers on a closed-loop sample
+    sample = list(range(0, k, max(1, k // 256)))
+    tune = {}
+    for w in workers_grid:
+        _, res = serve(w, sample, None)
+        tune[w] = sum(r.num_edges for r in res) / ((max(r.t_done_us for r in res) -
+                                                    min(r.t_submit_us for r in res)) / 1e6)
+    workers = max(tune, key=tune.get)
+    _, res = serve(workers, list(range(k)), None)
+    span = (max(r.t_done_us for r in res) - min(r.t_submit_us for r in res)) / 1e6
+    cap_edges = sum(r.num_edges for r in res)
+    bad += sum(r.status != gg.GIRG_OK for r in res)
+    t0, res = serve(workers, list(range(k)), arrivals)
+    lat = [(r.t_done_us - (t0 + arrivals[r.request_id] * 1e6)) / 1e3 for r in res]
+    span2 = (max(r.t_done_us for r in res) - t0) / 1e6
+    bad += sum(r.status != gg.GIRG_OK for r in res)
+    return {"workload": BATCH["workload"], "requests": k, "edges": edges,
+            "recipe": "n log-uniform [1e3,1e6], d in {1,2,3}, beta U[2.1,3.0], T U[0,0.9], "
+                      "avg deg log-uniform [4,32], seeds splitmix64(2^32 + r), int32 edges",
+            "failed_requests": int(bad),
+            "plain": {"edges_per_s": edges / plain_s, "seconds": plain_s,
+                      "p50_ms": _pct(plain_lat, 0.5) * 1e3, "p99_ms": _pct(plain_lat, 0.99) * 1e3,
+                      "note": "one girg_generate call at a time; latencies of a FIFO queue "
+                              "with the measured service times under the same arrivals"},
+            "server": {"workers": workers, "autotune_edges_per_s": tune,
+                       "capacity_edges_per_s": cap_edges / span,
+                       "poisson": {"rate_per_s": rate, "edges_per_s": cap_edges / span2,
+                                   "p50_ms": _pct(lat, 0.5), "p99_ms": _pct(lat, 0.99)}}}
+
+
 def cpu_baseline(cfg: dict) -> dict:
     """The FP64 oracle (as it stands) on a bounded sample: n = 1e5, same d, beta, T,
     average degree; points + search for c + cell-pair sampler, one host core."""
@@ -199,6 +310,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--batch-requests", type=int, default=4096,
+                    help="mixed requests of the batched/served run (0: skip it)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -353,6 +466,8 @@ def main():
             "gpu_launches": int(stats.get("kernel_launches", 0)) * args.steps,
             "clocks": clock_info,
         }
+        if args.batch_requests > 0:
+            line["batched"] = run_batched(gg, torch, args.batch_requests)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(cfg)
         print(json.dumps(line), flush=True)

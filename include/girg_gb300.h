@@ -179,6 +179,13 @@ int hrg_points(int64_t n, double alpha, double R, uint64_t seed, double* d_r, ui
  * weights generated from params->seed (params->c is the c evaluated). */
 int girg_expected_avg_degree(const girg_params* params, double* avg_deg, void* stream);
 
+/* The scale K of Eq. 1 used by the last generate call on this host thread: Eq. 1 is
+ * evaluated as p = min{1, (K q / r^d)^(1/T)}, q = w_u w_v / W, with K = c^T (T > 0),
+ * and the threshold variant as r^d <= K q with K = c^d (T = 0).  K stays a moderate
+ * number for every T, where c_used = K^(1/T) under- or overflows a double as T -> 0
+ * (it is then reported as 0 or infinity). */
+double girg_last_scale(void);
+
 /* Counters of the last generate call on this host thread: [0] type-I pairs tested,
  * [1] coins drawn, [2] FP64 rechecks, [3] type-II items (non-empty cell pairs),
  * [4] jump draws, [5] type-II candidates, [6] rows, [7] type-I items, [8] chunks of
@@ -208,6 +215,50 @@ int girg_sorted_order(int64_t n, int32_t d, const uint32_t* d_X, const double* d
  * 6 the GIRG probability of Eq. 1 at weights (x, y), r = 1/4, W = 1000, c = 1/2,
  * T = 3/4, d = 2.  Returns NaN for an unknown fn.  Diagnostic; no GPU needed. */
 double girg_det_eval(int32_t fn, double x, double y);
+
+/* ------------------------------------------------------------------------
+ * Continuous-batching server (many requests in flight on one GPU).
+ * Worker threads each run girg_generate on their own CUDA stream, so the kernels
+ * of concurrent requests overlap.  A request starts when a worker is free and its
+ * estimated scratch (girg_scratch_bytes) fits memory_budget_bytes next to the
+ * running ones (one request always may run); requests start in submission order,
+ * except that up to 16 later requests that fit may pass one that does not.  Each
+ * result equals that of a lone girg_generate call with the same parameters.  The
+ * caller owns the edge buffers and must keep them alive until the result is polled.
+ * The paper has no counterpart (its generator makes one graph per call). */
+typedef struct girg_server girg_server;
+
+typedef struct {
+    int64_t request_id;  /* as submitted */
+    int32_t status;      /* GIRG_* of the generation */
+    int32_t pad;
+    int64_t num_edges;
+    double c_used;
+    uint64_t checksum;   /* edge checksum, as girg_last_stats()[14] */
+    double t_submit_us;  /* server clock (girg_server_clock_us) */
+    double t_start_us;
+    double t_done_us;
+} girg_request_result;
+
+/* Estimated peak device scratch of girg_generate for these parameters (bytes), or -1. */
+int64_t girg_scratch_bytes(const girg_params* params);
+/* Start `workers` worker threads on the current device.  Errors: GIRG_E_PARAM, GIRG_E_CUDA. */
+int girg_server_create(int32_t workers, int64_t memory_budget_bytes, girg_server** out);
+/* Queue one request (non-blocking; parameters are copied).  d_edges / capacity_edges as
+ * for girg_generate (edge_bytes 0: count-only). */
+int girg_server_submit(girg_server* server, const girg_params* params, void* d_edges,
+                       int64_t capacity_edges, int64_t request_id);
+/* Move up to max_results finished results into out (completion order); if wait_for > 0,
+ * first block until min(wait_for, max_results) are available or nothing is queued or
+ * running.  Returns the number written, or -GIRG_E_PARAM. */
+int girg_server_poll(girg_server* server, girg_request_result* out, int32_t max_results,
+                     int32_t wait_for);
+/* Requests queued or running. */
+int girg_server_pending(girg_server* server);
+/* Microseconds since the server was created (the clock of the result timestamps). */
+double girg_server_clock_us(girg_server* server);
+/* Finish every queued request, stop the workers and free the server. */
+int girg_server_destroy(girg_server* server);
 
 /* Human-readable name of a status code (static storage). */
 const char* girg_status_string(int status);

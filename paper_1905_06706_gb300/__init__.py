@@ -71,7 +71,23 @@ SIGNATURES = {
     "girg_sorted_order": (I32, [I64, I32, P, P, DBL, DBL, I32, P, P]),
     "girg_status_string": (ctypes.c_char_p, [I32]),
     "girg_det_eval": (DBL, [I32, DBL, DBL]),
+    "girg_last_scale": (DBL, []),
+    "girg_scratch_bytes": (I64, [P]),
+    "girg_server_create": (I32, [I32, I64, P]),
+    "girg_server_submit": (I32, [P, P, P, I64, I64]),
+    "girg_server_poll": (I32, [P, P, I32, I32]),
+    "girg_server_pending": (I32, [P]),
+    "girg_server_clock_us": (DBL, [P]),
+    "girg_server_destroy": (I32, [P]),
 }
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("num_edges", ctypes.c_int64),
+                ("c_used", ctypes.c_double), ("checksum", ctypes.c_uint64),
+                ("t_submit_us", ctypes.c_double), ("t_start_us", ctypes.c_double),
+                ("t_done_us", ctypes.c_double)]
 
 
 def load(build_if_missing: bool = True):
@@ -127,6 +143,11 @@ def last_stats() -> dict:
     out = dict(zip(STAT_NAMES, list(buf)))
     out["edge_checksum"] &= (1 << 64) - 1  # unsigned
     return out
+
+
+def last_K() -> float:
+    """The scale K (c^T, or c^d at T = 0) of this thread's last generate call."""
+    return load().girg_last_scale()
 
 
 def last_phase_ms() -> dict:
@@ -282,3 +303,57 @@ def girg_sorted_order(X, w, *, T, c, level_cap=0, stream=None):
     if st != GIRG_OK:
         raise GirgError(st, "girg_sorted_order")
     return order
+
+
+class Server:
+    """Continuous-batching generation server (C++ worker threads, one CUDA stream each).
+
+    ``submit`` queues a request and returns at once; ``poll`` returns finished results
+    (``RequestResult``) with server-clock timestamps.  Edge buffers (or None for
+    count-only) must stay alive until their result has been polled."""
+
+    def __init__(self, workers=8, memory_budget_bytes=64 << 30):
+        _torch()
+        self._lib = load()
+        self._h = ctypes.c_void_p()
+        st = self._lib.girg_server_create(workers, memory_budget_bytes, ctypes.byref(self._h))
+        if st != GIRG_OK:
+            raise GirgError(st, "girg_server_create")
+        self._keep = {}
+
+    def submit(self, request_id, edges, *, n, d, beta, T, avg_deg=0.0, c=0.0, w_min=1.0,
+               seed=1, precision=PRECISION_FP32, level_cap=0):
+        eb, ep, cap = _edge_args(edges)
+        p = GirgParams(n, d, beta, T, avg_deg, c, w_min, seed, eb, precision, level_cap)
+        st = self._lib.girg_server_submit(self._h, ctypes.byref(p), ep, cap, request_id)
+        if st != GIRG_OK:
+            raise GirgError(st, "girg_server_submit")
+        self._keep[request_id] = edges
+
+    def poll(self, max_results=1024, wait_for=0):
+        buf = (RequestResult * max_results)()
+        k = self._lib.girg_server_poll(self._h, buf, max_results, wait_for)
+        if k < 0:
+            raise GirgError(-k, "girg_server_poll")
+        out = [buf[i] for i in range(k)]
+        for r in out:
+            self._keep.pop(r.request_id, None)
+        return out
+
+    def pending(self):
+        return self._lib.girg_server_pending(self._h)
+
+    def clock_us(self):
+        return self._lib.girg_server_clock_us(self._h)
+
+    def close(self):
+        if self._h:
+            self._lib.girg_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+

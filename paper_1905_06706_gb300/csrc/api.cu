@@ -47,16 +47,17 @@ struct Scratch {
     cudaStream_t st;
     std::vector<void*> ptrs;
     explicit Scratch(cudaStream_t s) : st(s) {
-        static bool pool_set = false;
-        if (!pool_set) {
+        // keep freed pool memory for reuse by later calls (once per process; thread-safe)
+        static const bool pool_set = [] {
             int dev = 0;
             cudaMemPool_t pool;
             if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
                 uint64_t thr = ~0ull;
                 cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
             }
-            pool_set = true;
-        }
+            return true;
+        }();
+        (void)pool_set;
     }
     template <class T>
     T* get(size_t count) {
@@ -132,7 +133,7 @@ struct Problem {
     int model = 0;  // 0 GIRG, 1 HRG
     int64_t n = 0;
     int d = 1;
-    double T = 0, c = 0, W = 0, w_min = 1, R = 0, alpha = 0;
+    double T = 0, K = 0, W = 0, w_min = 1, R = 0, alpha = 0;  // K: scale of Eq. 1
     uint64_t seed = 0;
     int precision = 0, edge_bytes = 4, level_cap = 0;
     const uint32_t* X = nullptr;  // d x n, original order
@@ -178,8 +179,8 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
             int cl;
             if (girg) {
                 const double qmax = (wmax[i] * wmax[j]) / P.W;
-                const double kappa = P.T > 0.0 ? root_d(det_pow(P.c, P.T) * qmax, d)
-                                               : P.c * root_d(qmax, d);
+                // the distance at which p reaches 1 (T > 0) or the threshold (T = 0)
+                const double kappa = root_d(P.K * qmax, d);
                 cl = level_for_kappa(kappa, lcap);
             } else {
                 double gap = 0.0;
@@ -267,7 +268,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
                         double p;
                         if (girg) {
                             const double rmin = (double)g * std::ldexp(1.0, -l);
-                            p = girg_p_at(wmax[i], wmax[j], rmin, P.W, P.c, invT, m_int, d);
+                            p = girg_p_at(wmax[i], wmax[j], rmin, P.W, P.K, invT, m_int, d);
                         } else {
                             double gap = 0.0;
                             if (rlo[j] > rhi[i]) gap = rlo[j] - rhi[i];
@@ -352,7 +353,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     const double log2W_half = girg ? 0.5 * std::log2(P.W) : 0.0;
     if (girg) {
         sv = S.get<float>(n);
-        gamma = (float)(tzero ? 0.5 * std::log2(P.c) : (P.T / (2.0 * d)) * std::log2(P.c));
+        gamma = (float)(std::log2(P.K) / (2.0 * d));  // kappa_uv = s_u s_v, kappa^d = K q
         launch_gather_girg(n, d, sid, P.X, P.w, P.w_min, log2W_half, gamma, (float)(1.0 / d), Xs,
                            ws, sv, slayer, st);
     } else {
@@ -419,7 +420,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     cfg.seed_lo = (uint32_t)P.seed;
     cfg.seed_hi = (uint32_t)(P.seed >> 32);
     cfg.W = P.W;
-    cfg.c = P.c;
+    cfg.K = P.K;
     cfg.T = P.T;
     cfg.invT = invT;
     cfg.w_min = P.w_min;
@@ -597,75 +598,102 @@ int guarded(F&& f) {
     }
 }
 
-// Host copy of the heaviest weights gathered and sorted on the device together with
-// the reduction (pinned, one per host thread, kept for the life of the process).
-struct TopWeights {
+// Host copy of a weight split (pinned, one per host thread, kept for the life of the
+// process): the weights above thr (sorted on the device when there are at most
+// kTopSortMax of them) and the four sums over the rest.
+struct SplitHost {
     unsigned int count[2];  // gathered, sorted flag
-    double thr;             // every weight above thr was gathered
+    double thr;
+    double sums[4];         // sum w, sum w^2, sum (w/thr)^(1/T), sum (w/thr)^(2/T)
     double w[kTopSortMax];
 };
 
-TopWeights* pinned_top() {
-    thread_local TopWeights* p = nullptr;
+SplitHost* pinned_split() {
+    thread_local SplitHost* p = nullptr;
     if (!p) {
         void* q = nullptr;
-        CK(cudaMallocHost(&q, sizeof(TopWeights)));
-        p = static_cast<TopWeights*>(q);
+        CK(cudaMallocHost(&q, sizeof(SplitHost)));
+        p = static_cast<SplitHost*>(q);
     }
     return p;
 }
 
-// Launch the device-side gather of the heaviest weights and queue their copy into
-// the pinned host buffer (read after the next synchronisation).
-TopWeights* queue_top_weights(Problem& P, const Reduce* red, double target, Scratch& S,
-                              cudaStream_t st) {
-    unsigned int* cnt = S.get<unsigned int>(2);
-    double* thr = S.get<double>(1);
-    double* buf = S.get<double>(kTopSortMax);
-    CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned int), st));
-    launch_top_weights(P.n, P.w, red, P.d, P.T, target, exponent_of_ulp(P.w_min), thr, buf,
-                       kTopSortMax, cnt, st);
-    TopWeights* h = pinned_top();
-    CK(cudaMemcpyAsync(h->count, cnt, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&h->thr, thr, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(h->w, buf, sizeof(h->w), cudaMemcpyDeviceToHost, st));
-    return h;
+// Device buffers of the weight split.
+struct SplitDev {
+    unsigned int* cnt;
+    double *thr, *sums, *part, *buf;
+    unsigned int cap;
+};
+
+SplitDev split_buffers(int64_t n, Scratch& S) {
+    SplitDev D;
+    D.cnt = S.get<unsigned int>(2);
+    D.thr = S.get<double>(1);
+    D.sums = S.get<double>(4);
+    D.part = S.get<double>((size_t)4 * reduce_blocks(n));
+    D.cap = kTopSortMax;
+    D.buf = S.get<double>(D.cap);
+    return D;
 }
 
-// Solve c for the target degree from the device sums and the heaviest weights
-// (`pre`: weights gathered with the reduction, if any).
-double solve_c(Problem& P, double target, Scratch& S, cudaStream_t st, const TopWeights* pre) {
-    DegreeModel M(P.n, P.d, P.T, P.W, P.red.s2, P.red.st, P.red.s2t);
-    double wmax = 0.0;
-    for (int i = 0; i < kMaxLayers; ++i)
-        if (P.red.cnt[i]) wmax = std::max(wmax, bits_to_double(P.red.wmax[i]));
-    M.set_wmax(wmax);
-    if (pre && pre->count[1] == 1u && pre->count[0] <= kTopSortMax && pre->thr > 0.0)
-        M.set_top(std::vector<double>(pre->w, pre->w + pre->count[0]), pre->thr, true);
-    unsigned int* cntp = S.get<unsigned int>(1);
-    unsigned int capv = 1u << 16;
-    double* buf = S.get<double>(capv);
+// Queue the split at the threshold in D.thr and the copy of its results into h
+// (read after the next synchronisation).
+void queue_split(const Problem& P, SplitDev& D, SplitHost* h, cudaStream_t st) {
+    CK(cudaMemsetAsync(D.cnt, 0, 2 * sizeof(unsigned int), st));
+    launch_split_weights(P.n, P.w, D.thr, P.T, D.buf, D.cap, D.cnt, D.part, D.sums, st);
+    CK(cudaMemcpyAsync(h->count, D.cnt, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&h->thr, D.thr, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h->sums, D.sums, sizeof(h->sums), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h->w, D.buf, sizeof(h->w), cudaMemcpyDeviceToHost, st));
+}
+
+// Hand a finished split to the degree model; when more weights than the device sorts
+// were gathered, copy and sort them here (the buffer is enlarged and the split rerun
+// when they did not fit).
+void take_split(const Problem& P, DegreeModel& M, SplitDev& D, SplitHost* h, Scratch& S,
+                cudaStream_t st) {
+    unsigned int k = h->count[0];
+    if (h->count[1] == 1u) {
+        M.set_split(h->thr, std::vector<double>(h->w, h->w + k), h->sums[0], h->sums[1],
+                    h->sums[2], h->sums[3]);
+        return;
+    }
+    if (k > D.cap) {
+        D.cap = k + 1024;
+        D.buf = S.get<double>(D.cap);
+        queue_split(P, D, h, st);
+        CK(cudaStreamSynchronize(st));
+        k = h->count[0];
+    }
+    std::vector<double> top(k);
+    if (k) CK(cudaMemcpyAsync(top.data(), D.buf, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::sort(top.begin(), top.end(), [](double a, double b) { return a > b; });
+    M.set_split(h->thr, std::move(top), h->sums[0], h->sums[1], h->sums[2], h->sums[3]);
+}
+
+// Solve the scale K for the target degree from the split queued with the reduction;
+// a new split at a lower threshold is made only if the search needs it.
+double solve_K(Problem& P, double target, SplitDev& D, SplitHost* h, Scratch& S,
+               cudaStream_t st) {
+    DegreeModel M(P.n, P.d, P.T, P.W);
+    take_split(P, M, D, h, S, st);
     auto fetch = [&](double thr) {
-        for (;;) {
-            CK(cudaMemsetAsync(cntp, 0, sizeof(unsigned int), st));
-            launch_gather_above(P.n, P.w, thr, buf, capv, cntp, st);
-            unsigned int k = 0;
-            CK(cudaMemcpyAsync(&k, cntp, sizeof(k), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            if (k > capv) {
-                capv = k + 1024;
-                buf = S.get<double>(capv);
-                continue;
-            }
-            std::vector<double> h(k);
-            if (k) CK(cudaMemcpyAsync(h.data(), buf, k * sizeof(double), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            M.set_top(std::move(h), thr);
-            return;
-        }
+        CK(cudaMemcpyAsync(D.thr, &thr, sizeof(double), cudaMemcpyHostToDevice, st));
+        queue_split(P, D, h, st);
+        CK(cudaStreamSynchronize(st));
+        take_split(P, M, D, h, S, st);
     };
     return M.solve(target, fetch);
 }
+
+// The c of Eq. 1 for a scale K (0 or inf where it leaves the range of doubles).
+double c_of_K(double K, int d, double T) {
+    const double e = std::log(K) / (T > 0.0 ? T : (double)d);
+    return e < -745.0 ? 0.0 : (e > 709.0 ? INFINITY : std::exp(e));
+}
+
+thread_local double g_last_K = 0.0;
 
 }  // namespace
 
@@ -691,10 +719,12 @@ double girg_det_eval(int32_t fn, double x, double y) {
         case 3: return det_pow(x, y);
         case 4: return det_sinpi(x);
         case 5: return det_acosh(x);
-        case 6: return girg_p_at(x, y, 0.25, 1000.0, 0.5, 1.0 / 0.75, 0, 2);
+        case 6: return girg_p_at(x, y, 0.25, 1000.0, girg_K_of_c(0.5, 2, 0.75), 1.0 / 0.75, 0, 2);
         default: return dnan();
     }
 }
+
+double girg_last_scale(void) { return g_last_K; }
 
 int girg_last_stats(int64_t* out, int32_t len) {
     const int k = len < kNumStats ? len : kNumStats;
@@ -759,20 +789,29 @@ int girg_generate(const girg_params* params, void* d_edges, int64_t capacity_edg
         P.w = w;
         P.X = X;
         const bool solve = !(params->c > 0.0);
+        const int E0 = exponent_of_ulp(P.w_min);
         Reduce* red = new_reduce(S, st);
-        launch_reduce(P.n, w, nullptr, P.w_min, exponent_of_ulp(P.w_min), solve ? 1 : 0,
-                      P.T > 0.0 ? 1.0 / P.T : 0.0, red, st);
-        const TopWeights* top = solve ? queue_top_weights(P, red, params->avg_deg, S, st) : nullptr;
+        double* part_s2 = solve ? S.get<double>(reduce_blocks(P.n)) : nullptr;
+        launch_reduce(P.n, w, nullptr, P.w_min, E0, part_s2, red, st);
+        SplitDev D{};
+        SplitHost* h = nullptr;
+        if (solve) {  // the weight split for the degree model, before the one readback
+            D = split_buffers(P.n, S);
+            h = pinned_split();
+            launch_split_threshold(red, part_s2, P.n, P.d, P.T, params->avg_deg, E0, D.thr, st);
+            queue_split(P, D, h, st);
+        }
         tm.mark();
         auto h0 = std::chrono::steady_clock::now();
         read_reduce(P, red, st);
         g_ms[7] = (float)host_ms_since(h0);
         if (P.red.range_error) return GIRG_E_RANGE;
-        P.W = round128(P.red.sum_hi, P.red.sum_lo, exponent_of_ulp(P.w_min));
+        P.W = round128(P.red.sum_hi, P.red.sum_lo, E0);
         h0 = std::chrono::steady_clock::now();
-        P.c = solve ? solve_c(P, params->avg_deg, S, st, top) : params->c;
+        P.K = solve ? solve_K(P, params->avg_deg, D, h, S, st) : girg_K_of_c(params->c, P.d, P.T);
         g_ms[8] = (float)host_ms_since(h0);
-        if (c_used) *c_used = P.c;
+        g_last_K = P.K;
+        if (c_used) *c_used = solve ? c_of_K(P.K, P.d, P.T) : params->c;
         run_sampler(P, S, st, tm, d_edges, capacity_edges, num_edges, nullptr);
         finish_timing(tm);
         return P.edge_bytes != 0 && *num_edges > capacity_edges ? GIRG_E_CAPACITY : GIRG_OK;
@@ -796,32 +835,26 @@ int girg_expected_avg_degree(const girg_params* params, double* avg_deg, void* s
         uint32_t* X = S.get<uint32_t>((size_t)P.d * P.n);
         launch_girg_points(P.n, P.d, q.beta, P.w_min, q.seed, w, X, st);
         P.w = w;
+        const int E0 = exponent_of_ulp(P.w_min);
         Reduce* red = new_reduce(S, st);
-        launch_reduce(P.n, w, nullptr, P.w_min, exponent_of_ulp(P.w_min), 1,
-                      P.T > 0.0 ? 1.0 / P.T : 0.0, red, st);
+        launch_reduce(P.n, w, nullptr, P.w_min, E0, nullptr, red, st);
         read_reduce(P, red, st);
         if (P.red.range_error) return GIRG_E_RANGE;
-        P.W = round128(P.red.sum_hi, P.red.sum_lo, exponent_of_ulp(P.w_min));
-        DegreeModel M(P.n, P.d, P.T, P.W, P.red.s2, P.red.st, P.red.s2t);
+        P.W = round128(P.red.sum_hi, P.red.sum_lo, E0);
         double wmax = 0.0;
         for (int i = 0; i < kMaxLayers; ++i)
             if (P.red.cnt[i]) wmax = std::max(wmax, bits_to_double(P.red.wmax[i]));
-        M.set_wmax(wmax);
-        const double thr = 0.5 * M.needed_threshold(q.c);
-        unsigned int* cntp = S.get<unsigned int>(1);
-        unsigned int capv = (unsigned int)std::min<int64_t>(P.n, 1 << 22);
-        double* buf = S.get<double>(capv);
-        CK(cudaMemsetAsync(cntp, 0, sizeof(unsigned int), st));
-        launch_gather_above(P.n, w, thr, buf, capv, cntp, st);
-        unsigned int k = 0;
-        CK(cudaMemcpyAsync(&k, cntp, sizeof(k), cudaMemcpyDeviceToHost, st));
+        const double K = girg_K_of_c(q.c, P.d, P.T);
+        // split below the weight at which E_R pairs can begin
+        const double thr = 0.5 * P.W / (std::ldexp(K, P.d) * wmax);
+        SplitDev D = split_buffers(P.n, S);
+        SplitHost* h = pinned_split();
+        CK(cudaMemcpyAsync(D.thr, &thr, sizeof(double), cudaMemcpyHostToDevice, st));
+        queue_split(P, D, h, st);
         CK(cudaStreamSynchronize(st));
-        if (k > capv) return GIRG_E_INTERNAL;
-        std::vector<double> h(k);
-        if (k) CK(cudaMemcpyAsync(h.data(), buf, k * sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        M.set_top(std::move(h), thr);
-        *avg_deg = M.f(q.c);
+        DegreeModel M(P.n, P.d, P.T, P.W);
+        take_split(P, M, D, h, S, st);
+        *avg_deg = M.f(K);
         return GIRG_OK;
     });
 }
@@ -846,7 +879,8 @@ static int from_points_impl(int64_t n, int32_t d, const uint32_t* d_X, const dou
         P.n = n;
         P.d = d;
         P.T = T;
-        P.c = c;
+        P.K = girg_K_of_c(c, d, T);
+        g_last_K = P.K;
         P.seed = seed;
         P.precision = precision;
         P.edge_bytes = edge_bytes;
@@ -863,7 +897,7 @@ static int from_points_impl(int64_t n, int32_t d, const uint32_t* d_X, const dou
         if (!(P.w_min > 0.0)) return GIRG_E_PARAM;
         const int E0 = exponent_of_ulp(P.w_min);
         Reduce* red = new_reduce(S, st);
-        launch_reduce(n, d_w, nullptr, P.w_min, E0, 0, 0.0, red, st);
+        launch_reduce(n, d_w, nullptr, P.w_min, E0, nullptr, red, st);
         tm.mark();
         read_reduce(P, red, st);
         if (P.red.range_error) return GIRG_E_RANGE;
@@ -950,7 +984,7 @@ int hrg_generate(const hrg_params* params, void* d_edges, int64_t capacity_edges
         P.w = w;
         P.X = X;
         Reduce* red = new_reduce(S, st);
-        launch_reduce(P.n, w, r, 1.0, exponent_of_ulp(1.0), 0, 0.0, red, st);
+        launch_reduce(P.n, w, r, 1.0, exponent_of_ulp(1.0), nullptr, red, st);
         tm.mark();
         read_reduce(P, red, st);  // the HRG needs no weight sum: a range error is harmless
         P.W = 1.0;
@@ -972,7 +1006,8 @@ int girg_allpairs(int64_t n, int32_t d, const uint32_t* d_X, const double* d_w, 
         Scratch S(st);
         float* sv = S.get<float>(n);
         const bool tzero = T == 0.0;
-        const float gamma = (float)(tzero ? 0.5 * std::log2(c) : (T / (2.0 * d)) * std::log2(c));
+        const double K = girg_K_of_c(c, d, T);
+        const float gamma = (float)(std::log2(K) / (2.0 * d));
         launch_scale(n, d_w, 0.5 * std::log2(W), gamma, (float)(1.0 / d), sv, st);
         unsigned long long* stats = S.get<unsigned long long>(kNumStats + 2);
         CK(cudaMemsetAsync(stats, 0, (kNumStats + 2) * sizeof(unsigned long long), st));
@@ -988,7 +1023,7 @@ int girg_allpairs(int64_t n, int32_t d, const uint32_t* d_X, const double* d_w, 
         cfg.seed_lo = (uint32_t)seed;
         cfg.seed_hi = (uint32_t)(seed >> 32);
         cfg.W = W;
-        cfg.c = c;
+        cfg.K = K;
         cfg.T = T;
         cfg.dT = T > 0.0 ? (float)(d / T) : 0.0f;
         cfg.bandG = cfg.dT * 0x1p-14f + 0x1p-15f;

@@ -250,37 +250,49 @@ GG_HD uint32_t circ_diff(uint32_t a, uint32_t b) {
     return t < u ? t : u;
 }
 
-// Eq. 1 at a real distance r > 0: min{1, c ((w_u w_v / W) / r^d)^(1/T)}.
-// m_int = 1/T when that is an integer in [1, 64] (repeated products), else 0.
-GG_HD double girg_p_at(double wu, double wv, double r, double W, double c, double invT, int m_int,
+// Eq. 1 with the model's scale K = c^T (K = c^d at T = 0), which stays a moderate
+// number for every T while c = K^(1/T) leaves the range of doubles as T -> 0:
+// x = K q / r^d with q = w_u w_v / W; p = 1 if x >= 1, else x^(1/T) (repeated
+// products when 1/T is an integer).
+GG_HD double girg_p_at(double wu, double wv, double r, double W, double K, double invT, int m_int,
                        int d) {
     const double q = DDIV(DMUL(wu, wv), W);
     double rd = r;
     for (int k = 1; k < d; ++k) rd = DMUL(rd, r);
-    const double base = DDIV(q, rd);
+    const double x = DDIV(DMUL(K, q), rd);
+    if (x >= 1.0) return 1.0;
     double p;
     if (m_int > 0) {
-        p = base;
-        for (int k = 1; k < m_int; ++k) p = DMUL(p, base);
+        p = x;
+        for (int k = 1; k < m_int; ++k) p = DMUL(p, x);
     } else {
-        p = det_exp(DMUL(invT, det_log(base)));
+        p = det_exp(DMUL(invT, det_log(x)));
     }
-    p = DMUL(c, p);
-    return p < 1.0 ? p : 1.0;
+    return p;
 }
 
 // Eq. 1 at the fixed-point distance D (r = D 2^-32; r = 0 gives p = 1).
-GG_HD double girg_p64(double wu, double wv, uint32_t D, double W, double c, double invT, int m_int,
+GG_HD double girg_p64(double wu, double wv, uint32_t D, double W, double K, double invT, int m_int,
                       int d) {
     if (D == 0) return 1.0;
-    return girg_p_at(wu, wv, (double)D * 0x1p-32, W, c, invT, m_int, d);
+    return girg_p_at(wu, wv, (double)D * 0x1p-32, W, K, invT, m_int, d);
 }
 
-// Threshold variant: edge iff r <= c (w_u w_v / W)^(1/d).
-GG_HD bool girg_thresh64(double wu, double wv, uint32_t D, double W, double c, int d) {
+// Threshold variant: edge iff r^d <= K w_u w_v / W (r <= c (w_u w_v / W)^(1/d)).
+GG_HD bool girg_thresh64(double wu, double wv, uint32_t D, double W, double K, int d) {
     const double q = DDIV(DMUL(wu, wv), W);
-    const double thr = DMUL(c, root_d(q, d));
-    return (double)D * 0x1p-32 <= thr;
+    const double r = (double)D * 0x1p-32;
+    double rd = r;
+    for (int k = 1; k < d; ++k) rd = DMUL(rd, r);
+    return rd <= DMUL(K, q);
+}
+
+// The scale K of the c of Eq. 1: c^T (T > 0) or c^d (T = 0).
+GG_HD double girg_K_of_c(double c, int d, double T) {
+    if (T > 0.0) return det_pow(c, T);
+    double k = c;
+    for (int i = 1; i < d; ++i) k = DMUL(k, c);
+    return k;
 }
 
 // cosh of the hyperbolic distance: cosh(r_u - r_v) + 2 sinh r_u sinh r_v sin^2(pi D 2^-32)

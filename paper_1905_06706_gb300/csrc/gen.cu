@@ -71,14 +71,14 @@ __device__ __forceinline__ void add128(unsigned long long& lo, unsigned long lon
 
 // Reductions over the weights (and radii for HRG) of all vertices.
 __global__ void k_reduce(int64_t n, const double* __restrict__ w, const double* __restrict__ r,
-                         double w_min, int E0, int want_sums, double invT, int m_int,
+                         double w_min, int E0, double* __restrict__ part_s2,
                          Reduce* __restrict__ out) {
     __shared__ unsigned int s_cnt[kMaxLayers];
     __shared__ unsigned long long s_wmax[kMaxLayers];
     __shared__ unsigned long long s_rmin[kMaxLayers];
     __shared__ unsigned long long s_rmax[kMaxLayers];
     __shared__ unsigned long long s_lo[32], s_hi[32];
-    __shared__ double s_sum[3][32];
+    __shared__ double s_sum[32];
     for (int t = threadIdx.x; t < kMaxLayers; t += blockDim.x) {
         s_cnt[t] = 0;
         s_wmax[t] = 0;
@@ -87,7 +87,7 @@ __global__ void k_reduce(int64_t n, const double* __restrict__ w, const double* 
     }
     __syncthreads();
     unsigned long long lo = 0, hi = 0;
-    double a2 = 0.0, at = 0.0, a2t = 0.0;
+    double a2 = 0.0;
     int range_err = 0;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
@@ -113,64 +113,38 @@ __global__ void k_reduce(int64_t n, const double* __restrict__ w, const double* 
             atomicMin(&s_rmin[layer], rb);
             atomicMax(&s_rmax[layer], rb);
         }
-        if (want_sums) {
-            a2 += wv * wv;
-            if (invT > 0.0) {
-                // w^(1/T) by repeated products when 1/T is a small integer
-                double t;
-                if (m_int > 0) {
-                    t = wv;
-                    for (int q = 1; q < m_int; ++q) t *= wv;
-                } else {
-                    t = exp2(invT * log2(wv));
-                }
-                at += t;
-                a2t += t * t;
-            }
-        }
+        if (part_s2) a2 += wv * wv;
     }
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long tlo = __shfl_down_sync(0xffffffffu, lo, o);
         const unsigned long long thi = __shfl_down_sync(0xffffffffu, hi, o);
         add128(lo, hi, tlo, thi);
         a2 += __shfl_down_sync(0xffffffffu, a2, o);
-        at += __shfl_down_sync(0xffffffffu, at, o);
-        a2t += __shfl_down_sync(0xffffffffu, a2t, o);
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (range_err) atomicOr(&out->range_error, 1u);
     if (lane == 0) {
         s_lo[warp] = lo;
         s_hi[warp] = hi;
-        s_sum[0][warp] = a2;
-        s_sum[1][warp] = at;
-        s_sum[2][warp] = a2t;
+        s_sum[warp] = a2;
     }
     __syncthreads();
     if (warp == 0) {
         const int nw = blockDim.x >> 5;
         lo = lane < nw ? s_lo[lane] : 0ull;
         hi = lane < nw ? s_hi[lane] : 0ull;
-        a2 = lane < nw ? s_sum[0][lane] : 0.0;
-        at = lane < nw ? s_sum[1][lane] : 0.0;
-        a2t = lane < nw ? s_sum[2][lane] : 0.0;
+        a2 = lane < nw ? s_sum[lane] : 0.0;
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long tlo = __shfl_down_sync(0xffffffffu, lo, o);
             const unsigned long long thi = __shfl_down_sync(0xffffffffu, hi, o);
             add128(lo, hi, tlo, thi);
             a2 += __shfl_down_sync(0xffffffffu, a2, o);
-            at += __shfl_down_sync(0xffffffffu, at, o);
-            a2t += __shfl_down_sync(0xffffffffu, a2t, o);
         }
         if (lane == 0) {
             const unsigned long long old = atomicAdd(&out->sum_lo, lo);
             const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
             atomicAdd(&out->sum_hi, hi + carry);
-            if (want_sums) {
-                atomicAdd(&out->s2, a2);
-                atomicAdd(&out->st, at);
-                atomicAdd(&out->s2t, a2t);
-            }
+            if (part_s2) part_s2[blockIdx.x] = a2;  // summed in block order later
         }
     }
     for (int t = threadIdx.x; t < kMaxLayers; t += blockDim.x) {
@@ -185,56 +159,100 @@ __global__ void k_reduce(int64_t n, const double* __restrict__ w, const double* 
     }
 }
 
-// Weights above a threshold, for the error term of App. B.2.
-__global__ void k_gather_above(int64_t n, const double* __restrict__ w, double thr,
-                               double* __restrict__ out, unsigned int cap,
-                               unsigned int* __restrict__ count) {
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const double wv = w[v];
-        if (wv > thr) {
-            const unsigned int s = atomicAdd(count, 1u);
-            if (s < cap) out[s] = wv;
-        }
+
+// Fixed-order sum of a per-block partial array by one block (deterministic).
+__device__ double block_ordered_sum(const double* __restrict__ part, int nb) {
+    __shared__ double s[256];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) a += part[i];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+        __syncthreads();
     }
+    const double r = s[0];
+    __syncthreads();
+    return r;
 }
 
-// Weight threshold for the heaviest weights the search for c will need (App. B.2):
-// 0.9 times the weight below which no vertex has a partner in E_R at the c0 where
-// the leading term of f(c) reaches the target.  The root lies at or a little above
-// c0, where that weight is smaller; the search starts at c0 and fetches more weights
-// only if it moves further.  One thread; an estimate, so CUDA's pow is good enough.
-__global__ void k_top_threshold(const Reduce* __restrict__ red, int64_t n, int d, double T,
-                                double target, int E0, double* __restrict__ thr) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// The split threshold of the degree model (App. B.2): the weight above which a
+// vertex can have partners in E_R at the scale K0 where the sum of
+// 2^d K w_u w_v / (W (1 - T)) over all pairs reaches the target, divided by a
+// margin.  The root K lies at or above K0 (the capping of E_R pairs and the
+// z^(1/T) terms only lower f), where that weight is smaller: K / K0 stays below
+// about 1.3 for T < 0.7 and 2.3 up to T = 0.9 (beta >= 2.1, degree <= 32), hence
+// margins 1.4 and 2.8; the search fetches a new split only if it moves further.
+// One block (256 threads): also finishes sum w^2 in block order.
+__global__ void k_top_threshold(Reduce* __restrict__ red, const double* __restrict__ part_s2,
+                                int nb, int64_t n, int d, double T, double target, int E0,
+                                double* __restrict__ thr) {
+    const double s2 = block_ordered_sum(part_s2, nb);
+    if (threadIdx.x != 0) return;
+    red->s2 = s2;
     const double W = ldexp((double)red->sum_hi * 0x1p64 + (double)red->sum_lo, E0);
     double wmax = 0.0;
     for (int i = 0; i < 64; ++i)
         if (red->cnt[i]) wmax = fmax(wmax, __longlong_as_double((long long)red->wmax[i]));
-    const double S1 = W - red->s2 / W, two_d = ldexp(1.0, d);
-    double qs;
-    if (T > 0.0) {
-        const double c0 = pow(target * (double)n * (1.0 - T) / (two_d * S1), 1.0 / T);
-        qs = 1.0 / (two_d * pow(c0, T));
-    } else {
-        const double c0 = pow(target * (double)n / (two_d * S1), 1.0 / d);
-        qs = 1.0 / (two_d * pow(c0, (double)d));
-    }
-    const double t = 0.9 * qs * W / wmax;
+    const double K0 = target * (double)n * W * (T > 0.0 ? 1.0 - T : 1.0) /
+                      (ldexp(W * W - s2, d));
+    const double margin = T >= 0.7 ? 2.8 : 1.4;
+    const double t = W / (margin * ldexp(K0, d) * wmax);
     *thr = (t > 0.0 && t < 1e300) ? t : 0.0;
 }
 
-__global__ void k_gather_above_dev(int64_t n, const double* __restrict__ w,
-                                   const double* __restrict__ thr, double* __restrict__ out,
-                                   unsigned int cap, unsigned int* __restrict__ count) {
+// One pass over the weights at the threshold: the weights above it are appended to
+// `out` (count[0]), and each block writes its sums over the weights at or below it:
+// sum w, sum w^2, sum (w/thr)^(1/T), sum (w/thr)^(2/T) (powers <= 1).
+__global__ void k_split_weights(int64_t n, const double* __restrict__ w,
+                                const double* __restrict__ thr, double invT, int m_int,
+                                double* __restrict__ out, unsigned int cap,
+                                unsigned int* __restrict__ count, double* __restrict__ part) {
+    __shared__ double s[4][8];
     const double t = *thr;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         const double wv = w[v];
         if (wv > t) {
-            const unsigned int s = atomicAdd(count, 1u);
-            if (s < cap) out[s] = wv;
+            const unsigned int slot = atomicAdd(count, 1u);
+            if (slot < cap) out[slot] = wv;
+        } else {
+            a[0] += wv;
+            a[1] += wv * wv;
+            if (invT > 0.0) {
+                const double x = wv / t;
+                double y;
+                if (m_int > 0) {
+                    y = x;
+                    for (int q = 1; q < m_int; ++q) y *= x;
+                } else {
+                    y = exp2(invT * log2(x));
+                }
+                a[2] += y;
+                a[3] += y * y;
+            }
         }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        for (int o = 16; o > 0; o >>= 1) a[q] += __shfl_down_sync(0xffffffffu, a[q], o);
+        if (lane == 0) s[q][warp] = a[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double acc = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) acc += s[threadIdx.x][i];
+        part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = acc;
+    }
+}
+
+// Finish the four split sums in block order.
+__global__ void k_split_finish(const double* __restrict__ part, int nb, double* __restrict__ sums) {
+    for (int q = 0; q < 4; ++q) {
+        const double v = block_ordered_sum(part + (size_t)q * nb, nb);
+        if (threadIdx.x == 0) sums[q] = v;
     }
 }
 
@@ -306,33 +324,37 @@ void launch_min_weight(int64_t n, const double* w, unsigned long long* out, cuda
     k_min_weight<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, w, out);
 }
 
+int reduce_blocks(int64_t n) { return grid_for(n, 256, 152 * 8); }
+
 void launch_reduce(int64_t n, const double* w, const double* r, double w_min, int E0,
-                   int want_sums, double invT, Reduce* out, cudaStream_t st) {
+                   double* part_s2, Reduce* out, cudaStream_t st) {
     ++g_launches;
-    int m_int = 0;
-    if (invT > 0.0 && invT == floor(invT) && invT <= 64.0) m_int = (int)invT;
-    k_reduce<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, w, r, w_min, E0, want_sums, invT,
-                                                        m_int, out);
+    k_reduce<<<reduce_blocks(n), 256, 0, st>>>(n, w, r, w_min, E0, part_s2, out);
 }
 
-void launch_gather_above(int64_t n, const double* w, double thr, double* out, unsigned int cap,
-                         unsigned int* count, cudaStream_t st) {
+
+void launch_split_threshold(Reduce* red, const double* part_s2, int64_t n, int d, double T,
+                            double target, int E0, double* thr, cudaStream_t st) {
     ++g_launches;
-    k_gather_above<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, w, thr, out, cap, count);
+    k_top_threshold<<<1, 256, 0, st>>>(red, part_s2, reduce_blocks(n), n, d, T, target, E0, thr);
 }
 
-void launch_top_weights(int64_t n, const double* w, const Reduce* red, int d, double T,
-                        double target, int E0, double* thr, double* out, unsigned int cap,
-                        unsigned int* count, cudaStream_t st) {
+void launch_split_weights(int64_t n, const double* w, const double* thr, double T, double* out,
+                          unsigned int cap, unsigned int* count, double* part, double* sums,
+                          cudaStream_t st) {
     static const bool attr = [] {
         return cudaFuncSetAttribute(k_sort_top, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)(kTopSortMax * sizeof(unsigned long long))) ==
                cudaSuccess;
     }();
     (void)attr;
+    const double invT = T > 0.0 ? 1.0 / T : 0.0;
+    int m_int = 0;
+    if (invT > 0.0 && invT == floor(invT) && invT <= 64.0) m_int = (int)invT;
+    const int nb = reduce_blocks(n);
     g_launches += 3;
-    k_top_threshold<<<1, 32, 0, st>>>(red, n, d, T, target, E0, thr);
-    k_gather_above_dev<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, w, thr, out, cap, count);
+    k_split_weights<<<nb, 256, 0, st>>>(n, w, thr, invT, m_int, out, cap, count, part);
+    k_split_finish<<<1, 256, 0, st>>>(part, nb, sums);
     k_sort_top<<<1, 1024, kTopSortMax * sizeof(unsigned long long), st>>>(out, count);
 }
 

@@ -68,7 +68,7 @@ struct DevCfg {
     int32_t n3, n6;  // 3^d and 6^d
     uint32_t seed_lo, seed_hi;
     uint32_t mode;
-    double W, c, T, invT, w_min, R, coshR;
+    double W, K, T, invT, w_min, R, coshR;  // K: scale of Eq. 1 (c^T, or c^d at T = 0)
     float dT;          // d / T (GIRG)
     float bandG;       // band in the log2 domain of decisions
     float band_ratio;  // relative band of kappa / r

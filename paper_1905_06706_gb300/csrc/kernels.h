@@ -18,7 +18,7 @@ struct Reduce {
     unsigned long long wmax[64];        // largest weight per bucket (bits)
     unsigned long long rmin[64];        // HRG: smallest radius per bucket (bits)
     unsigned long long rmax[64];        // HRG: largest radius per bucket (bits)
-    double s2, st, s2t;                 // sum w^2, sum w^(1/T), sum w^(2/T)
+    double s2;                          // sum w^2 (filled by the split threshold)
     unsigned int range_error;
     unsigned int pad;
 };
@@ -28,17 +28,22 @@ void launch_girg_points(int64_t n, int d, double beta, double w_min, uint64_t se
 void launch_hrg_points(int64_t n, double alpha, double R, uint64_t seed, double* r, double* w,
                        uint32_t* X, cudaStream_t st);
 void launch_min_weight(int64_t n, const double* w, unsigned long long* out, cudaStream_t st);
+// Blocks of the reduction (one per-block partial each).
+int reduce_blocks(int64_t n);
+// part_s2 (reduce_blocks(n) doubles, or null): per-block sums of w^2.
 void launch_reduce(int64_t n, const double* w, const double* r, double w_min, int E0,
-                   int want_sums, double invT, Reduce* out, cudaStream_t st);
-void launch_gather_above(int64_t n, const double* w, double thr, double* out, unsigned int cap,
-                         unsigned int* count, cudaStream_t st);
-// The heaviest weights for the search for c, without a host round trip: a threshold
-// estimated on the device from the reduction, the weights above it (count[0]) and,
-// when count[0] <= kTopSortMax, sorted in decreasing order (count[1] = 1).
+                   double* part_s2, Reduce* out, cudaStream_t st);
+// The split of the weights for the degree model (App. B.2): a threshold estimated on
+// the device from the reduction (also finishing red->s2 in block order), then one pass
+// that gathers the weights above *thr (count[0]; sorted in decreasing order when
+// count[0] <= kTopSortMax, count[1] = 1) and sums over the rest: sums[0..3] = sum w,
+// sum w^2, sum (w/thr)^(1/T), sum (w/thr)^(2/T).  part: 4 reduce_blocks(n) doubles.
 constexpr unsigned int kTopSortMax = 16384;
-void launch_top_weights(int64_t n, const double* w, const Reduce* red, int d, double T,
-                        double target, int E0, double* thr, double* out, unsigned int cap,
-                        unsigned int* count, cudaStream_t st);
+void launch_split_threshold(Reduce* red, const double* part_s2, int64_t n, int d, double T,
+                            double target, int E0, double* thr, cudaStream_t st);
+void launch_split_weights(int64_t n, const double* w, const double* thr, double T, double* out,
+                          unsigned int cap, unsigned int* count, double* part, double* sums,
+                          cudaStream_t st);
 
 // Sorting: keys (global cell index at the insertion level) with a histogram.
 void launch_keys(int64_t n, int d, const double* w, const uint32_t* X, double w_min,

@@ -75,7 +75,8 @@ extern "C" int girg_allpairs_noalloc(int64_t n, int32_t d, const uint32_t* d_X, 
     if (cudaMemsetAsync(counters, 0, kCounterWords * sizeof(unsigned long long), st) != cudaSuccess)
         return GIRG_E_CUDA;
     const bool tzero = T == 0.0;
-    const float gamma = (float)(tzero ? 0.5 * std::log2(c) : (T / (2.0 * d)) * std::log2(c));
+    const double K = girg_K_of_c(c, d, T);
+    const float gamma = (float)(std::log2(K) / (2.0 * d));
     launch_scale(n, d_w, 0.5 * std::log2(W), gamma, (float)(1.0 / d), sv, st);
     DevCfg cfg;
     memset(&cfg, 0, sizeof(cfg));
@@ -89,7 +90,7 @@ extern "C" int girg_allpairs_noalloc(int64_t n, int32_t d, const uint32_t* d_X, 
     cfg.seed_lo = (uint32_t)seed;
     cfg.seed_hi = (uint32_t)(seed >> 32);
     cfg.W = W;
-    cfg.c = c;
+    cfg.K = K;
     cfg.T = T;
     cfg.dT = T > 0.0 ? (float)(d / T) : 0.0f;
     cfg.bandG = cfg.dT * 0x1p-14f + 0x1p-15f;

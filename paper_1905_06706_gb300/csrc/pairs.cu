@@ -64,7 +64,7 @@ __device__ __forceinline__ float kappa_ratio(const View& V, uint32_t pu, uint32_
 
 __device__ __forceinline__ double girg_p_pair(const DevCfg& cfg, const View& V, uint32_t pu,
                                               uint32_t pv, uint32_t D) {
-    return girg_p64(V.w[pu], V.w[pv], D, cfg.W, cfg.c, cfg.invT, cfg.m_int, cfg.d);
+    return girg_p64(V.w[pu], V.w[pv], D, cfg.W, cfg.K, cfg.invT, cfg.m_int, cfg.d);
 }
 
 // HRG cosh d in FP64 from the radii of both vertices.
@@ -77,7 +77,7 @@ __device__ __noinline__ double hrg_coshd_pair(const View& V, uint32_t pu, uint32
 
 __device__ __noinline__ bool girg_t1_exact(const DevCfg& cfg, const View& V, uint32_t pu,
                                            uint32_t pv, uint32_t D, uint32_t lo, uint32_t hi) {
-    if (cfg.tzero) return girg_thresh64(V.w[pu], V.w[pv], D, cfg.W, cfg.c, cfg.d);
+    if (cfg.tzero) return girg_thresh64(V.w[pu], V.w[pv], D, cfg.W, cfg.K, cfg.d);
     return uniform53(lo, hi) < girg_p_pair(cfg, V, pu, pv, D);
 }
 

@@ -1,14 +1,4 @@
-// Expected average degree of a GIRG and the search for c (Sec. 4.1, App. B.2).
-//
-// f(c) = E[average degree] = (1/n) sum over ordered pairs u != v of E[X_uv].
-// Without the min of Eq. 1, E[X_uv] has the closed form
-//   T > 0:  c^T 2^d/(1-T) q - c 2^(d/T)/(1/T - 1) q^(1/T),   q = w_u w_v / W
-//   T = 0:  2^d c^d q
-// whose double sums reduce to sums of w, w^2, w^(1/T), w^(2/T).  Pairs where the
-// min takes effect (the set E_R: c^T q > 2^-d, resp. 2^d c^d q > 1) have
-// E[X_uv] = 1; their error is subtracted by walking the heaviest vertices in
-// decreasing weight, where each vertex's partners form a prefix (App. B.2).
-// The search brackets c by doubling / halving and bisects on log c.
+// Expected average degree of a GIRG and the search for its scale (Sec. 4.1, App. B.2).
 #include "solver.h"
 
 #include <algorithm>
@@ -17,138 +7,154 @@
 
 namespace gg {
 
-DegreeModel::DegreeModel(int64_t n, int d, double T, double W, double s2, double st, double s2t)
-    : n_(n), d_(d), T_(T), W_(W) {
-    S1_ = W - s2 / W;
-    S2_ = T > 0.0 ? (st * st - s2t) / std::pow(W, 1.0 / T) : 0.0;
-    wmax_ = 0.0;
-    have_thr_ = INFINITY;
-}
-
-void DegreeModel::set_top(std::vector<double> top, double fetched_above, bool descending) {
-    if (!descending) std::sort(top.begin(), top.end(), [](double a, double b) { return a > b; });
+void DegreeModel::set_split(double thr, std::vector<double> top, double sw, double s2, double sx,
+                            double sx2) {
+    thr_ = thr;
+    sw_ = sw;
+    s2_ = s2;
+    sx_ = sx;
+    sx2_ = sx2;
     top_ = std::move(top);
-    have_thr_ = fetched_above;
-    if (!top_.empty()) wmax_ = std::max(wmax_, top_[0]);
-    pre_w_.assign(top_.size() + 1, 0.0);
-    pre_wt_.assign(top_.size() + 1, 0.0);
-    wt_.assign(top_.size(), 0.0);
-    for (size_t a = 0; a < top_.size(); ++a) {
-        wt_[a] = T_ > 0.0 ? power(top_[a]) : 0.0;
-        pre_w_[a + 1] = pre_w_[a] + top_[a];
-        pre_wt_[a + 1] = pre_wt_[a] + wt_[a];
-    }
-    WT_ = T_ > 0.0 ? power(W_) : 1.0;
-}
-
-// x^(1/T): repeated products when 1/T is a small integer.
-double DegreeModel::power(double x) const {
-    const double e = 1.0 / T_;
-    if (e == std::floor(e) && e <= 16.0) {
-        double r = x;
-        for (int q = 1; q < (int)e; ++q) r *= x;
-        return r;
-    }
-    return std::pow(x, e);
-}
-
-double DegreeModel::qstar(double c) const {
-    if (T_ == 0.0) return 1.0 / std::ldexp(std::pow(c, d_), d_);
-    return std::ldexp(1.0, -d_) / std::pow(c, T_);
-}
-
-double DegreeModel::needed_threshold(double c) const {
-    // both endpoints of a pair in E_R weigh more than qstar W / w_max
-    return qstar(c) * W_ / wmax_;
-}
-
-double DegreeModel::f(double c) const {
-    const int d = d_;
-    const double T = T_;
-    double main_term;
-    double a1 = 0.0, a2 = 0.0;
-    if (T == 0.0) {
-        a1 = std::ldexp(std::pow(c, d), d);
-        main_term = a1 * S1_;
-    } else {
-        a1 = std::pow(c, T) * std::ldexp(1.0, d) / (1.0 - T);
-        a2 = c * std::pow(2.0, d / T) / (1.0 / T - 1.0);
-        main_term = a1 * S1_ - a2 * S2_;
-    }
-    const double qs = qstar(c);
-    double err = 0.0;
-    // partners of the heaviest vertex: the prefix of weights above qs W / w_max
-    // (binary search); for lighter vertices the prefix only shrinks
-    size_t k = 0;
-    if (!top_.empty()) {
-        const double lim0 = qs * W_ / top_[0];
-        k = (size_t)(std::upper_bound(top_.begin(), top_.end(), lim0,
-                                      [](double x, double y) { return x > y; }) -
-                     top_.begin());
-    }
-    for (size_t a = 0; a < top_.size(); ++a) {
-        const double wu = top_[a];
-        const double lim = qs * W_ / wu;
-        while (k > 0 && !(top_[k - 1] > lim)) --k;
-        if (k == 0) break;
-        double cnt = (double)k, sw = pre_w_[k], swt = pre_wt_[k];
-        if (a < k) {
-            cnt -= 1.0;
-            sw -= wu;
-            if (T > 0.0) swt -= wt_[a];
+    const size_t m = top_.size();
+    const bool tp = T_ > 0.0;
+    lw_.assign(m, 0.0);
+    b_.assign(m + 1, 0.0);
+    suf_.assign(m + 1, 0.0);
+    suf2_.assign(m + 1, 0.0);
+    sr_.assign(m + 1, 0.0);
+    sr2_.assign(m + 1, 0.0);
+    const double inv = tp ? 1.0 / T_ : 0.0;
+    mi_ = (tp && inv == std::floor(inv) && inv <= 8.0) ? (int)inv : 0;
+    py_.assign(mi_ ? m : 0, 0.0);
+    spy_.assign(mi_ ? m + 1 : 0, 0.0);
+    spy2_.assign(mi_ ? m + 1 : 0, 0.0);
+    for (size_t i = m; i-- > 0;) {  // from the light end
+        lw_[i] = std::log(top_[i]);
+        suf_[i] = suf_[i + 1] + top_[i];
+        suf2_[i] = suf2_[i + 1] + top_[i] * top_[i];
+        if (mi_) {
+            const double y = top_[i] / thr;
+            double p = y;
+            for (int q = 1; q < mi_; ++q) p *= y;
+            py_[i] = p;
+            spy_[i] = spy_[i + 1] + p;
+            spy2_[i] = spy2_[i + 1] + p * p;
+            continue;
         }
-        if (cnt <= 0.0) continue;
-        double s;
-        if (T == 0.0)
-            s = a1 * (wu / W_) * sw;
-        else
-            s = a1 * (wu / W_) * sw - a2 * (wt_[a] / WT_) * swt;
-        err += s - cnt;
+        if (tp) {
+            b_[i] = lw_[i] / T_;
+            const double r = i + 1 < m ? std::exp(b_[i + 1] - b_[i]) : 0.0;  // <= 1
+            sr_[i] = 1.0 + r * sr_[i + 1];
+            sr2_[i] = 1.0 + r * r * sr2_[i + 1];
+        }
     }
-    return (main_term - err) / (double)n_;
+}
+
+double DegreeModel::needed_threshold(double K) const {
+    const double wmax = top_.empty() ? thr_ : top_[0];
+    return W_ / (std::ldexp(K, d_) * wmax);
+}
+
+bool DegreeModel::valid(double K) const { return thr_ < needed_threshold(K); }
+
+// Sum over ordered pairs u != v of E[X_uv]: rest x rest, rest x top (both orders), and
+// top x top.  In the last, the top vertices u with E_R partners (a prefix of the
+// decreasing order, usually a few) and the heaviest one are taken one by one; every
+// other u has all other top weights as non-E_R partners, and their sums over such u
+// come from the suffix aggregates: sum_u w_u (S - w_u) and sum_u e_u (E - e_u) with
+// e = w^(1/T), E = sum e (the self terms are at most half of the products there, as
+// every such u has the heaviest vertex as a heavier partner).
+double DegreeModel::f(double K) const {
+    const double T = T_, A = std::ldexp(K, d_) / W_, lA = std::log(A);
+    const double lt = std::log(thr_);
+    const bool tp = T > 0.0;
+    const double inv1mT = tp ? 1.0 / (1.0 - T) : 1.0, lAT = tp ? lA / T : 0.0;
+    // rest x rest
+    double rr = A * (sw_ * sw_ - s2_);
+    if (tp) rr = (rr - T * std::exp(lAT + 2.0 * lt / T) * (sx_ * sx_ - sx2_)) * inv1mT;
+    const size_t m = top_.size();
+    double C = 0.0;  // (A thr^2)^mi on the integer path
+    if (mi_) {
+        const double a = A * thr_ * thr_;
+        C = a;
+        for (int q = 1; q < mi_; ++q) C *= a;
+    }
+    // top x rest: sum_u [A w_u sw - T (A w_u thr)^(1/T) sx] / (1 - T)
+    double tr = A * suf_[0] * sw_;
+    if (tp && m)
+        tr = (tr - T * (mi_ ? C * spy_[0] : std::exp(lAT + lt / T + b_[0]) * sr_[0]) * sx_) *
+             inv1mT;
+    // top x top
+    double tt = 0.0;
+    size_t k = m, u = 0;
+    for (; u < m; ++u) {
+        const double wu = top_[u];
+        while (k > 0 && A * wu * top_[k - 1] < 1.0) --k;
+        if (k == 0 && u > 0) break;  // from here on no u has E_R partners
+        const size_t k1 = u == k ? k + 1 : k;  // first non-E_R partner
+        double e = A * wu * (u > k ? suf_[k] - wu : suf_[k1]);
+        if (mi_) {
+            double zt = C * py_[u] * spy_[k1];
+            if (u > k) zt -= C * py_[u] * py_[u];  // at most half of the sum
+            e = (e - T * zt) * inv1mT;
+        } else if (tp) {
+            const double xu = lAT + b_[u];  // log (A w_u)^(1/T)
+            double zt = k1 < m ? std::exp(xu + b_[k1]) * sr_[k1] : 0.0;
+            if (u > k) zt -= std::exp(xu + b_[u]);  // at most half of the sum
+            e = (e - T * zt) * inv1mT;
+        }
+        tt += (double)k - (u < k ? 1.0 : 0.0) + e;
+    }
+    if (u < m) {  // u .. m-1: no E_R partners, all other top weights are partners
+        double e = A * (suf_[u] * suf_[0] - suf2_[u]);
+        if (mi_) {
+            e = (e - T * C * (spy_[u] * spy_[0] - spy2_[u])) * inv1mT;
+        } else if (tp) {
+            const double zt = std::exp(lAT + b_[u] + b_[0]) *
+                              (sr_[u] * sr_[0] - std::exp(b_[u] - b_[0]) * sr2_[u]);
+            e = (e - T * zt) * inv1mT;
+        }
+        tt += e;
+    }
+    return (rr + 2.0 * tr + tt) / (double)n_;
 }
 
 double DegreeModel::solve(double target, const std::function<void(double)>& fetch) {
-    auto eval = [&](double c) {
-        const double need = needed_threshold(c);
-        if (need < have_thr_) fetch(0.5 * need);
-        return f(c);
+    auto eval = [&](double K) {
+        if (!valid(K)) fetch(0.5 * needed_threshold(K));
+        return f(K);
     };
-    // start from the c at which the leading term of f alone reaches the target
-    // (c^T 2^d S1 / ((1 - T) n) = target, or 2^d c^d S1 / n = target at T = 0);
-    // the other terms only lower f, so the root lies near or above it
-    double c0;
-    if (T_ == 0.0)
-        c0 = std::pow(target * (double)n_ / (std::ldexp(1.0, d_) * S1_), 1.0 / d_);
-    else
-        c0 = std::pow(target * (double)n_ * (1.0 - T_) / (std::ldexp(1.0, d_) * S1_), 1.0 / T_);
-    if (!(c0 > 1e-300 && c0 < 1e300)) c0 = 1.0;
-    // bracket with steps growing from 5% (the root is usually within a few percent
-    // of c0, and small steps keep the needed weights within those already fetched)
-    double lo = c0, hi = c0;
-    if (eval(c0) < target) {
-        for (double f = 1.05; eval(hi) < target && hi < 1e300; f = f * f) {
+    // start where the sum without E_R capping reaches the target; the capping and the
+    // z^(1/T) terms only lower f, so the root lies at or above this K0
+    double s2 = s2_;
+    for (double w : top_) s2 += w * w;
+    const double lead = std::ldexp(1.0, d_) * (W_ * W_ - s2) / (W_ * (T_ > 0.0 ? 1.0 - T_ : 1.0));
+    double K0 = target * (double)n_ / lead;
+    if (!(K0 > 1e-300 && K0 < 1e300)) K0 = 1.0;
+    // bracket with steps growing from 5% (the root is usually close to K0, and small
+    // steps keep the needed top weights within those already held)
+    double lo = K0, hi = K0;
+    if (eval(K0) < target) {
+        for (double g = 1.05; eval(hi) < target && hi < 1e300; g = g * g) {
             lo = hi;
-            hi *= f;
+            hi *= g;
         }
     } else {
-        for (double f = 1.05; eval(lo) >= target && lo > 1e-300; f = f * f) {
+        for (double g = 1.05; eval(lo) >= target && lo > 1e-300; g = g * g) {
             hi = lo;
-            lo /= f;
+            lo /= g;
         }
     }
-    // Illinois variant of regula falsi on log c: the bracket [lo, hi] with
-    // f(lo) < target <= f(hi) shrinks superlinearly; bisection steps guard it
+    // Illinois regula falsi on log K; bisection steps guard it
     double flo = eval(lo) - target, fhi = eval(hi) - target;
     int side = 0;
     for (int it = 0; it < 200 && hi - lo > 1e-13 * hi; ++it) {
         double mid;
         const double a = std::log(lo), b = std::log(hi);
-        if (it % 8 == 7 || !(fhi > flo)) {
+        if (it % 8 == 7 || !(fhi > flo))
             mid = std::sqrt(lo * hi);
-        } else {
+        else
             mid = std::exp(b - fhi * (b - a) / (fhi - flo));
-        }
         if (!(mid > lo && mid < hi)) mid = std::sqrt(lo * hi);
         if (!(mid > lo && mid < hi)) mid = 0.5 * (lo + hi);
         const double fm = eval(mid) - target;

@@ -190,6 +190,26 @@ def test_generate_internal_points_and_c():
     assert f == pytest.approx(10.0, rel=1e-9)
 
 
+@pytest.mark.parametrize("d,T,beta,deg", [(2, 0.05, 2.5, 10.0), (3, 0.02, 2.2, 16.0),
+                                         (1, 0.12, 2.9, 6.0), (2, 0.85, 2.1, 20.0)])
+def test_small_and_large_temperature_scale(d, T, beta, deg):
+    """Solve mode at temperatures where Eq. 1's c leaves the range of doubles: the scale
+    K = c^T equals the oracle's, the graph equals the oracle's at that K, and the
+    average degree is close to the target."""
+    n = 60_000
+    w, X = O.girg_points(n, d, beta, 1.0, 17)
+    W = O.exact_sum(w)
+    K_ref = O.girg_solve_K(deg, w, d, T, W)
+    ed = _edges(n * 48)
+    r = gg.girg_generate(ed, n=n, d=d, beta=beta, T=T, avg_deg=deg, seed=17)
+    assert r.status == gg.GIRG_OK
+    K = gg.last_K()
+    assert K == pytest.approx(K_ref, rel=1e-9)
+    ref = O.girg_cellpairs(X, w, 1.0, W, T, None, 17, cap=n * 64, K=K)
+    assert _set(ed, r.num_edges) == O.edge_set(ref.edges)
+    assert abs(2.0 * r.num_edges / n - deg) < 0.15 * deg
+
+
 def test_int64_edges_and_capacity():
     n, d, T = 20_000, 2, 0.5
     w, X = O.girg_points(n, d, 2.5, 1.0, 31)
