@@ -97,6 +97,7 @@ def _load():
             "orc_girg_avg_degree": (dbl, [dbl, i64, i32, dbl, P, dbl]),
             "orc_girg_solve_K": (dbl, [dbl, i64, i32, dbl, P, dbl]),
             "orc_girg_K_of_c": (dbl, [dbl, i32, dbl]),
+            "orc_girg_thresh_neighbors": (i64, [i64, i32, P, P, dbl, dbl, P, i64, P, i64]),
             "orc_hrg_avg_degree": (dbl, [i64, dbl, dbl, dbl]),
             "orc_hrg_solve_R": (dbl, [i64, dbl, dbl, dbl]),
         }
@@ -401,6 +402,23 @@ def hrg_avg_degree(n, alpha, T, R):
 def hrg_solve_R(n, alpha, T, target):
     """The disk radius R with expected average degree ``target`` (bisection)."""
     return _load().orc_hrg_solve_R(n, alpha, T, target)
+
+
+def girg_thresh_neighbors(X, w, W, K, us, cap=None):
+    """Threshold model by brute force: every (u, v), u in ``us``, v != u, with
+    r^d <= K w_u w_v / W, as an (m, 2) int64 array."""
+    X = np.ascontiguousarray(X, dtype=np.uint32)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    us = np.ascontiguousarray(us, dtype=np.int64)
+    n, d = X.shape
+    cap = cap or 1 << 16
+    while True:
+        out = np.zeros((cap, 2), dtype=np.int64)
+        m = _load().orc_girg_thresh_neighbors(n, d, _ptr(X), _ptr(w), W, K, _ptr(us), len(us),
+                                              _ptr(out), cap)
+        if m <= cap:
+            return out[:m]
+        cap = m
 
 
 def splitmix64_finalize(z):

@@ -1563,3 +1563,30 @@ double orc_hrg_solve_R(int64_t n, double alpha, double T, double target) {
     }
     return 0.5 * (lo + hi);
 }
+
+/* Threshold model (T = 0), brute force: for each vertex u of us[0..nu), every v != u
+ * with r^d <= K w_u w_v / W, written as (u, v) pairs (u < v not required); returns
+ * the number of pairs (at most cap are written).  For checking sampled vertices of
+ * graphs too large for the samplers above. */
+int64_t orc_girg_thresh_neighbors(int64_t n, int d, const uint32_t* X, const double* w, double W,
+                                  double K, const int64_t* us, int64_t nu, int64_t* out,
+                                  int64_t cap) {
+    girg_model M;
+    girg_model_init(&M, d, 0.0, K, W);
+    int64_t m = 0;
+    for (int64_t a = 0; a < nu; a++) {
+        int64_t u = us[a];
+        for (int64_t v = 0; v < n; v++) {
+            if (v == u) continue;
+            uint32_t D = torus_dist(X + u * d, X + v * d, d);
+            if (girg_thresh_edge(&M, w[u], w[v], D)) {
+                if (m < cap) {
+                    out[2 * m] = u;
+                    out[2 * m + 1] = v;
+                }
+                m++;
+            }
+        }
+    }
+    return m;
+}

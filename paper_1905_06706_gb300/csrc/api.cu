@@ -391,14 +391,19 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     unsigned int* counters = S.get<unsigned int>(16);
     // stats, then the edge count and the two work counters of the type-I / type-II kernels
     unsigned long long* stats = S.get<unsigned long long>(kNumStats + 3);
+    // one round's work-list counts (type-I items, streams, segments) and statistics
+    unsigned long long* wcount = S.get<unsigned long long>(3);
+    unsigned long long* estats = S.get<unsigned long long>(kNumStats);
     CK(cudaMemsetAsync(counters, 0, 16 * sizeof(unsigned int), st));
     CK(cudaMemsetAsync(stats, 0, (kNumStats + 3) * sizeof(unsigned long long), st));
     // work lists, sized from typical counts per vertex; the enumeration only writes
     // work (no edges), so an overflow is repaired by resizing and running it again
-    auto clamp_cap = [](uint64_t c) { return c > 0xfffffff0ull ? 0xfffffff0ull : c; };
-    uint64_t t1_cap = clamp_cap((uint64_t)n * (1 + (uint64_t)(0.75 * n3)) + 65536);
-    uint64_t stream_cap = tzero ? 1024 : clamp_cap((uint64_t)n * (2 + 2 * (uint64_t)d) + 65536);
-    uint64_t seg_cap = tzero ? 1024 : clamp_cap((uint64_t)n * (4 + (uint64_t)(1.5 * n3)) + 65536);
+    auto clamp_cap = [](uint64_t c, uint64_t mx) { return c > mx ? mx : c; };
+    uint64_t t1_cap = clamp_cap((uint64_t)n * (1 + (uint64_t)(0.75 * n3)) + 65536, 1ull << 30);
+    uint64_t stream_cap =
+        tzero ? 1024 : clamp_cap((uint64_t)n * (2 + 2 * (uint64_t)d) + 65536, 1ull << 28);
+    uint64_t seg_cap =
+        tzero ? 1024 : clamp_cap((uint64_t)n * (4 + (uint64_t)(1.5 * n3)) + 65536, 1ull << 31);
     T1Item* t1 = S.get<T1Item>(t1_cap);
     uint32_t* t1_pairs = S.get<uint32_t>(t1_cap + 1);
     Stream* streams = S.get<Stream>(stream_cap);
@@ -470,67 +475,118 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     cfg.ent1_count = counters + 7;
     cfg.ent1_cap = (uint32_t)ent1_cap;
     cfg.t1 = t1;
-    cfg.t1_count = counters + 1;
+    cfg.t1_count = wcount + 0;
     cfg.t1_cap = (uint32_t)t1_cap;
     cfg.t1_pairs = t1_pairs;
     cfg.streams = streams;
-    cfg.stream_count = counters + 2;
+    cfg.stream_count = wcount + 1;
     cfg.stream_cap = (uint32_t)stream_cap;
     cfg.stream_chunks = stream_chunks;
     cfg.segs = segs;
-    cfg.seg_count = counters + 3;
+    cfg.seg_count = wcount + 2;
     cfg.seg_cap = (uint32_t)seg_cap;
     cfg.error = counters + 5;
     cfg.work64 = stats + kNumStats + 1;
 
     launch_rows(cfg, st);
-    launch_enumerate(cfg, st);
-    unsigned int hc[4];  // rows, type-I items, streams, segments
+    // Enumeration and sampling in rounds over ranges of the work entries: a round's
+    // lists must fit their capacities (grown up to a maximum); a round whose lists
+    // would exceed the maximum is retried over fewer entries.  The enumeration writes
+    // no edges, so a retried round leaves no trace (its statistics are kept apart
+    // until it is accepted).
+    constexpr uint64_t kMaxT1 = 1ull << 30, kMaxStreams = 1ull << 28, kMaxSegs = 1ull << 31;
+    uint32_t lo2 = 0, lo1 = 0, hi2 = 0xffffffffu, hi1 = 0xffffffffu;
+    unsigned long long est_acc[kNumStats] = {0};
+    uint64_t total_streams = 0;
+    unsigned long long *t1_pre = nullptr, *chunk_pre = nullptr, *tmp = nullptr;
+    size_t pre_cap1 = 0, pre_cap2 = 0, tmp_cap = 0;
+    int round = 0;
     for (int attempt = 0;; ++attempt) {
-        CK(cudaMemcpyAsync(hc, counters, 4 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+        if (attempt > 64) throw Status{GIRG_E_INTERNAL};
+        cfg.ent2_lo = lo2;
+        cfg.ent2_hi = hi2;
+        cfg.ent1_lo = lo1;
+        cfg.ent1_hi = hi1;
+        CK(cudaMemsetAsync(wcount, 0, 3 * sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(estats, 0, kNumStats * sizeof(unsigned long long), st));
+        DevCfg ecfg = cfg;
+        ecfg.stats = estats;
+        launch_enumerate(ecfg, st);
+        unsigned long long wc[3], es[kNumStats];
+        unsigned int ec[2];
+        CK(cudaMemcpyAsync(wc, wcount, sizeof(wc), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ec, counters + 6, sizeof(ec), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(es, estats, sizeof(es), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        const bool over = hc[1] > cfg.t1_cap || hc[2] > cfg.stream_cap || hc[3] > cfg.seg_cap;
-        if (!over) break;
-        if (attempt > 0) throw Status{GIRG_E_INTERNAL};
-        if (hc[1] > cfg.t1_cap) {
-            cfg.t1_cap = hc[1] + 1024;
-            cfg.t1 = S.get<T1Item>(cfg.t1_cap);
-            cfg.t1_pairs = S.get<uint32_t>(cfg.t1_cap + 1);
+        const uint32_t e2 = std::min<uint32_t>(ec[0], cfg.ent2_cap);
+        const uint32_t e1 = std::min<uint32_t>(ec[1], cfg.ent1_cap);
+        const uint32_t end2 = std::min(hi2, e2), end1 = std::min(hi1, e1);
+        if (wc[0] > cfg.t1_cap || wc[1] > cfg.stream_cap || wc[2] > cfg.seg_cap) {
+            double f = 1.0;
+            if (wc[0] > kMaxT1) f = std::min(f, 0.8 * (double)kMaxT1 / (double)wc[0]);
+            if (wc[1] > kMaxStreams) f = std::min(f, 0.8 * (double)kMaxStreams / (double)wc[1]);
+            if (wc[2] > kMaxSegs) f = std::min(f, 0.8 * (double)kMaxSegs / (double)wc[2]);
+            if (f < 1.0) {  // fewer entries this round
+                hi2 = lo2 + std::max<uint32_t>(1, (uint32_t)((end2 - lo2) * f));
+                hi1 = lo1 + std::max<uint32_t>(1, (uint32_t)((end1 - lo1) * f));
+                continue;
+            }
+            if (wc[0] > cfg.t1_cap) {
+                cfg.t1_cap = (uint32_t)std::min<uint64_t>(kMaxT1, wc[0] + wc[0] / 16 + 1024);
+                cfg.t1 = S.get<T1Item>(cfg.t1_cap);
+                cfg.t1_pairs = S.get<uint32_t>((size_t)cfg.t1_cap + 1);
+            }
+            if (wc[1] > cfg.stream_cap) {
+                cfg.stream_cap = (uint32_t)std::min<uint64_t>(kMaxStreams, wc[1] + wc[1] / 16 + 1024);
+                cfg.streams = S.get<Stream>(cfg.stream_cap);
+                cfg.stream_chunks = S.get<uint32_t>((size_t)cfg.stream_cap + 1);
+            }
+            if (wc[2] > cfg.seg_cap) {
+                cfg.seg_cap = (uint32_t)std::min<uint64_t>(kMaxSegs, wc[2] + wc[2] / 16 + 1024);
+                cfg.segs = S.get<Seg>(cfg.seg_cap);
+            }
+            continue;
         }
-        if (hc[2] > cfg.stream_cap) {
-            cfg.stream_cap = hc[2] + 1024;
-            cfg.streams = S.get<Stream>(cfg.stream_cap);
-            cfg.stream_chunks = S.get<uint32_t>(cfg.stream_cap + 1);
+        for (int q = 0; q < kNumStats; ++q) est_acc[q] += es[q];
+        if (round == 0) tm.mark();  // (first round) enumeration done
+        // exclusive prefixes of the pairs per type-I item and of the chunks per stream
+        // (one past the last entry holds the total)
+        const uint32_t n1 = (uint32_t)wc[0], ns = (uint32_t)wc[1];
+        total_streams += ns;
+        if (n1 + 1ull > pre_cap1) {  // prefix buffers, reused by later rounds
+            pre_cap1 = n1 + 1ull + (n1 >> 3);
+            t1_pre = S.get<unsigned long long>(pre_cap1);
         }
-        if (hc[3] > cfg.seg_cap) {
-            cfg.seg_cap = hc[3] + 1024;
-            cfg.segs = S.get<Seg>(cfg.seg_cap);
+        if (ns + 1ull > pre_cap2) {
+            pre_cap2 = ns + 1ull + (ns >> 3);
+            chunk_pre = S.get<unsigned long long>(pre_cap2);
         }
-        CK(cudaMemsetAsync(counters + 1, 0, 3 * sizeof(unsigned int), st));  // t1, streams, segs
-        CK(cudaMemsetAsync(stats, 0, kNumStats * sizeof(unsigned long long), st));
-        launch_enumerate(cfg, st);
-    }
-    tm.mark();  // enumeration done
-    // exclusive prefixes of the pairs per type-I item and of the chunks per stream
-    // (one past the last entry holds the total)
-    const uint32_t ns = std::min<uint32_t>(hc[2], cfg.stream_cap);
-    {
-        const uint32_t n1 = std::min<uint32_t>(hc[1], cfg.t1_cap);
-        unsigned long long* t1_pre = S.get<unsigned long long>((size_t)n1 + 1);
-        unsigned long long* chunk_pre = S.get<unsigned long long>((size_t)ns + 1);
-        unsigned long long* tmp =
-            S.get<unsigned long long>(scan_tmp_words((int64_t)std::max(n1, ns) + 1));
+        const size_t tw = scan_tmp_words((int64_t)std::max(pre_cap1, pre_cap2));
+        if (tw > tmp_cap) {
+            tmp_cap = tw;
+            tmp = S.get<unsigned long long>(tmp_cap);
+        }
         CK(cudaMemsetAsync(cfg.t1_pairs + n1, 0, sizeof(uint32_t), st));
         CK(cudaMemsetAsync(cfg.stream_chunks + ns, 0, sizeof(uint32_t), st));
+        CK(cudaMemsetAsync(cfg.work64, 0, 2 * sizeof(unsigned long long), st));
         launch_scan_u32_to_u64(cfg.t1_pairs, t1_pre, (int64_t)n1 + 1, tmp, st);
         launch_scan_u32_to_u64(cfg.stream_chunks, chunk_pre, (int64_t)ns + 1, tmp, st);
         cfg.t1_pre = t1_pre;
         cfg.chunk_pre = chunk_pre;
+        launch_type1(cfg, st);
+        if (round == 0) tm.mark();  // (first round) type I done
+        launch_type2(cfg, st);
+        ++round;
+        if (end2 >= e2 && end1 >= e1) break;
+        // the next round: as many entries as this one
+        const uint32_t span2 = end2 - lo2, span1 = end1 - lo1;
+        lo2 = end2;
+        lo1 = end1;
+        hi2 = (uint32_t)std::min<uint64_t>(0xffffffffull, (uint64_t)lo2 + std::max<uint32_t>(span2, 1));
+        hi1 = (uint32_t)std::min<uint64_t>(0xffffffffull, (uint64_t)lo1 + std::max<uint32_t>(span1, 1));
+        attempt = 0;
     }
-    launch_type1(cfg, st);
-    tm.mark();  // type I done
-    launch_type2(cfg, st);
-    tm.mark();  // type II done
+    tm.mark();  // type II done (with every later round)
     unsigned long long hs[kNumStats + 1];
     CK(cudaMemcpyAsync(hs, stats, (kNumStats + 1) * sizeof(unsigned long long),
                        cudaMemcpyDeviceToHost, st));
@@ -539,9 +595,10 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     if (rc[5]) throw Status{GIRG_E_INTERNAL};
+    for (int q = 0; q < kNumStats; ++q) hs[q] += est_acc[q];
     hs[kStatRows] = rc[0];
     hs[kStatEdges] = hs[kNumStats];
-    hs[kStatStreams] = ns;
+    hs[kStatStreams] = total_streams;
     for (int q = 0; q < kNumStats; ++q) g_stats[q] = (int64_t)hs[q];
     g_stats[kStatLaunches] = (int64_t)g_launches;
     *num_edges = (int64_t)hs[kNumStats];

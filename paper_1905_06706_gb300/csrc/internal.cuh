@@ -106,18 +106,20 @@ struct DevCfg {
     uint64_t* ent1;           // type-I work entries
     unsigned int* ent1_count;
     uint32_t ent1_cap;
+    // the entries enumerated in this round: [lo, min(hi, count))
+    uint32_t ent2_lo, ent2_hi, ent1_lo, ent1_hi;
     T1Item* t1;
-    unsigned int* t1_count;
+    unsigned long long* t1_count;  // 64-bit: a round may produce more than it holds
     uint32_t t1_cap;
     uint32_t* t1_pairs;                 // pairs per type-I item (a_len * b_len)
     const unsigned long long* t1_pre;   // its exclusive prefix (t1 count + 1 entries)
     Stream* streams;
-    unsigned int* stream_count;
+    unsigned long long* stream_count;
     uint32_t stream_cap;
     uint32_t* stream_chunks;             // chunks per stream (>= 1)
     const unsigned long long* chunk_pre; // its exclusive prefix (stream count + 1 entries)
     Seg* segs;
-    unsigned int* seg_count;
+    unsigned long long* seg_count;
     uint32_t seg_cap;
     unsigned int* error;         // set when a stream needs 2^32 chunks or more
     unsigned long long* work64;  // [0] type-I pairs taken, [1] type-II chunks taken

@@ -438,9 +438,10 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum2(DevCfg cfg) {
     const int d = DIM ? DIM : cfg.d;
     Counters C;
     unsigned long long t2_items_local = 0;
-    const unsigned int count = *cfg.ent2_count < cfg.ent2_cap ? *cfg.ent2_count : cfg.ent2_cap;
+    unsigned int count = *cfg.ent2_count < cfg.ent2_cap ? *cfg.ent2_count : cfg.ent2_cap;
+    if (count > cfg.ent2_hi) count = cfg.ent2_hi;
     const unsigned int stride = gridDim.x * blockDim.x;
-    for (unsigned int b0 = blockIdx.x * blockDim.x; b0 < count; b0 += stride) {
+    for (unsigned int b0 = cfg.ent2_lo + blockIdx.x * blockDim.x; b0 < count; b0 += stride) {
         const unsigned int q = b0 + threadIdx.x;
         const bool active = q < count;
         EntryCtx x;
@@ -490,15 +491,16 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum2(DevCfg cfg) {
                 isg += b;
             }
         }
-        uint32_t st_base = 0, sg_base = 0;
+        unsigned long long st_base = 0, sg_base = 0;
         if (lane == 31) {
-            if (ist) st_base = atomicAdd(cfg.stream_count, ist);
-            if (isg) sg_base = atomicAdd(cfg.seg_count, isg);
+            if (ist) st_base = atomicAdd(cfg.stream_count, (unsigned long long)ist);
+            if (isg) sg_base = atomicAdd(cfg.seg_count, (unsigned long long)isg);
         }
         st_base = __shfl_sync(0xffffffffu, st_base, 31) + ist - nst;
         sg_base = __shfl_sync(0xffffffffu, sg_base, 31) + isg - nsg;
         if (nst) {
-            uint32_t off[2], pos[2] = {0u, 0u}, pre[2] = {0u, 0u};
+            unsigned long long off[2];
+            uint32_t pos[2] = {0u, 0u}, pre[2] = {0u, 0u};
             off[0] = sg_base;
             off[1] = sg_base + (keep[0] ? cnt[0] : 0u);
 #pragma unroll
@@ -519,7 +521,7 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum2(DevCfg cfg) {
                     st.pack = pack[g];
                     st.a_begin = x.a_lo;
                     st.a_len = x.a_len;
-                    st.seg_off = off[g];
+                    st.seg_off = (uint32_t)off[g];  // < seg_cap <= 2^32 when kept
                     st.seg_cnt = cnt[g];
                     st.S = sum[g];
                     st.tii = tidx[g];
@@ -534,7 +536,7 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum2(DevCfg cfg) {
                 uint32_t lo, len;
                 range_of(cfg, x, B, &lo, &len);
                 if (!len) return;
-                const uint32_t at = off[g - 1] + pos[g - 1];
+                const unsigned long long at = off[g - 1] + pos[g - 1];
                 if (at < cfg.seg_cap) cfg.segs[at] = Seg{lo, pre[g - 1]};
                 pos[g - 1] += 1u;
                 pre[g - 1] += len;
@@ -560,9 +562,10 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum1(DevCfg cfg) {
         for (int k = 0; k < d; ++k) n3 *= 3u;
     }
     unsigned long long t1_items_local = 0, t1_refs_local = 0;
-    const unsigned int count = *cfg.ent1_count < cfg.ent1_cap ? *cfg.ent1_count : cfg.ent1_cap;
+    unsigned int count = *cfg.ent1_count < cfg.ent1_cap ? *cfg.ent1_count : cfg.ent1_cap;
+    if (count > cfg.ent1_hi) count = cfg.ent1_hi;
     const unsigned int stride = gridDim.x * blockDim.x;
-    for (unsigned int b0 = blockIdx.x * blockDim.x; b0 < count; b0 += stride) {
+    for (unsigned int b0 = cfg.ent1_lo + blockIdx.x * blockDim.x; b0 < count; b0 += stride) {
         const unsigned int q = b0 + threadIdx.x;
         const bool active = q < count;
         EntryCtx x;
@@ -603,8 +606,8 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum1(DevCfg cfg) {
             const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += t;
         }
-        uint32_t tbase = 0;
-        if (lane == 31 && incl) tbase = atomicAdd(cfg.t1_count, incl);
+        unsigned long long tbase = 0;
+        if (lane == 31 && incl) tbase = atomicAdd(cfg.t1_count, (unsigned long long)incl);
         tbase = __shfl_sync(0xffffffffu, tbase, 31) + incl - nsub;
         if (nsub) {
             for (uint32_t c = 0; c < n3; ++c) {
@@ -699,7 +702,7 @@ __global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
     WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
     const View V = sorted_view(cfg);
     Counters C;
-    const uint32_t nit = *cfg.t1_count < cfg.t1_cap ? *cfg.t1_count : cfg.t1_cap;
+    const uint32_t nit = (uint32_t)(*cfg.t1_count < cfg.t1_cap ? *cfg.t1_count : cfg.t1_cap);
     const unsigned long long* pre = cfg.t1_pre;
     const unsigned long long total = pre[nit];
     uint32_t t1_edges = 0;
@@ -795,7 +798,8 @@ __global__ void __launch_bounds__(kT2Threads, 4) k_type2(DevCfg cfg) {
     WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
     const View V = sorted_view(cfg);
     Counters C;
-    const uint32_t nst = *cfg.stream_count < cfg.stream_cap ? *cfg.stream_count : cfg.stream_cap;
+    const uint32_t nst =
+        (uint32_t)(*cfg.stream_count < cfg.stream_cap ? *cfg.stream_count : cfg.stream_cap);
     const unsigned long long* pre = cfg.chunk_pre;
     const unsigned long long total = pre[nst];
     // the warp's bundle: lane j holds stream and chunk index of bundle chunk j
