@@ -247,6 +247,24 @@ def run_batched(gg, torch, k: int, workers_grid=(4, 8, 16)) -> dict:
                                    "p50_ms": _pct(lat, 0.5), "p99_ms": _pct(lat, 0.99)}}}
 
 
+def aggregate_ranks(vals, world: int, dist):
+    """Whole-job throughputs from every rank's [seconds, edges] for the device-timed,
+    end-to-end and FP64 runs: each is the edges of all ranks over the slowest rank's
+    time (replicas, "weak" scaling).  Every rank takes part in the gather."""
+    import torch
+    if world > 1:
+        gathered = [torch.zeros_like(vals) for _ in range(world)]
+        dist.all_gather(gathered, vals)
+        allv = torch.stack(gathered).cpu()
+    else:
+        allv = vals.cpu().unsqueeze(0)
+    out = []
+    for k in range(0, allv.shape[1], 2):
+        t = float(allv[:, k].max())
+        out.append(float(allv[:, k + 1].sum()) / t if t > 0 else None)
+    return tuple(out)
+
+
 def cpu_baseline(cfg: dict) -> dict:
     """The FP64 oracle (as it stands) on a bounded sample: n = 1e5, same d, beta, T,
     average degree; points + search for c + cell-pair sampler, one host core."""
@@ -399,18 +417,10 @@ def main():
     barrier()
     vals = torch.tensor([t_rank, float(m_total), sum(ms_e2e) / 1e3, float(m_e2e),
                          sum(ms64) / 1e3, float(m64)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        gathered = [torch.zeros_like(vals) for _ in range(world)]
-        dist.all_gather(gathered, vals)
-        allv = torch.stack(gathered).cpu()
-    else:
-        allv = vals.cpu().unsqueeze(0)
+    value, e2e_value, fp64_value = aggregate_ranks(vals, world, dist)
     if rank == 0:
-        t_max = float(allv[:, 0].max())
-        m_all = float(allv[:, 1].sum())
-        value = m_all / t_max
-        e2e_value = (float(allv[:, 3].sum()) / float(allv[:, 2].max())) if ms_e2e else None
-        fp64_value = (float(allv[:, 5].sum()) / float(allv[:, 4].max())) if ms64 else None
+        e2e_value = e2e_value if ms_e2e else None
+        fp64_value = fp64_value if ms64 else None
         m_step = m_total / args.steps
         # dominant kernel: the longer of the two single-kernel sampling phases
         ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}

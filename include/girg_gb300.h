@@ -186,6 +186,13 @@ int girg_expected_avg_degree(const girg_params* params, double* avg_deg, void* s
  * (it is then reported as 0 or infinity). */
 double girg_last_scale(void);
 
+/* Expected number of edges of the graph girg_generate would make with these parameters
+ * (n f / 2, f the expected average degree of App. B.2 for the generated weights; c > 0
+ * is used as given, else the c solved for avg_deg), for sizing the edge buffer; the
+ * realized count fluctuates around it.  Returns -1 on invalid parameters or a CUDA
+ * error. */
+int64_t girg_expected_edges(const girg_params* params, void* stream);
+
 /* Counters of the last generate call on this host thread: [0] type-I pairs tested,
  * [1] coins drawn, [2] FP64 rechecks, [3] type-II items (non-empty cell pairs),
  * [4] jump draws, [5] type-II candidates, [6] rows, [7] type-I items, [8] chunks of

@@ -72,6 +72,7 @@ SIGNATURES = {
     "girg_status_string": (ctypes.c_char_p, [I32]),
     "girg_det_eval": (DBL, [I32, DBL, DBL]),
     "girg_last_scale": (DBL, []),
+    "girg_expected_edges": (I64, [P, P]),
     "girg_scratch_bytes": (I64, [P]),
     "girg_server_create": (I32, [I32, I64, P]),
     "girg_server_submit": (I32, [P, P, P, I64, I64]),
@@ -143,6 +144,17 @@ def last_stats() -> dict:
     out = dict(zip(STAT_NAMES, list(buf)))
     out["edge_checksum"] &= (1 << 64) - 1  # unsigned
     return out
+
+
+def girg_expected_edges(*, n, d, beta, T, avg_deg=0.0, c=0.0, w_min=1.0, seed=1,
+                        stream=None) -> int:
+    """Expected edge count (for sizing the edge buffer)."""
+    _torch()
+    p = GirgParams(n, d, beta, T, avg_deg, c, w_min, seed, 4, PRECISION_FP32, 0)
+    m = load().girg_expected_edges(ctypes.byref(p), _stream(stream))
+    if m < 0:
+        raise GirgError(GIRG_E_PARAM, "girg_expected_edges")
+    return m
 
 
 def last_K() -> float:

@@ -781,6 +781,18 @@ double girg_det_eval(int32_t fn, double x, double y) {
     }
 }
 
+int64_t girg_expected_edges(const girg_params* params, void* stream) {
+    if (!params) return -1;
+    if (params->c > 0.0) {
+        double f = 0.0;
+        if (girg_expected_avg_degree(params, &f, stream) != GIRG_OK) return -1;
+        return (int64_t)std::llround(0.5 * f * (double)params->n);
+    }
+    // solved c: the expected degree is the target by construction
+    if (check_girg(params) != GIRG_OK) return -1;
+    return (int64_t)std::llround(0.5 * params->avg_deg * (double)params->n);
+}
+
 double girg_last_scale(void) { return g_last_K; }
 
 int girg_last_stats(int64_t* out, int32_t len) {

@@ -188,6 +188,8 @@ def test_generate_internal_points_and_c():
     # expected degree through the C ABI
     f = gg.girg_expected_avg_degree(n=n, d=d, beta=beta, T=T, c=c_ref, seed=21)
     assert f == pytest.approx(10.0, rel=1e-9)
+    assert gg.girg_expected_edges(n=n, d=d, beta=beta, T=T, c=c_ref, seed=21) == round(5.0 * n)
+    assert gg.girg_expected_edges(n=n, d=d, beta=beta, T=T, avg_deg=7.0, seed=21) == 7 * n // 2
 
 
 @pytest.mark.parametrize("d,T,beta,deg", [(2, 0.05, 2.5, 10.0), (3, 0.02, 2.2, 16.0),
