@@ -175,6 +175,12 @@ int girg_points(int64_t n, int32_t d, double beta, double w_min, uint64_t seed, 
 int hrg_points(int64_t n, double alpha, double R, uint64_t seed, double* d_r, uint32_t* d_X,
                void* stream);
 
+/* The vertices of hrg_generate as GIRG points through the mapping of Sec. 2.3:
+ * d_w n doubles, w_v = e^((R - r_v)/2); d_X n uint32, the 1-dimensional torus
+ * coordinate theta_v / (2 pi) in fixed point (the same bits as hrg_points). */
+int hrg_girg_points(int64_t n, double alpha, double R, uint64_t seed, double* d_w, uint32_t* d_X,
+                    void* stream);
+
 /* Expected average degree f(c) of App. B.2 for a GIRG with these parameters and
  * weights generated from params->seed (params->c is the c evaluated). */
 int girg_expected_avg_degree(const girg_params* params, double* avg_deg, void* stream);

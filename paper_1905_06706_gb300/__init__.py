@@ -65,6 +65,7 @@ SIGNATURES = {
                                     P]),
     "girg_points": (I32, [I64, I32, DBL, DBL, U64, P, P, P]),
     "hrg_points": (I32, [I64, DBL, DBL, U64, P, P, P]),
+    "hrg_girg_points": (I32, [I64, DBL, DBL, U64, P, P, P]),
     "girg_expected_avg_degree": (I32, [P, P, P]),
     "girg_last_stats": (I32, [P, I32]),
     "girg_last_phase_ms": (I32, [P, I32]),
@@ -292,6 +293,19 @@ def hrg_points(n, alpha, R, seed=1, stream=None):
     if st != GIRG_OK:
         raise GirgError(st, "hrg_points")
     return r, X
+
+
+def hrg_girg_points(n, alpha, R, seed=1, stream=None):
+    """The HRG's vertices as GIRG points (Sec. 2.3): weights (n,) float64 and 1-dimensional
+    positions (1, n) int32 (uint32 bit patterns)."""
+    torch = _torch()
+    lib = load()
+    w = torch.empty(n, dtype=torch.float64, device="cuda")
+    X = torch.empty((1, n), dtype=torch.int32, device="cuda")
+    st = lib.hrg_girg_points(n, alpha, R, seed, _ptr(w), _ptr(X), _stream(stream))
+    if st != GIRG_OK:
+        raise GirgError(st, "hrg_girg_points")
+    return w, X
 
 
 def girg_expected_avg_degree(*, n, d, beta, T, c, w_min=1.0, seed=1, stream=None) -> float:

@@ -831,6 +831,20 @@ int hrg_points(int64_t n, double alpha, double R, uint64_t seed, double* d_r, ui
     });
 }
 
+int hrg_girg_points(int64_t n, double alpha, double R, uint64_t seed, double* d_w, uint32_t* d_X,
+                    void* stream) {
+    if (n < 1 || !(alpha > 0.5) || !(R > 0.0) || !d_w || !d_X) return GIRG_E_PARAM;
+    return guarded([&] {
+        cudaStream_t st = (cudaStream_t)stream;
+        Scratch S(st);
+        double* r = S.get<double>(n);
+        launch_hrg_points(n, alpha, R, seed, r, d_w, d_X, st);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(st));
+        return GIRG_OK;
+    });
+}
+
 int girg_generate(const girg_params* params, void* d_edges, int64_t capacity_edges,
                   int64_t* num_edges, double* c_used, void* stream) {
     const int chk = check_girg(params);
