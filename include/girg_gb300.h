@@ -205,8 +205,9 @@ int64_t girg_expected_edges(const girg_params* params, void* stream);
  * all type-II streams, [9] edges, [10] kernel launches, [11] vertex references of the type-I items
  * (sum of both side lengths), [12] type-I edges, [13] type-II streams, [14] edge
  * checksum: the sum mod 2^64 over the edges (u < v) of the splitmix64 finalizer of
- * u 2^32 + v (as an int64 bit pattern; independent of the edge order).  Copies
- * min(len, 15) values; returns the number copied. */
+ * u 2^32 + v (as an int64 bit pattern; independent of the edge order), [15] type-II
+ * partner segments, [16] enumeration passes (rounds plus reruns after a work list
+ * grew).  Copies min(len, 17) values; returns the number copied. */
 int girg_last_stats(int64_t* out, int32_t len);
 
 /* Milliseconds spent in each phase of the last call on this host thread

@@ -402,8 +402,10 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     uint64_t t1_cap = clamp_cap((uint64_t)n * (1 + (uint64_t)(0.75 * n3)) + 65536, 1ull << 30);
     uint64_t stream_cap =
         tzero ? 1024 : clamp_cap((uint64_t)n * (2 + 2 * (uint64_t)d) + 65536, 1ull << 28);
-    uint64_t seg_cap =
-        tzero ? 1024 : clamp_cap((uint64_t)n * (4 + (uint64_t)(1.5 * n3)) + 65536, 1ull << 31);
+    // partner segments per vertex measured at n = 10^6, beta = 2.2, T = 0.7: about 4.4,
+    // 26, 136 and 656 for d = 1..4 (they grow like 6^d); sized with headroom
+    const uint64_t seg_per_v = d == 1 ? 8 : d == 2 ? 40 : d == 3 ? 224 : d == 4 ? 1024 : 4 * (uint64_t)n6;
+    uint64_t seg_cap = tzero ? 1024 : clamp_cap((uint64_t)n * seg_per_v + 65536, 1ull << 31);
     T1Item* t1 = S.get<T1Item>(t1_cap);
     uint32_t* t1_pairs = S.get<uint32_t>(t1_cap + 1);
     Stream* streams = S.get<Stream>(stream_cap);
@@ -497,7 +499,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     constexpr uint64_t kMaxT1 = 1ull << 30, kMaxStreams = 1ull << 28, kMaxSegs = 1ull << 31;
     uint32_t lo2 = 0, lo1 = 0, hi2 = 0xffffffffu, hi1 = 0xffffffffu;
     unsigned long long est_acc[kNumStats] = {0};
-    uint64_t total_streams = 0;
+    uint64_t total_streams = 0, total_segs = 0, passes = 0;
     unsigned long long *t1_pre = nullptr, *chunk_pre = nullptr, *tmp = nullptr;
     size_t pre_cap1 = 0, pre_cap2 = 0, tmp_cap = 0;
     int round = 0;
@@ -512,6 +514,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
         DevCfg ecfg = cfg;
         ecfg.stats = estats;
         launch_enumerate(ecfg, st);
+        ++passes;
         unsigned long long wc[3], es[kNumStats];
         unsigned int ec[2];
         CK(cudaMemcpyAsync(wc, wcount, sizeof(wc), cudaMemcpyDeviceToHost, st));
@@ -553,6 +556,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
         // (one past the last entry holds the total)
         const uint32_t n1 = (uint32_t)wc[0], ns = (uint32_t)wc[1];
         total_streams += ns;
+        total_segs += wc[2];
         if (n1 + 1ull > pre_cap1) {  // prefix buffers, reused by later rounds
             pre_cap1 = n1 + 1ull + (n1 >> 3);
             t1_pre = S.get<unsigned long long>(pre_cap1);
@@ -599,6 +603,8 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     hs[kStatRows] = rc[0];
     hs[kStatEdges] = hs[kNumStats];
     hs[kStatStreams] = total_streams;
+    hs[kStatSegs] = total_segs;
+    hs[kStatEnumPasses] = passes;
     for (int q = 0; q < kNumStats; ++q) g_stats[q] = (int64_t)hs[q];
     g_stats[kStatLaunches] = (int64_t)g_launches;
     *num_edges = (int64_t)hs[kNumStats];

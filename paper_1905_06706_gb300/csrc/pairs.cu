@@ -379,9 +379,12 @@ __device__ __forceinline__ void range_of(const DevCfg& cfg, const EntryCtx& x, u
 
 // Visit the distant partner cells B of A (children of the neighbours of A's
 // parent, not neighbours of A) in rank order, rank = (sum_k (e_k + 1) 3^(d-1-k)) 2^d
-// + sum_k kid_k 2^(d-1-k); f(B, g) for each one that counts for bucket j.
+// + sum_k kid_k 2^(d-1-k); f(B, g, lo, len) for each one that counts for bucket j,
+// with its range of sorted positions (len may be 0).  The 2^d children of a parent
+// neighbour are consecutive cells, so their ranges come from 2^d + 1 consecutive
+// offsets, and a parent neighbour without a vertex of bucket j is skipped after two.
 template <int DIM, class F>
-__device__ __forceinline__ void for_partners(const EntryCtx& x, int d, F f) {
+__device__ __forceinline__ void for_partners(const DevCfg& cfg, const EntryCtx& x, int d, F f) {
     constexpr int DM = DIM ? DIM : kMaxDim;
     const uint32_t n3d = DIM == 1 ? 3u : DIM == 2 ? 9u : DIM == 3 ? 27u : DIM == 4 ? 81u : 0u;
     uint32_t n3 = n3d;
@@ -393,6 +396,7 @@ __device__ __forceinline__ void for_partners(const EntryCtx& x, int d, F f) {
     int alpha[DM];
 #pragma unroll
     for (int k = 0; k < DM; ++k) alpha[k] = (k < d) ? (int)((x.A >> (d - 1 - k)) & 1u) : 0;
+    const uint32_t nk = 1u << d;
     for (uint32_t eidx = 0; eidx < n3; ++eidx) {
         int ek[DM];
         uint32_t q = eidx, P = 0;
@@ -409,8 +413,19 @@ __device__ __forceinline__ void for_partners(const EntryCtx& x, int d, F f) {
             P |= dil_add(PA, dim_mask(d, k, x.l - 1), 1u << (d - 1 - k), ek[k]);
         }
         if (!ok) continue;
-        const uint32_t nk = 1u << d;
+        bool any = false;  // a distant child of this parent neighbour that counts
+#pragma unroll
+        for (int k = 0; k < DM; ++k)
+            if (k < d && ek[k] != 0) any = true;  // the own parent has only neighbour kids
+        if (!any) continue;
+        const uint32_t first = P << d;
+        uint32_t lo = cfg.offs[x.baseB + (uint32_t)((uint64_t)first << x.sB)];
+        const uint32_t end = cfg.offs[x.baseB + (uint32_t)((uint64_t)(first + nk) << x.sB)];
+        if (lo == end) continue;  // no vertex of bucket j under this parent neighbour
         for (uint32_t kids = 0; kids < nk; ++kids) {
+            const uint32_t hi =
+                kids + 1 < nk ? cfg.offs[x.baseB + (uint32_t)((uint64_t)(first + kids + 1) << x.sB)]
+                              : end;
             int linf = 0;
 #pragma unroll
             for (int k = 0; k < DM; ++k) {
@@ -421,10 +436,9 @@ __device__ __forceinline__ void for_partners(const EntryCtx& x, int d, F f) {
                 if (x.l == 2 && diff > 2) diff = 4 - diff;  // 4 cells per dimension
                 linf = diff > linf ? diff : linf;
             }
-            if (linf <= 1) continue;  // a neighbour of A, not distant
-            const uint32_t B = (P << d) | kids;
-            if (x.j == x.i && B <= x.A) continue;
-            f(B, (uint32_t)(linf - 1));
+            const uint32_t B = first | kids;
+            if (linf > 1 && !(x.j == x.i && B <= x.A)) f(B, (uint32_t)(linf - 1), lo, hi - lo);
+            lo = hi;
         }
     }
 }
@@ -449,9 +463,7 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum2(DevCfg cfg) {
         uint32_t pack[2] = {0u, 0u};
         if (active) {
             x = decode_entry<DIM>(cfg, cfg.ent2[q], d, false);
-            for_partners<DIM>(x, d, [&](uint32_t B, uint32_t g) {
-                uint32_t lo, len;
-                range_of(cfg, x, B, &lo, &len);
+            for_partners<DIM>(cfg, x, d, [&](uint32_t, uint32_t g, uint32_t, uint32_t len) {
                 if (len) {
                     cnt[g - 1] += 1u;
                     sum[g - 1] += len;
@@ -531,10 +543,8 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum2(DevCfg cfg) {
                 }
                 ++st_base;
             }
-            for_partners<DIM>(x, d, [&](uint32_t B, uint32_t g) {
+            for_partners<DIM>(cfg, x, d, [&](uint32_t, uint32_t g, uint32_t lo, uint32_t len) {
                 if (!keep[g - 1]) return;
-                uint32_t lo, len;
-                range_of(cfg, x, B, &lo, &len);
                 if (!len) return;
                 const unsigned long long at = off[g - 1] + pos[g - 1];
                 if (at < cfg.seg_cap) cfg.segs[at] = Seg{lo, pre[g - 1]};

@@ -113,10 +113,19 @@ extern "C" {
 
 int64_t girg_scratch_bytes(const girg_params* p) {
     if (!p || p->n < 1 || p->d < 1 || p->d > 8) return -1;
-    int64_t n3 = 1;
-    for (int k = 0; k < p->d; ++k) n3 *= 3;
-    // per-vertex arrays, sort buffers, work lists at their sizing rules, and slack
-    return p->n * (int64_t)(240 + 32 * n3 + 64 * p->d) + (64ll << 20);
+    const int d = p->d;
+    int64_t n3 = 1, n6 = 1;
+    for (int k = 0; k < d; ++k) {
+        n3 *= 3;
+        n6 *= 6;
+    }
+    // per vertex: points, sort buffers, sorted arrays, cell offsets and work entries
+    // (about 400 + 112 d bytes), type-I items with pair counts and prefixes (28 bytes
+    // each, 1 + 0.75 3^d per vertex), and the partner segments (8 bytes each) at the
+    // library's initial work-list sizes; more is allocated only when a list grows
+    const int64_t seg = p->T > 0.0 ? (d == 1 ? 8 : d == 2 ? 40 : d == 3 ? 224 : d == 4 ? 1024 : 4 * n6) : 0;
+    const int64_t per_v = 400 + 112 * d + 21 * n3 + 8 * seg;
+    return p->n * per_v + (64ll << 20);
 }
 
 int girg_server_create(int32_t workers, int64_t memory_budget_bytes, girg_server** out) {
