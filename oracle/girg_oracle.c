@@ -153,8 +153,8 @@ static double two_atanh_series(double s) {
 }
 
 /* ln x = e ln 2 + ln m with x = m 2^e, m in (sqrt(1/2), sqrt(2)];
- * ln m = 2 atanh((m-1)/(m+1)). */
-double orc_det_log(double x) {
+ * ln m = 2 atanh((m-1)/(m+1)).  Builds the tables of orc_det_log below. */
+static double det_log_series(double x) {
     if (x != x || x < 0.0) return NAN;
     if (x == 0.0) return -INFINITY;
     if (x == INFINITY) return INFINITY;
@@ -180,17 +180,9 @@ double orc_det_log(double x) {
     return ed * LN2_HI + (lm + ed * LN2_LO);
 }
 
-/* ln(1+x) for x > -1; for |x| < 1/4 via 2 atanh(x/(2+x)), else det_log(1+x). */
-double orc_det_log1p(double x) {
-    if (x != x || x < -1.0) return NAN;
-    if (x == -1.0) return -INFINITY;
-    if (x < -0.25 || x > 0.25) return orc_det_log(1.0 + x);
-    double s = x / (2.0 + x);
-    return two_atanh_series(s);
-}
-
-/* e^x = 2^k e^r, k = nearest integer to x / ln 2, r = x - k ln 2, Taylor to r^17. */
-double orc_det_exp(double x) {
+/* e^x = 2^k e^r, k = nearest integer to x / ln 2, r = x - k ln 2, Taylor to r^17.
+ * Builds the table of orc_det_exp below. */
+static double det_exp_series(double x) {
     if (x != x) return NAN;
     if (x > 710.0) return INFINITY;
     if (x < -746.0) return 0.0;
@@ -219,6 +211,98 @@ double orc_det_exp(double x) {
     if (k < -1021) return (p * pow2i(k + 600)) * pow2i(-600);
     return p * pow2i(k);
 }
+
+/* Table-driven ln and exp.  The tables come from the series forms above:
+ * E2[j] = 2^(j/64) (j = 0..63), LC[j-45] = ln(j/64), IC[j-45] = 64/j (j = 45..91). */
+static double E2[64], LC[47], IC[47];
+static int det_tab_ready = 0;
+
+static void det_tab_init(void) {
+    if (det_tab_ready) return;
+    for (int j = 0; j < 64; j++)
+        E2[j] = det_exp_series((double)j * 0x1.62e42fee00000p-7 + (double)j * 0x1.a39ef35793c76p-39);
+    for (int j = 45; j <= 91; j++) {
+        LC[j - 45] = det_log_series((double)j * 0x1p-6);
+        IC[j - 45] = 64.0 / (double)j;
+    }
+    det_tab_ready = 1;
+}
+
+/* ln x: x = m 2^e with m in (sqrt(1/2), sqrt(2)]; c = j/64 the table point nearest
+ * to m, r = (m - c) 64/j, ln(1 + r) by its series to r^9 (|r| <= 1/90);
+ * ln x = e ln 2 + ln c + ln(1 + r). */
+double orc_det_log(double x) {
+    if (x != x || x < 0.0) return NAN;
+    if (x == 0.0) return -INFINITY;
+    if (x == INFINITY) return INFINITY;
+    det_tab_init();
+    int e_adj = 0;
+    if (x < 0x1p-1022) { /* subnormal: scale into the normal range */
+        x = x * 0x1p54;
+        e_adj = -54;
+    }
+    uint64_t bits;
+    memcpy(&bits, &x, 8);
+    int e = (int)((bits >> 52) & 0x7ff) - 1023;
+    bits = (bits & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL;
+    double m;
+    memcpy(&m, &bits, 8); /* m in [1,2) */
+    if (m > 0x1.6a09e667f3bcdp+0) { /* sqrt(2) */
+        m = m * 0.5;
+        e = e + 1;
+    }
+    e = e + e_adj;
+    int j = (int)floor(m * 64.0 + 0.5);
+    double r = (m - (double)j * 0x1p-6) * IC[j - 45];
+    double t = 1.0 / 9.0;
+    t = 1.0 / 8.0 - r * t;
+    t = 1.0 / 7.0 - r * t;
+    t = 1.0 / 6.0 - r * t;
+    t = 1.0 / 5.0 - r * t;
+    t = 1.0 / 4.0 - r * t;
+    t = 1.0 / 3.0 - r * t;
+    t = 0.5 - r * t;
+    t = 1.0 - r * t;
+    double l1 = r * t;
+    double ed = (double)e;
+    return ed * LN2_HI + (LC[j - 45] + (l1 + ed * LN2_LO));
+}
+
+/* e^x = 2^m 2^(j/64) e^r, k = nearest integer to 64 x / ln 2 = 64 m + j,
+ * r = x - k ln2/64 (|r| <= ln2/128), e^r by its series to r^7. */
+double orc_det_exp(double x) {
+    if (x != x) return NAN;
+    if (x > 710.0) return INFINITY;
+    if (x < -746.0) return 0.0;
+    det_tab_init();
+    double kd = floor(x * 0x1.71547652b82fep+6 + 0.5);
+    int k = (int)kd;
+    double r = (x - kd * 0x1.62e42fee00000p-7) - kd * 0x1.a39ef35793c76p-39;
+    int j = k & 63;
+    int m = (k - j) / 64;
+    double p = 1.0 / 5040.0;
+    p = 1.0 / 720.0 + r * p;
+    p = 1.0 / 120.0 + r * p;
+    p = 1.0 / 24.0 + r * p;
+    p = 1.0 / 6.0 + r * p;
+    p = 0.5 + r * p;
+    p = 1.0 + r * p;
+    p = 1.0 + r * p;
+    double v = E2[j] * p;
+    if (m > 1023) return (v * pow2i(1023)) * pow2i(m - 1023);
+    if (m < -1021) return (v * pow2i(m + 600)) * pow2i(-600);
+    return v * pow2i(m);
+}
+
+/* ln(1+x) for x > -1; for |x| < 1/4 via 2 atanh(x/(2+x)), else det_log(1+x). */
+double orc_det_log1p(double x) {
+    if (x != x || x < -1.0) return NAN;
+    if (x == -1.0) return -INFINITY;
+    if (x < -0.25 || x > 0.25) return orc_det_log(1.0 + x);
+    double s = x / (2.0 + x);
+    return two_atanh_series(s);
+}
+
 
 double orc_det_pow(double x, double y) { return orc_det_exp(y * orc_det_log(x)); }
 

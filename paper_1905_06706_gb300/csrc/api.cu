@@ -650,6 +650,7 @@ int check_girg(const girg_params* p) {
 template <class F>
 int guarded(F&& f) {
     try {
+        if (!det_tables_gen() || !det_tables_pairs()) return GIRG_E_CUDA;
         return f();
     } catch (const CudaFail& e) {
         fprintf(stderr, "girg_gb300: CUDA error %s\n", cudaGetErrorString(e.err));

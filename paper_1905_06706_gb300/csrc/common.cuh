@@ -10,6 +10,7 @@
 // so that host and device -- and any other IEEE machine following the same
 // steps -- produce identical bits.
 #pragma once
+#include <mutex>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <math.h>
@@ -140,8 +141,9 @@ GG_HD double two_atanh(double s) {
     return DADD(DMUL(2.0, s), DMUL(2.0, t));
 }
 
-// ln x: x = m 2^e with m in (sqrt(1/2), sqrt(2)], ln m = 2 atanh((m-1)/(m+1)).
-GG_HD double det_log(double x) {
+// ln x by the series: x = m 2^e with m in (sqrt(1/2), sqrt(2)], ln m = 2 atanh((m-1)/(m+1)).
+// Only builds the tables of det_log / det_exp below.
+GG_HD double det_log_series(double x) {
     if (x != x || x < 0.0) return dnan();
     if (x == 0.0) return -dinf();
     if (x == dinf()) return dinf();
@@ -164,16 +166,8 @@ GG_HD double det_log(double x) {
     return DADD(DMUL(ed, kLn2Hi), DADD(lm, DMUL(ed, kLn2Lo)));
 }
 
-// ln(1+x), x > -1: 2 atanh(x/(2+x)) for |x| <= 1/4, else ln(1+x).
-GG_HD double det_log1p(double x) {
-    if (x != x || x < -1.0) return dnan();
-    if (x == -1.0) return -dinf();
-    if (x < -0.25 || x > 0.25) return det_log(DADD(1.0, x));
-    return two_atanh(DDIV(x, DADD(2.0, x)));
-}
-
 // e^x = 2^k e^r, k = round(x / ln 2), r = x - k ln 2, Taylor series to r^17.
-GG_HD double det_exp(double x) {
+GG_HD double det_exp_series(double x) {
     if (x != x) return x;
     if (x > 710.0) return dinf();
     if (x < -746.0) return 0.0;
@@ -202,6 +196,132 @@ GG_HD double det_exp(double x) {
     if (k < -1021) return DMUL(DMUL(p, pow2i(k + 600)), pow2i(-600));
     return DMUL(p, pow2i(k));
 }
+
+// ---------------------------------------------------------------- table-driven log / exp
+// Tables of the deterministic log and exp, built from the series forms above (the
+// same IEEE operations on every machine, so every copy holds the same bits):
+// e2[j] = 2^(j/64), j = 0..63; lc[j - 45] = ln(j/64), ic[j - 45] = 64/j, j = 45..91.
+struct DetTab {
+    double e2[64];
+    double lc[47];
+    double ic[47];
+};
+
+inline DetTab make_det_tab() {
+    DetTab t;
+    for (int j = 0; j < 64; ++j)
+        t.e2[j] = det_exp_series(DADD(DMUL((double)j, 0x1.62e42fee00000p-7),
+                                      DMUL((double)j, 0x1.a39ef35793c76p-39)));
+    for (int j = 45; j <= 91; ++j) {
+        t.lc[j - 45] = det_log_series((double)j * 0x1p-6);
+        t.ic[j - 45] = 64.0 / (double)j;
+    }
+    return t;
+}
+
+inline const DetTab& det_tab_host() {
+    static const DetTab t = make_det_tab();
+    return t;
+}
+
+#ifdef __CUDACC__
+// One device copy per translation unit, filled once per device by det_tables_ready()
+// before the first launch of a kernel that uses det_log / det_exp.
+static __device__ DetTab g_det_tab;
+
+static inline bool det_tables_ready() {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+        if (cudaMemcpyToSymbol(g_det_tab, &det_tab_host(), sizeof(DetTab)) != cudaSuccess)
+            return false;
+        done[dev] = true;
+    }
+    return true;
+}
+#endif
+
+GG_HD const DetTab& det_tab() {
+#ifdef __CUDA_ARCH__
+    return g_det_tab;
+#else
+    return det_tab_host();
+#endif
+}
+
+// ln x: x = m 2^e with m in (sqrt(1/2), sqrt(2)]; m = c (1 + r) with c = j/64 the
+// nearest table point, r = (m - c) 64/j (m - c is exact), |r| <= 1/90; ln(1 + r) by
+// its series to r^9.  ln x = e ln 2 + ln c + ln(1 + r).
+GG_HD double det_log(double x) {
+    if (x != x || x < 0.0) return dnan();
+    if (x == 0.0) return -dinf();
+    if (x == dinf()) return dinf();
+    int e_adj = 0;
+    if (x < 0x1p-1022) {
+        x = DMUL(x, 0x1p54);
+        e_adj = -54;
+    }
+    const uint64_t b = double_to_bits(x);
+    int e = (int)((b >> 52) & 0x7ff) - 1023;
+    double m = bits_to_double((b & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL);
+    if (m > kSqrt2) {
+        m = DMUL(m, 0.5);
+        e = e + 1;
+    }
+    e = e + e_adj;
+    const int j = (int)floor(DADD(DMUL(m, 64.0), 0.5));
+    const DetTab& T = det_tab();
+    const double r = DMUL(DSUB(m, (double)j * 0x1p-6), T.ic[j - 45]);
+    double t = 1.0 / 9.0;
+    t = DSUB(1.0 / 8.0, DMUL(r, t));
+    t = DSUB(1.0 / 7.0, DMUL(r, t));
+    t = DSUB(1.0 / 6.0, DMUL(r, t));
+    t = DSUB(1.0 / 5.0, DMUL(r, t));
+    t = DSUB(1.0 / 4.0, DMUL(r, t));
+    t = DSUB(1.0 / 3.0, DMUL(r, t));
+    t = DSUB(0.5, DMUL(r, t));
+    t = DSUB(1.0, DMUL(r, t));
+    const double l1 = DMUL(r, t);
+    const double ed = (double)e;
+    return DADD(DMUL(ed, kLn2Hi), DADD(T.lc[j - 45], DADD(l1, DMUL(ed, kLn2Lo))));
+}
+
+// e^x = 2^m 2^(j/64) e^r with k = round(64 x / ln 2) = 64 m + j, r = x - k ln2/64
+// (|r| <= ln2/128), e^r by its series to r^7.
+GG_HD double det_exp(double x) {
+    if (x != x) return x;
+    if (x > 710.0) return dinf();
+    if (x < -746.0) return 0.0;
+    const double kd = floor(DADD(DMUL(x, 0x1.71547652b82fep+6), 0.5));
+    const int k = (int)kd;
+    const double r = DSUB(DSUB(x, DMUL(kd, 0x1.62e42fee00000p-7)), DMUL(kd, 0x1.a39ef35793c76p-39));
+    const int j = k & 63;
+    const int m = (k - j) / 64;
+    double p = 1.0 / 5040.0;
+    p = DADD(1.0 / 720.0, DMUL(r, p));
+    p = DADD(1.0 / 120.0, DMUL(r, p));
+    p = DADD(1.0 / 24.0, DMUL(r, p));
+    p = DADD(1.0 / 6.0, DMUL(r, p));
+    p = DADD(0.5, DMUL(r, p));
+    p = DADD(1.0, DMUL(r, p));
+    p = DADD(1.0, DMUL(r, p));
+    const double v = DMUL(det_tab().e2[j], p);
+    if (m > 1023) return DMUL(DMUL(v, pow2i(1023)), pow2i(m - 1023));
+    if (m < -1021) return DMUL(DMUL(v, pow2i(m + 600)), pow2i(-600));
+    return DMUL(v, pow2i(m));
+}
+
+// ln(1+x), x > -1: 2 atanh(x/(2+x)) for |x| <= 1/4, else ln(1+x).
+GG_HD double det_log1p(double x) {
+    if (x != x || x < -1.0) return dnan();
+    if (x == -1.0) return -dinf();
+    if (x < -0.25 || x > 0.25) return det_log(DADD(1.0, x));
+    return two_atanh(DDIV(x, DADD(2.0, x)));
+}
+
 
 GG_HD double det_pow(double x, double y) { return det_exp(DMUL(y, det_log(x))); }
 

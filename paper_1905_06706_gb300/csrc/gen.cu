@@ -209,7 +209,7 @@ __global__ void k_split_weights(int64_t n, const double* __restrict__ w,
                                 double* __restrict__ out, unsigned int cap,
                                 unsigned int* __restrict__ count, double* __restrict__ part) {
     __shared__ double s[4][8];
-    const double t = *thr;
+    const double t = *thr, inv_t = 1.0 / t;  // only feeds the search for K: no exact rounding needed
     double a[4] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
@@ -221,7 +221,7 @@ __global__ void k_split_weights(int64_t n, const double* __restrict__ w,
             a[0] += wv;
             a[1] += wv * wv;
             if (invT > 0.0) {
-                const double x = wv / t;
+                const double x = fmin(wv * inv_t, 1.0);
                 double y;
                 if (m_int > 0) {
                     y = x;
@@ -292,6 +292,8 @@ __global__ void __launch_bounds__(1024) k_sort_top(double* __restrict__ buf,
         buf[i] = __longlong_as_double((long long)s_key[i]);
     if (threadIdx.x == 0) count[1] = 1u;
 }
+
+bool det_tables_gen() { return det_tables_ready(); }
 
 // ------------------------------------------------------------------ launchers
 static int grid_for(int64_t n, int threads, int max_blocks) {

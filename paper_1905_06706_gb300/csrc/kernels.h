@@ -7,6 +7,11 @@ namespace gg {
 
 struct DevCfg;
 
+// Copy the tables of det_log / det_exp to the current device for the kernels of
+// gen.cu and pairs.cu (once per device; false if the copy failed).
+bool det_tables_gen();
+bool det_tables_pairs();
+
 // Kernel launches issued by the library on this host thread (for the benchmark's
 // launch count).
 extern thread_local unsigned long long g_launches;

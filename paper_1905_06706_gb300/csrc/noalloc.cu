@@ -100,6 +100,7 @@ extern "C" int girg_allpairs_noalloc(int64_t n, int32_t d, const uint32_t* d_X, 
     cfg.cap = capacity_edges;
     cfg.stats = counters;
     cfg.edge_count = counters + kNumStats;
+    if (!det_tables_pairs()) return GIRG_E_CUDA;
     launch_allpairs(cfg, d_X, d_w, sv, st);
     unsigned long long m = 0;
     if (cudaMemcpyAsync(&m, counters + kNumStats, sizeof(m), cudaMemcpyDeviceToHost, st) !=

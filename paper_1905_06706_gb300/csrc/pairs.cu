@@ -958,6 +958,8 @@ __global__ void __launch_bounds__(256) k_allpairs(DevCfg cfg, View V, unsigned i
     flush_edges(cfg, we, 1);
 }
 
+bool det_tables_pairs() { return det_tables_ready(); }
+
 // ------------------------------------------------------------------ launchers
 void launch_rows(const DevCfg& cfg, cudaStream_t st) {
     int64_t b = (cfg.n + 255) / 256;

@@ -99,7 +99,8 @@ def test_det_log_exp_against_mpmath():
     worst = 0
     for y in ys:
         worst = max(worst, _ulp_err(O.det_exp(y), mp.exp(mp.mpf(y))))
-    assert worst <= 2.0, worst
+    # table-driven: 2^(j/64) from the series (about 1 ulp) times e^r (about 1 ulp)
+    assert worst <= 3.0, worst
     assert O.det_exp(0.0) == 1.0 and O.det_log(1.0) == 0.0
     assert O.det_exp(800.0) == math.inf and O.det_exp(-800.0) == 0.0
     assert O.det_log(0.0) == -math.inf
