@@ -695,7 +695,7 @@ SplitDev split_buffers(int64_t n, Scratch& S) {
     D.thr = S.get<double>(1);
     D.sums = S.get<double>(4);
     D.part = S.get<double>((size_t)4 * reduce_blocks(n));
-    D.cap = kTopSortMax;
+    D.cap = 4 * kTopSortMax;  // more than the device sorts: the host sorts those
     D.buf = S.get<double>(D.cap);
     return D;
 }

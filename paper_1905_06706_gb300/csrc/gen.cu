@@ -261,7 +261,7 @@ __global__ void k_split_finish(const double* __restrict__ part, int nb, double* 
 // when sorted, 0 when there were more than kTopSortMax.
 __global__ void __launch_bounds__(1024) k_sort_top(double* __restrict__ buf,
                                                    unsigned int* __restrict__ count) {
-    extern __shared__ unsigned long long s_key[];
+    __shared__ unsigned long long s_key[kTopSortMax];
     const unsigned int k = count[0];
     if (k > kTopSortMax) {
         if (threadIdx.x == 0) count[1] = 0u;
@@ -344,12 +344,6 @@ void launch_split_threshold(Reduce* red, const double* part_s2, int64_t n, int d
 void launch_split_weights(int64_t n, const double* w, const double* thr, double T, double* out,
                           unsigned int cap, unsigned int* count, double* part, double* sums,
                           cudaStream_t st) {
-    static const bool attr = [] {
-        return cudaFuncSetAttribute(k_sort_top, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(kTopSortMax * sizeof(unsigned long long))) ==
-               cudaSuccess;
-    }();
-    (void)attr;
     const double invT = T > 0.0 ? 1.0 / T : 0.0;
     int m_int = 0;
     if (invT > 0.0 && invT == floor(invT) && invT <= 64.0) m_int = (int)invT;
@@ -357,7 +351,7 @@ void launch_split_weights(int64_t n, const double* w, const double* thr, double 
     g_launches += 3;
     k_split_weights<<<nb, 256, 0, st>>>(n, w, thr, invT, m_int, out, cap, count, part);
     k_split_finish<<<1, 256, 0, st>>>(part, nb, sums);
-    k_sort_top<<<1, 1024, kTopSortMax * sizeof(unsigned long long), st>>>(out, count);
+    k_sort_top<<<1, 1024, 0, st>>>(out, count);
 }
 
 }  // namespace gg

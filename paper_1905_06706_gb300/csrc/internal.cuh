@@ -263,15 +263,20 @@ __device__ __forceinline__ float one_minus_uniform32(uint32_t lo, uint32_t hi) {
                 __uint2float_rn(~hi) * 0x1p-32f);
 }
 
+// log2 U from the hardware approximation: U >= 2^-53 is a normal float and
+// |log2 U| <= 53, so the absolute error is at most 2 ulp of 64 (2^-17) plus the
+// 2^-23 relative rounding of U (2^-22.5): far inside the decision bands.
 __device__ __forceinline__ float log2_uniform32(uint32_t lo, uint32_t hi) {
-    return log2f(uniform32(lo, hi));
+    return __log2f(uniform32(lo, hi));
 }
 
-// ln U in single precision with relative error ~2^-22 for all U in (0, 1): for
-// U >= 1/2 through ln(1 - (1 - U)).
+// ln U in single precision with relative error <= 2^-20.5 for all U in (0, 1):
+// for U >= 1/2 through ln(1 - (1 - U)); below 1/2 the hardware approximation
+// (3 ulp off [1/2, 2], 2^-21.4 absolute at U = 1/2, i.e. 2^-20.9 relative) plus
+// the 2^-23 rounding of U.
 __device__ __forceinline__ float ln_uniform32(uint32_t lo, uint32_t hi) {
     if (hi >= 0x80000000u) return log1pf(-one_minus_uniform32(lo, hi));
-    return logf(uniform32(lo, hi));
+    return __logf(uniform32(lo, hi));
 }
 
 // Geometric jump X = floor(ln U / ln(1 - pbar)) against the remaining length rem

@@ -43,7 +43,7 @@ void launch_reduce(int64_t n, const double* w, const double* r, double w_min, in
 // that gathers the weights above *thr (count[0]; sorted in decreasing order when
 // count[0] <= kTopSortMax, count[1] = 1) and sums over the rest: sums[0..3] = sum w,
 // sum w^2, sum (w/thr)^(1/T), sum (w/thr)^(2/T).  part: 4 reduce_blocks(n) doubles.
-constexpr unsigned int kTopSortMax = 16384;
+constexpr unsigned int kTopSortMax = 4096;  // sorted in 32 KB of static shared memory
 void launch_split_threshold(Reduce* red, const double* part_s2, int64_t n, int d, double T,
                             double target, int E0, double* thr, cudaStream_t st);
 void launch_split_weights(int64_t n, const double* w, const double* thr, double T, double* out,

@@ -168,7 +168,7 @@ __device__ bool decide_t1(const DevCfg& cfg, const View& V, uint32_t pu, uint32_
         return girg_t1_exact(cfg, V, pu, pv, D, 0u, 0u);
     }
     if (ratio >= 1.0f + cfg.band_ratio) return true;  // p = 1
-    const float lp = cfg.dT * log2f(ratio);          // log2 p
+    const float lp = cfg.dT * __log2f(ratio);        // log2 p (ratio < 2^-126 gives -inf)
     if (lp < -54.0f - cfg.bandG) return false;        // p < 2^-54 < every U
     ++C.coins;
     const P4 o = philox(a, b, kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
@@ -198,7 +198,11 @@ __device__ bool accept_t2(const DevCfg& cfg, const View& V, uint32_t pu, uint32_
     if (D == 0) return true;
     const float ratio = kappa_ratio(V, pu, pv, D);
     if (ratio >= 1.0f + cfg.band_ratio) return true;
-    const float G = cfg.dT * log2f(ratio) - log2_uniform32(lo, hi) - e.log2pbar;
+    if (ratio < 0x1p-126f) {  // subnormal: no relative error bound in single precision
+        ++C.recheck;
+        return t2_exact(cfg, V, pu, pv, D, lo, hi, e.pbar);
+    }
+    const float G = cfg.dT * __log2f(ratio) - log2_uniform32(lo, hi) - e.log2pbar;
     if (G > cfg.bandG) return true;
     if (G < -cfg.bandG) return false;
     ++C.recheck;
@@ -377,77 +381,166 @@ __device__ __forceinline__ void range_of(const DevCfg& cfg, const EntryCtx& x, u
     *len = cfg.offs[x.baseB + (uint32_t)(((uint64_t)B + 1) << x.sB)] - a;
 }
 
+// Distances in cells along one dimension between A and the children of its parent's
+// neighbours: 3 bits for child position 2 (e + 1) + kid, where e in {-1, 0, 1} is the
+// parent offset and kid the child bit; A's own child bit alpha fixes the row
+// (alpha 0: 2 1 0 1 2 3, alpha 1: 3 2 1 0 1 2).  With 4 cells per dimension (level 2)
+// a distance of 3 wraps around the torus to 1.
+__host__ __device__ constexpr uint32_t pack6(uint32_t a, uint32_t b, uint32_t c, uint32_t d,
+                                             uint32_t e, uint32_t f) {
+    return a | b << 3 | c << 6 | d << 9 | e << 12 | f << 15;
+}
+__device__ __forceinline__ uint32_t child_dists(uint32_t alpha, bool four) {
+    if (alpha) return four ? pack6(1, 2, 1, 0, 1, 2) : pack6(3, 2, 1, 0, 1, 2);
+    return four ? pack6(2, 1, 0, 1, 2, 1) : pack6(2, 1, 0, 1, 2, 3);
+}
+
+// The children (d-bit numbers, dimension 0 most significant) whose bit of dimension k
+// is set, as a bit set over the 2^d children (d <= 5).
+__device__ __forceinline__ uint32_t kids_with_bit(int d, int k) {
+    const int b = d - 1 - k;
+    const uint32_t pat = b == 0 ? 0xAAAAAAAAu : b == 1 ? 0xCCCCCCCCu : b == 2 ? 0xF0F0F0F0u
+                       : b == 3 ? 0xFF00FF00u : 0xFFFF0000u;
+    return d >= 5 ? pat : pat & ((1u << (1u << d)) - 1u);
+}
+
 // Visit the distant partner cells B of A (children of the neighbours of A's
-// parent, not neighbours of A) in rank order, rank = (sum_k (e_k + 1) 3^(d-1-k)) 2^d
-// + sum_k kid_k 2^(d-1-k); f(B, g, lo, len) for each one that counts for bucket j,
-// with its range of sorted positions (len may be 0).  The 2^d children of a parent
-// neighbour are consecutive cells, so their ranges come from 2^d + 1 consecutive
-// offsets, and a parent neighbour without a vertex of bucket j is skipped after two.
+// parent, not neighbours of A) that count for bucket j and hold a vertex of it:
+// f(B, g, lo, len) with the gap g = L_inf distance - 1 in {1, 2} and the range of
+// sorted positions (len > 0), in rank order, rank = (sum_k (e_k + 1) 3^(d-1-k)) 2^d
+// + sum_k kid_k 2^(d-1-k).  The 2^d children of a parent neighbour are consecutive
+// cells with 2^d + 1 consecutive offsets.  The parent neighbours go in groups of
+// three that differ in the last digit only: the first and end offsets of a group are
+// loaded together, then (d <= 3) the inner offsets of its non-empty members, so a
+// group costs two dependent loads.  For d <= 4 the distant children of a parent
+// neighbour and their gaps come from per-dimension bit sets of the children.
 template <int DIM, class F>
 __device__ __forceinline__ void for_partners(const DevCfg& cfg, const EntryCtx& x, int d, F f) {
     constexpr int DM = DIM ? DIM : kMaxDim;
-    const uint32_t n3d = DIM == 1 ? 3u : DIM == 2 ? 9u : DIM == 3 ? 27u : DIM == 4 ? 81u : 0u;
-    uint32_t n3 = n3d;
+    constexpr uint32_t NG = DIM == 1 ? 1u : DIM == 2 ? 3u : DIM == 3 ? 9u : DIM == 4 ? 27u : 0u;
+    constexpr bool kMasks = DIM >= 1 && DIM <= 4;  // 2^d <= 16 children per bit set
+    constexpr bool kBatch = DIM >= 1 && DIM <= 3;  // inner offsets of a group in registers
+    constexpr int NKB = DIM >= 1 && DIM <= 3 ? (1 << DIM) - 1 : 1;
+    uint32_t ng = NG;
     if (DIM == 0) {
-        n3 = 1;
-        for (int k = 0; k < d; ++k) n3 *= 3u;
+        ng = 1;
+        for (int k = 1; k < d; ++k) ng *= 3u;
     }
-    const uint32_t PA = x.A >> d;
-    int alpha[DM];
-#pragma unroll
-    for (int k = 0; k < DM; ++k) alpha[k] = (k < d) ? (int)((x.A >> (d - 1 - k)) & 1u) : 0;
     const uint32_t nk = 1u << d;
-    for (uint32_t eidx = 0; eidx < n3; ++eidx) {
+    const uint32_t PA = x.A >> d;
+    const int lev = x.l - 1;  // the parents' level: 1 cell (only e = 0) or 2 (no e = -1)
+    const bool four = x.l == 2;
+    const bool same = x.j == x.i;  // only B > A
+    uint32_t pm[DM], p0[DM], pp[DM], dist[DM];
+#pragma unroll
+    for (int k = 0; k < DM; ++k) {
+        if (k >= d) break;
+        const uint32_t mask = dim_mask(d, k, lev), unit = 1u << (d - 1 - k);
+        pm[k] = dil_add(PA, mask, unit, -1);
+        p0[k] = PA & mask;
+        pp[k] = dil_add(PA, mask, unit, 1);
+        dist[k] = child_dists((x.A >> (d - 1 - k)) & 1u, four);
+    }
+    auto offs_at = [&](uint32_t cell) {
+        return cfg.offs[x.baseB + (uint32_t)((uint64_t)cell << x.sB)];
+    };
+    const int kl = d - 1;  // the dimension whose digit varies within a group
+#pragma unroll(DIM == 1 || DIM == 2 ? NG : 1)
+    for (uint32_t gi = 0; gi < ng; ++gi) {
         int ek[DM];
-        uint32_t q = eidx, P = 0;
-        bool ok = true;
+        uint32_t q = gi, Pg = 0;
+        bool okg = true, anyg = false;
 #pragma unroll
         for (int k = DM - 1; k >= 0; --k) {
-            if (k >= d) {
-                ek[k] = 0;
-                continue;
-            }
+            ek[k] = 0;
+            if (k >= kl) continue;
             ek[k] = (int)(q % 3u) - 1;
             q /= 3u;
-            ok = ok && digit_ok(ek[k], x.l - 1);
-            P |= dil_add(PA, dim_mask(d, k, x.l - 1), 1u << (d - 1 - k), ek[k]);
+            okg = okg && digit_ok(ek[k], lev);
+            anyg = anyg || ek[k] != 0;  // the own parent has only neighbour children
+            Pg |= ek[k] < 0 ? pm[k] : ek[k] > 0 ? pp[k] : p0[k];
         }
-        if (!ok) continue;
-        bool any = false;  // a distant child of this parent neighbour that counts
+        if (!okg) continue;
+        uint32_t first[3], lo0[3], end[3];
+        bool use[3];
 #pragma unroll
-        for (int k = 0; k < DM; ++k)
-            if (k < d && ek[k] != 0) any = true;  // the own parent has only neighbour kids
-        if (!any) continue;
-        const uint32_t first = P << d;
-        uint32_t lo = cfg.offs[x.baseB + (uint32_t)((uint64_t)first << x.sB)];
-        const uint32_t end = cfg.offs[x.baseB + (uint32_t)((uint64_t)(first + nk) << x.sB)];
-        if (lo == end) continue;  // no vertex of bucket j under this parent neighbour
-        for (uint32_t kids = 0; kids < nk; ++kids) {
-            const uint32_t hi =
-                kids + 1 < nk ? cfg.offs[x.baseB + (uint32_t)((uint64_t)(first + kids + 1) << x.sB)]
-                              : end;
-            int linf = 0;
-#pragma unroll
-            for (int k = 0; k < DM; ++k) {
-                if (k >= d) continue;
-                const int kid = (int)((kids >> (d - 1 - k)) & 1u);
-                int diff = 2 * ek[k] + kid - alpha[k];
-                diff = diff < 0 ? -diff : diff;
-                if (x.l == 2 && diff > 2) diff = 4 - diff;  // 4 cells per dimension
-                linf = diff > linf ? diff : linf;
+        for (int t = 0; t < 3; ++t) {
+            const int e = t - 1;
+            first[t] = (Pg | (e < 0 ? pm[kl] : e > 0 ? pp[kl] : p0[kl])) << d;
+            use[t] = digit_ok(e, lev) && (anyg || e != 0) && !(same && first[t] < x.A);
+            lo0[t] = 0;
+            end[t] = 0;
+            if (use[t]) {
+                lo0[t] = offs_at(first[t]);
+                end[t] = offs_at(first[t] + nk);
             }
-            const uint32_t B = first | kids;
-            if (linf > 1 && !(x.j == x.i && B <= x.A)) f(B, (uint32_t)(linf - 1), lo, hi - lo);
-            lo = hi;
+        }
+        uint32_t mid[3][NKB];
+        if constexpr (kBatch) {
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                if (use[t] && lo0[t] != end[t]) {
+#pragma unroll
+                    for (int c = 0; c < NKB; ++c) mid[t][c] = offs_at(first[t] + (uint32_t)c + 1u);
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            if (!use[t] || lo0[t] == end[t]) continue;  // no vertex of bucket j here
+            ek[kl] = t - 1;
+            if constexpr (kMasks) {
+                uint32_t far = 0, far3 = 0;  // children at distance >= 2 (>= 3) in some dimension
+#pragma unroll
+                for (int k = 0; k < DM; ++k) {
+                    const uint32_t s = 6u * (uint32_t)(ek[k] + 1);
+                    const uint32_t d0 = (dist[k] >> s) & 7u, d1 = (dist[k] >> (s + 3u)) & 7u;
+                    const uint32_t m1 = kids_with_bit(d, k), m0 = ~m1 & ((1u << nk) - 1u);
+                    far |= (d0 >= 2u ? m0 : 0u) | (d1 >= 2u ? m1 : 0u);
+                    far3 |= (d0 >= 3u ? m0 : 0u) | (d1 >= 3u ? m1 : 0u);
+                }
+                uint32_t lo = lo0[t];
+#pragma unroll
+                for (uint32_t kid = 0; kid < (1u << DM); ++kid) {
+                    uint32_t hi;
+                    if constexpr (kBatch)
+                        hi = kid + 1 < nk ? mid[t][kid < (uint32_t)NKB ? kid : 0] : end[t];
+                    else
+                        hi = kid + 1 < nk ? offs_at(first[t] + kid + 1) : end[t];
+                    const uint32_t g = ((far >> kid) & 1u) + ((far3 >> kid) & 1u);
+                    if (g && hi > lo) f(first[t] | kid, g, lo, hi - lo);
+                    lo = hi;
+                }
+            } else {
+                // d > 4: one child at a time
+                uint32_t lo = lo0[t];
+                for (uint32_t kid = 0; kid < nk; ++kid) {
+                    const uint32_t hi = kid + 1 < nk ? offs_at(first[t] + kid + 1) : end[t];
+                    uint32_t linf = 0;
+#pragma unroll
+                    for (int k = 0; k < DM; ++k) {
+                        if (k >= d) break;
+                        const uint32_t pos =
+                            2u * (uint32_t)(ek[k] + 1) + ((kid >> (d - 1 - k)) & 1u);
+                        const uint32_t dk = (dist[k] >> (3u * pos)) & 7u;
+                        linf = dk > linf ? dk : linf;
+                    }
+                    if (linf > 1 && hi > lo) f(first[t] | kid, linf - 1, lo, hi - lo);
+                    lo = hi;
+                }
+            }
         }
     }
 }
 
 // Type-II entries (thread per (row, bucket j)): the per-gap totals of the partner
 // sets, draw 0 of each single-chunk stream (most streams end there), and for the
-// remaining streams a descriptor plus their partner segments in rank order.
+// remaining streams a descriptor plus their partner segments in rank order.  A
+// partner set whose sorted positions continue those of the previous set of the
+// same gap extends its segment (the index-to-vertex map is the same), so the
+// children of a parent neighbour that share a gap usually form one segment.
 template <int DIM>
-__global__ void __launch_bounds__(kEnumThreads) k_enum2(DevCfg cfg) {
+__global__ void __launch_bounds__(kEnumThreads, 4) k_enum2(DevCfg cfg) {
     const int lane = threadIdx.x & 31;
     const int d = DIM ? DIM : cfg.d;
     Counters C;
@@ -459,15 +552,23 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum2(DevCfg cfg) {
         const unsigned int q = b0 + threadIdx.x;
         const bool active = q < count;
         EntryCtx x;
-        uint32_t cnt[2] = {0u, 0u}, sum[2] = {0u, 0u}, keep[2] = {0u, 0u}, s0[2], tidx[2];
-        uint32_t pack[2] = {0u, 0u};
+        // per gap: partner cells, segments, total size, end of the last segment
+        uint32_t cnt[2] = {0u, 0u}, nseg[2] = {0u, 0u}, sum[2] = {0u, 0u}, keep[2] = {0u, 0u};
+        uint32_t s0[2], tidx[2], pack[2] = {0u, 0u};
         if (active) {
             x = decode_entry<DIM>(cfg, cfg.ent2[q], d, false);
-            for_partners<DIM>(cfg, x, d, [&](uint32_t, uint32_t g, uint32_t, uint32_t len) {
-                if (len) {
-                    cnt[g - 1] += 1u;
-                    sum[g - 1] += len;
-                }
+            uint32_t nxt[2] = {0xffffffffu, 0xffffffffu};
+            auto add = [&](int gi, uint32_t lo, uint32_t len) {
+                cnt[gi] += 1u;
+                nseg[gi] += lo != nxt[gi] ? 1u : 0u;
+                sum[gi] += len;
+                nxt[gi] = lo + len;
+            };
+            for_partners<DIM>(cfg, x, d, [&](uint32_t, uint32_t g, uint32_t lo, uint32_t len) {
+                if (g == 1)
+                    add(0, lo, len);
+                else
+                    add(1, lo, len);
             });
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
@@ -493,7 +594,7 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum2(DevCfg cfg) {
         }
         // one atomic per warp for the streams and one for their segments
         const uint32_t nst = keep[0] + keep[1];
-        const uint32_t nsg = (keep[0] ? cnt[0] : 0u) + (keep[1] ? cnt[1] : 0u);
+        const uint32_t nsg = (keep[0] ? nseg[0] : 0u) + (keep[1] ? nseg[1] : 0u);
         uint32_t ist = nst, isg = nsg;
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t a = __shfl_up_sync(0xffffffffu, ist, o);
@@ -512,9 +613,9 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum2(DevCfg cfg) {
         sg_base = __shfl_sync(0xffffffffu, sg_base, 31) + isg - nsg;
         if (nst) {
             unsigned long long off[2];
-            uint32_t pos[2] = {0u, 0u}, pre[2] = {0u, 0u};
+            uint32_t pos[2] = {0u, 0u}, pre[2] = {0u, 0u}, nxt[2] = {0xffffffffu, 0xffffffffu};
             off[0] = sg_base;
-            off[1] = sg_base + (keep[0] ? cnt[0] : 0u);
+            off[1] = sg_base + (keep[0] ? nseg[0] : 0u);
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
                 if (!keep[g]) continue;
@@ -534,7 +635,7 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum2(DevCfg cfg) {
                     st.a_begin = x.a_lo;
                     st.a_len = x.a_len;
                     st.seg_off = (uint32_t)off[g];  // < seg_cap <= 2^32 when kept
-                    st.seg_cnt = cnt[g];
+                    st.seg_cnt = nseg[g];
                     st.S = sum[g];
                     st.tii = tidx[g];
                     st.s0 = s0[g];
@@ -543,13 +644,21 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum2(DevCfg cfg) {
                 }
                 ++st_base;
             }
+            auto put = [&](int gi, uint32_t lo, uint32_t len) {
+                if (!keep[gi]) return;
+                if (lo != nxt[gi]) {
+                    const unsigned long long at = off[gi] + pos[gi];
+                    if (at < cfg.seg_cap) cfg.segs[at] = Seg{lo, pre[gi]};
+                    pos[gi] += 1u;
+                }
+                pre[gi] += len;
+                nxt[gi] = lo + len;
+            };
             for_partners<DIM>(cfg, x, d, [&](uint32_t, uint32_t g, uint32_t lo, uint32_t len) {
-                if (!keep[g - 1]) return;
-                if (!len) return;
-                const unsigned long long at = off[g - 1] + pos[g - 1];
-                if (at < cfg.seg_cap) cfg.segs[at] = Seg{lo, pre[g - 1]};
-                pos[g - 1] += 1u;
-                pre[g - 1] += len;
+                if (g == 1)
+                    put(0, lo, len);
+                else
+                    put(1, lo, len);
             });
         }
     }
@@ -691,6 +800,17 @@ __device__ __forceinline__ int warp_last_le(unsigned long long v, unsigned long 
     return j;
 }
 
+// The same for 32-bit signed values.
+__device__ __forceinline__ int warp_last_le32(int v, int f) {
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int x = __shfl_sync(0xffffffffu, v, j + step);
+        if (x <= f) j += step;
+    }
+    return j;
+}
+
 // ------------------------------------------------------------------ type I
 // Every pair of every type-I item (Algorithm 1: "emit each edge with p_uv").  The
 // pairs of all items form one index space through the exclusive prefix t1_pre;
@@ -721,29 +841,31 @@ __global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
         if (lane == 0) F0 = atomicAdd(&cfg.work64[0], (unsigned long long)kT1Grab);
         F0 = __shfl_sync(0xffffffffu, F0, 0);
         if (F0 >= total) break;
-        const unsigned long long F1 = F0 + kT1Grab < total ? F0 + kT1Grab : total;
+        // pair indices relative to F0: an item holds at most kSplitAB pairs, so the
+        // 32 items of a window lie within (-2^13, 2^18) of F0
+        const int F1 = (int)(total - F0 < kT1Grab ? total - F0 : kT1Grab);
         uint32_t k = warp_search(pre, nit, F0), wk = 0xffffffffu;
-        unsigned long long wpre = 0, wend = 0;
+        int wpre = 0, wend = 0;
         T1Item wit{0u, 0u, 0u, 0u};
-        for (unsigned long long f0 = F0; f0 < F1;) {
+        for (int f0 = 0; f0 < F1;) {
             if (k != wk) {  // window: items k .. k + 31 with their first and end pairs
                 const uint32_t q = k + (uint32_t)lane;
-                wpre = q <= nit ? pre[q] : ~0ull;
-                wend = q < nit ? pre[q + 1] : ~0ull;
+                wpre = q <= nit ? (int)(long long)(pre[q] - F0) : 0x7fffffff;
+                wend = q < nit ? (int)(long long)(pre[q + 1] - F0) : 0x7fffffff;
                 if (q < nit) wit = cfg.t1[q];
                 wk = k;
             }
             // the round: pairs [f0, fe), at most 32 and inside the window
-            const unsigned long long wlast = __shfl_sync(0xffffffffu, wend, 31);
-            unsigned long long fe = f0 + 32;
+            const int wlast = __shfl_sync(0xffffffffu, wend, 31);
+            int fe = f0 + 32;
             if (fe > wlast) fe = wlast;
             if (fe > F1) fe = F1;
-            const unsigned long long f = f0 + (unsigned long long)lane;
-            const int j = warp_last_le(wpre, f);
+            const int f = f0 + lane;
+            const int j = warp_last_le32(wpre, f);
             const uint32_t a_begin = __shfl_sync(0xffffffffu, wit.a_begin, j);
             const uint32_t b_begin = __shfl_sync(0xffffffffu, wit.b_begin, j);
             const uint32_t b_len = __shfl_sync(0xffffffffu, wit.b_len, j);
-            const unsigned long long pj = __shfl_sync(0xffffffffu, wpre, j);
+            const int pj = __shfl_sync(0xffffffffu, wpre, j);
             bool edge = false;
             uint32_t pu = 0, pv = 0;
             if (f < fe) {
