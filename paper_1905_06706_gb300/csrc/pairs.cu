@@ -262,15 +262,24 @@ __global__ void k_rows(DevCfg cfg) {
             prev = first ? 0u : cfg.skey[p - 1] - base;
             top = cfg.CLd[i];
         }
+        // p heads its cell on level l iff the cells of p - 1 and p differ there, i.e. for
+        // every l >= l0 with l0 from the highest differing bit of the two keys (a key of
+        // bucket i has d I(i) bits, level l keeps the top d l of them)
+        int l0 = top + 1;
+        if (p < n) {
+            const uint32_t diff = cell ^ prev;
+            if (first)
+                l0 = 0;
+            else if (diff)
+                l0 = cfg.I[i] - (31 - __clz(diff)) / cfg.d;
+            if (l0 < 0) l0 = 0;
+        }
         uint32_t heads = 0, m2 = 0, m1 = 0;
-        for (int l = 0; l <= top; ++l) {
-            const int s = cfg.d * (cfg.I[i] - l);
-            if (first || ((uint64_t)cell >> s) != ((uint64_t)prev >> s)) {
-                const RowClass rc = cfg.classes[(uint32_t)i * (kMaxLevel + 1) + l];
-                ++heads;
-                m2 += rc.n2;
-                m1 += rc.n1;
-            }
+        for (int l = l0; l <= top; ++l) {
+            const RowClass rc = cfg.classes[(uint32_t)i * (kMaxLevel + 1) + l];
+            ++heads;
+            m2 += rc.n2;
+            m1 += rc.n1;
         }
         uint32_t ih = heads, i2 = m2, i1 = m1;
         for (int o = 1; o < 32; o <<= 1) {
@@ -291,15 +300,12 @@ __global__ void k_rows(DevCfg cfg) {
         }
         b2 = __shfl_sync(0xffffffffu, b2, 31) + i2 - m2;
         b1 = __shfl_sync(0xffffffffu, b1, 31) + i1 - m1;
-        for (int l = 0; l <= top; ++l) {
-            const int s = cfg.d * (cfg.I[i] - l);
-            if (first || ((uint64_t)cell >> s) != ((uint64_t)prev >> s)) {
-                const RowClass rc = cfg.classes[(uint32_t)i * (kMaxLevel + 1) + l];
-                for (uint32_t e = 0; e < rc.n2; ++e, ++b2)
-                    if (b2 < cfg.ent2_cap) cfg.ent2[b2] = pack_entry((uint32_t)p, l, i, e);
-                for (uint32_t e = 0; e < rc.n1; ++e, ++b1)
-                    if (b1 < cfg.ent1_cap) cfg.ent1[b1] = pack_entry((uint32_t)p, l, i, e);
-            }
+        for (int l = l0; l <= top; ++l) {
+            const RowClass rc = cfg.classes[(uint32_t)i * (kMaxLevel + 1) + l];
+            for (uint32_t e = 0; e < rc.n2; ++e, ++b2)
+                if (b2 < cfg.ent2_cap) cfg.ent2[b2] = pack_entry((uint32_t)p, l, i, e);
+            for (uint32_t e = 0; e < rc.n1; ++e, ++b1)
+                if (b1 < cfg.ent1_cap) cfg.ent1[b1] = pack_entry((uint32_t)p, l, i, e);
         }
     }
 }
@@ -667,6 +673,61 @@ __global__ void __launch_bounds__(kEnumThreads, 4) k_enum2(DevCfg cfg) {
     flush_counters(cfg, C);
 }
 
+// Visit the neighbour cells B of A on level l (B >= A when j = i) that hold a
+// vertex of bucket j: f(B, lo, len) with the range of sorted positions (len > 0),
+// in the order of the offset index (digits e_k + 1, dimension 0 most significant).
+// The neighbours go in groups of three that differ in the last digit only; the
+// offsets of a group are loaded together.
+template <int DIM, class F>
+__device__ __forceinline__ void for_neighbours(const DevCfg& cfg, const EntryCtx& x, int d, F f) {
+    constexpr int DM = DIM ? DIM : kMaxDim;
+    constexpr uint32_t NG = DIM == 1 ? 1u : DIM == 2 ? 3u : DIM == 3 ? 9u : DIM == 4 ? 27u : 0u;
+    uint32_t ng = NG;
+    if (DIM == 0) {
+        ng = 1;
+        for (int k = 1; k < d; ++k) ng *= 3u;
+    }
+    const bool same = x.j == x.i;
+    uint32_t am[DM], a0[DM], ap[DM];
+#pragma unroll
+    for (int k = 0; k < DM; ++k) {
+        if (k >= d) break;
+        const uint32_t mask = dim_mask(d, k, x.l), unit = 1u << (d - 1 - k);
+        am[k] = dil_add(x.A, mask, unit, -1);
+        a0[k] = x.A & mask;
+        ap[k] = dil_add(x.A, mask, unit, 1);
+    }
+    const int kl = d - 1;
+#pragma unroll(DIM == 1 || DIM == 2 ? NG : 1)
+    for (uint32_t gi = 0; gi < ng; ++gi) {
+        uint32_t q = gi, Bg = 0;
+        bool okg = true;
+#pragma unroll
+        for (int k = DM - 1; k >= 0; --k) {
+            if (k >= kl) continue;
+            const int e = (int)(q % 3u) - 1;
+            q /= 3u;
+            okg = okg && digit_ok(e, x.l);
+            Bg |= e < 0 ? am[k] : e > 0 ? ap[k] : a0[k];
+        }
+        if (!okg) continue;
+        uint32_t B[3], lo[3], len[3];
+        bool use[3];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int e = t - 1;
+            B[t] = Bg | (e < 0 ? am[kl] : e > 0 ? ap[kl] : a0[kl]);
+            use[t] = digit_ok(e, x.l) && !(same && B[t] < x.A);
+            lo[t] = 0;
+            len[t] = 0;
+            if (use[t]) range_of(cfg, x, B[t], &lo[t], &len[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+            if (use[t] && len[t]) f(B[t], lo[t], len[t]);
+    }
+}
+
 // Type-I entries (thread per (row, bucket j)): every non-empty neighbour cell B
 // of A (B >= A when j = i) gives an item V_i^A x V_j^B, split into sub-items of at
 // most kSplitAB pairs.
@@ -674,12 +735,6 @@ template <int DIM>
 __global__ void __launch_bounds__(kEnumThreads) k_enum1(DevCfg cfg) {
     const int lane = threadIdx.x & 31;
     const int d = DIM ? DIM : cfg.d;
-    constexpr int DM = DIM ? DIM : kMaxDim;
-    uint32_t n3 = DIM == 1 ? 3u : DIM == 2 ? 9u : DIM == 3 ? 27u : DIM == 4 ? 81u : 0u;
-    if (DIM == 0) {
-        n3 = 1;
-        for (int k = 0; k < d; ++k) n3 *= 3u;
-    }
     unsigned long long t1_items_local = 0, t1_refs_local = 0;
     unsigned int count = *cfg.ent1_count < cfg.ent1_cap ? *cfg.ent1_count : cfg.ent1_cap;
     if (count > cfg.ent1_hi) count = cfg.ent1_hi;
@@ -689,21 +744,6 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum1(DevCfg cfg) {
         const bool active = q < count;
         EntryCtx x;
         if (active) x = decode_entry<DIM>(cfg, cfg.ent1[q], d, true);
-        // neighbour cell of offset index c (digits of dimension 0 most significant)
-        auto neighbour = [&](uint32_t c, uint32_t* B) {
-            uint32_t qq = c, Bv = 0;
-            bool ok = true;
-#pragma unroll
-            for (int k = DM - 1; k >= 0; --k) {
-                if (k >= d) continue;
-                const int ek = (int)(qq % 3u) - 1;
-                qq /= 3u;
-                ok = ok && digit_ok(ek, x.l);
-                Bv |= dil_add(x.A, dim_mask(d, k, x.l), 1u << (d - 1 - k), ek);
-            }
-            *B = Bv;
-            return ok && !(x.j == x.i && Bv < x.A);
-        };
         auto split = [&](uint32_t b_len, uint32_t* ac, uint32_t* bc, uint32_t* na) {
             *bc = b_len < kSplitB ? b_len : kSplitB;
             *ac = kSplitAB / *bc;
@@ -713,12 +753,10 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum1(DevCfg cfg) {
         };
         uint32_t nsub = 0;
         if (active) {
-            for (uint32_t c = 0; c < n3; ++c) {
-                uint32_t B, lo, len, ac, bc, na;
-                if (!neighbour(c, &B)) continue;
-                range_of(cfg, x, B, &lo, &len);
-                if (len) nsub += split(len, &ac, &bc, &na);
-            }
+            for_neighbours<DIM>(cfg, x, d, [&](uint32_t, uint32_t, uint32_t len) {
+                uint32_t ac, bc, na;
+                nsub += split(len, &ac, &bc, &na);
+            });
         }
         uint32_t incl = nsub;
         for (int o = 1; o < 32; o <<= 1) {
@@ -729,11 +767,8 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum1(DevCfg cfg) {
         if (lane == 31 && incl) tbase = atomicAdd(cfg.t1_count, (unsigned long long)incl);
         tbase = __shfl_sync(0xffffffffu, tbase, 31) + incl - nsub;
         if (nsub) {
-            for (uint32_t c = 0; c < n3; ++c) {
-                uint32_t B, lo, len, ac, bc, na;
-                if (!neighbour(c, &B)) continue;
-                range_of(cfg, x, B, &lo, &len);
-                if (!len) continue;
+            for_neighbours<DIM>(cfg, x, d, [&](uint32_t B, uint32_t lo, uint32_t len) {
+                uint32_t ac, bc, na;
                 split(len, &ac, &bc, &na);
                 const uint32_t tri = (B == x.A && x.j == x.i) ? 0x80000000u : 0u;
                 for (uint32_t ya = 0; ya < x.a_len; ya += ac) {
@@ -753,7 +788,7 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum1(DevCfg cfg) {
                 // every a-chunk meets every b-chunk: sum of side lengths over sub-items
                 t1_refs_local += (unsigned long long)x.a_len * ((len + bc - 1) / bc) +
                                  (unsigned long long)len * na;
-            }
+            });
             t1_items_local += nsub;
         }
     }
@@ -1021,7 +1056,20 @@ __global__ void __launch_bounds__(kT2Threads, 4) k_type2(DevCfg cfg) {
                 ++C.cands;
                 const unsigned long long idx = start + (unsigned long long)s;
                 uint32_t ia, ib;
-                if (small) {
+                if (idx < (1ull << 24)) {
+                    // idx / S from a float reciprocal (exact to one unit below 2^24)
+                    const uint32_t ix = (uint32_t)idx;
+                    ia = __float2uint_rz(__uint2float_rn(ix) * __frcp_rn((float)st.S));
+                    int r = (int)ix - (int)(ia * st.S);
+                    if (r < 0) {
+                        --ia;
+                        r += (int)st.S;
+                    } else if (r >= (int)st.S) {
+                        ++ia;
+                        r -= (int)st.S;
+                    }
+                    ib = (uint32_t)r;
+                } else if (small) {
                     ia = (uint32_t)idx / st.S;
                     ib = (uint32_t)idx - ia * st.S;
                 } else {
