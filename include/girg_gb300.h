@@ -207,7 +207,8 @@ int64_t girg_expected_edges(const girg_params* params, void* stream);
  * checksum: the sum mod 2^64 over the edges (u < v) of the splitmix64 finalizer of
  * u 2^32 + v (as an int64 bit pattern; independent of the edge order), [15] type-II
  * partner segments, [16] enumeration passes (rounds plus reruns after a work list
- * grew).  Copies min(len, 17) values; returns the number copied. */
+ * grew), [17] type-II work entries and [18] type-I work entries (rows times the
+ * buckets they pair with).  Copies min(len, 19) values; returns the number copied. */
 int girg_last_stats(int64_t* out, int32_t len);
 
 /* Milliseconds spent in each phase of the last call on this host thread

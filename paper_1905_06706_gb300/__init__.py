@@ -27,7 +27,8 @@ PRECISION_FP64 = 1
 STAT_NAMES = ("type1_pairs", "coins", "rechecks", "type2_items", "jump_draws",
               "type2_candidates", "rows", "type1_items", "type2_chunks", "edges",
               "kernel_launches", "type1_vertex_refs", "type1_edges", "type2_streams",
-              "edge_checksum", "type2_segments", "enum_passes")
+              "edge_checksum", "type2_segments", "enum_passes", "type2_entries",
+              "type1_entries")
 PHASE_NAMES = ("points_reduce", "tables", "sort", "enumerate", "type1", "type2",
                "total", "host_reduce_readback", "host_c_search", "host_tables")
 

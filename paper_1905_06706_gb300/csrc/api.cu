@@ -499,7 +499,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     constexpr uint64_t kMaxT1 = 1ull << 30, kMaxStreams = 1ull << 28, kMaxSegs = 1ull << 31;
     uint32_t lo2 = 0, lo1 = 0, hi2 = 0xffffffffu, hi1 = 0xffffffffu;
     unsigned long long est_acc[kNumStats] = {0};
-    uint64_t total_streams = 0, total_segs = 0, passes = 0;
+    uint64_t total_streams = 0, total_segs = 0, passes = 0, n_ent2 = 0, n_ent1 = 0;
     unsigned long long *t1_pre = nullptr, *chunk_pre = nullptr, *tmp = nullptr;
     size_t pre_cap1 = 0, pre_cap2 = 0, tmp_cap = 0;
     int round = 0;
@@ -524,6 +524,8 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
         const uint32_t e2 = std::min<uint32_t>(ec[0], cfg.ent2_cap);
         const uint32_t e1 = std::min<uint32_t>(ec[1], cfg.ent1_cap);
         const uint32_t end2 = std::min(hi2, e2), end1 = std::min(hi1, e1);
+        n_ent2 = ec[0];
+        n_ent1 = ec[1];
         if (wc[0] > cfg.t1_cap || wc[1] > cfg.stream_cap || wc[2] > cfg.seg_cap) {
             double f = 1.0;
             if (wc[0] > kMaxT1) f = std::min(f, 0.8 * (double)kMaxT1 / (double)wc[0]);
@@ -605,6 +607,8 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     hs[kStatStreams] = total_streams;
     hs[kStatSegs] = total_segs;
     hs[kStatEnumPasses] = passes;
+    hs[kStatEnt2] = n_ent2;
+    hs[kStatEnt1] = n_ent1;
     for (int q = 0; q < kNumStats; ++q) g_stats[q] = (int64_t)hs[q];
     g_stats[kStatLaunches] = (int64_t)g_launches;
     *num_edges = (int64_t)hs[kNumStats];

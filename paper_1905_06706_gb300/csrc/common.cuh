@@ -256,6 +256,44 @@ GG_HD const DetTab& det_tab() {
 // nearest table point, r = (m - c) 64/j (m - c is exact), |r| <= 1/90; ln(1 + r) by
 // its series to r^9.  ln x = e ln 2 + ln c + ln(1 + r).
 GG_HD double det_log(double x) {
+#ifdef __CUDA_ARCH__
+    {
+        // positive normal x: the same operations, with the classification, the choice
+        // of m and the index j taken from the bits (integer units, not the FP64 pipe);
+        // j = floor(64 m + 1/2) is (f + 2^45) >> 46 above 1 and (f + 2^46) >> 47 below,
+        // f the fraction bits, since 64 m + 1/2 is exact or rounds within its integer
+        const uint64_t b = double_to_bits(x);
+        if (b - 0x0010000000000000ULL < 0x7FE0000000000000ULL) {
+            const uint64_t f = b & 0x000fffffffffffffULL;
+            int e = (int)(b >> 52) - 1023, j;
+            double m, c;
+            if (f > 0x6a09e667f3bcdULL) {  // m > sqrt 2: m / 2 in (sqrt 1/2, 1)
+                m = bits_to_double(f | 0x3fe0000000000000ULL);
+                e = e + 1;
+                j = 32 + (int)((f + (1ULL << 46)) >> 47);
+            } else {
+                m = bits_to_double(f | 0x3ff0000000000000ULL);
+                j = 64 + (int)((f + (1ULL << 45)) >> 46);
+            }
+            c = j < 64 ? bits_to_double(0x3fe0000000000000ULL | ((uint64_t)(j - 32) << 47))
+                       : bits_to_double(0x3ff0000000000000ULL | ((uint64_t)(j - 64) << 46));
+            const DetTab& T = det_tab();
+            const double r = DMUL(DSUB(m, c), T.ic[j - 45]);
+            double t = 1.0 / 9.0;
+            t = DSUB(1.0 / 8.0, DMUL(r, t));
+            t = DSUB(1.0 / 7.0, DMUL(r, t));
+            t = DSUB(1.0 / 6.0, DMUL(r, t));
+            t = DSUB(1.0 / 5.0, DMUL(r, t));
+            t = DSUB(1.0 / 4.0, DMUL(r, t));
+            t = DSUB(1.0 / 3.0, DMUL(r, t));
+            t = DSUB(0.5, DMUL(r, t));
+            t = DSUB(1.0, DMUL(r, t));
+            const double l1 = DMUL(r, t);
+            const double ed = (double)e;
+            return DADD(DMUL(ed, kLn2Hi), DADD(T.lc[j - 45], DADD(l1, DMUL(ed, kLn2Lo))));
+        }
+    }
+#endif
     if (x != x || x < 0.0) return dnan();
     if (x == 0.0) return -dinf();
     if (x == dinf()) return dinf();
@@ -292,6 +330,27 @@ GG_HD double det_log(double x) {
 // e^x = 2^m 2^(j/64) e^r with k = round(64 x / ln 2) = 64 m + j, r = x - k ln2/64
 // (|r| <= ln2/128), e^r by its series to r^7.
 GG_HD double det_exp(double x) {
+#ifdef __CUDA_ARCH__
+    // |x| <= 700 (the integer test covers NaN): the same operations without the range
+    // checks; there m = floor(k / 64) lies in [-1011, 1010], a normal power of two
+    if ((double_to_bits(x) & 0x7fffffffffffffffULL) <= 0x4085e00000000000ULL) {
+        const double kd = floor(DADD(DMUL(x, 0x1.71547652b82fep+6), 0.5));
+        const int k = (int)kd;
+        const double r =
+            DSUB(DSUB(x, DMUL(kd, 0x1.62e42fee00000p-7)), DMUL(kd, 0x1.a39ef35793c76p-39));
+        const int j = k & 63;
+        const int m = (k - j) / 64;
+        double p = 1.0 / 5040.0;
+        p = DADD(1.0 / 720.0, DMUL(r, p));
+        p = DADD(1.0 / 120.0, DMUL(r, p));
+        p = DADD(1.0 / 24.0, DMUL(r, p));
+        p = DADD(1.0 / 6.0, DMUL(r, p));
+        p = DADD(0.5, DMUL(r, p));
+        p = DADD(1.0, DMUL(r, p));
+        p = DADD(1.0, DMUL(r, p));
+        return DMUL(DMUL(det_tab().e2[j], p), pow2i(m));
+    }
+#endif
     if (x != x) return x;
     if (x > 710.0) return dinf();
     if (x < -746.0) return 0.0;

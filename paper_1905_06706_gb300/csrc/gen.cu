@@ -256,40 +256,86 @@ __global__ void k_split_finish(const double* __restrict__ part, int nb, double* 
     }
 }
 
-// Sort the gathered weights in decreasing order (one block, bitonic network in
-// shared memory on the bit patterns, which order positive doubles); count[1] = 1
-// when sorted, 0 when there were more than kTopSortMax.
+// Sort the gathered weights in decreasing order (one block, bitonic network on the
+// bit patterns, which order positive doubles); count[1] = 1 when sorted, 0 when there
+// were more than kTopSortMax.  Thread t holds elements t + 1024 r in registers: a
+// compare-exchange at stride >= 1024 stays in the thread, one below 32 is a warp
+// shuffle, and only strides 32 .. 512 go through shared memory.
+__device__ __forceinline__ unsigned long long bitonic_keep(unsigned long long a, unsigned long long b,
+                                                           unsigned int i, unsigned int size,
+                                                           unsigned int stride) {
+    const bool desc = (i & size) == 0, lower = (i & stride) == 0;
+    return (lower == desc) ? (a > b ? a : b) : (a < b ? a : b);
+}
+
 __global__ void __launch_bounds__(1024) k_sort_top(double* __restrict__ buf,
                                                    unsigned int* __restrict__ count) {
+    constexpr int R = (int)(kTopSortMax / 1024);
+    static_assert(R == 4, "register layout below assumes 4 elements per thread");
     __shared__ unsigned long long s_key[kTopSortMax];
     const unsigned int k = count[0];
     if (k > kTopSortMax) {
         if (threadIdx.x == 0) count[1] = 0u;
         return;
     }
-    unsigned int m = 1;
+    unsigned int m = 32;  // whole warps
     while (m < k) m <<= 1;
-    for (unsigned int i = threadIdx.x; i < m; i += blockDim.x)
-        s_key[i] = i < k ? (unsigned long long)__double_as_longlong(buf[i]) : 0ull;
-    __syncthreads();
+    const unsigned int tid = threadIdx.x;
+    unsigned long long v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const unsigned int i = (unsigned int)r * 1024u + tid;
+        v[r] = i < k ? (unsigned long long)__double_as_longlong(buf[i]) : 0ull;
+    }
     for (unsigned int size = 2; size <= m; size <<= 1) {
         for (unsigned int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (unsigned int i = threadIdx.x; i < m; i += blockDim.x) {
-                const unsigned int j = i ^ stride;
-                if (j > i) {
-                    const bool desc = (i & size) == 0;  // final order: decreasing
-                    const unsigned long long a = s_key[i], b = s_key[j];
-                    if (desc ? (a < b) : (a > b)) {
-                        s_key[i] = b;
-                        s_key[j] = a;
+            if (stride >= 1024) {  // pairs of registers (m >= 2048 here)
+                const unsigned int h = stride >> 10;  // 1 or 2
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int rp = r ^ (int)h;
+                    if (rp < r) continue;
+                    const unsigned int i = (unsigned int)r * 1024u + tid;
+                    if (i >= m) continue;
+                    const unsigned long long a = v[r], b = h == 1 ? v[r ^ 1] : v[r ^ 2];
+                    const unsigned long long hi = a > b ? a : b, lo = a > b ? b : a;
+                    const bool desc = (i & size) == 0;
+                    v[r] = desc ? hi : lo;
+                    if (h == 1)
+                        v[r ^ 1] = desc ? lo : hi;
+                    else
+                        v[r ^ 2] = desc ? lo : hi;
+                }
+            } else if (stride >= 32) {
+                __syncthreads();  // the previous stage's reads are done
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const unsigned int i = (unsigned int)r * 1024u + tid;
+                    if (i < m) s_key[i] = v[r];
+                }
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const unsigned int i = (unsigned int)r * 1024u + tid;
+                    if (i < m) v[r] = bitonic_keep(v[r], s_key[i ^ stride], i, size, stride);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const unsigned int i = (unsigned int)r * 1024u + tid;
+                    if (i < m) {  // whole warps
+                        const unsigned long long p = __shfl_xor_sync(0xffffffffu, v[r], (int)stride);
+                        v[r] = bitonic_keep(v[r], p, i, size, stride);
                     }
                 }
             }
-            __syncthreads();
         }
     }
-    for (unsigned int i = threadIdx.x; i < k; i += blockDim.x)
-        buf[i] = __longlong_as_double((long long)s_key[i]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const unsigned int i = (unsigned int)r * 1024u + tid;
+        if (i < k) buf[i] = __longlong_as_double((long long)v[r]);
+    }
     if (threadIdx.x == 0) count[1] = 1u;
 }
 

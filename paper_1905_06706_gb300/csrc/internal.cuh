@@ -60,7 +60,7 @@ struct Seg {
 enum : int { kStatT1Pairs = 0, kStatCoins, kStatRecheck, kStatT2Items, kStatDraws,
              kStatCands, kStatRows, kStatT1Items, kStatT2Chunks, kStatEdges,
              kStatLaunches, kStatT1VertexRefs, kStatT1Edges, kStatStreams, kStatChecksum,
-             kStatSegs, kStatEnumPasses, kNumStats };
+             kStatSegs, kStatEnumPasses, kStatEnt2, kStatEnt1, kNumStats };
 
 
 struct DevCfg {

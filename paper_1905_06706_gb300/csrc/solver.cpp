@@ -29,7 +29,6 @@ void DegreeModel::set_split(double thr, std::vector<double> top, double sw, doub
     spy_.assign(mi_ ? m + 1 : 0, 0.0);
     spy2_.assign(mi_ ? m + 1 : 0, 0.0);
     for (size_t i = m; i-- > 0;) {  // from the light end
-        lw_[i] = std::log(top_[i]);
         suf_[i] = suf_[i + 1] + top_[i];
         suf2_[i] = suf2_[i + 1] + top_[i] * top_[i];
         if (mi_) {
@@ -41,7 +40,8 @@ void DegreeModel::set_split(double thr, std::vector<double> top, double sw, doub
             spy2_[i] = spy2_[i + 1] + p * p;
             continue;
         }
-        if (tp) {
+        if (tp) {  // logs only off the integer path
+            lw_[i] = std::log(top_[i]);
             b_[i] = lw_[i] / T_;
             const double r = i + 1 < m ? std::exp(b_[i + 1] - b_[i]) : 0.0;  // <= 1
             sr_[i] = 1.0 + r * sr_[i + 1];
