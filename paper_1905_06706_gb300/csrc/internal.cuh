@@ -191,6 +191,7 @@ struct WarpEdges {
     uint32_t* a;      // kEdgeBuf entries
     uint32_t* b;
     unsigned int* n;  // count (shared)
+    unsigned long long mix = 0;  // this lane's share of the checksum of the flushed edges
 };
 
 // Order-independent checksum of an edge set: the sum mod 2^64 of the splitmix64
@@ -226,7 +227,18 @@ __device__ __forceinline__ void push_edge(const DevCfg& cfg, WarpEdges& we, uint
     }
 }
 
-// Whole warp: write out the buffer if it holds at least `threshold` edges.
+// Whole warp, once at the end: add the lanes' checksum shares (one atomic per warp).
+__device__ __forceinline__ void flush_mix(const DevCfg& cfg, WarpEdges& we) {
+    unsigned long long m = we.mix;
+    for (int o = 16; o > 0; o >>= 1) m += __shfl_down_sync(0xffffffffu, m, o);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&cfg.stats[kStatChecksum], m);
+    we.mix = 0;
+}
+
+// Whole warp: write out the buffer if it holds at least `threshold` edges.  The
+// checksum goes to each lane's share (kLaneMix, for kernels that flush often; added by
+// flush_mix at the end) or to one atomic per flush.
+template <bool kLaneMix = false>
 __device__ __forceinline__ void flush_edges(const DevCfg& cfg, WarpEdges& we, unsigned threshold) {
     __syncwarp();
     unsigned int cnt = *we.n;
@@ -241,8 +253,12 @@ __device__ __forceinline__ void flush_edges(const DevCfg& cfg, WarpEdges& we, un
             write_edge(cfg, base + t, we.a[t], we.b[t]);
             mix += edge_mix(we.a[t], we.b[t]);
         }
-        for (int o = 16; o > 0; o >>= 1) mix += __shfl_down_sync(0xffffffffu, mix, o);
-        if (lane == 0) atomicAdd(&cfg.stats[kStatChecksum], mix);
+        if (kLaneMix) {
+            we.mix += mix;
+        } else {
+            for (int o = 16; o > 0; o >>= 1) mix += __shfl_down_sync(0xffffffffu, mix, o);
+            if (lane == 0) atomicAdd(&cfg.stats[kStatChecksum], mix);
+        }
         __syncwarp();
         if (lane == 0) *we.n = 0;
     }

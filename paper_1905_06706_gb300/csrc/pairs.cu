@@ -224,6 +224,47 @@ __device__ __forceinline__ int draw_jump(const DevCfg& cfg, const TwoEntry& e, c
     return r;
 }
 
+// The fast-path fields of a TwoEntry a type-II lane keeps; the FP64 fields are
+// reloaded from the table in the rare fallback paths.
+struct TwoFast {
+    float invLb, log2pbar;
+    uint32_t tii;
+    bool one;
+};
+
+__device__ __forceinline__ int draw_jump_fast(const DevCfg& cfg, const TwoFast& e, const P4& o,
+                                              unsigned long long rem, unsigned long long* X,
+                                              Counters& C) {
+    *X = 0;
+    if (e.one) return rem == 0 ? 0 : 1;
+    int r = 2;
+    if (cfg.precision == 0) r = jump32(o.x, o.y, e.invLb, rem, X);
+    if (r == 2) {
+        if (cfg.precision == 0) ++C.recheck;
+        r = jump64(o.x, o.y, cfg.tii[e.tii].Lb, rem, X);
+    }
+    return r;
+}
+
+template <int DIM>
+__device__ __forceinline__ bool accept_t2_fast(const DevCfg& cfg, const View& V, uint32_t pu,
+                                               uint32_t pv, uint32_t lo, uint32_t hi,
+                                               const TwoFast& e, Counters& C) {
+    if ((DIM == 1 || DIM == 0) && cfg.model == 1) return accept_t2<DIM>(cfg, V, pu, pv, lo, hi, cfg.tii[e.tii], C);
+    const uint32_t D = torus_D<DIM>(cfg.d, V, pu, pv);
+    if (cfg.precision == 1) return t2_exact(cfg, V, pu, pv, D, lo, hi, cfg.tii[e.tii].pbar);
+    if (D == 0) return true;
+    const float ratio = kappa_ratio(V, pu, pv, D);
+    if (ratio >= 1.0f + cfg.band_ratio) return true;
+    if (ratio >= 0x1p-126f) {
+        const float G = cfg.dT * __log2f(ratio) - log2_uniform32(lo, hi) - e.log2pbar;
+        if (G > cfg.bandG) return true;
+        if (G < -cfg.bandG) return false;
+    }  // else subnormal: no relative error bound in single precision
+    ++C.recheck;
+    return t2_exact(cfg, V, pu, pv, D, lo, hi, cfg.tii[e.tii].pbar);
+}
+
 __device__ __forceinline__ void flush_counters(const DevCfg& cfg, const Counters& C) {
     unsigned long long v[6] = {C.t1pairs, C.coins, C.recheck, C.t2items, C.draws, C.cands};
     const int idx[6] = {kStatT1Pairs, kStatCoins, kStatRecheck, kStatT2Items, kStatDraws, kStatCands};
@@ -245,8 +286,47 @@ __device__ __forceinline__ uint64_t pack_entry(uint32_t p, int l, int i, uint32_
     return (uint64_t)p | ((uint64_t)l << 32) | ((uint64_t)i << 38) | ((uint64_t)e << 44);
 }
 
-__global__ void k_rows(DevCfg cfg) {
-    const int lane = threadIdx.x & 31;
+// Block-wide slot allocation: each thread passes its counts x[q]; one atomicAdd per
+// counter and block (a same-address atomic per warp serialises in L2 and dominated
+// the enumeration kernels).  Returns each thread's first slot per counter.  Every
+// thread of a block of kAllocThreads must call it.
+constexpr int kAllocThreads = 256;
+
+template <int NQ, class C>
+__device__ __forceinline__ void block_alloc(const uint32_t (&x)[NQ], C* const (&ctr)[NQ],
+                                            C (&base)[NQ]) {
+    constexpr int NW = kAllocThreads / 32;
+    __shared__ C s_w[NW][NQ];
+    __shared__ C s_b[NQ];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        incl[q] = x[q];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl[q], o);
+            if (lane >= o) incl[q] += t;
+        }
+        if (lane == 31) s_w[warp][q] = (C)incl[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < NQ) {
+        const int q = threadIdx.x;
+        C acc = 0;
+        for (int w = 0; w < NW; ++w) {
+            const C t = s_w[w][q];
+            s_w[w][q] = acc;
+            acc += t;
+        }
+        s_b[q] = acc ? atomicAdd(ctr[q], acc) : (C)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) base[q] = s_b[q] + s_w[warp][q] + (C)(incl[q] - x[q]);
+    __syncthreads();  // s_w and s_b are reused by the next call
+}
+
+__global__ void __launch_bounds__(kAllocThreads) k_rows(DevCfg cfg) {
     const int64_t n = cfg.n;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p0 = blockIdx.x * (int64_t)blockDim.x; p0 < n; p0 += stride) {
@@ -281,25 +361,11 @@ __global__ void k_rows(DevCfg cfg) {
             m2 += rc.n2;
             m1 += rc.n1;
         }
-        uint32_t ih = heads, i2 = m2, i1 = m1;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t a = __shfl_up_sync(0xffffffffu, ih, o);
-            const uint32_t b = __shfl_up_sync(0xffffffffu, i2, o);
-            const uint32_t c = __shfl_up_sync(0xffffffffu, i1, o);
-            if (lane >= o) {
-                ih += a;
-                i2 += b;
-                i1 += c;
-            }
-        }
-        uint32_t b2 = 0, b1 = 0;
-        if (lane == 31) {
-            if (ih) atomicAdd(cfg.row_count, ih);
-            if (i2) b2 = atomicAdd(cfg.ent2_count, i2);
-            if (i1) b1 = atomicAdd(cfg.ent1_count, i1);
-        }
-        b2 = __shfl_sync(0xffffffffu, b2, 31) + i2 - m2;
-        b1 = __shfl_sync(0xffffffffu, b1, 31) + i1 - m1;
+        const uint32_t cnt[3] = {heads, m2, m1};
+        unsigned int* const ctr[3] = {cfg.row_count, cfg.ent2_count, cfg.ent1_count};
+        unsigned int slot[3];
+        block_alloc<3>(cnt, ctr, slot);
+        uint32_t b2 = slot[1], b1 = slot[2];
         for (int l = l0; l <= top; ++l) {
             const RowClass rc = cfg.classes[(uint32_t)i * (kMaxLevel + 1) + l];
             for (uint32_t e = 0; e < rc.n2; ++e, ++b2)
@@ -312,6 +378,7 @@ __global__ void k_rows(DevCfg cfg) {
 
 // ------------------------------------------------------------------ enumeration
 constexpr int kEnumThreads = 256;
+static_assert(kEnumThreads == kAllocThreads, "the enumeration allocates slots per block");
 constexpr int kWarps = kEnumThreads / 32;
 constexpr uint32_t kSplitB = 1024, kSplitAB = 4096;
 
@@ -598,25 +665,14 @@ __global__ void __launch_bounds__(kEnumThreads, 4) k_enum2(DevCfg cfg) {
                 }
             }
         }
-        // one atomic per warp for the streams and one for their segments
+        // one atomic per block for the streams and one for their segments
         const uint32_t nst = keep[0] + keep[1];
         const uint32_t nsg = (keep[0] ? nseg[0] : 0u) + (keep[1] ? nseg[1] : 0u);
-        uint32_t ist = nst, isg = nsg;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t a = __shfl_up_sync(0xffffffffu, ist, o);
-            const uint32_t b = __shfl_up_sync(0xffffffffu, isg, o);
-            if (lane >= o) {
-                ist += a;
-                isg += b;
-            }
-        }
-        unsigned long long st_base = 0, sg_base = 0;
-        if (lane == 31) {
-            if (ist) st_base = atomicAdd(cfg.stream_count, (unsigned long long)ist);
-            if (isg) sg_base = atomicAdd(cfg.seg_count, (unsigned long long)isg);
-        }
-        st_base = __shfl_sync(0xffffffffu, st_base, 31) + ist - nst;
-        sg_base = __shfl_sync(0xffffffffu, sg_base, 31) + isg - nsg;
+        const uint32_t want[2] = {nst, nsg};
+        unsigned long long* const ctr[2] = {cfg.stream_count, cfg.seg_count};
+        unsigned long long slot[2];
+        block_alloc<2>(want, ctr, slot);
+        unsigned long long st_base = slot[0], sg_base = slot[1];
         if (nst) {
             unsigned long long off[2];
             uint32_t pos[2] = {0u, 0u}, pre[2] = {0u, 0u}, nxt[2] = {0xffffffffu, 0xffffffffu};
@@ -758,14 +814,11 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum1(DevCfg cfg) {
                 nsub += split(len, &ac, &bc, &na);
             });
         }
-        uint32_t incl = nsub;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        unsigned long long tbase = 0;
-        if (lane == 31 && incl) tbase = atomicAdd(cfg.t1_count, (unsigned long long)incl);
-        tbase = __shfl_sync(0xffffffffu, tbase, 31) + incl - nsub;
+        const uint32_t want[1] = {nsub};
+        unsigned long long* const ctr[1] = {cfg.t1_count};
+        unsigned long long slot[1];
+        block_alloc<1>(want, ctr, slot);
+        unsigned long long tbase = slot[0];
         if (nsub) {
             for_neighbours<DIM>(cfg, x, d, [&](uint32_t B, uint32_t lo, uint32_t len) {
                 uint32_t ac, bc, na;
@@ -927,13 +980,14 @@ __global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
                 push_edge(cfg, we, V.ids[pu], V.ids[pv]);
                 ++t1_edges;
             }
-            flush_edges(cfg, we, kEdgeBuf - 32);
+            flush_edges<true>(cfg, we, kEdgeBuf - 32);
             // the next round starts in the first item that ends after fe
             f0 = fe;
             k += (uint32_t)__popc(__ballot_sync(0xffffffffu, wend <= fe));
         }
     }
-    flush_edges(cfg, we, 1);
+    flush_edges<true>(cfg, we, 1);
+    flush_mix(cfg, we);
     flush_counters(cfg, C);
     unsigned long long te = t1_edges;
     for (int o = 16; o > 0; o >>= 1) te += __shfl_down_sync(0xffffffffu, te, o);
@@ -976,7 +1030,7 @@ __global__ void __launch_bounds__(kT2Threads, 4) k_type2(DevCfg cfg) {
     // the lane's chunk
     bool live = false, resumed = false;
     Stream st{};
-    TwoEntry e{};
+    TwoFast e{};
     uint32_t h = 0, t = 0;
     long long s = -1;
     unsigned long long start = 0, len = 0;
@@ -1015,12 +1069,13 @@ __global__ void __launch_bounds__(kT2Threads, 4) k_type2(DevCfg cfg) {
                 const uint32_t hh = __shfl_sync(0xffffffffu, bh, src);
                 if (((idle >> lane) & 1u) && r < take) {
                     st = cfg.streams[q];
-                    e = cfg.tii[st.tii];
+                    const TwoEntry te = cfg.tii[st.tii];
+                    e = TwoFast{te.invLb, te.log2pbar, st.tii, te.one != 0};
                     const unsigned long long tot = (unsigned long long)st.a_len * st.S;
                     small = tot <= 0xffffffffull;
                     h = hh;
-                    start = (unsigned long long)h << e.k;
-                    len = tot - start < (1ull << e.k) ? tot - start : (1ull << e.k);
+                    start = (unsigned long long)h << te.k;
+                    len = tot - start < (1ull << te.k) ? tot - start : (1ull << te.k);
                     t = 0;
                     s = -1;
                     resumed = st.s0 != 0xffffffffu;
@@ -1044,7 +1099,7 @@ __global__ void __launch_bounds__(kT2Threads, 4) k_type2(DevCfg cfg) {
             } else {
                 ++C.draws;
                 unsigned long long X;
-                if (draw_jump(cfg, e, o, len - (unsigned long long)(s + 1), &X, C) == 0) {
+                if (draw_jump_fast(cfg, e, o, len - (unsigned long long)(s + 1), &X, C) == 0) {
                     live = false;
                     cand = false;
                 } else {
@@ -1084,7 +1139,7 @@ __global__ void __launch_bounds__(kT2Threads, 4) k_type2(DevCfg cfg) {
                 const Seg sg = cfg.segs[st.seg_off + lo];
                 pu = st.a_begin + ia;
                 pv = sg.b_begin + (ib - sg.pre);
-                edge = accept_t2<DIM>(cfg, V, pu, pv, o.z, o.w, e, C);
+                edge = accept_t2_fast<DIM>(cfg, V, pu, pv, o.z, o.w, e, C);
             }
         }
         if (edge) push_edge(cfg, we, vid(V, pu), vid(V, pv));
@@ -1132,11 +1187,11 @@ bool det_tables_pairs() { return det_tables_ready(); }
 
 // ------------------------------------------------------------------ launchers
 void launch_rows(const DevCfg& cfg, cudaStream_t st) {
-    int64_t b = (cfg.n + 255) / 256;
+    int64_t b = (cfg.n + kAllocThreads - 1) / kAllocThreads;
     if (b > 152 * 16) b = 152 * 16;
     if (b < 1) b = 1;
     ++g_launches;
-    k_rows<<<(unsigned)b, 256, 0, st>>>(cfg);
+    k_rows<<<(unsigned)b, kAllocThreads, 0, st>>>(cfg);
 }
 
 void launch_enumerate(const DevCfg& cfg, cudaStream_t st) {
