@@ -11,6 +11,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -398,13 +399,24 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     CK(cudaMemsetAsync(stats, 0, (kNumStats + 3) * sizeof(unsigned long long), st));
     // work lists, sized from typical counts per vertex; the enumeration only writes
     // work (no edges), so an overflow is repaired by resizing and running it again
-    auto clamp_cap = [](uint64_t c, uint64_t mx) { return c > mx ? mx : c; };
+    // GIRG_INITIAL_LIST_SCALE in (0, 1] shrinks the initial sizes (tests use it to
+    // drive the overflow, growth and rerun paths at small n)
+    double list_scale = 1.0;
+    if (const char* env = std::getenv("GIRG_INITIAL_LIST_SCALE")) {
+        const double v = std::atof(env);
+        if (v > 0.0 && v <= 1.0) list_scale = v;
+    }
+    auto clamp_cap = [list_scale](uint64_t c, uint64_t mx) {
+        c = (uint64_t)((double)c * list_scale);
+        c = c < 16 ? 16 : c;
+        return c > mx ? mx : c;
+    };
     uint64_t t1_cap = clamp_cap((uint64_t)n * (1 + (uint64_t)(0.75 * n3)) + 65536, 1ull << 30);
     uint64_t stream_cap =
         tzero ? 1024 : clamp_cap((uint64_t)n * (2 + 2 * (uint64_t)d) + 65536, 1ull << 28);
-    // partner segments per vertex measured at n = 10^6, beta = 2.2, T = 0.7: about 4.4,
-    // 26, 136 and 656 for d = 1..4 (they grow like 6^d); sized with headroom
-    const uint64_t seg_per_v = d == 1 ? 8 : d == 2 ? 40 : d == 3 ? 224 : d == 4 ? 1024 : 4 * (uint64_t)n6;
+    // partner segments per vertex measured at n = 10^6, beta = 2.2, T = 0.7: about 4.3,
+    // 19, 81 and 325 for d = 1..4 (they grow like 6^d); sized with headroom
+    const uint64_t seg_per_v = d == 1 ? 8 : d == 2 ? 28 : d == 3 ? 112 : d == 4 ? 448 : 4 * (uint64_t)n6;
     uint64_t seg_cap = tzero ? 1024 : clamp_cap((uint64_t)n * seg_per_v + 65536, 1ull << 31);
     T1Item* t1 = S.get<T1Item>(t1_cap);
     uint32_t* t1_pairs = S.get<uint32_t>(t1_cap + 1);
@@ -503,7 +515,71 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     unsigned long long *t1_pre = nullptr, *chunk_pre = nullptr, *tmp = nullptr;
     size_t pre_cap1 = 0, pre_cap2 = 0, tmp_cap = 0;
     int round = 0;
-    for (int attempt = 0;; ++attempt) {
+    unsigned long long hs[kNumStats + 1];
+    unsigned int rc[6];
+    // The first round runs without a host round trip: the scans take the list
+    // lengths from the device and the counts are checked afterwards, read back with
+    // the statistics.  If a list overflowed, the round is undone (statistics and
+    // edge count restored from a copy; the edges it wrote are overwritten later) and
+    // the rounds below take over.
+    bool done = false;
+    {
+        cfg.ent2_lo = 0;
+        cfg.ent2_hi = 0xffffffffu;
+        cfg.ent1_lo = 0;
+        cfg.ent1_hi = 0xffffffffu;
+        CK(cudaMemsetAsync(wcount, 0, 3 * sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(estats, 0, kNumStats * sizeof(unsigned long long), st));
+        DevCfg ecfg = cfg;
+        ecfg.stats = estats;
+        launch_enumerate(ecfg, st);
+        ++passes;
+        tm.mark();  // enumeration done
+        pre_cap1 = cfg.t1_cap + 1ull;
+        pre_cap2 = cfg.stream_cap + 1ull;
+        t1_pre = S.get<unsigned long long>(pre_cap1);
+        chunk_pre = S.get<unsigned long long>(pre_cap2);
+        tmp_cap = scan_tmp_words((int64_t)std::max(pre_cap1, pre_cap2));
+        tmp = S.get<unsigned long long>(tmp_cap);
+        unsigned long long* lens = S.get<unsigned long long>(2);
+        unsigned int* ok = S.get<unsigned int>(1);
+        unsigned long long* snap = S.get<unsigned long long>(kNumStats + 3);
+        CK(cudaMemcpyAsync(snap, stats, (kNumStats + 3) * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToDevice, st));
+        launch_prep_lists(cfg, lens, ok, st);
+        cfg.lists_ok = ok;  // an overflowed round samples nothing
+        launch_scan_u32_to_u64_dev(cfg.t1_pairs, t1_pre, lens, (int64_t)pre_cap1, tmp, st);
+        launch_scan_u32_to_u64_dev(cfg.stream_chunks, chunk_pre, lens + 1, (int64_t)pre_cap2, tmp, st);
+        cfg.t1_pre = t1_pre;
+        cfg.chunk_pre = chunk_pre;
+        launch_type1(cfg, st);
+        tm.mark();  // type I done
+        launch_type2(cfg, st);
+        tm.mark();  // type II done
+        cfg.lists_ok = nullptr;  // the rounds below check the counts on the host first
+        unsigned long long wc[3], es[kNumStats];
+        unsigned int ec[2];
+        CK(cudaMemcpyAsync(wc, wcount, sizeof(wc), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ec, counters + 6, sizeof(ec), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(es, estats, sizeof(es), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(rc, counters, sizeof(rc), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        n_ent2 = ec[0];
+        n_ent1 = ec[1];
+        if (wc[0] <= cfg.t1_cap && wc[1] <= cfg.stream_cap && wc[2] <= cfg.seg_cap) {
+            for (int q = 0; q < kNumStats; ++q) est_acc[q] += es[q];
+            total_streams += wc[1];
+            total_segs += wc[2];
+            round = 1;
+            done = true;
+        } else {
+            CK(cudaMemcpyAsync(stats, snap, (kNumStats + 3) * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToDevice, st));
+            tm.used -= 3;  // the rounds below mark these phases again
+        }
+    }
+    for (int attempt = 0; !done; ++attempt) {
         if (attempt > 64) throw Status{GIRG_E_INTERNAL};
         cfg.ent2_lo = lo2;
         cfg.ent2_hi = hi2;
@@ -592,13 +668,13 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
         hi1 = (uint32_t)std::min<uint64_t>(0xffffffffull, (uint64_t)lo1 + std::max<uint32_t>(span1, 1));
         attempt = 0;
     }
-    tm.mark();  // type II done (with every later round)
-    unsigned long long hs[kNumStats + 1];
-    CK(cudaMemcpyAsync(hs, stats, (kNumStats + 1) * sizeof(unsigned long long),
-                       cudaMemcpyDeviceToHost, st));
-    unsigned int rc[6];
-    CK(cudaMemcpyAsync(rc, counters, 6 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    if (!done) {
+        tm.mark();  // type II done (with every later round)
+        CK(cudaMemcpyAsync(hs, stats, (kNumStats + 1) * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(rc, counters, 6 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
     CK(cudaGetLastError());
     if (rc[5]) throw Status{GIRG_E_INTERNAL};
     for (int q = 0; q < kNumStats; ++q) hs[q] += est_acc[q];

@@ -122,6 +122,9 @@ struct DevCfg {
     unsigned long long* seg_count;
     uint32_t seg_cap;
     unsigned int* error;         // set when a stream needs 2^32 chunks or more
+    // optional: 0 when a work list of this round overflowed (its entries past the
+    // capacity were not written), and the sampling kernels then do nothing
+    const unsigned int* lists_ok;
     unsigned long long* work64;  // [0] type-I pairs taken, [1] type-II chunks taken
 };
 

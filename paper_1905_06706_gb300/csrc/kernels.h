@@ -60,6 +60,10 @@ void launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp
 // Exclusive scan of n uint32 counts into uint64 prefixes; tmp >= scan_tmp_words(n) uint64s.
 void launch_scan_u32_to_u64(const uint32_t* in, unsigned long long* out, int64_t n,
                             unsigned long long* tmp, cudaStream_t st);
+// The same with the length min(*n_dev, n_max) read on the device (tmp sized for n_max).
+void launch_scan_u32_to_u64_dev(const uint32_t* in, unsigned long long* out,
+                                const unsigned long long* n_dev, int64_t n_max,
+                                unsigned long long* tmp, cudaStream_t st);
 // Stable LSD radix sort of (key, val) on the low `bits` bits of key.
 size_t radix_tmp_words(int64_t n);
 void radix_sort_pairs(uint32_t* key, uint32_t* val, uint32_t* key_alt, uint32_t* val_alt,
@@ -77,6 +81,12 @@ void launch_gather_hrg(int64_t n, const uint32_t* perm, const uint32_t* X, const
 // Pair sampling.
 void launch_rows(const DevCfg& cfg, cudaStream_t st);
 void launch_enumerate(const DevCfg& cfg, cudaStream_t st);
+// After an enumeration, on the device: the list lengths clamped to their capacities
+// plus one (lens[0] type-I items, lens[1] streams) for the scans, the zero sentinels
+// past the lists, the work counters of the sampling kernels reset, and *ok = 1 iff
+// no list overflowed (read by the sampling kernels through cfg.lists_ok).
+void launch_prep_lists(const DevCfg& cfg, unsigned long long* lens, unsigned int* ok,
+                       cudaStream_t st);
 // Type I over the pair prefix cfg.t1_pre, type II over the chunk prefix cfg.chunk_pre.
 void launch_type1(const DevCfg& cfg, cudaStream_t st);
 void launch_type2(const DevCfg& cfg, cudaStream_t st);

@@ -912,6 +912,7 @@ constexpr unsigned kT1Grab = 1024;
 
 template <int DIM>
 __global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
+    if (cfg.lists_ok && *cfg.lists_ok == 0u) return;  // a list overflowed: the round is redone
     __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
     __shared__ unsigned int s_en[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1011,6 +1012,7 @@ constexpr int kT2RefillMin = 8;  // refill idle lanes once this many are idle
 
 template <int DIM>
 __global__ void __launch_bounds__(kT2Threads, 4) k_type2(DevCfg cfg) {
+    if (cfg.lists_ok && *cfg.lists_ok == 0u) return;  // a list overflowed: the round is redone
     __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
     __shared__ unsigned int s_en[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1192,6 +1194,25 @@ void launch_rows(const DevCfg& cfg, cudaStream_t st) {
     if (b < 1) b = 1;
     ++g_launches;
     k_rows<<<(unsigned)b, kAllocThreads, 0, st>>>(cfg);
+}
+
+__global__ void k_prep_lists(DevCfg cfg, unsigned long long* lens, unsigned int* ok) {
+    const unsigned long long c1 = *cfg.t1_count, cs = *cfg.stream_count;
+    *ok = c1 <= cfg.t1_cap && cs <= cfg.stream_cap && *cfg.seg_count <= cfg.seg_cap ? 1u : 0u;
+    const unsigned long long n1 = c1 < cfg.t1_cap ? c1 : cfg.t1_cap;
+    const unsigned long long ns = cs < cfg.stream_cap ? cs : cfg.stream_cap;
+    cfg.t1_pairs[n1] = 0u;
+    cfg.stream_chunks[ns] = 0u;
+    cfg.work64[0] = 0ull;
+    cfg.work64[1] = 0ull;
+    lens[0] = n1 + 1;
+    lens[1] = ns + 1;
+}
+
+void launch_prep_lists(const DevCfg& cfg, unsigned long long* lens, unsigned int* ok,
+                       cudaStream_t st) {
+    ++g_launches;
+    k_prep_lists<<<1, 1, 0, st>>>(cfg, lens, ok);
 }
 
 void launch_enumerate(const DevCfg& cfg, cudaStream_t st) {

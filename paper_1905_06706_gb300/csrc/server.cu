@@ -123,7 +123,7 @@ int64_t girg_scratch_bytes(const girg_params* p) {
     // (about 400 + 112 d bytes), type-I items with pair counts and prefixes (28 bytes
     // each, 1 + 0.75 3^d per vertex), and the partner segments (8 bytes each) at the
     // library's initial work-list sizes; more is allocated only when a list grows
-    const int64_t seg = p->T > 0.0 ? (d == 1 ? 8 : d == 2 ? 40 : d == 3 ? 224 : d == 4 ? 1024 : 4 * n6) : 0;
+    const int64_t seg = p->T > 0.0 ? (d == 1 ? 8 : d == 2 ? 28 : d == 3 ? 112 : d == 4 ? 448 : 4 * n6) : 0;
     const int64_t per_v = 400 + 112 * d + 21 * n3 + 8 * seg;
     return p->n * per_v + (64ll << 20);
 }

@@ -67,10 +67,23 @@ __device__ __forceinline__ T block_exclusive_scan(T x, T* s_warp, T* total) {
     return r;
 }
 
+// n_dev (optional): the length is min(*n_dev, n), read on the device.
+__device__ __forceinline__ int64_t scan_len(int64_t n, const unsigned long long* n_dev) {
+    if (!n_dev) return n;
+    const unsigned long long m = *n_dev;
+    return m < (unsigned long long)n ? (int64_t)m : n;
+}
+
 template <class Tin, class T>
-__global__ void k_scan_reduce(const Tin* __restrict__ in, int64_t n, T* __restrict__ sums) {
+__global__ void k_scan_reduce(const Tin* __restrict__ in, int64_t n, T* __restrict__ sums,
+                              const unsigned long long* __restrict__ n_dev) {
     __shared__ T s_warp[33];
+    n = scan_len(n, n_dev);
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    if (base >= n) {  // past the end: an empty tile
+        if (threadIdx.x == 0) sums[blockIdx.x] = T(0);
+        return;
+    }
     T acc = 0;
     for (int it = 0; it < kScanItems; ++it) {
         const int64_t i = base + (int64_t)it * kScanThreads + threadIdx.x;
@@ -83,8 +96,10 @@ __global__ void k_scan_reduce(const Tin* __restrict__ in, int64_t n, T* __restri
 
 template <class Tin, class T>
 __global__ void k_scan_down(const Tin* __restrict__ in, T* __restrict__ out, int64_t n,
-                            const T* __restrict__ prefix) {
+                            const T* __restrict__ prefix, const unsigned long long* __restrict__ n_dev) {
     __shared__ T s_warp[33];
+    n = scan_len(n, n_dev);
+    if ((int64_t)blockIdx.x * kScanTile >= n) return;  // uniform per block
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     T v[kScanItems];
     T acc = 0;
@@ -114,21 +129,24 @@ size_t scan_tmp_words(int64_t n) {
     return words + 64;
 }
 
+// n: the length, or with n_dev its upper bound (the grid is sized for n; tiles past
+// *n_dev are empty).
 template <class Tin, class T>
-static void scan_impl(const Tin* in, T* out, int64_t n, T* tmp, cudaStream_t st) {
+static void scan_impl(const Tin* in, T* out, int64_t n, T* tmp, cudaStream_t st,
+                      const unsigned long long* n_dev = nullptr) {
     if (n <= 0) return;
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
     if (nb == 1) {
         ++g_launches;
-        k_scan_down<Tin, T><<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
+        k_scan_down<Tin, T><<<1, kScanThreads, 0, st>>>(in, out, n, nullptr, n_dev);
         return;
     }
     T* sums = tmp;
     ++g_launches;
-    k_scan_reduce<Tin, T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums);
+    k_scan_reduce<Tin, T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums, n_dev);
     scan_impl<T, T>(sums, sums, nb, tmp + nb + 32, st);
     ++g_launches;
-    k_scan_down<Tin, T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums);
+    k_scan_down<Tin, T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums, n_dev);
 }
 
 void launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t st) {
@@ -138,6 +156,12 @@ void launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp
 void launch_scan_u32_to_u64(const uint32_t* in, unsigned long long* out, int64_t n,
                             unsigned long long* tmp, cudaStream_t st) {
     scan_impl<uint32_t, unsigned long long>(in, out, n, tmp, st);
+}
+
+void launch_scan_u32_to_u64_dev(const uint32_t* in, unsigned long long* out,
+                                const unsigned long long* n_dev, int64_t n_max,
+                                unsigned long long* tmp, cudaStream_t st) {
+    scan_impl<uint32_t, unsigned long long>(in, out, n_max, tmp, st, n_dev);
 }
 
 // ------------------------------------------------------------------ radix sort

@@ -160,6 +160,29 @@ def test_level_cap_keeps_parity(lcap):
     assert _generate_from(X, w, T, c, 3, gg.PRECISION_FP32, level_cap=lcap) == O.edge_set(ref.edges)
 
 
+@pytest.mark.parametrize("d,T,n", [(1, 0.7, 20_000), (2, 0.5, 20_000), (2, 0.0, 20_000),
+                                   (3, 0.3, 10_000)])
+def test_worklist_growth_keeps_parity(d, T, n, monkeypatch):
+    """Initial work lists far too small: the first sampling round overflows, is undone
+    (statistics and edge count restored) and the enumeration reruns with grown lists;
+    the graph is the same edge for edge and its statistics are those of one pass."""
+    w, X = O.girg_points(n, d, 2.4, 1.0, 60 + d)
+    W = O.exact_sum(w)
+    c = O.girg_solve_c(9.0, w, d, T, W)
+    ref = O.girg_cellpairs(X, w, float(w.min()), W, T, c, 4, cap=n * 64)
+    base = _generate_from(X, w, T, c, 4, gg.PRECISION_FP32)
+    st0 = gg.last_stats()
+    assert st0["enum_passes"] == 1
+    monkeypatch.setenv("GIRG_INITIAL_LIST_SCALE", "0.001")
+    got = _generate_from(X, w, T, c, 4, gg.PRECISION_FP32)
+    st = gg.last_stats()
+    assert st["enum_passes"] > 1
+    assert got == base == O.edge_set(ref.edges)
+    for k in ("type1_pairs", "coins", "type2_items", "jump_draws", "type2_candidates",
+              "edges", "edge_checksum", "type2_streams", "type2_segments"):
+        assert st[k] == st0[k], k
+
+
 def test_user_weights_synthetic_points():
     """User-defined weights (App. B.2 / Sec. 4.1): log-normal weights, clustered positions."""
     rng = np.random.default_rng(4)
