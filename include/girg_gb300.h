@@ -97,7 +97,10 @@ typedef struct {
 } hrg_params;
 
 /* Generate one GIRG (Sec. 2.1) by the cell-pair sampler (Algorithm 1).
- *   d_edges        device buffer of capacity_edges edges (layout above)
+ *   d_edges        buffer of capacity_edges edges (layout above): device memory, or
+ *                  page-locked host memory mapped into the device address space
+ *                  (cudaHostAlloc), which the kernels then fill across the host link
+ *                  with no separate copy; pageable host memory gives GIRG_E_PARAM
  *   num_edges      host out: number of edges of the graph
  *   c_used         host out (may be NULL): the c of Eq. 1 that was used
  * Errors: GIRG_E_PARAM, GIRG_E_CAPACITY, GIRG_E_CUDA, GIRG_E_RANGE, GIRG_E_INTERNAL. */

@@ -145,8 +145,24 @@ struct Problem {
 
 // Everything after the reductions: tables, sort, sampling.  If order_out is set,
 // stops after the sort and writes the sorted original ids there.
+// The edge buffer is device memory or page-locked host memory mapped into the
+// device's address space (the kernels then write the edges across the host link, so
+// no copy follows).  Pageable host memory is refused.
+void* device_view(void* p) {
+    if (!p) return p;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        throw Status{GIRG_E_PARAM};
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+    throw Status{GIRG_E_PARAM};
+}
+
 void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edges, int64_t cap,
                  int64_t* num_edges, int64_t* order_out) {
+    d_edges = device_view(d_edges);
     const int64_t n = P.n;
     const int d = P.d;
     const bool girg = P.model == 0;
@@ -1173,6 +1189,7 @@ int girg_allpairs(int64_t n, int32_t d, const uint32_t* d_X, const double* d_w, 
     if ((edge_bytes != 4 && edge_bytes != 8) || (precision != 0 && precision != 1)) return GIRG_E_PARAM;
     return guarded([&] {
         cudaStream_t st = (cudaStream_t)stream;
+        d_edges = device_view(d_edges);
         Scratch S(st);
         float* sv = S.get<float>(n);
         const bool tzero = T == 0.0;

@@ -249,6 +249,26 @@ def test_int64_edges_and_capacity():
     assert r.status == gg.GIRG_E_CAPACITY and r.num_edges == len(ref)
 
 
+def test_pinned_host_edge_buffer():
+    """Edges written by the kernels straight into page-locked host memory: the same graph
+    as into device memory; pageable host memory is refused."""
+    n, d, T = 30_000, 2, 0.5
+    w, X = O.girg_points(n, d, 2.5, 1.0, 12)
+    W = O.exact_sum(w)
+    c = O.girg_solve_c(10.0, w, d, T, W)
+    res = O.girg_cellpairs(X, w, 1.0, W, T, c, 12, cap=n * 64)
+    ref, cs = O.edge_set(res.edges), O.edge_checksum(res.edges)
+    for dt in (torch.int32, torch.int64):
+        host = torch.empty((n * 16, 2), dtype=dt, pin_memory=True)
+        r = gg.girg_generate(host, n=n, d=d, beta=2.5, T=T, c=c, seed=12)
+        assert r.status == gg.GIRG_OK
+        assert _set(host, r.num_edges) == ref
+        assert gg.last_stats()["edge_checksum"] == cs
+    pageable = torch.empty((n * 16, 2), dtype=torch.int32)
+    r = gg.girg_generate(pageable, n=n, d=d, beta=2.5, T=T, c=c, seed=12)
+    assert r.status == gg.GIRG_E_PARAM
+
+
 def test_degenerate_inputs():
     # two vertices, identical positions: p = 1
     X = np.zeros((2, 1), dtype=np.uint32)
