@@ -787,7 +787,7 @@ struct SplitDev {
 
 SplitDev split_buffers(int64_t n, Scratch& S) {
     SplitDev D;
-    D.cnt = S.get<unsigned int>(2);
+    D.cnt = S.get<unsigned int>(3);  // gathered, sorted flag, blocks done
     D.thr = S.get<double>(1);
     D.sums = S.get<double>(4);
     D.part = S.get<double>((size_t)4 * reduce_blocks(n));
@@ -799,7 +799,7 @@ SplitDev split_buffers(int64_t n, Scratch& S) {
 // Queue the split at the threshold in D.thr and the copy of its results into h
 // (read after the next synchronisation).
 void queue_split(const Problem& P, SplitDev& D, SplitHost* h, cudaStream_t st) {
-    CK(cudaMemsetAsync(D.cnt, 0, 2 * sizeof(unsigned int), st));
+    CK(cudaMemsetAsync(D.cnt, 0, 3 * sizeof(unsigned int), st));
     launch_split_weights(P.n, P.w, D.thr, P.T, D.buf, D.cap, D.cnt, D.part, D.sums, st);
     CK(cudaMemcpyAsync(h->count, D.cnt, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&h->thr, D.thr, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -978,14 +978,16 @@ int girg_generate(const girg_params* params, void* d_edges, int64_t capacity_edg
         const int E0 = exponent_of_ulp(P.w_min);
         Reduce* red = new_reduce(S, st);
         double* part_s2 = solve ? S.get<double>(reduce_blocks(P.n)) : nullptr;
-        launch_reduce(P.n, w, nullptr, P.w_min, E0, part_s2, red, st);
         SplitDev D{};
         SplitHost* h = nullptr;
         if (solve) {  // the weight split for the degree model, before the one readback
             D = split_buffers(P.n, S);
             h = pinned_split();
-            launch_split_threshold(red, part_s2, P.n, P.d, P.T, params->avg_deg, E0, D.thr, st);
+            const ThresholdJob job{P.d, P.T, params->avg_deg, D.thr};
+            launch_reduce(P.n, w, nullptr, P.w_min, E0, part_s2, red, st, &job);
             queue_split(P, D, h, st);
+        } else {
+            launch_reduce(P.n, w, nullptr, P.w_min, E0, nullptr, red, st);
         }
         tm.mark();
         auto h0 = std::chrono::steady_clock::now();

@@ -69,10 +69,15 @@ __device__ __forceinline__ void add128(unsigned long long& lo, unsigned long lon
     lo = s;
 }
 
+__device__ __forceinline__ bool last_block(unsigned int* ticket);
+__device__ void top_threshold(Reduce* __restrict__ red, const double* __restrict__ part_s2,
+                              int nb, int64_t n, int d, double T, double target, int E0,
+                              double* __restrict__ thr);
+
 // Reductions over the weights (and radii for HRG) of all vertices.
 __global__ void k_reduce(int64_t n, const double* __restrict__ w, const double* __restrict__ r,
                          double w_min, int E0, double* __restrict__ part_s2,
-                         Reduce* __restrict__ out) {
+                         Reduce* __restrict__ out, ThresholdJob job) {
     __shared__ unsigned int s_cnt[kMaxLayers];
     __shared__ unsigned long long s_wmax[kMaxLayers];
     __shared__ unsigned long long s_rmin[kMaxLayers];
@@ -157,14 +162,19 @@ __global__ void k_reduce(int64_t n, const double* __restrict__ w, const double* 
             }
         }
     }
+    // the split threshold, by the last block once every block's sums are in
+    if (job.thr && last_block(&out->blocks_done))
+        top_threshold(out, part_s2, gridDim.x, n, job.d, job.T, job.target, E0, job.thr);
 }
 
 
-// Fixed-order sum of a per-block partial array by one block (deterministic).
+// Fixed-order sum of a per-block partial array by one block of 256 threads
+// (deterministic; loads through L2, as the last block of a grid reads the partials
+// the other blocks wrote).
 __device__ double block_ordered_sum(const double* __restrict__ part, int nb) {
     __shared__ double s[256];
     double a = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) a += part[i];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) a += __ldcg(part + i);
     s[threadIdx.x] = a;
     __syncthreads();
     for (int h = blockDim.x / 2; h > 0; h >>= 1) {
@@ -176,6 +186,17 @@ __device__ double block_ordered_sum(const double* __restrict__ part, int nb) {
     return r;
 }
 
+// True in the last block of the grid to get here (after __threadfence, so that the
+// writes of every other block are visible to it).  *ticket starts at 0.
+__device__ __forceinline__ bool last_block(unsigned int* ticket) {
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    return s_last;
+}
+
 // The split threshold of the degree model (App. B.2): the weight above which a
 // vertex can have partners in E_R at the scale K0 where the sum of
 // 2^d K w_u w_v / (W (1 - T)) over all pairs reaches the target, divided by a
@@ -184,16 +205,17 @@ __device__ double block_ordered_sum(const double* __restrict__ part, int nb) {
 // about 1.3 for T < 0.7 and 2.3 up to T = 0.9 (beta >= 2.1, degree <= 32), hence
 // margins 1.4 and 2.8; the search fetches a new split only if it moves further.
 // One block (256 threads): also finishes sum w^2 in block order.
-__global__ void k_top_threshold(Reduce* __restrict__ red, const double* __restrict__ part_s2,
-                                int nb, int64_t n, int d, double T, double target, int E0,
-                                double* __restrict__ thr) {
+__device__ void top_threshold(Reduce* __restrict__ red, const double* __restrict__ part_s2,
+                              int nb, int64_t n, int d, double T, double target, int E0,
+                              double* __restrict__ thr) {
     const double s2 = block_ordered_sum(part_s2, nb);
     if (threadIdx.x != 0) return;
     red->s2 = s2;
-    const double W = ldexp((double)red->sum_hi * 0x1p64 + (double)red->sum_lo, E0);
+    const double W = ldexp((double)__ldcg(&red->sum_hi) * 0x1p64 + (double)__ldcg(&red->sum_lo), E0);
     double wmax = 0.0;
     for (int i = 0; i < 64; ++i)
-        if (red->cnt[i]) wmax = fmax(wmax, __longlong_as_double((long long)red->wmax[i]));
+        if (__ldcg(&red->cnt[i]))
+            wmax = fmax(wmax, __longlong_as_double((long long)__ldcg(&red->wmax[i])));
     const double K0 = target * (double)n * W * (T > 0.0 ? 1.0 - T : 1.0) /
                       (ldexp(W * W - s2, d));
     const double margin = T >= 0.7 ? 2.8 : 1.4;
@@ -207,7 +229,8 @@ __global__ void k_top_threshold(Reduce* __restrict__ red, const double* __restri
 __global__ void k_split_weights(int64_t n, const double* __restrict__ w,
                                 const double* __restrict__ thr, double invT, int m_int,
                                 double* __restrict__ out, unsigned int cap,
-                                unsigned int* __restrict__ count, double* __restrict__ part) {
+                                unsigned int* __restrict__ count, double* __restrict__ part,
+                                double* __restrict__ sums) {
     __shared__ double s[4][8];
     const double t = *thr, inv_t = 1.0 / t;  // only feeds the search for K: no exact rounding needed
     double a[4] = {0.0, 0.0, 0.0, 0.0};
@@ -246,13 +269,13 @@ __global__ void k_split_weights(int64_t n, const double* __restrict__ w,
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) acc += s[threadIdx.x][i];
         part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = acc;
     }
-}
-
-// Finish the four split sums in block order.
-__global__ void k_split_finish(const double* __restrict__ part, int nb, double* __restrict__ sums) {
-    for (int q = 0; q < 4; ++q) {
-        const double v = block_ordered_sum(part + (size_t)q * nb, nb);
-        if (threadIdx.x == 0) sums[q] = v;
+    // the four sums in block order, by the last block
+    if (last_block(&count[2])) {
+        const int nb = gridDim.x;
+        for (int q = 0; q < 4; ++q) {
+            const double v = block_ordered_sum(part + (size_t)q * nb, nb);
+            if (threadIdx.x == 0) sums[q] = v;
+        }
     }
 }
 
@@ -375,17 +398,14 @@ void launch_min_weight(int64_t n, const double* w, unsigned long long* out, cuda
 int reduce_blocks(int64_t n) { return grid_for(n, 256, 152 * 8); }
 
 void launch_reduce(int64_t n, const double* w, const double* r, double w_min, int E0,
-                   double* part_s2, Reduce* out, cudaStream_t st) {
+                   double* part_s2, Reduce* out, cudaStream_t st, const ThresholdJob* job) {
     ++g_launches;
-    k_reduce<<<reduce_blocks(n), 256, 0, st>>>(n, w, r, w_min, E0, part_s2, out);
+    ThresholdJob j{};
+    if (job && part_s2) j = *job;
+    k_reduce<<<reduce_blocks(n), 256, 0, st>>>(n, w, r, w_min, E0, part_s2, out, j);
 }
 
 
-void launch_split_threshold(Reduce* red, const double* part_s2, int64_t n, int d, double T,
-                            double target, int E0, double* thr, cudaStream_t st) {
-    ++g_launches;
-    k_top_threshold<<<1, 256, 0, st>>>(red, part_s2, reduce_blocks(n), n, d, T, target, E0, thr);
-}
 
 void launch_split_weights(int64_t n, const double* w, const double* thr, double T, double* out,
                           unsigned int cap, unsigned int* count, double* part, double* sums,
@@ -394,9 +414,8 @@ void launch_split_weights(int64_t n, const double* w, const double* thr, double 
     int m_int = 0;
     if (invT > 0.0 && invT == floor(invT) && invT <= 64.0) m_int = (int)invT;
     const int nb = reduce_blocks(n);
-    g_launches += 3;
-    k_split_weights<<<nb, 256, 0, st>>>(n, w, thr, invT, m_int, out, cap, count, part);
-    k_split_finish<<<1, 256, 0, st>>>(part, nb, sums);
+    g_launches += 2;
+    k_split_weights<<<nb, 256, 0, st>>>(n, w, thr, invT, m_int, out, cap, count, part, sums);
     k_sort_top<<<1, 1024, 0, st>>>(out, count);
 }
 

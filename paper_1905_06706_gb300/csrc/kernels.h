@@ -25,7 +25,14 @@ struct Reduce {
     unsigned long long rmax[64];        // HRG: largest radius per bucket (bits)
     double s2;                          // sum w^2 (filled by the split threshold)
     unsigned int range_error;
-    unsigned int pad;
+    unsigned int blocks_done;           // blocks of the reduction finished
+};
+
+// The split threshold computed by the last block of the reduction (thr null: none).
+struct ThresholdJob {
+    int d;
+    double T, target;
+    double* thr;
 };
 
 void launch_girg_points(int64_t n, int d, double beta, double w_min, uint64_t seed, double* w,
@@ -35,17 +42,18 @@ void launch_hrg_points(int64_t n, double alpha, double R, uint64_t seed, double*
 void launch_min_weight(int64_t n, const double* w, unsigned long long* out, cudaStream_t st);
 // Blocks of the reduction (one per-block partial each).
 int reduce_blocks(int64_t n);
-// part_s2 (reduce_blocks(n) doubles, or null): per-block sums of w^2.
+// part_s2 (reduce_blocks(n) doubles, or null): per-block sums of w^2.  With job (and
+// part_s2), the last block also finishes red->s2 in block order and writes the split
+// threshold of the degree model (App. B.2), estimated from the reduction, to job->thr.
 void launch_reduce(int64_t n, const double* w, const double* r, double w_min, int E0,
-                   double* part_s2, Reduce* out, cudaStream_t st);
-// The split of the weights for the degree model (App. B.2): a threshold estimated on
-// the device from the reduction (also finishing red->s2 in block order), then one pass
-// that gathers the weights above *thr (count[0]; sorted in decreasing order when
-// count[0] <= kTopSortMax, count[1] = 1) and sums over the rest: sums[0..3] = sum w,
-// sum w^2, sum (w/thr)^(1/T), sum (w/thr)^(2/T).  part: 4 reduce_blocks(n) doubles.
+                   double* part_s2, Reduce* out, cudaStream_t st,
+                   const ThresholdJob* job = nullptr);
+// The split of the weights for the degree model: one pass that gathers the weights
+// above *thr (count[0]; sorted in decreasing order when count[0] <= kTopSortMax,
+// count[1] = 1) and sums over the rest: sums[0..3] = sum w, sum w^2, sum (w/thr)^(1/T),
+// sum (w/thr)^(2/T) (finished in block order by the last block; count[2] counts the
+// blocks and starts at 0).  part: 4 reduce_blocks(n) doubles.
 constexpr unsigned int kTopSortMax = 4096;  // sorted in 32 KB of static shared memory
-void launch_split_threshold(Reduce* red, const double* part_s2, int64_t n, int d, double T,
-                            double target, int E0, double* thr, cudaStream_t st);
 void launch_split_weights(int64_t n, const double* w, const double* thr, double T, double* out,
                           unsigned int cap, unsigned int* count, double* part, double* sums,
                           cudaStream_t st);

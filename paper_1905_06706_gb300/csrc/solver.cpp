@@ -64,14 +64,21 @@ bool DegreeModel::valid(double K) const { return thr_ < needed_threshold(K); }
 // come from the suffix aggregates: sum_u w_u (S - w_u) and sum_u e_u (E - e_u) with
 // e = w^(1/T), E = sum e (the self terms are at most half of the products there, as
 // every such u has the heaviest vertex as a heavier partner).
-double DegreeModel::f(double K) const {
+double DegreeModel::f(double K, double* slope) const {
+    // Every non-E_R pair adds (z - T z^(1/T)) / (1 - T), so K d/dK adds (z - z^(1/T)) /
+    // (1 - T): each term below is accumulated as (s1 - T s2) / (1 - T) for f and
+    // (s1 - s2) / (1 - T) for the slope K f'(K) (E_R pairs contribute no slope).
     const double T = T_, A = std::ldexp(K, d_) / W_, lA = std::log(A);
     const double lt = std::log(thr_);
     const bool tp = T > 0.0;
     const double inv1mT = tp ? 1.0 / (1.0 - T) : 1.0, lAT = tp ? lA / T : 0.0;
+    double val = 0.0, slp = 0.0;
+    auto add = [&](double s1, double s2) {  // s2 = 0 when T = 0
+        val += (s1 - T * s2) * inv1mT;
+        slp += (s1 - s2) * inv1mT;
+    };
     // rest x rest
-    double rr = A * (sw_ * sw_ - s2_);
-    if (tp) rr = (rr - T * std::exp(lAT + 2.0 * lt / T) * (sx_ * sx_ - sx2_)) * inv1mT;
+    add(A * (sw_ * sw_ - s2_), tp ? std::exp(lAT + 2.0 * lt / T) * (sx_ * sx_ - sx2_) : 0.0);
     const size_t m = top_.size();
     double C = 0.0;  // (A thr^2)^mi on the integer path
     if (mi_) {
@@ -79,50 +86,52 @@ double DegreeModel::f(double K) const {
         C = a;
         for (int q = 1; q < mi_; ++q) C *= a;
     }
-    // top x rest: sum_u [A w_u sw - T (A w_u thr)^(1/T) sx] / (1 - T)
-    double tr = A * suf_[0] * sw_;
-    if (tp && m)
-        tr = (tr - T * (mi_ ? C * spy_[0] : std::exp(lAT + lt / T + b_[0]) * sr_[0]) * sx_) *
-             inv1mT;
+    // top x rest, both orders: sum_u [A w_u sw - T (A w_u thr)^(1/T) sx] / (1 - T)
+    {
+        const double s1 = A * suf_[0] * sw_;
+        double s2 = 0.0;
+        if (tp && m) s2 = (mi_ ? C * spy_[0] : std::exp(lAT + lt / T + b_[0]) * sr_[0]) * sx_;
+        add(2.0 * s1, 2.0 * s2);
+    }
     // top x top
-    double tt = 0.0;
     size_t k = m, u = 0;
     for (; u < m; ++u) {
         const double wu = top_[u];
         while (k > 0 && A * wu * top_[k - 1] < 1.0) --k;
         if (k == 0 && u > 0) break;  // from here on no u has E_R partners
         const size_t k1 = u == k ? k + 1 : k;  // first non-E_R partner
-        double e = A * wu * (u > k ? suf_[k] - wu : suf_[k1]);
+        const double s1 = A * wu * (u > k ? suf_[k] - wu : suf_[k1]);
+        double s2 = 0.0;
         if (mi_) {
-            double zt = C * py_[u] * spy_[k1];
-            if (u > k) zt -= C * py_[u] * py_[u];  // at most half of the sum
-            e = (e - T * zt) * inv1mT;
+            s2 = C * py_[u] * spy_[k1];
+            if (u > k) s2 -= C * py_[u] * py_[u];  // at most half of the sum
         } else if (tp) {
             const double xu = lAT + b_[u];  // log (A w_u)^(1/T)
-            double zt = k1 < m ? std::exp(xu + b_[k1]) * sr_[k1] : 0.0;
-            if (u > k) zt -= std::exp(xu + b_[u]);  // at most half of the sum
-            e = (e - T * zt) * inv1mT;
+            s2 = k1 < m ? std::exp(xu + b_[k1]) * sr_[k1] : 0.0;
+            if (u > k) s2 -= std::exp(xu + b_[u]);  // at most half of the sum
         }
-        tt += (double)k - (u < k ? 1.0 : 0.0) + e;
+        val += (double)k - (u < k ? 1.0 : 0.0);
+        add(s1, s2);
     }
     if (u < m) {  // u .. m-1: no E_R partners, all other top weights are partners
-        double e = A * (suf_[u] * suf_[0] - suf2_[u]);
+        const double s1 = A * (suf_[u] * suf_[0] - suf2_[u]);
+        double s2 = 0.0;
         if (mi_) {
-            e = (e - T * C * (spy_[u] * spy_[0] - spy2_[u])) * inv1mT;
+            s2 = C * (spy_[u] * spy_[0] - spy2_[u]);
         } else if (tp) {
-            const double zt = std::exp(lAT + b_[u] + b_[0]) *
-                              (sr_[u] * sr_[0] - std::exp(b_[u] - b_[0]) * sr2_[u]);
-            e = (e - T * zt) * inv1mT;
+            s2 = std::exp(lAT + b_[u] + b_[0]) *
+                 (sr_[u] * sr_[0] - std::exp(b_[u] - b_[0]) * sr2_[u]);
         }
-        tt += e;
+        add(s1, s2);
     }
-    return (rr + 2.0 * tr + tt) / (double)n_;
+    if (slope) *slope = slp / (double)n_;
+    return val / (double)n_;
 }
 
 double DegreeModel::solve(double target, const std::function<void(double)>& fetch) {
-    auto eval = [&](double K) {
+    auto eval = [&](double K, double* slope) {
         if (!valid(K)) fetch(0.5 * needed_threshold(K));
-        return f(K);
+        return f(K, slope);
     };
     // start where the sum without E_R capping reaches the target; the capping and the
     // z^(1/T) terms only lower f, so the root lies at or above this K0
@@ -131,47 +140,31 @@ double DegreeModel::solve(double target, const std::function<void(double)>& fetc
     const double lead = std::ldexp(1.0, d_) * (W_ * W_ - s2) / (W_ * (T_ > 0.0 ? 1.0 - T_ : 1.0));
     double K0 = target * (double)n_ / lead;
     if (!(K0 > 1e-300 && K0 < 1e300)) K0 = 1.0;
-    // bracket with steps growing from 5% (the root is usually close to K0, and small
-    // steps keep the needed top weights within those already held)
-    double lo = K0, hi = K0;
-    if (eval(K0) < target) {
-        for (double g = 1.05; eval(hi) < target && hi < 1e300; g = g * g) {
-            lo = hi;
-            hi *= g;
-        }
-    } else {
-        for (double g = 1.05; eval(lo) >= target && lo > 1e-300; g = g * g) {
-            hi = lo;
-            lo /= g;
-        }
-    }
-    // Illinois regula falsi on log K; bisection steps guard it
-    double flo = eval(lo) - target, fhi = eval(hi) - target;
-    int side = 0;
-    for (int it = 0; it < 200 && hi - lo > 1e-13 * hi; ++it) {
-        double mid;
-        const double a = std::log(lo), b = std::log(hi);
-        if (it % 8 == 7 || !(fhi > flo))
-            mid = std::sqrt(lo * hi);
+    // Newton on x = ln K with the exact slope K f'(K) > 0 (f is increasing and C^1),
+    // safeguarded by the bracket of the iterates seen so far: a step leaving it, or a
+    // step longer than ln 4 while one side is open, is replaced by bisection or capped
+    const double kMaxStep = std::log(4.0);
+    double x = std::log(K0), lo = -HUGE_VAL, hi = HUGE_VAL;
+    for (int it = 0; it < 200; ++it) {
+        const double K = std::exp(x);
+        double slope = 0.0;
+        const double g = eval(K, &slope) - target;
+        if (std::fabs(g) <= 1e-14 * target) return K;
+        if (g < 0.0)
+            lo = x;
         else
-            mid = std::exp(b - fhi * (b - a) / (fhi - flo));
-        if (!(mid > lo && mid < hi)) mid = std::sqrt(lo * hi);
-        if (!(mid > lo && mid < hi)) mid = 0.5 * (lo + hi);
-        const double fm = eval(mid) - target;
-        if (fm < 0.0) {
-            lo = mid;
-            flo = fm;
-            if (side == -1) fhi *= 0.5;
-            side = -1;
+            hi = x;
+        double xn = slope > 0.0 ? x - g / slope : (g < 0.0 ? x + kMaxStep : x - kMaxStep);
+        if (lo > -HUGE_VAL && hi < HUGE_VAL) {
+            if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+            if (hi - lo <= 1e-14 * std::fabs(hi) + 1e-300) return std::exp(0.5 * (lo + hi));
         } else {
-            hi = mid;
-            fhi = fm;
-            if (side == 1) flo *= 0.5;
-            side = 1;
+            xn = std::fmin(std::fmax(xn, x - kMaxStep), x + kMaxStep);
         }
-        if (std::fabs(fm) <= 1e-14 * target) return mid;
+        if (std::fabs(xn - x) <= 1e-15 * std::fmax(1.0, std::fabs(x))) return std::exp(xn);
+        x = xn;
     }
-    return 0.5 * (lo + hi);
+    return std::exp(x);
 }
 
 }  // namespace gg

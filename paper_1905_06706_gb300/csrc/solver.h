@@ -27,7 +27,8 @@ class DegreeModel {
     bool valid(double K) const;
     // the largest threshold that is valid at K
     double needed_threshold(double K) const;
-    double f(double K) const;
+    // f(K); with slope, also K f'(K)
+    double f(double K, double* slope = nullptr) const;
     // K with f(K) = target; fetch(t) must call set_split with a threshold <= t
     double solve(double target, const std::function<void(double)>& fetch);
 
