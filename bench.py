@@ -63,6 +63,27 @@ def kernel_source_digest() -> str:
     return h.hexdigest()[:16]
 
 
+def _ncu_metric(kernel: str, metric: str):
+    """A metric of `kernel` from its committed ncu summary, when the summary was taken
+    from the current source of the sampling kernels (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_girg_d2_n1e6.md")
+    try:
+        text = open(path).read()
+        if f"kernel-source-sha256 {kernel_source_digest()}" not in text:
+            return None
+        for ln in text.splitlines():
+            if f"(`{metric}`)" in ln:
+                return float(ln.split("|")[2].split()[0])
+    except (OSError, ValueError, IndexError):
+        pass
+    return None
+
+
+# Instruction issue peak of the GPU: 4 warp schedulers per SM, each issuing at most one
+# warp instruction per cycle, 152 SMs, 2070 MHz maximum SM clock.
+ISSUE_PEAK = 4 * 152 * 2.07e9
+
+
 def _ncu_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, when the
     summary was taken from the current source of the sampling kernels (else None)."""
@@ -451,6 +472,17 @@ def main():
                 "peak_kind": peak_kind, "algorithmic_bytes": kbytes, "launch_ms": kms}
         if roof["achieved"] is not None:
             roof["frac"] = roof["achieved"] / hbm
+        # what actually bounds the sampling kernels: instruction issue (warp instructions
+        # per launch from the committed ncu summary over the live launch duration)
+        winst = _ncu_metric(kname, "smsp__inst_executed.sum")
+        issue_roof = {"kernel": kname, "bound": "alu", "unit": "warp instructions/s",
+                      "peak": ISSUE_PEAK,
+                      "peak_kind": "derived: 4 schedulers x 152 SMs x 2070 MHz",
+                      "warp_instructions": winst,
+                      "achieved": (winst / (kms / 1e3)) if (winst and kms > 0) else None}
+        if issue_roof["achieved"] is not None:
+            issue_roof["frac"] = issue_roof["achieved"] / ISSUE_PEAK
+        samp_ms = ph["enumerate"] + ph["type1"] + ph["type2"]
         edge_roof = (m_step * eb / (statistics.mean(ms) / 1e3)) / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
@@ -482,6 +514,11 @@ def main():
             "roofline": roof,
             "edge_output_roofline": {"achieved": edge_roof, "peak": hbm, "unit": "GB/s",
                                      "frac": edge_roof / hbm},
+            "issue_roofline": issue_roof,
+            "sampling_only": {"value": m_step / (samp_ms / 1e3) if samp_ms > 0 else None,
+                              "unit": "edges/s", "ms_per_step": samp_ms,
+                              "note": "cell-pair enumeration, type I and type II (a3-a7) "
+                                      "from the sorted points, device events"},
             "phases_ms": ph,
             "stats": stats,
             "gpu_launches": int(stats.get("kernel_launches", 0)) * args.steps,
