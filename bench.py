@@ -459,7 +459,7 @@ def main():
         algo = {
             "k_type1": (24 * stats["type1_items"] + vrec * stats["type1_vertex_refs"] +
                         eb * stats["type1_edges"], ph["type1"]),
-            "k_type2": (48 * stats["type2_streams"] +
+            "k_type2": (56 * stats["type2_streams"] +
                         (8 + 2 * vrec) * stats["type2_candidates"] + eb * t2_edges,
                         ph["type2"]),
         }

@@ -34,7 +34,7 @@ struct T1Item {
 // A type-II stream: geometric jumps over V_i^A x (V_j^B1 ++ V_j^B2 ++ ...), the
 // distant partner cells B of A with one gap g, in increasing rank; the partner
 // sets are seg_cnt entries of the segment pool from seg_off.
-struct Stream {
+struct alignas(16) Stream {
     uint32_t A;
     uint32_t pack;  // l | i << 5 | j << 11 | (g - 1) << 17 | kTagJump << 18
     uint32_t a_begin, a_len;
@@ -43,8 +43,10 @@ struct Stream {
     uint32_t tii;   // index of its TwoEntry
     uint32_t s0;    // single-chunk streams: offset of the first candidate (draw 0),
                     // already drawn by the enumeration; 0xffffffff otherwise
-    uint32_t pad;
+    float invLb, log2pbar;  // copies of its TwoEntry's fast-path fields
+    uint32_t kone;          // its TwoEntry's k | one << 8
 };
+static_assert(sizeof(Stream) == 48, "stream record layout");
 // Work beyond the enumeration is balanced through exclusive prefixes: of the
 // pairs of the type-I items and of the chunks of the type-II streams.  A warp
 // takes the next range of pairs (chunks) from a 64-bit counter and finds the

@@ -683,7 +683,8 @@ __global__ void __launch_bounds__(kEnumThreads, 4) k_enum2(DevCfg cfg) {
                 if (!keep[g]) continue;
                 if (st_base < cfg.stream_cap) {
                     // chunks of 2^k indices; a stream needing 2^32 or more is an error
-                    const int k = cfg.tii[tidx[g]].k;
+                    const TwoEntry te = cfg.tii[tidx[g]];
+                    const int k = te.k;
                     const unsigned long long tot = (unsigned long long)x.a_len * sum[g];
                     unsigned long long nch = (tot + (1ull << k) - 1) >> k;
                     if (nch > 0xffffffffull) {
@@ -701,7 +702,9 @@ __global__ void __launch_bounds__(kEnumThreads, 4) k_enum2(DevCfg cfg) {
                     st.S = sum[g];
                     st.tii = tidx[g];
                     st.s0 = s0[g];
-                    st.pad = 0;
+                    st.invLb = te.invLb;
+                    st.log2pbar = te.log2pbar;
+                    st.kone = (uint32_t)te.k | (te.one ? 0x100u : 0u);
                     cfg.streams[st_base] = st;
                 }
                 ++st_base;
@@ -1071,13 +1074,13 @@ __global__ void __launch_bounds__(kT2Threads, 4) k_type2(DevCfg cfg) {
                 const uint32_t hh = __shfl_sync(0xffffffffu, bh, src);
                 if (((idle >> lane) & 1u) && r < take) {
                     st = cfg.streams[q];
-                    const TwoEntry te = cfg.tii[st.tii];
-                    e = TwoFast{te.invLb, te.log2pbar, st.tii, te.one != 0};
+                    e = TwoFast{st.invLb, st.log2pbar, st.tii, (st.kone >> 8) != 0u};
+                    const int kc = (int)(st.kone & 0xffu);
                     const unsigned long long tot = (unsigned long long)st.a_len * st.S;
                     small = tot <= 0xffffffffull;
                     h = hh;
-                    start = (unsigned long long)h << te.k;
-                    len = tot - start < (1ull << te.k) ? tot - start : (1ull << te.k);
+                    start = (unsigned long long)h << kc;
+                    len = tot - start < (1ull << kc) ? tot - start : (1ull << kc);
                     t = 0;
                     s = -1;
                     resumed = st.s0 != 0xffffffffu;
@@ -1133,12 +1136,27 @@ __global__ void __launch_bounds__(kT2Threads, 4) k_type2(DevCfg cfg) {
                     ia = (uint32_t)(idx / st.S);
                     ib = (uint32_t)(idx - (unsigned long long)ia * st.S);
                 }
-                uint32_t lo = 0, hi = st.seg_cnt;  // last partner set with pre <= ib
-                while (hi - lo > 1) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (cfg.segs[st.seg_off + mid].pre <= ib) lo = mid; else hi = mid;
+                // the last partner set with pre <= ib: up to 4 segments loaded at once
+                // (one dependent load), else a binary search
+                const Seg* sp = cfg.segs + st.seg_off;
+                Seg sg;
+                if (st.seg_cnt <= 4) {
+                    Seg s1{0u, 0xffffffffu}, s2{0u, 0xffffffffu}, s3{0u, 0xffffffffu};
+                    sg = sp[0];
+                    if (st.seg_cnt > 1) s1 = sp[1];
+                    if (st.seg_cnt > 2) s2 = sp[2];
+                    if (st.seg_cnt > 3) s3 = sp[3];
+                    if (s1.pre <= ib) sg = s1;
+                    if (s2.pre <= ib) sg = s2;
+                    if (s3.pre <= ib) sg = s3;
+                } else {
+                    uint32_t lo = 0, hi = st.seg_cnt;
+                    while (hi - lo > 1) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (sp[mid].pre <= ib) lo = mid; else hi = mid;
+                    }
+                    sg = sp[lo];
                 }
-                const Seg sg = cfg.segs[st.seg_off + lo];
                 pu = st.a_begin + ia;
                 pv = sg.b_begin + (ib - sg.pre);
                 edge = accept_t2_fast<DIM>(cfg, V, pu, pv, o.z, o.w, e, C);
