@@ -187,8 +187,9 @@ def _edge_args(edges):
 
 def girg_generate(edges, *, n, d, beta, T, avg_deg=0.0, c=0.0, w_min=1.0, seed=1,
                   precision=PRECISION_FP32, level_cap=0, stream=None) -> Result:
-    """Generate a GIRG into ``edges`` (CUDA tensor (cap, 2) of int32 or int64; None:
-    count-only, see ``last_stats()['edge_checksum']``)."""
+    """Generate a GIRG into ``edges`` ((cap, 2) tensor of int32 or int64: on the GPU, or
+    a pinned CPU tensor that the kernels fill directly; None: count-only, see
+    ``last_stats()['edge_checksum']``)."""
     _torch()
     lib = load()
     eb, ep, cap = _edge_args(edges)

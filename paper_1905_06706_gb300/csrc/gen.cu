@@ -208,14 +208,17 @@ __device__ __forceinline__ bool last_block(unsigned int* ticket) {
 __device__ void top_threshold(Reduce* __restrict__ red, const double* __restrict__ part_s2,
                               int nb, int64_t n, int d, double T, double target, int E0,
                               double* __restrict__ thr) {
-    const double s2 = block_ordered_sum(part_s2, nb);
+    __shared__ unsigned long long s_wmax;  // bits of the largest weight (positive doubles
+                                           // order like their bit patterns)
+    if (threadIdx.x == 0) s_wmax = 0ull;
+    const double s2 = block_ordered_sum(part_s2, nb);  // synchronises the block
+    if (threadIdx.x < 64 && __ldcg(&red->cnt[threadIdx.x]))
+        atomicMax(&s_wmax, __ldcg(&red->wmax[threadIdx.x]));
+    __syncthreads();
     if (threadIdx.x != 0) return;
     red->s2 = s2;
     const double W = ldexp((double)__ldcg(&red->sum_hi) * 0x1p64 + (double)__ldcg(&red->sum_lo), E0);
-    double wmax = 0.0;
-    for (int i = 0; i < 64; ++i)
-        if (__ldcg(&red->cnt[i]))
-            wmax = fmax(wmax, __longlong_as_double((long long)__ldcg(&red->wmax[i])));
+    const double wmax = __longlong_as_double((long long)s_wmax);
     const double K0 = target * (double)n * W * (T > 0.0 ? 1.0 - T : 1.0) /
                       (ldexp(W * W - s2, d));
     const double margin = T >= 0.7 ? 2.8 : 1.4;
@@ -269,13 +272,18 @@ __global__ void k_split_weights(int64_t n, const double* __restrict__ w,
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) acc += s[threadIdx.x][i];
         part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = acc;
     }
-    // the four sums in block order, by the last block
+    // the four sums in a fixed order, by the last block: 64 threads per sum, each over
+    // every 64th partial, then a fixed tree within the group
     if (last_block(&count[2])) {
-        const int nb = gridDim.x;
-        for (int q = 0; q < 4; ++q) {
-            const double v = block_ordered_sum(part + (size_t)q * nb, nb);
-            if (threadIdx.x == 0) sums[q] = v;
-        }
+        static_assert(sizeof(s) >= 8 * sizeof(double), "group results fit the block buffer");
+        const int nb = gridDim.x, q = threadIdx.x >> 6, g = threadIdx.x & 63;
+        double a = 0.0;
+        for (int i = g; i < nb; i += 64) a += __ldcg(part + (size_t)q * nb + i);
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        __syncthreads();  // s is reused
+        if ((threadIdx.x & 31) == 0) s[0][threadIdx.x >> 5] = a;  // 8 warp results
+        __syncthreads();
+        if (threadIdx.x < 4) sums[threadIdx.x] = s[0][2 * threadIdx.x] + s[0][2 * threadIdx.x + 1];
     }
 }
 
