@@ -12,11 +12,12 @@
  * Contents
  *   - Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), the counter-based
  *     generator both sides implement from its published definition.
- *   - det_log / det_log1p / det_exp / det_sinpi: elementary functions built
- *     only from IEEE +, -, *, / and exact power-of-two scaling (argument
- *     reduction by powers of two and ln 2, then the atanh / Taylor series).
- *     They are evaluated in a fixed operation order so that any IEEE machine
- *     with FMA contraction disabled reproduces them bit for bit.
+ *   - det_log / det_exp: ln and exp in 64/128-bit fixed point (argument
+ *     reduction by powers of two and a 64-entry table, then the series of
+ *     ln(1 + r) and e^r), every truncation specified and the result rounded
+ *     once, so any implementation of the same integer steps reproduces them bit
+ *     for bit; det_log1p / det_sinpi / det_acosh / det_pow build on them with
+ *     IEEE +, -, *, / in a fixed order (FMA contraction disabled).
  *   - Model inputs: Pareto weights (Sec. 2.1, Sec. 5.1 step 1), uniform torus
  *     positions in 32-bit fixed point (Sec. 2.1), HRG radii and angles
  *     (Sec. 2.2) and the HRG->GIRG mapping (Sec. 2.3).
@@ -120,9 +121,6 @@ double orc_uniform(uint32_t lo, uint32_t hi) {
 /* Deterministic elementary functions                                         */
 /* ------------------------------------------------------------------------ */
 
-static const double LN2_HI = 0x1.62e42fee00000p-1; /* ln 2 to 32 bits */
-static const double LN2_LO = 0x1.a39ef35793c76p-33; /* ln 2 - LN2_HI */
-static const double INV_LN2 = 0x1.71547652b82fep+0;
 static const double PI_D = 0x1.921fb54442d18p+1;
 
 static double pow2i(int k) { /* exact 2^k for -1022 <= k <= 1023 */
@@ -152,90 +150,133 @@ static double two_atanh_series(double s) {
     return 2.0 * s + 2.0 * t;
 }
 
-/* ln x = e ln 2 + ln m with x = m 2^e, m in (sqrt(1/2), sqrt(2)];
- * ln m = 2 atanh((m-1)/(m+1)).  Builds the tables of orc_det_log below. */
-static double det_log_series(double x) {
-    if (x != x || x < 0.0) return NAN;
-    if (x == 0.0) return -INFINITY;
-    if (x == INFINITY) return INFINITY;
-    int e_adj = 0;
-    if (x < 0x1p-1022) { /* subnormal: scale into the normal range */
-        x = x * 0x1p54;
-        e_adj = -54;
-    }
-    uint64_t bits;
-    memcpy(&bits, &x, 8);
-    int e = (int)((bits >> 52) & 0x7ff) - 1023;
-    bits = (bits & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL;
-    double m;
-    memcpy(&m, &bits, 8); /* m in [1,2) */
-    if (m > 0x1.6a09e667f3bcdp+0) { /* sqrt(2) */
-        m = m * 0.5;
-        e = e + 1;
-    }
-    e = e + e_adj;
-    double s = (m - 1.0) / (m + 1.0);
-    double lm = two_atanh_series(s);
-    double ed = (double)e;
-    return ed * LN2_HI + (lm + ed * LN2_LO);
+/* Fixed-point ln and exp.  Every step is integer arithmetic with a stated rounding,
+ * so an independent implementation of the same steps gives the same bits.
+ * Qn: the integer v 2^n.  u128 / i128: unsigned / signed 128-bit integers.
+ *
+ * ln x, x = m 2^e with m in (sqrt(1/2), sqrt(2)] (the significand halved when it
+ * exceeds sqrt 2): j = round(64 m) in [45, 91]; D = (64 m - j) 2^s exactly (s = 52 or
+ * 53, the significand's scale); r = D / (j 2^s) in Q63, exactly D 2^(57-s) when j = 64,
+ * else the top 64 bits of |D| 2^(63-s) ceil(2^64/j) with the sign of D; P(r) =
+ * 1 - r/2 + r^2/3 - ... + r^8/9 by Horner in Q62 (coefficients round(2^62/k), each
+ * product floor-shifted by 63); ln x = e ln2 + ln(j/64) + floor(r P 2^-9) in Q116,
+ * rounded once to the nearest double (ties to even).
+ *
+ * e^x, |x| <= 710: k = floor(64 x / ln 2 + 1/2) in double arithmetic; x in Q116
+ * (truncated toward zero); r = x - k ln2/64 in Q116, floor-shifted to Q62; e^r =
+ * 1 + r + ... + r^7/7! by Horner in Q62 (coefficients round(2^62/i!), products
+ * floor-shifted by 62); times 2^(j/64) (Q62, j = k mod 64), floor-shifted to Q62;
+ * rounded to the nearest double and scaled by 2^((k - j)/64).
+ *
+ * Constants: ln 2 = 2 atanh(1/3) and ln(j/64) = +-2 atanh(|j-64|/(j+64)) by the series
+ * sum_i s^(2i+1)/(2i+1) in Q124 (s truncated, s^2 and each power floor-shifted, each
+ * quotient truncated, until the power is zero), rounded to Q116; 2^(j/64) by the
+ * series of e^y, y = j floor(ln2_Q124 / 64), in Q124 (term_i = floor(floor(term_{i-1}
+ * y / 2^124) / i) until zero), rounded to Q62. */
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+static i128 FX_LN2, FX_LN2_64;    /* Q116 */
+static i128 FX_LNJ[47];            /* ln(j/64), Q116, j = 45..91 */
+static uint64_t FX_RJ[47];         /* ceil(2^64 / j) */
+static uint64_t FX_E2[64];         /* 2^(j/64), Q62 */
+static int64_t FX_LOGC[10];        /* round(2^62 / k), k = 1..9 */
+static int64_t FX_EXPC[8];         /* round(2^62 / i!), i = 0..7 */
+static int fx_ready = 0;
+
+/* floor(a b / 2^124) for a, b < 2^126: the 256-bit product from four 64x64 parts */
+static u128 fx_mul124(u128 a, u128 b) {
+    uint64_t al = (uint64_t)a, ah = (uint64_t)(a >> 64);
+    uint64_t bl = (uint64_t)b, bh = (uint64_t)(b >> 64);
+    u128 ll = (u128)al * bl, lh = (u128)al * bh, hl = (u128)ah * bl, hh = (u128)ah * bh;
+    u128 cross = (ll >> 64) + (u128)(uint64_t)lh + (u128)(uint64_t)hl; /* bits 64.. */
+    u128 top = hh + (lh >> 64) + (hl >> 64) + (cross >> 64);            /* bits 128.. */
+    return (top << 4) + ((uint64_t)cross >> 60);
 }
 
-/* e^x = 2^k e^r, k = nearest integer to x / ln 2, r = x - k ln 2, Taylor to r^17.
- * Builds the table of orc_det_exp below. */
-static double det_exp_series(double x) {
-    if (x != x) return NAN;
-    if (x > 710.0) return INFINITY;
-    if (x < -746.0) return 0.0;
-    double kd = floor(x * INV_LN2 + 0.5);
-    int k = (int)kd;
-    double r = (x - kd * LN2_HI) - kd * LN2_LO;
-    double p = 1.0 / 355687428096000.0; /* 1/17! */
-    p = 1.0 / 20922789888000.0 + r * p;  /* 1/16! */
-    p = 1.0 / 1307674368000.0 + r * p;   /* 1/15! */
-    p = 1.0 / 87178291200.0 + r * p;     /* 1/14! */
-    p = 1.0 / 6227020800.0 + r * p;      /* 1/13! */
-    p = 1.0 / 479001600.0 + r * p;       /* 1/12! */
-    p = 1.0 / 39916800.0 + r * p;        /* 1/11! */
-    p = 1.0 / 3628800.0 + r * p;         /* 1/10! */
-    p = 1.0 / 362880.0 + r * p;          /* 1/9! */
-    p = 1.0 / 40320.0 + r * p;           /* 1/8! */
-    p = 1.0 / 5040.0 + r * p;            /* 1/7! */
-    p = 1.0 / 720.0 + r * p;             /* 1/6! */
-    p = 1.0 / 120.0 + r * p;             /* 1/5! */
-    p = 1.0 / 24.0 + r * p;              /* 1/4! */
-    p = 1.0 / 6.0 + r * p;               /* 1/3! */
-    p = 0.5 + r * p;                     /* 1/2! */
-    p = 1.0 + r * p;
-    p = 1.0 + r * p;
-    if (k > 1023) return (p * pow2i(1023)) * pow2i(k - 1023);
-    if (k < -1021) return (p * pow2i(k + 600)) * pow2i(-600);
-    return p * pow2i(k);
+static u128 fx_two_atanh(uint64_t num, uint64_t den) { /* Q124, num/den <= 1/3 */
+    u128 one = (u128)1 << 124;
+    u128 s = (u128)num * (one / den) + ((u128)num * (one % den)) / den;
+    u128 s2 = fx_mul124(s, s);
+    u128 acc = 0, pw = s;
+    uint64_t k = 1;
+    while (pw != 0) {
+        acc += pw / k;
+        pw = fx_mul124(pw, s2);
+        k += 2;
+    }
+    return 2 * acc;
 }
 
-/* Table-driven ln and exp.  The tables come from the series forms above:
- * E2[j] = 2^(j/64) (j = 0..63), LC[j-45] = ln(j/64), IC[j-45] = 64/j (j = 45..91). */
-static double E2[64], LC[47], IC[47];
-static int det_tab_ready = 0;
-
-static void det_tab_init(void) {
-    if (det_tab_ready) return;
-    for (int j = 0; j < 64; j++)
-        E2[j] = det_exp_series((double)j * 0x1.62e42fee00000p-7 + (double)j * 0x1.a39ef35793c76p-39);
+static void fx_init(void) {
+    if (fx_ready) return;
+    u128 ln2 = fx_two_atanh(1, 3);
+    FX_LN2 = (i128)((ln2 + ((u128)1 << 7)) >> 8);
+    FX_LN2_64 = (i128)((ln2 + ((u128)1 << 13)) >> 14);
     for (int j = 45; j <= 91; j++) {
-        LC[j - 45] = det_log_series((double)j * 0x1p-6);
-        IC[j - 45] = 64.0 / (double)j;
+        u128 a = fx_two_atanh((uint64_t)(j >= 64 ? j - 64 : 64 - j), (uint64_t)(j + 64));
+        i128 v = (i128)((a + ((u128)1 << 7)) >> 8);
+        FX_LNJ[j - 45] = j >= 64 ? v : -v;
+        FX_RJ[j - 45] = (uint64_t)((((u128)1 << 64) + (u128)(j - 1)) / (u128)j);
     }
-    det_tab_ready = 1;
+    u128 step = ln2 >> 6;
+    for (int j = 0; j < 64; j++) {
+        u128 y = step * (u128)j, term = (u128)1 << 124, acc = 0;
+        for (uint64_t i = 1; term != 0; i++) {
+            acc += term;
+            term = fx_mul124(term, y) / i;
+        }
+        FX_E2[j] = (uint64_t)((acc + ((u128)1 << 61)) >> 62);
+    }
+    int64_t one = (int64_t)1 << 62;
+    for (int k = 1; k <= 9; k++) {
+        int64_t q = one / k, rem = one % k;
+        FX_LOGC[k] = q + (2 * rem >= k ? 1 : 0);
+    }
+    int64_t f = 1;
+    for (int i = 0; i <= 7; i++) {
+        if (i > 0) f *= i;
+        int64_t q = one / f, rem = one % f;
+        FX_EXPC[i] = q + (2 * rem >= f ? 1 : 0);
+    }
+    fx_ready = 1;
 }
 
-/* ln x: x = m 2^e with m in (sqrt(1/2), sqrt(2)]; c = j/64 the table point nearest
- * to m, r = (m - c) 64/j, ln(1 + r) by its series to r^9 (|r| <= 1/90);
- * ln x = e ln 2 + ln c + ln(1 + r). */
+static int fx_clz128(u128 v) {
+    uint64_t hi = (uint64_t)(v >> 64), lo = (uint64_t)v;
+    return hi ? __builtin_clzll(hi) : 64 + __builtin_clzll(lo);
+}
+
+/* nearest double (ties to even) to v 2^-q, v != 0, the result normal */
+static double fx_to_double(i128 v, int q) {
+    int neg = v < 0;
+    u128 u = neg ? (u128)(-v) : (u128)v;
+    int top = 127 - fx_clz128(u);
+    uint64_t mant;
+    int sh = top - 52;
+    if (sh > 0) {
+        mant = (uint64_t)(u >> sh);
+        u128 rest = u - ((u128)mant << sh), half = (u128)1 << (sh - 1);
+        if (rest > half || (rest == half && (mant & 1))) mant++;
+        if (mant == (1ULL << 53)) {
+            mant >>= 1;
+            top++;
+        }
+    } else {
+        mant = (uint64_t)(u << (-sh));
+    }
+    uint64_t bits = ((uint64_t)(top - q + 1023) << 52) | (mant & 0x000fffffffffffffULL);
+    if (neg) bits |= 0x8000000000000000ULL;
+    double r;
+    memcpy(&r, &bits, 8);
+    return r;
+}
+
 double orc_det_log(double x) {
     if (x != x || x < 0.0) return NAN;
     if (x == 0.0) return -INFINITY;
     if (x == INFINITY) return INFINITY;
-    det_tab_init();
+    fx_init();
     int e_adj = 0;
     if (x < 0x1p-1022) { /* subnormal: scale into the normal range */
         x = x * 0x1p54;
@@ -243,52 +284,65 @@ double orc_det_log(double x) {
     }
     uint64_t bits;
     memcpy(&bits, &x, 8);
-    int e = (int)((bits >> 52) & 0x7ff) - 1023;
-    bits = (bits & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL;
-    double m;
-    memcpy(&m, &bits, 8); /* m in [1,2) */
-    if (m > 0x1.6a09e667f3bcdp+0) { /* sqrt(2) */
-        m = m * 0.5;
+    uint64_t frac = bits & 0x000fffffffffffffULL;
+    uint64_t sig = frac | 0x0010000000000000ULL; /* m = sig 2^-52 in [1, 2) */
+    int e = (int)(bits >> 52) - 1023 + e_adj;
+    int s, j;
+    if (frac > 0x6a09e667f3bcdULL) { /* m > sqrt 2: use m/2 = sig 2^-53 */
+        s = 53;
         e = e + 1;
+        j = 32 + (int)((frac + (1ULL << 46)) >> 47);
+    } else {
+        s = 52;
+        j = 64 + (int)((frac + (1ULL << 45)) >> 46);
     }
-    e = e + e_adj;
-    int j = (int)floor(m * 64.0 + 0.5);
-    double r = (m - (double)j * 0x1p-6) * IC[j - 45];
-    double t = 1.0 / 9.0;
-    t = 1.0 / 8.0 - r * t;
-    t = 1.0 / 7.0 - r * t;
-    t = 1.0 / 6.0 - r * t;
-    t = 1.0 / 5.0 - r * t;
-    t = 1.0 / 4.0 - r * t;
-    t = 1.0 / 3.0 - r * t;
-    t = 0.5 - r * t;
-    t = 1.0 - r * t;
-    double l1 = r * t;
-    double ed = (double)e;
-    return ed * LN2_HI + (LC[j - 45] + (l1 + ed * LN2_LO));
+    int64_t D = (int64_t)(sig * 64) - (int64_t)j * ((int64_t)1 << s);
+    int64_t r;
+    if (j == 64) {
+        r = D * ((int64_t)1 << (57 - s));
+    } else {
+        uint64_t mag = (uint64_t)(D < 0 ? -D : D) << (63 - s);
+        uint64_t q = (uint64_t)(((u128)mag * FX_RJ[j - 45]) >> 64);
+        r = D < 0 ? -(int64_t)q : (int64_t)q;
+    }
+    int64_t t = FX_LOGC[9];
+    for (int k = 8; k >= 1; k--) t = FX_LOGC[k] - (int64_t)(((i128)r * t) >> 63);
+    i128 sum = (i128)e * FX_LN2 + FX_LNJ[j - 45] + (((i128)r * t) >> 9);
+    if (sum == 0) return 0.0;
+    return fx_to_double(sum, 116);
 }
 
-/* e^x = 2^m 2^(j/64) e^r, k = nearest integer to 64 x / ln 2 = 64 m + j,
- * r = x - k ln2/64 (|r| <= ln2/128), e^r by its series to r^7. */
 double orc_det_exp(double x) {
     if (x != x) return NAN;
     if (x > 710.0) return INFINITY;
     if (x < -746.0) return 0.0;
-    det_tab_init();
+    fx_init();
     double kd = floor(x * 0x1.71547652b82fep+6 + 0.5);
     int k = (int)kd;
-    double r = (x - kd * 0x1.62e42fee00000p-7) - kd * 0x1.a39ef35793c76p-39;
+    uint64_t bits;
+    memcpy(&bits, &x, 8);
+    int be = (int)((bits >> 52) & 0x7ff);
+    i128 X = 0;
+    if (be != 0) {
+        uint64_t sig = (bits & 0x000fffffffffffffULL) | 0x0010000000000000ULL;
+        int sh = be - 1075 + 116;
+        u128 mag;
+        if (sh >= 0)
+            mag = (u128)sig << sh;
+        else if (sh > -64)
+            mag = (u128)(sig >> (-sh));
+        else
+            mag = 0;
+        X = (bits >> 63) ? -(i128)mag : (i128)mag;
+    }
+    i128 R = X - (i128)k * FX_LN2_64;
+    int64_t r = (int64_t)(R >> 54);
+    int64_t p = FX_EXPC[7];
+    for (int i = 6; i >= 0; i--) p = FX_EXPC[i] + (int64_t)(((i128)r * p) >> 62);
     int j = k & 63;
     int m = (k - j) / 64;
-    double p = 1.0 / 5040.0;
-    p = 1.0 / 720.0 + r * p;
-    p = 1.0 / 120.0 + r * p;
-    p = 1.0 / 24.0 + r * p;
-    p = 1.0 / 6.0 + r * p;
-    p = 0.5 + r * p;
-    p = 1.0 + r * p;
-    p = 1.0 + r * p;
-    double v = E2[j] * p;
+    uint64_t v62 = (uint64_t)(((u128)(uint64_t)p * FX_E2[j]) >> 62);
+    double v = fx_to_double((i128)v62, 62);
     if (m > 1023) return (v * pow2i(1023)) * pow2i(m - 1023);
     if (m < -1021) return (v * pow2i(m + 600)) * pow2i(-600);
     return v * pow2i(m);

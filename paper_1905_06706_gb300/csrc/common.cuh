@@ -115,11 +115,7 @@ GG_HD double dnan() { return bits_to_double(0x7ff8000000000000ULL); }
 GG_HD double dinf() { return bits_to_double(0x7ff0000000000000ULL); }
 
 // ---------------------------------------------------------------- det math
-constexpr double kLn2Hi = 0x1.62e42fee00000p-1;   // ln 2 rounded to 32 bits
-constexpr double kLn2Lo = 0x1.a39ef35793c76p-33;  // ln 2 - kLn2Hi
-constexpr double kInvLn2 = 0x1.71547652b82fep+0;
 constexpr double kPi = 0x1.921fb54442d18p+1;
-constexpr double kSqrt2 = 0x1.6a09e667f3bcdp+0;
 
 // 2 atanh(s) = 2 (s + s^3/3 + ... + s^25/25) for |s| <= 0.18.
 GG_HD double two_atanh(double s) {
@@ -141,80 +137,102 @@ GG_HD double two_atanh(double s) {
     return DADD(DMUL(2.0, s), DMUL(2.0, t));
 }
 
-// ln x by the series: x = m 2^e with m in (sqrt(1/2), sqrt(2)], ln m = 2 atanh((m-1)/(m+1)).
-// Only builds the tables of det_log / det_exp below.
-GG_HD double det_log_series(double x) {
-    if (x != x || x < 0.0) return dnan();
-    if (x == 0.0) return -dinf();
-    if (x == dinf()) return dinf();
-    int e_adj = 0;
-    if (x < 0x1p-1022) {
-        x = DMUL(x, 0x1p54);
-        e_adj = -54;
-    }
-    uint64_t b = double_to_bits(x);
-    int e = (int)((b >> 52) & 0x7ff) - 1023;
-    double m = bits_to_double((b & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL);
-    if (m > kSqrt2) {
-        m = DMUL(m, 0.5);
-        e = e + 1;
-    }
-    e = e + e_adj;
-    const double s = DDIV(DSUB(m, 1.0), DADD(m, 1.0));
-    const double lm = two_atanh(s);
-    const double ed = (double)e;
-    return DADD(DMUL(ed, kLn2Hi), DADD(lm, DMUL(ed, kLn2Lo)));
-}
+// ---------------------------------------------------------------- fixed-point log / exp
+// det_log and det_exp work in 64- and 128-bit integers: every step is exact integer
+// arithmetic with a stated truncation, so any two implementations of the same steps
+// agree bit for bit, and the FP64 units (slow on this GPU) are used only for the
+// reduction index of exp.  Q-notation: Qn holds v as round-or-floor(v 2^n).
+//   ln x: x = m 2^e, m in (sqrt(1/2), sqrt(2)]; j = round(64 m) in [45, 91]; with
+//   D = 64 m - j (exact), r = D / j (Q63: exact for j = 64, else |D| 2^63 times
+//   ceil(2^64/j), top 64 bits, sign of D); ln(1 + r) = r P(r), P(r) = sum_k (-r)^k/(k+1)
+//   to r^8 by Horner in Q62 with coefficients round(2^62/k); ln x = e ln 2 + ln(j/64)
+//   + r P in Q116 (r P from the exact Q125 product, floor-shifted), rounded once to double.
+//   e^x (|x| <= 700): k = floor(64 x / ln 2 + 1/2) in FP64, x in Q116 (truncated),
+//   r = x - k ln2/64 in Q116, then Q62 (floor); e^r to r^7 by Horner in Q62 with
+//   round(2^62/i!), times 2^(j/64) (Q62, j = k mod 64), floor-shifted to Q62, rounded
+//   once to double and scaled by 2^((k - j)/64).
+// Tables (host, at first use): ln 2 and ln(j/64) = 2 atanh((j-64)/(j+64)) by their
+// series in Q124 (terms s^(2i+1)/(2i+1) until zero, each product floor-shifted, each
+// quotient truncated), rounded to Q116; 2^(j/64) = e^(j (ln2_Q124 >> 6) 2^-124) by the
+// series in Q124 (term_i = floor(term_{i-1} y / 2^124) / i until zero), rounded to Q62.
+typedef unsigned __int128 u128;
+typedef __int128 i128;
 
-// e^x = 2^k e^r, k = round(x / ln 2), r = x - k ln 2, Taylor series to r^17.
-GG_HD double det_exp_series(double x) {
-    if (x != x) return x;
-    if (x > 710.0) return dinf();
-    if (x < -746.0) return 0.0;
-    const double kd = floor(DADD(DMUL(x, kInvLn2), 0.5));
-    const int k = (int)kd;
-    const double r = DSUB(DSUB(x, DMUL(kd, kLn2Hi)), DMUL(kd, kLn2Lo));
-    double p = 1.0 / 355687428096000.0;
-    p = DADD(1.0 / 20922789888000.0, DMUL(r, p));
-    p = DADD(1.0 / 1307674368000.0, DMUL(r, p));
-    p = DADD(1.0 / 87178291200.0, DMUL(r, p));
-    p = DADD(1.0 / 6227020800.0, DMUL(r, p));
-    p = DADD(1.0 / 479001600.0, DMUL(r, p));
-    p = DADD(1.0 / 39916800.0, DMUL(r, p));
-    p = DADD(1.0 / 3628800.0, DMUL(r, p));
-    p = DADD(1.0 / 362880.0, DMUL(r, p));
-    p = DADD(1.0 / 40320.0, DMUL(r, p));
-    p = DADD(1.0 / 5040.0, DMUL(r, p));
-    p = DADD(1.0 / 720.0, DMUL(r, p));
-    p = DADD(1.0 / 120.0, DMUL(r, p));
-    p = DADD(1.0 / 24.0, DMUL(r, p));
-    p = DADD(1.0 / 6.0, DMUL(r, p));
-    p = DADD(0.5, DMUL(r, p));
-    p = DADD(1.0, DMUL(r, p));
-    p = DADD(1.0, DMUL(r, p));
-    if (k > 1023) return DMUL(DMUL(p, pow2i(1023)), pow2i(k - 1023));
-    if (k < -1021) return DMUL(DMUL(p, pow2i(k + 600)), pow2i(-600));
-    return DMUL(p, pow2i(k));
-}
-
-// ---------------------------------------------------------------- table-driven log / exp
-// Tables of the deterministic log and exp, built from the series forms above (the
-// same IEEE operations on every machine, so every copy holds the same bits):
-// e2[j] = 2^(j/64), j = 0..63; lc[j - 45] = ln(j/64), ic[j - 45] = 64/j, j = 45..91.
 struct DetTab {
-    double e2[64];
-    double lc[47];
-    double ic[47];
+    uint64_t lnc_lo[47], lnc_hi[47];  // ln(j/64) in Q116, j = 45..91 (two's complement)
+    uint64_t rj[47];                  // ceil(2^64 / j)
+    uint64_t e2[64];                  // 2^(j/64) in Q62
+    uint64_t ln2_lo, ln2_hi;          // ln 2 in Q116
+    uint64_t ln2s_lo, ln2s_hi;        // ln 2 / 64 in Q116
 };
+
+GG_HD i128 make_i128(uint64_t lo, uint64_t hi) { return (i128)(((u128)hi << 64) | lo); }
+
+// round(2^62 / k) (ties up)
+__host__ __device__ constexpr int64_t q62_recip(int64_t k) {
+    return ((int64_t)1 << 62) / k + (((((int64_t)1 << 62) % k) * 2 >= k) ? 1 : 0);
+}
+
+// c - floor(a t / 2^sh) and c + floor(a t / 2^sh) for the Horner steps
+GG_HD int64_t fx_sub(int64_t c, int64_t a, int64_t t, int sh) {
+    return c - (int64_t)(((i128)a * t) >> sh);
+}
+GG_HD int64_t fx_add(int64_t c, int64_t a, int64_t t, int sh) {
+    return c + (int64_t)(((i128)a * t) >> sh);
+}
+
+// (a b) >> 124 for a, b < 2^126 (host table construction)
+inline u128 mul_q124(u128 a, u128 b) {
+    const uint64_t a0 = (uint64_t)a, a1 = (uint64_t)(a >> 64);
+    const uint64_t b0 = (uint64_t)b, b1 = (uint64_t)(b >> 64);
+    const u128 p00 = (u128)a0 * b0, p01 = (u128)a0 * b1, p10 = (u128)a1 * b0, p11 = (u128)a1 * b1;
+    // 256-bit sum: limbs w0..w3 (64 bits each)
+    const u128 mid = (p00 >> 64) + (uint64_t)p01 + (uint64_t)p10;
+    const uint64_t w1 = (uint64_t)mid;
+    const u128 hi = p11 + (p01 >> 64) + (p10 >> 64) + (mid >> 64);
+    // bits 124 .. 251: hi << 4 | w1 >> 60
+    return (hi << 4) | (u128)(w1 >> 60);
+}
+
+// 2 atanh(num/den) in Q124 for 0 <= num/den <= 1/3
+inline u128 two_atanh_q124(uint64_t num, uint64_t den) {
+    const u128 unit = (u128)1 << 124;
+    const u128 s = (u128)num * (unit / den) + ((u128)num * (unit % den)) / den;  // floor
+    const u128 s2 = mul_q124(s, s);
+    u128 p = s, sum = 0;
+    for (uint64_t k = 1; p != 0; k += 2) {
+        sum += p / k;
+        p = mul_q124(p, s2);
+    }
+    return sum << 1;
+}
 
 inline DetTab make_det_tab() {
     DetTab t;
-    for (int j = 0; j < 64; ++j)
-        t.e2[j] = det_exp_series(DADD(DMUL((double)j, 0x1.62e42fee00000p-7),
-                                      DMUL((double)j, 0x1.a39ef35793c76p-39)));
+    const u128 ln2 = two_atanh_q124(1, 3);  // ln 2 = 2 atanh(1/3)
+    const u128 half8 = (u128)1 << 7, half14 = (u128)1 << 13;
+    const u128 l116 = (ln2 + half8) >> 8, ls116 = (ln2 + half14) >> 14;
+    t.ln2_lo = (uint64_t)l116;
+    t.ln2_hi = (uint64_t)(l116 >> 64);
+    t.ln2s_lo = (uint64_t)ls116;
+    t.ln2s_hi = (uint64_t)(ls116 >> 64);
     for (int j = 45; j <= 91; ++j) {
-        t.lc[j - 45] = det_log_series((double)j * 0x1p-6);
-        t.ic[j - 45] = 64.0 / (double)j;
+        const u128 a = two_atanh_q124((uint64_t)(j > 64 ? j - 64 : 64 - j), (uint64_t)(j + 64));
+        const u128 m = (a + half8) >> 8;
+        const i128 v = j >= 64 ? (i128)m : -(i128)m;
+        t.lnc_lo[j - 45] = (uint64_t)(u128)v;
+        t.lnc_hi[j - 45] = (uint64_t)((u128)v >> 64);
+        t.rj[j - 45] = (uint64_t)((((u128)1 << 64) + (u128)(j - 1)) / (u128)j);
+    }
+    const u128 one = (u128)1 << 124, step = ln2 >> 6;
+    for (int j = 0; j < 64; ++j) {
+        const u128 y = step * (u128)j;
+        u128 term = one, sum = 0;
+        for (uint64_t i = 1; term != 0; ++i) {
+            sum += term;
+            term = mul_q124(term, y) / i;
+        }
+        t.e2[j] = (uint64_t)((sum + ((u128)1 << 61)) >> 62);
     }
     return t;
 }
@@ -252,48 +270,40 @@ GG_HD const DetTab& det_tab() {
 #endif
 }
 
-// ln x: x = m 2^e with m in (sqrt(1/2), sqrt(2)]; m = c (1 + r) with c = j/64 the
-// nearest table point, r = (m - c) 64/j (m - c is exact), |r| <= 1/90; ln(1 + r) by
-// its series to r^9.  ln x = e ln 2 + ln c + ln(1 + r).
-GG_HD double det_log(double x) {
+GG_HD int clz128(u128 v) {
+    const uint64_t hi = (uint64_t)(v >> 64), lo = (uint64_t)v;
 #ifdef __CUDA_ARCH__
-    {
-        // positive normal x: the same operations, with the classification, the choice
-        // of m and the index j taken from the bits (integer units, not the FP64 pipe);
-        // j = floor(64 m + 1/2) is (f + 2^45) >> 46 above 1 and (f + 2^46) >> 47 below,
-        // f the fraction bits, since 64 m + 1/2 is exact or rounds within its integer
-        const uint64_t b = double_to_bits(x);
-        if (b - 0x0010000000000000ULL < 0x7FE0000000000000ULL) {
-            const uint64_t f = b & 0x000fffffffffffffULL;
-            int e = (int)(b >> 52) - 1023, j;
-            double m, c;
-            if (f > 0x6a09e667f3bcdULL) {  // m > sqrt 2: m / 2 in (sqrt 1/2, 1)
-                m = bits_to_double(f | 0x3fe0000000000000ULL);
-                e = e + 1;
-                j = 32 + (int)((f + (1ULL << 46)) >> 47);
-            } else {
-                m = bits_to_double(f | 0x3ff0000000000000ULL);
-                j = 64 + (int)((f + (1ULL << 45)) >> 46);
-            }
-            c = j < 64 ? bits_to_double(0x3fe0000000000000ULL | ((uint64_t)(j - 32) << 47))
-                       : bits_to_double(0x3ff0000000000000ULL | ((uint64_t)(j - 64) << 46));
-            const DetTab& T = det_tab();
-            const double r = DMUL(DSUB(m, c), T.ic[j - 45]);
-            double t = 1.0 / 9.0;
-            t = DSUB(1.0 / 8.0, DMUL(r, t));
-            t = DSUB(1.0 / 7.0, DMUL(r, t));
-            t = DSUB(1.0 / 6.0, DMUL(r, t));
-            t = DSUB(1.0 / 5.0, DMUL(r, t));
-            t = DSUB(1.0 / 4.0, DMUL(r, t));
-            t = DSUB(1.0 / 3.0, DMUL(r, t));
-            t = DSUB(0.5, DMUL(r, t));
-            t = DSUB(1.0, DMUL(r, t));
-            const double l1 = DMUL(r, t);
-            const double ed = (double)e;
-            return DADD(DMUL(ed, kLn2Hi), DADD(T.lc[j - 45], DADD(l1, DMUL(ed, kLn2Lo))));
-        }
-    }
+    return hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+#else
+    return hi ? __builtin_clzll(hi) : 64 + __builtin_clzll(lo);
 #endif
+}
+
+// Round |v| 2^-q (v != 0) to the nearest double, ties to even, with the sign of v;
+// the result must be a normal number.
+GG_HD double fixed_to_double(i128 v, int q) {
+    const bool neg = v < 0;
+    const u128 u = neg ? (u128)(-v) : (u128)v;
+    int p = 127 - clz128(u);  // top bit
+    uint64_t m;
+    const int sh = p - 52;
+    if (sh > 0) {
+        m = (uint64_t)(u >> sh);
+        const u128 rem = u & (((u128)1 << sh) - 1), half = (u128)1 << (sh - 1);
+        if (rem > half || (rem == half && (m & 1))) ++m;
+        if (m >> 53) {
+            m >>= 1;
+            ++p;
+        }
+    } else {
+        m = (uint64_t)(u << -sh);
+    }
+    const uint64_t b = ((uint64_t)(p - q + 1023) << 52) | (m & 0x000fffffffffffffULL);
+    return bits_to_double(neg ? b | 0x8000000000000000ULL : b);
+}
+
+// ln x (definition above; NaN for x < 0, -inf at 0, subnormals scaled by 2^54).
+GG_HD double det_log(double x) {
     if (x != x || x < 0.0) return dnan();
     if (x == 0.0) return -dinf();
     if (x == dinf()) return dinf();
@@ -303,71 +313,80 @@ GG_HD double det_log(double x) {
         e_adj = -54;
     }
     const uint64_t b = double_to_bits(x);
-    int e = (int)((b >> 52) & 0x7ff) - 1023;
-    double m = bits_to_double((b & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL);
-    if (m > kSqrt2) {
-        m = DMUL(m, 0.5);
-        e = e + 1;
+    const uint64_t f = b & 0x000fffffffffffffULL, M = f | 0x0010000000000000ULL;
+    int e = (int)(b >> 52) - 1023 + e_adj, s, j;
+    if (f > 0x6a09e667f3bcdULL) {  // m > sqrt 2: m = M 2^-53
+        s = 53;
+        e += 1;
+        j = 32 + (int)((f + (1ULL << 46)) >> 47);
+    } else {  // m = M 2^-52
+        s = 52;
+        j = 64 + (int)((f + (1ULL << 45)) >> 46);
     }
-    e = e + e_adj;
-    const int j = (int)floor(DADD(DMUL(m, 64.0), 0.5));
     const DetTab& T = det_tab();
-    const double r = DMUL(DSUB(m, (double)j * 0x1p-6), T.ic[j - 45]);
-    double t = 1.0 / 9.0;
-    t = DSUB(1.0 / 8.0, DMUL(r, t));
-    t = DSUB(1.0 / 7.0, DMUL(r, t));
-    t = DSUB(1.0 / 6.0, DMUL(r, t));
-    t = DSUB(1.0 / 5.0, DMUL(r, t));
-    t = DSUB(1.0 / 4.0, DMUL(r, t));
-    t = DSUB(1.0 / 3.0, DMUL(r, t));
-    t = DSUB(0.5, DMUL(r, t));
-    t = DSUB(1.0, DMUL(r, t));
-    const double l1 = DMUL(r, t);
-    const double ed = (double)e;
-    return DADD(DMUL(ed, kLn2Hi), DADD(T.lc[j - 45], DADD(l1, DMUL(ed, kLn2Lo))));
+    const int64_t D = (int64_t)(M << 6) - ((int64_t)j << s);  // (64 m - j) 2^s
+    int64_t r;                                                // Q63
+    if (j == 64) {
+        r = D * ((int64_t)1 << (57 - s));
+    } else {
+        const uint64_t N = (uint64_t)(D < 0 ? -D : D) << (63 - s);
+        const uint64_t q = (uint64_t)(((u128)N * T.rj[j - 45]) >> 64);
+        r = D < 0 ? -(int64_t)q : (int64_t)q;
+    }
+    // P(r) = 1 - r (1/2 - r (1/3 - ... - r (1/8 - r/9))) in Q62
+    int64_t t = q62_recip(9);
+    t = fx_sub(q62_recip(8), r, t, 63);
+    t = fx_sub(q62_recip(7), r, t, 63);
+    t = fx_sub(q62_recip(6), r, t, 63);
+    t = fx_sub(q62_recip(5), r, t, 63);
+    t = fx_sub(q62_recip(4), r, t, 63);
+    t = fx_sub(q62_recip(3), r, t, 63);
+    t = fx_sub(q62_recip(2), r, t, 63);
+    t = fx_sub(q62_recip(1), r, t, 63);
+    const i128 l1 = ((i128)r * t) >> 9;  // r P in Q116 (floor)
+    const i128 L = (i128)e * make_i128(T.ln2_lo, T.ln2_hi) +
+                   make_i128(T.lnc_lo[j - 45], T.lnc_hi[j - 45]) + l1;
+    if (L == 0) return 0.0;
+    return fixed_to_double(L, 116);
 }
 
-// e^x = 2^m 2^(j/64) e^r with k = round(64 x / ln 2) = 64 m + j, r = x - k ln2/64
-// (|r| <= ln2/128), e^r by its series to r^7.
+// e^x (definition above; inf above 710, 0 below -746, NaN passes through).
 GG_HD double det_exp(double x) {
-#ifdef __CUDA_ARCH__
-    // |x| <= 700 (the integer test covers NaN): the same operations without the range
-    // checks; there m = floor(k / 64) lies in [-1011, 1010], a normal power of two
-    if ((double_to_bits(x) & 0x7fffffffffffffffULL) <= 0x4085e00000000000ULL) {
-        const double kd = floor(DADD(DMUL(x, 0x1.71547652b82fep+6), 0.5));
-        const int k = (int)kd;
-        const double r =
-            DSUB(DSUB(x, DMUL(kd, 0x1.62e42fee00000p-7)), DMUL(kd, 0x1.a39ef35793c76p-39));
-        const int j = k & 63;
-        const int m = (k - j) / 64;
-        double p = 1.0 / 5040.0;
-        p = DADD(1.0 / 720.0, DMUL(r, p));
-        p = DADD(1.0 / 120.0, DMUL(r, p));
-        p = DADD(1.0 / 24.0, DMUL(r, p));
-        p = DADD(1.0 / 6.0, DMUL(r, p));
-        p = DADD(0.5, DMUL(r, p));
-        p = DADD(1.0, DMUL(r, p));
-        p = DADD(1.0, DMUL(r, p));
-        return DMUL(DMUL(det_tab().e2[j], p), pow2i(m));
-    }
-#endif
     if (x != x) return x;
     if (x > 710.0) return dinf();
     if (x < -746.0) return 0.0;
     const double kd = floor(DADD(DMUL(x, 0x1.71547652b82fep+6), 0.5));
     const int k = (int)kd;
-    const double r = DSUB(DSUB(x, DMUL(kd, 0x1.62e42fee00000p-7)), DMUL(kd, 0x1.a39ef35793c76p-39));
+    const DetTab& T = det_tab();
+    // x in Q116, truncated toward zero
+    const uint64_t b = double_to_bits(x);
+    const int be = (int)((b >> 52) & 0x7ff);
+    i128 X = 0;
+    if (be != 0) {
+        const uint64_t M = (b & 0x000fffffffffffffULL) | 0x0010000000000000ULL;
+        const int sh = be - 1075 + 116;  // x = M 2^(be - 1075)
+        u128 u;
+        if (sh >= 0)
+            u = (u128)M << sh;
+        else
+            u = sh > -64 ? (u128)(M >> -sh) : (u128)0;
+        X = (b >> 63) ? -(i128)u : (i128)u;
+    }
+    const i128 R = X - (i128)k * make_i128(T.ln2s_lo, T.ln2s_hi);
+    const int64_t r = (int64_t)(R >> 54);  // Q62
+    // e^r = 1 + r (1 + r (1/2 + r (1/6 + ... + r/5040))) in Q62
+    int64_t sacc = q62_recip(5040);
+    sacc = fx_add(q62_recip(720), r, sacc, 62);
+    sacc = fx_add(q62_recip(120), r, sacc, 62);
+    sacc = fx_add(q62_recip(24), r, sacc, 62);
+    sacc = fx_add(q62_recip(6), r, sacc, 62);
+    sacc = fx_add(q62_recip(2), r, sacc, 62);
+    sacc = fx_add(q62_recip(1), r, sacc, 62);
+    sacc = fx_add(q62_recip(1), r, sacc, 62);
     const int j = k & 63;
     const int m = (k - j) / 64;
-    double p = 1.0 / 5040.0;
-    p = DADD(1.0 / 720.0, DMUL(r, p));
-    p = DADD(1.0 / 120.0, DMUL(r, p));
-    p = DADD(1.0 / 24.0, DMUL(r, p));
-    p = DADD(1.0 / 6.0, DMUL(r, p));
-    p = DADD(0.5, DMUL(r, p));
-    p = DADD(1.0, DMUL(r, p));
-    p = DADD(1.0, DMUL(r, p));
-    const double v = DMUL(det_tab().e2[j], p);
+    const uint64_t V = (uint64_t)(((u128)(uint64_t)sacc * T.e2[j]) >> 62);  // Q62
+    const double v = fixed_to_double((i128)V, 62);
     if (m > 1023) return DMUL(DMUL(v, pow2i(1023)), pow2i(m - 1023));
     if (m < -1021) return DMUL(DMUL(v, pow2i(m + 600)), pow2i(-600));
     return DMUL(v, pow2i(m));

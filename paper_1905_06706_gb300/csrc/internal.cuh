@@ -335,7 +335,7 @@ __device__ __forceinline__ int jump32(uint32_t lo, uint32_t hi, float invLb, uns
 }
 
 // The exact FP64 rule: 0 stop, 1 continue with *X.
-__device__ __forceinline__ int jump64(uint32_t lo, uint32_t hi, double Lb, unsigned long long rem,
+static __device__ __forceinline__ int jump64(uint32_t lo, uint32_t hi, double Lb, unsigned long long rem,
                                       unsigned long long* X) {
     const double x = floor(DDIV(det_log(uniform53(lo, hi)), Lb));
     if (x >= 0x1p63) return 0;
