@@ -209,20 +209,6 @@ __device__ bool accept_t2(const DevCfg& cfg, const View& V, uint32_t pu, uint32_
     return t2_exact(cfg, V, pu, pv, D, lo, hi, e.pbar);
 }
 
-// The geometric jump of one draw (Sec. 3.2): 0 stop, 1 continue with *X.
-__device__ __forceinline__ int draw_jump(const DevCfg& cfg, const TwoEntry& e, const P4& o,
-                                         unsigned long long rem, unsigned long long* X,
-                                         Counters& C) {
-    *X = 0;
-    if (e.one) return rem == 0 ? 0 : 1;
-    int r = 2;
-    if (cfg.precision == 0) r = jump32(o.x, o.y, e.invLb, rem, X);
-    if (r == 2) {
-        if (cfg.precision == 0) ++C.recheck;
-        r = jump64(o.x, o.y, e.Lb, rem, X);
-    }
-    return r;
-}
 
 // The fast-path fields of a TwoEntry a type-II lane keeps; the FP64 fields are
 // reloaded from the table in the rare fallback paths.
@@ -232,6 +218,7 @@ struct TwoFast {
     bool one;
 };
 
+// The geometric jump of one draw (Sec. 3.2): 0 stop, 1 continue with *X.
 __device__ __forceinline__ int draw_jump_fast(const DevCfg& cfg, const TwoFast& e, const P4& o,
                                               unsigned long long rem, unsigned long long* X,
                                               Counters& C) {
@@ -655,13 +642,23 @@ __global__ void __launch_bounds__(kEnumThreads, 4) k_enum2(DevCfg cfg) {
                 const unsigned long long tot = (unsigned long long)x.a_len * sum[g];
                 keep[g] = 1u;
                 if (tot <= (1ull << te.k)) {
+                    // draw 0 when single precision decides it; otherwise (inside the
+                    // band, or in FP64 mode) the stream is kept whole and the sampling
+                    // kernel takes the same draw with its exact rule
                     const P4 o = philox(x.A, pack[g], 0u, 0u, cfg.seed_lo, cfg.seed_hi);
-                    ++C.draws;
-                    unsigned long long X;
-                    if (draw_jump(cfg, te, o, tot, &X, C) == 0)
-                        keep[g] = 0u;
-                    else
-                        s0[g] = (uint32_t)X;
+                    unsigned long long X = 0;
+                    int rj = 2;
+                    if (te.one)
+                        rj = tot == 0 ? 0 : 1;
+                    else if (cfg.precision == 0)
+                        rj = jump32(o.x, o.y, te.invLb, tot, &X);
+                    if (rj != 2) {
+                        ++C.draws;
+                        if (rj == 0)
+                            keep[g] = 0u;
+                        else
+                            s0[g] = (uint32_t)X;
+                    }
                 }
             }
         }
