@@ -369,6 +369,18 @@ static_assert(kEnumThreads == kAllocThreads, "the enumeration allocates slots pe
 constexpr int kWarps = kEnumThreads / 32;
 constexpr uint32_t kSplitB = 1024, kSplitAB = 4096;
 
+// floor(a / b) for a < 2^24 and b >= 1 with a / b < 2^23: a float reciprocal estimate
+// (within one of the quotient there), corrected by one step.
+__device__ __forceinline__ uint32_t udiv24(uint32_t a, uint32_t b) {
+    uint32_t q = __float2uint_rz(__uint2float_rn(a) * __frcp_rn(__uint2float_rn(b)));
+    const int r = (int)a - (int)(q * b);
+    if (r < 0)
+        --q;
+    else if (r >= (int)b)
+        ++q;
+    return q;
+}
+
 // An offset digit e in {-1, 0, 1} is a distinct neighbour on a level with 2^lev cells
 // per dimension unless the grid is too small: 1 cell -> only 0; 2 cells -> not -1.
 __device__ __forceinline__ bool digit_ok(int e, int lev) {
@@ -800,12 +812,14 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum1(DevCfg cfg) {
         const bool active = q < count;
         EntryCtx x;
         if (active) x = decode_entry<DIM>(cfg, cfg.ent1[q], d, true);
+        // sub-items: a-chunks of ac = kSplitAB / bc rows (>= 4) times b-chunks of
+        // bc = min(b_len, kSplitB) columns, ceil(b_len / kSplitB) of them
         auto split = [&](uint32_t b_len, uint32_t* ac, uint32_t* bc, uint32_t* na) {
             *bc = b_len < kSplitB ? b_len : kSplitB;
-            *ac = kSplitAB / *bc;
-            if (*ac < 1) *ac = 1;
-            *na = (x.a_len + *ac - 1) / *ac;
-            return *na * ((b_len + *bc - 1) / *bc);
+            *ac = udiv24(kSplitAB, *bc);
+            const uint32_t num = x.a_len + *ac - 1;
+            *na = num < (1u << 24) ? udiv24(num, *ac) : num / *ac;
+            return *na * ((b_len + kSplitB - 1) / kSplitB);
         };
         uint32_t nsub = 0;
         if (active) {
@@ -839,7 +853,7 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum1(DevCfg cfg) {
                     }
                 }
                 // every a-chunk meets every b-chunk: sum of side lengths over sub-items
-                t1_refs_local += (unsigned long long)x.a_len * ((len + bc - 1) / bc) +
+                t1_refs_local += (unsigned long long)x.a_len * ((len + kSplitB - 1) / kSplitB) +
                                  (unsigned long long)len * na;
             });
             t1_items_local += nsub;
