@@ -107,6 +107,30 @@ def test_det_log_exp_against_mpmath():
     assert O.det_log(0.0) == -math.inf
 
 
+def test_det_log_exp_monotone_and_exact_points():
+    """Monotone across every table boundary (a wrong table entry or reduction breaks this),
+    exact at 1 and 0, and correctly rounded at powers of two and at the table points."""
+    mp.mp.dps = 60
+    rng = np.random.default_rng(8)
+    xs = np.sort(np.concatenate([rng.uniform(0.70, 1.42, 200000),
+                                 np.exp(rng.uniform(-700, 700, 20000))]))
+    logs = np.array([O.det_log(float(x)) for x in xs])
+    assert np.all(np.diff(logs) >= 0)
+    ys = np.sort(np.concatenate([rng.uniform(-0.02, 0.02, 100000), rng.uniform(-740, 709, 50000)]))
+    exps = np.array([O.det_exp(float(y)) for y in ys])
+    assert np.all(np.diff(exps) >= 0)
+    assert O.det_log(1.0) == 0.0 and O.det_exp(0.0) == 1.0
+    for k in range(-1074, 1024, 7):
+        x = math.ldexp(1.0, k)
+        assert O.det_log(x) == float(mp.mpf(k) * mp.log(2)), k
+    for j in range(45, 92):
+        x = j / 64.0
+        assert O.det_log(x) == float(mp.log(mp.mpf(x))), j
+    for j in range(64):  # 2^(j/64) at the reduction points k ln2/64 (up to the rounding of x)
+        x = j * math.log(2) / 64
+        assert _ulp_err(O.det_exp(x), mp.exp(mp.mpf(x))) <= 0.51, j
+
+
 def test_det_log1p_and_pow_against_mpmath():
     mp.mp.dps = 60
     rng = np.random.default_rng(6)
