@@ -94,28 +94,56 @@ __global__ void k_scan_reduce(const Tin* __restrict__ in, int64_t n, T* __restri
     if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
+// Tile staging in shared memory: one pad element per 128 bytes, so that both the
+// striped (coalesced global) and the blocked (16 consecutive items per thread) accesses
+// are free of bank conflicts for 4- and 8-byte elements.
+template <class E>
+__device__ __forceinline__ int stage_pos(int i) {
+    return i + (i >> (sizeof(E) == 8 ? 4 : 5));
+}
+constexpr int kStageWords = (kScanTile + kScanTile / 16) * 2;  // 8-byte elements, padded
+
 template <class Tin, class T>
-__global__ void k_scan_down(const Tin* __restrict__ in, T* __restrict__ out, int64_t n,
-                            const T* __restrict__ prefix, const unsigned long long* __restrict__ n_dev) {
+__global__ void k_scan_down(const Tin* in, T* out, int64_t n, const T* __restrict__ prefix,
+                            const unsigned long long* __restrict__ n_dev) {
+    static_assert(sizeof(Tin) == 4 || sizeof(Tin) == 8, "4- or 8-byte inputs");
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte prefixes");
+    __shared__ __align__(16) uint32_t s_buf[kStageWords];
     __shared__ T s_warp[33];
     n = scan_len(n, n_dev);
-    if ((int64_t)blockIdx.x * kScanTile >= n) return;  // uniform per block
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    if (base >= n) return;  // uniform per block
+    const int tid = threadIdx.x;
+    const int64_t rem = n - base;
+    const int m = rem < kScanTile ? (int)rem : kScanTile;  // items of this tile
+    // the tile, striped (coalesced), into shared memory; zeros past the end
+    Tin* s_in = reinterpret_cast<Tin*>(s_buf);
+#pragma unroll
+    for (int it = 0; it < kScanItems; ++it) {
+        const int i = it * kScanThreads + tid;
+        s_in[stage_pos<Tin>(i)] = i < m ? in[base + i] : Tin(0);
+    }
+    __syncthreads();
     T v[kScanItems];
     T acc = 0;
 #pragma unroll
     for (int it = 0; it < kScanItems; ++it) {
-        const int64_t i = base + it;
-        v[it] = i < n ? (T)in[i] : T(0);
+        v[it] = (T)s_in[stage_pos<Tin>(tid * kScanItems + it)];
         acc += v[it];
     }
-    T total;
+    T total;  // block_exclusive_scan ends with a barrier: s_in is free after it
     T run = block_exclusive_scan<T>(acc, s_warp, &total) + (prefix ? prefix[blockIdx.x] : T(0));
+    T* s_out = reinterpret_cast<T*>(s_buf);
 #pragma unroll
     for (int it = 0; it < kScanItems; ++it) {
-        const int64_t i = base + it;
-        if (i < n) out[i] = run;
+        s_out[stage_pos<T>(tid * kScanItems + it)] = run;
         run += v[it];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kScanItems; ++it) {
+        const int i = it * kScanThreads + tid;
+        if (i < m) out[base + i] = s_out[stage_pos<T>(i)];
     }
 }
 
