@@ -215,9 +215,11 @@ int64_t girg_expected_edges(const girg_params* params, void* stream);
 int girg_last_stats(int64_t* out, int32_t len);
 
 /* Milliseconds spent in each phase of the last call on this host thread
- * (CUDA events): [0] points+reductions, [1] tables/host, [2] keys+sort+gather,
- * [3] cell-pair enumeration, [4] type I, [5] type-II streams, [6] total; host wall
- * clock: [7] reduction readback, [8] search for c, [9] table build.  Copies
+ * (CUDA events): [0] points+reductions, [1] host work up to the layer partition
+ * (search for c, levels), [2] keys+sort+gather, [3] cell-pair enumeration, [4] type I,
+ * [5] type-II streams, [6] total; host wall clock: [7] reduction readback, [8] search
+ * for c, [9] table build (the type-II bound tables are built while the sort runs on
+ * the device).  Copies
  * min(len, 10) values; returns the number copied. */
 int girg_last_phase_ms(float* out, int32_t len);
 

@@ -244,14 +244,60 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
             if (i < kMaxLayers) run += (uint64_t)cnt[i];
         }
     }
-    // row classes (i, l): the buckets j >= i with type II (CL >= l >= 2), then with
-    // type I (CL = l)
     int n3 = 1, n6 = 1;
     for (int k = 0; k < d; ++k) {
         n3 *= 3;
         n6 *= 6;
     }
     const bool tzero = P.T == 0.0;
+    double host_ms = host_ms_since(host_t0);
+    tm.mark();  // layer partition done
+    // ---------------------------------------------------------------- sort
+    uint32_t* key = S.get<uint32_t>(n);
+    uint32_t* val = S.get<uint32_t>(n);
+    uint32_t* key2 = S.get<uint32_t>(n);
+    uint32_t* val2 = S.get<uint32_t>(n);
+    uint32_t* offs = S.get<uint32_t>(total_cells + 1);
+    uint32_t* stmp = S.get<uint32_t>(std::max(scan_tmp_words((int64_t)total_cells + 1), radix_tmp_words(n)));
+    CK(cudaMemsetAsync(offs, 0, (total_cells + 1) * sizeof(uint32_t), st));
+    int8_t I8[kMaxLayers];
+    for (int i = 0; i < kMaxLayers; ++i) I8[i] = (int8_t)I[i];
+    const double* wsrc = P.w;
+    launch_keys(n, d, wsrc, P.X, girg ? P.w_min : 1.0, I8, layer_base, key, val, offs, st);
+    launch_scan_u32(offs, offs, (int64_t)total_cells + 1, stmp, st);
+    uint32_t *skey, *sid;
+    radix_sort_pairs(key, val, key2, val2, n, std::max(1, bitlen64(total_cells - 1)), stmp, st, &skey, &sid);
+    if (order_out) {
+        std::vector<uint32_t> h(n);
+        CK(cudaMemcpyAsync(h.data(), sid, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::vector<int64_t> o(h.begin(), h.end());
+        CK(cudaMemcpyAsync(order_out, o.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        return;
+    }
+    uint32_t* Xs = S.get<uint32_t>((size_t)d * n);
+    double* ws = S.get<double>(n);
+    uint8_t* slayer = S.get<uint8_t>(n);
+    float *sv = nullptr, *E32 = nullptr, *einv32 = nullptr, *sh32 = nullptr;
+    float gamma = 0.0f;
+    const double log2W_half = girg ? 0.5 * std::log2(P.W) : 0.0;
+    if (girg) {
+        sv = S.get<float>(n);
+        gamma = (float)(std::log2(P.K) / (2.0 * d));  // kappa_uv = s_u s_v, kappa^d = K q
+        launch_gather_girg(n, d, sid, P.X, P.w, P.w_min, log2W_half, gamma, (float)(1.0 / d), Xs,
+                           ws, sv, slayer, st);
+    } else {
+        E32 = S.get<float>(n);
+        einv32 = S.get<float>(n);
+        sh32 = S.get<float>(n);
+        launch_gather_hrg(n, sid, P.X, P.r, P.w, Xs, ws, E32, einv32, sh32, slayer, st);
+    }
+    tm.mark();  // sort done
+    // the host tables of the sampler, built while the sort runs on the device
+    const auto host_t1 = std::chrono::steady_clock::now();
+    // row classes (i, l): the buckets j >= i with type II (CL >= l >= 2), then with
+    // type I (CL = l)
     std::vector<RowClass> classes((size_t)std::max(L, 1) * (kMaxLevel + 1), RowClass{0, 0, 0});
     std::vector<uint8_t> jlist;
     for (int i = 0; i < L; ++i) {
@@ -336,50 +382,8 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
             fhi[m] = std::isinf(F) ? INFINITY : std::nextafterf(f, INFINITY) * (1.0f + 0x1p-22f);
         }
     }
-    g_ms[9] = (float)host_ms_since(host_t0);
-    tm.mark();  // tables done
-    // ---------------------------------------------------------------- sort
-    uint32_t* key = S.get<uint32_t>(n);
-    uint32_t* val = S.get<uint32_t>(n);
-    uint32_t* key2 = S.get<uint32_t>(n);
-    uint32_t* val2 = S.get<uint32_t>(n);
-    uint32_t* offs = S.get<uint32_t>(total_cells + 1);
-    uint32_t* stmp = S.get<uint32_t>(std::max(scan_tmp_words((int64_t)total_cells + 1), radix_tmp_words(n)));
-    CK(cudaMemsetAsync(offs, 0, (total_cells + 1) * sizeof(uint32_t), st));
-    int8_t I8[kMaxLayers];
-    for (int i = 0; i < kMaxLayers; ++i) I8[i] = (int8_t)I[i];
-    const double* wsrc = P.w;
-    launch_keys(n, d, wsrc, P.X, girg ? P.w_min : 1.0, I8, layer_base, key, val, offs, st);
-    launch_scan_u32(offs, offs, (int64_t)total_cells + 1, stmp, st);
-    uint32_t *skey, *sid;
-    radix_sort_pairs(key, val, key2, val2, n, std::max(1, bitlen64(total_cells - 1)), stmp, st, &skey, &sid);
-    if (order_out) {
-        std::vector<uint32_t> h(n);
-        CK(cudaMemcpyAsync(h.data(), sid, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        std::vector<int64_t> o(h.begin(), h.end());
-        CK(cudaMemcpyAsync(order_out, o.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-        CK(cudaStreamSynchronize(st));
-        return;
-    }
-    uint32_t* Xs = S.get<uint32_t>((size_t)d * n);
-    double* ws = S.get<double>(n);
-    uint8_t* slayer = S.get<uint8_t>(n);
-    float *sv = nullptr, *E32 = nullptr, *einv32 = nullptr, *sh32 = nullptr;
-    float gamma = 0.0f;
-    const double log2W_half = girg ? 0.5 * std::log2(P.W) : 0.0;
-    if (girg) {
-        sv = S.get<float>(n);
-        gamma = (float)(std::log2(P.K) / (2.0 * d));  // kappa_uv = s_u s_v, kappa^d = K q
-        launch_gather_girg(n, d, sid, P.X, P.w, P.w_min, log2W_half, gamma, (float)(1.0 / d), Xs,
-                           ws, sv, slayer, st);
-    } else {
-        E32 = S.get<float>(n);
-        einv32 = S.get<float>(n);
-        sh32 = S.get<float>(n);
-        launch_gather_hrg(n, sid, P.X, P.r, P.w, Xs, ws, E32, einv32, sh32, slayer, st);
-    }
-    tm.mark();  // sort done
+    host_ms += host_ms_since(host_t1);
+    g_ms[9] = (float)host_ms;
     // ---------------------------------------------------------------- device tables
     TwoEntry* d_tii = S.get<TwoEntry>(tii.size());
     RowClass* d_classes = S.get<RowClass>(classes.size());
@@ -708,7 +712,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
 
 void finish_timing(Timer& tm) {
     for (int q = 0; q < 7; ++q) g_ms[q] = 0.0f;
-    // marks: 0 start, 1 reduce done, 2 tables, 3 sort, 4 enumerate, 5 type I, 6 type II
+    // marks: 0 start, 1 reduce done, 2 layer partition, 3 sort, 4 enumerate, 5 type I, 6 type II
     for (int q = 1; q < tm.used && q <= 6; ++q) cudaEventElapsedTime(&g_ms[q - 1], tm.ev[q - 1], tm.ev[q]);
     if (tm.used >= 2) cudaEventElapsedTime(&g_ms[6], tm.ev[0], tm.ev[tm.used - 1]);
 }
