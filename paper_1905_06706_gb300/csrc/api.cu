@@ -258,15 +258,34 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     uint32_t* key2 = S.get<uint32_t>(n);
     uint32_t* val2 = S.get<uint32_t>(n);
     uint32_t* offs = S.get<uint32_t>(total_cells + 1);
-    uint32_t* stmp = S.get<uint32_t>(std::max(scan_tmp_words((int64_t)total_cells + 1), radix_tmp_words(n)));
+    uint32_t* stmp = S.get<uint32_t>(std::max({scan_tmp_words((int64_t)total_cells + 1),
+                                               radix_tmp_words(n), place_tmp_words(n)}));
     CK(cudaMemsetAsync(offs, 0, (total_cells + 1) * sizeof(uint32_t), st));
     int8_t I8[kMaxLayers];
     for (int i = 0; i < kMaxLayers; ++i) I8[i] = (int8_t)I[i];
     const double* wsrc = P.w;
-    launch_keys(n, d, wsrc, P.X, girg ? P.w_min : 1.0, I8, layer_base, key, val, offs, st);
+    // the order by placement, unless some layer averages more than 16 vertices a cell
+    // (the large-cell sort would then carry much of the work): a stable radix sort
+    // instead.  GIRG_SORT=radix or GIRG_SORT=place forces one (tests compare the two).
+    bool place = true;
+    for (int i = 0; i < L; ++i)
+        if (cnt[i] > 0 && (uint64_t)cnt[i] > (16ull << (d * I[i]))) place = false;
+    if (const char* env = std::getenv("GIRG_SORT")) {
+        if (!std::strcmp(env, "radix")) place = false;
+        if (!std::strcmp(env, "place")) place = true;
+    }
+    launch_keys(n, d, wsrc, P.X, girg ? P.w_min : 1.0, I8, layer_base, key, val, offs, place, st);
     launch_scan_u32(offs, offs, (int64_t)total_cells + 1, stmp, st);
     uint32_t *skey, *sid;
-    radix_sort_pairs(key, val, key2, val2, n, std::max(1, bitlen64(total_cells - 1)), stmp, st, &skey, &sid);
+    if (place) {
+        CK(cudaMemsetAsync(stmp, 0, sizeof(uint32_t), st));
+        place_by_counts(key, val, offs, n, key2, val2, key, stmp, st);
+        skey = key2;
+        sid = key;
+    } else {
+        radix_sort_pairs(key, val, key2, val2, n, std::max(1, bitlen64(total_cells - 1)), stmp, st,
+                         &skey, &sid);
+    }
     if (order_out) {
         std::vector<uint32_t> h(n);
         CK(cudaMemcpyAsync(h.data(), sid, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));

@@ -58,10 +58,11 @@ void launch_split_weights(int64_t n, const double* w, const double* thr, double 
                           unsigned int cap, unsigned int* count, double* part, double* sums,
                           cudaStream_t st);
 
-// Sorting: keys (global cell index at the insertion level) with a histogram.
+// Sorting: keys (global cell index at the insertion level) with a histogram; val
+// receives each vertex's arrival slot in its cell (slots) or its id (for the radix sort).
 void launch_keys(int64_t n, int d, const double* w, const uint32_t* X, double w_min,
                  const int8_t* I, const uint32_t* layer_base, uint32_t* key, uint32_t* val,
-                 uint32_t* cnt, cudaStream_t st);
+                 uint32_t* cnt, bool slots, cudaStream_t st);
 // Exclusive scan of n uint32 values in place (out may alias in); tmp >= scan_tmp_words(n).
 size_t scan_tmp_words(int64_t n);
 void launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t st);
@@ -77,6 +78,13 @@ size_t radix_tmp_words(int64_t n);
 void radix_sort_pairs(uint32_t* key, uint32_t* val, uint32_t* key_alt, uint32_t* val_alt,
                       int64_t n, int bits, uint32_t* tmp, cudaStream_t st, uint32_t** key_out,
                       uint32_t** val_out);
+// The same order by placement: key and slot from launch_keys (slots) and the scanned
+// cell histogram offs; writes the sorted keys to skey and the sorted ids to sid (tid:
+// scratch of n words).  tmp >= place_tmp_words(n) words with tmp[0] zeroed.
+size_t place_tmp_words(int64_t n);
+void place_by_counts(const uint32_t* key, const uint32_t* slot, const uint32_t* offs, int64_t n,
+                     uint32_t* skey, uint32_t* tid, uint32_t* sid, uint32_t* tmp,
+                     cudaStream_t st);
 // Sorted per-vertex arrays.
 void launch_gather_girg(int64_t n, int d, const uint32_t* perm, const uint32_t* X,
                         const double* w, double w_min, double log2W_half, float gamma,

@@ -1,10 +1,12 @@
 // The geometric data structure of Sec. 3.4 / Lemma 1: every vertex gets the key
 // (bucket, Morton code of its cell at the bucket's insertion level) as one dense
 // global cell index; a histogram over the cells plus an exclusive scan gives
-// the prefix sums P_C of all buckets at once, and a stable LSD radix sort of
-// (key, id) gives the vertex order (ties by original id, Sec. 4.4 sorts by
-// bucket first and Morton code second with a radix sort).  The gather kernels
-// lay out the sorted per-vertex arrays (structure of arrays, coalesced).
+// the prefix sums P_C of all buckets at once.  The vertex order (ties by original
+// id) then comes from placing each vertex by those prefix sums and ranking it among
+// the ids of its cell, or, where cells hold many vertices on average, from a stable
+// LSD radix sort of (key, id) as in Sec. 4.4 (bucket first, Morton code second).
+// The gather kernels lay out the sorted per-vertex arrays (structure of arrays,
+// coalesced).
 #include "internal.cuh"
 #include "kernels.h"
 
@@ -17,7 +19,7 @@ struct KeyTab {
 
 __global__ void k_keys(int64_t n, int d, const double* __restrict__ w, const uint32_t* __restrict__ X,
                        double w_min, KeyTab tab, uint32_t* __restrict__ key,
-                       uint32_t* __restrict__ val, uint32_t* __restrict__ cnt) {
+                       uint32_t* __restrict__ val, uint32_t* __restrict__ cnt, bool slots) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int layer = layer_of(w[v], w_min);
@@ -27,8 +29,9 @@ __global__ void k_keys(int64_t n, int d, const double* __restrict__ w, const uin
         const uint32_t code = lev ? morton_encode(coord, d) : 0u;
         const uint32_t kk = tab.base[layer] + code;
         key[v] = kk;
-        val[v] = (uint32_t)v;
-        atomicAdd(&cnt[kk], 1u);
+        // slots: the arrival slot of v in its cell (placement by counts); else v (radix sort)
+        const uint32_t slot = atomicAdd(&cnt[kk], 1u);
+        val[v] = slots ? slot : (uint32_t)v;
     }
 }
 
@@ -295,6 +298,112 @@ void radix_sort_pairs(uint32_t* key, uint32_t* val, uint32_t* key_alt, uint32_t*
     *val_out = vi;
 }
 
+static int grid_for(int64_t n, int threads, int max_blocks) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b > max_blocks) b = max_blocks;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// ------------------------------------------------------------------ placement by counts
+// The same order without the radix passes.  With the cell histogram scanned (offs[c] =
+// first sorted position of cell c, offs[C] = n), a vertex goes to offs[key] plus its
+// arrival slot in the cell.  Arrival order is not deterministic, so k_rank then puts
+// each vertex at offs[key] + (the number of smaller ids in its cell): the order of the
+// stable sort (ties by original id).  Cells with more than kRankMax vertices are copied
+// as they are and sorted afterwards, one block per cell (k_sort_cells).
+constexpr uint32_t kRankMax = 64;
+
+__global__ void k_place(int64_t n, const uint32_t* __restrict__ key,
+                        const uint32_t* __restrict__ slot, const uint32_t* __restrict__ offs,
+                        uint32_t* __restrict__ skey, uint32_t* __restrict__ tid) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = key[v];
+        const uint32_t pos = offs[c] + slot[v];
+        skey[pos] = c;
+        tid[pos] = (uint32_t)v;
+    }
+}
+
+__global__ void k_rank(int64_t n, const uint32_t* __restrict__ skey,
+                       const uint32_t* __restrict__ offs, const uint32_t* __restrict__ tid,
+                       uint32_t* __restrict__ sid, uint32_t* __restrict__ big,
+                       uint32_t* __restrict__ nbig, uint32_t big_cap) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = skey[p];
+        const uint32_t a = offs[c], b = offs[c + 1];
+        const uint32_t v = tid[p];
+        if (b - a > kRankMax) {  // a large cell: copied, sorted by k_sort_cells
+            sid[p] = v;
+            if ((uint32_t)p == a) {
+                const uint32_t q = atomicAdd(nbig, 1u);
+                if (q < big_cap) big[q] = c;
+            }
+            continue;
+        }
+        uint32_t r = 0;
+        for (uint32_t q = a; q < b; ++q) r += tid[q] < v ? 1u : 0u;
+        sid[a + r] = v;
+    }
+}
+
+// One block per large cell: a bitonic network over the cell's ids in place, on the
+// cell padded to a power of two P with +inf (a comparator whose upper element lies past
+// the end never swaps, so those comparators are skipped).  Each merge starts with the
+// mirrored comparator (i, i ^ (size - 1)), so every comparator puts the smaller id
+// first.  The ids stay in global memory; the barrier after each stage orders them
+// within the block.
+__global__ void __launch_bounds__(256) k_sort_cells(const uint32_t* __restrict__ offs,
+                                                    const uint32_t* __restrict__ big,
+                                                    const uint32_t* __restrict__ nbig,
+                                                    uint32_t big_cap, uint32_t* sid) {
+    uint32_t nb = *nbig;
+    if (nb > big_cap) nb = big_cap;
+    for (uint32_t q = blockIdx.x; q < nb; q += gridDim.x) {
+        const uint32_t c = big[q];
+        uint32_t* x = sid + offs[c];
+        const uint32_t m = offs[c + 1] - offs[c];
+        uint64_t P = 1;
+        while (P < m) P <<= 1;
+        const uint32_t half = (uint32_t)(P >> 1);
+        for (int lg = 1; (1ull << lg) <= P; ++lg) {
+            const uint32_t size = 1u << lg;
+            for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+                const bool mirror = stride == (size >> 1);
+                for (uint32_t t = threadIdx.x; t < half; t += blockDim.x) {
+                    const uint32_t i = (t / stride) * 2u * stride + (t % stride);
+                    const uint32_t j = mirror ? (i ^ (size - 1u)) : i + stride;
+                    if (j < m) {
+                        const uint32_t lo = x[i], hi = x[j];
+                        if (lo > hi) {
+                            x[i] = hi;
+                            x[j] = lo;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+size_t place_tmp_words(int64_t n) { return (size_t)(n / (kRankMax + 1)) + 2; }
+
+void place_by_counts(const uint32_t* key, const uint32_t* slot, const uint32_t* offs, int64_t n,
+                     uint32_t* skey, uint32_t* tid, uint32_t* sid, uint32_t* tmp,
+                     cudaStream_t st) {
+    const uint32_t big_cap = (uint32_t)(place_tmp_words(n) - 1);
+    uint32_t* nbig = tmp;  // zeroed by the caller
+    uint32_t* big = tmp + 1;
+    const int grid = grid_for(n, 256, 152 * 16);
+    g_launches += 3;
+    k_place<<<grid, 256, 0, st>>>(n, key, slot, offs, skey, tid);
+    k_rank<<<grid, 256, 0, st>>>(n, skey, offs, tid, sid, big, nbig, big_cap);
+    k_sort_cells<<<152 * 2, 256, 0, st>>>(offs, big, nbig, big_cap, sid);
+}
+
 // ------------------------------------------------------------------ gathers
 // Per-vertex scale s with kappa_uv = s_u s_v (kappa: distance at which p = 1, or the
 // threshold distance at T = 0): log2 s = (log2 w - log2(W)/2) / d + gamma.  Only the
@@ -342,21 +451,14 @@ __global__ void k_gather_hrg(int64_t n, const uint32_t* __restrict__ perm,
     }
 }
 
-static int grid_for(int64_t n, int threads, int max_blocks) {
-    int64_t b = (n + threads - 1) / threads;
-    if (b > max_blocks) b = max_blocks;
-    if (b < 1) b = 1;
-    return (int)b;
-}
-
 void launch_keys(int64_t n, int d, const double* w, const uint32_t* X, double w_min,
                  const int8_t* I, const uint32_t* layer_base, uint32_t* key, uint32_t* val,
-                 uint32_t* cnt, cudaStream_t st) {
+                 uint32_t* cnt, bool slots, cudaStream_t st) {
     KeyTab tab;
     memcpy(tab.I, I, sizeof(tab.I));
     memcpy(tab.base, layer_base, sizeof(tab.base));
     ++g_launches;
-    k_keys<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, d, w, X, w_min, tab, key, val, cnt);
+    k_keys<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, d, w, X, w_min, tab, key, val, cnt, slots);
 }
 
 void launch_gather_girg(int64_t n, int d, const uint32_t* perm, const uint32_t* X,

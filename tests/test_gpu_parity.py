@@ -123,6 +123,41 @@ def test_sorted_order_matches_oracle(n, d, T):
     assert np.array_equal(order.cpu().numpy(), res.order)
 
 
+@pytest.mark.parametrize("mode", ["place", "radix"])
+@pytest.mark.parametrize("n,d,T,lcap", [(30_001, 1, 0.5, 2), (20_000, 2, 0.5, 1), (9_000, 3, 0.0, 1),
+                                        (40_000, 2, 0.7, 0), (1_000, 1, 0.5, 0), (5_003, 2, 0.5, 3)])
+def test_sort_modes_match_oracle(n, d, T, lcap, mode, monkeypatch):
+    """Both orderings (placement by counts with the rank and large-cell sorts, and the
+    stable radix sort) give the oracle's order, with small level caps making cells of
+    thousands of vertices (the large-cell path, cell sizes not powers of two)."""
+    monkeypatch.setenv("GIRG_SORT", mode)
+    w, X = O.girg_points(n, d, 2.5, 1.0, 12 + d)
+    W = O.exact_sum(w)
+    c = O.girg_solve_c(8.0, w, d, T, W)
+    res = O.girg_cellpairs(X, w, float(w.min()), W, T, c, 3, skip_sampling=True, level_cap=lcap)
+    Xg, wg = _gpu_points(X, w)
+    order = gg.girg_sorted_order(Xg, wg, T=T, c=c, level_cap=lcap)
+    assert np.array_equal(order.cpu().numpy(), res.order)
+
+
+def test_clustered_points_place_and_radix_agree(monkeypatch):
+    """Positions packed into a few cells (large cells under placement) and a level cap of
+    2: the same edges edge for edge with either ordering, equal to the oracle's."""
+    rng = np.random.default_rng(17)
+    n, d, T = 4_000, 2, 0.5
+    w = np.exp(rng.normal(0.5, 0.8, n))
+    X = (rng.normal(0.5, 0.05, (n, d)) % 1.0 * 2 ** 32).astype(np.uint64).astype(np.uint32)
+    W = O.exact_sum(w)
+    c = O.girg_solve_c(6.0, w, d, T, W)
+    ref = O.edge_set(O.girg_cellpairs(X, w, float(w.min()), W, T, c, 6, cap=n * 600,
+                                      level_cap=2).edges)
+    got = {}
+    for mode in ("place", "radix"):
+        monkeypatch.setenv("GIRG_SORT", mode)
+        got[mode] = _generate_from(X, w, T, c, 6, gg.PRECISION_FP32, level_cap=2, cap=n * 600)
+    assert got["place"] == got["radix"] == ref
+
+
 # --------------------------------------------------------------------- cell-pair sampler
 
 CASES = [(1, 0.5, 20_000), (1, 0.0, 30_000), (2, 0.5, 40_000), (2, 0.0, 40_000),
