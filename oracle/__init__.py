@@ -90,6 +90,7 @@ def _load():
             "orc_cell_linf": (u32, [u64, u64, i32, i32]),
             "orc_level_cap": (i32, [i64, i32]),
             "orc_chunk_log": (i32, [dbl]),
+            "orc_geometric_jumps": (None, [i64, dbl, P, P, P]),
             "orc_girg_cellpairs": (i64, [i64, i32, P, P, dbl, dbl, dbl, dbl, u64, P, i64,
                                          P, P, P, P, P, i64, P, i32, i32]),
             "orc_hrg_cellpairs": (i64, [i64, P, P, dbl, dbl, u64, P, i64, P, P, P, P, P,
@@ -168,6 +169,16 @@ def cell_linf(A: int, B: int, d: int, level: int) -> int:
 
 def level_cap(n: int, d: int) -> int:
     return _load().orc_level_cap(n, d)
+
+
+def geometric_jumps(pbar: float, lo, hi):
+    """Jumps X = floor(ln U / ln(1 - pbar)) (Sec. 3.2) from word pairs (lo, hi); -1 marks
+    a jump of 2^63 or more."""
+    lo = np.ascontiguousarray(lo, dtype=np.uint32)
+    hi = np.ascontiguousarray(hi, dtype=np.uint32)
+    out = np.zeros(len(lo), dtype=np.int64)
+    _load().orc_geometric_jumps(len(lo), float(pbar), _ptr(lo), _ptr(hi), _ptr(out))
+    return out
 
 
 def chunk_log(pbar: float) -> int:

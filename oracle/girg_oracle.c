@@ -1035,6 +1035,21 @@ static int cmp_t2(const void* a, const void* b) {
     return 0;
 }
 
+/* One geometric jump (Sec. 3.2) under a bound pbar < 1, Lb = ln(1 - pbar), from the
+ * uniform U of the words (lo, hi): X = floor(ln U / Lb), the number of positions skipped
+ * before the next candidate; -1 where X >= 2^63 (the stream then leaves its chunk). */
+static int64_t geometric_jump(double Lb, uint32_t lo, uint32_t hi) {
+    double x = floor(orc_det_log(orc_uniform(lo, hi)) / Lb);
+    return x >= 0x1p63 ? -1 : (int64_t)x;
+}
+
+/* The jumps under a bound pbar in (0, 1) for n word pairs (the tests check their law). */
+void orc_geometric_jumps(int64_t n, double pbar, const uint32_t* lo, const uint32_t* hi,
+                         int64_t* out) {
+    double Lb = orc_det_log1p(-pbar);
+    for (int64_t q = 0; q < n; q++) out[q] = geometric_jump(Lb, lo[q], hi[q]);
+}
+
 /* Geometric jumps (Sec. 3.2) with the bound pbar over the index space
  * idx = a S + b of V_i^A x (V_j^B1 ++ V_j^B2 ++ ...), S the total size of the
  * stream's partner sets, cut into chunks of 2^k indices; a candidate is
@@ -1072,12 +1087,12 @@ static void sample_stream(cp_ctx* C, const struct t2rec* m, int64_t nm) {
             uint32_t o[4];
             philox_seed(C->seed, (uint32_t)A, pack, (uint32_t)h, t, o);
             C->stats[2]++;
-            /* X = floor(ln U / ln(1 - pbar)); stop when the jump leaves the chunk */
+            /* stop when the jump leaves the chunk */
             uint64_t remaining = len - (uint64_t)(s + 1);
             uint64_t X = 0;
             if (pbar < 1.0) {
-                double x = floor(orc_det_log(orc_uniform(o[0], o[1])) / Lb);
-                if (x >= 0x1p63) break;
+                int64_t x = geometric_jump(Lb, o[0], o[1]);
+                if (x < 0) break;
                 X = (uint64_t)x;
             }
             if (X >= remaining) break;

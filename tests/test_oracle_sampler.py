@@ -208,3 +208,24 @@ def test_hrg_partition_bound_and_threshold_equality():
     e2 = O.hrg_cellpairs(X, r, R, 0.0, 1).edges
     assert len(e1) > 1000
     assert O.edge_set(e1) == O.edge_set(e2)
+
+
+@pytest.mark.parametrize("pbar", [0.9, 0.5, 0.1, 0.01, 1e-4])
+def test_geometric_jump_law(pbar):
+    """Sec. 3.2: the jump between candidates is geometric: P(X >= k) = (1 - pbar)^k,
+    mean (1 - pbar) / pbar, variance (1 - pbar) / pbar^2.  A wrong log, sign, rounding
+    direction or pbar in place of 1 - pbar fails one of these."""
+    N = 400_000
+    rng = np.random.default_rng(int(pbar * 1e6) + 5)
+    lo = rng.integers(0, 2 ** 32, N, dtype=np.uint64).astype(np.uint32)
+    hi = rng.integers(0, 2 ** 32, N, dtype=np.uint64).astype(np.uint32)
+    X = O.geometric_jumps(pbar, lo, hi)
+    assert (X >= 0).all()
+    q = 1.0 - pbar
+    mean, var = q / pbar, q / pbar ** 2
+    assert abs(X.mean() - mean) < 6.0 * math.sqrt(var / N)
+    assert abs(X.var() / var - 1.0) < 0.045
+    for k in sorted({1, 2, 5, round(1 / pbar), round(3 / pbar)}):
+        pk = q ** k
+        emp = (X >= k).mean()
+        assert abs(emp - pk) < 6.0 * math.sqrt(pk * (1.0 - pk) / N) + 1e-12, k
