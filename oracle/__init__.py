@@ -90,6 +90,7 @@ def _load():
             "orc_cell_linf": (u32, [u64, u64, i32, i32]),
             "orc_level_cap": (i32, [i64, i32]),
             "orc_chunk_log": (i32, [dbl]),
+            "orc_layer_of": (i32, [dbl, dbl]),
             "orc_geometric_jumps": (None, [i64, dbl, P, P, P]),
             "orc_girg_cellpairs": (i64, [i64, i32, P, P, dbl, dbl, dbl, dbl, u64, P, i64,
                                          P, P, P, P, P, i64, P, i32, i32]),
@@ -179,6 +180,11 @@ def geometric_jumps(pbar: float, lo, hi):
     out = np.zeros(len(lo), dtype=np.int64)
     _load().orc_geometric_jumps(len(lo), float(pbar), _ptr(lo), _ptr(hi), _ptr(out))
     return out
+
+
+def layer_of(w: float, w_min: float) -> int:
+    """Weight bucket: floor(log2(w / w_min)) of the FP64 quotient, clamped to [0, 63]."""
+    return _load().orc_layer_of(float(w), float(w_min))
 
 
 def chunk_log(pbar: float) -> int:

@@ -826,6 +826,9 @@ static int layer_of(double w, double w_min) {
     return layer;
 }
 
+/* The weight bucket of Sec. 3.1 (exported for its tests). */
+int orc_layer_of(double w, double w_min) { return layer_of(w, w_min); }
+
 /* Sorting key: (bucket, Morton code of the insertion-level cell, id). */
 typedef struct {
     int layer;

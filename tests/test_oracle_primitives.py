@@ -259,3 +259,27 @@ def test_edge_checksum_is_order_independent():
     e = rng.integers(0, 1 << 31, size=(1000, 2))
     assert O.edge_checksum(e) == O.edge_checksum(e[::-1]) == O.edge_checksum(e[:, ::-1])
     assert O.edge_checksum(e[:999]) != O.edge_checksum(e)
+
+
+def test_layer_boundaries():
+    """Sec. 3.1 buckets: weights in [w_min 2^i, w_min 2^(i+1)) form bucket i.  Checked at
+    every boundary, one ulp on either side, against the exact binary logarithm of the
+    rounded quotient (Fraction arithmetic), and clamped below at 0."""
+    from fractions import Fraction
+
+    def exact(w, w_min):
+        q = Fraction(w / w_min)  # the FP64 quotient, exactly
+        i = 0
+        while q >= 2:
+            q /= 2
+            i += 1
+        return min(i, 63)
+
+    for w_min in (1.0, 0.75, 1.5, 3.0e-7, 12345.678):
+        for i in range(0, 62):
+            b = w_min * 2.0 ** i
+            for w in (b, math.nextafter(b, 0.0), math.nextafter(b, math.inf)):
+                if w >= w_min:
+                    assert O.layer_of(w, w_min) == exact(w, w_min), (w_min, i, w)
+        assert O.layer_of(w_min, w_min) == 0
+        assert O.layer_of(math.nextafter(w_min, 0.0), w_min) == 0
