@@ -27,3 +27,14 @@ def test_reference_arm_prints_one_contract_line():
     assert e2e["value"] == rec["value"] and e2e["unit"] == rec["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert rec["config"]["workload"] == "girg_d2_n1e6_T0.5_deg10"
+
+
+def test_cpu_baseline_one_core_and_all_cores():
+    """The CPU baseline: the oracle on one core, and independent samples on every host
+    core in spawned processes (the batch's edges over its wall time)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    cb = bench.cpu_baseline(bench.WORKLOAD)
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] > 0
+    ac = cb["all_cores"]
+    assert ac["cores"] == bench.host_cores() and ac["value"] > 0 and ac["unit"] == "edges/s"
