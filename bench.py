@@ -15,9 +15,17 @@ Reported:
   e2e        the same step through the public API with the edge list copied to
              pinned host memory inside the timed region
   fp64_plain the same step with every decision in FP64 (identical edge set)
-  roofline   the dominant kernel against the measured HBM bandwidth
+  roofline   the dominant kernel against the measured HBM bandwidth, with algorithmic
+             bytes = 8 B per edge it emits + one read of every sorted vertex record
+  step_roofline  all algorithmic bytes of a step (edges + per-vertex bytes of every
+             kernel) over the step time
+  configs    the other workloads, device-timed: the all-pairs configuration (d = 1,
+             n = 10^4), the dimension sweep (d = 1..4, T in {0, 0.7}, n = 2^24, int64
+             edges) and the large HRG (n = 10^7)
   cpu_baseline  the FP64 oracle (cell-pair sampler) on a bounded sample: one core, and
              independent samples on every host core (all_cores)
+
+Step times are medians over the timed steps (CUDA events on the launching stream).
 
 --impl reference runs the FP64 CPU oracle on every host core on the same
 configuration (a bounded sample per core and step) and prints the same JSON line.
@@ -100,6 +108,17 @@ def _ncu_traffic(kernel: str):
     except (OSError, ValueError):
         pass
     return None
+
+
+def vertex_bytes(d: int) -> dict:
+    """Algorithmic bytes per vertex of each kernel of a GIRG step (the minimum each must
+    read and write; the per-unit figures of the design notes): weights and positions
+    written, the weight reductions, keys and cell histogram, placement and rank within
+    the cell, the gather into sorted arrays, the row heads, and one read of every sorted
+    vertex record by the sampling kernels."""
+    return {"points": 8 + 4 * d, "reduce": 8, "split": 8, "keys": 8 + 4 * d + 8,
+            "place": 12 + 8, "rank": 16 + 4, "gather": 4 + 4 * d + 8 + 4 * d + 8 + 4 + 1,
+            "rows": 5, "sampling": 4 * d + 8}
 
 
 class ClockSampler:
@@ -276,6 +295,117 @@ def run_batched(gg, torch, k: int, workers_grid=(4, 8, 16)) -> dict:
                                    "p50_ms": _pct(lat, 0.5), "p99_ms": _pct(lat, 0.99)}}}
 
 
+def _median_ms(fn, torch, flush, steps: int, warmup: int):
+    """Median CUDA-event time (ms) of fn() over `steps` calls after `warmup` calls, L2
+    flushed before each timed call; returns (ms, the last call's result)."""
+    res = None
+    for _ in range(warmup):
+        res = fn()
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms), res
+
+
+def _rate(m, ms, eb, hbm):
+    """edges/s and the fraction of the edge-output HBM roofline (2 eb bytes per edge)."""
+    if not ms:
+        return None, None
+    eps = m / (ms / 1e3)
+    return eps, eps * 2 * eb / 1e9 / hbm
+
+
+def run_configs(gg, torch, hbm: float, flush, steps: int = 3, warmup: int = 1) -> dict:
+    """The workloads beside the headline one, device-timed (median of `steps` calls):
+    the all-pairs configuration (d = 1, n = 10^4, beta = 2.5, T = 0.5, degree 10, seed 1:
+    the quadratic kernel and the cell-pair sampler, FP32 and FP64 decisions), the
+    dimension sweep (d = 1..4, n = 2^24, beta = 2.2, T in {0, 0.7}, degree 16, seed 1,
+    int64 edges) and the large HRG (n = 10^7, alpha = 0.75, T = 0.5, R solved for degree
+    10, seed 1, int32 edges).  Each entry: edges, median ms, edges/s, the fraction of the
+    edge-output roofline, the phases of the last call and its algorithmic bytes."""
+    out = {}
+
+    def check(r, what):
+        if r.status != gg.GIRG_OK:
+            raise RuntimeError(f"{what}: {gg.status_string(r.status)}")
+        return r
+
+    # all-pairs configuration
+    n, d, T, beta = 10_000, 1, 0.5, 2.5
+    w, X = gg.girg_points(n, d, beta, 1.0, 1)
+    W = math.fsum(w.cpu().tolist())  # the exactly rounded sum, as the library's
+    ed = torch.empty((n * 16, 2), dtype=torch.int32, device="cuda")
+    c = check(gg.girg_generate(ed, n=n, d=d, beta=beta, T=T, avg_deg=10.0, seed=1),
+              "config 1").c_used
+    cfg1 = {"workload": "girg_d1_n1e4_T0.5_deg10", "n": n, "d": d, "T": T, "c": c}
+    runs = {
+        "allpairs_fp32": lambda: gg.girg_allpairs(ed, X, w, W=W, T=T, c=c, seed=1, precision=0),
+        "allpairs_fp64": lambda: gg.girg_allpairs(ed, X, w, W=W, T=T, c=c, seed=1, precision=1),
+        "cellpairs_fp32": lambda: gg.girg_generate_from_points(ed, X, w, T=T, c=c, seed=1,
+                                                               precision=0),
+        "cellpairs_fp64": lambda: gg.girg_generate_from_points(ed, X, w, T=T, c=c, seed=1,
+                                                               precision=1),
+    }
+    for name, fn in runs.items():
+        ms, r = _median_ms(fn, torch, flush, max(steps, 5), warmup)
+        check(r, name)
+        eps, frac = _rate(r.num_edges, ms, 4, hbm)
+        cfg1[name] = {"edges": r.num_edges, "ms": ms, "edges_per_s": eps,
+                      "edge_output_frac": frac}
+    out["allpairs_config"] = cfg1
+    del ed
+
+    # dimension sweep
+    n, beta, deg = 1 << 24, 2.2, 16.0
+    ed = torch.empty((int(n * deg * 0.75), 2), dtype=torch.int64, device="cuda")
+    sweep = []
+    for T in (0.0, 0.7):
+        for d in (1, 2, 3, 4):
+            ms, r = _median_ms(lambda: gg.girg_generate(ed, n=n, d=d, beta=beta, T=T,
+                                                        avg_deg=deg, seed=1),
+                               torch, flush, steps, warmup)
+            check(r, f"sweep d={d} T={T}")
+            st, ph = gg.last_stats(), gg.last_phase_ms()
+            eps, frac = _rate(r.num_edges, ms, 8, hbm)
+            algo = r.num_edges * 16 + n * sum(vertex_bytes(d).values())
+            sweep.append({"workload": f"girg_d{d}_n2^24_T{T}_deg16", "d": d, "T": T,
+                          "edges": r.num_edges, "ms": ms, "edges_per_s": eps,
+                          "edge_output_frac": frac,
+                          "step_algorithmic_frac": algo / (ms / 1e3) / 1e9 / hbm,
+                          "phases_ms": ph,
+                          "stats": {k: st[k] for k in ("type1_pairs", "type2_candidates",
+                                                       "jump_draws", "type2_segments",
+                                                       "enum_passes")}})
+    out["dimension_sweep"] = sweep
+    del ed
+
+    # large HRG
+    n = 10_000_000
+    ed = torch.empty((n * 8, 2), dtype=torch.int32, device="cuda")
+    R = check(gg.hrg_generate(ed, n=n, alpha=0.75, T=0.5, avg_deg=10.0, seed=1),
+              "config 4").R_used
+    ms, r = _median_ms(lambda: gg.hrg_generate(ed, n=n, alpha=0.75, T=0.5, avg_deg=10.0,
+                                               seed=1), torch, flush, steps, warmup)
+    check(r, "large HRG")
+    ph = gg.last_phase_ms()
+    eps, frac = _rate(r.num_edges, ms, 4, hbm)
+    out["large_hrg"] = {"workload": "hrg_n1e7_alpha0.75_T0.5_deg10", "R": R,
+                        "edges": r.num_edges, "ms": ms, "edges_per_s": eps,
+                        "edge_output_frac": frac, "phases_ms": ph,
+                        "note": "R solved on the host for degree 10 in every call"}
+    del ed
+    return out
+
+
 def aggregate_ranks(vals, world: int, dist):
     """Whole-job throughputs from every rank's [seconds, edges] for the device-timed,
     end-to-end and FP64 runs: each is the edges of all ranks over the slowest rank's
@@ -403,6 +533,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--batch-requests", type=int, default=4096,
                     help="mixed requests of the batched/served run (0: skip it)")
+    ap.add_argument("--config-steps", type=int, default=3,
+                    help="timed calls per workload of the other configurations (0: skip)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -474,7 +606,8 @@ def main():
     barrier()
     clock_info = clocks.stop()
     stats = gg.last_stats()
-    t_rank = sum(ms) / 1e3
+    # every step makes the same graph: the step time is the median over the steps
+    t_rank = statistics.median(ms) * len(ms) / 1e3
     # e2e: public API with the edge list in pinned host memory, written there by the
     # kernels (zero copy across the host link); beside it the same step into device
     # memory followed by a copy to pinned host memory
@@ -495,51 +628,62 @@ def main():
     # count-only mode (no edge list stored; count and checksum only, as in Sec. 5)
     ms_co, m_co, _ = timed(gg.PRECISION_FP32, ke2e, out=False)
     barrier()
-    vals = torch.tensor([t_rank, float(m_total), sum(ms_e2e) / 1e3, float(m_e2e),
-                         sum(ms64) / 1e3, float(m64)], dtype=torch.float64, device="cuda")
+    med_total = (lambda xs: statistics.median(xs) * len(xs) / 1e3 if xs else 0.0)
+    vals = torch.tensor([t_rank, float(m_total), med_total(ms_e2e), float(m_e2e),
+                         med_total(ms64), float(m64)], dtype=torch.float64, device="cuda")
     value, e2e_value, fp64_value = aggregate_ranks(vals, world, dist)
     if rank == 0:
         e2e_value = e2e_value if ms_e2e else None
         fp64_value = fp64_value if ms64 else None
         m_step = m_total / args.steps
-        # dominant kernel: the longer of the two single-kernel sampling phases
-        ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
+        # dominant kernel: the longer of the two single-kernel sampling phases (each
+        # is one launch per step, timed by events on the launching stream)
+        ph = {k: statistics.median(p[k] for p in phases) for k in phases[0]}
         hbm, peak_kind = _peaks()
         eb = cfg["edge_bytes"] * 2
-        vrec = 4 * d + 8  # coordinates, scale, id of one vertex
+        vrec = 4 * d + 8  # coordinates, scale and id of one sorted vertex record
         t2_edges = stats["edges"] - stats["type1_edges"]
-        # algorithmic bytes per launch (per-unit figures in the design doc section 6)
-        algo = {
-            "k_type1": (24 * stats["type1_items"] + vrec * stats["type1_vertex_refs"] +
-                        eb * stats["type1_edges"], ph["type1"]),
-            "k_type2": (56 * stats["type2_streams"] +
-                        (8 + 2 * vrec) * stats["type2_candidates"] + eb * t2_edges,
-                        ph["type2"]),
-        }
+        # algorithmic bytes per launch: the edges the kernel emits (8 B each) and one read
+        # of every sorted vertex record
+        algo = {"k_type1": (eb * stats["type1_edges"] + vrec * n, ph["type1"]),
+                "k_type2": (eb * t2_edges + vrec * n, ph["type2"])}
         kname = max(algo, key=lambda k: algo[k][1])
         kbytes, kms = algo[kname]
         traffic = _ncu_traffic(kname)
         roof = {"kernel": kname, "bound": "hbm",
                 "achieved": (kbytes / (kms / 1e3)) / 1e9 if kms > 0 else None,
                 "peak": hbm, "unit": "GB/s", "traffic": traffic,
-                "peak_kind": peak_kind, "algorithmic_bytes": kbytes, "launch_ms": kms}
+                "peak_kind": peak_kind, "algorithmic_bytes": kbytes, "launch_ms": kms,
+                "bytes_rule": f"{eb} B per edge the kernel emits + {vrec} B per vertex "
+                              "(one read of the sorted vertex records)"}
         if roof["achieved"] is not None:
             roof["frac"] = roof["achieved"] / hbm
-        # what actually bounds the sampling kernels: instruction issue (warp instructions
-        # per launch from the committed ncu summary over the live launch duration)
-        winst = _ncu_metric(kname, "smsp__inst_executed.sum")
-        issue_roof = {"kernel": kname, "bound": "alu", "unit": "warp instructions/s",
-                      "peak": ISSUE_PEAK,
-                      "peak_kind": "derived: 4 schedulers x 152 SMs x 2070 MHz",
-                      "warp_instructions": winst,
-                      "achieved": (winst / (kms / 1e3)) if (winst and kms > 0) else None}
-        if issue_roof["achieved"] is not None:
-            issue_roof["frac"] = issue_roof["achieved"] / ISSUE_PEAK
+        # the same kernels with the bytes their work lists and cache-served vertex
+        # re-reads move (stream records and prefixes, 8 B per candidate segment lookup,
+        # both vertex records of every candidate): what the design reads, not a minimum
+        design = {"k_type1": 24 * stats["type1_items"] + vrec * stats["type1_vertex_refs"] +
+                             eb * stats["type1_edges"],
+                  "k_type2": 56 * stats["type2_streams"] +
+                             (8 + 2 * vrec) * stats["type2_candidates"] + eb * t2_edges}
+        design_roof = {"kernel": kname, "bytes": design[kname],
+                       "achieved": design[kname] / (kms / 1e3) / 1e9 if kms > 0 else None,
+                       "peak": hbm, "unit": "GB/s"}
+        if design_roof["achieved"] is not None:
+            design_roof["frac"] = design_roof["achieved"] / hbm
+        # the whole step: every kernel's per-vertex bytes plus the edges
+        vb = vertex_bytes(d)
+        step_bytes = eb * stats["edges"] + n * sum(vb.values())
+        step_ms = statistics.median(ms)
+        step_roof = {"bytes": step_bytes, "per_vertex_bytes": vb,
+                     "achieved": step_bytes / (step_ms / 1e3) / 1e9, "peak": hbm,
+                     "unit": "GB/s"}
+        step_roof["frac"] = step_roof["achieved"] / hbm
         samp_ms = ph["enumerate"] + ph["type1"] + ph["type2"]
-        edge_roof = (m_step * eb / (statistics.mean(ms) / 1e3)) / 1e9
+        edge_roof = (m_step * eb / (statistics.median(ms) / 1e3)) / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(ms),
+            "ms_per_step_mean": statistics.mean(ms),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": cfg["workload"], "n": n, "d": d, "beta": cfg["beta"],
@@ -549,24 +693,28 @@ def main():
                        "decisions": "FP32 with FP64 recheck in the error band"},
             "e2e": {"value": e2e_value, "unit": "edges/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": int(m_e2e / max(1, len(ms_e2e))) * eb,
-                    "ms_per_step": statistics.mean(ms_e2e) if ms_e2e else None,
+                    "ms_per_step": statistics.median(ms_e2e) if ms_e2e else None,
                     "note": "inputs are the parameters; weights and positions are drawn on "
                             "the device (Sec. 5.1 steps 1-2); the kernels write the edge "
                             "list into pinned host memory (mapped, no separate copy)",
                     "copy_variant": {
-                        "value": (m_cp / (sum(ms_cp) / 1e3)) if ms_cp else None,
-                        "ms_per_step": statistics.mean(ms_cp) if ms_cp else None,
+                        "value": (m_cp / len(ms_cp) / (statistics.median(ms_cp) / 1e3))
+                        if ms_cp else None,
+                        "ms_per_step": statistics.median(ms_cp) if ms_cp else None,
                         "note": "edges into device memory, then one device-to-host copy "
                                 "to pinned memory inside the timed step"}},
             "fp64_plain": {"value": fp64_value, "unit": "edges/s",
-                           "ms_per_step": statistics.mean(ms64) if ms64 else None},
-            "count_only": {"value": (m_co / (sum(ms_co) / 1e3)) if ms_co else None,
+                           "ms_per_step": statistics.median(ms64) if ms64 else None},
+            "count_only": {"value": (m_co / len(ms_co) / (statistics.median(ms_co) / 1e3))
+                           if ms_co else None,
                            "unit": "edges/s",
-                           "ms_per_step": statistics.mean(ms_co) if ms_co else None,
+                           "ms_per_step": statistics.median(ms_co) if ms_co else None,
                            "note": "edge count and checksum, no edge list stored"},
             "roofline": roof,
             "edge_output_roofline": {"achieved": edge_roof, "peak": hbm, "unit": "GB/s",
                                      "frac": edge_roof / hbm},
+            "step_roofline": step_roof,
+            "design_bytes_roofline": design_roof,
             "issue_roofline": issue_roof,
             "sampling_only": {"value": m_step / (samp_ms / 1e3) if samp_ms > 0 else None,
                               "unit": "edges/s", "ms_per_step": samp_ms,
@@ -577,6 +725,8 @@ def main():
             "gpu_launches": int(stats.get("kernel_launches", 0)) * args.steps,
             "clocks": clock_info,
         }
+        if args.config_steps > 0 and world == 1:
+            line["configs"] = run_configs(gg, torch, hbm, flush, steps=args.config_steps)
         if args.batch_requests > 0:
             line["batched"] = run_batched(gg, torch, args.batch_requests)
         if not args.no_cpu_baseline and world == 1:

@@ -16,13 +16,19 @@
  *     on it.  Calls return after the edge count has been copied to the host,
  *     i.e. they synchronise the stream once at the end (and once after the
  *     weight reductions).
- *   - Scratch memory is allocated with cudaMallocAsync on `stream` and freed
- *     before return; the caller owns every buffer it passes.
+ *   - Scratch memory comes from a memory pool the library owns (one per device,
+ *     cudaMallocFromPoolAsync on `stream`) and goes back to it before return; the
+ *     pool keeps freed memory for later calls (girg_scratch_pool_trim returns it
+ *     to the driver).  The caller's pools are not touched; the caller owns every
+ *     buffer it passes.
  *   - Edges are unordered pairs (u, v), u < v, of original vertex ids, stored
  *     as two uint32 (edge_bytes = 4) or two uint64 (edge_bytes = 8) per edge,
  *     in unspecified order.  No self loops, no multi-edges.
  *   - The edge set is a deterministic function of the parameters and seed, and
- *     equals the FP64 oracle's edge for edge in both precision modes.
+ *     equals the FP64 oracle's edge for edge in both precision modes (the oracle's
+ *     default build evaluates ln and exp by the same fixed-point method).  Against
+ *     an oracle built on the C library's log / exp / pow, at most 1e-9 of the
+ *     decisions differ, each within a relative 1e-12 of its threshold.
  *   - Return value: a GIRG_* status.  On GIRG_E_CAPACITY *num_edges holds the
  *     number of edges the graph has and the buffer holds an unspecified subset.
  */
@@ -155,14 +161,19 @@ int girg_allpairs(int64_t n, int32_t d, const uint32_t* d_X, const double* d_w, 
  * latency-critical loop where an allocation could block or fail under memory
  * pressure.  Arguments, results and errors are those of girg_allpairs, except that
  * n must not exceed GIRG_NOALLOC_MAX_N (larger n returns GIRG_E_PARAM before any
- * device work).  Its scratch (a per-vertex scale and the edge counters, about 4 MiB)
+ * device work), and that d_X, d_w and d_edges are checked before any device work:
+ * each must be device memory or page-locked host memory mapped into the device
+ * (cudaHostAlloc); pageable host memory or a pointer CUDA does not know returns
+ * GIRG_E_PARAM.  Its scratch (a per-vertex scale and the edge counters, about 4 MiB)
  * is a fixed device array of the library, held by every GPU that loads the library
  * until the process exits.  The first call on a device looks up that array's device
  * address (once per device, with the device current); make that first call before
- * any stream capture.  All calls share the array, which keeps the last call's
- * contents (the counters are cleared at the start of every call): calls whose device
- * work overlaps -- on different streams or host threads -- race on it and must be
- * serialised by the caller. */
+ * any stream capture.  The address is kept for the life of the process, so
+ * cudaDeviceReset is not supported while the library is loaded.  All calls share the
+ * array, which keeps the last call's contents (the counters are cleared at the start
+ * of every call): calls whose device work overlaps -- on different streams or host
+ * threads -- race on it and must be serialised by the caller.  Like girg_allpairs,
+ * the call synchronises `stream` before it returns (it reads the edge count back). */
 int girg_allpairs_noalloc(int64_t n, int32_t d, const uint32_t* d_X, const double* d_w,
                           double W, double T, double c, uint64_t seed, int32_t precision,
                           int32_t edge_bytes, void* d_edges, int64_t capacity_edges,
@@ -194,6 +205,18 @@ int girg_expected_avg_degree(const girg_params* params, double* avg_deg, void* s
  * number for every T, where c_used = K^(1/T) under- or overflows a double as T -> 0
  * (it is then reported as 0 or infinity). */
 double girg_last_scale(void);
+
+/* The library's scratch pool on the current device: bytes reserved from the driver,
+ * bytes in use now, and the most bytes in use at once since the pool was created or
+ * last reset (reset_high != 0 resets that mark after reading it).  Out pointers may be
+ * NULL.  Errors: GIRG_E_CUDA. */
+int girg_scratch_pool_usage(int64_t* reserved, int64_t* used, int64_t* used_high,
+                            int32_t reset_high);
+
+/* Return unused memory of the library's scratch pool on the current device to the
+ * driver, keeping at most keep_bytes reserved.  Errors: GIRG_E_PARAM (keep_bytes < 0),
+ * GIRG_E_CUDA. */
+int girg_scratch_pool_trim(int64_t keep_bytes);
 
 /* Expected number of edges of the graph girg_generate would make with these parameters
  * (n f / 2, f the expected average degree of App. B.2 for the generated weights; c > 0

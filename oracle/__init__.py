@@ -8,7 +8,12 @@ shares no code with the CUDA library.
 
 The C file is compiled on first use (or by :func:`build`) with
 ``-ffp-contract=off`` so that the deterministic elementary functions give the
-same bits on every IEEE machine.
+same bits on every IEEE machine.  It is compiled twice: the default build uses
+the file's fixed-point ln / exp (the method the CUDA library implements too, so
+the two take identical decisions), the plain build (``plain=True`` on every
+function below) the C library's log, exp, log1p, pow, sin and acosh.  The plain
+build shares no elementary function with the CUDA library; :class:`audit`
+records the decisions that a different rounding could flip.
 """
 from __future__ import annotations
 
@@ -24,8 +29,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "girg_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libgirg_oracle.so")
+_PLAIN_PATH = os.path.join(_BUILD, "libgirg_oracle_plain.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 MAXL = 64
 
@@ -42,27 +48,32 @@ STAT_NAMES = (
 )
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle's shared library (gcc, FP contraction off)."""
-    os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+def _build_one(path: str, defines, force: bool) -> str:
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+        return path
+    tmp = path + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+           "-fno-fast-math", *defines, "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
-def _load():
-    global _lib
+def build(force: bool = False) -> str:
+    """Compile the oracle's two shared libraries (gcc, FP contraction off): the default
+    build and the plain build (-DORC_PLAIN).  Returns the default one's path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    _build_one(_PLAIN_PATH, ["-DORC_PLAIN"], force)
+    return _build_one(_LIB_PATH, [], force)
+
+
+def _load(plain: bool = False):
     with _lock:
-        if _lib is not None:
-            return _lib
+        if plain in _libs:
+            return _libs[plain]
         build()
-        lib = ctypes.CDLL(_LIB_PATH)
+        lib = ctypes.CDLL(_PLAIN_PATH if plain else _LIB_PATH)
         P = ctypes.c_void_p
         i64, i32, u32, u64, dbl = (ctypes.c_int64, ctypes.c_int, ctypes.c_uint32,
                                    ctypes.c_uint64, ctypes.c_double)
@@ -102,12 +113,14 @@ def _load():
             "orc_girg_thresh_neighbors": (i64, [i64, i32, P, P, dbl, dbl, P, i64, P, i64]),
             "orc_hrg_avg_degree": (dbl, [i64, dbl, dbl, dbl]),
             "orc_hrg_solve_R": (dbl, [i64, dbl, dbl, dbl]),
+            "orc_audit_begin": (None, [dbl, P, i64]),
+            "orc_audit_end": (i64, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
             fn.restype = res
             fn.argtypes = args
-        _lib = lib
+        _libs[plain] = lib
         return lib
 
 
@@ -117,87 +130,87 @@ def _ptr(a):
 
 # ---------------------------------------------------------------- primitives
 
-def philox(ctr, key):
+def philox(ctr, key, plain=False):
     """Philox4x32-10 of one 128-bit counter under a 64-bit key (4 + 2 words)."""
     c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
     k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
     out = np.zeros(4, dtype=np.uint32)
-    _load().orc_philox(_ptr(c), _ptr(k), _ptr(out))
+    _load(plain).orc_philox(_ptr(c), _ptr(k), _ptr(out))
     return out
 
 
-def uniform(lo: int, hi: int) -> float:
-    return _load().orc_uniform(lo, hi)
+def uniform(lo: int, hi: int, plain=False) -> float:
+    return _load(plain).orc_uniform(lo, hi)
 
 
-def det_log(x):
-    return _load().orc_det_log(float(x))
+def det_log(x, plain=False):
+    return _load(plain).orc_det_log(float(x))
 
 
-def det_log1p(x):
-    return _load().orc_det_log1p(float(x))
+def det_log1p(x, plain=False):
+    return _load(plain).orc_det_log1p(float(x))
 
 
-def det_exp(x):
-    return _load().orc_det_exp(float(x))
+def det_exp(x, plain=False):
+    return _load(plain).orc_det_exp(float(x))
 
 
-def det_pow(x, y):
-    return _load().orc_det_pow(float(x), float(y))
+def det_pow(x, y, plain=False):
+    return _load(plain).orc_det_pow(float(x), float(y))
 
 
-def det_sinpi(x):
-    return _load().orc_det_sinpi(float(x))
+def det_sinpi(x, plain=False):
+    return _load(plain).orc_det_sinpi(float(x))
 
 
-def det_acosh(x):
-    return _load().orc_det_acosh(float(x))
+def det_acosh(x, plain=False):
+    return _load(plain).orc_det_acosh(float(x))
 
 
-def exact_sum(w) -> float:
+def exact_sum(w, plain=False) -> float:
     w = np.ascontiguousarray(w, dtype=np.float64)
-    return _load().orc_exact_sum(len(w), _ptr(w))
+    return _load(plain).orc_exact_sum(len(w), _ptr(w))
 
 
-def morton(x, d: int, level: int) -> int:
+def morton(x, d: int, level: int, plain=False) -> int:
     x = np.ascontiguousarray(np.asarray(x, dtype=np.uint32))
-    return _load().orc_morton(_ptr(x), d, level)
+    return _load(plain).orc_morton(_ptr(x), d, level)
 
 
-def cell_linf(A: int, B: int, d: int, level: int) -> int:
-    return _load().orc_cell_linf(A, B, d, level)
+def cell_linf(A: int, B: int, d: int, level: int, plain=False) -> int:
+    return _load(plain).orc_cell_linf(A, B, d, level)
 
 
-def level_cap(n: int, d: int) -> int:
-    return _load().orc_level_cap(n, d)
+def level_cap(n: int, d: int, plain=False) -> int:
+    return _load(plain).orc_level_cap(n, d)
 
 
-def geometric_jumps(pbar: float, lo, hi):
+def geometric_jumps(pbar: float, lo, hi, plain=False):
     """Jumps X = floor(ln U / ln(1 - pbar)) (Sec. 3.2) from word pairs (lo, hi); -1 marks
     a jump of 2^63 or more."""
     lo = np.ascontiguousarray(lo, dtype=np.uint32)
     hi = np.ascontiguousarray(hi, dtype=np.uint32)
     out = np.zeros(len(lo), dtype=np.int64)
-    _load().orc_geometric_jumps(len(lo), float(pbar), _ptr(lo), _ptr(hi), _ptr(out))
+    _load(plain).orc_geometric_jumps(len(lo), float(pbar), _ptr(lo), _ptr(hi), _ptr(out))
     return out
 
 
-def layer_of(w: float, w_min: float) -> int:
+def layer_of(w: float, w_min: float, plain=False) -> int:
     """Weight bucket: floor(log2(w / w_min)) of the FP64 quotient, clamped to [0, 63]."""
-    return _load().orc_layer_of(float(w), float(w_min))
+    return _load(plain).orc_layer_of(float(w), float(w_min))
 
 
-def chunk_log(pbar: float) -> int:
-    return _load().orc_chunk_log(pbar)
+def chunk_log(pbar: float, plain=False) -> int:
+    return _load(plain).orc_chunk_log(pbar)
 
 
-def pair_coin(seed: int, u: int, v: int) -> float:
-    return _load().orc_pair_coin(seed, u, v)
+def pair_coin(seed: int, u: int, v: int, plain=False) -> float:
+    return _load(plain).orc_pair_coin(seed, u, v)
 
 
-def K_of_c(c, d, T) -> float:
+def K_of_c(c, d, T, plain=False) -> float:
     """The scale K of the model for the c of Eq. 1: c^T (T > 0) or c^d (T = 0)."""
-    return _load().orc_girg_K_of_c(c, d, T)
+    return _load(plain).orc_girg_K_of_c(c, d, T)
 
 
 def c_of_K(K, d, T) -> float:
@@ -206,47 +219,47 @@ def c_of_K(K, d, T) -> float:
     return 0.0 if e < -745.0 else (math.inf if e > 709.0 else math.exp(e))
 
 
-def _scale(c, d, T, K):
-    return K if K is not None else K_of_c(c, d, T)
+def _scale(c, d, T, K, plain=False):
+    return K if K is not None else K_of_c(c, d, T, plain=plain)
 
 
-def girg_p(d, T, c, W, wu, wv, D, K=None) -> float:
+def girg_p(d, T, c, W, wu, wv, D, K=None, plain=False) -> float:
     """Eq. 1, p = min{1, (K q / r^d)^(1/T)} with K = c^T (c ignored if K is given)."""
-    return _load().orc_girg_p(d, T, _scale(c, d, T, K), W, wu, wv, D)
+    return _load(plain).orc_girg_p(d, T, _scale(c, d, T, K, plain), W, wu, wv, D)
 
 
-def girg_thresh_edge(d, c, W, wu, wv, D, K=None) -> bool:
+def girg_thresh_edge(d, c, W, wu, wv, D, K=None, plain=False) -> bool:
     """Threshold variant: r^d <= K w_u w_v / W with K = c^d."""
-    return bool(_load().orc_girg_thresh_edge(d, _scale(c, d, 0.0, K), W, wu, wv, D))
+    return bool(_load(plain).orc_girg_thresh_edge(d, _scale(c, d, 0.0, K, plain), W, wu, wv, D))
 
 
-def hrg_coshd(ru, rv, D) -> float:
-    return _load().orc_hrg_coshd(ru, rv, D)
+def hrg_coshd(ru, rv, D, plain=False) -> float:
+    return _load(plain).orc_hrg_coshd(ru, rv, D)
 
 
-def hrg_p(T, R, ru, rv, D) -> float:
-    return _load().orc_hrg_p(T, R, ru, rv, D)
+def hrg_p(T, R, ru, rv, D, plain=False) -> float:
+    return _load(plain).orc_hrg_p(T, R, ru, rv, D)
 
 
-def hrg_weight(r, R) -> float:
-    return _load().orc_hrg_weight(r, R)
+def hrg_weight(r, R, plain=False) -> float:
+    return _load(plain).orc_hrg_weight(r, R)
 
 
 # ---------------------------------------------------------------- model inputs
 
-def girg_points(n: int, d: int, beta: float, w_min: float, seed: int):
+def girg_points(n: int, d: int, beta: float, w_min: float, seed: int, plain=False):
     """Weights (n,) float64 and positions (n, d) uint32 of the generated GIRG."""
     w = np.zeros(n, dtype=np.float64)
     X = np.zeros((n, d), dtype=np.uint32)
-    _load().orc_girg_points(n, d, beta, w_min, seed, _ptr(w), _ptr(X))
+    _load(plain).orc_girg_points(n, d, beta, w_min, seed, _ptr(w), _ptr(X))
     return w, X
 
 
-def hrg_points(n: int, alpha: float, R: float, seed: int):
+def hrg_points(n: int, alpha: float, R: float, seed: int, plain=False):
     """Radii (n,) float64 and angular fixed-point coordinates (n,) uint32."""
     r = np.zeros(n, dtype=np.float64)
     X = np.zeros(n, dtype=np.uint32)
-    _load().orc_hrg_points(n, alpha, R, seed, _ptr(r), _ptr(X))
+    _load(plain).orc_hrg_points(n, alpha, R, seed, _ptr(r), _ptr(X))
     return r, X
 
 
@@ -256,23 +269,23 @@ def _edges_array(cap):
     return np.zeros((max(cap, 1), 2), dtype=np.uint32)
 
 
-def girg_allpairs(X, w, W, T, c, seed, cap=None, K=None):
+def girg_allpairs(X, w, W, T, c, seed, cap=None, K=None, plain=False):
     """Oracle 1: (m, 2) uint32 edges (u < v) of the quadratic generator."""
     X = np.ascontiguousarray(X, dtype=np.uint32)
     w = np.ascontiguousarray(w, dtype=np.float64)
     n, d = X.shape
-    K = _scale(c, d, T, K)
+    K = _scale(c, d, T, K, plain)
     if cap is None:
         cap = 1 << 16
     while True:
         e = _edges_array(cap)
-        m = _load().orc_girg_allpairs(n, d, _ptr(X), _ptr(w), W, T, K, seed, _ptr(e), cap)
+        m = _load(plain).orc_girg_allpairs(n, d, _ptr(X), _ptr(w), W, T, K, seed, _ptr(e), cap)
         if m <= cap:
             return e[:m].copy()
         cap = m
 
 
-def hrg_allpairs(X, r, R, T, seed, cap=None):
+def hrg_allpairs(X, r, R, T, seed, cap=None, plain=False):
     X = np.ascontiguousarray(X, dtype=np.uint32)
     r = np.ascontiguousarray(r, dtype=np.float64)
     n = len(X)
@@ -280,7 +293,7 @@ def hrg_allpairs(X, r, R, T, seed, cap=None):
         cap = 1 << 16
     while True:
         e = _edges_array(cap)
-        m = _load().orc_hrg_allpairs(n, _ptr(X), _ptr(r), R, T, seed, _ptr(e), cap)
+        m = _load(plain).orc_hrg_allpairs(n, _ptr(X), _ptr(r), R, T, seed, _ptr(e), cap)
         if m <= cap:
             return e[:m].copy()
         cap = m
@@ -324,12 +337,12 @@ def _items_to_records(raw, k):
 
 
 def girg_cellpairs(X, w, w_min, W, T, c, seed, cap=None, want_items=False, skip_sampling=False,
-                   items_cap=None, level_cap=0, K=None):
+                   items_cap=None, level_cap=0, K=None, plain=False):
     """Oracle 2 for GIRGs (Algorithm 1 with App. B.1)."""
     X = np.ascontiguousarray(X, dtype=np.uint32)
     w = np.ascontiguousarray(w, dtype=np.float64)
     n, d = X.shape
-    K = _scale(c, d, T, K)
+    K = _scale(c, d, T, K, plain)
     if cap is None:
         cap = 1 << 16
     while True:
@@ -341,7 +354,7 @@ def girg_cellpairs(X, w, w_min, W, T, c, seed, cap=None, want_items=False, skip_
         nitems = np.zeros(1, dtype=np.int64)
         icap = items_cap if items_cap is not None else (1 << 20)
         items = np.zeros((icap if want_items else 1, 12), dtype=np.int64)
-        m = _load().orc_girg_cellpairs(
+        m = _load(plain).orc_girg_cellpairs(
             n, d, _ptr(X), _ptr(w), w_min, W, T, K, seed, _ptr(e), cap, _ptr(stats),
             _ptr(order), _ptr(itab), _ptr(wtab), _ptr(items) if want_items else None,
             icap if want_items else 0, _ptr(nitems), 1 if skip_sampling else 0, level_cap)
@@ -357,7 +370,7 @@ def girg_cellpairs(X, w, w_min, W, T, c, seed, cap=None, want_items=False, skip_
 
 
 def hrg_cellpairs(X, r, R, T, seed, cap=None, want_items=False, skip_sampling=False,
-                  items_cap=None, level_cap=0):
+                  items_cap=None, level_cap=0, plain=False):
     """Oracle 2 for HRGs through the HRG -> GIRG mapping of Sec. 2.3."""
     X = np.ascontiguousarray(X, dtype=np.uint32)
     r = np.ascontiguousarray(r, dtype=np.float64)
@@ -373,7 +386,7 @@ def hrg_cellpairs(X, r, R, T, seed, cap=None, want_items=False, skip_sampling=Fa
         nitems = np.zeros(1, dtype=np.int64)
         icap = items_cap if items_cap is not None else (1 << 20)
         items = np.zeros((icap if want_items else 1, 12), dtype=np.int64)
-        m = _load().orc_hrg_cellpairs(
+        m = _load(plain).orc_hrg_cellpairs(
             n, _ptr(X), _ptr(r), R, T, seed, _ptr(e), cap, _ptr(stats), _ptr(order),
             _ptr(itab), _ptr(wtab), _ptr(items) if want_items else None,
             icap if want_items else 0, _ptr(nitems), 1 if skip_sampling else 0, level_cap)
@@ -390,38 +403,38 @@ def hrg_cellpairs(X, r, R, T, seed, cap=None, want_items=False, skip_sampling=Fa
 
 # ---------------------------------------------------------------- degree / c
 
-def girg_avg_degree(c, w, d, T, W=None, K=None):
+def girg_avg_degree(c, w, d, T, W=None, K=None, plain=False):
     """Expected average degree f of App. B.2 for the given weights at c (or scale K)."""
     w = np.ascontiguousarray(w, dtype=np.float64)
     if W is None:
-        W = exact_sum(w)
-    return _load().orc_girg_avg_degree(_scale(c, d, T, K), len(w), d, T, _ptr(w), W)
+        W = exact_sum(w, plain=plain)
+    return _load(plain).orc_girg_avg_degree(_scale(c, d, T, K, plain), len(w), d, T, _ptr(w), W)
 
 
-def girg_solve_K(target, w, d, T, W=None):
+def girg_solve_K(target, w, d, T, W=None, plain=False):
     """The scale K (c^T, or c^d at T = 0) whose expected average degree is ``target``."""
     w = np.ascontiguousarray(w, dtype=np.float64)
     if W is None:
-        W = exact_sum(w)
-    return _load().orc_girg_solve_K(target, len(w), d, T, _ptr(w), W)
+        W = exact_sum(w, plain=plain)
+    return _load(plain).orc_girg_solve_K(target, len(w), d, T, _ptr(w), W)
 
 
-def girg_solve_c(target, w, d, T, W=None):
+def girg_solve_c(target, w, d, T, W=None, plain=False):
     """The c of Eq. 1 whose expected average degree is ``target`` (App. B.2)."""
-    return c_of_K(girg_solve_K(target, w, d, T, W), d, T)
+    return c_of_K(girg_solve_K(target, w, d, T, W, plain=plain), d, T)
 
 
-def hrg_avg_degree(n, alpha, T, R):
+def hrg_avg_degree(n, alpha, T, R, plain=False):
     """Expected average degree of an HRG (radius R), by quadrature of its definition."""
-    return _load().orc_hrg_avg_degree(n, alpha, T, R)
+    return _load(plain).orc_hrg_avg_degree(n, alpha, T, R)
 
 
-def hrg_solve_R(n, alpha, T, target):
+def hrg_solve_R(n, alpha, T, target, plain=False):
     """The disk radius R with expected average degree ``target`` (bisection)."""
-    return _load().orc_hrg_solve_R(n, alpha, T, target)
+    return _load(plain).orc_hrg_solve_R(n, alpha, T, target)
 
 
-def girg_thresh_neighbors(X, w, W, K, us, cap=None):
+def girg_thresh_neighbors(X, w, W, K, us, cap=None, plain=False):
     """Threshold model by brute force: every (u, v), u in ``us``, v != u, with
     r^d <= K w_u w_v / W, as an (m, 2) int64 array."""
     X = np.ascontiguousarray(X, dtype=np.uint32)
@@ -431,11 +444,44 @@ def girg_thresh_neighbors(X, w, W, K, us, cap=None):
     cap = cap or 1 << 16
     while True:
         out = np.zeros((cap, 2), dtype=np.int64)
-        m = _load().orc_girg_thresh_neighbors(n, d, _ptr(X), _ptr(w), W, K, _ptr(us), len(us),
+        m = _load(plain).orc_girg_thresh_neighbors(n, d, _ptr(X), _ptr(w), W, K, _ptr(us), len(us),
                                               _ptr(out), cap)
         if m <= cap:
             return out[:m]
         cap = m
+
+
+class audit:
+    """Decision audit of the samplers in the selected build (a context manager):
+    counts every decision taken inside the ``with`` block and records the near ones,
+    whose two sides are within a relative ``eps`` of each other.  ``records`` is an
+    (k, 3) int64 array of (kind, a, b): kind 1 per-pair coin, 2 type-II acceptance,
+    3 threshold test (a < b vertex ids), 4 geometric jump near an integer (a = cell A,
+    b = stream word << 32 | chunk); ``count`` the number of near decisions (records
+    holds at most ``cap`` of them) and ``decisions`` the number of all decisions."""
+
+    def __init__(self, eps=1e-12, cap=1 << 16, plain=False):
+        self.eps, self.cap, self.plain = eps, cap, plain
+        self._buf = np.zeros((cap, 3), dtype=np.int64)
+        self.records = self._buf[:0]
+        self.count = 0
+        self.decisions = 0
+
+    def __enter__(self):
+        _load(self.plain).orc_audit_begin(self.eps, _ptr(self._buf), self.cap)
+        return self
+
+    def __exit__(self, *exc):
+        dec = np.zeros(1, dtype=np.int64)
+        self.count = int(_load(self.plain).orc_audit_end(_ptr(dec)))
+        self.decisions = int(dec[0])
+        self.records = self._buf[:min(self.count, self.cap)].copy()
+        return False
+
+    def pairs(self, kinds=(1, 2, 3)) -> set:
+        """The recorded vertex pairs (keys u 2^32 + v, u < v) of the given kinds."""
+        r = self.records[np.isin(self.records[:, 0], kinds)]
+        return set((r[:, 1] * (1 << 32) + r[:, 2]).tolist())
 
 
 def splitmix64_finalize(z):

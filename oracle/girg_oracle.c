@@ -17,7 +17,16 @@
  *     ln(1 + r) and e^r), every truncation specified and the result rounded
  *     once, so any implementation of the same integer steps reproduces them bit
  *     for bit; det_log1p / det_sinpi / det_acosh / det_pow build on them with
- *     IEEE +, -, *, / in a fixed order (FMA contraction disabled).
+ *     IEEE +, -, *, / in a fixed order (FMA contraction disabled).  The CUDA
+ *     library implements the same fixed-point method on its own, so that the
+ *     default build of this file and the library take identical decisions and
+ *     their edge sets are compared for equality.
+ *   - The plain build (compiled with -DORC_PLAIN): the same file with the C
+ *     library's log, exp, log1p, pow, sin and acosh in place of the det_*
+ *     functions, and nothing else changed.  It shares no arithmetic with the
+ *     CUDA library beyond IEEE +, -, *, /; the library's edge sets are checked
+ *     against it at a tolerance on flipped decisions, using the decision audit
+ *     (every decision within a relative eps of its threshold is recorded).
  *   - Model inputs: Pareto weights (Sec. 2.1, Sec. 5.1 step 1), uniform torus
  *     positions in 32-bit fixed point (Sec. 2.1), HRG radii and angles
  *     (Sec. 2.2) and the HRG->GIRG mapping (Sec. 2.3).
@@ -121,6 +130,20 @@ double orc_uniform(uint32_t lo, uint32_t hi) {
 /* Deterministic elementary functions                                         */
 /* ------------------------------------------------------------------------ */
 
+#ifdef ORC_PLAIN
+/* The plain build (-DORC_PLAIN): the elementary functions are the C library's own
+ * log, exp, log1p, pow, sin and acosh, with no table or series of this file, so the
+ * samplers below evaluate Eq. 1, p_T(d) and the geometric jumps of Sec. 3.2 exactly as
+ * the paper writes them, up to the library's rounding.  The CUDA library's edge sets
+ * are checked against this build at a stated tolerance on the flipped decisions (each
+ * flip within a relative 1e-12 of its threshold, see the decision audit below). */
+double orc_det_log(double x) { return log(x); }
+double orc_det_exp(double x) { return exp(x); }
+double orc_det_log1p(double x) { return log1p(x); }
+double orc_det_pow(double x, double y) { return pow(x, y); }
+double orc_det_sinpi(double x) { return sin(M_PI * x); }
+double orc_det_acosh(double z) { return acosh(z); }
+#else
 static const double PI_D = 0x1.921fb54442d18p+1;
 
 static double pow2i(int k) { /* exact 2^k for -1022 <= k <= 1023 */
@@ -390,6 +413,7 @@ double orc_det_sinpi(double x) {
 
 /* acosh z = ln(z + sqrt(z^2 - 1)), z >= 1. */
 double orc_det_acosh(double z) { return orc_det_log(z + sqrt(z * z - 1.0)); }
+#endif /* ORC_PLAIN */
 
 /* x^(1/d) for the threshold variant; x for d = 1. */
 static double root_d(double x, int d) {
@@ -541,13 +565,22 @@ static double girg_p(const girg_model* M, double wu, double wv, uint32_t D) {
     return girg_p_at(M, wu, wv, (double)D * 0x1p-32);
 }
 
-/* Threshold variant: edge iff ||x_u - x_v||^d <= K w_u w_v / W (r <= c q^(1/d)). */
-static int girg_thresh_edge(const girg_model* M, double wu, double wv, uint32_t D) {
+/* The two sides of the threshold variant's test: r^d and K w_u w_v / W. */
+static void girg_thresh_sides(const girg_model* M, double wu, double wv, uint32_t D, double* rd,
+                              double* kq) {
     double q = (wu * wv) / M->W;
     double r = (double)D * 0x1p-32;
-    double rd = r;
-    for (int k = 1; k < M->d; k++) rd = rd * r;
-    return rd <= M->K * q;
+    double x = r;
+    for (int k = 1; k < M->d; k++) x = x * r;
+    *rd = x;
+    *kq = M->K * q;
+}
+
+/* Threshold variant: edge iff ||x_u - x_v||^d <= K w_u w_v / W (r <= c q^(1/d)). */
+static int girg_thresh_edge(const girg_model* M, double wu, double wv, uint32_t D) {
+    double rd, kq;
+    girg_thresh_sides(M, wu, wv, D, &rd, &kq);
+    return rd <= kq;
 }
 
 /* K from the c of Eq. 1: c^T (T > 0) or c^d (T = 0). */
@@ -625,6 +658,54 @@ static double pair_coin(uint64_t seed, uint32_t u, uint32_t v) {
 
 double orc_pair_coin(uint64_t seed, uint32_t u, uint32_t v) { return pair_coin(seed, u, v); }
 
+/* Decision audit (a test aid; off unless orc_audit_begin was called).  It changes no
+ * decision: it counts every decision the samplers take and records those whose two
+ * sides are within a relative eps of each other, the only ones that a different
+ * rounding of the same formulas can flip.  A record is three int64 (kind, a, b):
+ *   kind 1  per-pair coin U < p (a < b vertex ids),
+ *   kind 2  type-II acceptance U' pbar < p (a < b vertex ids),
+ *   kind 3  threshold test r^d <= K q (GIRG) or cosh d < cosh R (HRG) (a < b ids),
+ *   kind 4  geometric jump whose quotient ln U / ln(1 - pbar) lies within a relative
+ *           eps of an integer (a = cell A, b = stream word << 32 | chunk). */
+static struct {
+    int on;
+    double eps;
+    int64_t* buf;
+    int64_t cap, n, decisions;
+} g_audit;
+
+void orc_audit_begin(double eps, int64_t* buf, int64_t cap) {
+    g_audit.on = 1;
+    g_audit.eps = eps;
+    g_audit.buf = buf;
+    g_audit.cap = cap;
+    g_audit.n = 0;
+    g_audit.decisions = 0;
+}
+
+/* Stops the audit; returns the number of records (more than cap: only cap stored). */
+int64_t orc_audit_end(int64_t* decisions) {
+    if (decisions) *decisions = g_audit.decisions;
+    g_audit.on = 0;
+    return g_audit.n;
+}
+
+static void audit_record(int64_t kind, int64_t a, int64_t b) {
+    if (g_audit.n < g_audit.cap) {
+        g_audit.buf[3 * g_audit.n] = kind;
+        g_audit.buf[3 * g_audit.n + 1] = a;
+        g_audit.buf[3 * g_audit.n + 2] = b;
+    }
+    g_audit.n++;
+}
+
+/* One decision between x and y (x < y or x <= y): recorded when |x - y| <= eps |y|. */
+static void audit_cmp(int kind, double x, double y, int64_t a, int64_t b) {
+    if (!g_audit.on) return;
+    g_audit.decisions++;
+    if (fabs(x - y) <= g_audit.eps * fabs(y)) audit_record(kind, a, b);
+}
+
 static void emit(uint32_t* edges, int64_t cap, int64_t* m, uint32_t a, uint32_t b) {
     if (a > b) {
         uint32_t t = a;
@@ -647,10 +728,16 @@ int64_t orc_girg_allpairs(int64_t n, int d, const uint32_t* X, const double* w, 
         for (int64_t v = u + 1; v < n; v++) {
             uint32_t D = torus_dist(X + u * d, X + v * d, d);
             int e;
-            if (T == 0.0)
-                e = girg_thresh_edge(&M, w[u], w[v], D);
-            else
-                e = pair_coin(seed, (uint32_t)u, (uint32_t)v) < girg_p(&M, w[u], w[v], D);
+            if (T == 0.0) {
+                double rd, kq;
+                girg_thresh_sides(&M, w[u], w[v], D, &rd, &kq);
+                audit_cmp(3, rd, kq, u, v);
+                e = rd <= kq;
+            } else {
+                double U = pair_coin(seed, (uint32_t)u, (uint32_t)v), p = girg_p(&M, w[u], w[v], D);
+                audit_cmp(1, U, p, u, v);
+                e = U < p;
+            }
             if (e) emit(edges, cap, &m, (uint32_t)u, (uint32_t)v);
         }
     }
@@ -673,10 +760,14 @@ int64_t orc_hrg_allpairs(int64_t n, const uint32_t* X, const double* r, double R
             uint32_t D = circ_diff(X[u], X[v]);
             double cd = hrg_coshd(E[u], sh[u], E[v], sh[v], D);
             int e;
-            if (T == 0.0)
+            if (T == 0.0) {
+                audit_cmp(3, cd, H.coshR, u, v);
                 e = cd < H.coshR;
-            else
-                e = pair_coin(seed, (uint32_t)u, (uint32_t)v) < hrg_p_from_coshd(&H, cd);
+            } else {
+                double U = pair_coin(seed, (uint32_t)u, (uint32_t)v), p = hrg_p_from_coshd(&H, cd);
+                audit_cmp(1, U, p, u, v);
+                e = U < p;
+            }
             if (e) emit(edges, cap, &m, (uint32_t)u, (uint32_t)v);
         }
     }
@@ -908,13 +999,25 @@ static int type1_decide(cp_ctx* C, int64_t u, int64_t v) {
     uint32_t a = (uint32_t)(u < v ? u : v), b = (uint32_t)(u < v ? v : u);
     if (C->model == 0) {
         uint32_t D = torus_dist(C->X + (int64_t)a * C->d, C->X + (int64_t)b * C->d, C->d);
-        if (C->M.T == 0.0) return girg_thresh_edge(&C->M, C->w[a], C->w[b], D);
-        return pair_coin(C->seed, a, b) < girg_p(&C->M, C->w[a], C->w[b], D);
+        if (C->M.T == 0.0) {
+            double rd, kq;
+            girg_thresh_sides(&C->M, C->w[a], C->w[b], D, &rd, &kq);
+            audit_cmp(3, rd, kq, a, b);
+            return rd <= kq;
+        }
+        double U = pair_coin(C->seed, a, b), p = girg_p(&C->M, C->w[a], C->w[b], D);
+        audit_cmp(1, U, p, a, b);
+        return U < p;
     }
     uint32_t D = circ_diff(C->X[a], C->X[b]);
     double cd = hrg_coshd(C->E[a], C->sh[a], C->E[b], C->sh[b], D);
-    if (C->H.T == 0.0) return cd < C->H.coshR;
-    return pair_coin(C->seed, a, b) < hrg_p_from_coshd(&C->H, cd);
+    if (C->H.T == 0.0) {
+        audit_cmp(3, cd, C->H.coshR, a, b);
+        return cd < C->H.coshR;
+    }
+    double U = pair_coin(C->seed, a, b), p = hrg_p_from_coshd(&C->H, cd);
+    audit_cmp(1, U, p, a, b);
+    return U < p;
 }
 
 static double pair_p(cp_ctx* C, int64_t u, int64_t v) {
@@ -1041,8 +1144,12 @@ static int cmp_t2(const void* a, const void* b) {
 /* One geometric jump (Sec. 3.2) under a bound pbar < 1, Lb = ln(1 - pbar), from the
  * uniform U of the words (lo, hi): X = floor(ln U / Lb), the number of positions skipped
  * before the next candidate; -1 where X >= 2^63 (the stream then leaves its chunk). */
+static double jump_quotient(double Lb, uint32_t lo, uint32_t hi) {
+    return orc_det_log(orc_uniform(lo, hi)) / Lb;
+}
+
 static int64_t geometric_jump(double Lb, uint32_t lo, uint32_t hi) {
-    double x = floor(orc_det_log(orc_uniform(lo, hi)) / Lb);
+    double x = floor(jump_quotient(Lb, lo, hi));
     return x >= 0x1p63 ? -1 : (int64_t)x;
 }
 
@@ -1095,6 +1202,12 @@ static void sample_stream(cp_ctx* C, const struct t2rec* m, int64_t nm) {
             uint64_t X = 0;
             if (pbar < 1.0) {
                 int64_t x = geometric_jump(Lb, o[0], o[1]);
+                if (g_audit.on) { /* distance of the quotient from its nearest integer */
+                    double xq = jump_quotient(Lb, o[0], o[1]), k = floor(xq + 0.5);
+                    g_audit.decisions++;
+                    if (k >= 1.0 && fabs(xq - k) <= g_audit.eps * k)
+                        audit_record(4, (int64_t)A, ((int64_t)pack << 32) | (int64_t)h);
+                }
                 if (x < 0) break;
                 X = (uint64_t)x;
             }
@@ -1107,7 +1220,9 @@ static void sample_stream(cp_ctx* C, const struct t2rec* m, int64_t nm) {
             int64_t u = C->order[alo + (int64_t)(idx / S)];
             int64_t v = C->order[blo[q] + (int64_t)(ib - pre[q])];
             C->stats[3]++;
-            if (orc_uniform(o[2], o[3]) * pbar < pair_p(C, u, v)) {
+            double acc = orc_uniform(o[2], o[3]) * pbar, p = pair_p(C, u, v);
+            audit_cmp(2, acc, p, u < v ? u : v, u < v ? v : u);
+            if (acc < p) {
                 emit(C->edges, C->cap, &C->m, (uint32_t)u, (uint32_t)v);
                 C->stats[7]++;
             }

@@ -76,6 +76,8 @@ SIGNATURES = {
     "girg_last_scale": (DBL, []),
     "girg_expected_edges": (I64, [P, P]),
     "girg_scratch_bytes": (I64, [P]),
+    "girg_scratch_pool_usage": (I32, [P, P, P, I32]),
+    "girg_scratch_pool_trim": (I32, [I64]),
     "girg_server_create": (I32, [I32, I64, P]),
     "girg_server_submit": (I32, [P, P, P, I64, I64]),
     "girg_server_poll": (I32, [P, P, I32, I32]),
@@ -162,6 +164,33 @@ def girg_expected_edges(*, n, d, beta, T, avg_deg=0.0, c=0.0, w_min=1.0, seed=1,
 def last_K() -> float:
     """The scale K (c^T, or c^d at T = 0) of this thread's last generate call."""
     return load().girg_last_scale()
+
+
+def scratch_pool_usage(reset_high: bool = False) -> dict:
+    """The library's scratch pool on the current device: reserved, used and high-water
+    bytes (``reset_high`` resets the high-water mark after reading it)."""
+    _torch()
+    r, u, h = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    st = load().girg_scratch_pool_usage(ctypes.byref(r), ctypes.byref(u), ctypes.byref(h),
+                                        1 if reset_high else 0)
+    if st != GIRG_OK:
+        raise GirgError(st, "girg_scratch_pool_usage")
+    return {"reserved": r.value, "used": u.value, "used_high": h.value}
+
+
+def scratch_pool_trim(keep_bytes: int = 0) -> None:
+    """Return the unused memory of the library's scratch pool to the driver."""
+    _torch()
+    st = load().girg_scratch_pool_trim(keep_bytes)
+    if st != GIRG_OK:
+        raise GirgError(st, "girg_scratch_pool_trim")
+
+
+def scratch_bytes(*, n, d, beta, T, avg_deg=0.0, c=0.0, w_min=1.0, seed=1, edge_bytes=4,
+                  precision=PRECISION_FP32, level_cap=0) -> int:
+    """The server's admission estimate of one request's peak scratch (bytes)."""
+    p = GirgParams(n, d, beta, T, avg_deg, c, w_min, seed, edge_bytes, precision, level_cap)
+    return load().girg_scratch_bytes(ctypes.byref(p))
 
 
 def last_phase_ms() -> dict:

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -43,29 +44,50 @@ struct Status {
         if (e_ != cudaSuccess) throw CudaFail{e_}; \
     } while (0)
 
-// Scratch allocations on the stream's memory pool, freed on scope exit.
+// The library's own memory pool on the current device, created on first use and kept
+// until the process exits.  Every call's scratch is taken from it with
+// cudaMallocFromPoolAsync and given back with cudaFreeAsync on the call's stream; its
+// release threshold is raised so that later calls reuse the freed memory instead of
+// returning it to the driver after each synchronisation.  The caller's pools (the
+// device's default pool, PyTorch's caching allocator) are left as they are;
+// girg_scratch_pool_trim hands the unused part back.
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+
+cudaMemPool_t library_pool() {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxPoolDevices) throw CudaFail{cudaErrorInvalidDevice};
+    std::lock_guard<std::mutex> lk(g_pool_mutex);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        CK(cudaMemPoolCreate(&pool, &props));
+        uint64_t thr = ~0ull;
+        CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        g_pools[dev] = pool;
+    }
+    return g_pools[dev];
+}
+
+// Scratch allocations from the library's pool, freed on scope exit (stream-ordered).
 struct Scratch {
     cudaStream_t st;
+    cudaMemPool_t pool;
     std::vector<void*> ptrs;
-    explicit Scratch(cudaStream_t s) : st(s) {
-        // keep freed pool memory for reuse by later calls (once per process; thread-safe)
-        static const bool pool_set = [] {
-            int dev = 0;
-            cudaMemPool_t pool;
-            if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-                uint64_t thr = ~0ull;
-                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-            }
-            return true;
-        }();
-        (void)pool_set;
-    }
+    explicit Scratch(cudaStream_t s) : st(s), pool(library_pool()) {}
     template <class T>
     T* get(size_t count) {
         void* p = nullptr;
         size_t bytes = count * sizeof(T);
         if (bytes < 256) bytes = 256;
-        CK(cudaMallocAsync(&p, bytes, st));
+        CK(cudaMallocFromPoolAsync(&p, bytes, pool, st));
         ptrs.push_back(p);
         return static_cast<T*>(p);
     }
@@ -920,6 +942,39 @@ int64_t girg_expected_edges(const girg_params* params, void* stream) {
 }
 
 double girg_last_scale(void) { return g_last_K; }
+
+int girg_scratch_pool_usage(int64_t* reserved, int64_t* used, int64_t* used_high,
+                            int32_t reset_high) {
+    return guarded([&] {
+        cudaMemPool_t pool = library_pool();
+        uint64_t v = 0;
+        if (reserved) {
+            CK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v));
+            *reserved = (int64_t)v;
+        }
+        if (used) {
+            CK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v));
+            *used = (int64_t)v;
+        }
+        if (used_high) {
+            CK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v));
+            *used_high = (int64_t)v;
+        }
+        if (reset_high) {
+            uint64_t zero = 0;
+            CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+        }
+        return GIRG_OK;
+    });
+}
+
+int girg_scratch_pool_trim(int64_t keep_bytes) {
+    if (keep_bytes < 0) return GIRG_E_PARAM;
+    return guarded([&] {
+        CK(cudaMemPoolTrimTo(library_pool(), (size_t)keep_bytes));
+        return GIRG_OK;
+    });
+}
 
 int girg_last_stats(int64_t* out, int32_t len) {
     const int k = len < kNumStats ? len : kNumStats;

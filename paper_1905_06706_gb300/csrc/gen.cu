@@ -7,6 +7,7 @@
 // 128-bit fixed point (so W is the exactly rounded sum), counts the buckets and
 // takes their largest weights (and HRG radius ranges), and optionally the FP64
 // sums the degree formula of App. B.2 needs.
+#include <atomic>
 #include "internal.cuh"
 #include "kernels.h"
 
@@ -373,6 +374,19 @@ __global__ void __launch_bounds__(1024) k_sort_top(double* __restrict__ buf,
 bool det_tables_gen() { return det_tables_ready(); }
 
 // ------------------------------------------------------------------ launchers
+int device_sms() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v == 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+            v = 1;
+        cache[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
 static int grid_for(int64_t n, int threads, int max_blocks) {
     int64_t b = (n + threads - 1) / threads;
     if (b > max_blocks) b = max_blocks;
@@ -384,7 +398,7 @@ void launch_girg_points(int64_t n, int d, double beta, double w_min, uint64_t se
                         uint32_t* X, cudaStream_t st) {
     const double expo = -1.0 / (beta - 1.0);
     ++g_launches;
-    k_girg_points<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(n, d, expo, w_min, (uint32_t)seed,
+    k_girg_points<<<grid_for(n, 256, device_sms() * 32), 256, 0, st>>>(n, d, expo, w_min, (uint32_t)seed,
                                                              (uint32_t)(seed >> 32), w, X);
 }
 
@@ -393,17 +407,17 @@ void launch_hrg_points(int64_t n, double alpha, double R, uint64_t seed, double*
     const double ea = det_exp(alpha * R);
     const double cosh_aR = (ea + 1.0 / ea) * 0.5;
     ++g_launches;
-    k_hrg_points<<<grid_for(n, 256, 152 * 32), 256, 0, st>>>(n, alpha, cosh_aR - 1.0, R,
+    k_hrg_points<<<grid_for(n, 256, device_sms() * 32), 256, 0, st>>>(n, alpha, cosh_aR - 1.0, R,
                                                             (uint32_t)seed, (uint32_t)(seed >> 32),
                                                             r, w, X);
 }
 
 void launch_min_weight(int64_t n, const double* w, unsigned long long* out, cudaStream_t st) {
     ++g_launches;
-    k_min_weight<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, w, out);
+    k_min_weight<<<grid_for(n, 256, device_sms() * 8), 256, 0, st>>>(n, w, out);
 }
 
-int reduce_blocks(int64_t n) { return grid_for(n, 256, 152 * 8); }
+int reduce_blocks(int64_t n) { return grid_for(n, 256, 1216); }
 
 void launch_reduce(int64_t n, const double* w, const double* r, double w_min, int E0,
                    double* part_s2, Reduce* out, cudaStream_t st, const ThresholdJob* job) {

@@ -12,6 +12,10 @@ struct DevCfg;
 bool det_tables_gen();
 bool det_tables_pairs();
 
+// Streaming multiprocessors of the current device (queried once per device); grids of
+// grid-stride and persistent kernels are sized from it.
+int device_sms();
+
 // Kernel launches issued by the library on this host thread (for the benchmark's
 // launch count).
 extern thread_local unsigned long long g_launches;
@@ -40,7 +44,9 @@ void launch_girg_points(int64_t n, int d, double beta, double w_min, uint64_t se
 void launch_hrg_points(int64_t n, double alpha, double R, uint64_t seed, double* r, double* w,
                        uint32_t* X, cudaStream_t st);
 void launch_min_weight(int64_t n, const double* w, unsigned long long* out, cudaStream_t st);
-// Blocks of the reduction (one per-block partial each).
+// Blocks of the reduction (one per-block partial each): a fixed partition of the
+// vertices, independent of the device, so that the sums finished in block order
+// round the same way on every GPU.
 int reduce_blocks(int64_t n);
 // part_s2 (reduce_blocks(n) doubles, or null): per-block sums of w^2.  With job (and
 // part_s2), the last block also finishes red->s2 in block order and writes the split

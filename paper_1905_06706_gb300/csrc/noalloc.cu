@@ -55,6 +55,28 @@ cudaError_t scratch_address(unsigned char** out) {
     return cudaSuccess;
 }
 
+// A caller pointer as the kernels see it: device (or managed) memory as given,
+// page-locked host memory mapped into the device through its device pointer.
+// Anything else -- pageable host memory, a pointer CUDA does not know -- returns
+// GIRG_E_PARAM before any device work, so a bad pointer becomes a status instead of
+// a memory fault on the GPU.
+int device_view(const void* p, void** out) {
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the error state of a failed lookup
+        return GIRG_E_PARAM;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        *out = const_cast<void*>(p);
+        return GIRG_OK;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+        *out = a.devicePointer;
+        return GIRG_OK;
+    }
+    return GIRG_E_PARAM;
+}
+
 }  // namespace
 
 extern "C" int girg_allpairs_noalloc(int64_t n, int32_t d, const uint32_t* d_X, const double* d_w,
@@ -65,6 +87,10 @@ extern "C" int girg_allpairs_noalloc(int64_t n, int32_t d, const uint32_t* d_X, 
         !(W > 0.0) || !num_edges || capacity_edges < 0)
         return GIRG_E_PARAM;
     if ((edge_bytes != 4 && edge_bytes != 8) || (precision != 0 && precision != 1))
+        return GIRG_E_PARAM;
+    void *edges = nullptr, *X = nullptr, *w = nullptr;
+    if (device_view(d_edges, &edges) != GIRG_OK || device_view(d_X, &X) != GIRG_OK ||
+        device_view(d_w, &w) != GIRG_OK)
         return GIRG_E_PARAM;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char* base = nullptr;
@@ -77,7 +103,8 @@ extern "C" int girg_allpairs_noalloc(int64_t n, int32_t d, const uint32_t* d_X, 
     const bool tzero = T == 0.0;
     const double K = girg_K_of_c(c, d, T);
     const float gamma = (float)(std::log2(K) / (2.0 * d));
-    launch_scale(n, d_w, 0.5 * std::log2(W), gamma, (float)(1.0 / d), sv, st);
+    launch_scale(n, static_cast<const double*>(w), 0.5 * std::log2(W), gamma, (float)(1.0 / d), sv,
+                 st);
     DevCfg cfg;
     memset(&cfg, 0, sizeof(cfg));
     cfg.n = (int32_t)n;
@@ -95,13 +122,13 @@ extern "C" int girg_allpairs_noalloc(int64_t n, int32_t d, const uint32_t* d_X, 
     cfg.dT = T > 0.0 ? (float)(d / T) : 0.0f;
     cfg.bandG = cfg.dT * 0x1p-14f + 0x1p-15f;
     cfg.band_ratio = 0x1p-16f;
-    cfg.edges = d_edges;
+    cfg.edges = edges;
     cfg.edge_bytes = edge_bytes;
     cfg.cap = capacity_edges;
     cfg.stats = counters;
     cfg.edge_count = counters + kNumStats;
     if (!det_tables_pairs()) return GIRG_E_CUDA;
-    launch_allpairs(cfg, d_X, d_w, sv, st);
+    launch_allpairs(cfg, static_cast<const uint32_t*>(X), static_cast<const double*>(w), sv, st);
     unsigned long long m = 0;
     if (cudaMemcpyAsync(&m, counters + kNumStats, sizeof(m), cudaMemcpyDeviceToHost, st) !=
         cudaSuccess)

@@ -1219,7 +1219,7 @@ bool det_tables_pairs() { return det_tables_ready(); }
 // ------------------------------------------------------------------ launchers
 void launch_rows(const DevCfg& cfg, cudaStream_t st) {
     int64_t b = (cfg.n + kAllocThreads - 1) / kAllocThreads;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > device_sms() * 16) b = device_sms() * 16;
     if (b < 1) b = 1;
     ++g_launches;
     k_rows<<<(unsigned)b, kAllocThreads, 0, st>>>(cfg);
@@ -1246,30 +1246,29 @@ void launch_prep_lists(const DevCfg& cfg, unsigned long long* lens, unsigned int
 
 void launch_enumerate(const DevCfg& cfg, cudaStream_t st) {
     g_launches += 2;
+    const unsigned grid = (unsigned)device_sms() * 8;
     switch (cfg.d) {
-        case 1: k_enum2<1><<<152 * 8, kEnumThreads, 0, st>>>(cfg);
-                k_enum1<1><<<152 * 8, kEnumThreads, 0, st>>>(cfg); break;
-        case 2: k_enum2<2><<<152 * 8, kEnumThreads, 0, st>>>(cfg);
-                k_enum1<2><<<152 * 8, kEnumThreads, 0, st>>>(cfg); break;
-        case 3: k_enum2<3><<<152 * 8, kEnumThreads, 0, st>>>(cfg);
-                k_enum1<3><<<152 * 8, kEnumThreads, 0, st>>>(cfg); break;
-        case 4: k_enum2<4><<<152 * 8, kEnumThreads, 0, st>>>(cfg);
-                k_enum1<4><<<152 * 8, kEnumThreads, 0, st>>>(cfg); break;
-        default: k_enum2<0><<<152 * 8, kEnumThreads, 0, st>>>(cfg);
-                 k_enum1<0><<<152 * 8, kEnumThreads, 0, st>>>(cfg); break;
+        case 1: k_enum2<1><<<grid, kEnumThreads, 0, st>>>(cfg);
+                k_enum1<1><<<grid, kEnumThreads, 0, st>>>(cfg); break;
+        case 2: k_enum2<2><<<grid, kEnumThreads, 0, st>>>(cfg);
+                k_enum1<2><<<grid, kEnumThreads, 0, st>>>(cfg); break;
+        case 3: k_enum2<3><<<grid, kEnumThreads, 0, st>>>(cfg);
+                k_enum1<3><<<grid, kEnumThreads, 0, st>>>(cfg); break;
+        case 4: k_enum2<4><<<grid, kEnumThreads, 0, st>>>(cfg);
+                k_enum1<4><<<grid, kEnumThreads, 0, st>>>(cfg); break;
+        default: k_enum2<0><<<grid, kEnumThreads, 0, st>>>(cfg);
+                 k_enum1<0><<<grid, kEnumThreads, 0, st>>>(cfg); break;
     }
 }
 
 // Blocks of a persistent launch: the resident blocks per SM times the SMs.
 template <class K>
 static unsigned persistent_grid(K kernel, int threads) {
-    int dev = 0, sms = 152, per = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0) != cudaSuccess ||
         per < 1)
         per = 1;
-    return (unsigned)(sms * per);
+    return (unsigned)(device_sms() * per);
 }
 
 void launch_type1(const DevCfg& cfg, cudaStream_t st) {
@@ -1313,7 +1312,8 @@ void launch_allpairs(const DevCfg& cfg, const uint32_t* X, const double* w, cons
     View V{X, sv, w, nullptr, nullptr, nullptr, nullptr, cfg.n};
     const unsigned int ntile = (unsigned int)((cfg.n + 63) / 64);
     unsigned long long ntri = (unsigned long long)ntile * (ntile + 1) / 2;
-    unsigned int grid = ntri < 152ull * 8 ? (unsigned int)ntri : 152 * 8;
+    const unsigned int gmax = (unsigned int)device_sms() * 8;
+    unsigned int grid = ntri < gmax ? (unsigned int)ntri : gmax;
     ++g_launches;
     switch (cfg.d) {
         case 1: k_allpairs<1><<<grid, 256, 0, st>>>(cfg, V, ntile); break;

@@ -397,11 +397,11 @@ void place_by_counts(const uint32_t* key, const uint32_t* slot, const uint32_t* 
     const uint32_t big_cap = (uint32_t)(place_tmp_words(n) - 1);
     uint32_t* nbig = tmp;  // zeroed by the caller
     uint32_t* big = tmp + 1;
-    const int grid = grid_for(n, 256, 152 * 16);
+    const int grid = grid_for(n, 256, device_sms() * 16);
     g_launches += 3;
     k_place<<<grid, 256, 0, st>>>(n, key, slot, offs, skey, tid);
     k_rank<<<grid, 256, 0, st>>>(n, skey, offs, tid, sid, big, nbig, big_cap);
-    k_sort_cells<<<152 * 2, 256, 0, st>>>(offs, big, nbig, big_cap, sid);
+    k_sort_cells<<<device_sms() * 2, 256, 0, st>>>(offs, big, nbig, big_cap, sid);
 }
 
 // ------------------------------------------------------------------ gathers
@@ -458,7 +458,7 @@ void launch_keys(int64_t n, int d, const double* w, const uint32_t* X, double w_
     memcpy(tab.I, I, sizeof(tab.I));
     memcpy(tab.base, layer_base, sizeof(tab.base));
     ++g_launches;
-    k_keys<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, d, w, X, w_min, tab, key, val, cnt, slots);
+    k_keys<<<grid_for(n, 256, device_sms() * 16), 256, 0, st>>>(n, d, w, X, w_min, tab, key, val, cnt, slots);
 }
 
 void launch_gather_girg(int64_t n, int d, const uint32_t* perm, const uint32_t* X,
@@ -466,21 +466,21 @@ void launch_gather_girg(int64_t n, int d, const uint32_t* perm, const uint32_t* 
                         float invd, uint32_t* Xs, double* ws, float* sv, uint8_t* slayer,
                         cudaStream_t st) {
     ++g_launches;
-    k_gather_girg<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, d, perm, X, w, w_min, log2W_half,
+    k_gather_girg<<<grid_for(n, 256, device_sms() * 16), 256, 0, st>>>(n, d, perm, X, w, w_min, log2W_half,
                                                               gamma, invd, Xs, ws, sv, slayer);
 }
 
 void launch_scale(int64_t n, const double* w, double log2W_half, float gamma, float invd,
                   float* sv, cudaStream_t st) {
     ++g_launches;
-    k_scale<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, w, log2W_half, gamma, invd, sv);
+    k_scale<<<grid_for(n, 256, device_sms() * 16), 256, 0, st>>>(n, w, log2W_half, gamma, invd, sv);
 }
 
 void launch_gather_hrg(int64_t n, const uint32_t* perm, const uint32_t* X, const double* r,
                        const double* w, uint32_t* Xs, double* rs, float* E32, float* einv32,
                        float* sh32, uint8_t* slayer, cudaStream_t st) {
     ++g_launches;
-    k_gather_hrg<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, perm, X, r, w, Xs, rs, E32,
+    k_gather_hrg<<<grid_for(n, 256, device_sms() * 16), 256, 0, st>>>(n, perm, X, r, w, Xs, rs, E32,
                                                              einv32, sh32, slayer);
 }
 

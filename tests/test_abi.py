@@ -57,6 +57,19 @@ def test_invalid_parameters_rejected_on_host(lib, bad):
     assert m.value == -1  # nothing was written
 
 
+def test_noalloc_refuses_pointers_the_gpu_cannot_use(lib):
+    """Pageable host buffers (and, on a machine without a GPU, every pointer) are
+    refused by the no-allocation entry point before any device work."""
+    import numpy as np
+    X = np.zeros(1000, dtype=np.uint32)
+    w = np.ones(1000, dtype=np.float64)
+    out = np.zeros((4000, 2), dtype=np.int32)
+    m = ctypes.c_int64(-1)
+    st = lib.girg_allpairs_noalloc(1000, 1, X.ctypes.data, w.ctypes.data, 1000.0, 0.5, 1.0, 1,
+                                   0, 4, out.ctypes.data, len(out), ctypes.byref(m), None)
+    assert st == gg.GIRG_E_PARAM and m.value == -1 and not out.any()
+
+
 def test_invalid_hrg_and_points_rejected(lib):
     m = ctypes.c_int64(0)
     for hp in (gg.HrgParams(1000, 0.5, 0.5, 0.0, 10.0, 1, 4, 0, 0),    # alpha must exceed 1/2

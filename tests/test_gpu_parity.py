@@ -420,11 +420,15 @@ def test_benchmark_workload_full_size_edge_for_edge():
     w, X = O.girg_points(n, d, beta, 1.0, 1)
     W = O.exact_sum(w)
     c = O.girg_solve_c(10.0, w, d, T, W)
-    ref = O.girg_cellpairs(X, w, 1.0, W, T, c, 1, cap=n * 8)
     ed = _edges(n * 8)
+    # the graph the benchmark times: the scale K solved on the device
     r = gg.girg_generate(ed, n=n, d=d, beta=beta, T=T, avg_deg=10.0, seed=1)
     assert r.status == gg.GIRG_OK
     assert r.c_used == pytest.approx(c, rel=1e-9)
+    ref_solved = O.girg_cellpairs(X, w, 1.0, W, T, None, 1, cap=n * 8, K=gg.last_K())
+    assert _set(ed, r.num_edges) == O.edge_set(ref_solved.edges)
+    # and at the oracle's own c
+    ref = O.girg_cellpairs(X, w, 1.0, W, T, c, 1, cap=n * 8)
     r = gg.girg_generate(ed, n=n, d=d, beta=beta, T=T, c=c, seed=1)
     assert r.status == gg.GIRG_OK
     assert _set(ed, r.num_edges) == O.edge_set(ref.edges)

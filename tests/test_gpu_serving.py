@@ -1,13 +1,16 @@
 """The continuous-batching server: every request's graph is the same alone and in
 the mix (edge count and order-independent checksum, and the edge set itself for a
-few), with requests of mixed size, dimension, exponent, temperature and degree."""
+few), with requests of mixed size, dimension, exponent, temperature and degree; in the
+mix, requests equal the oracle's cell-pair sampler edge for edge; the admission
+estimate of a request's scratch is at least the scratch it actually takes."""
 import math
 
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
-import paper_1905_06706_gb300 as gg
+import oracle as O  # noqa: E402
+import paper_1905_06706_gb300 as gg  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -78,3 +81,64 @@ def test_tiny_budget_runs_one_at_a_time():
         assert b.t_start_us >= a.t_done_us  # never two at once under a 1-byte budget
     for r in res:
         assert (r.num_edges, r.checksum) == alone[r.request_id]
+
+
+def test_requests_in_the_mix_equal_the_oracle():
+    """Requests with the oracle's c (so both sides use the same scale K) run in a mix
+    with others; each stored edge set equals the oracle's cell-pair sampler."""
+    reqs = _mixed_requests(24, 11, n_max=60_000)
+    checked = [i for i, q in enumerate(reqs) if q["n"] <= 40_000][:5]
+    assert len(checked) >= 4
+    for i in checked:
+        q = reqs[i]
+        w, X = O.girg_points(q["n"], q["d"], q["beta"], 1.0, q["seed"])
+        W = O.exact_sum(w)
+        q["c"] = O.girg_solve_c(q["avg_deg"], w, q["d"], q["T"], W)
+        q["_ref"] = O.edge_set(O.girg_cellpairs(X, w, 1.0, W, q["T"], q["c"], q["seed"],
+                                                cap=_cap(q)).edges)
+    bufs = [torch.empty((_cap(q), 2), dtype=torch.int32, device="cuda") for q in reqs]
+    torch.cuda.synchronize()
+    with gg.Server(workers=8, memory_budget_bytes=8 << 30) as srv:
+        for i, q in enumerate(reqs):
+            srv.submit(i, bufs[i], **{k: v for k, v in q.items() if not k.startswith("_")})
+        got = {}
+        while len(got) < len(reqs):
+            for r in srv.poll(64, wait_for=1):
+                got[r.request_id] = r
+    for i in checked:
+        r = got[i]
+        assert r.status == gg.GIRG_OK
+        e = bufs[i][: r.num_edges].cpu().numpy().astype(np.int64)
+        assert set((e[:, 0] * (1 << 32) + e[:, 1]).tolist()) == reqs[i]["_ref"], i
+
+
+def test_admission_estimate_bounds_the_scratch_taken():
+    """The server admits requests by girg_scratch_bytes; each request's actual peak
+    scratch (the high-water mark of the library's pool, the request running alone) must
+    not exceed it, and a mix under a budget of the largest estimate keeps the pool's
+    high-water mark within the budget plus one request."""
+    reqs = _mixed_requests(16, 13, n_max=1_000_000)
+    est = []
+    for q in reqs:
+        e = gg.scratch_bytes(**q)
+        torch.cuda.synchronize()
+        gg.scratch_pool_trim(0)
+        gg.scratch_pool_usage(reset_high=True)
+        r = gg.girg_generate(None, **q)
+        assert r.status == gg.GIRG_OK
+        torch.cuda.synchronize()
+        peak = gg.scratch_pool_usage()["used_high"]
+        print(f"n={q['n']} d={q['d']} T={q['T']:.2f}: peak {peak} estimate {e} "
+              f"({peak / e:.2f})")
+        assert peak <= e, (q, peak, e)
+        est.append(e)
+    budget = max(est)
+    gg.scratch_pool_usage(reset_high=True)
+    with gg.Server(workers=8, memory_budget_bytes=budget) as srv:
+        for i, q in enumerate(reqs):
+            srv.submit(i, None, **q)
+        res = []
+        while len(res) < len(reqs):
+            res += srv.poll(64, wait_for=1)
+    assert all(r.status == gg.GIRG_OK for r in res)
+    assert gg.scratch_pool_usage()["used_high"] <= budget

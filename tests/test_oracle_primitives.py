@@ -131,6 +131,37 @@ def test_det_log_exp_monotone_and_exact_points():
         assert _ulp_err(O.det_exp(x), mp.exp(mp.mpf(x))) <= 0.51, j
 
 
+def test_det_log_exp_dense_at_table_boundaries_against_mpmath():
+    """The fixed-point ln and exp are the same method as the CUDA library's (so that both
+    take identical decisions); this sweep pins that method itself against 60-digit
+    arithmetic where a wrong table entry or reduction would show first: significands
+    within 64 ulps of every switch of the table index j = round(64 m), and arguments
+    within 64 ulps of every switch of the reduction k = round(64 x / ln 2)."""
+    mp.mp.dps = 60
+    worst = 0
+    offs = list(range(-64, 65, 4))
+    for j in range(45, 92):
+        for e in (-600, -3, 0, 1, 40, 700):
+            edge = math.ldexp((j + 0.5) / 64.0, e)
+            for k in offs:
+                x = edge + k * math.ulp(edge)
+                if x <= 0:
+                    continue
+                worst = max(worst, _ulp_err(O.det_log(x), mp.log(mp.mpf(x))))
+    assert worst <= 0.55, worst
+    worst = 0
+    ln2_64 = mp.log(2) / 64
+    for kk in list(range(-40, 41)) + list(range(-60000, 60001, 1499)):
+        edge = float((kk - mp.mpf(0.5)) * ln2_64)
+        for k in offs:
+            y = edge + k * math.ulp(edge if edge else 1e-300)
+            ref = mp.exp(mp.mpf(y))
+            if float(ref) < 2.2250738585072014e-308:
+                continue
+            worst = max(worst, _ulp_err(O.det_exp(y), ref))
+    assert worst <= 0.55, worst
+
+
 def test_det_log1p_and_pow_against_mpmath():
     mp.mp.dps = 60
     rng = np.random.default_rng(6)
