@@ -66,7 +66,7 @@ def kernel_source_digest() -> str:
     """SHA-256 (16 hex digits) of the sources the sampling kernels are built from."""
     import hashlib
     h = hashlib.sha256()
-    for name in ("pairs.cu", "internal.cuh", "common.cuh"):
+    for name in ("pairs.cu", "internal.cuh", "common.cuh"):  # the sampling kernels' sources
         with open(os.path.join(ROOT, "paper_1905_06706_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -88,9 +88,11 @@ def _ncu_metric(kernel: str, metric: str):
     return None
 
 
-# Instruction issue peak of the GPU: 4 warp schedulers per SM, each issuing at most one
-# warp instruction per cycle, 152 SMs, 2070 MHz maximum SM clock.
-ISSUE_PEAK = 4 * 152 * 2.07e9
+def _sms() -> int:
+    """Streaming multiprocessors of the current GPU (the instruction-issue peak is 4 warp
+    schedulers per SM, each issuing at most one warp instruction per cycle)."""
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
 def _ncu_traffic(kernel: str):
@@ -678,6 +680,18 @@ def main():
                      "achieved": step_bytes / (step_ms / 1e3) / 1e9, "peak": hbm,
                      "unit": "GB/s"}
         step_roof["frac"] = step_roof["achieved"] / hbm
+        # what bounds the sampling kernels: instruction issue (warp instructions per
+        # launch from the committed ncu summary of the same kernel source, over the live
+        # launch duration)
+        winst = _ncu_metric(kname, "smsp__inst_executed.sum")
+        issue_peak = 4 * _sms() * 2.07e9
+        issue_roof = {"kernel": kname, "bound": "alu", "unit": "warp instructions/s",
+                      "peak": issue_peak,
+                      "peak_kind": f"derived: 4 schedulers x {_sms()} SMs x 2070 MHz",
+                      "warp_instructions": winst,
+                      "achieved": (winst / (kms / 1e3)) if (winst and kms > 0) else None}
+        if issue_roof["achieved"] is not None:
+            issue_roof["frac"] = issue_roof["achieved"] / issue_peak
         samp_ms = ph["enumerate"] + ph["type1"] + ph["type2"]
         edge_roof = (m_step * eb / (statistics.median(ms) / 1e3)) / 1e9
         line = {

@@ -65,8 +65,11 @@ extern "C" {
  *              edge count and the checksum of girg_last_stats are still produced, as
  *              the paper's benchmarks replace storage by a checksum, Sec. 5)
  *   precision  GIRG_PRECISION_FP32 or GIRG_PRECISION_FP64
- *   level_cap  deepest quadtree level to use, 0 = default min(32/d, (bitlen(n)+4)/d);
- *              a tuning knob: the sample stays exact for any value >= 1
+ *   level_cap  deepest quadtree level to use; 0 = default: min(32/d, (bitlen(n)+4)/d)
+ *              at T = 0, min(32/d, floor((2 bitlen(n) - 2 - d) / (2d))) at T > 0 (about
+ *              2^(d/2) vertices per cell, which balances the all-pairs tests of
+ *              neighbouring cells against the distant cells' jumps); a tuning knob:
+ *              the sample is exact for any value >= 1, the graph drawn depends on it
  */
 typedef struct {
     int64_t n;
@@ -239,8 +242,8 @@ int girg_last_stats(int64_t* out, int32_t len);
 
 /* Milliseconds spent in each phase of the last call on this host thread
  * (CUDA events): [0] points+reductions, [1] host work up to the layer partition
- * (search for c, levels), [2] keys+sort+gather, [3] cell-pair enumeration, [4] type I,
- * [5] type-II streams, [6] total; host wall clock: [7] reduction readback, [8] search
+ * (search for c, levels), [2] keys+sort+gather, [3] cell-pair enumeration with the
+ * scans of its lists, [4] the type-I kernel, [5] the type-II kernel, [6] total; host wall clock: [7] reduction readback, [8] search
  * for c, [9] table build (the type-II bound tables are built while the sort runs on
  * the device).  Copies
  * min(len, 10) values; returns the number copied. */

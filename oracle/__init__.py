@@ -99,7 +99,7 @@ def _load(plain: bool = False):
             "orc_hrg_allpairs": (i64, [i64, P, P, dbl, dbl, u64, P, i64]),
             "orc_morton": (u64, [P, i32, i32]),
             "orc_cell_linf": (u32, [u64, u64, i32, i32]),
-            "orc_level_cap": (i32, [i64, i32]),
+            "orc_level_cap": (i32, [i64, i32, dbl]),
             "orc_chunk_log": (i32, [dbl]),
             "orc_layer_of": (i32, [dbl, dbl]),
             "orc_geometric_jumps": (None, [i64, dbl, P, P, P]),
@@ -181,8 +181,9 @@ def cell_linf(A: int, B: int, d: int, level: int, plain=False) -> int:
     return _load(plain).orc_cell_linf(A, B, d, level)
 
 
-def level_cap(n: int, d: int, plain=False) -> int:
-    return _load(plain).orc_level_cap(n, d)
+def level_cap(n: int, d: int, T: float, plain=False) -> int:
+    """The default deepest quadtree level for n vertices in dimension d at temperature T."""
+    return _load(plain).orc_level_cap(n, d, T)
 
 
 def geometric_jumps(pbar: float, lo, hi, plain=False):

@@ -822,15 +822,20 @@ static uint32_t cell_linf(uint64_t A, uint64_t B, int d, int l) {
 
 uint32_t orc_cell_linf(uint64_t A, uint64_t B, int d, int l) { return cell_linf(A, B, d, l); }
 
-/* Deepest level used: levels beyond floor(32/d) have no room in a 32-bit
- * Morton code, and levels with more than 2^(bitlen(n)+4) <= 32 n cells gain
- * nothing (capping a comparison level only makes cells coarser; the sample
- * stays exact because every bound is computed from the actual cells). */
-int orc_level_cap(int64_t n, int d) {
+/* Deepest level used (the paper leaves the maximum depth open).  Capping a
+ * comparison level only makes cells coarser; the sample stays exact because every
+ * bound is computed from the actual cells.  Levels beyond floor(32/d) have no room
+ * in a 32-bit Morton code.  At T = 0 there are no distant items, and levels with
+ * more than 2^(bitlen(n)+4) <= 32 n cells gain nothing.  At T > 0 a cell with m
+ * vertices of a bucket costs about 3^d m^2 type-I pair tests and 6^d - 3^d distant
+ * partner cells; with N cells and n vertices the sum 3^d n^2 / N + (6^d - 3^d) N is
+ * smallest near N = n 2^(-d/2), i.e. at the level floor(log2(n) / d - 1/2), with
+ * log2 n taken as bitlen(n) - 1. */
+int orc_level_cap(int64_t n, int d, double T) {
     int bitlen = 0;
     while (bitlen < 63 && ((int64_t)1 << bitlen) <= n) bitlen++;
     int a = 32 / d;
-    int b = (bitlen + 4) / d;
+    int b = T > 0.0 ? (2 * bitlen - 2 - d) / (2 * d) : (bitlen + 4) / d;
     if (b < 1) b = 1;
     return a < b ? a : b;
 }
@@ -1298,7 +1303,7 @@ static void recur(cp_ctx* C, int l, uint64_t A, uint64_t B) {
 static int cp_prepare(cp_ctx* C, double w_min, int lcap_override) {
     int64_t n = C->n;
     int d = C->d;
-    C->lcap = orc_level_cap(n, d);
+    C->lcap = orc_level_cap(n, d, C->model == 0 ? C->M.T : C->H.T);
     if (lcap_override > 0) C->lcap = lcap_override < 32 / d ? lcap_override : 32 / d;
     memset(C->lcount, 0, sizeof(C->lcount));
     for (int i = 0; i < MAXL; i++) {

@@ -135,10 +135,16 @@ int bitlen64(uint64_t x) {
     return b;
 }
 
-int default_level_cap(int64_t n, int d) {
+// Deepest quadtree level by default: floor(32/d) at most (32-bit Morton codes).  At
+// T = 0 (type-I items only) deep cells only cut pair tests, down to about 2^(bitlen+4)
+// cells.  At T > 0 the type-I pairs of a level (3^d m^2 per cell of m vertices) and its
+// distant partner cells (6^d - 3^d per cell) balance near n 2^(-d/2) cells, the level
+// floor(log2(n)/d - 1/2) with log2 n = bitlen - 1; timing level caps on GB300 put the
+// fastest one there for d = 1..4 and n = 10^6 .. 2^24.
+int default_level_cap(int64_t n, int d, double T) {
     int bl = 0;
     while (bl < 63 && ((int64_t)1 << bl) <= n) ++bl;
-    int a = 32 / d, b = (bl + 4) / d;
+    int a = 32 / d, b = T > 0.0 ? (2 * bl - 2 - d) / (2 * d) : (bl + 4) / d;
     if (b < 1) b = 1;
     return a < b ? a : b;
 }
@@ -200,7 +206,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
         rhi[i] = bits_to_double(P.red.rmax[i]);
         if (cnt[i]) L = i + 1;
     }
-    int lcap = P.level_cap > 0 ? std::min(P.level_cap, 32 / d) : default_level_cap(n, d);
+    int lcap = P.level_cap > 0 ? std::min(P.level_cap, 32 / d) : default_level_cap(n, d, P.T);
     const double invT = P.T > 0.0 ? 1.0 / P.T : 0.0;
     int m_int = 0;
     if (P.T > 0.0 && invT == std::floor(invT) && invT <= 64.0) m_int = (int)invT;
@@ -595,7 +601,6 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
         ecfg.stats = estats;
         launch_enumerate(ecfg, st);
         ++passes;
-        tm.mark();  // enumeration done
         pre_cap1 = cfg.t1_cap + 1ull;
         pre_cap2 = cfg.stream_cap + 1ull;
         t1_pre = S.get<unsigned long long>(pre_cap1);
@@ -613,6 +618,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
         launch_scan_u32_to_u64_dev(cfg.stream_chunks, chunk_pre, lens + 1, (int64_t)pre_cap2, tmp, st);
         cfg.t1_pre = t1_pre;
         cfg.chunk_pre = chunk_pre;
+        tm.mark();  // enumeration and its list scans done
         launch_type1(cfg, st);
         tm.mark();  // type I done
         launch_type2(cfg, st);
@@ -690,7 +696,6 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
             continue;
         }
         for (int q = 0; q < kNumStats; ++q) est_acc[q] += es[q];
-        if (round == 0) tm.mark();  // (first round) enumeration done
         // exclusive prefixes of the pairs per type-I item and of the chunks per stream
         // (one past the last entry holds the total)
         const uint32_t n1 = (uint32_t)wc[0], ns = (uint32_t)wc[1];
@@ -716,6 +721,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
         launch_scan_u32_to_u64(cfg.stream_chunks, chunk_pre, (int64_t)ns + 1, tmp, st);
         cfg.t1_pre = t1_pre;
         cfg.chunk_pre = chunk_pre;
+        if (round == 0) tm.mark();  // (first round) enumeration and list scans done
         launch_type1(cfg, st);
         if (round == 0) tm.mark();  // (first round) type I done
         launch_type2(cfg, st);

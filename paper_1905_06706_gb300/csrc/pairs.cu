@@ -925,16 +925,9 @@ constexpr int kT1Threads = 256;
 constexpr unsigned kT1Grab = 1024;
 
 template <int DIM>
-__global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
-    if (cfg.lists_ok && *cfg.lists_ok == 0u) return;  // a list overflowed: the round is redone
-    __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
-    __shared__ unsigned int s_en[kWarps];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_en[warp] = 0;
-    __syncwarp();
-    WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
-    const View V = sorted_view(cfg);
-    Counters C;
+__device__ __forceinline__ void type1_loop(const DevCfg& cfg, const View& V, WarpEdges& we,
+                                           Counters& C) {
+    const int lane = threadIdx.x & 31;
     const uint32_t nit = (uint32_t)(*cfg.t1_count < cfg.t1_cap ? *cfg.t1_count : cfg.t1_cap);
     const unsigned long long* pre = cfg.t1_pre;
     const unsigned long long total = pre[nit];
@@ -1003,10 +996,23 @@ __global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
     }
     flush_edges<true>(cfg, we, 1);
     flush_mix(cfg, we);
-    flush_counters(cfg, C);
     unsigned long long te = t1_edges;
     for (int o = 16; o > 0; o >>= 1) te += __shfl_down_sync(0xffffffffu, te, o);
     if (lane == 0 && te) atomicAdd(&cfg.stats[kStatT1Edges], te);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
+    if (cfg.lists_ok && *cfg.lists_ok == 0u) return;  // a list overflowed: the round is redone
+    __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
+    __shared__ unsigned int s_en[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_en[warp] = 0;
+    __syncwarp();
+    WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
+    Counters C;
+    type1_loop<DIM>(cfg, sorted_view(cfg), we, C);
+    flush_counters(cfg, C);
 }
 
 // ------------------------------------------------------------------ type II
@@ -1025,16 +1031,9 @@ constexpr int kT2Threads = 256;
 constexpr int kT2RefillMin = 8;  // refill idle lanes once this many are idle
 
 template <int DIM>
-__global__ void __launch_bounds__(kT2Threads, 4) k_type2(DevCfg cfg) {
-    if (cfg.lists_ok && *cfg.lists_ok == 0u) return;  // a list overflowed: the round is redone
-    __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
-    __shared__ unsigned int s_en[kWarps];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_en[warp] = 0;
-    __syncwarp();
-    WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
-    const View V = sorted_view(cfg);
-    Counters C;
+__device__ __forceinline__ void type2_loop(const DevCfg& cfg, const View& V, WarpEdges& we,
+                                           Counters& C) {
+    const int lane = threadIdx.x & 31;
     const uint32_t nst =
         (uint32_t)(*cfg.stream_count < cfg.stream_cap ? *cfg.stream_count : cfg.stream_cap);
     const unsigned long long* pre = cfg.chunk_pre;
@@ -1177,8 +1176,21 @@ __global__ void __launch_bounds__(kT2Threads, 4) k_type2(DevCfg cfg) {
         flush_edges(cfg, we, kEdgeBuf - 32);
     }
     flush_edges(cfg, we, 1);
-    flush_counters(cfg, C);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cfg.stats[kStatT2Chunks], total);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kT2Threads, 4) k_type2(DevCfg cfg) {
+    if (cfg.lists_ok && *cfg.lists_ok == 0u) return;  // a list overflowed: the round is redone
+    __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
+    __shared__ unsigned int s_en[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_en[warp] = 0;
+    __syncwarp();
+    WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
+    Counters C;
+    type2_loop<DIM>(cfg, sorted_view(cfg), we, C);
+    flush_counters(cfg, C);
 }
 
 // ------------------------------------------------------------------ all pairs

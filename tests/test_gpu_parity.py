@@ -436,3 +436,4 @@ def test_benchmark_workload_full_size_edge_for_edge():
     assert st["type1_pairs"] == ref.stats["type1_pairs"]
     assert st["type2_candidates"] == ref.stats["type2_candidates"]
     assert st["jump_draws"] == ref.stats["jump_draws"]
+

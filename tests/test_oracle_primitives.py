@@ -227,9 +227,19 @@ def test_morton_worked_example():
 
 
 def test_level_cap_and_chunk_log():
-    assert O.level_cap(10000, 1) == 18
-    assert O.level_cap(1_000_000, 2) == 12
-    assert O.level_cap(2 ** 24, 4) == 7
+    # T = 0: (bitlen(n) + 4) / d, at most 32 / d
+    assert O.level_cap(10000, 1, 0.0) == 18
+    assert O.level_cap(1_000_000, 2, 0.0) == 12
+    assert O.level_cap(2 ** 24, 4, 0.0) == 7
+    assert O.level_cap(2 ** 30, 1, 0.0) == 32
+    # T > 0: floor(log2(n)/d - 1/2) with log2 n = bitlen(n) - 1, about 2^(d/2) vertices
+    # per cell of the deepest level
+    assert O.level_cap(2 ** 24, 1, 0.7) == 23
+    assert O.level_cap(2 ** 24, 2, 0.7) == 11
+    assert O.level_cap(2 ** 24, 3, 0.7) == 7
+    assert O.level_cap(2 ** 24, 4, 0.7) == 5
+    assert O.level_cap(1_000_000, 2, 0.5) == 9
+    assert O.level_cap(10, 4, 0.5) == 1
     for p in (0.75, 0.5, 1e-3, 3e-9):
         k = O.chunk_log(p)
         assert 4 <= p * 2 ** k < 8

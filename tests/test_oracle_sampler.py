@@ -160,12 +160,16 @@ def test_girg_edge_frequencies_match_p(d, T, c):
     for u in range(n):
         for v in range(u + 1, n):
             pmat[u, v] = O.girg_p(d, T, c, W, w[u], w[v], _torus_D(X, u, v))
-    res = O.girg_cellpairs(X, w, 1.0, W, T, c, 1, want_items=True, skip_sampling=True)
+    # levels down to (bitlen(n) + 4) / d, so that most pairs go through geometric jumps
+    lcap = 8 // d
+    res = O.girg_cellpairs(X, w, 1.0, W, T, c, 1, want_items=True, skip_sampling=True,
+                           level_cap=lcap)
     cnt, typ = _coverage(res, n)
     assert (typ == 2).sum() >= 25  # most pairs go through geometric jumps
 
     def run(s):
-        return O.girg_cellpairs(X, w, 1.0, W, T, c, s, cap=256).edges.astype(np.int64)
+        return O.girg_cellpairs(X, w, 1.0, W, T, c, s, cap=256,
+                                level_cap=lcap).edges.astype(np.int64)
 
     _frequency_test(run, pmat, 20000, n)
 
