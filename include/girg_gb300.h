@@ -209,6 +209,24 @@ int girg_expected_avg_degree(const girg_params* params, double* avg_deg, void* s
  * (it is then reported as 0 or infinity). */
 double girg_last_scale(void);
 
+/* Resident point sets, for serving the same point set more than once.  With
+ * max_bytes > 0, girg_generate keeps the layout of each graph it builds on the device:
+ * the weight buckets and levels, the Morton-sorted vertex arrays with their cell
+ * offsets (Sec. 3.1, 3.4, Lemma 1) and the bound tables of the distant cell pairs
+ * (Sec. 3.2), keyed by n, d, beta, w_min, seed, T, c (or avg_deg when c <= 0) and
+ * level_cap.  A later call with the same values skips the weights and positions, the
+ * reductions, the search for c and the sort, and makes the same graph.  Least recently
+ * used layouts are dropped beyond max_bytes (a layout larger than max_bytes is not
+ * kept); an entry still in use by a call is freed when that call returns.  The memory
+ * comes from the library's scratch pool and is not part of girg_scratch_bytes.
+ * max_bytes = 0 (the default) turns the cache off and frees it.  Errors: GIRG_E_PARAM
+ * (max_bytes < 0). */
+int girg_point_cache(int64_t max_bytes);
+
+/* Layouts kept, their bytes, and the cache hits and misses of girg_generate calls since
+ * the cache was turned on.  Out pointers may be NULL. */
+int girg_point_cache_stats(int64_t* entries, int64_t* bytes, int64_t* hits, int64_t* misses);
+
 /* The library's scratch pool on the current device: bytes reserved from the driver,
  * bytes in use now, and the most bytes in use at once since the pool was created or
  * last reset (reset_high != 0 resets that mark after reading it).  Out pointers may be

@@ -78,6 +78,8 @@ SIGNATURES = {
     "girg_scratch_bytes": (I64, [P]),
     "girg_scratch_pool_usage": (I32, [P, P, P, I32]),
     "girg_scratch_pool_trim": (I32, [I64]),
+    "girg_point_cache": (I32, [I64]),
+    "girg_point_cache_stats": (I32, [P, P, P, P]),
     "girg_server_create": (I32, [I32, I64, P]),
     "girg_server_submit": (I32, [P, P, P, I64, I64]),
     "girg_server_poll": (I32, [P, P, I32, I32]),
@@ -184,6 +186,22 @@ def scratch_pool_trim(keep_bytes: int = 0) -> None:
     st = load().girg_scratch_pool_trim(keep_bytes)
     if st != GIRG_OK:
         raise GirgError(st, "girg_scratch_pool_trim")
+
+
+def point_cache(max_bytes: int) -> None:
+    """Keep the layouts (sorted points, cell offsets, bound tables) of generated graphs
+    on the device, up to max_bytes (0: off), so that repeated requests for the same
+    point set skip points, reductions, the scale search and the sort."""
+    st = load().girg_point_cache(max_bytes)
+    if st != GIRG_OK:
+        raise GirgError(st, "girg_point_cache")
+
+
+def point_cache_stats() -> dict:
+    e, b, h, m = (ctypes.c_int64(0) for _ in range(4))
+    load().girg_point_cache_stats(ctypes.byref(e), ctypes.byref(b), ctypes.byref(h),
+                                  ctypes.byref(m))
+    return {"entries": e.value, "bytes": b.value, "hits": h.value, "misses": m.value}
 
 
 def scratch_bytes(*, n, d, beta, T, avg_deg=0.0, c=0.0, w_min=1.0, seed=1, edge_bytes=4,

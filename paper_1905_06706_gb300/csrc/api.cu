@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -76,20 +77,28 @@ cudaMemPool_t library_pool() {
     return g_pools[dev];
 }
 
-// Scratch allocations from the library's pool, freed on scope exit (stream-ordered).
+// Scratch allocations from the library's pool, freed on scope exit (stream-ordered),
+// unless release() hands them to a longer-lived owner (the resident point-set cache).
 struct Scratch {
     cudaStream_t st;
     cudaMemPool_t pool;
     std::vector<void*> ptrs;
+    size_t bytes = 0;
     explicit Scratch(cudaStream_t s) : st(s), pool(library_pool()) {}
     template <class T>
     T* get(size_t count) {
         void* p = nullptr;
-        size_t bytes = count * sizeof(T);
-        if (bytes < 256) bytes = 256;
-        CK(cudaMallocFromPoolAsync(&p, bytes, pool, st));
+        size_t b = count * sizeof(T);
+        if (b < 256) b = 256;
+        CK(cudaMallocFromPoolAsync(&p, b, pool, st));
         ptrs.push_back(p);
+        bytes += b;
         return static_cast<T*>(p);
+    }
+    std::vector<void*> release() {
+        std::vector<void*> out;
+        out.swap(ptrs);
+        return out;
     }
     ~Scratch() {
         for (void* p : ptrs) cudaFreeAsync(p, st);
@@ -171,8 +180,29 @@ struct Problem {
     Reduce red{};
 };
 
-// Everything after the reductions: tables, sort, sampling.  If order_out is set,
-// stops after the sort and writes the sorted original ids there.
+// What the sampling rounds read, built from the points and the scale K: the layer
+// partition and levels (host), and the sorted vertex arrays, cell offsets and bound
+// tables (device).  Built by build_layout for every call, or kept by the resident
+// point-set cache.
+struct Layout {
+    int L = 0, lcap = 0, m_int = 0, n3 = 1, n6 = 1, filt_k = 0;
+    bool tzero = false;
+    double invT = 0.0, coshR = 0.0;
+    int64_t cnt[kMaxLayers] = {0};
+    int I[kMaxLayers] = {0}, CLd[kMaxLayers] = {0};
+    uint32_t layer_base[kMaxLayers + 1] = {0}, lstart[kMaxLayers + 1] = {0};
+    std::vector<RowClass> classes;
+    uint32_t *offs = nullptr, *skey = nullptr, *sid = nullptr, *Xs = nullptr;
+    double* ws = nullptr;
+    uint8_t* slayer = nullptr;
+    float *sv = nullptr, *E32 = nullptr, *einv32 = nullptr, *sh32 = nullptr;
+    uint4* vrec = nullptr;
+    TwoEntry* tii = nullptr;
+    RowClass* d_classes = nullptr;
+    uint8_t* jlist = nullptr;
+    float *flo = nullptr, *fhi = nullptr;
+};
+
 // The edge buffer is device memory or page-locked host memory mapped into the
 // device's address space (the kernels then write the edges across the host link, so
 // no copy follows).  Pageable host memory is refused.
@@ -188,9 +218,11 @@ void* device_view(void* p) {
     throw Status{GIRG_E_PARAM};
 }
 
-void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edges, int64_t cap,
-                 int64_t* num_edges, int64_t* order_out) {
-    d_edges = device_view(d_edges);
+// Tables and sort (Sec. 3.1, 3.4, Lemma 1): fills Lo.  Buffers that Lo keeps come from
+// A, temporaries from S (A may be S).  If order_out is set, stops after the sort and
+// writes the sorted original ids there.
+void build_layout(Problem& P, Scratch& A, Scratch& S, cudaStream_t st, Timer& tm, Layout& Lo,
+                  int64_t* order_out) {
     const int64_t n = P.n;
     const int d = P.d;
     const bool girg = P.model == 0;
@@ -281,11 +313,12 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     double host_ms = host_ms_since(host_t0);
     tm.mark();  // layer partition done
     // ---------------------------------------------------------------- sort
-    uint32_t* key = S.get<uint32_t>(n);
-    uint32_t* val = S.get<uint32_t>(n);
-    uint32_t* key2 = S.get<uint32_t>(n);
-    uint32_t* val2 = S.get<uint32_t>(n);
-    uint32_t* offs = S.get<uint32_t>(total_cells + 1);
+    // the sorted keys and ids end up in two of these four (kept), the other two are free
+    uint32_t* key = A.get<uint32_t>(n);
+    uint32_t* val = A.get<uint32_t>(n);
+    uint32_t* key2 = A.get<uint32_t>(n);
+    uint32_t* val2 = A.get<uint32_t>(n);
+    uint32_t* offs = A.get<uint32_t>(total_cells + 1);
     uint32_t* stmp = S.get<uint32_t>(std::max({scan_tmp_words((int64_t)total_cells + 1),
                                                radix_tmp_words(n), place_tmp_words(n)}));
     CK(cudaMemsetAsync(offs, 0, (total_cells + 1) * sizeof(uint32_t), st));
@@ -323,21 +356,28 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
         CK(cudaStreamSynchronize(st));
         return;
     }
-    uint32_t* Xs = S.get<uint32_t>((size_t)d * n);
-    double* ws = S.get<double>(n);
-    uint8_t* slayer = S.get<uint8_t>(n);
+    // GIRG with d <= 4: packed vertex records (one or two 16-byte loads per vertex in the
+    // pair tests); otherwise separate coordinate and scale arrays
+    const bool packed = girg && d <= 4;
+    uint32_t* Xs = packed ? nullptr : A.get<uint32_t>((size_t)d * n);
+    double* ws = A.get<double>(n);
+    uint8_t* slayer = A.get<uint8_t>(n);
     float *sv = nullptr, *E32 = nullptr, *einv32 = nullptr, *sh32 = nullptr;
+    uint4* vrec = nullptr;
     float gamma = 0.0f;
     const double log2W_half = girg ? 0.5 * std::log2(P.W) : 0.0;
     if (girg) {
-        sv = S.get<float>(n);
+        if (packed)
+            vrec = A.get<uint4>((size_t)n * (d <= 2 ? 1 : 2));
+        else
+            sv = A.get<float>(n);
         gamma = (float)(std::log2(P.K) / (2.0 * d));  // kappa_uv = s_u s_v, kappa^d = K q
         launch_gather_girg(n, d, sid, P.X, P.w, P.w_min, log2W_half, gamma, (float)(1.0 / d), Xs,
-                           ws, sv, slayer, st);
+                           ws, sv, slayer, vrec, st);
     } else {
-        E32 = S.get<float>(n);
-        einv32 = S.get<float>(n);
-        sh32 = S.get<float>(n);
+        E32 = A.get<float>(n);
+        einv32 = A.get<float>(n);
+        sh32 = A.get<float>(n);
         launch_gather_hrg(n, sid, P.X, P.r, P.w, Xs, ws, E32, einv32, sh32, slayer, st);
     }
     tm.mark();  // sort done
@@ -432,17 +472,77 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     host_ms += host_ms_since(host_t1);
     g_ms[9] = (float)host_ms;
     // ---------------------------------------------------------------- device tables
-    TwoEntry* d_tii = S.get<TwoEntry>(tii.size());
-    RowClass* d_classes = S.get<RowClass>(classes.size());
-    uint8_t* d_jlist = S.get<uint8_t>(jlist.size());
-    float* d_flo = S.get<float>(K);
-    float* d_fhi = S.get<float>(K);
+    TwoEntry* d_tii = A.get<TwoEntry>(tii.size());
+    RowClass* d_classes = A.get<RowClass>(classes.size());
+    uint8_t* d_jlist = A.get<uint8_t>(jlist.size());
+    float* d_flo = A.get<float>(K);
+    float* d_fhi = A.get<float>(K);
     CK(cudaMemcpyAsync(d_tii, tii.data(), tii.size() * sizeof(TwoEntry), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_classes, classes.data(), classes.size() * sizeof(RowClass),
                        cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_jlist, jlist.data(), jlist.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_flo, flo.data(), K * 4, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_fhi, fhi.data(), K * 4, cudaMemcpyHostToDevice, st));
+    // the host copies above read pageable vectors: they complete before the calls
+    // return, so the vectors may go out of scope
+    Lo.L = L;
+    Lo.lcap = lcap;
+    Lo.m_int = m_int;
+    Lo.n3 = n3;
+    Lo.n6 = n6;
+    Lo.filt_k = K;
+    Lo.tzero = tzero;
+    Lo.invT = invT;
+    Lo.coshR = coshR;
+    for (int i = 0; i < kMaxLayers; ++i) {
+        Lo.cnt[i] = cnt[i];
+        Lo.I[i] = I[i];
+        Lo.CLd[i] = CLd[i];
+    }
+    memcpy(Lo.layer_base, layer_base, sizeof(layer_base));
+    memcpy(Lo.lstart, lstart, sizeof(lstart));
+    Lo.classes = std::move(classes);
+    Lo.offs = offs;
+    Lo.skey = skey;
+    Lo.sid = sid;
+    Lo.Xs = Xs;
+    Lo.ws = ws;
+    Lo.slayer = slayer;
+    Lo.sv = sv;
+    Lo.E32 = E32;
+    Lo.einv32 = einv32;
+    Lo.sh32 = sh32;
+    Lo.vrec = vrec;
+    Lo.tii = d_tii;
+    Lo.d_classes = d_classes;
+    Lo.jlist = d_jlist;
+    Lo.flo = d_flo;
+    Lo.fhi = d_fhi;
+}
+
+// Cell-pair enumeration and sampling (Algorithm 1, Sec. 3.2, 3.3) over a layout: rows,
+// work lists in rounds, type I and type II, edge count and statistics.
+void run_sampler(Problem& P, const Layout& Lo, Scratch& S, cudaStream_t st, Timer& tm,
+                 void* d_edges, int64_t cap, int64_t* num_edges) {
+    d_edges = device_view(d_edges);
+    const int64_t n = P.n;
+    const int d = P.d;
+    const bool girg = P.model == 0;
+    const int L = Lo.L, lcap = Lo.lcap, m_int = Lo.m_int, n3 = Lo.n3, n6 = Lo.n6, K = Lo.filt_k;
+    const bool tzero = Lo.tzero;
+    const double invT = Lo.invT, coshR = Lo.coshR;
+    const int64_t* cnt = Lo.cnt;
+    const int *I = Lo.I, *CLd = Lo.CLd;
+    const std::vector<RowClass>& classes = Lo.classes;
+    uint32_t *offs = Lo.offs, *skey = Lo.skey, *sid = Lo.sid, *Xs = Lo.Xs;
+    double* ws = Lo.ws;
+    uint8_t* slayer = Lo.slayer;
+    float *sv = Lo.sv, *E32 = Lo.E32, *einv32 = Lo.einv32, *sh32 = Lo.sh32;
+    uint4* vrec = Lo.vrec;
+    TwoEntry* d_tii = Lo.tii;
+    RowClass* d_classes = Lo.d_classes;
+    uint8_t* d_jlist = Lo.jlist;
+    float *d_flo = Lo.flo, *d_fhi = Lo.fhi;
     // work entries: at most min(|V_i|, 2^(d l)) rows per (i, l), one entry per bucket
     uint64_t ent2_cap = 0, ent1_cap = 0;
     for (int i = 0; i < L; ++i)
@@ -526,8 +626,8 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
         cfg.I[i] = (int8_t)I[i];
         cfg.CLd[i] = (uint8_t)CLd[i];
     }
-    memcpy(cfg.layer_base, layer_base, sizeof(layer_base));
-    memcpy(cfg.lstart, lstart, sizeof(lstart));
+    memcpy(cfg.layer_base, Lo.layer_base, sizeof(Lo.layer_base));
+    memcpy(cfg.lstart, Lo.lstart, sizeof(Lo.lstart));
     cfg.tii = d_tii;
     cfg.classes = d_classes;
     cfg.jlist = d_jlist;
@@ -541,6 +641,7 @@ void run_sampler(Problem& P, Scratch& S, cudaStream_t st, Timer& tm, void* d_edg
     cfg.E32 = E32;
     cfg.einv32 = einv32;
     cfg.sh32 = sh32;
+    cfg.vrec = vrec;
     cfg.filt_lo = d_flo;
     cfg.filt_hi = d_fhi;
     cfg.edges = d_edges;
@@ -842,7 +943,9 @@ SplitDev split_buffers(int64_t n, Scratch& S) {
     D.thr = S.get<double>(1);
     D.sums = S.get<double>(4);
     D.part = S.get<double>((size_t)4 * reduce_blocks(n));
-    D.cap = 4 * kTopSortMax;  // more than the device sorts: the host sorts those
+    // more than the one-block sort takes: a radix sort orders those; sized so that the
+    // split rarely has to run a second time with a larger buffer
+    D.cap = (unsigned int)std::max<int64_t>(4 * kTopSortMax, n / 32);
     D.buf = S.get<double>(D.cap);
     return D;
 }
@@ -858,9 +961,9 @@ void queue_split(const Problem& P, SplitDev& D, SplitHost* h, cudaStream_t st) {
     CK(cudaMemcpyAsync(h->w, D.buf, sizeof(h->w), cudaMemcpyDeviceToHost, st));
 }
 
-// Hand a finished split to the degree model; when more weights than the device sorts
-// were gathered, copy and sort them here (the buffer is enlarged and the split rerun
-// when they did not fit).
+// Hand a finished split to the degree model; when more weights were gathered than the
+// one-block sort takes, a device radix sort orders them before the copy (the buffer is
+// enlarged and the split rerun when they did not fit).
 void take_split(const Problem& P, DegreeModel& M, SplitDev& D, SplitHost* h, Scratch& S,
                 cudaStream_t st) {
     unsigned int k = h->count[0];
@@ -877,9 +980,12 @@ void take_split(const Problem& P, DegreeModel& M, SplitDev& D, SplitHost* h, Scr
         k = h->count[0];
     }
     std::vector<double> top(k);
-    if (k) CK(cudaMemcpyAsync(top.data(), D.buf, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (k) {
+        double* sorted = S.get<double>(k);
+        sort_f64_desc(D.buf, k, sorted, S.get<uint32_t>(sort_desc_words(k)), st);
+        CK(cudaMemcpyAsync(top.data(), sorted, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
     CK(cudaStreamSynchronize(st));
-    std::sort(top.begin(), top.end(), [](double a, double b) { return a > b; });
     M.set_split(h->thr, std::move(top), h->sums[0], h->sums[1], h->sums[2], h->sums[3]);
 }
 
@@ -905,6 +1011,91 @@ double c_of_K(double K, int d, double T) {
 }
 
 thread_local double g_last_K = 0.0;
+
+// ------------------------------------------------------------------ resident point sets
+// With the cache on (girg_point_cache), girg_generate keeps the layout of each graph it
+// builds -- sorted vertex arrays, cell offsets, bound tables, levels -- on the device,
+// keyed by every input the layout depends on: the points (n, d, beta, w_min, seed), the
+// scale (T with c, or with the target degree) and the level cap.  A call with the same
+// values samples from the kept layout and makes the same graph.  Entries are evicted
+// least recently used first beyond the byte limit; an entry in use by a call is freed
+// when that call releases it (every call has synchronised its stream by then).
+struct CacheKey {
+    int64_t n;
+    int d, level_cap, dev;
+    double beta, w_min, T, c, avg_deg;
+    uint64_t seed;
+    bool operator==(const CacheKey& o) const {
+        return n == o.n && d == o.d && level_cap == o.level_cap && dev == o.dev &&
+               beta == o.beta && w_min == o.w_min && T == o.T && c == o.c &&
+               avg_deg == o.avg_deg && seed == o.seed;
+    }
+};
+
+struct CacheEntry {
+    CacheKey key;
+    Layout Lo;
+    double K = 0.0, W = 0.0, w_min = 0.0, c_used = 0.0;
+    std::vector<void*> bufs;
+    size_t bytes = 0;
+    uint64_t last_use = 0;
+    ~CacheEntry() {  // on the entry's device; the calling thread's device is restored
+        int prev = 0;
+        const bool switch_dev = cudaGetDevice(&prev) == cudaSuccess && prev != key.dev;
+        if (switch_dev) cudaSetDevice(key.dev);
+        for (void* p : bufs) cudaFree(p);
+        if (switch_dev) cudaSetDevice(prev);
+    }
+};
+
+struct PointCache {
+    std::mutex mu;
+    int64_t max_bytes = 0;  // 0: off
+    int64_t bytes = 0, hits = 0, misses = 0;
+    uint64_t clock = 0;
+    std::vector<std::shared_ptr<CacheEntry>> entries;
+
+    std::shared_ptr<CacheEntry> find(const CacheKey& k) {
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto& e : entries)
+            if (e->key == k) {
+                e->last_use = ++clock;
+                ++hits;
+                return e;
+            }
+        ++misses;
+        return nullptr;
+    }
+    // Keep e unless an equal entry arrived meanwhile or it alone exceeds the limit;
+    // evict least recently used entries beyond the limit.
+    void insert(std::shared_ptr<CacheEntry> e) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (max_bytes <= 0 || (int64_t)e->bytes > max_bytes) return;
+        for (auto& x : entries)
+            if (x->key == e->key) return;
+        e->last_use = ++clock;
+        bytes += (int64_t)e->bytes;
+        entries.push_back(std::move(e));
+        while (bytes > max_bytes && !entries.empty()) {
+            size_t oldest = 0;
+            for (size_t i = 1; i < entries.size(); ++i)
+                if (entries[i]->last_use < entries[oldest]->last_use) oldest = i;
+            bytes -= (int64_t)entries[oldest]->bytes;
+            entries.erase(entries.begin() + (long)oldest);
+        }
+    }
+};
+
+PointCache& point_cache() {
+    static PointCache* c = new PointCache();  // never destroyed: no CUDA calls at exit
+    return *c;
+}
+
+bool cache_on() {
+    PointCache& c = point_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    return c.max_bytes > 0;
+}
 
 }  // namespace
 
@@ -974,6 +1165,40 @@ int girg_scratch_pool_usage(int64_t* reserved, int64_t* used, int64_t* used_high
     });
 }
 
+int girg_point_cache(int64_t max_bytes) {
+    if (max_bytes < 0) return GIRG_E_PARAM;
+    std::vector<std::shared_ptr<CacheEntry>> drop;
+    {
+        PointCache& c = point_cache();
+        std::lock_guard<std::mutex> lk(c.mu);
+        c.max_bytes = max_bytes;
+        if (max_bytes == 0) {
+            drop.swap(c.entries);
+            c.bytes = 0;
+            c.hits = c.misses = 0;
+        }
+        while (c.bytes > c.max_bytes && !c.entries.empty()) {  // a lower limit
+            size_t oldest = 0;
+            for (size_t i = 1; i < c.entries.size(); ++i)
+                if (c.entries[i]->last_use < c.entries[oldest]->last_use) oldest = i;
+            c.bytes -= (int64_t)c.entries[oldest]->bytes;
+            drop.push_back(c.entries[oldest]);
+            c.entries.erase(c.entries.begin() + (long)oldest);
+        }
+    }
+    return GIRG_OK;  // the dropped entries are freed here, outside the lock
+}
+
+int girg_point_cache_stats(int64_t* entries, int64_t* bytes, int64_t* hits, int64_t* misses) {
+    PointCache& c = point_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    if (entries) *entries = (int64_t)c.entries.size();
+    if (bytes) *bytes = c.bytes;
+    if (hits) *hits = c.hits;
+    if (misses) *misses = c.misses;
+    return GIRG_OK;
+}
+
 int girg_scratch_pool_trim(int64_t keep_bytes) {
     if (keep_bytes < 0) return GIRG_E_PARAM;
     return guarded([&] {
@@ -1039,6 +1264,7 @@ int girg_generate(const girg_params* params, void* d_edges, int64_t capacity_edg
     if (!num_edges || capacity_edges < 0) return GIRG_E_PARAM;
     return guarded([&] {
         cudaStream_t st = (cudaStream_t)stream;
+        d_edges = device_view(d_edges);
         Scratch S(st);
         Timer tm(st);
         g_launches = 0;
@@ -1053,6 +1279,28 @@ int girg_generate(const girg_params* params, void* d_edges, int64_t capacity_edg
         P.precision = params->precision;
         P.edge_bytes = params->edge_bytes;
         P.level_cap = params->level_cap;
+        const bool caching = cache_on();
+        CacheKey key{};
+        if (caching) {
+            int dev = 0;
+            CK(cudaGetDevice(&dev));
+            key = CacheKey{P.n, P.d, P.level_cap, dev, params->beta, P.w_min, P.T,
+                           params->c > 0.0 ? params->c : 0.0,
+                           params->c > 0.0 ? 0.0 : params->avg_deg, P.seed};
+            if (std::shared_ptr<CacheEntry> e = point_cache().find(key)) {
+                // a kept layout: no points, reductions, scale search or sort
+                tm.mark();
+                tm.mark();
+                tm.mark();
+                P.K = e->K;
+                P.W = e->W;
+                g_last_K = P.K;
+                if (c_used) *c_used = e->c_used;
+                run_sampler(P, e->Lo, S, st, tm, d_edges, capacity_edges, num_edges);
+                finish_timing(tm);
+                return P.edge_bytes != 0 && *num_edges > capacity_edges ? GIRG_E_CAPACITY : GIRG_OK;
+            }
+        }
         double* w = S.get<double>(P.n);
         uint32_t* X = S.get<uint32_t>((size_t)P.d * P.n);
         launch_girg_points(P.n, P.d, params->beta, P.w_min, P.seed, w, X, st);
@@ -1083,8 +1331,26 @@ int girg_generate(const girg_params* params, void* d_edges, int64_t capacity_edg
         P.K = solve ? solve_K(P, params->avg_deg, D, h, S, st) : girg_K_of_c(params->c, P.d, P.T);
         g_ms[8] = (float)host_ms_since(h0);
         g_last_K = P.K;
-        if (c_used) *c_used = solve ? c_of_K(P.K, P.d, P.T) : params->c;
-        run_sampler(P, S, st, tm, d_edges, capacity_edges, num_edges, nullptr);
+        const double cu = solve ? c_of_K(P.K, P.d, P.T) : params->c;
+        if (c_used) *c_used = cu;
+        if (caching) {  // build the layout into buffers the cache keeps
+            auto e = std::make_shared<CacheEntry>();
+            e->key = key;
+            e->K = P.K;
+            e->W = P.W;
+            e->c_used = cu;
+            Scratch A(st);  // frees what it holds if the build throws
+            build_layout(P, A, S, st, tm, e->Lo, nullptr);
+            e->bytes = A.bytes;
+            e->bufs = A.release();
+            run_sampler(P, e->Lo, S, st, tm, d_edges, capacity_edges, num_edges);  // syncs st
+            finish_timing(tm);
+            point_cache().insert(e);
+            return P.edge_bytes != 0 && *num_edges > capacity_edges ? GIRG_E_CAPACITY : GIRG_OK;
+        }
+        Layout Lo;
+        build_layout(P, S, S, st, tm, Lo, nullptr);
+        run_sampler(P, Lo, S, st, tm, d_edges, capacity_edges, num_edges);
         finish_timing(tm);
         return P.edge_bytes != 0 && *num_edges > capacity_edges ? GIRG_E_CAPACITY : GIRG_OK;
     });
@@ -1175,8 +1441,10 @@ static int from_points_impl(int64_t n, int32_t d, const uint32_t* d_X, const dou
         if (P.red.range_error) return GIRG_E_RANGE;
         P.W = round128(P.red.sum_hi, P.red.sum_lo, E0);
         int64_t dummy = 0;
-        run_sampler(P, S, st, tm, d_edges, capacity_edges, num_edges ? num_edges : &dummy, order_out);
+        Layout Lo;
+        build_layout(P, S, S, st, tm, Lo, order_out);
         if (order_out) return GIRG_OK;
+        run_sampler(P, Lo, S, st, tm, d_edges, capacity_edges, num_edges ? num_edges : &dummy);
         finish_timing(tm);
         return edge_bytes != 0 && *num_edges > capacity_edges ? GIRG_E_CAPACITY : GIRG_OK;
     });
@@ -1260,7 +1528,9 @@ int hrg_generate(const hrg_params* params, void* d_edges, int64_t capacity_edges
         tm.mark();
         read_reduce(P, red, st);  // the HRG needs no weight sum: a range error is harmless
         P.W = 1.0;
-        run_sampler(P, S, st, tm, d_edges, capacity_edges, num_edges, nullptr);
+        Layout Lo;
+        build_layout(P, S, S, st, tm, Lo, nullptr);
+        run_sampler(P, Lo, S, st, tm, d_edges, capacity_edges, num_edges);
         finish_timing(tm);
         return P.edge_bytes != 0 && *num_edges > capacity_edges ? GIRG_E_CAPACITY : GIRG_OK;
     });

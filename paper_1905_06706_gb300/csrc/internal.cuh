@@ -94,6 +94,10 @@ struct DevCfg {
     const float* E32;     // HRG e^r, e^-r, sinh r (sorted)
     const float* einv32;
     const float* sh32;
+    // packed sorted GIRG records for d <= 4 (null otherwise; then Xs and sv): d <= 2 one
+    // uint4 {x0, x1, scale bits, id} per vertex, d = 3, 4 two {x0, x1, x2, x3},
+    // {scale bits, id, 0, 0}
+    const uint4* vrec;
     const float* filt_lo;  // HRG distance filter (cosh thresholds), rounded down
     const float* filt_hi;  // rounded up
     void* edges;

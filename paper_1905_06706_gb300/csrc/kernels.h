@@ -84,6 +84,10 @@ size_t radix_tmp_words(int64_t n);
 void radix_sort_pairs(uint32_t* key, uint32_t* val, uint32_t* key_alt, uint32_t* val_alt,
                       int64_t n, int bits, uint32_t* tmp, cudaStream_t st, uint32_t** key_out,
                       uint32_t** val_out);
+// n positive doubles in decreasing order (out must not alias in); words >=
+// sort_desc_words(n) uint32 of scratch.
+size_t sort_desc_words(int64_t n);
+void sort_f64_desc(const double* in, int64_t n, double* out, uint32_t* words, cudaStream_t st);
 // The same order by placement: key and slot from launch_keys (slots) and the scanned
 // cell histogram offs; writes the sorted keys to skey and the sorted ids to sid (tid:
 // scratch of n words).  tmp >= place_tmp_words(n) words with tmp[0] zeroed.
@@ -92,10 +96,11 @@ void place_by_counts(const uint32_t* key, const uint32_t* slot, const uint32_t* 
                      uint32_t* skey, uint32_t* tid, uint32_t* sid, uint32_t* tmp,
                      cudaStream_t st);
 // Sorted per-vertex arrays.
+// With rec (d <= 4): packed records instead of Xs and sv (see DevCfg::vrec).
 void launch_gather_girg(int64_t n, int d, const uint32_t* perm, const uint32_t* X,
                         const double* w, double w_min, double log2W_half, float gamma,
                         float invd, uint32_t* Xs, double* ws, float* sv, uint8_t* slayer,
-                        cudaStream_t st);
+                        uint4* rec, cudaStream_t st);
 void launch_gather_hrg(int64_t n, const uint32_t* perm, const uint32_t* X, const double* r,
                        const double* w, uint32_t* Xs, double* rs, float* E32, float* einv32,
                        float* sh32, uint8_t* slayer, cudaStream_t st);

@@ -37,13 +37,64 @@ struct View {  // per-vertex arrays indexed by position
     const float* einv32;
     const float* sh32;
     int64_t n;
+    const uint4* rec;     // packed GIRG records (d <= 4), or nullptr: the arrays above
 };
 
 __device__ __forceinline__ View sorted_view(const DevCfg& cfg) {
-    return View{cfg.Xs, cfg.sv, cfg.ws, cfg.ids, cfg.E32, cfg.einv32, cfg.sh32, cfg.n};
+    return View{cfg.Xs, cfg.sv, cfg.ws, cfg.ids, cfg.E32, cfg.einv32, cfg.sh32, cfg.n, cfg.vrec};
 }
 
 __device__ __forceinline__ uint32_t vid(const View& V, uint32_t p) { return V.ids ? V.ids[p] : p; }
+
+// What a GIRG decision reads of one vertex: its coordinates, its single-precision scale
+// and its original id.  From a packed record (one 16-byte load for d <= 2, two for
+// d = 3, 4) when the view has them, else from the separate arrays.
+template <int DIM>
+struct VRec {
+    uint32_t x[DIM];
+    float s;
+    uint32_t id;
+};
+
+template <int DIM>
+__device__ __forceinline__ VRec<DIM> load_rec(const View& V, uint32_t p) {
+    static_assert(DIM >= 1 && DIM <= 4, "packed records hold up to four coordinates");
+    VRec<DIM> r;
+    if (V.rec) {
+        if constexpr (DIM <= 2) {
+            const uint4 a = __ldg(V.rec + p);
+            r.x[0] = a.x;
+            if constexpr (DIM == 2) r.x[1] = a.y;
+            r.s = __uint_as_float(a.z);
+            r.id = a.w;
+        } else {
+            const uint4 a = __ldg(V.rec + 2 * (size_t)p), b = __ldg(V.rec + 2 * (size_t)p + 1);
+            r.x[0] = a.x;
+            r.x[1] = a.y;
+            r.x[2] = a.z;
+            if constexpr (DIM == 4) r.x[3] = a.w;
+            r.s = __uint_as_float(b.x);
+            r.id = b.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) r.x[k] = V.X[(int64_t)k * V.n + p];
+        r.s = V.sv[p];
+        r.id = vid(V, p);
+    }
+    return r;
+}
+
+template <int DIM>
+__device__ __forceinline__ uint32_t rec_D(const VRec<DIM>& a, const VRec<DIM>& b) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const uint32_t t = circ_diff(a.x[k], b.x[k]);
+        m = t > m ? t : m;
+    }
+    return m;
+}
 
 template <int DIM>
 __device__ __forceinline__ uint32_t torus_D(int d, const View& V, uint32_t pu, uint32_t pv) {
@@ -108,11 +159,52 @@ __device__ __forceinline__ float hrg_p32(const DevCfg& cfg, float cd) {
     return 1.0f / (expf((acoshf(cd) - cfg.R32) * cfg.inv2T32) + 1.0f);
 }
 
-// Type I: edge iff U(seed, u, v) < p_uv (T > 0) or the threshold rule (T = 0).
+// Type I: edge iff U(seed, u, v) < p_uv (T > 0) or the threshold rule (T = 0).  The
+// pair's original ids go to *ida, *idb (ida < idb).
 template <int DIM>
-__device__ bool decide_t1(const DevCfg& cfg, const View& V, uint32_t pu, uint32_t pv, Counters& C) {
+__device__ bool decide_t1(const DevCfg& cfg, const View& V, uint32_t pu, uint32_t pv, Counters& C,
+                          uint32_t* ida, uint32_t* idb) {
+    if constexpr (DIM >= 1 && DIM <= 4) {
+        if (cfg.model == 0) {  // GIRG from the two vertex records
+            const VRec<DIM> ru = load_rec<DIM>(V, pu), rv = load_rec<DIM>(V, pv);
+            const uint32_t a = ru.id < rv.id ? ru.id : rv.id, b = ru.id < rv.id ? rv.id : ru.id;
+            *ida = a;
+            *idb = b;
+            const uint32_t D = rec_D<DIM>(ru, rv);
+            if (D == 0) return true;
+            if (cfg.precision == 1) {
+                uint32_t lo = 0, hi = 0;
+                if (!cfg.tzero) {
+                    ++C.coins;
+                    const P4 o = philox(a, b, kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
+                    lo = o.x;
+                    hi = o.y;
+                }
+                return girg_t1_exact(cfg, V, pu, pv, D, lo, hi);
+            }
+            const float ratio = ru.s * rv.s * __fdividef(4294967296.0f, __uint2float_rn(D));
+            if (cfg.tzero) {
+                if (ratio > 1.0f + cfg.band_ratio) return true;
+                if (ratio < 1.0f - cfg.band_ratio) return false;
+                ++C.recheck;
+                return girg_t1_exact(cfg, V, pu, pv, D, 0u, 0u);
+            }
+            if (ratio >= 1.0f + cfg.band_ratio) return true;  // p = 1
+            const float lp = cfg.dT * __log2f(ratio);        // log2 p
+            if (lp < -54.0f - cfg.bandG) return false;        // p < 2^-54 < every U
+            ++C.coins;
+            const P4 o = philox(a, b, kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
+            const float G = lp - log2_uniform32(o.x, o.y);
+            if (G > cfg.bandG) return true;
+            if (G < -cfg.bandG) return false;
+            ++C.recheck;
+            return girg_t1_exact(cfg, V, pu, pv, D, o.x, o.y);
+        }
+    }
     const uint32_t iu = vid(V, pu), iv = vid(V, pv);
     const uint32_t a = iu < iv ? iu : iv, b = iu < iv ? iv : iu;
+    *ida = a;
+    *idb = b;
     if ((DIM == 1 || DIM == 0) && cfg.model == 1) {
         // HRG (Sec. 2.2): threshold d < R, binomial U < p_T(d)
         const uint32_t D = circ_diff(V.X[pu], V.X[pv]);
@@ -236,7 +328,29 @@ __device__ __forceinline__ int draw_jump_fast(const DevCfg& cfg, const TwoFast& 
 template <int DIM>
 __device__ __forceinline__ bool accept_t2_fast(const DevCfg& cfg, const View& V, uint32_t pu,
                                                uint32_t pv, uint32_t lo, uint32_t hi,
-                                               const TwoFast& e, Counters& C) {
+                                               const TwoFast& e, Counters& C, uint32_t* idu,
+                                               uint32_t* idv) {
+    if constexpr (DIM >= 1 && DIM <= 4) {
+        if (cfg.model == 0) {  // GIRG from the two vertex records
+            const VRec<DIM> ru = load_rec<DIM>(V, pu), rv = load_rec<DIM>(V, pv);
+            *idu = ru.id;
+            *idv = rv.id;
+            const uint32_t D = rec_D<DIM>(ru, rv);
+            if (cfg.precision == 1) return t2_exact(cfg, V, pu, pv, D, lo, hi, cfg.tii[e.tii].pbar);
+            if (D == 0) return true;
+            const float ratio = ru.s * rv.s * __fdividef(4294967296.0f, __uint2float_rn(D));
+            if (ratio >= 1.0f + cfg.band_ratio) return true;
+            if (ratio >= 0x1p-126f) {
+                const float G = cfg.dT * __log2f(ratio) - log2_uniform32(lo, hi) - e.log2pbar;
+                if (G > cfg.bandG) return true;
+                if (G < -cfg.bandG) return false;
+            }  // else subnormal: no relative error bound in single precision
+            ++C.recheck;
+            return t2_exact(cfg, V, pu, pv, D, lo, hi, cfg.tii[e.tii].pbar);
+        }
+    }
+    *idu = vid(V, pu);
+    *idv = vid(V, pv);
     if ((DIM == 1 || DIM == 0) && cfg.model == 1) return accept_t2<DIM>(cfg, V, pu, pv, lo, hi, cfg.tii[e.tii], C);
     const uint32_t D = torus_D<DIM>(cfg.d, V, pu, pv);
     if (cfg.precision == 1) return t2_exact(cfg, V, pu, pv, D, lo, hi, cfg.tii[e.tii].pbar);
@@ -963,7 +1077,7 @@ __device__ __forceinline__ void type1_loop(const DevCfg& cfg, const View& V, War
             const uint32_t b_len = __shfl_sync(0xffffffffu, wit.b_len, j);
             const int pj = __shfl_sync(0xffffffffu, wpre, j);
             bool edge = false;
-            uint32_t pu = 0, pv = 0;
+            uint32_t pu = 0, pv = 0, ia_id = 0, ib_id = 0;
             if (f < fe) {
                 const uint32_t bl = b_len & 0x7fffffffu;
                 const uint32_t rr = (uint32_t)(f - pj);
@@ -981,11 +1095,11 @@ __device__ __forceinline__ void type1_loop(const DevCfg& cfg, const View& V, War
                 pv = b_begin + (uint32_t)ib;
                 if (!((b_len & 0x80000000u) && pv <= pu)) {
                     ++C.t1pairs;
-                    edge = decide_t1<DIM>(cfg, V, pu, pv, C);
+                    edge = decide_t1<DIM>(cfg, V, pu, pv, C, &ia_id, &ib_id);
                 }
             }
             if (edge) {
-                push_edge(cfg, we, V.ids[pu], V.ids[pv]);
+                push_edge(cfg, we, ia_id, ib_id);
                 ++t1_edges;
             }
             flush_edges<true>(cfg, we, kEdgeBuf - 32);
@@ -1002,7 +1116,7 @@ __device__ __forceinline__ void type1_loop(const DevCfg& cfg, const View& V, War
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kT1Threads) k_type1(DevCfg cfg) {
+__global__ void __launch_bounds__(kT1Threads, 4) k_type1(DevCfg cfg) {
     if (cfg.lists_ok && *cfg.lists_ok == 0u) return;  // a list overflowed: the round is redone
     __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
     __shared__ unsigned int s_en[kWarps];
@@ -1105,7 +1219,7 @@ __device__ __forceinline__ void type2_loop(const DevCfg& cfg, const View& V, War
             continue;
         }
         bool edge = false;
-        uint32_t pu = 0, pv = 0;
+        uint32_t pu = 0, pv = 0, idu = 0, idv = 0;
         if (live) {
             const P4 o = philox(st.A, st.pack, h, t, cfg.seed_lo, cfg.seed_hi);
             bool cand = true;
@@ -1169,10 +1283,10 @@ __device__ __forceinline__ void type2_loop(const DevCfg& cfg, const View& V, War
                 }
                 pu = st.a_begin + ia;
                 pv = sg.b_begin + (ib - sg.pre);
-                edge = accept_t2_fast<DIM>(cfg, V, pu, pv, o.z, o.w, e, C);
+                edge = accept_t2_fast<DIM>(cfg, V, pu, pv, o.z, o.w, e, C, &idu, &idv);
             }
         }
-        if (edge) push_edge(cfg, we, vid(V, pu), vid(V, pv));
+        if (edge) push_edge(cfg, we, idu, idv);
         flush_edges(cfg, we, kEdgeBuf - 32);
     }
     flush_edges(cfg, we, 1);
@@ -1218,8 +1332,9 @@ __global__ void __launch_bounds__(256) k_allpairs(DevCfg cfg, View V, unsigned i
         for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) {
             const uint32_t u = tu * 64 + (q >> 6), v = tv * 64 + (q & 63);
             bool edge = false;
-            if (u < v && v < (uint32_t)V.n) edge = decide_t1<DIM>(cfg, V, u, v, C);
-            if (edge) push_edge(cfg, we, u, v);
+            uint32_t a = 0, b = 0;
+            if (u < v && v < (uint32_t)V.n) edge = decide_t1<DIM>(cfg, V, u, v, C, &a, &b);
+            if (edge) push_edge(cfg, we, a, b);
             flush_edges(cfg, we, kEdgeBuf - 32);
         }
     }
@@ -1321,7 +1436,7 @@ void launch_type2(const DevCfg& cfg, cudaStream_t st) {
 
 void launch_allpairs(const DevCfg& cfg, const uint32_t* X, const double* w, const float* sv,
                      cudaStream_t st) {
-    View V{X, sv, w, nullptr, nullptr, nullptr, nullptr, cfg.n};
+    View V{X, sv, w, nullptr, nullptr, nullptr, nullptr, cfg.n, nullptr};
     const unsigned int ntile = (unsigned int)((cfg.n + 63) / 64);
     unsigned long long ntri = (unsigned long long)ntile * (ntile + 1) / 2;
     const unsigned int gmax = (unsigned int)device_sms() * 8;

@@ -305,6 +305,60 @@ static int grid_for(int64_t n, int threads, int max_blocks) {
     return (int)b;
 }
 
+// ------------------------------------------------------------------ doubles, decreasing
+// Positive doubles order like their bit patterns, so the complemented patterns in
+// increasing order are the values in decreasing order: two stable radix sorts, by the
+// low word and then by the high word, order the 64-bit patterns.
+__global__ void k_f64_words(const double* __restrict__ x, int64_t n, uint32_t* __restrict__ lo,
+                            uint32_t* __restrict__ hi, uint32_t* __restrict__ idx) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long b = ~(unsigned long long)__double_as_longlong(x[i]);
+        lo[i] = (uint32_t)b;
+        hi[i] = (uint32_t)(b >> 32);
+        idx[i] = (uint32_t)i;
+    }
+}
+
+__global__ void k_gather_words(const uint32_t* __restrict__ src, const uint32_t* __restrict__ perm,
+                               int64_t n, uint32_t* __restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[perm[i]];
+}
+
+__global__ void k_gather_doubles(const double* __restrict__ src, const uint32_t* __restrict__ perm,
+                                 int64_t n, double* __restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[perm[i]];
+}
+
+size_t sort_desc_words(int64_t n) { return (size_t)5 * (size_t)n + radix_tmp_words(n) + 64; }
+
+void sort_f64_desc(const double* in, int64_t n, double* out, uint32_t* words, cudaStream_t st) {
+    if (n <= 0) return;
+    uint32_t* lo = words;
+    uint32_t* hi = lo + n;
+    uint32_t* idx = hi + n;
+    uint32_t* ka = idx + n;
+    uint32_t* va = ka + n;
+    uint32_t* tmp = va + n;
+    const int grid = grid_for(n, 256, device_sms() * 16);
+    ++g_launches;
+    k_f64_words<<<grid, 256, 0, st>>>(in, n, lo, hi, idx);
+    uint32_t *k1, *p1;
+    radix_sort_pairs(lo, idx, ka, va, n, 32, tmp, st, &k1, &p1);  // by the low word
+    uint32_t* kfree = k1 == lo ? ka : lo;
+    uint32_t* vfree = p1 == idx ? va : idx;
+    ++g_launches;
+    k_gather_words<<<grid, 256, 0, st>>>(hi, p1, n, kfree);  // high words in that order
+    uint32_t *k2, *p2;
+    radix_sort_pairs(kfree, p1, k1, vfree, n, 32, tmp, st, &k2, &p2);  // then by the high word
+    ++g_launches;
+    k_gather_doubles<<<grid, 256, 0, st>>>(in, p2, n, out);
+}
+
 // ------------------------------------------------------------------ placement by counts
 // The same order without the radix passes.  With the cell histogram scanned (offs[c] =
 // first sorted position of cell c, offs[C] = n), a vertex goes to offs[key] plus its
@@ -408,19 +462,36 @@ void place_by_counts(const uint32_t* key, const uint32_t* slot, const uint32_t* 
 // Per-vertex scale s with kappa_uv = s_u s_v (kappa: distance at which p = 1, or the
 // threshold distance at T = 0): log2 s = (log2 w - log2(W)/2) / d + gamma.  Only the
 // single-precision fast path uses it; its error is covered by the decision band.
+// The sorted GIRG vertex arrays: weights and buckets, and either packed records (rec,
+// d <= 4: coordinates, scale and id of a vertex in 16 or 32 bytes, so that a pair test
+// reads each vertex with one or two vector loads) or the separate coordinate and scale
+// arrays (Xs, sv).
 __global__ void k_gather_girg(int64_t n, int d, const uint32_t* __restrict__ perm,
                               const uint32_t* __restrict__ X, const double* __restrict__ w,
                               double w_min, double log2W_half, float gamma, float invd,
                               uint32_t* __restrict__ Xs, double* __restrict__ ws,
-                              float* __restrict__ sv, uint8_t* __restrict__ slayer) {
+                              float* __restrict__ sv, uint8_t* __restrict__ slayer,
+                              uint4* __restrict__ rec) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t v = perm[p];
-        for (int k = 0; k < d; ++k) Xs[(int64_t)k * n + p] = X[(int64_t)k * n + v];
         const double wv = w[v];
         ws[p] = wv;
-        sv[p] = exp2f((log2f((float)wv) - (float)log2W_half) * invd + gamma);
+        const float s = exp2f((log2f((float)wv) - (float)log2W_half) * invd + gamma);
         slayer[p] = (uint8_t)layer_of(wv, w_min);
+        if (rec) {
+            uint32_t x[4] = {0u, 0u, 0u, 0u};
+            for (int k = 0; k < d && k < 4; ++k) x[k] = X[(int64_t)k * n + v];
+            if (d <= 2) {
+                rec[p] = make_uint4(x[0], x[1], __float_as_uint(s), v);
+            } else {
+                rec[2 * p] = make_uint4(x[0], x[1], x[2], x[3]);
+                rec[2 * p + 1] = make_uint4(__float_as_uint(s), v, 0u, 0u);
+            }
+        } else {
+            for (int k = 0; k < d; ++k) Xs[(int64_t)k * n + p] = X[(int64_t)k * n + v];
+            sv[p] = s;
+        }
     }
 }
 
@@ -464,10 +535,10 @@ void launch_keys(int64_t n, int d, const double* w, const uint32_t* X, double w_
 void launch_gather_girg(int64_t n, int d, const uint32_t* perm, const uint32_t* X,
                         const double* w, double w_min, double log2W_half, float gamma,
                         float invd, uint32_t* Xs, double* ws, float* sv, uint8_t* slayer,
-                        cudaStream_t st) {
+                        uint4* rec, cudaStream_t st) {
     ++g_launches;
-    k_gather_girg<<<grid_for(n, 256, device_sms() * 16), 256, 0, st>>>(n, d, perm, X, w, w_min, log2W_half,
-                                                              gamma, invd, Xs, ws, sv, slayer);
+    k_gather_girg<<<grid_for(n, 256, device_sms() * 16), 256, 0, st>>>(
+        n, d, perm, X, w, w_min, log2W_half, gamma, invd, Xs, ws, sv, slayer, rec);
 }
 
 void launch_scale(int64_t n, const double* w, double log2W_half, float gamma, float invd,

@@ -98,3 +98,17 @@ def test_large_hrg_reduced_size_edge_for_edge():
     ref = O.hrg_cellpairs(X, rr, r.R_used, T, 2, cap=n * 16)
     assert r.num_edges == len(ref.edges)
     assert gg.last_stats()["edge_checksum"] == O.edge_checksum(ref.edges)
+
+
+@pytest.mark.parametrize("d,T", [(1, 0.0), (2, 0.7)])
+def test_scale_search_with_many_top_weights(d, T):
+    """At n = 2^21, beta = 2.2 the degree model's top set (weights that can meet an E_R
+    partner) holds tens of thousands of weights, more than the one-block sort takes:
+    the device radix sort orders them, and the scale K equals the oracle's search."""
+    n = 1 << 21
+    w, X = O.girg_points(n, d, BETA, 1.0, 5)
+    W = O.exact_sum(w)
+    K = O.girg_solve_K(DEG, w, d, T, W)
+    r = gg.girg_generate(None, n=n, d=d, beta=BETA, T=T, avg_deg=DEG, seed=5)
+    assert r.status == gg.GIRG_OK
+    assert gg.last_K() == pytest.approx(K, rel=1e-9)

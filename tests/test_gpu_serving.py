@@ -142,3 +142,52 @@ def test_admission_estimate_bounds_the_scratch_taken():
             res += srv.poll(64, wait_for=1)
     assert all(r.status == gg.GIRG_OK for r in res)
     assert gg.scratch_pool_usage()["used_high"] <= budget
+
+
+def test_resident_point_sets_give_the_same_graph():
+    """With the point cache on, a repeated request samples from the kept layout (no
+    points, reductions, scale search or sort on the device) and makes the same graph;
+    requests that differ in any input of the layout miss; a small limit evicts."""
+    q = dict(n=150_000, d=2, beta=2.5, T=0.5, avg_deg=10.0, seed=77)
+    ed0 = torch.empty((_cap(q), 2), dtype=torch.int32, device="cuda")
+    r0 = gg.girg_generate(ed0, **q)
+    cs0 = gg.last_stats()["edge_checksum"]
+    gg.point_cache(4 << 30)
+    try:
+        for rep in range(3):
+            ed = torch.empty((_cap(q), 2), dtype=torch.int32, device="cuda")
+            r = gg.girg_generate(ed, **q)
+            assert r.status == gg.GIRG_OK and r.num_edges == r0.num_edges
+            assert gg.last_stats()["edge_checksum"] == cs0
+            ph = gg.last_phase_ms()
+            if rep > 0:  # a hit: the points and the sort did not run
+                assert ph["points_reduce"] < 0.01 and ph["sort"] < 0.01
+        st = gg.point_cache_stats()
+        assert st["entries"] == 1 and st["hits"] == 2 and st["misses"] == 1
+        a = ed0[: r0.num_edges].cpu().numpy()
+        b = ed[: r.num_edges].cpu().numpy()
+        assert np.array_equal(np.sort(a[:, 0].astype(np.int64) << 32 | a[:, 1]),
+                              np.sort(b[:, 0].astype(np.int64) << 32 | b[:, 1]))
+        # a different seed or temperature misses and is a different entry
+        gg.girg_generate(None, **dict(q, seed=78))
+        gg.girg_generate(None, **dict(q, T=0.6))
+        assert gg.point_cache_stats()["entries"] == 3
+        # a limit below one layout keeps nothing more and evicts down to the limit
+        gg.point_cache(st["bytes"] // 2)
+        assert gg.point_cache_stats()["bytes"] <= st["bytes"] // 2
+        r = gg.girg_generate(None, **q)
+        assert r.num_edges == r0.num_edges and gg.last_stats()["edge_checksum"] == cs0
+        # and the server's requests use the cache
+        gg.point_cache(4 << 30)
+        with gg.Server(workers=4, memory_budget_bytes=8 << 30) as srv:
+            for i in range(6):
+                srv.submit(i, None, **q)
+            res = []
+            while len(res) < 6:
+                res += srv.poll(16, wait_for=1)
+        assert all(x.status == gg.GIRG_OK and x.num_edges == r0.num_edges and
+                   x.checksum == cs0 for x in res)
+        assert gg.point_cache_stats()["hits"] >= 5
+    finally:
+        gg.point_cache(0)
+    assert gg.point_cache_stats()["entries"] == 0
