@@ -592,9 +592,9 @@ __device__ __forceinline__ uint32_t kids_with_bit(int d, int k) {
 
 // Visit the distant partner cells B of A (children of the neighbours of A's
 // parent, not neighbours of A) that count for bucket j and hold a vertex of it:
-// f(B, g, lo, len) with the gap g = L_inf distance - 1 in {1, 2} and the range of
-// sorted positions (len > 0), in rank order, rank = (sum_k (e_k + 1) 3^(d-1-k)) 2^d
-// + sum_k kid_k 2^(d-1-k).  The 2^d children of a parent neighbour are consecutive
+// f(B, g, lo, len, rank) with the gap g = L_inf distance - 1 in {1, 2}, the range of
+// sorted positions (len > 0) and the rank, in rank order, rank = (sum_k (e_k + 1)
+// 3^(d-1-k)) 2^d + sum_k kid_k 2^(d-1-k).  The 2^d children of a parent neighbour are consecutive
 // cells with 2^d + 1 consecutive offsets.  The parent neighbours go in groups of
 // three that differ in the last digit only: the first and end offsets of a group are
 // loaded together, then (d <= 3) the inner offsets of its non-empty members, so a
@@ -694,7 +694,7 @@ __device__ __forceinline__ void for_partners(const DevCfg& cfg, const EntryCtx& 
                     else
                         hi = kid + 1 < nk ? offs_at(first[t] + kid + 1) : end[t];
                     const uint32_t g = ((far >> kid) & 1u) + ((far3 >> kid) & 1u);
-                    if (g && hi > lo) f(first[t] | kid, g, lo, hi - lo);
+                    if (g && hi > lo) f(first[t] | kid, g, lo, hi - lo, ((gi * 3u + (uint32_t)t) << d) | kid);
                     lo = hi;
                 }
             } else {
@@ -711,7 +711,7 @@ __device__ __forceinline__ void for_partners(const DevCfg& cfg, const EntryCtx& 
                         const uint32_t dk = (dist[k] >> (3u * pos)) & 7u;
                         linf = dk > linf ? dk : linf;
                     }
-                    if (linf > 1 && hi > lo) f(first[t] | kid, linf - 1, lo, hi - lo);
+                    if (linf > 1 && hi > lo) f(first[t] | kid, linf - 1, lo, hi - lo, ((gi * 3u + (uint32_t)t) << d) | kid);
                     lo = hi;
                 }
             }
@@ -741,6 +741,9 @@ __global__ void __launch_bounds__(kEnumThreads, 4) k_enum2(DevCfg cfg) {
         // per gap: partner cells, segments, total size, end of the last segment
         uint32_t cnt[2] = {0u, 0u}, nseg[2] = {0u, 0u}, sum[2] = {0u, 0u}, keep[2] = {0u, 0u};
         uint32_t s0[2], tidx[2], pack[2] = {0u, 0u};
+        // d = 2: the ranks (< 36) of the partner cells visited, per gap, so that the
+        // second visit below goes straight to them
+        unsigned long long vis0 = 0ull, vis1 = 0ull;
         if (active) {
             x = decode_entry<DIM>(cfg, cfg.ent2[q], d, false);
             uint32_t nxt[2] = {0xffffffffu, 0xffffffffu};
@@ -750,12 +753,16 @@ __global__ void __launch_bounds__(kEnumThreads, 4) k_enum2(DevCfg cfg) {
                 sum[gi] += len;
                 nxt[gi] = lo + len;
             };
-            for_partners<DIM>(cfg, x, d, [&](uint32_t, uint32_t g, uint32_t lo, uint32_t len) {
-                if (g == 1)
-                    add(0, lo, len);
-                else
-                    add(1, lo, len);
-            });
+            for_partners<DIM>(cfg, x, d,
+                              [&](uint32_t, uint32_t g, uint32_t lo, uint32_t len, uint32_t rank) {
+                                  if (g == 1) {
+                                      add(0, lo, len);
+                                      if (DIM == 2) vis0 |= 1ull << rank;
+                                  } else {
+                                      add(1, lo, len);
+                                      if (DIM == 2) vis1 |= 1ull << rank;
+                                  }
+                              });
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
                 s0[g] = 0xffffffffu;
@@ -842,12 +849,41 @@ __global__ void __launch_bounds__(kEnumThreads, 4) k_enum2(DevCfg cfg) {
                 pre[gi] += len;
                 nxt[gi] = lo + len;
             };
-            for_partners<DIM>(cfg, x, d, [&](uint32_t, uint32_t g, uint32_t lo, uint32_t len) {
-                if (g == 1)
-                    put(0, lo, len);
-                else
-                    put(1, lo, len);
-            });
+            if constexpr (DIM == 2) {
+                // the visited cells again, in rank order: the parent neighbour of digits
+                // (e0, e1) = (p / 3 - 1, p % 3 - 1), child kid, offsets from cache
+                const uint32_t PA = x.A >> 2;
+                const int lev = x.l - 1;
+                const uint32_t m0 = dim_mask(2, 0, lev), m1 = dim_mask(2, 1, lev);
+                const uint32_t a0 = dil_add(PA, m0, 2u, -1), b0 = PA & m0, c0 = dil_add(PA, m0, 2u, 1);
+                const uint32_t a1 = dil_add(PA, m1, 1u, -1), b1 = PA & m1, c1 = dil_add(PA, m1, 1u, 1);
+#pragma unroll
+                for (int gi = 0; gi < 2; ++gi) {
+                    if (!keep[gi]) continue;
+                    unsigned long long m = gi == 0 ? vis0 : vis1;
+                    while (m) {
+                        const uint32_t rank = (uint32_t)__ffsll((long long)m) - 1u;
+                        m &= m - 1ull;
+                        const uint32_t pidx = rank >> 2, kid = rank & 3u;
+                        const uint32_t e0 = pidx / 3u, e1 = pidx - 3u * e0;
+                        const uint32_t P0 = e0 == 0u ? a0 : (e0 == 1u ? b0 : c0);
+                        const uint32_t P1 = e1 == 0u ? a1 : (e1 == 1u ? b1 : c1);
+                        const uint32_t cell = ((P0 | P1) << 2) | kid;
+                        const uint32_t lo = cfg.offs[x.baseB + (uint32_t)((uint64_t)cell << x.sB)];
+                        const uint32_t hi =
+                            cfg.offs[x.baseB + (uint32_t)(((uint64_t)cell + 1) << x.sB)];
+                        put(gi, lo, hi - lo);
+                    }
+                }
+            } else {
+                for_partners<DIM>(cfg, x, d, [&](uint32_t, uint32_t g, uint32_t lo, uint32_t len,
+                                                 uint32_t) {
+                    if (g == 1)
+                        put(0, lo, len);
+                    else
+                        put(1, lo, len);
+                });
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) t2_items_local += __shfl_down_sync(0xffffffffu, t2_items_local, o);
