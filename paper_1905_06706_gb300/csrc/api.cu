@@ -79,22 +79,44 @@ cudaMemPool_t library_pool() {
 
 // Scratch allocations from the library's pool, freed on scope exit (stream-ordered),
 // unless release() hands them to a longer-lived owner (the resident point-set cache).
+// With a reservation, one pool allocation of that size is carved up in order (256-byte
+// aligned) and only what does not fit is allocated on its own: a call then makes one or
+// two pool calls instead of dozens, on its critical path at the start and at the end.
 struct Scratch {
     cudaStream_t st;
     cudaMemPool_t pool;
     std::vector<void*> ptrs;
     size_t bytes = 0;
-    explicit Scratch(cudaStream_t s) : st(s), pool(library_pool()) {}
+    char* arena = nullptr;
+    size_t arena_cap = 0, arena_used = 0;
+    explicit Scratch(cudaStream_t s, size_t reserve = 0) : st(s), pool(library_pool()) {
+        if (reserve > 0) {
+            void* p = nullptr;
+            if (cudaMallocFromPoolAsync(&p, reserve, pool, st) == cudaSuccess) {
+                arena = static_cast<char*>(p);
+                arena_cap = reserve;
+            } else {
+                cudaGetLastError();  // no reservation: every request allocates on its own
+            }
+        }
+    }
     template <class T>
     T* get(size_t count) {
-        void* p = nullptr;
         size_t b = count * sizeof(T);
         if (b < 256) b = 256;
+        b = (b + 255) & ~(size_t)255;
+        bytes += b;
+        if (arena && arena_used + b <= arena_cap) {
+            T* p = reinterpret_cast<T*>(arena + arena_used);
+            arena_used += b;
+            return p;
+        }
+        void* p = nullptr;
         CK(cudaMallocFromPoolAsync(&p, b, pool, st));
         ptrs.push_back(p);
-        bytes += b;
         return static_cast<T*>(p);
     }
+    // the allocations so far, for an owner that outlives this object (no reservation)
     std::vector<void*> release() {
         std::vector<void*> out;
         out.swap(ptrs);
@@ -102,21 +124,30 @@ struct Scratch {
     }
     ~Scratch() {
         for (void* p : ptrs) cudaFreeAsync(p, st);
+        if (arena) cudaFreeAsync(arena, st);
     }
 };
 
+// Phase marks of one call: CUDA events created once per host thread and device.
 struct Timer {
-    cudaEvent_t ev[8];
+    cudaEvent_t* ev;
     int used = 0;
     cudaStream_t st;
     explicit Timer(cudaStream_t s) : st(s) {
-        for (auto& e : ev) cudaEventCreate(&e);
+        thread_local cudaEvent_t events[8];
+        thread_local int events_dev = -1;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (events_dev != dev) {  // first use on this thread, or another device
+            if (events_dev >= 0)
+                for (auto& e : events) cudaEventDestroy(e);
+            for (auto& e : events) cudaEventCreate(&e);
+            events_dev = dev;
+        }
+        ev = events;
     }
     void mark() {
         if (used < 8) cudaEventRecord(ev[used++], st);
-    }
-    ~Timer() {
-        for (auto& e : ev) cudaEventDestroy(e);
     }
 };
 
@@ -556,14 +587,17 @@ void run_sampler(Problem& P, const Layout& Lo, Scratch& S, cudaStream_t st, Time
     if (ent2_cap >= 0xffffffffull || ent1_cap >= 0xffffffffull) throw Status{GIRG_E_INTERNAL};
     uint64_t* ent2 = S.get<uint64_t>(ent2_cap + 1);
     uint64_t* ent1 = S.get<uint64_t>(ent1_cap + 1);
-    unsigned int* counters = S.get<unsigned int>(16);
-    // stats, then the edge count and the two work counters of the type-I / type-II kernels
-    unsigned long long* stats = S.get<unsigned long long>(kNumStats + 3);
-    // one round's work-list counts (type-I items, streams, segments) and statistics
-    unsigned long long* wcount = S.get<unsigned long long>(3);
-    unsigned long long* estats = S.get<unsigned long long>(kNumStats);
-    CK(cudaMemsetAsync(counters, 0, 16 * sizeof(unsigned int), st));
-    CK(cudaMemsetAsync(stats, 0, (kNumStats + 3) * sizeof(unsigned long long), st));
+    // the small counters in one block, cleared with one memset: stats (then the edge
+    // count and the two work counters of the type-I / type-II kernels), one round's
+    // work-list counts (type-I items, streams, segments) and statistics, and the 32-bit
+    // row / entry / error counters
+    unsigned long long* small = S.get<unsigned long long>(kNumStats + 3 + 3 + kNumStats + 8);
+    unsigned long long* stats = small;
+    unsigned long long* wcount = stats + kNumStats + 3;
+    unsigned long long* estats = wcount + 3;
+    unsigned int* counters = reinterpret_cast<unsigned int*>(estats + kNumStats);
+    CK(cudaMemsetAsync(small, 0, (kNumStats + 3 + 3 + kNumStats + 8) * sizeof(unsigned long long),
+                       st));
     // work lists, sized from typical counts per vertex; the enumeration only writes
     // work (no edges), so an overflow is repaired by resizing and running it again
     // GIRG_INITIAL_LIST_SCALE in (0, 1] shrinks the initial sizes (tests use it to
@@ -695,9 +729,7 @@ void run_sampler(Problem& P, const Layout& Lo, Scratch& S, cudaStream_t st, Time
         cfg.ent2_lo = 0;
         cfg.ent2_hi = 0xffffffffu;
         cfg.ent1_lo = 0;
-        cfg.ent1_hi = 0xffffffffu;
-        CK(cudaMemsetAsync(wcount, 0, 3 * sizeof(unsigned long long), st));
-        CK(cudaMemsetAsync(estats, 0, kNumStats * sizeof(unsigned long long), st));
+        cfg.ent1_hi = 0xffffffffu;  // wcount and estats are clear from the block memset
         DevCfg ecfg = cfg;
         ecfg.stats = estats;
         launch_enumerate(ecfg, st);
@@ -933,7 +965,7 @@ SplitHost* pinned_split() {
 // Device buffers of the weight split.
 struct SplitDev {
     unsigned int* cnt;
-    double *thr, *sums, *part, *buf;
+    double *thr, *sums, *part, *buf, *sorted;
     unsigned int cap;
 };
 
@@ -947,6 +979,7 @@ SplitDev split_buffers(int64_t n, Scratch& S) {
     // split rarely has to run a second time with a larger buffer
     D.cap = (unsigned int)std::max<int64_t>(4 * kTopSortMax, n / 32);
     D.buf = S.get<double>(D.cap);
+    D.sorted = S.get<double>(kTopSortMax);
     return D;
 }
 
@@ -954,11 +987,11 @@ SplitDev split_buffers(int64_t n, Scratch& S) {
 // (read after the next synchronisation).
 void queue_split(const Problem& P, SplitDev& D, SplitHost* h, cudaStream_t st) {
     CK(cudaMemsetAsync(D.cnt, 0, 3 * sizeof(unsigned int), st));
-    launch_split_weights(P.n, P.w, D.thr, P.T, D.buf, D.cap, D.cnt, D.part, D.sums, st);
+    launch_split_weights(P.n, P.w, D.thr, P.T, D.buf, D.cap, D.cnt, D.part, D.sums, D.sorted, st);
     CK(cudaMemcpyAsync(h->count, D.cnt, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&h->thr, D.thr, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h->sums, D.sums, sizeof(h->sums), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(h->w, D.buf, sizeof(h->w), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h->w, D.sorted, sizeof(h->w), cudaMemcpyDeviceToHost, st));
 }
 
 // Hand a finished split to the degree model; when more weights were gathered than the
@@ -1011,6 +1044,13 @@ double c_of_K(double K, int d, double T) {
 }
 
 thread_local double g_last_K = 0.0;
+
+// The reservation of a generate call's scratch: the server's admission estimate, an
+// upper bound of what the call takes at its initial work-list sizes.
+size_t scratch_reserve(const girg_params& p) {
+    const int64_t b = girg_scratch_bytes(&p);
+    return b > 0 ? (size_t)b : 0;
+}
 
 // ------------------------------------------------------------------ resident point sets
 // With the cache on (girg_point_cache), girg_generate keeps the layout of each graph it
@@ -1265,7 +1305,7 @@ int girg_generate(const girg_params* params, void* d_edges, int64_t capacity_edg
     return guarded([&] {
         cudaStream_t st = (cudaStream_t)stream;
         d_edges = device_view(d_edges);
-        Scratch S(st);
+        Scratch S(st, scratch_reserve(*params));
         Timer tm(st);
         g_launches = 0;
         tm.mark();
@@ -1409,7 +1449,11 @@ static int from_points_impl(int64_t n, int32_t d, const uint32_t* d_X, const dou
     if (!order_out && (!num_edges || capacity_edges < 0)) return GIRG_E_PARAM;
     return guarded([&] {
         cudaStream_t st = (cudaStream_t)stream;
-        Scratch S(st);
+        girg_params est{};
+        est.n = n;
+        est.d = d;
+        est.T = T;
+        Scratch S(st, order_out ? 0 : scratch_reserve(est));
         Timer tm(st);
         g_launches = 0;
         tm.mark();
@@ -1500,7 +1544,11 @@ int hrg_generate(const hrg_params* params, void* d_edges, int64_t capacity_edges
     if (R_used) *R_used = q.R;
     return guarded([&] {
         cudaStream_t st = (cudaStream_t)stream;
-        Scratch S(st);
+        girg_params est{};
+        est.n = q.n;
+        est.d = 1;
+        est.T = q.T;
+        Scratch S(st, scratch_reserve(est));
         Timer tm(st);
         g_launches = 0;
         tm.mark();

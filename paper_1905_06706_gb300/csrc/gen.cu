@@ -288,87 +288,36 @@ __global__ void k_split_weights(int64_t n, const double* __restrict__ w,
     }
 }
 
-// Sort the gathered weights in decreasing order (one block, bitonic network on the
-// bit patterns, which order positive doubles); count[1] = 1 when sorted, 0 when there
-// were more than kTopSortMax.  Thread t holds elements t + 1024 r in registers: a
-// compare-exchange at stride >= 1024 stays in the thread, one below 32 is a warp
-// shuffle, and only strides 32 .. 512 go through shared memory.
-__device__ __forceinline__ unsigned long long bitonic_keep(unsigned long long a, unsigned long long b,
-                                                           unsigned int i, unsigned int size,
-                                                           unsigned int stride) {
-    const bool desc = (i & size) == 0, lower = (i & stride) == 0;
-    return (lower == desc) ? (a > b ? a : b) : (a < b ? a : b);
-}
+// The gathered weights in decreasing order, when there are at most kTopSortMax of them
+// (count[1] = 1; else count[1] = 0 and the host has them sorted): every thread places
+// one weight at its rank, the number of larger weights plus the number of equal ones
+// before it, reading all of them from shared memory.  k weights cost k^2 comparisons
+// spread over ceil(k / 256) blocks; they compare the bit patterns as integers (positive
+// doubles order like them), since the FP64 units are slow.
+constexpr unsigned int kRankThreads = 256;
 
-__global__ void __launch_bounds__(1024) k_sort_top(double* __restrict__ buf,
-                                                   unsigned int* __restrict__ count) {
-    constexpr int R = (int)(kTopSortMax / 1024);
-    static_assert(R == 4, "register layout below assumes 4 elements per thread");
-    __shared__ unsigned long long s_key[kTopSortMax];
+__global__ void __launch_bounds__(kRankThreads) k_rank_top(const double* __restrict__ buf,
+                                                          unsigned int* __restrict__ count,
+                                                          double* __restrict__ sorted) {
+    __shared__ unsigned long long s_w[kTopSortMax];
     const unsigned int k = count[0];
     if (k > kTopSortMax) {
-        if (threadIdx.x == 0) count[1] = 0u;
+        if (blockIdx.x == 0 && threadIdx.x == 0) count[1] = 0u;
         return;
     }
-    unsigned int m = 32;  // whole warps
-    while (m < k) m <<= 1;
-    const unsigned int tid = threadIdx.x;
-    unsigned long long v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const unsigned int i = (unsigned int)r * 1024u + tid;
-        v[r] = i < k ? (unsigned long long)__double_as_longlong(buf[i]) : 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) count[1] = 1u;
+    if (blockIdx.x * kRankThreads >= k) return;  // the whole block: no weight of its own
+    for (unsigned int i = threadIdx.x; i < k; i += kRankThreads)
+        s_w[i] = (unsigned long long)__double_as_longlong(buf[i]);
+    __syncthreads();
+    const unsigned int i = blockIdx.x * kRankThreads + threadIdx.x;
+    if (i < k) {
+        const unsigned long long x = s_w[i];
+        unsigned int r = 0;
+        for (unsigned int j = 0; j < i; ++j) r += s_w[j] >= x ? 1u : 0u;  // ties before i
+        for (unsigned int j = i + 1; j < k; ++j) r += s_w[j] > x ? 1u : 0u;
+        sorted[r] = __longlong_as_double((long long)x);
     }
-    for (unsigned int size = 2; size <= m; size <<= 1) {
-        for (unsigned int stride = size >> 1; stride > 0; stride >>= 1) {
-            if (stride >= 1024) {  // pairs of registers (m >= 2048 here)
-                const unsigned int h = stride >> 10;  // 1 or 2
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int rp = r ^ (int)h;
-                    if (rp < r) continue;
-                    const unsigned int i = (unsigned int)r * 1024u + tid;
-                    if (i >= m) continue;
-                    const unsigned long long a = v[r], b = h == 1 ? v[r ^ 1] : v[r ^ 2];
-                    const unsigned long long hi = a > b ? a : b, lo = a > b ? b : a;
-                    const bool desc = (i & size) == 0;
-                    v[r] = desc ? hi : lo;
-                    if (h == 1)
-                        v[r ^ 1] = desc ? lo : hi;
-                    else
-                        v[r ^ 2] = desc ? lo : hi;
-                }
-            } else if (stride >= 32) {
-                __syncthreads();  // the previous stage's reads are done
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const unsigned int i = (unsigned int)r * 1024u + tid;
-                    if (i < m) s_key[i] = v[r];
-                }
-                __syncthreads();
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const unsigned int i = (unsigned int)r * 1024u + tid;
-                    if (i < m) v[r] = bitonic_keep(v[r], s_key[i ^ stride], i, size, stride);
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const unsigned int i = (unsigned int)r * 1024u + tid;
-                    if (i < m) {  // whole warps
-                        const unsigned long long p = __shfl_xor_sync(0xffffffffu, v[r], (int)stride);
-                        v[r] = bitonic_keep(v[r], p, i, size, stride);
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const unsigned int i = (unsigned int)r * 1024u + tid;
-        if (i < k) buf[i] = __longlong_as_double((long long)v[r]);
-    }
-    if (threadIdx.x == 0) count[1] = 1u;
 }
 
 bool det_tables_gen() { return det_tables_ready(); }
@@ -431,14 +380,14 @@ void launch_reduce(int64_t n, const double* w, const double* r, double w_min, in
 
 void launch_split_weights(int64_t n, const double* w, const double* thr, double T, double* out,
                           unsigned int cap, unsigned int* count, double* part, double* sums,
-                          cudaStream_t st) {
+                          double* sorted, cudaStream_t st) {
     const double invT = T > 0.0 ? 1.0 / T : 0.0;
     int m_int = 0;
     if (invT > 0.0 && invT == floor(invT) && invT <= 64.0) m_int = (int)invT;
     const int nb = reduce_blocks(n);
     g_launches += 2;
     k_split_weights<<<nb, 256, 0, st>>>(n, w, thr, invT, m_int, out, cap, count, part, sums);
-    k_sort_top<<<1, 1024, 0, st>>>(out, count);
+    k_rank_top<<<kTopSortMax / kRankThreads, kRankThreads, 0, st>>>(out, count, sorted);
 }
 
 }  // namespace gg

@@ -55,14 +55,15 @@ void launch_reduce(int64_t n, const double* w, const double* r, double w_min, in
                    double* part_s2, Reduce* out, cudaStream_t st,
                    const ThresholdJob* job = nullptr);
 // The split of the weights for the degree model: one pass that gathers the weights
-// above *thr (count[0]; sorted in decreasing order when count[0] <= kTopSortMax,
-// count[1] = 1) and sums over the rest: sums[0..3] = sum w, sum w^2, sum (w/thr)^(1/T),
-// sum (w/thr)^(2/T) (finished in block order by the last block; count[2] counts the
-// blocks and starts at 0).  part: 4 reduce_blocks(n) doubles.
-constexpr unsigned int kTopSortMax = 4096;  // sorted in 32 KB of static shared memory
+// above *thr into out (count[0] of them; copied to `sorted` in decreasing order when
+// count[0] <= kTopSortMax, count[1] = 1) and sums over the rest: sums[0..3] = sum w,
+// sum w^2, sum (w/thr)^(1/T), sum (w/thr)^(2/T) (finished in block order by the last
+// block; count[2] counts the blocks and starts at 0).  part: 4 reduce_blocks(n)
+// doubles; sorted: kTopSortMax doubles.
+constexpr unsigned int kTopSortMax = 4096;  // ranked in 32 KB of static shared memory
 void launch_split_weights(int64_t n, const double* w, const double* thr, double T, double* out,
                           unsigned int cap, unsigned int* count, double* part, double* sums,
-                          cudaStream_t st);
+                          double* sorted, cudaStream_t st);
 
 // Sorting: keys (global cell index at the insertion level) with a histogram; val
 // receives each vertex's arrival slot in its cell (slots) or its id (for the radix sort).
