@@ -262,7 +262,7 @@ def run_batched(gg, torch, k: int, workers_grid=(4, 8, 16)) -> dict:
         gg.girg_generate(v, **q)
         plain_lat.append(time.perf_counter() - (t0 + a))
 
-    def serve(workers, idx, arrive):
+    def serve(workers, idx, arrive, rq=reqs):
         with gg.Server(workers=workers, memory_budget_bytes=96 << 30) as srv:
             t0 = srv.clock_us()
             for j, i in enumerate(idx):
@@ -270,7 +270,7 @@ def run_batched(gg, torch, k: int, workers_grid=(4, 8, 16)) -> dict:
                     wait = t0 + arrive[j] * 1e6 - srv.clock_us()
                     if wait > 0:
                         time.sleep(wait / 1e6)
-                srv.submit(i, views[i], **reqs[i])
+                srv.submit(i, views[i], **rq[i])
             res = []
             while len(res) < len(idx):
                 res += srv.poll(4096, wait_for=1)
@@ -297,6 +297,27 @@ def run_batched(gg, torch, k: int, workers_grid=(4, 8, 16)) -> dict:
         bad += sum(r.status != gg.GIRG_OK for r in res)
         runs.append({"edges_per_s": cap_edges / span2, "p50_ms": _pct(lat, 0.5),
                      "p99_ms": _pct(lat, 0.99)})
+    # level caps tuned per request class (d, T = 0 or not, n bucket) on one sample request
+    # each, then the mix again with the tuned caps (each graph drawn with its class's cap)
+    from paper_1905_06706_gb300 import autotune as at
+    table = {"level_cap": at.tune_level_caps(at.class_samples(reqs))}
+    treqs = [at.apply(table, q) for q in reqs]
+    _, res = serve(workers, list(range(k)), None, treqs)
+    tspan = (max(r.t_done_us for r in res) - min(r.t_submit_us for r in res)) / 1e6
+    tedges = sum(r.num_edges for r in res)
+    bad += sum(r.status != gg.GIRG_OK for r in res)
+    arr = poisson(0)
+    t0, res = serve(workers, list(range(k)), arr, treqs)
+    tlat = [(r.t_done_us - (t0 + arr[r.request_id] * 1e6)) / 1e3 for r in res]
+    bad += sum(r.status != gg.GIRG_OK for r in res)
+    tuned = {"capacity_edges_per_s": tedges / tspan, "poisson_p50_ms": _pct(tlat, 0.5),
+             "poisson_p99_ms": _pct(tlat, 0.99),
+             "level_caps": {c: {"tuned": e["level_cap"], "default": e["default"]}
+                            for c, e in table["level_cap"].items()},
+             "sample_gain": at.expected_gain(table),
+             "note": "level cap per request class chosen from the default and its two "
+                     "neighbours by timing one sample request of the class; same arrivals "
+                     "as the first Poisson run"}
     return {"workload": BATCH["workload"], "requests": k, "edges": edges,
             "recipe": "n log-uniform [1e3,1e6], d in {1,2,3}, beta U[2.1,3.0], T U[0,0.9], "
                       "avg deg log-uniform [4,32], seeds splitmix64(2^32 + r), int32 edges",
@@ -315,7 +336,8 @@ def run_batched(gg, torch, k: int, workers_grid=(4, 8, 16)) -> dict:
                                    "edges_per_s": statistics.median(r["edges_per_s"] for r in runs),
                                    "p50_ms": statistics.median(r["p50_ms"] for r in runs),
                                    "p99_ms": statistics.median(r["p99_ms"] for r in runs),
-                                   "note": "medians over the three runs"}}}
+                                   "note": "medians over the three runs"},
+                       "tuned_level_caps": tuned}}
 
 
 def _median_ms(fn, torch, flush, steps: int, warmup: int):
@@ -427,6 +449,48 @@ def run_configs(gg, torch, hbm: float, flush, steps: int = 3, warmup: int = 1) -
                         "note": "R solved on the host for degree 10 in every call"}
     del ed
     return out
+
+
+# Single workloads for profiling one configuration (bench.py --workload NAME): the
+# all-pairs configuration (quadratic kernel and cell sampler, FP32 decisions), the
+# dimension sweep's graphs and the large HRG, as in run_configs.
+SINGLE_WORKLOADS = {
+    "allpairs_d1_n1e4": dict(kind="allpairs"),
+    "cellpairs_d1_n1e4": dict(kind="cellpairs"),
+    **{f"sweep_d{d}_T{T}": dict(kind="sweep", d=d, T=T) for d in (1, 2, 3, 4) for T in (0.0, 0.7)},
+    "hrg_n1e7": dict(kind="hrg"),
+}
+
+
+def run_single(args) -> None:
+    import torch
+    import paper_1905_06706_gb300 as gg
+    gg.load()
+    spec = SINGLE_WORKLOADS[args.workload]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    if spec["kind"] in ("allpairs", "cellpairs"):
+        n, d, T = 10_000, 1, 0.5
+        w, X = gg.girg_points(n, d, 2.5, 1.0, 1)
+        W = math.fsum(w.cpu().tolist())
+        ed = torch.empty((n * 16, 2), dtype=torch.int32, device="cuda")
+        c = gg.girg_generate(ed, n=n, d=d, beta=2.5, T=T, avg_deg=10.0, seed=1).c_used
+        if spec["kind"] == "allpairs":
+            fn = lambda: gg.girg_allpairs(ed, X, w, W=W, T=T, c=c, seed=1)  # noqa: E731
+        else:
+            fn = lambda: gg.girg_generate_from_points(ed, X, w, T=T, c=c, seed=1)  # noqa: E731
+    elif spec["kind"] == "sweep":
+        n, d, T = args.n or (1 << 24), spec["d"], spec["T"]
+        ed = torch.empty((int(n * 16 * 0.75), 2), dtype=torch.int64, device="cuda")
+        fn = lambda: gg.girg_generate(ed, n=n, d=d, beta=2.2, T=T, avg_deg=16.0, seed=1)  # noqa: E731
+    else:
+        n = args.n or 10_000_000
+        ed = torch.empty((n * 8, 2), dtype=torch.int32, device="cuda")
+        fn = lambda: gg.hrg_generate(ed, n=n, alpha=0.75, T=0.5, avg_deg=10.0, seed=1)  # noqa: E731
+    ms, r = _median_ms(fn, torch, flush, max(1, args.steps), args.warmup)
+    if r.status != gg.GIRG_OK:
+        raise RuntimeError(f"{args.workload}: {gg.status_string(r.status)}")
+    print(json.dumps({"workload": args.workload, "ms": ms, "edges": r.num_edges,
+                      "phases_ms": gg.last_phase_ms()}), flush=True)
 
 
 def aggregate_ranks(vals, world: int, dist):
@@ -558,7 +622,16 @@ def main():
                     help="mixed requests of the batched/served run (0: skip it)")
     ap.add_argument("--config-steps", type=int, default=3,
                     help="timed calls per workload of the other configurations (0: skip)")
+    ap.add_argument("--workload", default=None, choices=sorted(SINGLE_WORKLOADS),
+                    help="run only this workload (--warmup calls, then --steps calls) and "
+                         "print its median time: for profiling one configuration")
+    ap.add_argument("--n", type=int, default=None,
+                    help="with --workload: vertices of a sweep or HRG workload (a smaller "
+                         "case of the same kernels for detailed profiles)")
     args = ap.parse_args()
+    if args.workload:
+        run_single(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

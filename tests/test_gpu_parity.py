@@ -437,3 +437,22 @@ def test_benchmark_workload_full_size_edge_for_edge():
     assert st["type2_candidates"] == ref.stats["type2_candidates"]
     assert st["jump_draws"] == ref.stats["jump_draws"]
 
+
+
+def test_autotuned_and_neighbouring_level_caps_keep_parity():
+    """The autotuner times the default level cap and its two neighbours; every one of them
+    draws an exact sample, so each equals the oracle at the same cap (two non-default
+    settings per class), and the tuned one is among them."""
+    from paper_1905_06706_gb300 import autotune as at
+    for (n, d, T) in [(30_000, 1, 0.6), (30_000, 2, 0.5)]:
+        q = dict(n=n, d=d, beta=2.4, T=T, avg_deg=9.0, seed=11)
+        tab = at.tune_level_caps({"c": q}, steps=1, warmup=1)["c"]
+        caps = sorted(int(c) for c in tab["ms"])
+        assert tab["level_cap"] in caps and tab["default"] in caps and len(caps) == 3
+        w, X = O.girg_points(n, d, 2.4, 1.0, 11)
+        W = O.exact_sum(w)
+        c = O.girg_solve_c(9.0, w, d, T, W)
+        for lc in caps:
+            ref = O.girg_cellpairs(X, w, float(w.min()), W, T, c, 11, cap=n * 64, level_cap=lc)
+            assert _generate_from(X, w, T, c, 11, gg.PRECISION_FP32, level_cap=lc) == \
+                O.edge_set(ref.edges), lc
