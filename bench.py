@@ -19,9 +19,12 @@ Reported:
              bytes = 8 B per edge it emits + one read of every sorted vertex record
   step_roofline  all algorithmic bytes of a step (edges + per-vertex bytes of every
              kernel) over the step time
+  issue_roofline  the dominant kernel's warp instructions per second against the
+             issue rate measured by the library's probe kernel
   configs    the other workloads, device-timed: the all-pairs configuration (d = 1,
              n = 10^4), the dimension sweep (d = 1..4, T in {0, 0.7}, n = 2^24, int64
-             edges) and the large HRG (n = 10^7)
+             edges), the large HRG (n = 10^7) and the benchmark's graph at n = 10^4..10^7
+             phase by phase
   cpu_baseline  the FP64 oracle (cell-pair sampler) on a bounded sample: one core, and
              independent samples on every host core (all_cores)
 
@@ -93,6 +96,50 @@ def _sms() -> int:
     schedulers per SM, each issuing at most one warp instruction per cycle)."""
     import torch
     return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def probe_source_digest() -> str:
+    """SHA-256 (16 hex digits) of the issue-rate probe's source."""
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1905_06706_gb300", "csrc", "probe.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _probe_ncu_instructions(kind: int):
+    """Warp instructions one probe launch of `kind` executed, from the committed ncu
+    summary of the probe (when it was taken from the current probe source)."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", "issue_probe.md")).read()
+        if f"probe-source-sha256 {probe_source_digest()}" not in text:
+            return None
+        for ln in text.splitlines():
+            if ln.startswith(f"| k_issue_probe<{kind}> |"):
+                return int(ln.split("|")[3].strip())
+    except (OSError, ValueError, IndexError):
+        pass
+    return None
+
+
+def measure_issue_peak(gg, iters: int = 2000, reps: int = 7) -> dict:
+    """The measured warp-instruction issue rate: the library's probe kernel over every
+    SM, one launch per instruction kind after two warm-up launches, median of `reps`.
+    The count is the probe's by construction, or ncu's count of the same launch (the
+    loop's own instructions included) when the committed summary matches the source."""
+    kinds = {}
+    for kind, name in enumerate(gg.ISSUE_PROBE_KINDS):
+        for _ in range(2):
+            gg.issue_probe(kind, iters)
+        runs = [gg.issue_probe(kind, iters) for _ in range(reps)]
+        ms = statistics.median(r[0] for r in runs)
+        nominal = runs[0][1]
+        counted = _probe_ncu_instructions(kind)
+        wi = counted if counted else nominal
+        kinds[name] = {"ms": ms, "warp_instructions": wi,
+                       "count": "ncu" if counted else "by construction",
+                       "rate": wi / (ms / 1e3)}
+    best = max(kinds, key=lambda k: kinds[k]["rate"])
+    return {"rate": kinds[best]["rate"], "kind": best, "kinds": kinds,
+            "nominal": 4 * _sms() * 2.07e9}
 
 
 def _ncu_traffic(kernel: str):
@@ -375,7 +422,8 @@ def run_configs(gg, torch, hbm: float, flush, steps: int = 3, warmup: int = 1) -
     the quadratic kernel and the cell-pair sampler, FP32 and FP64 decisions), the
     dimension sweep (d = 1..4, n = 2^24, beta = 2.2, T in {0, 0.7}, degree 16, seed 1,
     int64 edges) and the large HRG (n = 10^7, alpha = 0.75, T = 0.5, R solved for degree
-    10, seed 1, int32 edges).  Each entry: edges, median ms, edges/s, the fraction of the
+    10, seed 1, int32 edges), and the benchmark's graph at n = 10^4 .. 10^7 with the time
+    of each phase.  Each entry: edges, median ms, edges/s, the fraction of the
     edge-output roofline, the phases of the last call and its algorithmic bytes."""
     out = {}
 
@@ -433,6 +481,23 @@ def run_configs(gg, torch, hbm: float, flush, steps: int = 3, warmup: int = 1) -
     out["dimension_sweep"] = sweep
     del ed
 
+    # the benchmark's graph over a range of n: time and phases per call (Sec. 5.1's
+    # breakdown of the sampler's running time into its steps)
+    phase_sweep = []
+    for n in (10_000, 100_000, 1_000_000, 10_000_000):
+        ed = torch.empty((int(n * 6) + 200_000, 2), dtype=torch.int32, device="cuda")
+        ms, r = _median_ms(lambda: gg.girg_generate(ed, n=n, d=2, beta=2.5, T=0.5,
+                                                    avg_deg=10.0, seed=1),
+                           torch, flush, max(steps, 5), warmup + 1)
+        check(r, f"phase sweep n={n}")
+        eps, frac = _rate(r.num_edges, ms, 4, hbm)
+        phase_sweep.append({"workload": f"girg_d2_n{n:.0e}_T0.5_deg10".replace("+0", ""),
+                            "n": n, "edges": r.num_edges, "ms": ms, "edges_per_s": eps,
+                            "ns_per_vertex": ms * 1e6 / n, "edge_output_frac": frac,
+                            "phases_ms": gg.last_phase_ms()})
+        del ed
+    out["phase_sweep"] = phase_sweep
+
     # large HRG
     n = 10_000_000
     ed = torch.empty((n * 8, 2), dtype=torch.int32, device="cuda")
@@ -446,7 +511,8 @@ def run_configs(gg, torch, hbm: float, flush, steps: int = 3, warmup: int = 1) -
     out["large_hrg"] = {"workload": "hrg_n1e7_alpha0.75_T0.5_deg10", "R": R,
                         "edges": r.num_edges, "ms": ms, "edges_per_s": eps,
                         "edge_output_frac": frac, "phases_ms": ph,
-                        "note": "R solved on the host for degree 10 in every call"}
+                        "note": "R solved for degree 10 in every call (host search, "
+                                "distance CDF of each quadrature node on the device)"}
     del ed
     return out
 
@@ -459,6 +525,7 @@ SINGLE_WORKLOADS = {
     "cellpairs_d1_n1e4": dict(kind="cellpairs"),
     **{f"sweep_d{d}_T{T}": dict(kind="sweep", d=d, T=T) for d in (1, 2, 3, 4) for T in (0.0, 0.7)},
     "hrg_n1e7": dict(kind="hrg"),
+    "issue_probe": dict(kind="probe"),
 }
 
 
@@ -467,6 +534,17 @@ def run_single(args) -> None:
     import paper_1905_06706_gb300 as gg
     gg.load()
     spec = SINGLE_WORKLOADS[args.workload]
+    if spec["kind"] == "probe":
+        # --warmup launches, then --steps launches, of each instruction kind in turn
+        for kind, name in enumerate(gg.ISSUE_PROBE_KINDS):
+            for _ in range(args.warmup):
+                gg.issue_probe(kind)
+            runs = [gg.issue_probe(kind) for _ in range(max(1, args.steps))]
+            ms = statistics.median(r[0] for r in runs)
+            print(json.dumps({"workload": args.workload, "kind": name, "ms": ms,
+                              "warp_instructions": runs[0][1],
+                              "rate": runs[0][1] / (ms / 1e3)}), flush=True)
+        return
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     if spec["kind"] in ("allpairs", "cellpairs"):
         n, d, T = 10_000, 1, 0.5
@@ -724,6 +802,7 @@ def main():
     # count-only mode (no edge list stored; count and checksum only, as in Sec. 5)
     ms_co, m_co, _ = timed(gg.PRECISION_FP32, ke2e, out=False)
     barrier()
+    probe = measure_issue_peak(gg) if rank == 0 else None
     med_total = (lambda xs: statistics.median(xs) * len(xs) / 1e3 if xs else 0.0)
     vals = torch.tensor([t_rank, float(m_total), med_total(ms_e2e), float(m_e2e),
                          med_total(ms64), float(m64)], dtype=torch.float64, device="cuda")
@@ -778,10 +857,13 @@ def main():
         # launch from the committed ncu summary of the same kernel source, over the live
         # launch duration)
         winst = _ncu_metric(kname, "smsp__inst_executed.sum")
-        issue_peak = 4 * _sms() * 2.07e9
+        issue_peak = probe["rate"]
         issue_roof = {"kernel": kname, "bound": "alu", "unit": "warp instructions/s",
                       "peak": issue_peak,
-                      "peak_kind": f"derived: 4 schedulers x {_sms()} SMs x 2070 MHz",
+                      "peak_kind": f"measured: issue probe ({probe['kind']} runs over every "
+                                   f"SM; nominal 4 schedulers x {_sms()} SMs x 2070 MHz = "
+                                   f"{probe['nominal']:.4g})",
+                      "probe": probe["kinds"],
                       "warp_instructions": winst,
                       "achieved": (winst / (kms / 1e3)) if (winst and kms > 0) else None}
         if issue_roof["achieved"] is not None:

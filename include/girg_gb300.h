@@ -90,7 +90,9 @@ typedef struct {
  *   T          temperature, 0 <= T < 1
  *   avg_deg    target expected average degree, used when R <= 0 (0 < avg_deg < n - 1)
  *   R          disk radius R = 2 ln n + C (Sec. 2.2); R <= 0: solved from avg_deg
- *              (hrg_solve_radius)
+ *              by the search of hrg_solve_radius, with the quadrature's inner
+ *              integrals evaluated on the device at T > 0 (same rule; the radius
+ *              agrees with hrg_solve_radius to about 1e-12 relative)
  *   other fields as for girg_params.
  */
 typedef struct {
@@ -279,6 +281,19 @@ int girg_sorted_order(int64_t n, int32_t d, const uint32_t* d_X, const double* d
  * 6 the GIRG probability of Eq. 1 at weights (x, y), r = 1/4, W = 1000, c = 1/2,
  * T = 3/4, d = 2.  Returns NaN for an unknown fn.  Diagnostic; no GPU needed. */
 double girg_det_eval(int32_t fn, double x, double y);
+
+/* Measured warp-instruction issue rate (the denominator of the pair kernels' issue
+ * roofline).  One launch of a probe kernel that fills every SM (two 1024-thread
+ * blocks per SM) with runs of one instruction kind over eight independent register
+ * chains: kind 0 integer logic (lop3), 1 integer multiply-add (mad.lo.u32), 2 FP32
+ * fused multiply-add.  iters in [1, 2^24] loop trips of 128 instructions per thread.
+ * Writes the launch's CUDA-event time in *ms and the warp instructions the probe
+ * issues by construction (blocks x 32 warps x iters x 128; the loop's own few
+ * instructions per trip are not counted) in *warp_instructions.  Synchronises the
+ * stream.  Errors: GIRG_E_PARAM (kind, iters or a null pointer), GIRG_E_CUDA.
+ * Diagnostic: the paper has no counterpart. */
+int girg_issue_probe(int32_t kind, int64_t iters, void* stream, float* ms,
+                     int64_t* warp_instructions);
 
 /* ------------------------------------------------------------------------
  * Continuous-batching server (many requests in flight on one GPU).

@@ -80,6 +80,7 @@ SIGNATURES = {
     "girg_scratch_pool_trim": (I32, [I64]),
     "girg_point_cache": (I32, [I64]),
     "girg_point_cache_stats": (I32, [P, P, P, P]),
+    "girg_issue_probe": (I32, [I32, I64, P, P, P]),
     "girg_server_create": (I32, [I32, I64, P]),
     "girg_server_submit": (I32, [P, P, P, I64, I64]),
     "girg_server_poll": (I32, [P, P, I32, I32]),
@@ -202,6 +203,20 @@ def point_cache_stats() -> dict:
     load().girg_point_cache_stats(ctypes.byref(e), ctypes.byref(b), ctypes.byref(h),
                                   ctypes.byref(m))
     return {"entries": e.value, "bytes": b.value, "hits": h.value, "misses": m.value}
+
+
+ISSUE_PROBE_KINDS = ("lop3", "imad", "ffma")
+
+
+def issue_probe(kind: int, iters: int = 2000, stream=None) -> tuple:
+    """One launch of the issue-rate probe (kind 0 integer logic, 1 integer multiply-add,
+    2 FP32 fused multiply-add): (milliseconds, warp instructions issued by construction)."""
+    ms, wi = ctypes.c_float(0.0), ctypes.c_int64(0)
+    st = load().girg_issue_probe(kind, iters, _stream(stream), ctypes.byref(ms),
+                                 ctypes.byref(wi))
+    if st != GIRG_OK:
+        raise GirgError(st, "girg_issue_probe")
+    return float(ms.value), int(wi.value)
 
 
 def scratch_bytes(*, n, d, beta, T, avg_deg=0.0, c=0.0, w_min=1.0, seed=1, edge_bytes=4,

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgirg_gb300.so")
 
-CU_SOURCES = ["gen.cu", "sort.cu", "pairs.cu", "api.cu", "noalloc.cu", "server.cu"]
+CU_SOURCES = ["gen.cu", "sort.cu", "pairs.cu", "api.cu", "noalloc.cu", "server.cu", "probe.cu"]
 CPP_SOURCES = ["solver.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1528,6 +1528,37 @@ int hrg_solve_radius(int64_t n, double alpha, double T, double avg_deg, double* 
     return GIRG_OK;
 }
 
+// The radius for a target degree at T > 0 with the distance CDF of every node of the
+// logistic t rule evaluated on the device (one launch and one readback per step of
+// the search); the search itself and the sums over the nodes stay on the host.
+double hrg_radius_on_device(const hrg_params& q, Scratch& S, cudaStream_t st) {
+    HrgYRule Y;
+    Y.n = kHrgYNodes;
+    static_assert(kHrgYNodes <= kHrgYMax, "y rule fits");
+    hrg_unit_y_rule(Y.c, Y.w);
+    constexpr int kMaxNodes = 512;  // the t rule has at most 12 intervals of 20 nodes
+    double* d_ts = S.get<double>(kMaxNodes);
+    double* d_g = S.get<double>(kMaxNodes);
+    std::vector<double> ts, ws, g;
+    auto E = [&](double R) {
+        double tail = 0.0;
+        hrg_t_rule(R, q.T, ts, ws, &tail);
+        const int nt = (int)ts.size();
+        if (nt > kMaxNodes) throw Status{GIRG_E_INTERNAL};
+        g.assign(nt, 0.0);
+        CK(cudaMemcpyAsync(d_ts, ts.data(), nt * sizeof(double), cudaMemcpyHostToDevice, st));
+        launch_hrg_dist_cdf(q.alpha, R, Y, d_ts, nt, d_g, st);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(g.data(), d_g, nt * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        double p = 0.0;
+        for (int i = 0; i < nt; ++i) p += ws[i] * g[i];
+        p += tail;
+        return (double)(q.n - 1) * p;
+    };
+    return hrg_radius_for_degree(q.n, q.alpha, q.T, q.avg_deg, E);
+}
+
 int hrg_generate(const hrg_params* params, void* d_edges, int64_t capacity_edges,
                  int64_t* num_edges, double* R_used, void* stream) {
     if (!params || !num_edges || capacity_edges < 0) return GIRG_E_PARAM;
@@ -1537,11 +1568,8 @@ int hrg_generate(const hrg_params* params, void* d_edges, int64_t capacity_edges
         (q.precision != 0 && q.precision != 1) ||
         q.level_cap < 0)
         return GIRG_E_PARAM;
-    if (!(q.R > 0.0)) {
-        const int s = hrg_solve_radius(q.n, q.alpha, q.T, q.avg_deg, &q.R);
-        if (s != GIRG_OK) return s;
-    }
-    if (R_used) *R_used = q.R;
+    const bool solve = !(q.R > 0.0);
+    if (solve && !(q.avg_deg > 0.0 && q.avg_deg < (double)(q.n - 1))) return GIRG_E_PARAM;
     return guarded([&] {
         cudaStream_t st = (cudaStream_t)stream;
         girg_params est{};
@@ -1549,6 +1577,15 @@ int hrg_generate(const hrg_params* params, void* d_edges, int64_t capacity_edges
         est.d = 1;
         est.T = q.T;
         Scratch S(st, scratch_reserve(est));
+        for (int k = 7; k <= 9; ++k) g_ms[k] = 0.0f;
+        if (solve) {  // the radius for the target degree (host search)
+            const auto h0 = std::chrono::steady_clock::now();
+            q.R = q.T > 0.0 ? hrg_radius_on_device(q, S, st)
+                            : hrg_radius_for_degree(q.n, q.alpha, q.T, q.avg_deg);
+            g_ms[8] = (float)host_ms_since(h0);
+            if (!(q.R > 0.0 && q.R <= 350.0)) return GIRG_E_PARAM;
+        }
+        if (R_used) *R_used = q.R;
         Timer tm(st);
         g_launches = 0;
         tm.mark();
@@ -1574,7 +1611,9 @@ int hrg_generate(const hrg_params* params, void* d_edges, int64_t capacity_edges
         Reduce* red = new_reduce(S, st);
         launch_reduce(P.n, w, r, 1.0, exponent_of_ulp(1.0), nullptr, red, st);
         tm.mark();
+        const auto h1 = std::chrono::steady_clock::now();
         read_reduce(P, red, st);  // the HRG needs no weight sum: a range error is harmless
+        g_ms[7] = (float)host_ms_since(h1);
         P.W = 1.0;
         Layout Lo;
         build_layout(P, S, S, st, tm, Lo, nullptr);

@@ -254,7 +254,7 @@ __global__ void k_split_weights(int64_t n, const double* __restrict__ w,
                     y = x;
                     for (int q = 1; q < m_int; ++q) y *= x;
                 } else {
-                    y = exp2(invT * log2(x));
+                    y = det_pow(x, invT);  // integer pipes: the FP64 units are slow
                 }
                 a[2] += y;
                 a[3] += y * y;
@@ -377,6 +377,109 @@ void launch_reduce(int64_t n, const double* w, const double* r, double w_min, in
 }
 
 
+
+// ---------------------------------------------------------------- HRG degree
+// The distance CDF of the HRG's expected degree at T > 0 (Sec. 2.2): the probability
+// that two random vertices lie closer than t.  Radii have density
+// alpha sinh(alpha r) / (cosh(alpha R) - 1); in y = R - r the share of angle
+// differences with distance below t is (2/pi) asin(sqrt(s)),
+// s = (cosh t - cosh(r1 - r2)) / (2 sinh r1 sinh r2), between the ends where it is 0
+// or 1, so the integral runs over the intervals between 0, R and the kinks R - t,
+// 2R - t and t.  One block per t node; every thread takes (interval, y1 node, y2 node)
+// triples of the product rule, and the block sums them in a fixed order.
+constexpr int kCdfThreads = 256;
+
+__device__ __forceinline__ double disk_dens(double alpha, double R, double cm1, double y) {
+    return alpha * sinh(alpha * (R - y)) / cm1;
+}
+
+__device__ __forceinline__ double disk_cdf(double alpha, double R, double cm1, double y) {
+    return 1.0 - (cosh(alpha * (R - y)) - 1.0) / cm1;
+}
+
+__device__ __forceinline__ double angle_share(double r1, double r2, double t, double cosh_t) {
+    if (t >= r1 + r2) return 1.0;
+    if (t <= fabs(r1 - r2)) return 0.0;
+    const double s = (cosh_t - cosh(r1 - r2)) / (2.0 * sinh(r1) * sinh(r2));
+    if (!(s > 0.0)) return 0.0;
+    if (s >= 1.0) return 1.0;
+    return 0.63661977236758134308 * asin(sqrt(s));  // 2/pi
+}
+
+__global__ void __launch_bounds__(kCdfThreads)
+    k_hrg_dist_cdf(double alpha, double R, double cm1, HrgYRule Y,
+                   const double* __restrict__ ts, double* __restrict__ g) {
+    __shared__ double s_cut[5];
+    __shared__ int s_ncut;
+    __shared__ double s_part[kCdfThreads / 32];
+    const double t = ts[blockIdx.x];
+    if (!(t > 0.0) || t >= 2.0 * R) {
+        if (threadIdx.x == 0) g[blockIdx.x] = t >= 2.0 * R ? 1.0 : 0.0;
+        return;
+    }
+    if (threadIdx.x == 0) {
+        double c[5];
+        int m = 0;
+        c[m++] = 0.0;
+        c[m++] = R;
+        const double cand[3] = {R - t, 2.0 * R - t, t};
+        for (int q = 0; q < 3; ++q)
+            if (cand[q] > 0.0 && cand[q] < R) c[m++] = cand[q];
+        for (int i = 1; i < m; ++i) {  // insertion sort of at most five cuts
+            const double x = c[i];
+            int j = i - 1;
+            while (j >= 0 && c[j] > x) {
+                c[j + 1] = c[j];
+                --j;
+            }
+            c[j + 1] = x;
+        }
+        for (int i = 0; i < m; ++i) s_cut[i] = c[i];
+        s_ncut = m;
+    }
+    __syncthreads();
+    const int m = s_ncut, ny = Y.n, per = ny * ny;
+    const double ct = cosh(t);
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < (m - 1) * per; k += kCdfThreads) {
+        const int q = k / per, a = (k / ny) % ny, b = k % ny;
+        const double a0 = s_cut[q], a1 = s_cut[q + 1];
+        if (!(a1 > a0)) continue;
+        const double y1 = a0 + (a1 - a0) * Y.c[a];
+        const double lo = fmax(0.0, y1 - t), hi = fmin(R, y1 + t);
+        const double full = 2.0 * R - t - y1;  // share = 1 for y2 >= full
+        if (!(hi > lo)) continue;
+        if (full <= lo && b != 0) continue;
+        double in = 0.0;
+        if (full <= lo) {
+            in = disk_cdf(alpha, R, cm1, hi) - disk_cdf(alpha, R, cm1, lo);
+        } else {
+            const double top = fmin(hi, full);
+            const double y2 = lo + (top - lo) * Y.c[b];
+            in = (top - lo) * Y.w[b] * disk_dens(alpha, R, cm1, y2) *
+                 angle_share(R - y1, R - y2, t, ct);
+            if (b == 0 && full < hi)
+                in += disk_cdf(alpha, R, cm1, hi) - disk_cdf(alpha, R, cm1, full);
+        }
+        acc += (a1 - a0) * Y.w[a] * disk_dens(alpha, R, cm1, y1) * in;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int i = 0; i < kCdfThreads / 32; ++i) sum += s_part[i];
+        g[blockIdx.x] = sum;
+    }
+}
+
+void launch_hrg_dist_cdf(double alpha, double R, const HrgYRule& Y, const double* d_ts, int nt,
+                         double* d_g, cudaStream_t st) {
+    if (nt <= 0) return;
+    const double cm1 = cosh(alpha * R) - 1.0;
+    ++g_launches;
+    k_hrg_dist_cdf<<<nt, kCdfThreads, 0, st>>>(alpha, R, cm1, Y, d_ts, d_g);
+}
 
 void launch_split_weights(int64_t n, const double* w, const double* thr, double T, double* out,
                           unsigned int cap, unsigned int* count, double* part, double* sums,

@@ -44,6 +44,17 @@ void launch_girg_points(int64_t n, int d, double beta, double w_min, uint64_t se
 void launch_hrg_points(int64_t n, double alpha, double R, uint64_t seed, double* r, double* w,
                        uint32_t* X, cudaStream_t st);
 void launch_min_weight(int64_t n, const double* w, unsigned long long* out, cudaStream_t st);
+// P(dist < t) of two random vertices of the hyperbolic disk (radius R, dispersion
+// alpha) at each of the nt nodes d_ts, into d_g: the double integral over the radii
+// with the y rule (nodes a + (b - a) c[k], weights (b - a) w[k] on every smooth
+// interval [a, b]), one block per node, summed in a fixed order.
+constexpr int kHrgYMax = 32;
+struct HrgYRule {
+    double c[kHrgYMax], w[kHrgYMax];
+    int n;
+};
+void launch_hrg_dist_cdf(double alpha, double R, const HrgYRule& Y, const double* d_ts, int nt,
+                         double* d_g, cudaStream_t st);
 // Blocks of the reduction (one per-block partial each): a fixed partition of the
 // vertices, independent of the device, so that the sums finished in block order
 // round the same way on every GPU.

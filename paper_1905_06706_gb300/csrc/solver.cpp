@@ -294,9 +294,8 @@ double dist_cdf(const Disk& D, double t) {
 
 }  // namespace
 
-double hrg_expected_degree(int64_t n, double alpha, double T, double R) {
-    const Disk D{alpha, R, std::cosh(alpha * R) - 1.0};
-    if (T == 0.0) return (double)(n - 1) * dist_cdf(D, R);
+void hrg_t_rule(double R, double T, std::vector<double>& ts, std::vector<double>& ws,
+                double* tail) {
     // t panels growing geometrically away from R; the logistic weight outside
     // R +- 80 T is below e^-40
     const double s = 2.0 * T, tlo = std::max(0.0, R - 40.0 * s), thi = std::min(2.0 * R, R + 40.0 * s);
@@ -304,7 +303,8 @@ double hrg_expected_degree(int64_t n, double alpha, double T, double R) {
     for (double x = R, w = s; x > tlo; w *= 2.0) cuts.push_back(x = std::max(tlo, x - w));
     for (double x = R, w = s; x < thi; w *= 2.0) cuts.push_back(x = std::min(thi, x + w));
     std::sort(cuts.begin(), cuts.end());
-    std::vector<double> ts, ws;
+    ts.clear();
+    ws.clear();
     double tb[kTPanels * kGL], wtb[kTPanels * kGL];
     for (size_t q = 0; q + 1 < cuts.size(); ++q) {
         if (!(cuts[q + 1] > cuts[q])) continue;
@@ -315,6 +315,21 @@ double hrg_expected_degree(int64_t n, double alpha, double T, double R) {
             ws.push_back(wtb[a] * e / (s * (1.0 + e) * (1.0 + e)));
         }
     }
+    const double eh = std::exp(-(thi - R) / s);
+    *tail = eh / (1.0 + eh);  // t beyond thi: the distance CDF is 1 (or the weight negligible)
+}
+
+void hrg_unit_y_rule(double* c, double* w) {
+    static_assert(kHrgYNodes == kYPanels * kGL, "y rule size");
+    cos_mapped_rule(0.0, 1.0, kYPanels, c, w);
+}
+
+double hrg_expected_degree(int64_t n, double alpha, double T, double R) {
+    const Disk D{alpha, R, std::cosh(alpha * R) - 1.0};
+    if (T == 0.0) return (double)(n - 1) * dist_cdf(D, R);
+    std::vector<double> ts, ws;
+    double tail = 0.0;
+    hrg_t_rule(R, T, ts, ws, &tail);
     // the distance CDF at every node, spread over host threads; summed in node order
     std::vector<double> g(ts.size(), 0.0);
     const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
@@ -327,12 +342,17 @@ double hrg_expected_degree(int64_t n, double alpha, double T, double R) {
     for (auto& t : pool) t.join();
     double p = 0.0;
     for (size_t i = 0; i < ts.size(); ++i) p += ws[i] * g[i];
-    const double eh = std::exp(-(thi - R) / s);
-    p += eh / (1.0 + eh);  // t beyond thi: the distance CDF is 1 (or the weight negligible)
+    p += tail;
     return (double)(n - 1) * p;
 }
 
 double hrg_radius_for_degree(int64_t n, double alpha, double T, double target) {
+    return hrg_radius_for_degree(n, alpha, T, target,
+                                 [&](double R) { return hrg_expected_degree(n, alpha, T, R); });
+}
+
+double hrg_radius_for_degree(int64_t n, double alpha, double T, double target,
+                             const std::function<double(double)>& E) {
     // start from the large-R limit E ~ K n e^(-R/2), K = 8 alpha^2 / (pi (2 alpha - 1)^2)
     // times pi T / sin(pi T); ln E is nearly linear in R, so regula falsi (Illinois)
     // on ln E(R) - ln target converges in a few steps
@@ -340,7 +360,7 @@ double hrg_radius_for_degree(int64_t n, double alpha, double T, double target) {
     if (T > 0.0) K *= kPi * T / std::sin(kPi * T);
     double r0 = 2.0 * std::log(K * (double)n / target);
     if (!(r0 > 1e-3 && r0 < 700.0)) r0 = std::min(700.0, std::max(1.0, 2.0 * std::log((double)n)));
-    auto F = [&](double R) { return std::log(hrg_expected_degree(n, alpha, T, R)) - std::log(target); };
+    auto F = [&](double R) { return std::log(E(R)) - std::log(target); };
     double lo = r0, hi = r0, flo = F(r0), fhi = flo;
     if (flo == 0.0) return r0;
     // F decreases in R: find lo with F >= 0 and hi with F < 0

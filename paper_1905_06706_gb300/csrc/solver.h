@@ -60,5 +60,18 @@ namespace gg {
 double hrg_expected_degree(int64_t n, double alpha, double T, double R);
 // R with hrg_expected_degree(n, alpha, T, R) = target (NaN if none in (0, 700)).
 double hrg_radius_for_degree(int64_t n, double alpha, double T, double target);
+// The same search with another evaluation of the expected degree E(R).
+double hrg_radius_for_degree(int64_t n, double alpha, double T, double target,
+                             const std::function<double(double)>& E);
+
+// The pieces of the T > 0 quadrature, for evaluating it elsewhere (the device):
+// t nodes and weights (with the logistic density folded in) so that
+// P(adjacent) = sum_i ws[i] P(dist < ts[i]) + *tail;
+void hrg_t_rule(double R, double T, std::vector<double>& ts, std::vector<double>& ws,
+                double* tail);
+// and the y rule on [0, 1] that P(dist < t) applies to each of its intervals [a, b]
+// (nodes a + (b - a) c[k], weights (b - a) w[k], k < kHrgYNodes).
+constexpr int kHrgYNodes = 30;
+void hrg_unit_y_rule(double* c, double* w);
 
 }  // namespace gg

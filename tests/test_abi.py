@@ -70,6 +70,16 @@ def test_noalloc_refuses_pointers_the_gpu_cannot_use(lib):
     assert st == gg.GIRG_E_PARAM and m.value == -1 and not out.any()
 
 
+def test_issue_probe_rejects_bad_arguments(lib):
+    """The issue-rate probe checks its kind, trip count and result pointers on the host."""
+    ms, wi = ctypes.c_float(-1.0), ctypes.c_int64(-1)
+    for kind, iters in ((3, 10), (-1, 10), (0, 0), (2, (1 << 24) + 1)):
+        st = lib.girg_issue_probe(kind, iters, None, ctypes.byref(ms), ctypes.byref(wi))
+        assert st == gg.GIRG_E_PARAM
+    assert lib.girg_issue_probe(0, 10, None, None, ctypes.byref(wi)) == gg.GIRG_E_PARAM
+    assert ms.value == -1.0 and wi.value == -1
+
+
 def test_invalid_hrg_and_points_rejected(lib):
     m = ctypes.c_int64(0)
     for hp in (gg.HrgParams(1000, 0.5, 0.5, 0.0, 10.0, 1, 4, 0, 0),    # alpha must exceed 1/2

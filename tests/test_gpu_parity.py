@@ -373,6 +373,23 @@ def test_hrg_solved_radius_edge_for_edge(T, deg):
     assert abs(2.0 * res.num_edges / n - deg) < 0.15 * deg
 
 
+@pytest.mark.parametrize("n,alpha,T,deg", [(1_000, 0.75, 0.3, 10.0), (60_000, 0.6, 0.5, 5.0),
+                                           (200_000, 0.9, 0.9, 20.0),
+                                           (10_000_000, 0.75, 0.5, 10.0)])
+def test_device_radius_search_matches_host_and_oracle(n, alpha, T, deg):
+    """At T > 0 the generator evaluates the quadrature's distance CDF on the device; the
+    radius it solves agrees with the host search (same rule, CUDA's FP64 functions) to
+    1e-11 and with the oracle's to 1e-9, and its expected degree is the target."""
+    res = gg.hrg_generate(None, n=n, alpha=alpha, T=T, avg_deg=deg, seed=3)
+    assert res.status == gg.GIRG_OK
+    R_host = gg.hrg_solve_radius(n, alpha, T, deg)
+    assert abs(res.R_used - R_host) <= 1e-11 * R_host
+    R_orc = O.hrg_solve_R(n, alpha, T, deg)
+    assert abs(res.R_used - R_orc) <= 1e-9 * R_orc
+    assert abs(gg.hrg_expected_avg_degree(n, alpha, T, res.R_used) / deg - 1.0) < 1e-9
+    assert gg.last_phase_ms()["host_c_search"] > 0.0
+
+
 # --------------------------------------------------------------------- count-only mode
 
 @pytest.mark.parametrize("d,T", [(2, 0.5), (1, 0.0), (3, 0.7)])
