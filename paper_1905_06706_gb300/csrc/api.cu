@@ -591,13 +591,13 @@ void run_sampler(Problem& P, const Layout& Lo, Scratch& S, cudaStream_t st, Time
     // count and the two work counters of the type-I / type-II kernels), one round's
     // work-list counts (type-I items, streams, segments) and statistics, and the 32-bit
     // row / entry / error counters
-    unsigned long long* small = S.get<unsigned long long>(kNumStats + 3 + 3 + kNumStats + 8);
+    constexpr size_t kSmallWords = kNumStats + 3 + 3 + kNumStats + 8;
+    unsigned long long* small = S.get<unsigned long long>(kSmallWords);
     unsigned long long* stats = small;
     unsigned long long* wcount = stats + kNumStats + 3;
     unsigned long long* estats = wcount + 3;
     unsigned int* counters = reinterpret_cast<unsigned int*>(estats + kNumStats);
-    CK(cudaMemsetAsync(small, 0, (kNumStats + 3 + 3 + kNumStats + 8) * sizeof(unsigned long long),
-                       st));
+    CK(cudaMemsetAsync(small, 0, kSmallWords * sizeof(unsigned long long), st));
     // work lists, sized from typical counts per vertex; the enumeration only writes
     // work (no edges), so an overflow is repaired by resizing and running it again
     // GIRG_INITIAL_LIST_SCALE in (0, 1] shrinks the initial sizes (tests use it to
@@ -757,14 +757,20 @@ void run_sampler(Problem& P, const Layout& Lo, Scratch& S, cudaStream_t st, Time
         launch_type2(cfg, st);
         tm.mark();  // type II done
         cfg.lists_ok = nullptr;  // the rounds below check the counts on the host first
+        // the whole counter block in one readback: statistics and edge count, the
+        // round's list counts and statistics, the row / entry / error counters
+        unsigned long long hsmall[kSmallWords];
+        CK(cudaMemcpyAsync(hsmall, small, sizeof(hsmall), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
         unsigned long long wc[3], es[kNumStats];
         unsigned int ec[2];
-        CK(cudaMemcpyAsync(wc, wcount, sizeof(wc), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(ec, counters + 6, sizeof(ec), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(es, estats, sizeof(es), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(rc, counters, sizeof(rc), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        memcpy(wc, hsmall + (wcount - small), sizeof(wc));
+        memcpy(es, hsmall + (estats - small), sizeof(es));
+        memcpy(hs, hsmall + (stats - small), sizeof(hs));
+        const unsigned char* hcounters =
+            reinterpret_cast<const unsigned char*>(hsmall + (estats + kNumStats - small));
+        memcpy(rc, hcounters, sizeof(rc));
+        memcpy(ec, hcounters + 6 * sizeof(unsigned int), sizeof(ec));
         n_ent2 = ec[0];
         n_ent1 = ec[1];
         if (wc[0] <= cfg.t1_cap && wc[1] <= cfg.stream_cap && wc[2] <= cfg.seg_cap) {

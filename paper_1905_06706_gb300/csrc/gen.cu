@@ -289,12 +289,15 @@ __global__ void k_split_weights(int64_t n, const double* __restrict__ w,
 }
 
 // The gathered weights in decreasing order, when there are at most kTopSortMax of them
-// (count[1] = 1; else count[1] = 0 and the host has them sorted): every thread places
-// one weight at its rank, the number of larger weights plus the number of equal ones
-// before it, reading all of them from shared memory.  k weights cost k^2 comparisons
-// spread over ceil(k / 256) blocks; they compare the bit patterns as integers (positive
+// (count[1] = 1; else count[1] = 0 and the host has them sorted): each weight goes to its
+// rank, the number of larger weights plus the number of equal ones before it.  A block
+// ranks kRankPerBlock weights with kRankSplit threads each, every thread counting over
+// every kRankSplit-th weight of shared memory; k weights cost k^2 comparisons over
+// ceil(k / kRankPerBlock) blocks.  They compare the bit patterns as integers (positive
 // doubles order like them), since the FP64 units are slow.
 constexpr unsigned int kRankThreads = 256;
+constexpr unsigned int kRankSplit = 8;
+constexpr unsigned int kRankPerBlock = kRankThreads / kRankSplit;
 
 __global__ void __launch_bounds__(kRankThreads) k_rank_top(const double* __restrict__ buf,
                                                           unsigned int* __restrict__ count,
@@ -306,18 +309,24 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_top(const double* __restr
         return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) count[1] = 1u;
-    if (blockIdx.x * kRankThreads >= k) return;  // the whole block: no weight of its own
+    if (blockIdx.x * kRankPerBlock >= k) return;  // the whole block: no weight of its own
     for (unsigned int i = threadIdx.x; i < k; i += kRankThreads)
         s_w[i] = (unsigned long long)__double_as_longlong(buf[i]);
     __syncthreads();
-    const unsigned int i = blockIdx.x * kRankThreads + threadIdx.x;
+    const unsigned int i = blockIdx.x * kRankPerBlock + threadIdx.x / kRankSplit;
+    const unsigned int sub = threadIdx.x % kRankSplit;
+    unsigned int r = 0;
+    unsigned long long x = 0;
     if (i < k) {
-        const unsigned long long x = s_w[i];
-        unsigned int r = 0;
-        for (unsigned int j = 0; j < i; ++j) r += s_w[j] >= x ? 1u : 0u;  // ties before i
-        for (unsigned int j = i + 1; j < k; ++j) r += s_w[j] > x ? 1u : 0u;
-        sorted[r] = __longlong_as_double((long long)x);
+        x = s_w[i];
+        for (unsigned int j = sub; j < k; j += kRankSplit)
+            r += (j < i ? s_w[j] >= x : s_w[j] > x) ? 1u : 0u;  // ties before i count
     }
+    // the kRankSplit partial counts of a weight sit in consecutive lanes
+#pragma unroll
+    for (unsigned int o = kRankSplit / 2; o > 0; o >>= 1)
+        r += __shfl_down_sync(0xffffffffu, r, o, kRankSplit);
+    if (i < k && sub == 0) sorted[r] = __longlong_as_double((long long)x);
 }
 
 bool det_tables_gen() { return det_tables_ready(); }
@@ -490,7 +499,7 @@ void launch_split_weights(int64_t n, const double* w, const double* thr, double 
     const int nb = reduce_blocks(n);
     g_launches += 2;
     k_split_weights<<<nb, 256, 0, st>>>(n, w, thr, invT, m_int, out, cap, count, part, sums);
-    k_rank_top<<<kTopSortMax / kRankThreads, kRankThreads, 0, st>>>(out, count, sorted);
+    k_rank_top<<<kTopSortMax / kRankPerBlock, kRankThreads, 0, st>>>(out, count, sorted);
 }
 
 }  // namespace gg
