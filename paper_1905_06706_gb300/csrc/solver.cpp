@@ -7,6 +7,35 @@
 
 namespace gg {
 
+namespace {
+
+// Chunks [c kChunk, min((c + 1) kChunk, n)) of an index range, handed to up to 16 host
+// threads (chunk c to thread c mod threads) when `parallel` (work with an exp or log per
+// index; cheaper work does not repay starting the threads), else all on the caller's
+// thread.  The chunks do not depend on the thread count, so per-chunk results combined
+// in chunk order are the same either way and on every machine.
+constexpr size_t kChunk = 16384;
+
+template <class F>
+void for_chunks(size_t n, bool parallel, F f) {
+    const size_t nc = (n + kChunk - 1) / kChunk;
+    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const size_t nt = parallel ? std::min<size_t>(hw, nc) : 1;
+    if (nt <= 1) {
+        for (size_t c = 0; c < nc; ++c) f(c, c * kChunk, std::min(n, (c + 1) * kChunk));
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < nt; ++t)
+        pool.emplace_back([&, t] {
+            for (size_t c = t; c < nc; c += nt) f(c, c * kChunk, std::min(n, (c + 1) * kChunk));
+        });
+    for (size_t c = 0; c < nc; c += nt) f(c, c * kChunk, std::min(n, (c + 1) * kChunk));
+    for (auto& th : pool) th.join();
+}
+
+}  // namespace
+
 void DegreeModel::set_split(double thr, std::vector<double> top, double sw, double s2, double sx,
                             double sx2) {
     thr_ = thr;
@@ -17,17 +46,25 @@ void DegreeModel::set_split(double thr, std::vector<double> top, double sw, doub
     top_ = std::move(top);
     const size_t m = top_.size();
     const bool tp = T_ > 0.0;
-    lw_.assign(m, 0.0);
-    b_.assign(m + 1, 0.0);
-    suf_.assign(m + 1, 0.0);
-    suf2_.assign(m + 1, 0.0);
-    sr_.assign(m + 1, 0.0);
-    sr2_.assign(m + 1, 0.0);
     const double inv = tp ? 1.0 / T_ : 0.0;
     mi_ = (tp && inv == std::floor(inv) && inv <= 8.0) ? (int)inv : 0;
+    const bool logs = tp && !mi_;  // the log path's arrays; the others stay empty
+    suf_.assign(m + 1, 0.0);
+    suf2_.assign(m + 1, 0.0);
+    b_.assign(logs ? m + 1 : 0, 0.0);
+    sr_.assign(logs ? m + 1 : 0, 0.0);
+    sr2_.assign(logs ? m + 1 : 0, 0.0);
     py_.assign(mi_ ? m : 0, 0.0);
     spy_.assign(mi_ ? m + 1 : 0, 0.0);
     spy2_.assign(mi_ ? m + 1 : 0, 0.0);
+    if (logs) {  // b = log(w) / T and the ratios r_i = e^(b_(i+1) - b_i) <= 1, in parallel
+        for_chunks(m, true, [&](size_t, size_t lo, size_t hi) {
+            for (size_t i = lo; i < hi; ++i) b_[i] = std::log(top_[i]) / T_;
+        });
+        for_chunks(m, true, [&](size_t, size_t lo, size_t hi) {
+            for (size_t i = lo; i < hi; ++i) sr2_[i] = i + 1 < m ? std::exp(b_[i + 1] - b_[i]) : 0.0;
+        });
+    }
     for (size_t i = m; i-- > 0;) {  // from the light end
         suf_[i] = suf_[i + 1] + top_[i];
         suf2_[i] = suf2_[i + 1] + top_[i] * top_[i];
@@ -40,10 +77,8 @@ void DegreeModel::set_split(double thr, std::vector<double> top, double sw, doub
             spy2_[i] = spy2_[i + 1] + p * p;
             continue;
         }
-        if (tp) {  // logs only off the integer path
-            lw_[i] = std::log(top_[i]);
-            b_[i] = lw_[i] / T_;
-            const double r = i + 1 < m ? std::exp(b_[i + 1] - b_[i]) : 0.0;  // <= 1
+        if (logs) {
+            const double r = sr2_[i];  // the ratio, replaced by the suffix aggregate
             sr_[i] = 1.0 + r * sr_[i + 1];
             sr2_[i] = 1.0 + r * r * sr2_[i + 1];
         }
@@ -93,25 +128,52 @@ double DegreeModel::f(double K, double* slope) const {
         if (tp && m) s2 = (mi_ ? C * spy_[0] : std::exp(lAT + lt / T + b_[0]) * sr_[0]) * sx_;
         add(2.0 * s1, 2.0 * s2);
     }
-    // top x top
-    size_t k = m, u = 0;
-    for (; u < m; ++u) {
-        const double wu = top_[u];
-        while (k > 0 && A * wu * top_[k - 1] < 1.0) --k;
-        if (k == 0 && u > 0) break;  // from here on no u has E_R partners
-        const size_t k1 = u == k ? k + 1 : k;  // first non-E_R partner
-        const double s1 = A * wu * (u > k ? suf_[k] - wu : suf_[k1]);
-        double s2 = 0.0;
-        if (mi_) {
-            s2 = C * py_[u] * spy_[k1];
-            if (u > k) s2 -= C * py_[u] * py_[u];  // at most half of the sum
-        } else if (tp) {
-            const double xu = lAT + b_[u];  // log (A w_u)^(1/T)
-            s2 = k1 < m ? std::exp(xu + b_[k1]) * sr_[k1] : 0.0;
-            if (u > k) s2 -= std::exp(xu + b_[u]);  // at most half of the sum
+    // top x top: the u with E_R partners one by one (k = their number, non-increasing
+    // in u), in chunks of u (in parallel on the exp path) summed in chunk order; u_b is
+    // the first u > 0 whose heaviest partner is no E_R partner
+    size_t u = 1, ub_hi = m;
+    while (u < ub_hi) {  // first u >= 1 with A w_u w_0 < 1 (m if none)
+        const size_t mid = u + (ub_hi - u) / 2;
+        if (A * top_[mid] * top_[0] < 1.0) ub_hi = mid; else u = mid + 1;
+    }
+    u = m ? std::max<size_t>(u, 1) : 0;
+    const size_t nch = (u + kChunk - 1) / kChunk;
+    std::vector<double> cval(nch, 0.0), cslp(nch, 0.0);
+    for_chunks(u, tp && !mi_, [&](size_t c, size_t lo, size_t hi) {
+        // k at the chunk's first u: the number of v with A w_u w_v >= 1
+        size_t k = 0, kh = m;
+        {
+            const double wu = top_[lo];
+            while (k < kh) {
+                const size_t mid = k + (kh - k) / 2;
+                if (A * wu * top_[mid] < 1.0) kh = mid; else k = mid + 1;
+            }
         }
-        val += (double)k - (u < k ? 1.0 : 0.0);
-        add(s1, s2);
+        double v = 0.0, sl = 0.0;
+        for (size_t q = lo; q < hi; ++q) {
+            const double wu = top_[q];
+            while (k > 0 && A * wu * top_[k - 1] < 1.0) --k;
+            const size_t k1 = q == k ? k + 1 : k;  // first non-E_R partner
+            const double s1 = A * wu * (q > k ? suf_[k] - wu : suf_[k1]);
+            double s2 = 0.0;
+            if (mi_) {
+                s2 = C * py_[q] * spy_[k1];
+                if (q > k) s2 -= C * py_[q] * py_[q];  // at most half of the sum
+            } else if (tp) {
+                const double xu = lAT + b_[q];  // log (A w_u)^(1/T)
+                s2 = k1 < m ? std::exp(xu + b_[k1]) * sr_[k1] : 0.0;
+                if (q > k) s2 -= std::exp(xu + b_[q]);  // at most half of the sum
+            }
+            v += (double)k - (q < k ? 1.0 : 0.0);
+            v += (s1 - T * s2) * inv1mT;
+            sl += (s1 - s2) * inv1mT;
+        }
+        cval[c] = v;
+        cslp[c] = sl;
+    });
+    for (size_t c = 0; c < nch; ++c) {
+        val += cval[c];
+        slp += cslp[c];
     }
     if (u < m) {  // u .. m-1: no E_R partners, all other top weights are partners
         const double s1 = A * (suf_[u] * suf_[0] - suf2_[u]);

@@ -41,7 +41,7 @@ class DegreeModel {
     // sums of w and w^2, and the suffix sums of w^(1/T) and w^(2/T) scaled by the
     // suffix's first term: sum_{j >= k} e_j = exp(b_k) sr_[k], sum e_j^2 = exp(2 b_k)
     // sr2_[k], e = w^(1/T) (no power of a weight is formed, whatever T)
-    std::vector<double> top_, lw_, b_, suf_, suf2_, sr_, sr2_;
+    std::vector<double> top_, b_, suf_, suf2_, sr_, sr2_;
     // when 1/T is an integer mi <= 8: y = (w/thr)^mi (>= 1, no overflow) and suffix sums
     // of y and y^2, so that z^(1/T) = (A thr^2)^mi y_u y_v needs no exp
     int mi_ = 0;

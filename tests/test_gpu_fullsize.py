@@ -100,7 +100,7 @@ def test_large_hrg_reduced_size_edge_for_edge():
     assert gg.last_stats()["edge_checksum"] == O.edge_checksum(ref.edges)
 
 
-@pytest.mark.parametrize("d,T", [(1, 0.0), (2, 0.7)])
+@pytest.mark.parametrize("d,T", [(1, 0.0), (2, 0.7), (3, 0.5)])
 def test_scale_search_with_many_top_weights(d, T):
     """At n = 2^21, beta = 2.2 the degree model's top set (weights that can meet an E_R
     partner) holds tens of thousands of weights, more than the one-block sort takes:
