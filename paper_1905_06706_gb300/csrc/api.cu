@@ -725,6 +725,11 @@ void run_sampler(Problem& P, const Layout& Lo, Scratch& S, cudaStream_t st, Time
     // edge count restored from a copy; the edges it wrote are overwritten later) and
     // the rounds below take over.
     bool done = false;
+    // the list counts of an overflowed first round: the first attempt below would run
+    // the same enumeration again, so it starts from these instead
+    bool have_first = false;
+    unsigned long long first_wc[3] = {0, 0, 0};
+    unsigned int first_ec[2] = {0, 0};
     {
         cfg.ent2_lo = 0;
         cfg.ent2_hi = 0xffffffffu;
@@ -783,6 +788,9 @@ void run_sampler(Problem& P, const Layout& Lo, Scratch& S, cudaStream_t st, Time
             CK(cudaMemcpyAsync(stats, snap, (kNumStats + 3) * sizeof(unsigned long long),
                                cudaMemcpyDeviceToDevice, st));
             tm.used -= 3;  // the rounds below mark these phases again
+            memcpy(first_wc, wc, sizeof(wc));
+            memcpy(first_ec, ec, sizeof(ec));
+            have_first = true;
         }
     }
     for (int attempt = 0; !done; ++attempt) {
@@ -791,18 +799,25 @@ void run_sampler(Problem& P, const Layout& Lo, Scratch& S, cudaStream_t st, Time
         cfg.ent2_hi = hi2;
         cfg.ent1_lo = lo1;
         cfg.ent1_hi = hi1;
-        CK(cudaMemsetAsync(wcount, 0, 3 * sizeof(unsigned long long), st));
-        CK(cudaMemsetAsync(estats, 0, kNumStats * sizeof(unsigned long long), st));
-        DevCfg ecfg = cfg;
-        ecfg.stats = estats;
-        launch_enumerate(ecfg, st);
-        ++passes;
         unsigned long long wc[3], es[kNumStats];
         unsigned int ec[2];
-        CK(cudaMemcpyAsync(wc, wcount, sizeof(wc), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(ec, counters + 6, sizeof(ec), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(es, estats, sizeof(es), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        if (have_first) {  // same entries and capacities as the first round: its counts
+            have_first = false;
+            memcpy(wc, first_wc, sizeof(wc));
+            memcpy(ec, first_ec, sizeof(ec));
+            memset(es, 0, sizeof(es));  // unused: these counts overflow
+        } else {
+            CK(cudaMemsetAsync(wcount, 0, 3 * sizeof(unsigned long long), st));
+            CK(cudaMemsetAsync(estats, 0, kNumStats * sizeof(unsigned long long), st));
+            DevCfg ecfg = cfg;
+            ecfg.stats = estats;
+            launch_enumerate(ecfg, st);
+            ++passes;
+            CK(cudaMemcpyAsync(wc, wcount, sizeof(wc), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(ec, counters + 6, sizeof(ec), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(es, estats, sizeof(es), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+        }
         const uint32_t e2 = std::min<uint32_t>(ec[0], cfg.ent2_cap);
         const uint32_t e1 = std::min<uint32_t>(ec[1], cfg.ent1_cap);
         const uint32_t end2 = std::min(hi2, e2), end1 = std::min(hi1, e1);
