@@ -19,8 +19,11 @@ constexpr size_t kChunk = 16384;
 template <class F>
 void for_chunks(size_t n, bool parallel, F f) {
     const size_t nc = (n + kChunk - 1) / kChunk;
-    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    const size_t nt = parallel ? std::min<size_t>(hw, nc) : 1;
+    size_t nt = 1;
+    if (parallel && nc > 1) {  // the core count is read once (a file read on Linux)
+        static const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        nt = std::min<size_t>(hw, nc);
+    }
     if (nt <= 1) {
         for (size_t c = 0; c < nc; ++c) f(c, c * kChunk, std::min(n, (c + 1) * kChunk));
         return;
