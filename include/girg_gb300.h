@@ -279,7 +279,9 @@ int girg_sorted_order(int64_t n, int32_t d, const uint32_t* d_X, const double* d
  * host builds the type-II bound tables with them; the device uses the same steps):
  * fn 0 ln x, 1 ln(1+x), 2 e^x, 3 x^y, 4 sin(pi x) for x in [0, 1/2], 5 acosh x,
  * 6 the GIRG probability of Eq. 1 at weights (x, y), r = 1/4, W = 1000, c = 1/2,
- * T = 3/4, d = 2.  Returns NaN for an unknown fn.  Diagnostic; no GPU needed. */
+ * T = 3/4, d = 2, 7 the weight layer (Sec. 3.1) of weight x with minimum weight y as the
+ * reduction and key kernels take it (from the bit fields, no division).  Returns NaN for
+ * an unknown fn.  Diagnostic; no GPU needed. */
 double girg_det_eval(int32_t fn, double x, double y);
 
 /* Measured warp-instruction issue rate (the denominator of the pair kernels' issue

@@ -21,6 +21,7 @@
 #include "girg_gb300.h"
 #include "internal.cuh"
 #include "kernels.h"
+#include "layers.cuh"
 #include "solver.h"
 
 using namespace gg;
@@ -1183,6 +1184,7 @@ double girg_det_eval(int32_t fn, double x, double y) {
         case 4: return det_sinpi(x);
         case 5: return det_acosh(x);
         case 6: return girg_p_at(x, y, 0.25, 1000.0, girg_K_of_c(0.5, 2, 0.75), 1.0 / 0.75, 0, 2);
+        case 7: return (double)layer_of_bits(x, y);
         default: return dnan();
     }
 }

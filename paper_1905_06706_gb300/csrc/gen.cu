@@ -9,6 +9,7 @@
 // sums the degree formula of App. B.2 needs.
 #include <atomic>
 #include "internal.cuh"
+#include "layers.cuh"
 #include "kernels.h"
 
 namespace gg {
@@ -111,13 +112,17 @@ __global__ void k_reduce(int64_t n, const double* __restrict__ w, const double* 
         } else {
             add128(lo, hi, mant << sh, mant >> (64 - sh));
         }
-        const int layer = layer_of(wv, w_min);
-        atomicAdd(&s_cnt[layer], 1u);
-        atomicMax(&s_wmax[layer], b);
+        const int layer = layer_of_bits(wv, w_min);
+        // most weights share the lowest layers: one count increment per layer and
+        // warp, and the extremes only when they improve on the block's (a stale read
+        // costs one more atomic, never a wrong result)
+        const unsigned int peers = __match_any_sync(__activemask(), layer);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_cnt[layer], (unsigned)__popc(peers));
+        if (b > s_wmax[layer]) atomicMax(&s_wmax[layer], b);
         if (r) {
             const unsigned long long rb = double_to_bits(r[v]);
-            atomicMin(&s_rmin[layer], rb);
-            atomicMax(&s_rmax[layer], rb);
+            if (rb < s_rmin[layer]) atomicMin(&s_rmin[layer], rb);
+            if (rb > s_rmax[layer]) atomicMax(&s_rmax[layer], rb);
         }
         if (part_s2) a2 += wv * wv;
     }

@@ -9,6 +9,7 @@
 // coalesced).
 #include "internal.cuh"
 #include "kernels.h"
+#include "layers.cuh"
 
 namespace gg {
 
@@ -22,7 +23,7 @@ __global__ void k_keys(int64_t n, int d, const double* __restrict__ w, const uin
                        uint32_t* __restrict__ val, uint32_t* __restrict__ cnt, bool slots) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        const int layer = layer_of(w[v], w_min);
+        const int layer = layer_of_bits(w[v], w_min);
         const int lev = tab.I[layer];
         uint32_t coord[kMaxDim];
         for (int k = 0; k < d; ++k) coord[k] = lev ? (X[(int64_t)k * n + v] >> (32 - lev)) : 0u;
@@ -478,7 +479,7 @@ __global__ void k_gather_girg(int64_t n, int d, const uint32_t* __restrict__ per
         const double wv = w[v];
         ws[p] = wv;
         const float s = exp2f((log2f((float)wv) - (float)log2W_half) * invd + gamma);
-        slayer[p] = (uint8_t)layer_of(wv, w_min);
+        slayer[p] = (uint8_t)layer_of_bits(wv, w_min);
         if (rec) {
             uint32_t x[4] = {0u, 0u, 0u, 0u};
             for (int k = 0; k < d && k < 4; ++k) x[k] = X[(int64_t)k * n + v];
@@ -518,7 +519,7 @@ __global__ void k_gather_hrg(int64_t n, const uint32_t* __restrict__ perm,
         E32[p] = expf(rf);
         einv32[p] = expf(-rf);
         sh32[p] = sinhf(rf);
-        slayer[p] = (uint8_t)layer_of(w[v], 1.0);
+        slayer[p] = (uint8_t)layer_of_bits(w[v], 1.0);
     }
 }
 

@@ -80,6 +80,40 @@ def test_issue_probe_rejects_bad_arguments(lib):
     assert ms.value == -1.0 and wi.value == -1
 
 
+def test_weight_layer_from_bit_fields_matches_oracle(lib):
+    """The kernels take the weight layer of Sec. 3.1 from the bit fields of w and w_min
+    (no division); it equals the oracle's floor(log2) of the rounded quotient at every
+    layer boundary w_min 2^k, one and two ulps on either side, for minimum weights with
+    small and large mantissas, and on random weights, subnormals and extremes (positive
+    finite weights, the generator's domain)."""
+    import math
+    import random
+    import oracle as O
+    rng = random.Random(5)
+    mins = [1.0, 1.37, 1.9999999999999998, 1.0000000000000002, 0.75, 3e-300, 5e-324,
+            2.5e-308, 1e300, 7.0]
+    cases = []
+    for wm in mins:
+        for k in range(-2, 66):
+            if math.frexp(wm)[1] + k > 1024:  # beyond the doubles
+                break
+            b = math.ldexp(wm, k)
+            x = b
+            for _ in range(2):
+                x = math.nextafter(x, 0.0)
+            for _ in range(5):
+                cases.append((x, wm))
+                x = math.nextafter(x, math.inf)
+        for _ in range(200):
+            x = wm * math.exp(rng.uniform(0.0, 45.0))
+            if math.isfinite(x):
+                cases.append((x, wm))
+    cases += [(5e-324, 5e-324), (1e-308, 5e-324), (2e-320, 1e-320), (1e300, 1e290)]
+    for x, wm in cases:
+        got = lib.girg_det_eval(7, x, wm)
+        assert got == O.layer_of(x, wm), (x, wm, got)
+
+
 def test_invalid_hrg_and_points_rejected(lib):
     m = ctypes.c_int64(0)
     for hp in (gg.HrgParams(1000, 0.5, 0.5, 0.0, 10.0, 1, 4, 0, 0),    # alpha must exceed 1/2
