@@ -1561,21 +1561,21 @@ double hrg_radius_on_device(const hrg_params& q, Scratch& S, cudaStream_t st) {
     hrg_unit_y_rule(Y.c, Y.w);
     constexpr int kMaxNodes = 512;  // the t rule has at most 12 intervals of 20 nodes
     double* d_ts = S.get<double>(kMaxNodes);
-    double* d_g = S.get<double>(kMaxNodes);
+    double* d_g = S.get<double>(4 * kMaxNodes);
     std::vector<double> ts, ws, g;
     auto E = [&](double R) {
         double tail = 0.0;
         hrg_t_rule(R, q.T, ts, ws, &tail);
         const int nt = (int)ts.size();
         if (nt > kMaxNodes) throw Status{GIRG_E_INTERNAL};
-        g.assign(nt, 0.0);
+        g.assign(4 * (size_t)nt, 0.0);
         CK(cudaMemcpyAsync(d_ts, ts.data(), nt * sizeof(double), cudaMemcpyHostToDevice, st));
         launch_hrg_dist_cdf(q.alpha, R, Y, d_ts, nt, d_g, st);
         CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(g.data(), d_g, nt * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(g.data(), d_g, 4 * nt * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         double p = 0.0;
-        for (int i = 0; i < nt; ++i) p += ws[i] * g[i];
+        for (int i = 0; i < nt; ++i) p += ws[i] * (((g[4 * i] + g[4 * i + 1]) + g[4 * i + 2]) + g[4 * i + 3]);
         p += tail;
         return (double)(q.n - 1) * p;
     };

@@ -420,15 +420,24 @@ __device__ __forceinline__ double angle_share(double r1, double r2, double t, do
     return 0.63661977236758134308 * asin(sqrt(s));  // 2/pi
 }
 
+// Block (node i, interval q) writes the part of P(dist < ts[i]) from the q-th interval
+// of y1 to g[4 i + q] (0 where the node has fewer intervals); the host adds the four in
+// order.  The interval's y1 nodes, their weights times the radial density and their
+// y2 ranges are formed once in shared memory; the threads then take the (y1, y2)
+// products.
 __global__ void __launch_bounds__(kCdfThreads)
     k_hrg_dist_cdf(double alpha, double R, double cm1, HrgYRule Y,
                    const double* __restrict__ ts, double* __restrict__ g) {
     __shared__ double s_cut[5];
     __shared__ int s_ncut;
+    __shared__ double s_f[kHrgYMax], s_y1[kHrgYMax], s_lo[kHrgYMax], s_top[kHrgYMax],
+        s_tail[kHrgYMax];
     __shared__ double s_part[kCdfThreads / 32];
+    const int q = blockIdx.y;
+    double* const out = g + 4 * (size_t)blockIdx.x + q;
     const double t = ts[blockIdx.x];
     if (!(t > 0.0) || t >= 2.0 * R) {
-        if (threadIdx.x == 0) g[blockIdx.x] = t >= 2.0 * R ? 1.0 : 0.0;
+        if (threadIdx.x == 0) *out = (q == 0 && t >= 2.0 * R) ? 1.0 : 0.0;
         return;
     }
     if (threadIdx.x == 0) {
@@ -437,8 +446,8 @@ __global__ void __launch_bounds__(kCdfThreads)
         c[m++] = 0.0;
         c[m++] = R;
         const double cand[3] = {R - t, 2.0 * R - t, t};
-        for (int q = 0; q < 3; ++q)
-            if (cand[q] > 0.0 && cand[q] < R) c[m++] = cand[q];
+        for (int k = 0; k < 3; ++k)
+            if (cand[k] > 0.0 && cand[k] < R) c[m++] = cand[k];
         for (int i = 1; i < m; ++i) {  // insertion sort of at most five cuts
             const double x = c[i];
             int j = i - 1;
@@ -452,30 +461,48 @@ __global__ void __launch_bounds__(kCdfThreads)
         s_ncut = m;
     }
     __syncthreads();
-    const int m = s_ncut, ny = Y.n, per = ny * ny;
-    const double ct = cosh(t);
-    double acc = 0.0;
-    for (int k = threadIdx.x; k < (m - 1) * per; k += kCdfThreads) {
-        const int q = k / per, a = (k / ny) % ny, b = k % ny;
-        const double a0 = s_cut[q], a1 = s_cut[q + 1];
-        if (!(a1 > a0)) continue;
+    const int ny = Y.n;
+    if (q >= s_ncut - 1 || !(s_cut[q + 1] > s_cut[q])) {  // no such interval (block-uniform)
+        if (threadIdx.x == 0) *out = 0.0;
+        return;
+    }
+    const double a0 = s_cut[q], a1 = s_cut[q + 1];
+    if ((int)threadIdx.x < ny) {  // per y1 node: weight times density, y2 range, closed-form tail
+        const int a = threadIdx.x;
         const double y1 = a0 + (a1 - a0) * Y.c[a];
         const double lo = fmax(0.0, y1 - t), hi = fmin(R, y1 + t);
         const double full = 2.0 * R - t - y1;  // share = 1 for y2 >= full
-        if (!(hi > lo)) continue;
-        if (full <= lo && b != 0) continue;
-        double in = 0.0;
-        if (full <= lo) {
-            in = disk_cdf(alpha, R, cm1, hi) - disk_cdf(alpha, R, cm1, lo);
-        } else {
-            const double top = fmin(hi, full);
-            const double y2 = lo + (top - lo) * Y.c[b];
-            in = (top - lo) * Y.w[b] * disk_dens(alpha, R, cm1, y2) *
-                 angle_share(R - y1, R - y2, t, ct);
-            if (b == 0 && full < hi)
-                in += disk_cdf(alpha, R, cm1, hi) - disk_cdf(alpha, R, cm1, full);
+        double f = 0.0, tail = 0.0, top = lo;
+        if (hi > lo) {
+            f = (a1 - a0) * Y.w[a] * disk_dens(alpha, R, cm1, y1);
+            if (full <= lo) {
+                tail = disk_cdf(alpha, R, cm1, hi) - disk_cdf(alpha, R, cm1, lo);
+            } else {
+                top = fmin(hi, full);
+                if (full < hi) tail = disk_cdf(alpha, R, cm1, hi) - disk_cdf(alpha, R, cm1, full);
+            }
         }
-        acc += (a1 - a0) * Y.w[a] * disk_dens(alpha, R, cm1, y1) * in;
+        s_f[a] = f;
+        s_y1[a] = y1;
+        s_lo[a] = lo;
+        s_top[a] = top;
+        s_tail[a] = tail;
+    }
+    __syncthreads();
+    const double ct = cosh(t);
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < ny * ny; k += kCdfThreads) {
+        const int a = k / ny, b = k % ny;
+        const double f = s_f[a];
+        if (f == 0.0) continue;
+        double in = b == 0 ? s_tail[a] : 0.0;
+        const double lo = s_lo[a], top = s_top[a];
+        if (top > lo) {
+            const double y2 = lo + (top - lo) * Y.c[b];
+            in += (top - lo) * Y.w[b] * disk_dens(alpha, R, cm1, y2) *
+                  angle_share(R - s_y1[a], R - y2, t, ct);
+        }
+        acc += f * in;
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
@@ -483,7 +510,7 @@ __global__ void __launch_bounds__(kCdfThreads)
     if (threadIdx.x == 0) {
         double sum = 0.0;
         for (int i = 0; i < kCdfThreads / 32; ++i) sum += s_part[i];
-        g[blockIdx.x] = sum;
+        *out = sum;
     }
 }
 
@@ -492,7 +519,7 @@ void launch_hrg_dist_cdf(double alpha, double R, const HrgYRule& Y, const double
     if (nt <= 0) return;
     const double cm1 = cosh(alpha * R) - 1.0;
     ++g_launches;
-    k_hrg_dist_cdf<<<nt, kCdfThreads, 0, st>>>(alpha, R, cm1, Y, d_ts, d_g);
+    k_hrg_dist_cdf<<<dim3(nt, 4), kCdfThreads, 0, st>>>(alpha, R, cm1, Y, d_ts, d_g);
 }
 
 void launch_split_weights(int64_t n, const double* w, const double* thr, double T, double* out,

@@ -45,9 +45,10 @@ void launch_hrg_points(int64_t n, double alpha, double R, uint64_t seed, double*
                        uint32_t* X, cudaStream_t st);
 void launch_min_weight(int64_t n, const double* w, unsigned long long* out, cudaStream_t st);
 // P(dist < t) of two random vertices of the hyperbolic disk (radius R, dispersion
-// alpha) at each of the nt nodes d_ts, into d_g: the double integral over the radii
-// with the y rule (nodes a + (b - a) c[k], weights (b - a) w[k] on every smooth
-// interval [a, b]), one block per node, summed in a fixed order.
+// alpha) at each of the nt nodes d_ts: the double integral over the radii with the y
+// rule (nodes a + (b - a) c[k], weights (b - a) w[k] on every smooth interval [a, b]),
+// one block per node and interval, summed in a fixed order.  d_g (4 nt doubles)
+// receives the parts of the node's at most four intervals; their sum in order is the CDF.
 constexpr int kHrgYMax = 32;
 struct HrgYRule {
     double c[kHrgYMax], w[kHrgYMax];
