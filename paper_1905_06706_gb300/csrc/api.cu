@@ -348,8 +348,8 @@ void build_layout(Problem& P, Scratch& A, Scratch& S, cudaStream_t st, Timer& tm
     // the sorted keys and ids end up in two of these four (kept), the other two are free
     uint32_t* key = A.get<uint32_t>(n);
     uint32_t* val = A.get<uint32_t>(n);
-    uint32_t* key2 = A.get<uint32_t>(n);
-    uint32_t* val2 = A.get<uint32_t>(n);
+    uint32_t* key2 = A.get<uint32_t>(2 * (size_t)n);  // one block: the placement's pairs
+    uint32_t* val2 = key2 + n;
     uint32_t* offs = A.get<uint32_t>(total_cells + 1);
     uint32_t* stmp = S.get<uint32_t>(std::max({scan_tmp_words((int64_t)total_cells + 1),
                                                radix_tmp_words(n), place_tmp_words(n)}));
@@ -372,8 +372,9 @@ void build_layout(Problem& P, Scratch& A, Scratch& S, cudaStream_t st, Timer& tm
     uint32_t *skey, *sid;
     if (place) {
         CK(cudaMemsetAsync(stmp, 0, sizeof(uint32_t), st));
-        place_by_counts(key, val, offs, n, key2, val2, key, stmp, st);
-        skey = key2;
+        // the key-id pairs in key2 .. val2; the sorted keys and ids go to val and key
+        place_by_counts(key, val, offs, n, reinterpret_cast<uint2*>(key2), val, key, stmp, st);
+        skey = val;
         sid = key;
     } else {
         radix_sort_pairs(key, val, key2, val2, n, std::max(1, bitlen64(total_cells - 1)), stmp, st,

@@ -102,12 +102,12 @@ void radix_sort_pairs(uint32_t* key, uint32_t* val, uint32_t* key_alt, uint32_t*
 size_t sort_desc_words(int64_t n);
 void sort_f64_desc(const double* in, int64_t n, double* out, uint32_t* words, cudaStream_t st);
 // The same order by placement: key and slot from launch_keys (slots) and the scanned
-// cell histogram offs; writes the sorted keys to skey and the sorted ids to sid (tid:
-// scratch of n words).  tmp >= place_tmp_words(n) words with tmp[0] zeroed.
+// cell histogram offs; writes the sorted keys to skey and the sorted ids to sid (kt:
+// scratch of n key-id pairs; skey and sid may reuse key and slot).  tmp >=
+// place_tmp_words(n) words with tmp[0] zeroed.
 size_t place_tmp_words(int64_t n);
 void place_by_counts(const uint32_t* key, const uint32_t* slot, const uint32_t* offs, int64_t n,
-                     uint32_t* skey, uint32_t* tid, uint32_t* sid, uint32_t* tmp,
-                     cudaStream_t st);
+                     uint2* kt, uint32_t* skey, uint32_t* sid, uint32_t* tmp, cudaStream_t st);
 // Sorted per-vertex arrays.
 // With rec (d <= 4): packed records instead of Xs and sv (see DevCfg::vrec).
 void launch_gather_girg(int64_t n, int d, const uint32_t* perm, const uint32_t* X,

@@ -363,7 +363,9 @@ void sort_f64_desc(const double* in, int64_t n, double* out, uint32_t* words, cu
 // ------------------------------------------------------------------ placement by counts
 // The same order without the radix passes.  With the cell histogram scanned (offs[c] =
 // first sorted position of cell c, offs[C] = n), a vertex goes to offs[key] plus its
-// arrival slot in the cell.  Arrival order is not deterministic, so k_rank then puts
+// arrival slot in the cell (key and id as one 8-byte record: the placement is a random
+// scatter, and one write per vertex touches half the sectors of two).  Arrival order is
+// not deterministic, so k_rank then puts
 // each vertex at offs[key] + (the number of smaller ids in its cell): the order of the
 // stable sort (ties by original id).  Cells with more than kRankMax vertices are copied
 // as they are and sorted afterwards, one block per cell (k_sort_cells).
@@ -371,25 +373,23 @@ constexpr uint32_t kRankMax = 64;
 
 __global__ void k_place(int64_t n, const uint32_t* __restrict__ key,
                         const uint32_t* __restrict__ slot, const uint32_t* __restrict__ offs,
-                        uint32_t* __restrict__ skey, uint32_t* __restrict__ tid) {
+                        uint2* __restrict__ kt) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t c = key[v];
-        const uint32_t pos = offs[c] + slot[v];
-        skey[pos] = c;
-        tid[pos] = (uint32_t)v;
+        kt[offs[c] + slot[v]] = make_uint2(c, (uint32_t)v);  // one scattered 8-byte write
     }
 }
 
-__global__ void k_rank(int64_t n, const uint32_t* __restrict__ skey,
-                       const uint32_t* __restrict__ offs, const uint32_t* __restrict__ tid,
-                       uint32_t* __restrict__ sid, uint32_t* __restrict__ big,
-                       uint32_t* __restrict__ nbig, uint32_t big_cap) {
+__global__ void k_rank(int64_t n, const uint2* __restrict__ kt, const uint32_t* __restrict__ offs,
+                       uint32_t* __restrict__ skey, uint32_t* __restrict__ sid,
+                       uint32_t* __restrict__ big, uint32_t* __restrict__ nbig, uint32_t big_cap) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t c = skey[p];
+        const uint2 e = kt[p];
+        const uint32_t c = e.x, v = e.y;
         const uint32_t a = offs[c], b = offs[c + 1];
-        const uint32_t v = tid[p];
+        skey[p] = c;
         if (b - a > kRankMax) {  // a large cell: copied, sorted by k_sort_cells
             sid[p] = v;
             if ((uint32_t)p == a) {
@@ -399,7 +399,7 @@ __global__ void k_rank(int64_t n, const uint32_t* __restrict__ skey,
             continue;
         }
         uint32_t r = 0;
-        for (uint32_t q = a; q < b; ++q) r += tid[q] < v ? 1u : 0u;
+        for (uint32_t q = a; q < b; ++q) r += kt[q].y < v ? 1u : 0u;
         sid[a + r] = v;
     }
 }
@@ -447,15 +447,14 @@ __global__ void __launch_bounds__(256) k_sort_cells(const uint32_t* __restrict__
 size_t place_tmp_words(int64_t n) { return (size_t)(n / (kRankMax + 1)) + 2; }
 
 void place_by_counts(const uint32_t* key, const uint32_t* slot, const uint32_t* offs, int64_t n,
-                     uint32_t* skey, uint32_t* tid, uint32_t* sid, uint32_t* tmp,
-                     cudaStream_t st) {
+                     uint2* kt, uint32_t* skey, uint32_t* sid, uint32_t* tmp, cudaStream_t st) {
     const uint32_t big_cap = (uint32_t)(place_tmp_words(n) - 1);
     uint32_t* nbig = tmp;  // zeroed by the caller
     uint32_t* big = tmp + 1;
     const int grid = grid_for(n, 256, device_sms() * 16);
     g_launches += 3;
-    k_place<<<grid, 256, 0, st>>>(n, key, slot, offs, skey, tid);
-    k_rank<<<grid, 256, 0, st>>>(n, skey, offs, tid, sid, big, nbig, big_cap);
+    k_place<<<grid, 256, 0, st>>>(n, key, slot, offs, kt);
+    k_rank<<<grid, 256, 0, st>>>(n, kt, offs, skey, sid, big, nbig, big_cap);
     k_sort_cells<<<device_sms() * 2, 256, 0, st>>>(offs, big, nbig, big_cap, sid);
 }
 
