@@ -271,6 +271,68 @@ __device__ bool decide_t1(const DevCfg& cfg, const View& V, uint32_t pu, uint32_
     return girg_t1_exact(cfg, V, pu, pv, D, o.x, o.y);
 }
 
+// Two type-I pairs per lane (GIRG, packed records, single-precision decisions): the
+// four vertex records load together and the two coins' Philox rounds are independent,
+// so a lane carries two dependency chains.  The decisions are those of decide_t1; a
+// coin is computed for every pair (about 93% need one) but counted only when used.
+template <int DIM>
+__device__ __forceinline__ void decide_t1_x2(const DevCfg& cfg, const View& V, const bool (&ok)[2],
+                                             const uint32_t (&pu)[2], const uint32_t (&pv)[2],
+                                             Counters& C, bool (&edge)[2], uint32_t (&ida)[2],
+                                             uint32_t (&idb)[2]) {
+    VRec<DIM> ru[2], rv[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        ru[h] = load_rec<DIM>(V, ok[h] ? pu[h] : 0u);
+        rv[h] = load_rec<DIM>(V, ok[h] ? pv[h] : 0u);
+    }
+    uint32_t D[2];
+    P4 o[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        ida[h] = ru[h].id < rv[h].id ? ru[h].id : rv[h].id;
+        idb[h] = ru[h].id < rv[h].id ? rv[h].id : ru[h].id;
+        D[h] = rec_D<DIM>(ru[h], rv[h]);
+    }
+    if (!cfg.tzero) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) o[h] = philox(ida[h], idb[h], kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        edge[h] = false;
+        if (!ok[h]) continue;
+        if (D[h] == 0) {
+            edge[h] = true;
+            continue;
+        }
+        const float ratio = ru[h].s * rv[h].s * __fdividef(4294967296.0f, __uint2float_rn(D[h]));
+        if (cfg.tzero) {
+            if (ratio > 1.0f + cfg.band_ratio) {
+                edge[h] = true;
+            } else if (!(ratio < 1.0f - cfg.band_ratio)) {
+                ++C.recheck;
+                edge[h] = girg_t1_exact(cfg, V, pu[h], pv[h], D[h], 0u, 0u);
+            }
+            continue;
+        }
+        if (ratio >= 1.0f + cfg.band_ratio) {  // p = 1
+            edge[h] = true;
+            continue;
+        }
+        const float lp = cfg.dT * __log2f(ratio);  // log2 p
+        if (lp < -54.0f - cfg.bandG) continue;     // p < 2^-54 < every U
+        ++C.coins;
+        const float G = lp - log2_uniform32(o[h].x, o[h].y);
+        if (G > cfg.bandG) {
+            edge[h] = true;
+        } else if (!(G < -cfg.bandG)) {
+            ++C.recheck;
+            edge[h] = girg_t1_exact(cfg, V, pu[h], pv[h], D[h], o[h].x, o[h].y);
+        }
+    }
+}
+
 // Type-II acceptance: accept iff U' pbar < p_uv.
 template <int DIM>
 __device__ bool accept_t2(const DevCfg& cfg, const View& V, uint32_t pu, uint32_t pv, uint32_t lo,
@@ -1067,8 +1129,9 @@ __device__ __forceinline__ int warp_last_le32(int v, int f) {
 // Every pair of every type-I item (Algorithm 1: "emit each edge with p_uv").  The
 // pairs of all items form one index space through the exclusive prefix t1_pre;
 // a warp takes kT1Grab consecutive pairs at a time, so all warps end together
-// whatever the item sizes.  A round tests up to 32 consecutive pairs, lane f the
-// pair f0 + f, whose item it finds in a window of 32 consecutive items held one
+// whatever the item sizes.  A round tests up to 64 consecutive pairs, lane f the
+// pairs f0 + f and f0 + 32 + f (two independent chains of loads and Philox rounds
+// per lane), each finding its item in a window of 32 consecutive items held one
 // per lane; the window starts at the item of f0 and the round stops at the end
 // of the window's last item.
 constexpr int kT1Threads = 256;
@@ -1101,44 +1164,67 @@ __device__ __forceinline__ void type1_loop(const DevCfg& cfg, const View& V, War
                 if (q < nit) wit = cfg.t1[q];
                 wk = k;
             }
-            // the round: pairs [f0, fe), at most 32 and inside the window
+            // the round: pairs [f0, fe), at most 64 and inside the window; lane l takes
+            // pairs f0 + l and f0 + 32 + l
             const int wlast = __shfl_sync(0xffffffffu, wend, 31);
-            int fe = f0 + 32;
+            int fe = f0 + 64;
             if (fe > wlast) fe = wlast;
             if (fe > F1) fe = F1;
-            const int f = f0 + lane;
-            const int j = warp_last_le32(wpre, f);
-            const uint32_t a_begin = __shfl_sync(0xffffffffu, wit.a_begin, j);
-            const uint32_t b_begin = __shfl_sync(0xffffffffu, wit.b_begin, j);
-            const uint32_t b_len = __shfl_sync(0xffffffffu, wit.b_len, j);
-            const int pj = __shfl_sync(0xffffffffu, wpre, j);
-            bool edge = false;
-            uint32_t pu = 0, pv = 0, ia_id = 0, ib_id = 0;
-            if (f < fe) {
-                const uint32_t bl = b_len & 0x7fffffffu;
-                const uint32_t rr = (uint32_t)(f - pj);
-                // rr / bl from a float reciprocal (rr < 2^24), corrected to the exact quotient
-                uint32_t ia = __float2uint_rz(__uint2float_rn(rr) * __frcp_rn((float)bl));
-                int ib = (int)rr - (int)(ia * bl);
-                if (ib < 0) {
-                    --ia;
-                    ib += (int)bl;
-                } else if (ib >= (int)bl) {
-                    ++ia;
-                    ib -= (int)bl;
-                }
-                pu = a_begin + ia;
-                pv = b_begin + (uint32_t)ib;
-                if (!((b_len & 0x80000000u) && pv <= pu)) {
-                    ++C.t1pairs;
-                    edge = decide_t1<DIM>(cfg, V, pu, pv, C, &ia_id, &ib_id);
+            bool ok[2];
+            uint32_t pu[2], pv[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int f = f0 + 32 * h + lane;
+                const int j = warp_last_le32(wpre, f);
+                const uint32_t a_begin = __shfl_sync(0xffffffffu, wit.a_begin, j);
+                const uint32_t b_begin = __shfl_sync(0xffffffffu, wit.b_begin, j);
+                const uint32_t b_len = __shfl_sync(0xffffffffu, wit.b_len, j);
+                const int pj = __shfl_sync(0xffffffffu, wpre, j);
+                ok[h] = false;
+                pu[h] = 0;
+                pv[h] = 0;
+                if (f < fe) {
+                    const uint32_t bl = b_len & 0x7fffffffu;
+                    const uint32_t rr = (uint32_t)(f - pj);
+                    // rr / bl from a float reciprocal (rr < 2^24), corrected to the exact quotient
+                    uint32_t ia = __float2uint_rz(__uint2float_rn(rr) * __frcp_rn((float)bl));
+                    int ib = (int)rr - (int)(ia * bl);
+                    if (ib < 0) {
+                        --ia;
+                        ib += (int)bl;
+                    } else if (ib >= (int)bl) {
+                        ++ia;
+                        ib -= (int)bl;
+                    }
+                    pu[h] = a_begin + ia;
+                    pv[h] = b_begin + (uint32_t)ib;
+                    ok[h] = !((b_len & 0x80000000u) && pv[h] <= pu[h]);
+                    if (ok[h]) ++C.t1pairs;
                 }
             }
-            if (edge) {
-                push_edge(cfg, we, ia_id, ib_id);
-                ++t1_edges;
+            bool edge[2] = {false, false};
+            uint32_t ia_id[2] = {0u, 0u}, ib_id[2] = {0u, 0u};
+            if constexpr (DIM >= 1 && DIM <= 4) {
+                if (cfg.model == 0 && cfg.precision == 0 && V.rec) {
+                    decide_t1_x2<DIM>(cfg, V, ok, pu, pv, C, edge, ia_id, ib_id);
+                } else {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        if (ok[h]) edge[h] = decide_t1<DIM>(cfg, V, pu[h], pv[h], C, &ia_id[h], &ib_id[h]);
+                }
+            } else {
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (ok[h]) edge[h] = decide_t1<DIM>(cfg, V, pu[h], pv[h], C, &ia_id[h], &ib_id[h]);
             }
-            flush_edges<true>(cfg, we, kEdgeBuf - 32);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (edge[h]) {
+                    push_edge(cfg, we, ia_id[h], ib_id[h]);
+                    ++t1_edges;
+                }
+            }
+            flush_edges<true>(cfg, we, kEdgeBuf - 64);
             // the next round starts in the first item that ends after fe
             f0 = fe;
             k += (uint32_t)__popc(__ballot_sync(0xffffffffu, wend <= fe));
