@@ -271,35 +271,35 @@ __device__ bool decide_t1(const DevCfg& cfg, const View& V, uint32_t pu, uint32_
     return girg_t1_exact(cfg, V, pu, pv, D, o.x, o.y);
 }
 
-// Two type-I pairs per lane (GIRG, packed records, single-precision decisions): the
-// four vertex records load together and the two coins' Philox rounds are independent,
-// so a lane carries two dependency chains.  The decisions are those of decide_t1; a
+// NP type-I pairs per lane (GIRG, packed records, single-precision decisions): their
+// vertex records load together and the coins' Philox rounds are independent, so a lane
+// carries NP dependency chains.  The decisions are those of decide_t1; a
 // coin is computed for every pair (about 93% need one) but counted only when used.
-template <int DIM>
-__device__ __forceinline__ void decide_t1_x2(const DevCfg& cfg, const View& V, const bool (&ok)[2],
-                                             const uint32_t (&pu)[2], const uint32_t (&pv)[2],
-                                             Counters& C, bool (&edge)[2], uint32_t (&ida)[2],
-                                             uint32_t (&idb)[2]) {
-    VRec<DIM> ru[2], rv[2];
+template <int DIM, int NP>
+__device__ __forceinline__ void decide_t1_xp(const DevCfg& cfg, const View& V, const bool (&ok)[NP],
+                                             const uint32_t (&pu)[NP], const uint32_t (&pv)[NP],
+                                             Counters& C, bool (&edge)[NP], uint32_t (&ida)[NP],
+                                             uint32_t (&idb)[NP]) {
+    VRec<DIM> ru[NP], rv[NP];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < NP; ++h) {
         ru[h] = load_rec<DIM>(V, ok[h] ? pu[h] : 0u);
         rv[h] = load_rec<DIM>(V, ok[h] ? pv[h] : 0u);
     }
-    uint32_t D[2];
-    P4 o[2];
+    uint32_t D[NP];
+    P4 o[NP];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < NP; ++h) {
         ida[h] = ru[h].id < rv[h].id ? ru[h].id : rv[h].id;
         idb[h] = ru[h].id < rv[h].id ? rv[h].id : ru[h].id;
         D[h] = rec_D<DIM>(ru[h], rv[h]);
     }
     if (!cfg.tzero) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) o[h] = philox(ida[h], idb[h], kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
+        for (int h = 0; h < NP; ++h) o[h] = philox(ida[h], idb[h], kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < NP; ++h) {
         edge[h] = false;
         if (!ok[h]) continue;
         if (D[h] == 0) {
@@ -1129,13 +1129,14 @@ __device__ __forceinline__ int warp_last_le32(int v, int f) {
 // Every pair of every type-I item (Algorithm 1: "emit each edge with p_uv").  The
 // pairs of all items form one index space through the exclusive prefix t1_pre;
 // a warp takes kT1Grab consecutive pairs at a time, so all warps end together
-// whatever the item sizes.  A round tests up to 64 consecutive pairs, lane f the
-// pairs f0 + f and f0 + 32 + f (two independent chains of loads and Philox rounds
+// whatever the item sizes.  A round tests up to 32 kT1Pairs consecutive pairs, lane f
+// the pairs f0 + f, f0 + 32 + f, ... (independent chains of loads and Philox rounds
 // per lane), each finding its item in a window of 32 consecutive items held one
 // per lane; the window starts at the item of f0 and the round stops at the end
 // of the window's last item.
 constexpr int kT1Threads = 256;
 constexpr unsigned kT1Grab = 1024;
+constexpr int kT1Pairs = 2;  // pairs per lane and round
 
 template <int DIM>
 __device__ __forceinline__ void type1_loop(const DevCfg& cfg, const View& V, WarpEdges& we,
@@ -1167,13 +1168,13 @@ __device__ __forceinline__ void type1_loop(const DevCfg& cfg, const View& V, War
             // the round: pairs [f0, fe), at most 64 and inside the window; lane l takes
             // pairs f0 + l and f0 + 32 + l
             const int wlast = __shfl_sync(0xffffffffu, wend, 31);
-            int fe = f0 + 64;
+            int fe = f0 + 32 * kT1Pairs;
             if (fe > wlast) fe = wlast;
             if (fe > F1) fe = F1;
-            bool ok[2];
-            uint32_t pu[2], pv[2];
+            bool ok[kT1Pairs];
+            uint32_t pu[kT1Pairs], pv[kT1Pairs];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < kT1Pairs; ++h) {
                 const int f = f0 + 32 * h + lane;
                 const int j = warp_last_le32(wpre, f);
                 const uint32_t a_begin = __shfl_sync(0xffffffffu, wit.a_begin, j);
@@ -1202,29 +1203,34 @@ __device__ __forceinline__ void type1_loop(const DevCfg& cfg, const View& V, War
                     if (ok[h]) ++C.t1pairs;
                 }
             }
-            bool edge[2] = {false, false};
-            uint32_t ia_id[2] = {0u, 0u}, ib_id[2] = {0u, 0u};
+            bool edge[kT1Pairs];
+            uint32_t ia_id[kT1Pairs], ib_id[kT1Pairs];
+#pragma unroll
+            for (int h = 0; h < kT1Pairs; ++h) {
+                edge[h] = false;
+                ia_id[h] = ib_id[h] = 0u;
+            }
             if constexpr (DIM >= 1 && DIM <= 4) {
                 if (cfg.model == 0 && cfg.precision == 0 && V.rec) {
-                    decide_t1_x2<DIM>(cfg, V, ok, pu, pv, C, edge, ia_id, ib_id);
+                    decide_t1_xp<DIM, kT1Pairs>(cfg, V, ok, pu, pv, C, edge, ia_id, ib_id);
                 } else {
 #pragma unroll
-                    for (int h = 0; h < 2; ++h)
+                    for (int h = 0; h < kT1Pairs; ++h)
                         if (ok[h]) edge[h] = decide_t1<DIM>(cfg, V, pu[h], pv[h], C, &ia_id[h], &ib_id[h]);
                 }
             } else {
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
+                for (int h = 0; h < kT1Pairs; ++h)
                     if (ok[h]) edge[h] = decide_t1<DIM>(cfg, V, pu[h], pv[h], C, &ia_id[h], &ib_id[h]);
             }
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < kT1Pairs; ++h) {
                 if (edge[h]) {
                     push_edge(cfg, we, ia_id[h], ib_id[h]);
                     ++t1_edges;
                 }
             }
-            flush_edges<true>(cfg, we, kEdgeBuf - 64);
+            flush_edges<true>(cfg, we, kEdgeBuf - 32 * kT1Pairs);
             // the next round starts in the first item that ends after fe
             f0 = fe;
             k += (uint32_t)__popc(__ballot_sync(0xffffffffu, wend <= fe));
