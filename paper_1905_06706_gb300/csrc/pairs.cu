@@ -333,6 +333,66 @@ __device__ __forceinline__ void decide_t1_xp(const DevCfg& cfg, const View& V, c
     }
 }
 
+// The same for HRG pairs (single-precision decisions): the angles, radial terms and ids
+// of all NP pairs load together and their coins' Philox rounds interleave; the
+// decisions are those of decide_t1.
+template <int NP>
+__device__ __forceinline__ void decide_t1_hrg_xp(const DevCfg& cfg, const View& V,
+                                                 const bool (&ok)[NP], const uint32_t (&pu)[NP],
+                                                 const uint32_t (&pv)[NP], Counters& C,
+                                                 bool (&edge)[NP], uint32_t (&ida)[NP],
+                                                 uint32_t (&idb)[NP]) {
+    uint32_t D[NP];
+    float cd[NP];
+    P4 o[NP];
+#pragma unroll
+    for (int h = 0; h < NP; ++h) {
+        const uint32_t u = ok[h] ? pu[h] : 0u, v = ok[h] ? pv[h] : 0u;
+        const uint32_t iu = vid(V, u), iv = vid(V, v);
+        ida[h] = iu < iv ? iu : iv;
+        idb[h] = iu < iv ? iv : iu;
+        D[h] = circ_diff(V.X[u], V.X[v]);
+        cd[h] = hrg_coshd32(V, u, v, D[h]);
+    }
+    if (!cfg.tzero) {
+#pragma unroll
+        for (int h = 0; h < NP; ++h) o[h] = philox(ida[h], idb[h], kTagPair, 0u, cfg.seed_lo, cfg.seed_hi);
+    }
+#pragma unroll
+    for (int h = 0; h < NP; ++h) {
+        edge[h] = false;
+        if (!ok[h]) continue;
+        if (cfg.tzero) {
+            if (cd[h] < cfg.coshR32 * (1.0f - 0x1p-16f)) {
+                edge[h] = true;
+            } else if (!(cd[h] > cfg.coshR32 * (1.0f + 0x1p-16f))) {
+                ++C.recheck;
+                edge[h] = hrg_t1_exact(cfg, V, pu[h], pv[h], D[h], 0u, 0u);
+            }
+            continue;
+        }
+        ++C.coins;
+        // distance filter (Sec. 4.3): the bin of U brackets the threshold on cosh d;
+        // bin m = floor(U (K - 1)) exactly, from the 53-bit integer of U
+        const unsigned long long odd =
+            2ull * ((((unsigned long long)o[h].y << 32) | o[h].x) >> 12) + 1ull;
+        const int m = (int)((odd * (unsigned long long)(cfg.filt_k - 1)) >> 53);
+        if (cd[h] * (1.0f + 0x1p-16f) < cfg.filt_lo[m + 1]) {
+            edge[h] = true;
+            continue;
+        }
+        if (cd[h] * (1.0f - 0x1p-16f) >= cfg.filt_hi[m]) continue;
+        const float p32 = hrg_p32(cfg, cd[h]);
+        const float u32 = uniform32(o[h].x, o[h].y);
+        if (u32 < p32 * (1.0f - cfg.bandG)) {
+            edge[h] = true;
+        } else if (!(u32 > p32 * (1.0f + cfg.bandG))) {
+            ++C.recheck;
+            edge[h] = hrg_t1_exact(cfg, V, pu[h], pv[h], D[h], o[h].x, o[h].y);
+        }
+    }
+}
+
 // Type-II acceptance: accept iff U' pbar < p_uv.
 template <int DIM>
 __device__ bool accept_t2(const DevCfg& cfg, const View& V, uint32_t pu, uint32_t pv, uint32_t lo,
@@ -1138,7 +1198,9 @@ constexpr int kT1Threads = 256;
 constexpr unsigned kT1Grab = 1024;
 constexpr int kT1Pairs = 2;  // pairs per lane and round
 
-template <int DIM>
+// HRG: the HRG instantiation (d = 1; its own registers, so that the GIRG d = 1 kernel
+// keeps the budget of its own decisions).
+template <int DIM, bool HRG = false>
 __device__ __forceinline__ void type1_loop(const DevCfg& cfg, const View& V, WarpEdges& we,
                                            Counters& C) {
     const int lane = threadIdx.x & 31;
@@ -1210,7 +1272,15 @@ __device__ __forceinline__ void type1_loop(const DevCfg& cfg, const View& V, War
                 edge[h] = false;
                 ia_id[h] = ib_id[h] = 0u;
             }
-            if constexpr (DIM >= 1 && DIM <= 4) {
+            if constexpr (HRG) {
+                if (cfg.precision == 0) {
+                    decide_t1_hrg_xp<kT1Pairs>(cfg, V, ok, pu, pv, C, edge, ia_id, ib_id);
+                } else {
+#pragma unroll
+                    for (int h = 0; h < kT1Pairs; ++h)
+                        if (ok[h]) edge[h] = decide_t1<DIM>(cfg, V, pu[h], pv[h], C, &ia_id[h], &ib_id[h]);
+                }
+            } else if constexpr (DIM >= 1 && DIM <= 4) {
                 if (cfg.model == 0 && cfg.precision == 0 && V.rec) {
                     decide_t1_xp<DIM, kT1Pairs>(cfg, V, ok, pu, pv, C, edge, ia_id, ib_id);
                 } else {
@@ -1243,7 +1313,7 @@ __device__ __forceinline__ void type1_loop(const DevCfg& cfg, const View& V, War
     if (lane == 0 && te) atomicAdd(&cfg.stats[kStatT1Edges], te);
 }
 
-template <int DIM>
+template <int DIM, bool HRG = false>
 __global__ void __launch_bounds__(kT1Threads, 4) k_type1(DevCfg cfg) {
     if (cfg.lists_ok && *cfg.lists_ok == 0u) return;  // a list overflowed: the round is redone
     __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
@@ -1253,7 +1323,7 @@ __global__ void __launch_bounds__(kT1Threads, 4) k_type1(DevCfg cfg) {
     __syncwarp();
     WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
     Counters C;
-    type1_loop<DIM>(cfg, sorted_view(cfg), we, C);
+    type1_loop<DIM, HRG>(cfg, sorted_view(cfg), we, C);
     flush_counters(cfg, C);
 }
 
@@ -1528,6 +1598,11 @@ static unsigned persistent_grid(K kernel, int threads) {
 
 void launch_type1(const DevCfg& cfg, cudaStream_t st) {
     ++g_launches;
+    if (cfg.model == 1) {  // HRG (d = 1)
+        static const unsigned grid = persistent_grid(k_type1<1, true>, kT1Threads);
+        k_type1<1, true><<<grid, kT1Threads, 0, st>>>(cfg);
+        return;
+    }
     switch (cfg.d) {
 #define GG_T1(D)                                                                     \
     {                                                                                \
