@@ -447,11 +447,16 @@ __device__ __forceinline__ int draw_jump_fast(const DevCfg& cfg, const TwoFast& 
     return r;
 }
 
-template <int DIM>
+template <int DIM, bool HRG = false>
 __device__ __forceinline__ bool accept_t2_fast(const DevCfg& cfg, const View& V, uint32_t pu,
                                                uint32_t pv, uint32_t lo, uint32_t hi,
                                                const TwoFast& e, Counters& C, uint32_t* idu,
                                                uint32_t* idv) {
+    if constexpr (HRG) {  // the HRG instantiation (d = 1)
+        *idu = vid(V, pu);
+        *idv = vid(V, pv);
+        return accept_t2<DIM>(cfg, V, pu, pv, lo, hi, cfg.tii[e.tii], C);
+    }
     if constexpr (DIM >= 1 && DIM <= 4) {
         if (cfg.model == 0) {  // GIRG from the two vertex records
             const VRec<DIM> ru = load_rec<DIM>(V, pu), rv = load_rec<DIM>(V, pv);
@@ -473,7 +478,6 @@ __device__ __forceinline__ bool accept_t2_fast(const DevCfg& cfg, const View& V,
     }
     *idu = vid(V, pu);
     *idv = vid(V, pv);
-    if ((DIM == 1 || DIM == 0) && cfg.model == 1) return accept_t2<DIM>(cfg, V, pu, pv, lo, hi, cfg.tii[e.tii], C);
     const uint32_t D = torus_D<DIM>(cfg.d, V, pu, pv);
     if (cfg.precision == 1) return t2_exact(cfg, V, pu, pv, D, lo, hi, cfg.tii[e.tii].pbar);
     if (D == 0) return true;
@@ -1342,7 +1346,7 @@ __global__ void __launch_bounds__(kT1Threads, 4) k_type1(DevCfg cfg) {
 constexpr int kT2Threads = 256;
 constexpr int kT2RefillMin = 8;  // refill idle lanes once this many are idle
 
-template <int DIM>
+template <int DIM, bool HRG = false>
 __device__ __forceinline__ void type2_loop(const DevCfg& cfg, const View& V, WarpEdges& we,
                                            Counters& C) {
     const int lane = threadIdx.x & 31;
@@ -1481,7 +1485,7 @@ __device__ __forceinline__ void type2_loop(const DevCfg& cfg, const View& V, War
                 }
                 pu = st.a_begin + ia;
                 pv = sg.b_begin + (ib - sg.pre);
-                edge = accept_t2_fast<DIM>(cfg, V, pu, pv, o.z, o.w, e, C, &idu, &idv);
+                edge = accept_t2_fast<DIM, HRG>(cfg, V, pu, pv, o.z, o.w, e, C, &idu, &idv);
             }
         }
         if (edge) push_edge(cfg, we, idu, idv);
@@ -1491,7 +1495,7 @@ __device__ __forceinline__ void type2_loop(const DevCfg& cfg, const View& V, War
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cfg.stats[kStatT2Chunks], total);
 }
 
-template <int DIM>
+template <int DIM, bool HRG = false>
 __global__ void __launch_bounds__(kT2Threads, 4) k_type2(DevCfg cfg) {
     if (cfg.lists_ok && *cfg.lists_ok == 0u) return;  // a list overflowed: the round is redone
     __shared__ uint32_t s_ea[kWarps][kEdgeBuf], s_eb[kWarps][kEdgeBuf];
@@ -1501,7 +1505,7 @@ __global__ void __launch_bounds__(kT2Threads, 4) k_type2(DevCfg cfg) {
     __syncwarp();
     WarpEdges we{s_ea[warp], s_eb[warp], &s_en[warp]};
     Counters C;
-    type2_loop<DIM>(cfg, sorted_view(cfg), we, C);
+    type2_loop<DIM, HRG>(cfg, sorted_view(cfg), we, C);
     flush_counters(cfg, C);
 }
 
@@ -1621,6 +1625,11 @@ void launch_type1(const DevCfg& cfg, cudaStream_t st) {
 
 void launch_type2(const DevCfg& cfg, cudaStream_t st) {
     ++g_launches;
+    if (cfg.model == 1) {  // HRG (d = 1)
+        static const unsigned grid = persistent_grid(k_type2<1, true>, kT2Threads);
+        k_type2<1, true><<<grid, kT2Threads, 0, st>>>(cfg);
+        return;
+    }
     switch (cfg.d) {
 #define GG_T2(D)                                                                     \
     {                                                                                \
