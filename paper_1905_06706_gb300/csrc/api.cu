@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <exception>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -961,6 +962,9 @@ int guarded(F&& f) {
     } catch (const Status& s) {
         return s.code;
     } catch (const std::bad_alloc&) {
+        return GIRG_E_INTERNAL;
+    } catch (const std::exception& e) {  // e.g. a host thread that could not start
+        fprintf(stderr, "girg_gb300: %s\n", e.what());
         return GIRG_E_INTERNAL;
     }
 }

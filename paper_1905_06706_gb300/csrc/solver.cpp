@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <system_error>
 #include <thread>
 
 namespace gg {
@@ -28,12 +29,19 @@ void for_chunks(size_t n, bool parallel, F f) {
         for (size_t c = 0; c < nc; ++c) f(c, c * kChunk, std::min(n, (c + 1) * kChunk));
         return;
     }
+    auto run = [&](size_t t) {
+        for (size_t c = t; c < nc; c += nt) f(c, c * kChunk, std::min(n, (c + 1) * kChunk));
+    };
     std::vector<std::thread> pool;
-    for (size_t t = 1; t < nt; ++t)
-        pool.emplace_back([&, t] {
-            for (size_t c = t; c < nc; c += nt) f(c, c * kChunk, std::min(n, (c + 1) * kChunk));
-        });
-    for (size_t c = 0; c < nc; c += nt) f(c, c * kChunk, std::min(n, (c + 1) * kChunk));
+    std::vector<size_t> mine = {0};  // the caller's share, plus that of any thread not started
+    for (size_t t = 1; t < nt; ++t) {
+        try {
+            pool.emplace_back(run, t);
+        } catch (const std::system_error&) {
+            mine.push_back(t);
+        }
+    }
+    for (size_t t : mine) run(t);
     for (auto& th : pool) th.join();
 }
 
@@ -399,11 +407,19 @@ double hrg_expected_degree(int64_t n, double alpha, double T, double R) {
     std::vector<double> g(ts.size(), 0.0);
     const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
     const size_t nthreads = std::min<size_t>(hw, ts.size());
+    auto run = [&](size_t th) {
+        for (size_t i = th; i < ts.size(); i += nthreads) g[i] = dist_cdf(D, ts[i]);
+    };
     std::vector<std::thread> pool;
-    for (size_t th = 0; th < nthreads; ++th)
-        pool.emplace_back([&, th] {
-            for (size_t i = th; i < ts.size(); i += nthreads) g[i] = dist_cdf(D, ts[i]);
-        });
+    std::vector<size_t> mine;  // shares of threads that could not start: this thread's
+    for (size_t th = 0; th < nthreads; ++th) {
+        try {
+            pool.emplace_back(run, th);
+        } catch (const std::system_error&) {
+            mine.push_back(th);
+        }
+    }
+    for (size_t th : mine) run(th);
     for (auto& t : pool) t.join();
     double p = 0.0;
     for (size_t i = 0; i < ts.size(); ++i) p += ws[i] * g[i];
