@@ -230,6 +230,7 @@ struct Layout {
     uint8_t* slayer = nullptr;
     float *sv = nullptr, *E32 = nullptr, *einv32 = nullptr, *sh32 = nullptr;
     uint4* vrec = nullptr;
+    uint4* hrec = nullptr;
     TwoEntry* tii = nullptr;
     RowClass* d_classes = nullptr;
     uint8_t* jlist = nullptr;
@@ -397,7 +398,7 @@ void build_layout(Problem& P, Scratch& A, Scratch& S, cudaStream_t st, Timer& tm
     double* ws = A.get<double>(n);
     uint8_t* slayer = A.get<uint8_t>(n);
     float *sv = nullptr, *E32 = nullptr, *einv32 = nullptr, *sh32 = nullptr;
-    uint4* vrec = nullptr;
+    uint4 *vrec = nullptr, *hrec = nullptr;
     float gamma = 0.0f;
     const double log2W_half = girg ? 0.5 * std::log2(P.W) : 0.0;
     if (girg) {
@@ -409,10 +410,8 @@ void build_layout(Problem& P, Scratch& A, Scratch& S, cudaStream_t st, Timer& tm
         launch_gather_girg(n, d, sid, P.X, P.w, P.w_min, log2W_half, gamma, (float)(1.0 / d), Xs,
                            ws, sv, slayer, vrec, st);
     } else {
-        E32 = A.get<float>(n);
-        einv32 = A.get<float>(n);
-        sh32 = A.get<float>(n);
-        launch_gather_hrg(n, sid, P.X, P.r, P.w, Xs, ws, E32, einv32, sh32, slayer, st);
+        hrec = A.get<uint4>(n);  // angle, e^r, e^-r, sinh r of each sorted vertex
+        launch_gather_hrg(n, sid, P.X, P.r, P.w, Xs, ws, E32, einv32, sh32, slayer, hrec, st);
     }
     tm.mark();  // sort done
     // the host tables of the sampler, built while the sort runs on the device
@@ -547,6 +546,7 @@ void build_layout(Problem& P, Scratch& A, Scratch& S, cudaStream_t st, Timer& tm
     Lo.einv32 = einv32;
     Lo.sh32 = sh32;
     Lo.vrec = vrec;
+    Lo.hrec = hrec;
     Lo.tii = d_tii;
     Lo.d_classes = d_classes;
     Lo.jlist = d_jlist;
@@ -678,6 +678,7 @@ void run_sampler(Problem& P, const Layout& Lo, Scratch& S, cudaStream_t st, Time
     cfg.E32 = E32;
     cfg.einv32 = einv32;
     cfg.sh32 = sh32;
+    cfg.hrec = Lo.hrec;
     cfg.vrec = vrec;
     cfg.filt_lo = d_flo;
     cfg.filt_hi = d_fhi;

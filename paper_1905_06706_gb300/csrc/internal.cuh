@@ -91,9 +91,10 @@ struct DevCfg {
     const uint32_t* ids;  // sorted original ids
     const uint32_t* skey; // sorted keys (global cell index at the insertion level)
     const uint8_t* slayer;
-    const float* E32;     // HRG e^r, e^-r, sinh r (sorted)
+    const float* E32;     // HRG e^r, e^-r, sinh r (sorted; null when hrec holds them)
     const float* einv32;
     const float* sh32;
+    const uint4* hrec;    // HRG packed records {angle, e^r, e^-r, sinh r} (FP32 bits, sorted)
     // packed sorted GIRG records for d <= 4 (null otherwise; then Xs and sv): d <= 2 one
     // uint4 {x0, x1, scale bits, id} per vertex, d = 3, 4 two {x0, x1, x2, x3},
     // {scale bits, id, 0, 0}

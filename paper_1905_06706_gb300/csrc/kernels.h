@@ -116,7 +116,7 @@ void launch_gather_girg(int64_t n, int d, const uint32_t* perm, const uint32_t* 
                         uint4* rec, cudaStream_t st);
 void launch_gather_hrg(int64_t n, const uint32_t* perm, const uint32_t* X, const double* r,
                        const double* w, uint32_t* Xs, double* rs, float* E32, float* einv32,
-                       float* sh32, uint8_t* slayer, cudaStream_t st);
+                       float* sh32, uint8_t* slayer, uint4* hrec, cudaStream_t st);
 
 // Pair sampling.
 void launch_rows(const DevCfg& cfg, cudaStream_t st);

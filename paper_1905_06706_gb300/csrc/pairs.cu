@@ -38,10 +38,26 @@ struct View {  // per-vertex arrays indexed by position
     const float* sh32;
     int64_t n;
     const uint4* rec;     // packed GIRG records (d <= 4), or nullptr: the arrays above
+    const uint4* hrec;    // packed HRG records, or nullptr: X, E32, einv32, sh32
 };
 
 __device__ __forceinline__ View sorted_view(const DevCfg& cfg) {
-    return View{cfg.Xs, cfg.sv, cfg.ws, cfg.ids, cfg.E32, cfg.einv32, cfg.sh32, cfg.n, cfg.vrec};
+    return View{cfg.Xs, cfg.sv, cfg.ws, cfg.ids, cfg.E32, cfg.einv32, cfg.sh32, cfg.n, cfg.vrec, cfg.hrec};
+}
+
+// What a single-precision HRG decision reads of one vertex: its angle, e^r, e^-r and
+// sinh r, from one 16-byte record when the view has them.
+struct HRec {
+    uint32_t X;
+    float E, ei, sh;
+};
+
+__device__ __forceinline__ HRec load_hrec(const View& V, uint32_t p) {
+    if (V.hrec) {
+        const uint4 a = __ldg(V.hrec + p);
+        return HRec{a.x, __uint_as_float(a.y), __uint_as_float(a.z), __uint_as_float(a.w)};
+    }
+    return HRec{V.X[p], V.E32[p], V.einv32[p], V.sh32[p]};
 }
 
 __device__ __forceinline__ uint32_t vid(const View& V, uint32_t p) { return V.ids ? V.ids[p] : p; }
@@ -149,10 +165,15 @@ __device__ __noinline__ bool t2_exact(const DevCfg& cfg, const View& V, uint32_t
     return DMUL(uniform53(lo, hi), pbar) < p;
 }
 
-__device__ __forceinline__ float hrg_coshd32(const View& V, uint32_t pu, uint32_t pv, uint32_t D) {
+// cosh d of two HRG vertices in single precision from their records (D: angle gap).
+__device__ __forceinline__ float hrg_coshd32_rec(const HRec& u, const HRec& v, uint32_t D) {
     const float s = sinpif(__uint2float_rn(D) * 0x1p-32f);
-    const float ch = 0.5f * (V.E32[pu] * V.einv32[pv] + V.E32[pv] * V.einv32[pu]);
-    return ch + 2.0f * V.sh32[pu] * V.sh32[pv] * (s * s);
+    const float ch = 0.5f * (u.E * v.ei + v.E * u.ei);
+    return ch + 2.0f * u.sh * v.sh * (s * s);
+}
+
+__device__ __forceinline__ float hrg_coshd32(const View& V, uint32_t pu, uint32_t pv, uint32_t D) {
+    return hrg_coshd32_rec(load_hrec(V, pu), load_hrec(V, pv), D);
 }
 
 __device__ __forceinline__ float hrg_p32(const DevCfg& cfg, float cd) {
@@ -351,8 +372,9 @@ __device__ __forceinline__ void decide_t1_hrg_xp(const DevCfg& cfg, const View& 
         const uint32_t iu = vid(V, u), iv = vid(V, v);
         ida[h] = iu < iv ? iu : iv;
         idb[h] = iu < iv ? iv : iu;
-        D[h] = circ_diff(V.X[u], V.X[v]);
-        cd[h] = hrg_coshd32(V, u, v, D[h]);
+        const HRec ru = load_hrec(V, u), rv = load_hrec(V, v);
+        D[h] = circ_diff(ru.X, rv.X);
+        cd[h] = hrg_coshd32_rec(ru, rv, D[h]);
     }
     if (!cfg.tzero) {
 #pragma unroll
@@ -398,9 +420,10 @@ template <int DIM>
 __device__ bool accept_t2(const DevCfg& cfg, const View& V, uint32_t pu, uint32_t pv, uint32_t lo,
                           uint32_t hi, const TwoEntry& e, Counters& C) {
     if ((DIM == 1 || DIM == 0) && cfg.model == 1) {
-        const uint32_t D = circ_diff(V.X[pu], V.X[pv]);
+        const HRec ru = load_hrec(V, pu), rv = load_hrec(V, pv);
+        const uint32_t D = circ_diff(ru.X, rv.X);
         if (cfg.precision == 1) return t2_exact(cfg, V, pu, pv, D, lo, hi, e.pbar);
-        const float p32 = hrg_p32(cfg, hrg_coshd32(V, pu, pv, D));
+        const float p32 = hrg_p32(cfg, hrg_coshd32_rec(ru, rv, D));
         const float up = uniform32(lo, hi) * exp2f(e.log2pbar);
         if (up < p32 * (1.0f - cfg.bandG)) return true;
         if (up > p32 * (1.0f + cfg.bandG)) return false;

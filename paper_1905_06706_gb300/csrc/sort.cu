@@ -507,7 +507,7 @@ __global__ void k_gather_hrg(int64_t n, const uint32_t* __restrict__ perm,
                              const double* __restrict__ w, uint32_t* __restrict__ Xs,
                              double* __restrict__ rs, float* __restrict__ E32,
                              float* __restrict__ einv32, float* __restrict__ sh32,
-                             uint8_t* __restrict__ slayer) {
+                             uint8_t* __restrict__ slayer, uint4* __restrict__ hrec) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t v = perm[p];
@@ -515,9 +515,14 @@ __global__ void k_gather_hrg(int64_t n, const uint32_t* __restrict__ perm,
         const double rv = r[v];
         rs[p] = rv;
         const float rf = (float)rv;
-        E32[p] = expf(rf);
-        einv32[p] = expf(-rf);
-        sh32[p] = sinhf(rf);
+        const float E = expf(rf), ei = expf(-rf), sh = sinhf(rf);
+        if (hrec) {
+            hrec[p] = make_uint4(X[v], __float_as_uint(E), __float_as_uint(ei), __float_as_uint(sh));
+        } else {
+            E32[p] = E;
+            einv32[p] = ei;
+            sh32[p] = sh;
+        }
         slayer[p] = (uint8_t)layer_of_bits(w[v], 1.0);
     }
 }
@@ -549,10 +554,10 @@ void launch_scale(int64_t n, const double* w, double log2W_half, float gamma, fl
 
 void launch_gather_hrg(int64_t n, const uint32_t* perm, const uint32_t* X, const double* r,
                        const double* w, uint32_t* Xs, double* rs, float* E32, float* einv32,
-                       float* sh32, uint8_t* slayer, cudaStream_t st) {
+                       float* sh32, uint8_t* slayer, uint4* hrec, cudaStream_t st) {
     ++g_launches;
     k_gather_hrg<<<grid_for(n, 256, device_sms() * 16), 256, 0, st>>>(n, perm, X, r, w, Xs, rs, E32,
-                                                             einv32, sh32, slayer);
+                                                             einv32, sh32, slayer, hrec);
 }
 
 }  // namespace gg
