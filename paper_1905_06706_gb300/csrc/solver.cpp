@@ -435,15 +435,37 @@ double hrg_radius_for_degree(int64_t n, double alpha, double T, double target) {
 double hrg_radius_for_degree(int64_t n, double alpha, double T, double target,
                              const std::function<double(double)>& E) {
     // start from the large-R limit E ~ K n e^(-R/2), K = 8 alpha^2 / (pi (2 alpha - 1)^2)
-    // times pi T / sin(pi T); ln E is nearly linear in R, so regula falsi (Illinois)
-    // on ln E(R) - ln target converges in a few steps
+    // times pi T / sin(pi T); ln E is nearly linear in R, so the secant method (and as a
+    // fallback regula falsi, Illinois) on ln E(R) - ln target converges in a few steps
     double K = 8.0 * alpha * alpha / (kPi * (2.0 * alpha - 1.0) * (2.0 * alpha - 1.0));
     if (T > 0.0) K *= kPi * T / std::sin(kPi * T);
     double r0 = 2.0 * std::log(K * (double)n / target);
     if (!(r0 > 1e-3 && r0 < 700.0)) r0 = std::min(700.0, std::max(1.0, 2.0 * std::log((double)n)));
     auto F = [&](double R) { return std::log(E(R)) - std::log(target); };
-    double lo = r0, hi = r0, flo = F(r0), fhi = flo;
-    if (flo == 0.0) return r0;
+    const double f_start = F(r0);
+    if (f_start == 0.0) return r0;
+    // secant steps from r0 and the point the slope -1/2 of ln E predicts (three to five
+    // evaluations to 1e-13); a step that leaves (1e-3, 700) or stalls falls back to the
+    // bracketing search below, which starts again from r0
+    {
+        double a = r0, fa = f_start, b = r0 + 2.0 * f_start;
+        if (b > 1e-3 && b < 700.0) {
+            double fb = F(b);
+            for (int it = 0; it < 30 && std::isfinite(fb); ++it) {
+                if (std::fabs(fb) <= 1e-14) return b;
+                if (fb == fa) break;
+                double c = b - fb * (b - a) / (fb - fa);
+                c = std::min(b + 4.0, std::max(b - 4.0, c));
+                if (!(c > 1e-3 && c < 700.0)) break;
+                if (std::fabs(c - b) <= 1e-13 * b) return c;
+                a = b;
+                fa = fb;
+                b = c;
+                fb = F(b);
+            }
+        }
+    }
+    double lo = r0, hi = r0, flo = f_start, fhi = flo;
     // F decreases in R: find lo with F >= 0 and hi with F < 0
     for (double step = 0.5; flo < 0.0; step *= 2.0) {
         hi = lo;
