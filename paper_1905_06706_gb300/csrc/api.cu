@@ -615,13 +615,18 @@ void run_sampler(Problem& P, const Layout& Lo, Scratch& S, cudaStream_t st, Time
         c = c < 16 ? 16 : c;
         return c > mx ? mx : c;
     };
-    uint64_t t1_cap = clamp_cap((uint64_t)n * (1 + (uint64_t)(0.75 * n3)) + 65536, 1ull << 30);
+    // estimated list sizes at or beyond the maxima of one round: the first round would
+    // overflow, so it only counts (the rounds below are planned from its counts)
+    const uint64_t est_t1 = (uint64_t)n * (1 + (uint64_t)(0.75 * n3)) + 65536;
+    uint64_t t1_cap = clamp_cap(est_t1, 1ull << 30);
     uint64_t stream_cap =
         tzero ? 1024 : clamp_cap((uint64_t)n * (2 + 2 * (uint64_t)d) + 65536, 1ull << 28);
     // partner segments per vertex measured at n = 10^6, beta = 2.2, T = 0.7: about 4.3,
     // 19, 81 and 325 for d = 1..4 (they grow like 6^d); sized with headroom
     const uint64_t seg_per_v = d == 1 ? 8 : d == 2 ? 28 : d == 3 ? 112 : d == 4 ? 448 : 4 * (uint64_t)n6;
-    uint64_t seg_cap = tzero ? 1024 : clamp_cap((uint64_t)n * seg_per_v + 65536, 1ull << 31);
+    const uint64_t est_seg = (uint64_t)n * seg_per_v + 65536;
+    uint64_t seg_cap = tzero ? 1024 : clamp_cap(est_seg, 1ull << 31);
+    const bool count_first = list_scale == 1.0 && (est_t1 > (1ull << 30) || (!tzero && est_seg > (1ull << 31)));
     T1Item* t1 = S.get<T1Item>(t1_cap);
     uint32_t* t1_pairs = S.get<uint32_t>(t1_cap + 1);
     Stream* streams = S.get<Stream>(stream_cap);
@@ -734,7 +739,29 @@ void run_sampler(Problem& P, const Layout& Lo, Scratch& S, cudaStream_t st, Time
     bool have_first = false;
     unsigned long long first_wc[3] = {0, 0, 0};
     unsigned int first_ec[2] = {0, 0};
-    {
+    if (count_first) {  // entries, lists and statistics counted, nothing written
+        cfg.ent2_lo = 0;
+        cfg.ent2_hi = 0xffffffffu;
+        cfg.ent1_lo = 0;
+        cfg.ent1_hi = 0xffffffffu;
+        DevCfg ecfg = cfg;
+        ecfg.stats = estats;
+        ecfg.count_only = 1;
+        launch_enumerate(ecfg, st);
+        ++passes;
+        unsigned long long wc[3];
+        unsigned int ec[2];
+        CK(cudaMemcpyAsync(wc, wcount, sizeof(wc), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ec, counters + 6, sizeof(ec), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        n_ent2 = ec[0];
+        n_ent1 = ec[1];
+        if (wc[0] > cfg.t1_cap || wc[1] > cfg.stream_cap || wc[2] > cfg.seg_cap) {
+            memcpy(first_wc, wc, sizeof(wc));
+            memcpy(first_ec, ec, sizeof(ec));
+            have_first = true;
+        }  // else the rounds below enumerate again, writing
+    } else {
         cfg.ent2_lo = 0;
         cfg.ent2_hi = 0xffffffffu;
         cfg.ent1_lo = 0;

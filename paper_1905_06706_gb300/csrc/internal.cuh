@@ -132,6 +132,7 @@ struct DevCfg {
     // optional: 0 when a work list of this round overflowed (its entries past the
     // capacity were not written), and the sampling kernels then do nothing
     const unsigned int* lists_ok;
+    uint32_t count_only;         // enumeration: count the work lists, write nothing
     unsigned long long* work64;  // [0] type-I pairs taken, [1] type-II chunks taken
 };
 

@@ -952,7 +952,7 @@ __global__ void __launch_bounds__(kEnumThreads, 4) k_enum2(DevCfg cfg) {
         unsigned long long slot[2];
         block_alloc<2>(want, ctr, slot);
         unsigned long long st_base = slot[0], sg_base = slot[1];
-        if (nst) {
+        if (nst && !cfg.count_only) {
             unsigned long long off[2];
             uint32_t pos[2] = {0u, 0u}, pre[2] = {0u, 0u}, nxt[2] = {0xffffffffu, 0xffffffffu};
             off[0] = sg_base;
@@ -1132,7 +1132,7 @@ __global__ void __launch_bounds__(kEnumThreads) k_enum1(DevCfg cfg) {
         unsigned long long slot[1];
         block_alloc<1>(want, ctr, slot);
         unsigned long long tbase = slot[0];
-        if (nsub) {
+        if (nsub && !cfg.count_only) {
             for_neighbours<DIM>(cfg, x, d, [&](uint32_t B, uint32_t lo, uint32_t len) {
                 uint32_t ac, bc, na;
                 split(len, &ac, &bc, &na);
