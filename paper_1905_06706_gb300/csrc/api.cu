@@ -626,7 +626,9 @@ void run_sampler(Problem& P, const Layout& Lo, Scratch& S, cudaStream_t st, Time
     const uint64_t seg_per_v = d == 1 ? 8 : d == 2 ? 28 : d == 3 ? 112 : d == 4 ? 448 : 4 * (uint64_t)n6;
     const uint64_t est_seg = (uint64_t)n * seg_per_v + 65536;
     uint64_t seg_cap = tzero ? 1024 : clamp_cap(est_seg, 1ull << 31);
-    const bool count_first = list_scale == 1.0 && (est_t1 > (1ull << 30) || (!tzero && est_seg > (1ull << 31)));
+    bool count_first = list_scale == 1.0 && (est_t1 > (1ull << 30) || (!tzero && est_seg > (1ull << 31)));
+    // GIRG_COUNT_FIRST=1 forces it (tests drive that path at small n with shrunk lists)
+    if (const char* env = std::getenv("GIRG_COUNT_FIRST")) count_first = env[0] == '1';
     T1Item* t1 = S.get<T1Item>(t1_cap);
     uint32_t* t1_pairs = S.get<uint32_t>(t1_cap + 1);
     Stream* streams = S.get<Stream>(stream_cap);

@@ -195,12 +195,15 @@ def test_level_cap_keeps_parity(lcap):
     assert _generate_from(X, w, T, c, 3, gg.PRECISION_FP32, level_cap=lcap) == O.edge_set(ref.edges)
 
 
+@pytest.mark.parametrize("count_first", [False, True])
 @pytest.mark.parametrize("d,T,n", [(1, 0.7, 20_000), (2, 0.5, 20_000), (2, 0.0, 20_000),
                                    (3, 0.3, 10_000)])
-def test_worklist_growth_keeps_parity(d, T, n, monkeypatch):
+def test_worklist_growth_keeps_parity(d, T, n, count_first, monkeypatch):
     """Initial work lists far too small: the first sampling round overflows, is undone
-    (statistics and edge count restored) and the enumeration reruns with grown lists;
-    the graph is the same edge for edge and its statistics are those of one pass."""
+    (statistics and edge count restored) and the enumeration reruns with grown lists --
+    or, with count_first, a first enumeration only counts the lists and the rounds are
+    planned from its counts; the graph is the same edge for edge and its statistics are
+    those of one pass."""
     w, X = O.girg_points(n, d, 2.4, 1.0, 60 + d)
     W = O.exact_sum(w)
     c = O.girg_solve_c(9.0, w, d, T, W)
@@ -209,6 +212,8 @@ def test_worklist_growth_keeps_parity(d, T, n, monkeypatch):
     st0 = gg.last_stats()
     assert st0["enum_passes"] == 1
     monkeypatch.setenv("GIRG_INITIAL_LIST_SCALE", "0.001")
+    if count_first:
+        monkeypatch.setenv("GIRG_COUNT_FIRST", "1")
     got = _generate_from(X, w, T, c, 4, gg.PRECISION_FP32)
     st = gg.last_stats()
     assert st["enum_passes"] > 1
