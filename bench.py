@@ -282,12 +282,13 @@ def run_batched(gg, torch, k: int, workers_grid=(4, 8, 16)) -> dict:
     for q, v in zip(reqs[:8], views[:8]):
         gg.girg_generate(v, **q)
     torch.cuda.synchronize()
-    service, edges, bad = [], 0, 0
+    service, edges, bad, launches = [], 0, 0, []
     t_all = time.perf_counter()
     for q, v in zip(reqs, views):
         t0 = time.perf_counter()
         r = gg.girg_generate(v, **q)
         service.append(time.perf_counter() - t0)
+        launches.append(gg.last_stats()["kernel_launches"])
         edges += r.num_edges
         bad += r.status != gg.GIRG_OK
     plain_s = time.perf_counter() - t_all
@@ -372,6 +373,9 @@ def run_batched(gg, torch, k: int, workers_grid=(4, 8, 16)) -> dict:
             "offered_rate_per_s": rate,
             "plain": {"edges_per_s": edges / plain_s, "seconds": plain_s,
                       "p50_ms": _pct(plain_lat, 0.5) * 1e3, "p99_ms": _pct(plain_lat, 0.99) * 1e3,
+                      "kernel_launches_per_request": {
+                          "mean": sum(launches) / max(1, len(launches)),
+                          "min": min(launches, default=0), "max": max(launches, default=0)},
                       "note": "one girg_generate call at a time; latencies measured under the "
                               "first of the server's Poisson arrival sequences (offered load "
                               f"{BATCH['offered_load']}x the one-at-a-time capacity, so the "
