@@ -380,7 +380,10 @@ void launch_min_weight(int64_t n, const double* w, unsigned long long* out, cuda
     k_min_weight<<<grid_for(n, 256, device_sms() * 8), 256, 0, st>>>(n, w, out);
 }
 
-int reduce_blocks(int64_t n) { return grid_for(n, 256, 1216); }
+// At least eight weights a thread: each block ends in FP64 shuffle trees (four of them in
+// the split), which cost as much as the weights themselves on the slow FP64 pipes when a
+// thread holds only a few; at most 1216 blocks, enough loads in flight at large n.
+int reduce_blocks(int64_t n) { return grid_for((n + 7) / 8, 256, 1216); }
 
 void launch_reduce(int64_t n, const double* w, const double* r, double w_min, int E0,
                    double* part_s2, Reduce* out, cudaStream_t st, const ThresholdJob* job) {

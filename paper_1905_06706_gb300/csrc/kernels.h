@@ -57,8 +57,9 @@ struct HrgYRule {
 void launch_hrg_dist_cdf(double alpha, double R, const HrgYRule& Y, const double* d_ts, int nt,
                          double* d_g, cudaStream_t st);
 // Blocks of the reduction (one per-block partial each): a fixed partition of the
-// vertices, independent of the device, so that the sums finished in block order
-// round the same way on every GPU.
+// vertices (a function of n alone, at least eight weights a thread up to 1216 blocks),
+// independent of the device, so that the sums finished in block order round the same
+// way on every GPU.
 int reduce_blocks(int64_t n);
 // part_s2 (reduce_blocks(n) doubles, or null): per-block sums of w^2.  With job (and
 // part_s2), the last block also finishes red->s2 in block order and writes the split
